@@ -1,0 +1,205 @@
+"""Pins for the oracle's dense dual step, GA, Nystrom/PCG and line search.
+
+The checks use identities the paper proves (push-through / primal-dual
+equivalence, Thm. 3.1 and Prop. 3.2; KKT conditions, App. A.1), textbook
+closed forms (SVD, stacked least squares) and library routines for special
+cases, so that a dropped term, a wrong sign or a transposed operand fails.
+"""
+import numpy as np
+import pytest
+
+from oracle import linesearch, mlp, nystrom, residual as res, step
+from paper_2505_21404_gb300 import workloads
+
+
+def _rng(s):
+    return np.random.default_rng(s)
+
+
+def _tiny_problem(seed=0, widths=(3, 6, 5, 1), n_int=6, n_bnd=4):
+    widths = list(widths)
+    prob = res.poisson_problem(widths, n_int, n_bnd)
+    X = np.concatenate([_rng(seed).uniform(size=(n_int, widths[0])),
+                        _rng(seed + 1).uniform(size=(n_bnd, widths[0]))])
+    tgt = _rng(seed + 2).normal(size=n_int + n_bnd)
+    th = _rng(seed + 3).normal(0, 0.7, size=mlp.n_params(widths))
+    return prob, X, tgt, th
+
+
+# -- linear algebra building blocks ------------------------------------------
+
+def test_textbook_cholesky_and_solves_match_library():
+    A = _rng(1).normal(size=(30, 40))
+    K = A @ A.T + 1e-3 * np.eye(30)
+    L = step.cholesky(K)
+    assert np.allclose(L, np.linalg.cholesky(K), rtol=1e-12, atol=1e-12)
+    assert np.allclose(np.triu(L, 1), 0.0)
+    b = _rng(2).normal(size=30)
+    x = step.chol_solve(L, b)
+    assert np.allclose(x, np.linalg.solve(K, b), rtol=1e-10, atol=1e-12)
+    assert np.allclose(L @ step.forward_subst(L, b), b, atol=1e-12)
+    assert np.allclose(L.T @ step.back_subst_t(L, b), b, atol=1e-12)
+
+
+def test_cholesky_reports_failing_column():
+    K = np.eye(5)
+    K[3, 3] = -1.0
+    with pytest.raises(step.NotSPD) as e:
+        step.cholesky(K)
+    assert e.value.column == 3
+
+
+# -- the step itself -----------------------------------------------------------
+
+@pytest.mark.parametrize("lam", [1e-1, 1e-3])
+def test_dual_step_equals_primal_svd_and_stacked_least_squares(lam):
+    """Push-through identity (J^T J + lam I)^{-1} J^T r = J^T (J J^T + lam I)^{-1} r
+    (Sec. 3.1, Thm. 3.1) checked four ways on a tiny well-conditioned case."""
+    prob, X, tgt, th = _tiny_problem(seed=10)
+    out = step.dense_step(th, prob, X, tgt, lam, use_ga=False)
+    J, r, v = out["J"], out["r"], out["v"]
+    # (1) primal normal equations (Prop. 3.1)
+    vp = step.primal_step(J, r, lam)
+    # (2) SVD closed form: -V diag(s/(s^2+lam)) U^T r
+    U, s, Vt = np.linalg.svd(J, full_matrices=False)
+    vs = -(Vt.T @ ((s / (s * s + lam)) * (U.T @ r)))
+    # (3) stacked least squares [J; sqrt(lam) I] d = [-r; 0]
+    A = np.vstack([J, np.sqrt(lam) * np.eye(J.shape[1])])
+    vq = np.linalg.lstsq(A, np.concatenate([-r, np.zeros(J.shape[1])]), rcond=None)[0]
+    # (4) the paper's literal recovery (Thm. 3.1)
+    vl, _ = step.dense_step_literal(J, r, lam)
+    scale = np.linalg.norm(vs)
+    for other in (vp, vq, vl):
+        assert np.linalg.norm(v - other) <= 1e-10 * scale
+
+
+def test_kkt_conditions_of_the_step():
+    """Optimality of F_lambda (App. A.1): J^T (r + J d) + lam d = 0."""
+    prob, X, tgt, th = _tiny_problem(seed=20, widths=(2, 8, 8, 1), n_int=12, n_bnd=8)
+    lam = 1e-4
+    out = step.dense_step(th, prob, X, tgt, lam, use_ga=False)
+    J, r, d = out["J"], out["r"], out["v"]
+    g = J.T @ (r + J @ d) + lam * d
+    assert np.linalg.norm(g) <= 1e-9 * np.linalg.norm(J.T @ r)
+    # dual variables: y = J d solves (K + lam I) y = -K r (Thm. 3.1 with grad L = J^T r)
+    y = J @ d
+    K = J @ J.T
+    assert np.linalg.norm((K + lam * np.eye(K.shape[0])) @ y + K @ r) <= 1e-9 * np.linalg.norm(K @ r)
+
+
+def test_ga_primal_dual_equivalence():
+    """Prop. 3.2: (J^T J + lam I) a = -J^T f_vv equals the dual form, and the
+    literal dual recovery agrees at moderate lambda."""
+    prob, X, tgt, th = _tiny_problem(seed=30)
+    lam = 1e-2
+    out = step.dense_step(th, prob, X, tgt, lam, use_ga=True)
+    J, fvv, a = out["J"], out["fvv"], out["a"]
+    ap = np.linalg.solve(J.T @ J + lam * np.eye(J.shape[1]), -(J.T @ fvv))
+    _, al = step.dense_step_literal(J, out["r"], lam, fvv)
+    assert np.linalg.norm(a - ap) <= 1e-10 * np.linalg.norm(ap)
+    assert np.linalg.norm(a - al) <= 1e-8 * np.linalg.norm(ap)
+    # f_vv is taken along v (the un-line-searched velocity)
+    assert np.allclose(fvv, res.second_directional(th, prob, X, tgt, out["v"]))
+
+
+def test_ga_acceptance_rule():
+    v = np.array([3.0, 4.0])                  # ||v|| = 5
+    d, ratio, acc = step.ga_accept(v, np.array([0.0, 1.25]))   # 2*1.25/5 = 0.5
+    assert acc and ratio == 0.5 and np.allclose(d, [3.0, 4.625])
+    d, ratio, acc = step.ga_accept(v, np.array([0.0, 1.26]))
+    assert not acc and np.allclose(d, v)
+    d, ratio, acc = step.ga_accept(np.zeros(2), np.ones(2))
+    assert not acc and np.allclose(d, 0.0)
+    d, ratio, acc = step.ga_accept(v, np.array([0.0, 0.1]), eps_norm=6.0)
+    assert not acc
+
+
+def test_linear_residual_gives_zero_acceleration_and_exact_least_squares():
+    """If r is affine in theta (only output-layer parameters move), f_vv = 0
+    so a = 0, and with lam -> 0 one step solves the least-squares problem."""
+    prob, X, tgt, th = _tiny_problem(seed=40, widths=(2, 12, 1), n_int=5, n_bnd=3)
+    r, J = res.residual_and_jacobian(th, prob, X, tgt)
+    nout = 13
+    Jo = J[:, -nout:]                          # output-layer block
+    lam = 1e-12
+    alpha = step.chol_solve(step.cholesky(Jo @ Jo.T + lam * np.eye(Jo.shape[0])), r)
+    v = np.zeros(th.size)
+    v[-nout:] = -(Jo.T @ alpha)
+    assert np.max(np.abs(res.second_directional(th, prob, X, tgt, v))) < 1e-12
+    # m = 8 < 13 unknowns: the affine residual is driven to zero
+    r_new = res.residual(th + v, prob, X, tgt)
+    assert np.linalg.norm(r_new) <= 1e-6 * np.linalg.norm(r)
+
+
+def test_dense_step_on_benchmark_workload_reduces_loss():
+    """Convergence on the 2-D manufactured solution: a few D-NGD steps from
+    the same seeded start lower the loss monotonically (line search on)."""
+    wl = workloads.poisson_sine(2, [2, 10, 10, 1], 60, 20, k=1, seed=0, lam=1e-8)
+    prob = res.problem_from_spec(wl)
+    th = wl["theta"].copy()
+    losses = [res.loss(th, prob, wl["X"], wl["target"])]
+    for _ in range(12):
+        lam = min(losses[-1], 1e-5)            # lambda_k = min(loss, 1e-5), App. A.3
+        out = step.dense_step(th, prob, wl["X"], wl["target"], lam, use_ga=True)
+        eta, _ = linesearch.line_search(th, prob, wl["X"], wl["target"], out["delta"])
+        th = th + eta * out["delta"]
+        losses.append(res.loss(th, prob, wl["X"], wl["target"]))
+    assert all(b < a for a, b in zip(losses, losses[1:]))
+    assert losses[-1] < 1e-4 * losses[0]
+
+
+# -- Nystrom + PCG -----------------------------------------------------------
+
+def test_nystrom_exact_with_all_landmarks_and_pcg_one_iteration():
+    """With ell = m landmarks the Nystrom approximation is exact, so
+    P^{-1} = (K + lam I)^{-1} and PCG stops after one iteration."""
+    J = _rng(50).normal(size=(25, 60))
+    lam = 1e-3
+    U, lh = nystrom.nystrom(J, np.arange(25))
+    K = J @ J.T
+    assert np.allclose(U @ np.diag(lh) @ U.T, K, rtol=1e-10, atol=1e-10 * np.abs(K).max())
+    Pinv = np.stack([nystrom.precond_apply(U, lh, lam, e) for e in np.eye(25)], 1)
+    assert np.allclose(Pinv, np.linalg.inv(K + lam * np.eye(25)), rtol=1e-8, atol=1e-8)
+    b = _rng(51).normal(size=25)
+    y, it, ok, _ = nystrom.pcg(J, lam, b, U, lh, 1e-10, 50)
+    assert ok and it == 1
+    assert np.allclose(y, np.linalg.solve(K + lam * np.eye(25), b), rtol=1e-9)
+
+
+def test_nystrom_low_rank_is_eigendecomposition_of_column_sampled_kernel():
+    """K_hat = K_{:,I} K_II^+ K_{I,:} (column-sampling Nystrom) equals
+    U Lambda_hat U^T, U has orthonormal columns."""
+    J = _rng(60).normal(size=(40, 30))
+    I = np.sort(_rng(61).permutation(40)[:12])
+    U, lh = nystrom.nystrom(J, I)
+    K = J @ J.T
+    Khat = K[:, I] @ np.linalg.pinv(K[np.ix_(I, I)]) @ K[I, :]
+    assert np.allclose(U @ np.diag(lh) @ U.T, Khat, atol=1e-9 * np.abs(K).max())
+    assert np.allclose(U.T @ U, np.eye(U.shape[1]), atol=1e-12)
+
+
+def test_pcg_matches_dense_solve_with_partial_sketch():
+    prob, X, tgt, th = _tiny_problem(seed=70, widths=(2, 16, 16, 1), n_int=48, n_bnd=16)
+    lam = 1e-5
+    lm = workloads.landmarks(64, 16, seed=3)
+    out = nystrom.pcg_step(th, prob, X, tgt, lam, lm, tol=1e-12, max_it=400, use_ga=True)
+    ref = step.dense_step(th, prob, X, tgt, lam, use_ga=True)
+    assert all(out["converged"])
+    for key in ("alpha", "v", "a", "delta"):
+        assert np.linalg.norm(out[key] - ref[key]) <= 1e-6 * np.linalg.norm(ref[key]), key
+
+
+# -- line search ----------------------------------------------------------------
+
+def test_line_search_grid_and_tie_rule():
+    g = linesearch.grid()
+    assert g.size == 31 and g[0] == 1.0 and g[-1] == 2.0 ** -30
+    assert np.all(np.diff(g) < 0)
+    # on a quadratic in eta the grid minimiser is the grid point closest in loss
+    prob, X, tgt, th = _tiny_problem(seed=80, widths=(2, 4, 1), n_int=3, n_bnd=2)
+    out = step.dense_step(th, prob, X, tgt, 1e-2, use_ga=False)
+    eta, losses = linesearch.line_search(th, prob, X, tgt, out["delta"])
+    assert losses[list(g).index(eta)] == losses.min()
+    # zero step: every loss ties, the largest eta wins
+    eta0, _ = linesearch.line_search(th, prob, X, tgt, np.zeros(th.size))
+    assert eta0 == 1.0
