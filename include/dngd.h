@@ -1,0 +1,210 @@
+/*
+ * dngd.h - C ABI of the GB300 (sm_103a) Dual Natural Gradient Descent step.
+ *
+ * The library computes one damped Gauss-Newton (Levenberg-Marquardt) step of
+ * a tanh-MLP physics-informed network in residual space, as defined by
+ * Jnini & Vella, "Dual Natural Gradient Descent for Scalable Training of
+ * Physics-Informed Neural Networks" (TMLR 2025):
+ *
+ *   residuals r(theta) in R^m, classes scaled by 1/sqrt(N_gamma)   (Sec. 2.2)
+ *   Jacobian  J = dr/dtheta in R^{m x n}                            (Sec. 2.2)
+ *   residual Gramian K = J J^T                                      (Def. 3.1)
+ *   dual system (K + lambda I) alpha = r, v = -J^T alpha            (Thm. 3.1,
+ *        push-through form of Eq. dual-system / dual-recovery)
+ *   geodesic acceleration: f_vv = d^2/dt^2 r(theta + t v), (K + lambda I)
+ *        beta = f_vv, a = -J^T beta, accept v + a/2 when 2||a||/||v|| <= 0.5
+ *                                  (Sec. 3.2, Prop. 3.2, Alg. DenseDualSolve)
+ *   Nystrom-preconditioned CG for large m                       (Sec. 3.3,
+ *        Eq. spec_precond_nystrom_main_final, Alg. PCGStep)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - theta layout: for each affine layer l in order, W_l [w_l x w_{l-1}]
+ *   row-major followed by b_l [w_l].  Hidden layers use tanh, the output
+ *   layer (width 1) is affine.
+ * - X is [m x d_in] row-major float64; rows are grouped by residual class in
+ *   the order of dngd_problem_desc.classes.  target is [m] float64.
+ * - The step returned in delta_out is the increment to ADD to theta.
+ * - Unless a function says otherwise, pointer arguments may be device
+ *   pointers (used in place) or host pointers (pageable or pinned; the
+ *   library stages them through its own device buffers).  The caller owns
+ *   every pointer it passes.  The library owns its workspace, allocated in
+ *   dngd_create.
+ * - All device work is ordered on the stream given to dngd_create.  A call
+ *   returns after the work is enqueued, except where it must read a result
+ *   on the host (dngd_step with info != NULL, host output pointers), in which
+ *   case it synchronises that stream.
+ * - Errors: functions return DNGD_OK (0) or a negative dngd_status.  Device
+ *   side failures (non-SPD pivot, non-finite values, bounded-wait timeouts)
+ *   are recorded in a device status word and reported by the next call that
+ *   synchronises.  No entry point traps the GPU.
+ */
+#ifndef DNGD_H
+#define DNGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int dngd_status;
+
+enum {
+  DNGD_OK = 0,
+  DNGD_ERR_INVALID_ARG = -1,  /* bad descriptor, size or pointer */
+  DNGD_ERR_NOT_SPD = -2,      /* Cholesky pivot <= 0; info->not_spd_column */
+  DNGD_ERR_NO_CONVERGE = -3,  /* CG / refinement hit its iteration cap */
+  DNGD_ERR_NONFINITE = -4,    /* NaN/Inf in r, K, the factor or the step */
+  DNGD_ERR_BUDGET = -5,       /* serving admission refused (HBM budget) */
+  DNGD_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+  DNGD_ERR_CUDA = -7,         /* CUDA runtime/driver error */
+  DNGD_ERR_STATE = -8,        /* call out of order (e.g. solve before step) */
+  DNGD_ERR_OOM = -9           /* device allocation failed */
+};
+
+enum dngd_precision {
+  DNGD_FP64 = 0,        /* every stage in float64 */
+  DNGD_MIXED_BF16 = 1,  /* FP32 jets/J, BF16 tensor-core Gram (FP32 accum),
+                           FP32 Cholesky of K + (lambda+mu) I with FP64
+                           diagonal blocks, PCG refinement on the FP32-J
+                           operator with double-float accumulation */
+  DNGD_MIXED_TF32 = 2   /* as MIXED_BF16 with a TF32 tensor-core Gram */
+};
+
+enum dngd_solver { DNGD_DENSE = 0, DNGD_PCG = 1 };
+
+#define DNGD_MAX_LAYERS 12
+#define DNGD_MAX_DIM 8
+#define DNGD_MAX_CLASSES 4
+
+/* One residual class gamma (Sec. 2.2): N_gamma points and the linear
+ * operator Op u = c_val u + sum_k c_grad[k] d_k u + c_lap sum_{k: lap_mask[k]} d_kk u.
+ * The class residual is (Op u(x_i) - target_i) / sqrt(count). */
+typedef struct {
+  int count;
+  double c_val;
+  double c_grad[DNGD_MAX_DIM];
+  double c_lap;
+  int lap_mask[DNGD_MAX_DIM];
+} dngd_class_desc;
+
+typedef struct {
+  int n_layers;                      /* affine layers (hidden + output), >= 1 */
+  int widths[DNGD_MAX_LAYERS + 1];   /* widths[0] = d_in, widths[n_layers] = 1 */
+  int n_classes;
+  dngd_class_desc classes[DNGD_MAX_CLASSES];
+  int precision;                     /* enum dngd_precision */
+  int solver;                        /* enum dngd_solver */
+  double lambda;                     /* Levenberg-Marquardt damping, > 0 */
+  int use_ga;                        /* geodesic acceleration on/off */
+  double eps_norm;                   /* GA guard: accept only if ||v|| > eps_norm */
+  double ga_ratio_max;               /* GA threshold on 2||a||/||v|| (paper: 0.5) */
+  /* mixed precision refinement (ignored for DNGD_FP64) */
+  int refine_max_it;                 /* PCG iterations per solve, e.g. 200 */
+  double refine_tol;                 /* stop at ||rhs - A x|| <= tol ||rhs|| */
+  double shift_mu;                   /* extra diagonal shift of the factored
+                                        preconditioner K_lowp + (lambda+mu) I */
+  /* matrix-free PCG solver (DNGD_PCG) */
+  int pcg_rank;                      /* landmarks ell */
+  double pcg_tol;
+  int pcg_max_it;
+  uint64_t pcg_seed;                 /* landmark permutation seed */
+  int keep_gram;                     /* keep K + lambda I for dngd_get_stage(6)
+                                        (debug; one extra m x m buffer) */
+} dngd_problem_desc;
+
+typedef struct {
+  double loss;              /* 1/2 ||r(theta)||^2 */
+  double norm_v;            /* ||v|| */
+  double norm_a;            /* ||a|| (0 when GA is off) */
+  double ga_ratio;          /* 2||a||/||v|| */
+  int ga_accepted;
+  int solve_iters[2];       /* CG/refinement iterations for r and for f_vv */
+  double solve_relres[2];   /* final ||rhs - A x|| / ||rhs|| */
+  int not_spd_column;       /* failing pivot column, or -1 */
+  int device_status;        /* raw device status word */
+  float phase_ms[8];        /* jets+J, Gram, factor, solve r, f_vv, solve f_vv,
+                               finish, total (filled when timing is enabled) */
+} dngd_step_info;
+
+typedef struct dngd_ctx dngd_ctx;
+
+/* Human-readable message for a status code. */
+const char* dngd_status_string(dngd_status s);
+
+/* Library version string. */
+const char* dngd_version(void);
+
+/* Number of parameters n of the MLP described by desc (Sec. 2.1 layout). */
+int64_t dngd_num_params(const dngd_problem_desc* desc);
+
+/* Create a step context for one problem shape.  Allocates the workspace
+ * (J, K / factor, jet buffers, Krylov vectors) with cudaMalloc on the current
+ * device.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: INVALID_ARG for an inconsistent descriptor, OOM, CUDA. */
+dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* stream);
+
+/* Device bytes dngd_create would allocate for desc. */
+dngd_status dngd_workspace_bytes(const dngd_problem_desc* desc, size_t* bytes);
+
+dngd_status dngd_destroy(dngd_ctx* ctx);
+
+/* Enable (1) or disable (0) per-phase CUDA-event timing in dngd_step_info. */
+dngd_status dngd_set_timing(dngd_ctx* ctx, int enable);
+
+/* Override the damping lambda for the following calls (the paper's rule
+ * lambda_k = min(L, cap) changes it every step). */
+dngd_status dngd_set_lambda(dngd_ctx* ctx, double lambda);
+
+/* One D-NGD step (Alg. DenseDualSolve or PCGStep; push-through recovery).
+ *   theta [n], X [m x d_in], target [m]: inputs (float64).
+ *   delta_out [n]: the step to add to theta (float64).
+ *   info: optional (NULL allowed); when given, the call synchronises the
+ *   stream and fills it.
+ * Keeps r, J, the factor / preconditioner and v for dngd_solve and the
+ * stage accessors below until the next step. */
+dngd_status dngd_step(dngd_ctx* ctx, const double* theta, const double* X, const double* target,
+                      double* delta_out, dngd_step_info* info);
+
+/* Solve (K + lambda I) x = rhs with the factor / preconditioner of the last
+ * dngd_step (Remark 3.1: the GA solve reuses the same operator).
+ * rhs [m] -> x [m], float64.  Errors: STATE if no step was taken. */
+dngd_status dngd_solve(dngd_ctx* ctx, const double* rhs, double* x_out);
+
+/* Loss L(theta + eta_j delta) = 1/2 ||r||^2 for k step sizes (the line search
+ * of Alg. D-NGD Workflow).  etas [k] host array; loss_out [k] host array.
+ * delta may be NULL (then every entry is L(theta)).  Synchronises. */
+dngd_status dngd_loss(dngd_ctx* ctx, const double* theta, const double* X, const double* target,
+                      const double* delta, const double* etas, int k, double* loss_out);
+
+/* Grid line search and update: picks eta* = argmin over etas of
+ * L(theta + eta delta) (first minimum in the given order) and writes
+ * theta_out = theta + eta* delta.  theta_out may alias theta.  eta_out host. */
+dngd_status dngd_line_search(dngd_ctx* ctx, const double* theta, const double* X, const double* target,
+                             const double* delta, const double* etas, int k, double* theta_out,
+                             double* eta_out);
+
+/* Residuals and Jacobian at theta (Sec. 2.2) through the step's own kernels
+ * and precision.  r_out [m] float64; J_out [m x n] row-major float64 or NULL. */
+dngd_status dngd_residual_jacobian(dngd_ctx* ctx, const double* theta, const double* X,
+                                   const double* target, double* r_out, double* J_out);
+
+/* Second directional derivative f_vv = d^2/dt^2 r(theta + t v)|_0 (Sec. 3.2)
+ * through the step's f_vv kernel.  v [n] -> fvv_out [m], float64. */
+dngd_status dngd_fvv(dngd_ctx* ctx, const double* theta, const double* X, const double* target,
+                     const double* v, double* fvv_out);
+
+/* Stage outputs of the last dngd_step, copied to dst (host or device):
+ * which = 0 r [m], 1 alpha [m], 2 v [n], 3 f_vv [m], 4 beta [m], 5 a [n],
+ *         6 lower triangle of K + lambda I [m x m] row-major (dense, before
+ *           factorisation; the upper triangle is left as zero),
+ *         7 Cholesky factor L [m x m] row-major (dense solver).
+ * Values are converted to float64. */
+dngd_status dngd_get_stage(dngd_ctx* ctx, int which, double* dst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DNGD_H */

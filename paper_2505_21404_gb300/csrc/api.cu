@@ -1,0 +1,792 @@
+// C ABI of the D-NGD step: context set-up, workspace, and the step pipeline
+//   jets + J  ->  Gram K + lambda I  ->  factor  ->  alpha  ->  v = -J^T alpha
+//   -> f_vv  ->  beta (same factor / preconditioner)  ->  a  ->  GA test  ->  delta
+// following Alg. DenseDualSolve of the paper (push-through recovery).
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "step_kernels.h"
+
+using namespace dngd;
+
+struct dngd_ctx {
+  dngd_problem_desc desc;
+  NetInfo net;
+  cudaStream_t st = nullptr;
+  int m = 0, R = 0;
+  long long n = 0;
+  int prec = 0;
+  double lambda = 0.0;
+  bool timing = false;
+  bool have_step = false;
+  std::vector<void*> allocs;
+
+  // staging for host inputs / outputs
+  double *theta_s = nullptr, *X_s = nullptr, *target_s = nullptr, *nvec_s = nullptr, *mvec_s = nullptr;
+  double* theta_tmp = nullptr;  // line search
+  float *theta32 = nullptr, *v32 = nullptr;
+
+  // jets
+  void* Z[kMaxLayers] = {};
+  void* H[kMaxLayers] = {};
+  void* D[kMaxLayers] = {};
+  void* Hbar = nullptr;
+  void *Z3 = nullptr, *H3a = nullptr, *H3b = nullptr;
+
+  // Jacobian and Gram
+  void* J = nullptr;
+  long long ldJ = 0;
+  __nv_bfloat16* Jb = nullptr;
+  long long ldb = 0;
+  void* K = nullptr;
+  long long ldk = 0;
+  void* Kcopy = nullptr;
+  float* Linv = nullptr;
+  float* trtri_work = nullptr;
+  float* gram_partials = nullptr;
+  size_t gram_partial_bytes = 0;
+  GramPlan* gram = nullptr;
+
+  // vectors
+  double *r = nullptr, *alpha = nullptr, *v = nullptr, *fvv = nullptr, *beta = nullptr, *a = nullptr,
+         *delta = nullptr;
+  double *cg_res = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *cg_u = nullptr,
+         *cg_y = nullptr, *xsol = nullptr;
+  double* partials = nullptr;
+  double* dot_partials = nullptr;
+  double* scal = nullptr;
+  double* scal_h = nullptr;  // pinned
+  int* status = nullptr;
+  int* status_h = nullptr;  // pinned
+  int iters[2] = {0, 0};
+  double relres[2] = {0.0, 0.0};
+  cudaEvent_t ev[9] = {};
+};
+
+namespace {
+
+constexpr const char* kVersion = "dngd-gb300 0.1 (sm_103a)";
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+dngd_status dalloc(dngd_ctx* c, T** p, size_t count) {
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return DNGD_ERR_OOM;
+  }
+  c->allocs.push_back(q);
+  *p = (T*)q;
+  return DNGD_OK;
+}
+
+long long round_up(long long a, long long b) { return ((a + b - 1) / b) * b; }
+
+dngd_status build_net(const dngd_problem_desc* d, NetInfo* net) {
+  memset(net, 0, sizeof(*net));
+  if (d->n_layers < 1 || d->n_layers > kMaxLayers) return DNGD_ERR_INVALID_ARG;
+  if (d->widths[0] < 1 || d->widths[0] > kMaxDim) return DNGD_ERR_INVALID_ARG;
+  if (d->widths[d->n_layers] != 1) return DNGD_ERR_INVALID_ARG;
+  if (d->n_classes < 1 || d->n_classes > kMaxClasses) return DNGD_ERR_INVALID_ARG;
+  net->n_layers = d->n_layers;
+  net->d_in = d->widths[0];
+  long long off = 0;
+  int maxw = 1;
+  for (int l = 0; l <= d->n_layers; ++l) {
+    if (d->widths[l] < 1 || d->widths[l] > 65536) return DNGD_ERR_INVALID_ARG;
+    net->widths[l] = d->widths[l];
+  }
+  for (int l = 0; l < d->n_layers; ++l) {
+    net->w_off[l] = off;
+    off += (long long)d->widths[l + 1] * d->widths[l];
+    net->b_off[l] = off;
+    off += d->widths[l + 1];
+    if (l + 1 < d->n_layers) maxw = d->widths[l + 1] > maxw ? d->widths[l + 1] : maxw;
+  }
+  net->n = off;
+  net->max_w = maxw;
+  int p0 = 0, row0 = 0;
+  for (int c = 0; c < d->n_classes; ++c) {
+    const dngd_class_desc& cd = d->classes[c];
+    if (cd.count < 1) return DNGD_ERR_INVALID_ARG;
+    ClassInfo& ci = net->cls[c];
+    ci.p0 = p0;
+    ci.count = cd.count;
+    ci.c_val = cd.c_val;
+    ci.c_lap = cd.c_lap;
+    ci.scale = 1.0 / sqrt((double)cd.count);
+    ci.nD = 0;
+    bool any_lap = false;
+    for (int k = 0; k < net->d_in; ++k) {
+      const bool lap = cd.lap_mask[k] != 0 && cd.c_lap != 0.0;
+      if (cd.c_grad[k] != 0.0 || lap) {
+        ci.D[ci.nD] = k;
+        ci.c_gradD[ci.nD] = cd.c_grad[k];
+        ci.lapD[ci.nD] = lap ? 1 : 0;
+        ci.nD++;
+      }
+      any_lap = any_lap || lap;
+    }
+    ci.has_lap = any_lap ? 1 : 0;
+    ci.S = 1 + ci.nD + ci.has_lap;
+    ci.row0 = row0;
+    row0 += ci.S * cd.count;
+    p0 += cd.count;
+  }
+  net->n_classes = d->n_classes;
+  net->m = p0;
+  net->R = row0;
+  return DNGD_OK;
+}
+
+struct Sizes {
+  size_t total = 0;
+};
+
+void evrec(dngd_ctx* c, int i) {
+  if (c->timing) cudaEventRecord(c->ev[i], c->st);
+}
+
+// Resolve an input pointer: device pointers are used in place, host pointers
+// are copied into the staging buffer.
+const double* in_ptr(dngd_ctx* c, const double* p, double* stage, size_t count) {
+  if (!p) return nullptr;
+  if (is_device_ptr(p)) return p;
+  cudaMemcpyAsync(stage, p, count * sizeof(double), cudaMemcpyHostToDevice, c->st);
+  return stage;
+}
+
+dngd_status read_status(dngd_ctx* c) {
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->status_h, c->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+  const int s = c->status_h[0];
+  if (s & ST_TIMEOUT) return DNGD_ERR_TIMEOUT;
+  if (s & ST_NOT_SPD) return DNGD_ERR_NOT_SPD;
+  if (s & ST_NONFINITE) return DNGD_ERR_NONFINITE;
+  if (s & ST_NO_CONVERGE) return DNGD_ERR_NO_CONVERGE;
+  return DNGD_OK;
+}
+
+template <typename T>
+LayerPtrs<T> lp(void* const* a) {
+  LayerPtrs<T> r;
+  for (int l = 0; l < kMaxLayers; ++l) r.p[l] = (T*)a[l];
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Residuals + Jacobian in the context's precision
+// ---------------------------------------------------------------------------
+
+template <typename T>
+const T* theta_in_T(dngd_ctx* c, const double* theta);
+template <>
+const double* theta_in_T<double>(dngd_ctx* c, const double* theta) {
+  (void)c;
+  return theta;
+}
+template <>
+const float* theta_in_T<float>(dngd_ctx* c, const double* theta) {
+  to_float(c->n, theta, c->theta32, c->st);
+  return c->theta32;
+}
+
+template <typename T>
+dngd_status forward_only(dngd_ctx* c, const T* thT, const double* X, const double* target, double* r) {
+  return jets_forward<T>(c->net, thT, X, target, lp<T>(c->Z), lp<T>(c->H), r, c->status, c->st);
+}
+
+template <typename T>
+dngd_status residual_jacobian_T(dngd_ctx* c, const T* thT, const double* X, const double* target) {
+  dngd_status s = forward_only<T>(c, thT, X, target, c->r);
+  if (s) return s;
+  return jets_backward_jacobian<T, T>(c->net, thT, X, lp<T>(c->Z), lp<T>(c->H), lp<T>(c->D), (T*)c->Hbar,
+                                      (T*)c->J, c->ldJ, c->prec == DNGD_MIXED_BF16 ? c->Jb : nullptr, c->ldb,
+                                      c->st);
+}
+
+// ---------------------------------------------------------------------------
+// Solves with the factor of the last step
+// ---------------------------------------------------------------------------
+
+// Preconditioner of the mixed path: z = (L L^T)^{-1} q = Linv^T (Linv q).
+dngd_status precond_mixed(dngd_ctx* c, const double* q, double* z) {
+  dngd_status s = gemv_n<float>(c->m, c->m, c->Linv, c->ldk, q, 1.0, c->cg_y, c->st);
+  if (s) return s;
+  return gemv_t<float>(c->m, c->m, c->Linv, c->ldk, c->cg_y, 1.0, z, c->partials, c->st);
+}
+
+// A p = J (J^T p) + lambda p with the FP32 J (double-float accumulation).
+dngd_status apply_A_mixed(dngd_ctx* c, const double* p, double* Ap) {
+  dngd_status s = gemv_t<float>(c->m, (int)c->n, (const float*)c->J, c->ldJ, p, 1.0, c->cg_u, c->partials, c->st);
+  if (s) return s;
+  s = gemv_n<float>(c->m, (int)c->n, (const float*)c->J, c->ldJ, c->cg_u, 1.0, Ap, c->st);
+  if (s) return s;
+  return add_scaled(c->m, c->lambda, p, Ap, c->st);
+}
+
+// PCG on (J J^T + lambda I) x = b preconditioned by the low-precision factor
+// (iterative refinement of the mixed path).
+dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
+  const int m = c->m;
+  double* sc = c->scal;
+  dngd_status s;
+  DNGD_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * m, c->st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->cg_res, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st));
+  DNGD_CUDA_CHECK(cudaMemsetAsync(sc + S_BREAK, 0, sizeof(double), c->st));
+  if ((s = dot_dev(m, b, b, sc + S_BB, c->dot_partials, c->st))) return s;
+  if ((s = precond_mixed(c, c->cg_res, c->cg_z))) return s;
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->cg_p, c->cg_z, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st));
+  if ((s = dot_dev(m, c->cg_res, c->cg_z, sc + S_RHO, c->dot_partials, c->st))) return s;
+  const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
+  const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
+  int it = 0;
+  double rel = 1.0;
+  bool conv = false;
+  for (it = 0; it < maxit;) {
+    if ((s = apply_A_mixed(c, c->cg_p, c->cg_Ap))) return s;
+    if ((s = dot_dev(m, c->cg_p, c->cg_Ap, sc + S_PAP, c->dot_partials, c->st))) return s;
+    if ((s = cg_alpha(sc, c->st))) return s;
+    if ((s = cg_update_x(m, sc, x, c->cg_res, c->cg_p, c->cg_Ap, c->st))) return s;
+    if ((s = dot_dev(m, c->cg_res, c->cg_res, sc + S_RR, c->dot_partials, c->st))) return s;
+    ++it;
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+    DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+    const double bb = c->scal_h[S_BB];
+    rel = bb > 0 ? sqrt(c->scal_h[S_RR] / bb) : 0.0;
+    if (rel <= tol || bb == 0.0) {
+      conv = true;
+      break;
+    }
+    if (c->scal_h[S_BREAK] != 0.0) break;
+    if ((s = precond_mixed(c, c->cg_res, c->cg_z))) return s;
+    if ((s = dot_dev(m, c->cg_res, c->cg_z, sc + S_RHONEW, c->dot_partials, c->st))) return s;
+    if ((s = cg_beta(sc, c->st))) return s;
+    if ((s = cg_update_p(m, sc, c->cg_z, c->cg_p, c->st))) return s;
+  }
+  c->iters[slot] = it;
+  c->relres[slot] = rel;
+  (void)conv;
+  return DNGD_OK;
+}
+
+dngd_status solve_last(dngd_ctx* c, const double* b, double* x, int slot) {
+  if (c->prec == DNGD_FP64) {
+    c->iters[slot] = 0;
+    c->relres[slot] = 0.0;
+    return chol_solve_f64(c->m, (const double*)c->K, c->ldk, b, x, c->st);
+  }
+  return pcg_mixed(c, b, x, slot);
+}
+
+// ---------------------------------------------------------------------------
+// The step
+// ---------------------------------------------------------------------------
+
+template <typename T>
+dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const double* target, dngd_step_info* info) {
+  dngd_status s;
+  const int m = c->m;
+  const int n = (int)c->n;
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+  evrec(c, 0);
+  const T* thT = theta_in_T<T>(c, theta);
+  if ((s = residual_jacobian_T<T>(c, thT, X, target))) return s;
+  evrec(c, 1);
+  // K + lambda I (lower)
+  if (c->prec == DNGD_FP64) {
+    if ((s = gemm_nt<double>(m, m, n, 1.0, (const double*)c->J, c->ldJ, (const double*)c->J, c->ldJ, 0.0,
+                             (double*)c->K, c->ldk, true, c->st)))
+      return s;
+    if ((s = add_diag<double>(m, (double*)c->K, c->ldk, c->lambda, c->st))) return s;
+    if (c->Kcopy)
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(double) * (size_t)m * c->ldk,
+                                      cudaMemcpyDeviceToDevice, c->st));
+  } else {
+    gram_tc_set_shift(c->gram, c->lambda + c->desc.shift_mu);
+    if ((s = gram_tc_run(c->gram, c->status, c->st))) return s;
+    if (c->Kcopy)
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(float) * (size_t)m * c->ldk, cudaMemcpyDeviceToDevice,
+                                      c->st));
+  }
+  evrec(c, 2);
+  // factor
+  if (c->prec == DNGD_FP64) {
+    if ((s = cholesky<double>(m, (double*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
+  } else {
+    if ((s = cholesky<float>(m, (float*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
+    if ((s = trtri_lower_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
+  }
+  // a failed factorisation stops the step here
+  if ((s = read_status(c))) return s;
+  evrec(c, 3);
+  // alpha = (K + lambda I)^{-1} r ; v = -J^T alpha
+  if ((s = solve_last(c, c->r, c->alpha, 0))) return s;
+  if ((s = gemv_t<T>(m, n, (const T*)c->J, c->ldJ, c->alpha, -1.0, c->v, c->partials, c->st))) return s;
+  evrec(c, 4);
+  if (c->desc.use_ga) {
+    const T* vT;
+    if (sizeof(T) == sizeof(double)) {
+      vT = (const T*)c->v;
+    } else {
+      to_float(n, c->v, c->v32, c->st);
+      vT = (const T*)c->v32;
+    }
+    if ((s = jets_fvv<T>(c->net, thT, vT, X, (T*)c->Z3, (T*)c->H3a, (T*)c->H3b, c->fvv, c->st))) return s;
+    evrec(c, 5);
+    if ((s = solve_last(c, c->fvv, c->beta, 1))) return s;
+    if ((s = gemv_t<T>(m, n, (const T*)c->J, c->ldJ, c->beta, -1.0, c->a, c->partials, c->st))) return s;
+    evrec(c, 6);
+  } else {
+    evrec(c, 5);
+    evrec(c, 6);
+  }
+  if ((s = ga_finish(n, c->v, c->a, c->desc.use_ga, c->desc.eps_norm,
+                     c->desc.ga_ratio_max > 0 ? c->desc.ga_ratio_max : 0.5, c->delta, c->scal, c->dot_partials,
+                     c->status, c->st)))
+    return s;
+  if ((s = dot_dev(m, c->r, c->r, c->scal + S_LOSS, c->dot_partials, c->st))) return s;
+  evrec(c, 7);
+  c->have_step = true;
+  (void)info;
+  return DNGD_OK;
+}
+
+dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+  dngd_status s = read_status(c);
+  if (!info) return s;
+  memset(info, 0, sizeof(*info));
+  info->loss = 0.5 * c->scal_h[S_LOSS];
+  info->norm_v = sqrt(c->scal_h[S_NV2]);
+  info->norm_a = sqrt(c->scal_h[S_NA2]);
+  info->ga_ratio = c->scal_h[S_RATIO];
+  info->ga_accepted = c->scal_h[S_ACCEPT] != 0.0;
+  info->solve_iters[0] = c->iters[0];
+  info->solve_iters[1] = c->iters[1];
+  info->solve_relres[0] = c->relres[0];
+  info->solve_relres[1] = c->relres[1];
+  info->device_status = c->status_h[0];
+  info->not_spd_column = (c->status_h[0] & ST_NOT_SPD) ? c->status_h[1] : -1;
+  if (c->timing) {
+    for (int i = 0; i < 7; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+      info->phase_ms[i] = ms;
+    }
+    float tot = 0.f;
+    cudaEventElapsedTime(&tot, c->ev[0], c->ev[7]);
+    info->phase_ms[7] = tot;
+  }
+  return s;
+}
+
+dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
+  const NetInfo& net = c->net;
+  const int m = net.m;
+  const long long n = net.n;
+  const int L = net.n_layers - 1;
+  const bool f64 = c->prec == DNGD_FP64;
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  size_t tot = 0;
+  auto add = [&](size_t b) { tot += (b + 255) & ~(size_t)255; };
+  c->ldJ = f64 ? n : round_up(n, 64);
+  c->ldb = round_up(n, 64);
+  c->ldk = round_up(m, 4);
+  add(sizeof(double) * n);        // theta_s
+  add(sizeof(double) * m * net.d_in);
+  add(sizeof(double) * m);        // target_s
+  add(sizeof(double) * n);        // nvec_s
+  add(sizeof(double) * m);        // mvec_s
+  add(sizeof(double) * n);        // theta_tmp
+  if (!f64) {
+    add(sizeof(float) * n);
+    add(sizeof(float) * n);
+  }
+  for (int l = 0; l < L; ++l) {
+    const size_t b = es * (size_t)net.R * net.widths[l + 1];
+    add(b);
+    add(b);
+    add(b);
+  }
+  const size_t rowbuf = es * (size_t)net.R * net.max_w;
+  add(rowbuf);            // Hbar
+  add(3 * rowbuf);        // Z3
+  add(3 * rowbuf);        // H3a
+  add(3 * rowbuf);        // H3b
+  add(es * (size_t)m * c->ldJ);
+  if (c->prec == DNGD_MIXED_BF16) add(sizeof(__nv_bfloat16) * (size_t)m * c->ldb);
+  add(es * (size_t)m * c->ldk);
+  if (c->desc.keep_gram) add(es * (size_t)m * c->ldk);
+  if (!f64) {
+    add(sizeof(float) * (size_t)m * c->ldk);      // Linv
+    add(sizeof(float) * (size_t)m * m);           // trtri work
+    add(gram_tc_partial_bytes(m, (int)n));
+  }
+  add(sizeof(double) * m * 4 + sizeof(double) * n * 3);
+  add(sizeof(double) * m * 6 + sizeof(double) * n);
+  add(sizeof(double) * (size_t)16 * (n > m ? n : m));
+  add(sizeof(double) * 256 + sizeof(double) * S_COUNT + 16);
+  if (bytes_out) *bytes_out = tot;
+  if (dry) return DNGD_OK;
+
+  dngd_status s;
+#define A_(p, T, cnt) \
+  if ((s = dalloc<T>(c, (T**)&(p), (cnt)))) return s;
+  A_(c->theta_s, double, n);
+  A_(c->X_s, double, (size_t)m * net.d_in);
+  A_(c->target_s, double, m);
+  A_(c->nvec_s, double, n);
+  A_(c->mvec_s, double, m);
+  A_(c->theta_tmp, double, n);
+  if (!f64) {
+    A_(c->theta32, float, n);
+    A_(c->v32, float, n);
+  }
+  for (int l = 0; l < L; ++l) {
+    const size_t cnt = (size_t)net.R * net.widths[l + 1];
+    if (f64) {
+      A_(c->Z[l], double, cnt);
+      A_(c->H[l], double, cnt);
+      A_(c->D[l], double, cnt);
+    } else {
+      A_(c->Z[l], float, cnt);
+      A_(c->H[l], float, cnt);
+      A_(c->D[l], float, cnt);
+    }
+  }
+  const size_t rb = (size_t)net.R * net.max_w;
+  if (f64) {
+    A_(c->Hbar, double, rb);
+    A_(c->Z3, double, 3 * rb);
+    A_(c->H3a, double, 3 * rb);
+    A_(c->H3b, double, 3 * rb);
+    A_(c->J, double, (size_t)m * c->ldJ);
+    A_(c->K, double, (size_t)m * c->ldk);
+    if (c->desc.keep_gram) A_(c->Kcopy, double, (size_t)m * c->ldk);
+  } else {
+    A_(c->Hbar, float, rb);
+    A_(c->Z3, float, 3 * rb);
+    A_(c->H3a, float, 3 * rb);
+    A_(c->H3b, float, 3 * rb);
+    A_(c->J, float, (size_t)m * c->ldJ);
+    DNGD_CUDA_CHECK(cudaMemset(c->J, 0, sizeof(float) * (size_t)m * c->ldJ));
+    if (c->prec == DNGD_MIXED_BF16) {
+      A_(c->Jb, __nv_bfloat16, (size_t)m * c->ldb);
+      DNGD_CUDA_CHECK(cudaMemset(c->Jb, 0, sizeof(__nv_bfloat16) * (size_t)m * c->ldb));
+    }
+    A_(c->K, float, (size_t)m * c->ldk);
+    if (c->desc.keep_gram) A_(c->Kcopy, float, (size_t)m * c->ldk);
+    A_(c->Linv, float, (size_t)m * c->ldk);
+    A_(c->trtri_work, float, (size_t)m * m);
+    c->gram_partial_bytes = gram_tc_partial_bytes(m, (int)n);
+    A_(c->gram_partials, float, c->gram_partial_bytes / sizeof(float));
+  }
+  A_(c->r, double, m);
+  A_(c->alpha, double, m);
+  A_(c->fvv, double, m);
+  A_(c->beta, double, m);
+  A_(c->v, double, n);
+  A_(c->a, double, n);
+  A_(c->delta, double, n);
+  A_(c->cg_res, double, m);
+  A_(c->cg_z, double, m);
+  A_(c->cg_p, double, m);
+  A_(c->cg_Ap, double, m);
+  A_(c->cg_y, double, m);
+  A_(c->xsol, double, m);
+  A_(c->cg_u, double, n);
+  A_(c->partials, double, (size_t)16 * (n > m ? n : m));
+  A_(c->dot_partials, double, 256);
+  A_(c->scal, double, S_COUNT);
+  A_(c->status, int, 4);
+#undef A_
+  DNGD_CUDA_CHECK(cudaMemset(c->a, 0, sizeof(double) * n));
+  DNGD_CUDA_CHECK(cudaMemset(c->scal, 0, sizeof(double) * S_COUNT));
+  DNGD_CUDA_CHECK(cudaMemset(c->status, 0, sizeof(int) * 4));
+  DNGD_CUDA_CHECK(cudaMallocHost(&c->scal_h, sizeof(double) * S_COUNT));
+  DNGD_CUDA_CHECK(cudaMallocHost(&c->status_h, sizeof(int) * 4));
+  if (!f64) {
+    const void* Jlow = c->prec == DNGD_MIXED_BF16 ? (const void*)c->Jb : (const void*)c->J;
+    const long long ld = c->prec == DNGD_MIXED_BF16 ? c->ldb : c->ldJ;
+    s = gram_tc_plan(&c->gram, c->prec == DNGD_MIXED_BF16 ? 0 : 1, Jlow, m, (int)n, ld, (float*)c->K, c->ldk,
+                     c->gram_partials, c->gram_partial_bytes);
+    if (s) return s;
+  }
+  for (int i = 0; i < 9; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
+  return DNGD_OK;
+}
+
+void free_ctx(dngd_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->scal_h) cudaFreeHost(c->scal_h);
+  if (c->status_h) cudaFreeHost(c->status_h);
+  if (c->gram) gram_tc_free(c->gram);
+  for (int i = 0; i < 9; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  delete c;
+}
+
+dngd_status out_copy(dngd_ctx* c, double* dst, const double* src, size_t count) {
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, c->st));
+  if (!is_device_ptr(dst)) DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+  return DNGD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Exported C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char* dngd_status_string(dngd_status s) {
+  switch (s) {
+    case DNGD_OK: return "ok";
+    case DNGD_ERR_INVALID_ARG: return "invalid argument";
+    case DNGD_ERR_NOT_SPD: return "matrix not positive definite";
+    case DNGD_ERR_NO_CONVERGE: return "iteration did not converge";
+    case DNGD_ERR_NONFINITE: return "non-finite value";
+    case DNGD_ERR_BUDGET: return "memory budget exceeded";
+    case DNGD_ERR_TIMEOUT: return "device wait timed out";
+    case DNGD_ERR_CUDA: return "CUDA error";
+    case DNGD_ERR_STATE: return "call out of order";
+    case DNGD_ERR_OOM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+const char* dngd_version(void) { return kVersion; }
+
+int64_t dngd_num_params(const dngd_problem_desc* desc) {
+  NetInfo net;
+  if (!desc || build_net(desc, &net)) return -1;
+  return net.n;
+}
+
+dngd_status dngd_workspace_bytes(const dngd_problem_desc* desc, size_t* bytes) {
+  if (!desc || !bytes) return DNGD_ERR_INVALID_ARG;
+  dngd_ctx tmp;
+  tmp.desc = *desc;
+  dngd_status s = build_net(desc, &tmp.net);
+  if (s) return s;
+  tmp.prec = desc->precision;
+  return alloc_workspace(&tmp, true, bytes);
+}
+
+dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* stream) {
+  if (!out || !desc) return DNGD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (desc->precision < DNGD_FP64 || desc->precision > DNGD_MIXED_TF32) return DNGD_ERR_INVALID_ARG;
+  if (desc->solver != DNGD_DENSE) return DNGD_ERR_INVALID_ARG;
+  if (!(desc->lambda > 0.0)) return DNGD_ERR_INVALID_ARG;
+  dngd_ctx* c = new dngd_ctx();
+  c->desc = *desc;
+  dngd_status s = build_net(desc, &c->net);
+  if (s) {
+    delete c;
+    return s;
+  }
+  c->st = (cudaStream_t)stream;
+  c->m = c->net.m;
+  c->n = c->net.n;
+  c->R = c->net.R;
+  c->prec = desc->precision;
+  c->lambda = desc->lambda;
+  if ((s = alloc_workspace(c, false, nullptr))) {
+    free_ctx(c);
+    return s;
+  }
+  *out = c;
+  return DNGD_OK;
+}
+
+dngd_status dngd_destroy(dngd_ctx* c) {
+  if (!c) return DNGD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->st);
+  free_ctx(c);
+  return DNGD_OK;
+}
+
+dngd_status dngd_set_timing(dngd_ctx* c, int enable) {
+  if (!c) return DNGD_ERR_INVALID_ARG;
+  c->timing = enable != 0;
+  return DNGD_OK;
+}
+
+dngd_status dngd_set_lambda(dngd_ctx* c, double lambda) {
+  if (!c || !(lambda > 0.0)) return DNGD_ERR_INVALID_ARG;
+  c->lambda = lambda;
+  return DNGD_OK;
+}
+
+dngd_status dngd_step(dngd_ctx* c, const double* theta, const double* X, const double* target, double* delta_out,
+                      dngd_step_info* info) {
+  if (!c || !theta || !X || !target || !delta_out) return DNGD_ERR_INVALID_ARG;
+  const double* th = in_ptr(c, theta, c->theta_s, c->n);
+  const double* x = in_ptr(c, X, c->X_s, (size_t)c->m * c->net.d_in);
+  const double* tg = in_ptr(c, target, c->target_s, c->m);
+  c->have_step = false;
+  dngd_status s = c->prec == DNGD_FP64 ? step_T<double>(c, th, x, tg, info) : step_T<float>(c, th, x, tg, info);
+  if (s) {
+    dngd_status ds = read_status(c);
+    if (info) fill_info(c, info);
+    return ds ? ds : s;
+  }
+  if ((s = out_copy(c, delta_out, c->delta, c->n))) return s;
+  if (info) return fill_info(c, info);
+  return DNGD_OK;
+}
+
+dngd_status dngd_solve(dngd_ctx* c, const double* rhs, double* x_out) {
+  if (!c || !rhs || !x_out) return DNGD_ERR_INVALID_ARG;
+  if (!c->have_step) return DNGD_ERR_STATE;
+  const double* b = in_ptr(c, rhs, c->mvec_s, c->m);
+  dngd_status s = solve_last(c, b, c->xsol, 0);
+  if (s) return s;
+  return out_copy(c, x_out, c->xsol, c->m);
+}
+
+dngd_status dngd_residual_jacobian(dngd_ctx* c, const double* theta, const double* X, const double* target,
+                                   double* r_out, double* J_out) {
+  if (!c || !theta || !X || !target || !r_out) return DNGD_ERR_INVALID_ARG;
+  const double* th = in_ptr(c, theta, c->theta_s, c->n);
+  const double* x = in_ptr(c, X, c->X_s, (size_t)c->m * c->net.d_in);
+  const double* tg = in_ptr(c, target, c->target_s, c->m);
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+  dngd_status s;
+  if (c->prec == DNGD_FP64) s = residual_jacobian_T<double>(c, theta_in_T<double>(c, th), x, tg);
+  else s = residual_jacobian_T<float>(c, theta_in_T<float>(c, th), x, tg);
+  if (s) return s;
+  c->have_step = false;
+  if ((s = out_copy(c, r_out, c->r, c->m))) return s;
+  if (J_out) {
+    double* dst = J_out;
+    const bool dev = is_device_ptr(J_out);
+    std::vector<double> tmp;
+    double* dbuf = nullptr;
+    if (!dev) {
+      if (cudaMalloc(&dbuf, sizeof(double) * (size_t)c->m * c->n) != cudaSuccess) return DNGD_ERR_OOM;
+      dst = dbuf;
+    }
+    if (c->prec == DNGD_FP64) s = rows_to_f64<double>(c->m, c->n, (const double*)c->J, c->ldJ, dst, c->st);
+    else s = rows_to_f64<float>(c->m, c->n, (const float*)c->J, c->ldJ, dst, c->st);
+    if (!s && !dev) {
+      cudaMemcpyAsync(J_out, dbuf, sizeof(double) * (size_t)c->m * c->n, cudaMemcpyDeviceToHost, c->st);
+      cudaStreamSynchronize(c->st);
+    }
+    if (dbuf) cudaFree(dbuf);
+    if (s) return s;
+  }
+  return read_status(c);
+}
+
+dngd_status dngd_fvv(dngd_ctx* c, const double* theta, const double* X, const double* target, const double* v,
+                     double* fvv_out) {
+  if (!c || !theta || !X || !v || !fvv_out) return DNGD_ERR_INVALID_ARG;
+  (void)target;
+  const double* th = in_ptr(c, theta, c->theta_s, c->n);
+  const double* x = in_ptr(c, X, c->X_s, (size_t)c->m * c->net.d_in);
+  const double* vv = in_ptr(c, v, c->nvec_s, c->n);
+  dngd_status s;
+  if (c->prec == DNGD_FP64) {
+    s = jets_fvv<double>(c->net, th, vv, x, (double*)c->Z3, (double*)c->H3a, (double*)c->H3b, c->fvv, c->st);
+  } else {
+    const float* t32 = theta_in_T<float>(c, th);
+    to_float(c->n, vv, c->v32, c->st);
+    s = jets_fvv<float>(c->net, t32, c->v32, x, (float*)c->Z3, (float*)c->H3a, (float*)c->H3b, c->fvv, c->st);
+  }
+  if (s) return s;
+  c->have_step = false;
+  return out_copy(c, fvv_out, c->fvv, c->m);
+}
+
+dngd_status dngd_loss(dngd_ctx* c, const double* theta, const double* X, const double* target, const double* delta,
+                      const double* etas, int k, double* loss_out) {
+  if (!c || !theta || !X || !target || !etas || !loss_out || k < 1) return DNGD_ERR_INVALID_ARG;
+  const double* th = in_ptr(c, theta, c->theta_s, c->n);
+  const double* x = in_ptr(c, X, c->X_s, (size_t)c->m * c->net.d_in);
+  const double* tg = in_ptr(c, target, c->target_s, c->m);
+  const double* dl = delta ? in_ptr(c, delta, c->nvec_s, c->n) : nullptr;
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+  std::vector<double> out(k);
+  for (int j = 0; j < k; ++j) {
+    dngd_status s = axpy_to(c->n, th, etas[j], dl, c->theta_tmp, c->st);
+    if (s) return s;
+    if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, x, tg, c->cg_res);
+    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), x, tg, c->cg_res);
+    if (s) return s;
+    if ((s = dot_dev(c->m, c->cg_res, c->cg_res, c->scal + S_LOSS, c->dot_partials, c->st))) return s;
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(&c->scal_h[S_LOSS], c->scal + S_LOSS, sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->st));
+    DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+    loss_out[j] = 0.5 * c->scal_h[S_LOSS];
+  }
+  c->have_step = false;
+  (void)out;
+  return read_status(c);
+}
+
+dngd_status dngd_line_search(dngd_ctx* c, const double* theta, const double* X, const double* target,
+                             const double* delta, const double* etas, int k, double* theta_out, double* eta_out) {
+  if (!c || !theta || !delta || !etas || !theta_out || !eta_out || k < 1) return DNGD_ERR_INVALID_ARG;
+  std::vector<double> losses(k);
+  dngd_status s = dngd_loss(c, theta, X, target, delta, etas, k, losses.data());
+  if (s) return s;
+  int best = 0;
+  for (int j = 1; j < k; ++j)
+    if (losses[j] < losses[best]) best = j;
+  *eta_out = etas[best];
+  const double* th = in_ptr(c, theta, c->theta_s, c->n);
+  const double* dl = in_ptr(c, delta, c->nvec_s, c->n);
+  if ((s = axpy_to(c->n, th, etas[best], dl, c->theta_tmp, c->st))) return s;
+  return out_copy(c, theta_out, c->theta_tmp, c->n);
+}
+
+dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
+  if (!c || !dst) return DNGD_ERR_INVALID_ARG;
+  if (!c->have_step) return DNGD_ERR_STATE;
+  const int m = c->m;
+  switch (which) {
+    case 0: return out_copy(c, dst, c->r, m);
+    case 1: return out_copy(c, dst, c->alpha, m);
+    case 2: return out_copy(c, dst, c->v, c->n);
+    case 3: return out_copy(c, dst, c->fvv, m);
+    case 4: return out_copy(c, dst, c->beta, m);
+    case 5: return out_copy(c, dst, c->a, c->n);
+    case 6:
+    case 7: {
+      const void* src = which == 6 ? c->Kcopy : c->K;
+      if (!src) return DNGD_ERR_STATE;
+      if (which == 7 && c->prec != DNGD_FP64) return DNGD_ERR_STATE;
+      double* buf = nullptr;
+      if (cudaMalloc(&buf, sizeof(double) * (size_t)m * m) != cudaSuccess) return DNGD_ERR_OOM;
+      dngd_status s = c->prec == DNGD_FP64 ? lower_to_f64<double>(m, (const double*)src, c->ldk, buf, c->st)
+                                           : lower_to_f64<float>(m, (const float*)src, c->ldk, buf, c->st);
+      if (!s) {
+        cudaMemcpyAsync(dst, buf, sizeof(double) * (size_t)m * m, cudaMemcpyDefault, c->st);
+        cudaStreamSynchronize(c->st);
+      }
+      cudaFree(buf);
+      return s;
+    }
+    default: return DNGD_ERR_INVALID_ARG;
+  }
+}
+
+}  // extern "C"

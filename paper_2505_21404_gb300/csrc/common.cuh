@@ -1,0 +1,129 @@
+// Shared definitions of the D-NGD CUDA library (internal, not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/dngd.h"
+
+namespace dngd {
+
+constexpr int kMaxLayers = DNGD_MAX_LAYERS;
+constexpr int kMaxDim = DNGD_MAX_DIM;
+constexpr int kMaxClasses = DNGD_MAX_CLASSES;
+
+// Device status word bits (ctx->d_status[0]); d_status[1] holds the first
+// failing Cholesky column, d_status[2] a code for the wait that timed out.
+enum : int {
+  ST_NOT_SPD = 1,
+  ST_NONFINITE = 2,
+  ST_TIMEOUT = 4,
+  ST_NO_CONVERGE = 8,
+};
+
+// One residual class laid out for the kernels.  Points of the class are
+// [p0, p0 + count); each point owns S consecutive rows of every stream
+// matrix starting at row0 + (i - p0) * S.  Stream order inside a point:
+// 0 = value, 1..nD = first derivatives along coords D[0..nD-1], nD+1 =
+// masked Laplacian (present when has_lap).
+struct ClassInfo {
+  int p0, count, S, row0, nD, has_lap;
+  int D[kMaxDim];
+  double c_val, c_lap, scale;      // scale = 1/sqrt(count)
+  double c_gradD[kMaxDim];         // c_grad of coord D[j]
+  int lapD[kMaxDim];               // 1 if D[j] is in the Laplacian mask
+};
+
+struct NetInfo {
+  int n_layers;                    // affine layers; hidden = n_layers - 1
+  int widths[kMaxLayers + 1];
+  long long w_off[kMaxLayers], b_off[kMaxLayers];
+  long long n;                     // parameters
+  int d_in, m, R;                  // input dim, residuals, stream rows
+  int n_classes;
+  int max_w;                       // widest hidden layer
+  ClassInfo cls[kMaxClasses];
+};
+
+__host__ __device__ inline const ClassInfo& class_of(const NetInfo& net, int p) {
+  int c = 0;
+  while (c + 1 < net.n_classes && p >= net.cls[c + 1].p0) ++c;
+  return net.cls[c];
+}
+
+#define DNGD_CUDA_CHECK(expr)                                                     \
+  do {                                                                            \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      fprintf(stderr, "dngd: CUDA error %s at %s:%d: %s\n", cudaGetErrorName(_e), \
+              __FILE__, __LINE__, cudaGetErrorString(_e));                        \
+      return DNGD_ERR_CUDA;                                                       \
+    }                                                                             \
+  } while (0)
+
+#define DNGD_LAUNCH_CHECK() DNGD_CUDA_CHECK(cudaGetLastError())
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// tanh in the working precision (library call; derivatives use t' = 1 - t^2).
+__device__ __forceinline__ double tanh_t(double x) { return tanh(x); }
+__device__ __forceinline__ float tanh_t(float x) { return tanhf(x); }
+
+// Double-float ("float2 as hi+lo") accumulation for FP32 data that needs an
+// accumulator with ~48 significant bits.  two_sum / two_prod are the
+// error-free transformations of Knuth and Dekker (the latter with fma).
+struct dfloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  float hi = s + e;
+  float lo = e - (hi - s);
+  return {hi, lo};
+}
+
+// a + x*y with x*y formed exactly (hi by rounding, lo by fma residual).
+__device__ __forceinline__ dfloat df_fma(dfloat a, float x, float y) {
+  float p = x * y;
+  float pe = fmaf(x, y, -p);
+  float s, e;
+  two_sum(a.hi, p, s, e);
+  e += pe + a.lo;
+  float hi = s + e;
+  float lo = e - (hi - s);
+  return {hi, lo};
+}
+
+__device__ __forceinline__ dfloat df_shfl_xor(dfloat v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+__device__ __forceinline__ dfloat df_warp_sum(dfloat v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  return v;
+}
+
+}  // namespace dngd

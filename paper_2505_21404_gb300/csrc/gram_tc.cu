@@ -1,0 +1,441 @@
+// Residual Gramian K = J J^T on the 5th-generation tensor cores (tcgen05).
+//
+// K is symmetric (Def. 3.1 of the paper; its assembly algorithm fills one
+// triangle and mirrors), so only the 128 x 256 output tiles that touch the
+// lower triangle are computed.  Per CTA (one output tile, one K-range):
+//   - warp 0 / lane 0 streams 128 x 64 (A) and 256 x 64 (B) operand tiles of
+//     the low-precision J into a 4-stage shared-memory ring with TMA
+//     (cp.async.bulk.tensor, 128-byte swizzle), signalling mbarriers;
+//   - warp 1 / lane 0 issues tcgen05.mma (M = 128, N = 256, FP32 accumulator
+//     in tensor memory, 256 columns) and releases each stage with
+//     tcgen05.commit;
+//   - all four warps drain the accumulator with tcgen05.ld (warp w owns TMEM
+//     lanes 32w..32w+31 = tile rows) and store FP32 partial tiles.
+// Operands: BF16 (kind::f16) or TF32 (kind::tf32); both use 128-byte K
+// blocks (64 bf16 / 32 tf32) and 32-byte K steps per instruction.
+// Split-K partials are summed in a fixed order by a reduction kernel that also
+// adds the diagonal shift, so results are deterministic.
+// Every mbarrier wait is bounded by a global-timer deadline; on expiry the
+// kernel records ST_TIMEOUT, drains what it issued and frees its TMEM.
+#include <cuda.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dngd {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int KBLK_BYTES = 128;                       // bytes of K per stage row
+constexpr int A_BYTES = BM * KBLK_BYTES;              // 16 KB
+constexpr int B_BYTES = BN * KBLK_BYTES;              // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;        // 48 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false (and records a timeout) after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int where) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) {
+      atomicOr(status, ST_TIMEOUT);
+      status[2] = where;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes stacked along M/N (stride byte offset 1024), version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format (1 = BF16, 2 = TF32),
+// both K-major, N = 256, M = 128.
+template <int KIND>
+__device__ __forceinline__ uint32_t make_idesc() {
+  const uint32_t fmt = KIND == 0 ? 1u : 2u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+#define TMEM_LD_32(taddr, r)                                                                                   \
+  asm volatile(                                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                       \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),        \
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), \
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),             \
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),             \
+        "=r"(r[30]), "=r"(r[31])                                                                               \
+      : "r"(taddr))
+
+// grid.x: tile index into tiles[] (pairs of row-block I, col-block J);
+// grid.y: split index over the K blocks.
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+          const int2* __restrict__ tiles, int m, int num_kblk, float* __restrict__ out, long long ldo,
+          long long split_stride, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int2 tile = tiles[blockIdx.x];
+  const int split = blockIdx.y, nsplit = gridDim.y;
+  const int kb_per = (num_kblk + nsplit - 1) / nsplit;
+  const int kb0 = split * kb_per;
+  const int kb1 = min(num_kblk, kb0 + kb_per);
+  const int nk = max(0, kb1 - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&acc_bar), 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base_sh;
+
+  volatile int* abort_flag = &abort_sh;
+  int issued = 0;  // producer: stages issued (for draining on abort)
+  if (warp == 0 && lane == 0) {
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      if (*abort_flag || !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, status, 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, STAGE_BYTES);
+      const uint32_t sa = smem_base + s * STAGE_BYTES;
+      const int kcoord = (kb0 + it) * (KIND == 0 ? 64 : 32);
+      tma_load_2d(sa, &mapA, fb, kcoord, tile.x * BM);
+      tma_load_2d(sa + A_BYTES, &mapB, fb, kcoord, tile.y * BN);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = make_idesc<KIND>();
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      if (*abort_flag || !mbar_wait(smem_u32(&full_bar[s]), ph, status, 2)) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sa = smem_base + s * STAGE_BYTES;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        umma<KIND>(tmem, sw128_desc(sa + 32 * k), sw128_desc(sa + A_BYTES + 32 * k), idesc,
+                   (it > 0 || k > 0) ? 1u : 0u);
+      }
+      umma_commit(smem_u32(&empty_bar[s]));
+    }
+    umma_commit(smem_u32(&acc_bar));  // fires when every MMA above has completed
+  }
+  __syncwarp();
+
+  // epilogue: TMEM -> registers -> FP32 tile (rows of this warp's lanes)
+  const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_bar), 0u, status, 3) ? 1 : 0) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const bool aborted = __any_sync(0xffffffffu, *abort_flag) != 0;
+  if (acc_ok && !aborted && nk > 0) {
+    const int row = tile.x * BM + warp * 32 + lane;
+    float* orow = out + (long long)split * split_stride + (long long)row * ldo;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32);
+      TMEM_LD_32(taddr, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int col0 = tile.y * BN + c * 32;
+      if (row < m) {
+        if (col0 + 32 <= m) {
+          float4* dst = reinterpret_cast<float4*>(orow + col0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                 __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (col0 + q < m) orow[col0 + q] = __uint_as_float(r[q]);
+        }
+      }
+    }
+  } else if (nk == 0) {
+    const int row = tile.x * BM + warp * 32 + lane;
+    float* orow = out + (long long)split * split_stride + (long long)row * ldo;
+    if (row < m)
+      for (int q = 0; q < BN; ++q)
+        if (tile.y * BN + q < m) orow[tile.y * BN + q] = 0.f;
+  }
+
+  // teardown: on abort, let issued TMA copies land before the CTA exits
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (int it = 0; it < issued; ++it) {
+      const int s = it % STAGES;
+      mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / STAGES) & 1), status, 4);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// K[i,j] (j <= i) = sum_s P_s[i,j] (+ shift on the diagonal); upper set to 0.
+__global__ void k_gram_reduce(int m, int nsplit, const float* __restrict__ P, long long ldp, long long sstride,
+                              float* __restrict__ K, long long ldk, double shift) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * m) return;
+  const int i = (int)(idx / m), j = (int)(idx % m);
+  float v = 0.f;
+  if (j <= i) {
+    for (int s = 0; s < nsplit; ++s) v += P[(long long)s * sstride + (long long)i * ldp + j];
+    if (i == j) v += (float)shift;
+  }
+  K[(long long)i * ldk + j] = v;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+struct GramPlan {
+  int kind, m, n;
+  long long ld;
+  CUtensorMap mapA, mapB;
+  int2* d_tiles = nullptr;
+  int ntiles = 0, nsplit = 1, num_kblk = 0;
+  float* K = nullptr;
+  long long ldk = 0;
+  float* partials = nullptr;
+  long long ldp = 0, sstride = 0;
+  double shift = 0.0;
+};
+
+static int choose_splits(int ntiles, int num_kblk, int nsm) {
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= 8; ++s) {
+    if (num_kblk / s < 8) break;
+    const long long units = (long long)ntiles * s;
+    const long long waves = (units + nsm - 1) / nsm;
+    const double eff = (double)units / (double)(waves * nsm);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
+}
+
+size_t gram_tc_partial_bytes(int m, int n) {
+  const int mp = ((m + BM - 1) / BM) * BM;
+  (void)n;
+  return (size_t)8 * mp * mp * sizeof(float);
+}
+
+dngd_status gram_tc_plan(GramPlan** out, int kind, const void* Jlow, int m, int n, long long ld, float* K,
+                         long long ldk, float* partials, size_t partial_bytes) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return DNGD_ERR_CUDA;
+  GramPlan* p = new GramPlan();
+  p->kind = kind;
+  p->m = m;
+  p->n = n;
+  p->ld = ld;
+  p->K = K;
+  p->ldk = ldk;
+  const int elem = kind == 0 ? 2 : 4;
+  const int kblk = KBLK_BYTES / elem;
+  p->num_kblk = (n + kblk - 1) / kblk;
+  if ((ld * elem) % 16 != 0) {
+    delete p;
+    return DNGD_ERR_INVALID_ARG;
+  }
+  const CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t gstride[1] = {(cuuint64_t)(ld * elem)};
+  cuuint32_t estride[2] = {1, 1};
+  cuuint32_t boxA[2] = {(cuuint32_t)kblk, (cuuint32_t)BM};
+  cuuint32_t boxB[2] = {(cuuint32_t)kblk, (cuuint32_t)BN};
+  CUresult r1 = enc(&p->mapA, dt, 2, const_cast<void*>(Jlow), gdim, gstride, boxA, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = enc(&p->mapB, dt, 2, const_cast<void*>(Jlow), gdim, gstride, boxB, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+    delete p;
+    return DNGD_ERR_CUDA;
+  }
+  std::vector<int2> tiles;
+  const int nI = (m + BM - 1) / BM;
+  for (int I = 0; I < nI; ++I)
+    for (int Jc = 0; Jc * BN <= I * BM + BM - 1 && Jc * BN < m; ++Jc) tiles.push_back(make_int2(I, Jc));
+  p->ntiles = (int)tiles.size();
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  p->nsplit = choose_splits(p->ntiles, p->num_kblk, nsm);
+  const int mp = nI * BM;
+  p->ldp = ((m + 3) / 4) * 4 + 4;
+  p->sstride = (long long)mp * p->ldp;
+  if ((size_t)p->nsplit * p->sstride * sizeof(float) > partial_bytes) p->nsplit = 1;
+  if ((size_t)p->sstride * sizeof(float) > partial_bytes) {
+    delete p;
+    return DNGD_ERR_INVALID_ARG;
+  }
+  p->partials = partials;
+  if (cudaMalloc(&p->d_tiles, sizeof(int2) * tiles.size()) != cudaSuccess) {
+    delete p;
+    return DNGD_ERR_OOM;
+  }
+  cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
+  static bool attr0 = false, attr1 = false;
+  if (kind == 0 && !attr0) {
+    cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr0 = true;
+  }
+  if (kind == 1 && !attr1) {
+    cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr1 = true;
+  }
+  *out = p;
+  return DNGD_OK;
+}
+
+dngd_status gram_tc_set_shift(GramPlan* p, double shift) {
+  p->shift = shift;
+  return DNGD_OK;
+}
+
+dngd_status gram_tc_run(GramPlan* p, int* status, cudaStream_t st) {
+  dim3 grid(p->ntiles, p->nsplit);
+  if (p->kind == 0)
+    k_gram_tc<0><<<grid, 128, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,
+                                                p->ldp, p->sstride, status);
+  else
+    k_gram_tc<1><<<grid, 128, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,
+                                                p->ldp, p->sstride, status);
+  DNGD_LAUNCH_CHECK();
+  const long long tot = (long long)p->m * p->m;
+  k_gram_reduce<<<(int)((tot + 255) / 256), 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->K,
+                                                          p->ldk, p->shift);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+void gram_tc_free(GramPlan* p) {
+  if (!p) return;
+  if (p->d_tiles) cudaFree(p->d_tiles);
+  delete p;
+}
+
+int gram_tc_nsplit(const GramPlan* p) { return p->nsplit; }
+int gram_tc_ntiles(const GramPlan* p) { return p->ntiles; }
+
+}  // namespace dngd

@@ -1,0 +1,516 @@
+// Taylor-mode jets of the tanh MLP, residuals, Jacobian rows and f_vv.
+//
+// Every collocation point carries S "streams" through the network (Taylor-mode
+// AD of Sec. 5 of the paper): the value, the first derivatives along the
+// coordinates its operator needs, and one collapsed second-order stream for
+// the masked Laplacian, using (t = tanh z, s = 1 - t^2)
+//     h = t,   d_k h = s d_k z,   Lap h = s Lap z - 2 t s sum_{k in mask} (d_k z)^2.
+// The residual of a class is linear in the output streams (Sec. 2.2), so the
+// Jacobian row of point i w.r.t. layer l is the rank-S sum
+//     dr_i/dW_l = sum_s delta_{l,i,s} h_{l-1,i,s}^T,   dr_i/db_l = delta_{l,i,value}
+// where delta are the stream adjoints from one reverse sweep.  The dense
+// matrix products of each layer run as GEMMs over all point-streams
+// (linalg.cu); the kernels here are the per-point elementwise parts.
+//
+// f_vv (Sec. 3.2) propagates, for every stream, the Taylor coefficients in the
+// parameter direction t of theta + t v: (q, q', q'') with
+//     z' = W h' + V h + b_v,   z'' = W h'' + 2 V h'
+// and the chain rules of tanh, s and t*s up to second order.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dngd {
+
+// ---------------------------------------------------------------------------
+// Forward sweep
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_first_layer(NetInfo net, const T* __restrict__ theta, const double* __restrict__ X,
+                              T* __restrict__ Z, T* __restrict__ H) {
+  const int p = blockIdx.x;
+  const int a = blockIdx.y * blockDim.x + threadIdx.x;
+  const int w = net.widths[1], din = net.d_in;
+  if (a >= w) return;
+  const ClassInfo& c = class_of(net, p);
+  const T* W = theta + net.w_off[0];
+  T z = theta[net.b_off[0] + a];
+  for (int k = 0; k < din; ++k) z += W[(long long)a * din + k] * (T)X[(long long)p * din + k];
+  const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+  const T t = tanh_t(z), s = T(1) - t * t;
+  Z[row * w + a] = z;
+  H[row * w + a] = t;
+  T Q = 0;
+  for (int j = 0; j < c.nD; ++j) {
+    const T zk = W[(long long)a * din + c.D[j]];
+    Z[(row + 1 + j) * w + a] = zk;
+    H[(row + 1 + j) * w + a] = s * zk;
+    if (c.lapD[j]) Q += zk * zk;
+  }
+  if (c.has_lap) {
+    Z[(row + 1 + c.nD) * w + a] = T(0);
+    H[(row + 1 + c.nD) * w + a] = T(-2) * t * s * Q;
+  }
+}
+
+// Hidden layer l >= 1: Z already holds W_l h_{l-1} for every stream row.
+template <typename T>
+__global__ void k_act_fwd(NetInfo net, int l, const T* __restrict__ theta, T* __restrict__ Z,
+                          T* __restrict__ H) {
+  const int p = blockIdx.x;
+  const int a = blockIdx.y * blockDim.x + threadIdx.x;
+  const int w = net.widths[l + 1];
+  if (a >= w) return;
+  const ClassInfo& c = class_of(net, p);
+  const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+  const T z = Z[row * w + a] + theta[net.b_off[l] + a];
+  const T t = tanh_t(z), s = T(1) - t * t;
+  Z[row * w + a] = z;
+  H[row * w + a] = t;
+  T Q = 0;
+  for (int j = 0; j < c.nD; ++j) {
+    const T zk = Z[(row + 1 + j) * w + a];
+    H[(row + 1 + j) * w + a] = s * zk;
+    if (c.lapD[j]) Q += zk * zk;
+  }
+  if (c.has_lap) {
+    const T L = Z[(row + 1 + c.nD) * w + a];
+    H[(row + 1 + c.nD) * w + a] = s * L - T(2) * t * s * Q;
+  }
+}
+
+// Output layer and residual: one warp per point.
+template <typename T>
+__global__ void k_output(NetInfo net, const T* __restrict__ theta, const double* __restrict__ X,
+                         const T* __restrict__ Hlast, const double* __restrict__ target,
+                         double* __restrict__ r, int* __restrict__ status) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= net.m) return;
+  const int p = warp;
+  const ClassInfo& c = class_of(net, p);
+  const int L = net.n_layers - 1;
+  const int w = net.widths[L];
+  const T* wo = theta + net.w_off[L];
+  T acc = 0;
+  if (L == 0) {
+    // no hidden layer: u = w.x + b, d_k u = w_k, Lap u = 0
+    if (lane == 0) {
+      T u = theta[net.b_off[0]];
+      for (int k = 0; k < net.d_in; ++k) u += wo[k] * (T)X[(long long)p * net.d_in + k];
+      acc = T(c.c_val) * u;
+      for (int j = 0; j < c.nD; ++j) acc += T(c.c_gradD[j]) * wo[c.D[j]];
+    }
+  } else {
+    const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+    for (int s = 0; s < c.S; ++s) {
+      T coef;
+      if (s == 0) coef = T(c.c_val);
+      else if (s <= c.nD) coef = T(c.c_gradD[s - 1]);
+      else coef = T(c.c_lap);
+      if (coef == T(0)) continue;
+      T u = 0;
+      for (int a = lane; a < w; a += 32) u += wo[a] * Hlast[(row + s) * w + a];
+      acc += coef * u;
+    }
+    if (lane == 0) acc += T(c.c_val) * theta[net.b_off[L]];
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const double ri = (double)acc * c.scale - target[p] * c.scale;
+    r[p] = ri;
+    if (!isfinite(ri)) atomicOr(status, ST_NONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reverse sweep
+// ---------------------------------------------------------------------------
+
+// Stream adjoints through tanh for hidden layer l.  Hbar holds the adjoints of
+// the layer's outputs (rows x w), or is null for the last hidden layer, whose
+// output adjoints are ubar_s * w_out with ubar the class coefficients.
+template <typename T>
+__global__ void k_act_bwd(NetInfo net, int l, const T* __restrict__ theta, const T* __restrict__ Z,
+                          const T* __restrict__ Hbar, T* __restrict__ Dl) {
+  const int p = blockIdx.x;
+  const int a = blockIdx.y * blockDim.x + threadIdx.x;
+  const int w = net.widths[l + 1];
+  if (a >= w) return;
+  const ClassInfo& c = class_of(net, p);
+  const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+  T hv, hk[kMaxDim], hL = 0;
+  if (Hbar == nullptr) {
+    const T wo = theta[net.w_off[net.n_layers - 1] + a];
+    const T sc = T(c.scale);
+    hv = sc * T(c.c_val) * wo;
+    for (int j = 0; j < c.nD; ++j) hk[j] = sc * T(c.c_gradD[j]) * wo;
+    if (c.has_lap) hL = sc * T(c.c_lap) * wo;
+  } else {
+    hv = Hbar[row * w + a];
+    for (int j = 0; j < c.nD; ++j) hk[j] = Hbar[(row + 1 + j) * w + a];
+    if (c.has_lap) hL = Hbar[(row + 1 + c.nD) * w + a];
+  }
+  const T z = Z[row * w + a];
+  const T t = tanh_t(z), s = T(1) - t * t;
+  const T ts = t * s, dts = s * (s - T(2) * t * t);
+  T Q = 0, gsum = 0;
+  T zk[kMaxDim];
+  for (int j = 0; j < c.nD; ++j) {
+    zk[j] = Z[(row + 1 + j) * w + a];
+    if (c.lapD[j]) Q += zk[j] * zk[j];
+    gsum += zk[j] * hk[j];
+  }
+  T Lz = c.has_lap ? Z[(row + 1 + c.nD) * w + a] : T(0);
+  const T zbar = s * hv - T(2) * ts * gsum - (T(2) * ts * Lz + T(2) * dts * Q) * hL;
+  Dl[row * w + a] = zbar;
+  for (int j = 0; j < c.nD; ++j) {
+    T zb = s * hk[j];
+    if (c.lapD[j]) zb -= T(4) * ts * zk[j] * hL;
+    Dl[(row + 1 + j) * w + a] = zb;
+  }
+  if (c.has_lap) Dl[(row + 1 + c.nD) * w + a] = s * hL;
+}
+
+// Jacobian rows: block (point p, layer l) writes dr_p/dW_l and dr_p/db_l.
+template <typename T, typename TJ>
+__global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const double* __restrict__ X,
+                            LayerPtrs<T> Hs, LayerPtrs<T> Ds, TJ* __restrict__ J, long long ldJ,
+                            __nv_bfloat16* __restrict__ Jb, long long ldb) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int p = blockIdx.x;
+  const int l = blockIdx.y;
+  const ClassInfo& c = class_of(net, p);
+  const int S = c.S;
+  const int L = net.n_layers - 1;
+  const int wout = net.widths[l + 1], win = net.widths[l];
+  T* dsh = sm;                   // [S][wout]
+  T* hsh = sm + S * wout;        // [S][win]
+  const long long row = c.row0 + (long long)(p - c.p0) * S;
+  // stream adjoints of this layer's pre-activations
+  for (int e = threadIdx.x; e < S * wout; e += blockDim.x) {
+    const int s = e / wout, a = e % wout;
+    T v;
+    if (l == L) {
+      const T sc = T(c.scale);
+      v = (s == 0) ? sc * T(c.c_val) : (s <= c.nD ? sc * T(c.c_gradD[s - 1]) : sc * T(c.c_lap));
+    } else {
+      v = Ds.p[l][(row + s) * wout + a];
+    }
+    dsh[e] = v;
+  }
+  // stream inputs of this layer
+  for (int e = threadIdx.x; e < S * win; e += blockDim.x) {
+    const int s = e / win, b = e % win;
+    T v;
+    if (l == 0) {
+      if (s == 0) v = (T)X[(long long)p * net.d_in + b];
+      else if (s <= c.nD) v = (b == c.D[s - 1]) ? T(1) : T(0);
+      else v = T(0);
+    } else {
+      v = Hs.p[l - 1][(row + s) * win + b];
+    }
+    hsh[e] = v;
+  }
+  __syncthreads();
+  TJ* Jrow = J + (long long)p * ldJ;
+  __nv_bfloat16* Jbrow = Jb ? Jb + (long long)p * ldb : nullptr;
+  const long long wo = net.w_off[l], bo = net.b_off[l];
+  for (int b = threadIdx.x; b < win; b += blockDim.x) {
+    T hreg[2 + kMaxDim];
+    for (int s = 0; s < S; ++s) hreg[s] = hsh[s * win + b];
+    for (int a = 0; a < wout; ++a) {
+      T acc = 0;
+      for (int s = 0; s < S; ++s) acc += dsh[s * wout + a] * hreg[s];
+      Jrow[wo + (long long)a * win + b] = (TJ)acc;
+      if (Jbrow) Jbrow[wo + (long long)a * win + b] = __float2bfloat16_rn((float)acc);
+    }
+  }
+  for (int a = threadIdx.x; a < wout; a += blockDim.x) {
+    Jrow[bo + a] = (TJ)dsh[a];
+    if (Jbrow) Jbrow[bo + a] = __float2bfloat16_rn((float)dsh[a]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// f_vv: second-order Taylor coefficients along the parameter direction v
+// ---------------------------------------------------------------------------
+
+// 2-jet (in t) of one unit's streams through tanh.
+template <typename T>
+__device__ __forceinline__ void act2_unit(const ClassInfo& c, T z0, T z1, T z2, const T* g0, const T* g1,
+                                          const T* g2, T L0, T L1, T L2, T* h0, T* h1, T* h2,
+                                          T* hk0, T* hk1, T* hk2, T* hL) {
+  const T t = tanh_t(z0), s = T(1) - t * t;
+  const T s_z = T(-2) * t * s;
+  const T s_zz = T(-2) * s * s + T(4) * t * t * s;
+  const T p = t * s;
+  const T p_z = s * (s - T(2) * t * t);
+  const T p_zz = T(-8) * t * s * s + T(4) * t * t * t * s;
+  *h0 = t;
+  *h1 = s * z1;
+  *h2 = s * z2 + s_z * z1 * z1;
+  const T S1 = s_z * z1, S2 = s_zz * z1 * z1 + s_z * z2;
+  const T P1 = p_z * z1, P2 = p_zz * z1 * z1 + p_z * z2;
+  T Q0 = 0, Q1 = 0, Q2 = 0;
+  for (int j = 0; j < c.nD; ++j) {
+    hk0[j] = s * g0[j];
+    hk1[j] = S1 * g0[j] + s * g1[j];
+    hk2[j] = S2 * g0[j] + T(2) * S1 * g1[j] + s * g2[j];
+    if (c.lapD[j]) {
+      Q0 += g0[j] * g0[j];
+      Q1 += T(2) * g0[j] * g1[j];
+      Q2 += T(2) * (g1[j] * g1[j] + g0[j] * g2[j]);
+    }
+  }
+  hL[0] = s * L0 - T(2) * p * Q0;
+  hL[1] = S1 * L0 + s * L1 - T(2) * (P1 * Q0 + p * Q1);
+  hL[2] = S2 * L0 + T(2) * S1 * L1 + s * L2 - T(2) * (P2 * Q0 + T(2) * P1 * Q1 + p * Q2);
+}
+
+// Z3/H3 hold three blocks of R rows: coefficient 0, 1 (d/dt), 2 (d^2/dt^2).
+template <typename T>
+__global__ void k_first_layer_fvv(NetInfo net, const T* __restrict__ theta, const T* __restrict__ v,
+                                  const double* __restrict__ X, T* __restrict__ H3) {
+  const int p = blockIdx.x;
+  const int a = blockIdx.y * blockDim.x + threadIdx.x;
+  const int w = net.widths[1], din = net.d_in;
+  if (a >= w) return;
+  const ClassInfo& c = class_of(net, p);
+  const T* W = theta + net.w_off[0];
+  const T* V = v + net.w_off[0];
+  T z0 = theta[net.b_off[0] + a], z1 = v[net.b_off[0] + a];
+  for (int k = 0; k < din; ++k) {
+    const T x = (T)X[(long long)p * din + k];
+    z0 += W[(long long)a * din + k] * x;
+    z1 += V[(long long)a * din + k] * x;
+  }
+  T g0[kMaxDim], g1[kMaxDim], g2[kMaxDim];
+  for (int j = 0; j < c.nD; ++j) {
+    g0[j] = W[(long long)a * din + c.D[j]];
+    g1[j] = V[(long long)a * din + c.D[j]];
+    g2[j] = 0;
+  }
+  T h0, h1, h2, hk0[kMaxDim], hk1[kMaxDim], hk2[kMaxDim], hL[3];
+  act2_unit(c, z0, z1, T(0), g0, g1, g2, T(0), T(0), T(0), &h0, &h1, &h2, hk0, hk1, hk2, hL);
+  const long long R = net.R;
+  const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+  T* B0 = H3;
+  T* B1 = H3 + R * w;
+  T* B2 = H3 + 2 * R * w;
+  B0[row * w + a] = h0; B1[row * w + a] = h1; B2[row * w + a] = h2;
+  for (int j = 0; j < c.nD; ++j) {
+    B0[(row + 1 + j) * w + a] = hk0[j];
+    B1[(row + 1 + j) * w + a] = hk1[j];
+    B2[(row + 1 + j) * w + a] = hk2[j];
+  }
+  if (c.has_lap) {
+    B0[(row + 1 + c.nD) * w + a] = hL[0];
+    B1[(row + 1 + c.nD) * w + a] = hL[1];
+    B2[(row + 1 + c.nD) * w + a] = hL[2];
+  }
+}
+
+// Hidden layer l >= 1: Z3 holds W h (block 0), W h' + V h (block 1) and
+// W h'' + 2 V h' (block 2); add biases and apply the tanh 2-jet.
+template <typename T>
+__global__ void k_act_fvv(NetInfo net, int l, const T* __restrict__ theta, const T* __restrict__ v,
+                          const T* __restrict__ Z3, T* __restrict__ H3) {
+  const int p = blockIdx.x;
+  const int a = blockIdx.y * blockDim.x + threadIdx.x;
+  const int w = net.widths[l + 1];
+  if (a >= w) return;
+  const ClassInfo& c = class_of(net, p);
+  const long long R = net.R;
+  const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+  const T* Z0 = Z3;
+  const T* Z1 = Z3 + R * w;
+  const T* Z2 = Z3 + 2 * R * w;
+  const T z0 = Z0[row * w + a] + theta[net.b_off[l] + a];
+  const T z1 = Z1[row * w + a] + v[net.b_off[l] + a];
+  const T z2 = Z2[row * w + a];
+  T g0[kMaxDim], g1[kMaxDim], g2[kMaxDim];
+  for (int j = 0; j < c.nD; ++j) {
+    g0[j] = Z0[(row + 1 + j) * w + a];
+    g1[j] = Z1[(row + 1 + j) * w + a];
+    g2[j] = Z2[(row + 1 + j) * w + a];
+  }
+  T L0 = 0, L1 = 0, L2 = 0;
+  if (c.has_lap) {
+    L0 = Z0[(row + 1 + c.nD) * w + a];
+    L1 = Z1[(row + 1 + c.nD) * w + a];
+    L2 = Z2[(row + 1 + c.nD) * w + a];
+  }
+  T h0, h1, h2, hk0[kMaxDim], hk1[kMaxDim], hk2[kMaxDim], hL[3];
+  act2_unit(c, z0, z1, z2, g0, g1, g2, L0, L1, L2, &h0, &h1, &h2, hk0, hk1, hk2, hL);
+  T* B0 = H3;
+  T* B1 = H3 + R * w;
+  T* B2 = H3 + 2 * R * w;
+  B0[row * w + a] = h0; B1[row * w + a] = h1; B2[row * w + a] = h2;
+  for (int j = 0; j < c.nD; ++j) {
+    B0[(row + 1 + j) * w + a] = hk0[j];
+    B1[(row + 1 + j) * w + a] = hk1[j];
+    B2[(row + 1 + j) * w + a] = hk2[j];
+  }
+  if (c.has_lap) {
+    B0[(row + 1 + c.nD) * w + a] = hL[0];
+    B1[(row + 1 + c.nD) * w + a] = hL[1];
+    B2[(row + 1 + c.nD) * w + a] = hL[2];
+  }
+}
+
+// Output layer of the t-2-jet: f_vv_p = scale * Op(u'') with
+// u'' = w.h'' + 2 w_v.h' (the output bias moves linearly and drops out).
+template <typename T>
+__global__ void k_output_fvv(NetInfo net, const T* __restrict__ theta, const T* __restrict__ v,
+                             const T* __restrict__ H3, double* __restrict__ fvv) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= net.m) return;
+  const int p = warp;
+  const ClassInfo& c = class_of(net, p);
+  const int L = net.n_layers - 1;
+  T acc = 0;
+  if (L > 0) {
+    const int w = net.widths[L];
+    const long long R = net.R;
+    const T* wo = theta + net.w_off[L];
+    const T* wv = v + net.w_off[L];
+    const T* B1 = H3 + R * w;
+    const T* B2 = H3 + 2 * R * w;
+    const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+    for (int s = 0; s < c.S; ++s) {
+      T coef;
+      if (s == 0) coef = T(c.c_val);
+      else if (s <= c.nD) coef = T(c.c_gradD[s - 1]);
+      else coef = T(c.c_lap);
+      if (coef == T(0)) continue;
+      T u = 0;
+      for (int a = lane; a < w; a += 32)
+        u += wo[a] * B2[(row + s) * w + a] + T(2) * wv[a] * B1[(row + s) * w + a];
+      acc += coef * u;
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) fvv[p] = (double)acc * c.scale;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, const double* target,
+                         LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st) {
+  const int L = net.n_layers - 1;
+  const int thr = 128;
+  for (int l = 0; l < L; ++l) {
+    const int w = net.widths[l + 1];
+    dim3 grid(net.m, cdiv(w, thr));
+    if (l == 0) {
+      k_first_layer<T><<<grid, thr, 0, st>>>(net, theta, X, Z.p[0], H.p[0]);
+    } else {
+      dngd_status s = gemm_nt<T>(net.R, w, net.widths[l], T(1), H.p[l - 1], net.widths[l],
+                                 theta + net.w_off[l], net.widths[l], T(0), Z.p[l], w, false, st);
+      if (s) return s;
+      k_act_fwd<T><<<grid, thr, 0, st>>>(net, l, theta, Z.p[l], H.p[l]);
+    }
+    DNGD_LAUNCH_CHECK();
+  }
+  const T* Hlast = L > 0 ? H.p[L - 1] : nullptr;
+  k_output<T><<<cdiv((long long)net.m * 32, 256), 256, 0, st>>>(net, theta, X, Hlast, target, r, status);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+template <typename T, typename TJ>
+dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
+                                   LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
+                                   __nv_bfloat16* Jb, long long ldb, cudaStream_t st) {
+  const int L = net.n_layers - 1;
+  const int thr = 128;
+  for (int l = L - 1; l >= 0; --l) {
+    const int w = net.widths[l + 1];
+    dim3 grid(net.m, cdiv(w, thr));
+    k_act_bwd<T><<<grid, thr, 0, st>>>(net, l, theta, Z.p[l], l == L - 1 ? nullptr : Hbar, D.p[l]);
+    DNGD_LAUNCH_CHECK();
+    if (l > 0) {
+      // Hbar_{l-1} = D_l W_l  (rows x w_l)
+      dngd_status s = gemm_nn<T>(net.R, net.widths[l], w, T(1), D.p[l], w, theta + net.w_off[l],
+                                 net.widths[l], T(0), Hbar, net.widths[l], st);
+      if (s) return s;
+    }
+  }
+  int maxS = 1;
+  for (int c = 0; c < net.n_classes; ++c) maxS = net.cls[c].S > maxS ? net.cls[c].S : maxS;
+  int maxw = 1;
+  for (int l = 0; l <= L; ++l) {
+    const int ws = net.widths[l + 1] + net.widths[l];
+    maxw = ws > maxw ? ws : maxw;
+  }
+  const size_t smem = (size_t)maxS * maxw * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_jac_write<T, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  dim3 grid(net.m, L + 1);
+  k_jac_write<T, TJ><<<grid, 256, smem, st>>>(net, theta, X, H, D, J, ldJ, Jb, ldb);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+template <typename T>
+dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const double* X, T* Z3, T* H3a,
+                     T* H3b, double* fvv, cudaStream_t st) {
+  const int L = net.n_layers - 1;
+  const int thr = 128;
+  const long long R = net.R;
+  T* Hprev = H3a;
+  T* Hcur = H3b;
+  for (int l = 0; l < L; ++l) {
+    const int w = net.widths[l + 1];
+    dim3 grid(net.m, cdiv(w, thr));
+    if (l == 0) {
+      k_first_layer_fvv<T><<<grid, thr, 0, st>>>(net, theta, v, X, Hcur);
+    } else {
+      const int win = net.widths[l];
+      const T* W = theta + net.w_off[l];
+      const T* V = v + net.w_off[l];
+      // blocks 0..2: W h^(j)
+      dngd_status s = gemm_nt<T>(3 * net.R, w, win, T(1), Hprev, win, W, win, T(0), Z3, w, false, st);
+      if (s) return s;
+      // block 1 += V h ; block 2 += 2 V h'
+      s = gemm_nt<T>(net.R, w, win, T(1), Hprev, win, V, win, T(1), Z3 + R * w, w, false, st);
+      if (s) return s;
+      s = gemm_nt<T>(net.R, w, win, T(2), Hprev + R * win, win, V, win, T(1), Z3 + 2 * R * w, w, false, st);
+      if (s) return s;
+      k_act_fvv<T><<<grid, thr, 0, st>>>(net, l, theta, v, Z3, Hcur);
+    }
+    DNGD_LAUNCH_CHECK();
+    T* tmp = Hprev;
+    Hprev = Hcur;
+    Hcur = tmp;
+  }
+  k_output_fvv<T><<<cdiv((long long)net.m * 32, 256), 256, 0, st>>>(net, theta, v, Hprev, fvv);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+template dngd_status jets_forward<double>(const NetInfo&, const double*, const double*, const double*,
+                                          LayerPtrs<double>, LayerPtrs<double>, double*, int*, cudaStream_t);
+template dngd_status jets_forward<float>(const NetInfo&, const float*, const double*, const double*,
+                                         LayerPtrs<float>, LayerPtrs<float>, double*, int*, cudaStream_t);
+template dngd_status jets_backward_jacobian<double, double>(const NetInfo&, const double*, const double*,
+                                                            LayerPtrs<double>, LayerPtrs<double>,
+                                                            LayerPtrs<double>, double*, double*, long long,
+                                                            __nv_bfloat16*, long long, cudaStream_t);
+template dngd_status jets_backward_jacobian<float, float>(const NetInfo&, const float*, const double*,
+                                                          LayerPtrs<float>, LayerPtrs<float>,
+                                                          LayerPtrs<float>, float*, float*, long long,
+                                                          __nv_bfloat16*, long long, cudaStream_t);
+template dngd_status jets_fvv<double>(const NetInfo&, const double*, const double*, const double*, double*,
+                                      double*, double*, double*, cudaStream_t);
+template dngd_status jets_fvv<float>(const NetInfo&, const float*, const float*, const double*, float*,
+                                     float*, float*, double*, cudaStream_t);
+
+}  // namespace dngd

@@ -1,0 +1,87 @@
+// Internal kernel launchers of the D-NGD library.
+#pragma once
+
+#include "common.cuh"
+
+namespace dngd {
+
+template <typename T>
+struct LayerPtrs {
+  T* p[kMaxLayers];
+};
+
+// ---- jets.cu --------------------------------------------------------------
+template <typename T>
+dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, const double* target,
+                         LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st);
+
+template <typename T, typename TJ>
+dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
+                                   LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
+                                   __nv_bfloat16* Jb, long long ldb, cudaStream_t st);
+
+template <typename T>
+dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const double* X, T* Z3, T* H3a,
+                     T* H3b, double* fvv, cudaStream_t st);
+
+// ---- linalg.cu ------------------------------------------------------------
+// C[M x N] = alpha * A[M x K] * B^T + beta * C, B is [N x K] (both row-major).
+// lower: skip output tiles strictly above the diagonal (syrk-style use).
+template <typename T>
+dngd_status gemm_nt(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb,
+                    T beta, T* C, long long ldc, bool lower, cudaStream_t st);
+
+// C[M x N] = alpha * A[M x K] * B[K x N] + beta * C (row-major).
+template <typename T>
+dngd_status gemm_nn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb,
+                    T beta, T* C, long long ldc, cudaStream_t st);
+
+// In-place blocked Cholesky of the lower triangle of A [m x m] (lda).
+// TA = double: everything in FP64.  TA = float: FP32 panels and trailing
+// updates with every diagonal block factored in FP64.
+// On a non-positive pivot sets status bit ST_NOT_SPD and status[1] = column.
+template <typename TA>
+dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cudaStream_t st);
+
+// x = (L L^T)^{-1} b with the FP64 factor (two triangular solves).
+dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* b, double* x, cudaStream_t st);
+
+// Explicit inverse of a lower-triangular FP32 factor: Linv = L^{-1} (lower).
+dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
+                            cudaStream_t st);
+
+// y = alpha * A^T x  (A [m x n] row-major, x [m], y [n]); partials: [splits x n]
+template <typename TA>
+dngd_status gemv_t(int m, int n, const TA* A, long long lda, const double* x, double alpha, double* y,
+                   double* partials, cudaStream_t st);
+
+// y = alpha * A x + beta_y * y0 + gamma * z   (A [m x n] row-major, y [m])
+template <typename TA>
+dngd_status gemv_n(int m, int n, const TA* A, long long lda, const double* x, double alpha, double* y,
+                   cudaStream_t st);
+
+// y = L x (lower) or y = L^T x for an explicit FP32 lower-triangular matrix.
+dngd_status trmv_f32(int m, const float* L, long long ldl, const double* x, double* y, bool trans,
+                     cudaStream_t st);
+
+// K[i,i] += shift for i < m.
+template <typename T>
+dngd_status add_diag(int m, T* K, long long ldk, double shift, cudaStream_t st);
+
+// Deterministic dot products / norms into a device scalar.
+dngd_status dot_dev(int n, const double* x, const double* y, double* out, double* partials, cudaStream_t st);
+
+// Device-side vector kernels used by the refinement / PCG loops.
+dngd_status axpy_dev(int n, double alpha, const double* x, double* y, cudaStream_t st);
+
+// ---- gram_tc.cu -----------------------------------------------------------
+// K (FP32, lower 128x256 tiles) = Jlow Jlow^T with tcgen05 tensor cores.
+// kind: 0 = BF16 operands (Jlow is bf16 [rows x ld]), 1 = TF32 (float).
+struct GramPlan;
+dngd_status gram_tc_plan(GramPlan** plan, int kind, const void* Jlow, int m, int n, long long ld, float* K,
+                         long long ldk, float* partials, size_t partial_bytes);
+dngd_status gram_tc_run(GramPlan* plan, int* status, cudaStream_t st);
+void gram_tc_free(GramPlan* plan);
+size_t gram_tc_partial_bytes(int m, int n);
+
+}  // namespace dngd

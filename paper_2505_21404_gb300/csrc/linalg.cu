@@ -1,0 +1,589 @@
+// Dense linear algebra of the dual solve: SIMT GEMMs (FP64 / FP32), the
+// blocked Cholesky factorisation of K + lambda I, triangular solves and
+// inverses, and the HBM-bound J^T x / J x products.
+//
+// All reductions use a fixed order (no atomics on floating point), so every
+// result is bitwise reproducible run to run.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dngd {
+
+// ---------------------------------------------------------------------------
+// SIMT GEMM, register-tiled: C = alpha * A * op(B) + beta * C.
+// BT = true: B is [N x K] (C = A B^T); BT = false: B is [K x N].
+// ---------------------------------------------------------------------------
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool BT>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, const T* __restrict__ B,
+       long long ldb, T beta, T* __restrict__ C, long long ldc, int lower) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
+  if (lower && bn > bm + BM - 1) return;
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int e = tid; e < BM * BK; e += NT) {
+      const int r = e / BK, kk = e % BK;
+      const int gr = bm + r, gk = k0 + kk;
+      As[kk][r] = (gr < M && gk < K) ? A[(long long)gr * lda + gk] : T(0);
+    }
+    if (BT) {
+#pragma unroll
+      for (int e = tid; e < BN * BK; e += NT) {
+        const int c = e / BK, kk = e % BK;
+        const int gc = bn + c, gk = k0 + kk;
+        Bs[kk][c] = (gc < N && gk < K) ? B[(long long)gc * ldb + gk] : T(0);
+      }
+    } else {
+#pragma unroll
+      for (int e = tid; e < BN * BK; e += NT) {
+        const int kk = e / BN, c = e % BN;
+        const int gc = bn + c, gk = k0 + kk;
+        Bs[kk][c] = (gc < N && gk < K) ? B[(long long)gk * ldb + gc] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gr = bm + ty * TM + i;
+    if (gr >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gc = bn + tx * TN + j;
+      if (gc >= N) continue;
+      T* cp = C + (long long)gr * ldc + gc;
+      *cp = (beta == T(0)) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *cp;
+    }
+  }
+}
+
+template <typename T>
+struct GemmCfg;
+template <>
+struct GemmCfg<double> {
+  static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+};
+template <>
+struct GemmCfg<float> {
+  static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+};
+
+template <typename T>
+dngd_status gemm_nt(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb, T beta,
+                    T* C, long long ldc, bool lower, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DNGD_OK;
+  using G = GemmCfg<T>;
+  dim3 grid(cdiv(N, G::BN), cdiv(M, G::BM));
+  k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN, true>
+      <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                          lower ? 1 : 0);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+template <typename T>
+dngd_status gemm_nn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb, T beta,
+                    T* C, long long ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DNGD_OK;
+  using G = GemmCfg<T>;
+  dim3 grid(cdiv(N, G::BN), cdiv(M, G::BM));
+  k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN, false>
+      <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+template dngd_status gemm_nt<double>(int, int, int, double, const double*, long long, const double*, long long,
+                                     double, double*, long long, bool, cudaStream_t);
+template dngd_status gemm_nt<float>(int, int, int, float, const float*, long long, const float*, long long, float,
+                                    float*, long long, bool, cudaStream_t);
+template dngd_status gemm_nn<double>(int, int, int, double, const double*, long long, const double*, long long,
+                                     double, double*, long long, cudaStream_t);
+template dngd_status gemm_nn<float>(int, int, int, float, const float*, long long, const float*, long long, float,
+                                    float*, long long, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Blocked right-looking Cholesky (lower).  Per block column k:
+//   1. factor the diagonal block in FP64 in shared memory,
+//   2. panel: A21 <- A21 L11^{-T} by row-wise forward substitution,
+//   3. trailing update A22 <- A22 - A21 A21^T (lower tiles, SIMT GEMM).
+// ---------------------------------------------------------------------------
+
+constexpr int kCholNB = 64;
+
+template <typename TA>
+__global__ void __launch_bounds__(256) k_potrf_diag(int k0, int kb, TA* A, long long lda, int* status) {
+  __shared__ double S[kCholNB][kCholNB + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    S[i][j] = (j <= i) ? (double)A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  __shared__ int bad;
+  if (tid == 0) bad = -1;
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    const double piv = S[j][j];
+    if (!(piv > 0.0)) {  // not SPD (or NaN): record and stop this block
+      if (tid == 0) bad = j;
+      break;
+    }
+    const double d = sqrt(piv);
+    // thread per row i > j: scale column j, then rank-1 update of row i
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] /= d;
+    __syncthreads();
+    if (tid == 0) S[j][j] = d;
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) {
+      const double lij = S[i][j];
+      for (int c = j + 1; c <= i; ++c) S[i][c] -= lij * S[c][j];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad >= 0) {
+    if (tid == 0) {
+      const int old = atomicOr(status, ST_NOT_SPD);
+      if (!(old & ST_NOT_SPD)) status[1] = k0 + bad;
+    }
+    return;
+  }
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    if (j <= i) A[(long long)(k0 + i) * lda + k0 + j] = (TA)S[i][j];
+  }
+}
+
+// Panel rows i in [k0+kb, m): x L11^T = a, solved left to right; one thread
+// per row, the row kept in shared memory.
+template <typename TA>
+__global__ void __launch_bounds__(64) k_trsm_panel(int m, int k0, int kb, TA* A, long long lda,
+                                                    const int* status) {
+  if (status[0] & ST_NOT_SPD) return;
+  extern __shared__ unsigned char trsm_smem[];
+  TA(*Lsh)[kCholNB + 1] = reinterpret_cast<TA(*)[kCholNB + 1]>(trsm_smem);
+  TA(*X)[kCholNB + 1] = Lsh + kCholNB;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    Lsh[i][j] = (j <= i) ? A[(long long)(k0 + i) * lda + k0 + j] : TA(0);
+  }
+  const int r0 = k0 + kb + blockIdx.x * 64;
+  for (int e = tid; e < 64 * kb; e += blockDim.x) {
+    const int rr = e / kb, j = e % kb;
+    const int gr = r0 + rr;
+    X[rr][j] = (gr < m) ? A[(long long)gr * lda + k0 + j] : TA(0);
+  }
+  __syncthreads();
+  const int gr = r0 + tid;
+  if (gr < m) {
+    for (int j = 0; j < kb; ++j) {
+      TA s = X[tid][j];
+      for (int p = 0; p < j; ++p) s -= X[tid][p] * Lsh[j][p];
+      X[tid][j] = s / Lsh[j][j];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 64 * kb; e += blockDim.x) {
+    const int rr = e / kb, j = e % kb;
+    const int g = r0 + rr;
+    if (g < m) A[(long long)g * lda + k0 + j] = X[rr][j];
+  }
+}
+
+template <typename TA>
+dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cudaStream_t st) {
+  (void)work;
+  const int trsm_smem = 2 * kCholNB * (kCholNB + 1) * (int)sizeof(TA);
+  static bool attr_set = false;
+  if (!attr_set) {
+    DNGD_CUDA_CHECK(cudaFuncSetAttribute(k_trsm_panel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem));
+    attr_set = true;
+  }
+  for (int k0 = 0; k0 < m; k0 += kCholNB) {
+    const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
+    k_potrf_diag<TA><<<1, 256, 0, st>>>(k0, kb, A, lda, status);
+    DNGD_LAUNCH_CHECK();
+    const int rest = m - k0 - kb;
+    if (rest <= 0) break;
+    k_trsm_panel<TA><<<cdiv(rest, 64), 64, trsm_smem, st>>>(m, k0, kb, A, lda, status);
+    DNGD_LAUNCH_CHECK();
+    TA* P = A + (long long)(k0 + kb) * lda + k0;
+    TA* A22 = A + (long long)(k0 + kb) * lda + k0 + kb;
+    dngd_status s = gemm_nt<TA>(rest, rest, kb, TA(-1), P, lda, P, lda, TA(1), A22, lda, true, st);
+    if (s) return s;
+  }
+  return DNGD_OK;
+}
+
+template dngd_status cholesky<double>(int, double*, long long, int*, double*, cudaStream_t);
+template dngd_status cholesky<float>(int, float*, long long, int*, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Triangular solves with the FP64 factor, blocked: one small kernel solves a
+// diagonal block, a second applies that block to the remaining rows.
+// ---------------------------------------------------------------------------
+
+constexpr int kTrsvNB = 64;
+
+// forward: x[k0:k0+kb] = L_blk^{-1} x[k0:k0+kb]
+// backward: x[k0:k0+kb] = L_blk^{-T} x[k0:k0+kb]
+__global__ void k_trsv_diag(int k0, int kb, const double* __restrict__ L, long long ldl, double* x, int trans) {
+  __shared__ double Ls[kTrsvNB][kTrsvNB + 1];
+  __shared__ double xs[kTrsvNB];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    Ls[i][j] = (j <= i) ? L[(long long)(k0 + i) * ldl + k0 + j] : 0.0;
+  }
+  for (int i = tid; i < kb; i += blockDim.x) xs[i] = x[k0 + i];
+  __syncthreads();
+  if (!trans) {
+    for (int j = 0; j < kb; ++j) {
+      const double xj = xs[j] / Ls[j][j];
+      __syncthreads();
+      if (tid == 0) xs[j] = xj;
+      for (int i = j + 1 + tid; i < kb; i += blockDim.x) xs[i] -= Ls[i][j] * xj;
+      __syncthreads();
+    }
+  } else {
+    for (int j = kb - 1; j >= 0; --j) {
+      const double xj = xs[j] / Ls[j][j];
+      __syncthreads();
+      if (tid == 0) xs[j] = xj;
+      for (int i = tid; i < j; i += blockDim.x) xs[i] -= Ls[j][i] * xj;
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < kb; i += blockDim.x) x[k0 + i] = xs[i];
+}
+
+// forward update: x[i] -= sum_{j in blk} L[i,j] x[j] for i >= k0+kb (warp per row)
+__global__ void k_trsv_upd_fwd(int m, int k0, int kb, const double* __restrict__ L, long long ldl, double* x) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int i = k0 + kb + warp;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int j = lane; j < kb; j += 32) s += L[(long long)i * ldl + k0 + j] * x[k0 + j];
+  s = warp_sum(s);
+  if (lane == 0) x[i] -= s;
+}
+
+// backward update: x[i] -= sum_{j in blk} L[j,i] x[j] for i < k0 (thread per i)
+__global__ void k_trsv_upd_bwd(int k0, int kb, const double* __restrict__ L, long long ldl, double* x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k0) return;
+  double s = 0.0;
+  for (int j = 0; j < kb; ++j) s += L[(long long)(k0 + j) * ldl + i] * x[k0 + j];
+  x[i] -= s;
+}
+
+dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* b, double* x, cudaStream_t st) {
+  if (x != b) DNGD_CUDA_CHECK(cudaMemcpyAsync(x, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+  for (int k0 = 0; k0 < m; k0 += kTrsvNB) {
+    const int kb = (m - k0) < kTrsvNB ? (m - k0) : kTrsvNB;
+    k_trsv_diag<<<1, 64, 0, st>>>(k0, kb, L, ldl, x, 0);
+    const int rest = m - k0 - kb;
+    if (rest > 0) k_trsv_upd_fwd<<<cdiv((long long)rest * 32, 256), 256, 0, st>>>(m, k0, kb, L, ldl, x);
+  }
+  const int nblk = cdiv(m, kTrsvNB);
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int k0 = bi * kTrsvNB;
+    const int kb = (m - k0) < kTrsvNB ? (m - k0) : kTrsvNB;
+    k_trsv_diag<<<1, 64, 0, st>>>(k0, kb, L, ldl, x, 1);
+    if (k0 > 0) k_trsv_upd_bwd<<<cdiv(k0, 128), 128, 0, st>>>(k0, kb, L, ldl, x);
+  }
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Explicit inverse of a lower-triangular FP32 factor (recursive 2x2 blocks:
+// inv([[A,0],[B,C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]]); the diagonal blocks
+// are inverted in FP64 in shared memory.  Linv must be zero-initialised.
+// ---------------------------------------------------------------------------
+
+__global__ void k_trtri_diag(int k0, int kb, const float* __restrict__ L, long long ldl, float* Linv,
+                             long long ldi) {
+  extern __shared__ unsigned char trtri_smem[];
+  double(*Ls)[kCholNB + 1] = reinterpret_cast<double(*)[kCholNB + 1]>(trtri_smem);
+  double(*Xs)[kCholNB + 1] = Ls + kCholNB;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    Ls[i][j] = (j <= i) ? (double)L[(long long)(k0 + i) * ldl + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  // column c of the inverse by forward substitution (thread per column)
+  for (int c = tid; c < kb; c += blockDim.x) {
+    for (int i = 0; i < kb; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int p = c; p < i; ++p) s -= Ls[i][p] * Xs[p][c];
+      Xs[i][c] = (i < c) ? 0.0 : s / Ls[i][i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    Linv[(long long)(k0 + i) * ldi + k0 + j] = (j <= i) ? (float)Xs[i][j] : 0.0f;
+  }
+}
+
+static dngd_status trtri_rec(int k0, int n, const float* L, long long ldl, float* Linv, long long ldi, float* work,
+                             cudaStream_t st) {
+  if (n <= kCholNB) {
+    const int smem = 2 * kCholNB * (kCholNB + 1) * (int)sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+      DNGD_CUDA_CHECK(cudaFuncSetAttribute(k_trtri_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      attr_set = true;
+    }
+    k_trtri_diag<<<1, 64, smem, st>>>(k0, n, L, ldl, Linv, ldi);
+    DNGD_LAUNCH_CHECK();
+    return DNGD_OK;
+  }
+  const int n1 = ((n / 2 + kCholNB - 1) / kCholNB) * kCholNB;
+  const int n2 = n - n1;
+  dngd_status s = trtri_rec(k0, n1, L, ldl, Linv, ldi, work, st);
+  if (s) return s;
+  s = trtri_rec(k0 + n1, n2, L, ldl, Linv, ldi, work, st);
+  if (s) return s;
+  // T = L21 * Linv11  (n2 x n1), stored in work with ld n1
+  const float* L21 = L + (long long)(k0 + n1) * ldl + k0;
+  const float* I11 = Linv + (long long)k0 * ldi + k0;
+  const float* I22 = Linv + (long long)(k0 + n1) * ldi + k0 + n1;
+  float* I21 = Linv + (long long)(k0 + n1) * ldi + k0;
+  s = gemm_nn<float>(n2, n1, n1, 1.0f, L21, ldl, I11, ldi, 0.0f, work, n1, st);
+  if (s) return s;
+  return gemm_nn<float>(n2, n1, n2, -1.0f, I22, ldi, work, n1, 0.0f, I21, ldi, st);
+}
+
+dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
+                            cudaStream_t st) {
+  DNGD_CUDA_CHECK(cudaMemsetAsync(Linv, 0, sizeof(float) * (size_t)m * ldi, st));
+  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st);
+}
+
+// ---------------------------------------------------------------------------
+// GEMV.  FP64 data accumulates in FP64; FP32 data accumulates the exact
+// products of the FP32 entry with the hi/lo FP32 split of the FP64 vector in
+// double-float arithmetic, so the FP32 operator is applied without adding
+// FP32 rounding of its own, at HBM speed.
+// ---------------------------------------------------------------------------
+
+template <typename TA>
+struct Acc;
+template <>
+struct Acc<double> {
+  double v;
+  __device__ void init() { v = 0.0; }
+  __device__ void add(double a, double xhi, double xlo) { v = fma(a, xhi, v); (void)xlo; }
+  __device__ double get() const { return v; }
+  __device__ void warp_reduce() { v = warp_sum(v); }
+};
+template <>
+struct Acc<float> {
+  dfloat v;
+  __device__ void init() { v.hi = 0.f; v.lo = 0.f; }
+  __device__ void add(float a, float xhi, float xlo) {
+    v = df_fma(v, a, xhi);
+    v.lo = fmaf(a, xlo, v.lo);
+  }
+  // hi + lo is exact in float64 (|lo| <= ulp(hi)/2)
+  __device__ double get() const { return (double)v.hi + (double)v.lo; }
+  __device__ void warp_reduce() { v = df_warp_sum(v); }
+};
+
+template <typename TA>
+__device__ __forceinline__ void split_x(double x, TA& hi, TA& lo);
+template <>
+__device__ __forceinline__ void split_x<double>(double x, double& hi, double& lo) { hi = x; lo = 0.0; }
+template <>
+__device__ __forceinline__ void split_x<float>(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+constexpr int kGemvSplits = 16;
+
+// partials[split][p] = sum_{i in split rows} A[i,p] x[i]
+template <typename TA>
+__global__ void __launch_bounds__(256) k_gemv_t(int m, int n, const TA* __restrict__ A, long long lda,
+                                                 const double* __restrict__ x, double* __restrict__ partials) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int split = blockIdx.y;
+  const int rows = (m + gridDim.y - 1) / gridDim.y;
+  const int i0 = split * rows, i1 = min(m, i0 + rows);
+  if (p >= n) return;
+  Acc<TA> acc;
+  acc.init();
+  for (int i = i0; i < i1; ++i) {
+    TA hi, lo;
+    split_x<TA>(x[i], hi, lo);
+    acc.add(A[(long long)i * lda + p], hi, lo);
+  }
+  partials[(long long)split * n + p] = acc.get();
+}
+
+__global__ void k_reduce_splits(int n, int splits, const double* __restrict__ partials, double alpha,
+                                double* __restrict__ y) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < splits; ++k) s += partials[(long long)k * n + p];
+  y[p] = alpha * s;
+}
+
+template <typename TA>
+dngd_status gemv_t(int m, int n, const TA* A, long long lda, const double* x, double alpha, double* y,
+                   double* partials, cudaStream_t st) {
+  const int splits = m >= kGemvSplits * 8 ? kGemvSplits : 1;
+  dim3 grid(cdiv(n, 256), splits);
+  k_gemv_t<TA><<<grid, 256, 0, st>>>(m, n, A, lda, x, partials);
+  k_reduce_splits<<<cdiv(n, 256), 256, 0, st>>>(n, splits, partials, alpha, y);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// y[i] = alpha * sum_p A[i,p] x[p]; 4 rows per block of 256 threads.
+template <typename TA>
+__global__ void __launch_bounds__(256) k_gemv_n(int m, int n, const TA* __restrict__ A, long long lda,
+                                                 const double* __restrict__ x, double alpha, double* __restrict__ y) {
+  constexpr int RPB = 4;
+  const int i0 = blockIdx.x * RPB;
+  Acc<TA> acc[RPB];
+#pragma unroll
+  for (int r = 0; r < RPB; ++r) acc[r].init();
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    TA hi, lo;
+    split_x<TA>(x[p], hi, lo);
+#pragma unroll
+    for (int r = 0; r < RPB; ++r)
+      if (i0 + r < m) acc[r].add(A[(long long)(i0 + r) * lda + p], hi, lo);
+  }
+  __shared__ double red[RPB][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < RPB; ++r) {
+    acc[r].warp_reduce();
+    if (lane == 0) red[r][warp] = acc[r].get();
+  }
+  __syncthreads();
+  if (threadIdx.x < RPB && i0 + (int)threadIdx.x < m) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
+    y[i0 + threadIdx.x] = alpha * t;
+  }
+}
+
+template <typename TA>
+dngd_status gemv_n(int m, int n, const TA* A, long long lda, const double* x, double alpha, double* y,
+                   cudaStream_t st) {
+  k_gemv_n<TA><<<cdiv(m, 4), 256, 0, st>>>(m, n, A, lda, x, alpha, y);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+template dngd_status gemv_t<double>(int, int, const double*, long long, const double*, double, double*, double*,
+                                    cudaStream_t);
+template dngd_status gemv_t<float>(int, int, const float*, long long, const double*, double, double*, double*,
+                                   cudaStream_t);
+template dngd_status gemv_n<double>(int, int, const double*, long long, const double*, double, double*,
+                                    cudaStream_t);
+template dngd_status gemv_n<float>(int, int, const float*, long long, const double*, double, double*,
+                                   cudaStream_t);
+
+// y = L x or L^T x with an explicit lower-triangular FP32 matrix (zeros above).
+dngd_status trmv_f32(int m, const float* L, long long ldl, const double* x, double* y, bool trans,
+                     cudaStream_t st) {
+  (void)trans;
+  return gemv_n<float>(m, m, L, ldl, x, 1.0, y, st);
+}
+
+template <typename T>
+__global__ void k_add_diag(int m, T* K, long long ldk, double shift) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) K[(long long)i * ldk + i] += (T)shift;
+}
+
+template <typename T>
+dngd_status add_diag(int m, T* K, long long ldk, double shift, cudaStream_t st) {
+  k_add_diag<T><<<cdiv(m, 256), 256, 0, st>>>(m, K, ldk, shift);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+template dngd_status add_diag<double>(int, double*, long long, double, cudaStream_t);
+template dngd_status add_diag<float>(int, float*, long long, double, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Deterministic dot product: fixed grid, per-block partial, second pass.
+// ---------------------------------------------------------------------------
+
+constexpr int kDotBlocks = 128;
+
+__global__ void k_dot_partial(int n, const double* __restrict__ x, const double* __restrict__ y,
+                              double* __restrict__ partials) {
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += x[i] * y[i];
+  s = warp_sum(s);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_dot_final(int nb, const double* __restrict__ partials, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) s += partials[i];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+dngd_status dot_dev(int n, const double* x, const double* y, double* out, double* partials, cudaStream_t st) {
+  k_dot_partial<<<kDotBlocks, 256, 0, st>>>(n, x, y, partials);
+  k_dot_final<<<1, 32, 0, st>>>(kDotBlocks, partials, out);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+__global__ void k_axpy(int n, double alpha, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += alpha * x[i];
+}
+
+dngd_status axpy_dev(int n, double alpha, const double* x, double* y, cudaStream_t st) {
+  k_axpy<<<cdiv(n, 256), 256, 0, st>>>(n, alpha, x, y);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+}  // namespace dngd

@@ -1,0 +1,188 @@
+// Small device kernels of the step: precision conversion, the geodesic
+// acceleration acceptance test, and the scalar / vector updates of the
+// preconditioned CG loops (all scalars stay on the device).
+#include "common.cuh"
+#include "kernels.h"
+#include "step_kernels.h"
+
+namespace dngd {
+
+__global__ void k_to_float(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+dngd_status to_float(long long n, const double* x, float* y, cudaStream_t st) {
+  k_to_float<<<cdiv(n, 256), 256, 0, st>>>(n, x, y);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// theta_out = theta + eta * delta
+__global__ void k_axpy_to(long long n, const double* __restrict__ x, double eta, const double* __restrict__ d,
+                          double* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i] + eta * (d ? d[i] : 0.0);
+}
+
+dngd_status axpy_to(long long n, const double* x, double eta, const double* d, double* y, cudaStream_t st) {
+  k_axpy_to<<<cdiv(n, 256), 256, 0, st>>>(n, x, eta, d, y);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// GA acceptance (Alg. DenseDualSolve): scal[S_NV2], scal[S_NA2] hold ||v||^2,
+// ||a||^2.  Writes ratio / accepted to scal and delta = v (+ a/2).
+__global__ void k_ga_decide(double* scal, int use_ga, double eps_norm, double ratio_max) {
+  const double nv = sqrt(scal[S_NV2]);
+  const double na = sqrt(scal[S_NA2]);
+  double ratio = nan("");
+  int acc = 0;
+  if (use_ga && nv > eps_norm) {
+    ratio = 2.0 * na / nv;
+    acc = ratio <= ratio_max ? 1 : 0;
+  }
+  scal[S_RATIO] = ratio;
+  scal[S_ACCEPT] = (double)acc;
+}
+
+__global__ void k_ga_delta(long long n, const double* __restrict__ v, const double* __restrict__ a,
+                           const double* __restrict__ scal, double* __restrict__ delta, int* status) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool acc = scal[S_ACCEPT] != 0.0;
+  const double d = acc ? v[i] + 0.5 * a[i] : v[i];
+  delta[i] = d;
+  if (!isfinite(d)) atomicOr(status, ST_NONFINITE);
+}
+
+dngd_status ga_finish(int n, const double* v, const double* a, int use_ga, double eps_norm, double ratio_max,
+                      double* delta, double* scal, double* partials, int* status, cudaStream_t st) {
+  dngd_status s = dot_dev(n, v, v, scal + S_NV2, partials, st);
+  if (s) return s;
+  if (use_ga) {
+    s = dot_dev(n, a, a, scal + S_NA2, partials, st);
+    if (s) return s;
+  } else {
+    DNGD_CUDA_CHECK(cudaMemsetAsync(scal + S_NA2, 0, sizeof(double), st));
+  }
+  k_ga_decide<<<1, 1, 0, st>>>(scal, use_ga, eps_norm, ratio_max);
+  k_ga_delta<<<cdiv(n, 256), 256, 0, st>>>(n, v, use_ga ? a : v, scal, delta, status);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// ---- preconditioned CG helpers (device scalars) ---------------------------
+
+// alpha = rho / pAp (breakdown if pAp <= 1e-300)
+__global__ void k_cg_alpha(double* scal) {
+  const double pAp = scal[S_PAP];
+  if (!(pAp > 1e-300)) {
+    scal[S_ALPHA] = 0.0;
+    scal[S_BREAK] = 1.0;
+  } else {
+    scal[S_ALPHA] = scal[S_RHO] / pAp;
+  }
+}
+
+// x += alpha p ; res -= alpha Ap
+__global__ void k_cg_update_x(int m, const double* scal, double* __restrict__ x, double* __restrict__ res,
+                              const double* __restrict__ p, const double* __restrict__ Ap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const double al = scal[S_ALPHA];
+  x[i] += al * p[i];
+  res[i] -= al * Ap[i];
+}
+
+// beta = rho_new / rho ; rho = rho_new
+__global__ void k_cg_beta(double* scal) {
+  const double rn = scal[S_RHONEW];
+  if (rn == 0.0 || scal[S_RHO] == 0.0) {
+    scal[S_BETA] = 0.0;
+    scal[S_BREAK] = 1.0;
+  } else {
+    scal[S_BETA] = rn / scal[S_RHO];
+  }
+  scal[S_RHO] = rn;
+}
+
+// p = z + beta p
+__global__ void k_cg_update_p(int m, const double* scal, const double* __restrict__ z, double* __restrict__ p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  p[i] = z[i] + scal[S_BETA] * p[i];
+}
+
+dngd_status cg_alpha(double* scal, cudaStream_t st) {
+  k_cg_alpha<<<1, 1, 0, st>>>(scal);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+dngd_status cg_update_x(int m, const double* scal, double* x, double* res, const double* p, const double* Ap,
+                        cudaStream_t st) {
+  k_cg_update_x<<<cdiv(m, 256), 256, 0, st>>>(m, scal, x, res, p, Ap);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+dngd_status cg_beta(double* scal, cudaStream_t st) {
+  k_cg_beta<<<1, 1, 0, st>>>(scal);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+dngd_status cg_update_p(int m, const double* scal, const double* z, double* p, cudaStream_t st) {
+  k_cg_update_p<<<cdiv(m, 256), 256, 0, st>>>(m, scal, z, p);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// y = y + s * x  (s a host scalar)
+__global__ void k_axpby(int m, double s, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) y[i] += s * x[i];
+}
+dngd_status add_scaled(int m, double s, const double* x, double* y, cudaStream_t st) {
+  k_axpby<<<cdiv(m, 256), 256, 0, st>>>(m, s, x, y);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// Copy the lower triangle of a [m x m] matrix to float64 (upper = 0).
+template <typename T>
+__global__ void k_lower_to_f64(int m, const T* __restrict__ A, long long lda, double* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * m) return;
+  const int i = (int)(idx / m), j = (int)(idx % m);
+  out[idx] = j <= i ? (double)A[(long long)i * lda + j] : 0.0;
+}
+
+template <typename T>
+dngd_status lower_to_f64(int m, const T* A, long long lda, double* out, cudaStream_t st) {
+  const long long tot = (long long)m * m;
+  k_lower_to_f64<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(m, A, lda, out);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+template dngd_status lower_to_f64<double>(int, const double*, long long, double*, cudaStream_t);
+template dngd_status lower_to_f64<float>(int, const float*, long long, double*, cudaStream_t);
+
+// Row-major [m x n] (ld) -> dense float64 [m x n]
+template <typename T>
+__global__ void k_rows_to_f64(int m, long long n, const T* __restrict__ A, long long lda, double* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * n) return;
+  const long long i = idx / n, j = idx % n;
+  out[idx] = (double)A[i * lda + j];
+}
+
+template <typename T>
+dngd_status rows_to_f64(int m, long long n, const T* A, long long lda, double* out, cudaStream_t st) {
+  const long long tot = (long long)m * n;
+  k_rows_to_f64<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(m, n, A, lda, out);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+template dngd_status rows_to_f64<double>(int, long long, const double*, long long, double*, cudaStream_t);
+template dngd_status rows_to_f64<float>(int, long long, const float*, long long, double*, cudaStream_t);
+
+}  // namespace dngd

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the D-NGD C ABI (include/dngd.h).
+
+Argument marshalling only: every step of the D-NGD path runs in the CUDA
+library.  Arrays may be torch tensors (CUDA or CPU, float64, contiguous) or
+numpy float64 arrays (host).  Device tensors are passed by pointer; host
+arrays are staged by the library itself.  If the library is missing the import
+fails loudly; there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdngd.so")
+
+MAX_LAYERS = 12
+MAX_DIM = 8
+MAX_CLASSES = 4
+
+FP64, MIXED_BF16, MIXED_TF32 = 0, 1, 2
+DENSE, PCG = 0, 1
+
+STATUS = {
+    0: "DNGD_OK", -1: "DNGD_ERR_INVALID_ARG", -2: "DNGD_ERR_NOT_SPD", -3: "DNGD_ERR_NO_CONVERGE",
+    -4: "DNGD_ERR_NONFINITE", -5: "DNGD_ERR_BUDGET", -6: "DNGD_ERR_TIMEOUT", -7: "DNGD_ERR_CUDA",
+    -8: "DNGD_ERR_STATE", -9: "DNGD_ERR_OOM",
+}
+
+STAGES = dict(r=0, alpha=1, v=2, fvv=3, beta=4, a=5, gram=6, chol=7)
+
+
+class DngdError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class ClassDesc(C.Structure):
+    _fields_ = [("count", C.c_int), ("c_val", C.c_double), ("c_grad", C.c_double * MAX_DIM),
+                ("c_lap", C.c_double), ("lap_mask", C.c_int * MAX_DIM)]
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("widths", C.c_int * (MAX_LAYERS + 1)), ("n_classes", C.c_int),
+                ("classes", ClassDesc * MAX_CLASSES), ("precision", C.c_int), ("solver", C.c_int),
+                ("lam", C.c_double), ("use_ga", C.c_int), ("eps_norm", C.c_double),
+                ("ga_ratio_max", C.c_double), ("refine_max_it", C.c_int), ("refine_tol", C.c_double),
+                ("shift_mu", C.c_double), ("pcg_rank", C.c_int), ("pcg_tol", C.c_double),
+                ("pcg_max_it", C.c_int), ("pcg_seed", C.c_uint64), ("keep_gram", C.c_int)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("loss", C.c_double), ("norm_v", C.c_double), ("norm_a", C.c_double), ("ga_ratio", C.c_double),
+                ("ga_accepted", C.c_int), ("solve_iters", C.c_int * 2), ("solve_relres", C.c_double * 2),
+                ("not_spd_column", C.c_int), ("device_status", C.c_int), ("phase_ms", C.c_float * 8)]
+
+    def as_dict(self):
+        return dict(loss=self.loss, norm_v=self.norm_v, norm_a=self.norm_a, ga_ratio=self.ga_ratio,
+                    ga_accepted=bool(self.ga_accepted), solve_iters=list(self.solve_iters),
+                    solve_relres=list(self.solve_relres), not_spd_column=self.not_spd_column,
+                    device_status=self.device_status, phase_ms=list(self.phase_ms))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libdngd.so not built at {LIB_PATH}: run __graft_entry__.build() (no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    D = C.POINTER(C.c_double)
+    sigs = {
+        "dngd_status_string": (C.c_char_p, [C.c_int]),
+        "dngd_version": (C.c_char_p, []),
+        "dngd_num_params": (C.c_int64, [C.POINTER(ProblemDesc)]),
+        "dngd_create": (C.c_int, [C.POINTER(P), C.POINTER(ProblemDesc), P]),
+        "dngd_workspace_bytes": (C.c_int, [C.POINTER(ProblemDesc), C.POINTER(C.c_size_t)]),
+        "dngd_destroy": (C.c_int, [P]),
+        "dngd_set_timing": (C.c_int, [P, C.c_int]),
+        "dngd_set_lambda": (C.c_int, [P, C.c_double]),
+        "dngd_step": (C.c_int, [P, P, P, P, P, C.POINTER(StepInfo)]),
+        "dngd_solve": (C.c_int, [P, P, P]),
+        "dngd_loss": (C.c_int, [P, P, P, P, P, D, C.c_int, D]),
+        "dngd_line_search": (C.c_int, [P, P, P, P, P, D, C.c_int, P, D]),
+        "dngd_residual_jacobian": (C.c_int, [P, P, P, P, P, P]),
+        "dngd_fvv": (C.c_int, [P, P, P, P, P, P]),
+        "dngd_get_stage": (C.c_int, [P, C.c_int, P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+EXPORTED = ["dngd_status_string", "dngd_version", "dngd_num_params", "dngd_create", "dngd_workspace_bytes",
+            "dngd_destroy", "dngd_set_timing", "dngd_set_lambda", "dngd_step", "dngd_solve", "dngd_loss",
+            "dngd_line_search", "dngd_residual_jacobian", "dngd_fvv", "dngd_get_stage"]
+
+
+def _check(status, where):
+    if status != 0:
+        raise DngdError(status, where)
+
+
+def _ptr(a):
+    """Pointer of a float64 array: torch tensor (CUDA or CPU) or numpy."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return C.c_void_p(a.data_ptr())
+    assert isinstance(a, np.ndarray) and a.flags.c_contiguous
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_ratio_max=0.5, refine_max_it=200,
+              refine_tol=1e-10, shift_mu=0.0, keep_gram=False):
+    """Problem descriptor from a workload dict (see workloads.py)."""
+    d = ProblemDesc()
+    widths = list(spec["widths"])
+    d.n_layers = len(widths) - 1
+    for i, w in enumerate(widths):
+        d.widths[i] = int(w)
+    d.n_classes = len(spec["classes"])
+    for c, cl in enumerate(spec["classes"]):
+        cd = d.classes[c]
+        cd.count = int(cl["count"])
+        cd.c_val = float(cl["c_val"])
+        for k, g in enumerate(cl["c_grad"]):
+            cd.c_grad[k] = float(g)
+        cd.c_lap = float(cl["c_lap"])
+        for k, b in enumerate(cl["lap_mask"]):
+            cd.lap_mask[k] = int(bool(b))
+    d.precision = int(precision)
+    d.solver = DENSE
+    d.lam = float(spec["lam"] if lam is None else lam)
+    d.use_ga = int(bool(use_ga))
+    d.eps_norm = float(eps_norm)
+    d.ga_ratio_max = float(ga_ratio_max)
+    d.refine_max_it = int(refine_max_it)
+    d.refine_tol = float(refine_tol)
+    d.shift_mu = float(shift_mu)
+    d.keep_gram = int(bool(keep_gram))
+    return d
+
+
+def dngd_num_params(desc):
+    return int(lib.dngd_num_params(C.byref(desc)))
+
+
+def dngd_workspace_bytes(desc):
+    b = C.c_size_t(0)
+    _check(lib.dngd_workspace_bytes(C.byref(desc), C.byref(b)), "dngd_workspace_bytes")
+    return int(b.value)
+
+
+class Context:
+    """One step context (dngd_create / dngd_destroy)."""
+
+    def __init__(self, desc, stream=None):
+        self.desc = desc
+        self._h = C.c_void_p()
+        s = C.c_void_p(int(stream)) if stream else None
+        _check(lib.dngd_create(C.byref(self._h), C.byref(desc), s), "dngd_create")
+        self.n = dngd_num_params(desc)
+        self.m = sum(desc.classes[c].count for c in range(desc.n_classes))
+
+    def close(self):
+        if self._h:
+            lib.dngd_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_timing(self, on=True):
+        _check(lib.dngd_set_timing(self._h, int(on)), "dngd_set_timing")
+
+    def set_lambda(self, lam):
+        _check(lib.dngd_set_lambda(self._h, float(lam)), "dngd_set_lambda")
+
+    def step(self, theta, X, target, delta_out, want_info=True):
+        info = StepInfo() if want_info else None
+        st = lib.dngd_step(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(delta_out),
+                           C.byref(info) if info is not None else None)
+        _check(st, "dngd_step")
+        return info.as_dict() if info is not None else None
+
+    def solve(self, rhs, x_out):
+        _check(lib.dngd_solve(self._h, _ptr(rhs), _ptr(x_out)), "dngd_solve")
+
+    def loss(self, theta, X, target, delta, etas):
+        etas = np.ascontiguousarray(etas, dtype=np.float64)
+        out = np.zeros(etas.size)
+        dp = C.POINTER(C.c_double)
+        _check(lib.dngd_loss(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(delta),
+                             etas.ctypes.data_as(dp), int(etas.size), out.ctypes.data_as(dp)), "dngd_loss")
+        return out
+
+    def line_search(self, theta, X, target, delta, etas, theta_out):
+        etas = np.ascontiguousarray(etas, dtype=np.float64)
+        eta = C.c_double(0.0)
+        _check(lib.dngd_line_search(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(delta),
+                                    etas.ctypes.data_as(C.POINTER(C.c_double)), int(etas.size), _ptr(theta_out),
+                                    C.byref(eta)), "dngd_line_search")
+        return eta.value
+
+    def residual_jacobian(self, theta, X, target, r_out, J_out=None):
+        _check(lib.dngd_residual_jacobian(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(r_out),
+                                          _ptr(J_out)), "dngd_residual_jacobian")
+
+    def fvv(self, theta, X, target, v, out):
+        _check(lib.dngd_fvv(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(v), _ptr(out)), "dngd_fvv")
+
+    def get_stage(self, name, out):
+        _check(lib.dngd_get_stage(self._h, STAGES[name], _ptr(out)), "dngd_get_stage")
