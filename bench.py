@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the D-NGD step on one GB300 (one JSON line on stdout).
+
+Workload: 5-D Poisson -Laplace(u) = f on [0,1]^5, u = sum_i sin(pi x_i), tanh MLP
+5-256-256-256-1 (n = 133,377), 3,000 interior + 1,000 boundary points
+(m = 4,000), Glorot init (seed 0), lambda = 1e-5 (the paper's rule
+lambda_k = min(loss, 1e-5) at this loss).  One timed step = one D-NGD
+iteration: dngd_step (jets + J, Gram K + lambda I on tcgen05 tensor cores,
+factor, refined solve for v, f_vv, refined solve for a, GA test) followed by
+the 31-point grid line search and the parameter update (dngd_line_search).
+
+Reported: steps/s of the mixed path (value, device-resident inputs), the same
+through host buffers (e2e), the FP64 GPU path's steps/s and step errors
+against a full FP64 CPU oracle step at the same theta, Gram TFLOP/s against
+the measured tensor peak, p50/p99 step latency and clocks under load.
+
+--impl reference: the FP64 CPU oracle on the host cores (the slow baseline).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D-NGD steps/s mixed vs FP64 at equal step error; Gram TFLOP/s; p99 step latency"
+UNIT = "steps/s"
+WORKLOAD = "poisson5d_dense: -Lap u = f on [0,1]^5, MLP 5-256-256-256-1 (n=133377), 3000+1000 pts (m=4000)"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def _grid():
+    return np.array([2.0 ** (-j) for j in range(31)])
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks / throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_full_step(wl, lam):
+    """One full FP64 oracle step (stage timings in seconds)."""
+    from oracle import residual as ores, step as ostep
+    prob = ores.problem_from_spec(wl)
+    t = {}
+    t0 = time.perf_counter()
+    r, J = ores.residual_and_jacobian(wl["theta"], prob, wl["X"], wl["target"])
+    t["jacobian"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    K = ostep.gram(J, lam)
+    t["gram"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L = ostep.cholesky(K)
+    del K
+    t["cholesky"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    alpha = ostep.chol_solve(L, r)
+    v = -(J.T @ alpha)
+    t["solve_v"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    fvv = ores.second_directional(wl["theta"], prob, wl["X"], wl["target"], v)
+    t["fvv"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    beta = ostep.chol_solve(L, fvv)
+    a = -(J.T @ beta)
+    delta, ratio, acc = ostep.ga_accept(v, a)
+    t["solve_a"] = time.perf_counter() - t0
+    return dict(delta=delta, v=v, a=a, alpha=alpha, accepted=acc, ratio=ratio), t
+
+
+def _threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((i.get("num_threads", 0) for i in threadpool_info()), default=None)
+    except Exception:
+        return os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+
+
+def run_reference(args, wl):
+    """--impl reference: the FP64 CPU oracle (the paper's method written plainly)."""
+    steps = min(args.steps, 2)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle_full_step(wl, args.lam)
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * float(np.mean(times))
+    cores = len(os.sched_getaffinity(0))
+    value = 1000.0 / ms
+    sample = (f"{steps} full FP64 oracle step(s) of the workload from theta_0 (no warm-up; --steps capped at 2: "
+              f"one step is ~{ms / 1000:.0f} s of CPU work); line search not included")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lam": args.lam},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "blas_threads": _threads()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lam", type=float, default=1e-5)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle leg (no step error)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--refine-max-it", type=int, default=200)
+    ap.add_argument("--workload", default="poisson5d", choices=["poisson5d", "poisson5d_w128"],
+                    help="poisson5d_w128: same points, hidden width 128 (profiling case, n=33,537)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2505_21404_gb300 import workloads
+    if args.workload == "poisson5d":
+        wl = workloads.poisson5d_dense(seed=0, lam=args.lam)
+    else:
+        wl = workloads.poisson_sine(5, [5, 128, 128, 128, 1], 3000, 1000, k=1, seed=0, lam=args.lam)
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+
+    import torch
+    from paper_2505_21404_gb300 import dngd
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    dev = torch.device(f"cuda:{local_rank}")
+    stream = torch.cuda.current_stream(dev)
+
+    # CPU oracle leg first (rank 0, N = 1 only): timing + the error reference
+    ref = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_oracle:
+        t0 = time.perf_counter()
+        ref, stages = oracle_full_step(wl, args.lam)
+        t_or = time.perf_counter() - t0
+        cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": f"1 full FP64 oracle step of the workload at theta_0 ({t_or:.1f} s; stages " +
+                         ", ".join(f"{k} {v:.1f}s" for k, v in stages.items()) +
+                         "); line search not included",
+               "blas_threads": _threads()}
+
+    prec = dngd.MIXED_BF16 if args.precision == "bf16" else dngd.MIXED_TF32
+    m, n = int(wl["X"].shape[0]), dngd.dngd_num_params(dngd.make_desc(wl))
+    th0 = torch.tensor(wl["theta"], device=dev)
+    X = torch.tensor(wl["X"], device=dev)
+    tg = torch.tensor(wl["target"], device=dev)
+    etas = _grid()
+
+    ctx = dngd.Context(dngd.make_desc(wl, precision=prec, refine_tol=1e-7, refine_max_it=args.refine_max_it),
+                       stream=stream.cuda_stream)
+    ctx.set_timing(True)
+    delta = torch.zeros(n, dtype=torch.float64, device=dev)
+    theta = th0.clone()
+    theta_next = torch.zeros_like(theta)
+
+    # step error of the mixed path at theta_0
+    info0 = ctx.step(th0, X, tg, delta)
+    torch.cuda.synchronize(dev)
+    d_mixed0 = delta.cpu().numpy().copy()
+
+    def one_step(th, out_th):
+        info = ctx.step(th, X, tg, delta)
+        ctx.line_search(th, X, tg, delta, etas, out_th)
+        return info
+
+    for _ in range(args.warmup):
+        one_step(theta, theta_next)
+        theta, theta_next = theta_next, theta
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = dngd.dngd_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    infos = []
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for k in range(args.steps):
+        step_ev[k][0].record(stream)
+        infos.append(one_step(theta, theta_next))
+        step_ev[k][1].record(stream)
+        theta, theta_next = theta_next, theta
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = dngd.dngd_launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    lat = np.array([a.elapsed_time(b) for a, b in step_ev])
+    value = world * 1000.0 / ms_per_step
+    gram_ms = float(np.mean([i["phase_ms"][1] for i in infos]))
+    phase = np.mean(np.array([i["phase_ms"] for i in infos]), axis=0).tolist()
+    iters = np.mean(np.array([i["solve_iters"] for i in infos]), axis=0).tolist()
+
+    # end to end through host buffers (staging copies inside the timed region)
+    e2e_ms = float("nan")
+    h2d = 8 * (n + m * 5 + m) + 8 * (2 * n + m * 5 + m)   # step inputs + line-search inputs
+    d2h = 8 * n + 8 * n                                       # delta + updated theta
+    th_h = wl["theta"].copy()
+    X_h = np.ascontiguousarray(wl["X"])
+    tg_h = np.ascontiguousarray(wl["target"])
+    d_h = np.zeros(n)
+    th_next_h = np.zeros(n)
+    e2e_steps = max(3, min(args.steps, 10))
+    if not args.no_e2e:
+        ctx.step(th_h, X_h, tg_h, d_h, want_info=False)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.step(th_h, X_h, tg_h, d_h, want_info=False)
+            ctx.line_search(th_h, X_h, tg_h, d_h, etas, th_next_h)
+            th_h, th_next_h = th_next_h, th_h
+        torch.cuda.synchronize(dev)
+        e2e_ms = 1000.0 * (time.perf_counter() - t0) / e2e_steps
+    ctx.close()
+
+    # FP64 GPU path at theta_0
+    fp64 = None
+    if not args.no_fp64:
+        ctx64 = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64), stream=stream.cuda_stream)
+        ctx64.set_timing(True)
+        d64 = torch.zeros(n, dtype=torch.float64, device=dev)
+        ctx64.step(th0, X, tg, d64)
+        torch.cuda.synchronize(dev)
+        t64 = []
+        for _ in range(args.fp64_steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            i64 = ctx64.step(th0, X, tg, d64)
+            ctx64.line_search(th0, X, tg, d64, etas, theta_next)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t64.append(e0.elapsed_time(e1))
+        d64h = d64.cpu().numpy()
+        fp64 = {"steps_per_s": 1000.0 / float(np.mean(t64)), "ms_per_step": float(np.mean(t64)),
+                "gram_ms": i64["phase_ms"][1], "phase_ms": i64["phase_ms"]}
+        ctx64.close()
+
+    hbm, bf16_burst, bf16_sust, src = _peaks()
+    gram_flops = float(m) * (m + 1) * n
+    achieved = gram_flops / (gram_ms * 1e-3) / 1e12
+    peak = bf16_sust if prec == dngd.MIXED_BF16 else bf16_sust / 2.0
+    err = {}
+    if ref is not None:
+        nr = np.linalg.norm(ref["delta"])
+        err["mixed_vs_oracle"] = float(np.linalg.norm(d_mixed0 - ref["delta"]) / nr)
+        if fp64 is not None:
+            err["fp64_vs_oracle"] = float(np.linalg.norm(d64h - ref["delta"]) / nr)
+    if fp64 is not None:
+        err["mixed_vs_fp64_gpu"] = float(np.linalg.norm(d_mixed0 - d64h) / np.linalg.norm(d64h))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16/f32 (f64 diagonal blocks, double-float refinement)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "poisson5d" else args.workload, "lam": args.lam, "precision": f"mixed-{args.precision}",
+                   "step": "dngd_step + 31-point line search + update",
+                   "l2": "working set larger than L2 (J: 2.13 GB FP32 + 1.07 GB BF16 per step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "gram_tflops": achieved, "fp64": fp64, "step_error": err,
+        "speedup_vs_fp64": (value / world) / fp64["steps_per_s"] if fp64 else None,
+        "refine_iters": iters, "phase_ms": phase, "ga_accepted_at_theta0": info0["ga_accepted"],
+        "roofline": {"bound": "tensor", "kernel": "k_gram_tc (tcgen05 BF16 syrk, lower tiles)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"{src} bf16 sustained" + (" / 2 for tf32" if prec != dngd.MIXED_BF16 else ""),
+                     "traffic": None},
+        "cpu_baseline": cpu,
+        "e2e": {"value": 1000.0 / e2e_ms * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

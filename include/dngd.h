@@ -127,6 +127,12 @@ typedef struct {
   int device_status;        /* raw device status word */
   float phase_ms[8];        /* jets+J, Gram, factor, solve r, f_vv, solve f_vv,
                                finish, total (filled when timing is enabled) */
+  double shift_used;        /* diagonal shift mu of the factored preconditioner
+                               (mixed paths).  Starts at max(shift_mu, the
+                               shift that factored in the previous step) and
+                               is raised x10 (at least to 1e-8 trace(K)/m) on
+                               a failed low-precision factorisation, up to 8
+                               tries; the refinement keeps the exact lambda. */
 } dngd_step_info;
 
 typedef struct dngd_ctx dngd_ctx;
@@ -136,6 +142,10 @@ const char* dngd_status_string(dngd_status s);
 
 /* Library version string. */
 const char* dngd_version(void);
+
+/* Number of CUDA kernel launches this library has issued so far (all
+ * contexts, host-side counter).  Differences bracket a region of interest. */
+uint64_t dngd_launch_count(void);
 
 /* Number of parameters n of the MLP described by desc (Sec. 2.1 layout). */
 int64_t dngd_num_params(const dngd_problem_desc* desc);

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -12,6 +13,11 @@
 #include "step_kernels.h"
 
 using namespace dngd;
+
+namespace dngd {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace dngd
 
 struct dngd_ctx {
   dngd_problem_desc desc;
@@ -63,6 +69,8 @@ struct dngd_ctx {
   int* status = nullptr;
   int* status_h = nullptr;  // pinned
   int iters[2] = {0, 0};
+  double shift_used = 0.0;
+  double mu_sticky = 0.0;  // preconditioner shift that factored last time
   double relres[2] = {0.0, 0.0};
   cudaEvent_t ev[9] = {};
 };
@@ -312,23 +320,38 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     if ((s = gemm_nt<double>(m, m, n, 1.0, (const double*)c->J, c->ldJ, (const double*)c->J, c->ldJ, 0.0,
                              (double*)c->K, c->ldk, true, c->st)))
       return s;
+    evrec(c, 8);
     if ((s = add_diag<double>(m, (double*)c->K, c->ldk, c->lambda, c->st))) return s;
     if (c->Kcopy)
       DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(double) * (size_t)m * c->ldk,
                                       cudaMemcpyDeviceToDevice, c->st));
-  } else {
-    gram_tc_set_shift(c->gram, c->lambda + c->desc.shift_mu);
-    if ((s = gram_tc_run(c->gram, c->status, c->st))) return s;
-    if (c->Kcopy)
-      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(float) * (size_t)m * c->ldk, cudaMemcpyDeviceToDevice,
-                                      c->st));
-  }
-  evrec(c, 2);
-  // factor
-  if (c->prec == DNGD_FP64) {
+    evrec(c, 2);
     if ((s = cholesky<double>(m, (double*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
   } else {
-    if ((s = cholesky<float>(m, (float*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
+    // low-precision Gram + FP32 factor of K + (lambda + mu) I; a failed
+    // factorisation is retried with a larger shift mu (it only preconditions
+    // the refinement, whose operator keeps the exact lambda)
+    double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
+    for (int attempt = 0;; ++attempt) {
+      gram_tc_set_shift(c->gram, c->lambda + mu);
+      if ((s = gram_tc_run(c->gram, c->status, c->st, c->timing ? c->ev[8] : nullptr))) return s;
+      if (c->Kcopy)
+        DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(float) * (size_t)m * c->ldk,
+                                        cudaMemcpyDeviceToDevice, c->st));
+      if ((s = diag_sum<float>(m, (const float*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
+      evrec(c, 2);
+      if ((s = cholesky<float>(m, (float*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
+      const dngd_status fs = read_status(c);
+      if (fs != DNGD_ERR_NOT_SPD || attempt >= 7) break;
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+      DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+      const double tr = c->scal_h[S_TRACE] - m * (c->lambda + mu);
+      const double base = 1e-8 * (tr > 0 ? tr : 1.0) / m;
+      mu = mu * 10.0 > base ? mu * 10.0 : base;
+      DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+    }
+    c->mu_sticky = mu;
+    c->shift_used = mu;
     if ((s = trtri_lower_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
   }
   // a failed factorisation stops the step here
@@ -382,10 +405,14 @@ dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
   info->solve_relres[1] = c->relres[1];
   info->device_status = c->status_h[0];
   info->not_spd_column = (c->status_h[0] & ST_NOT_SPD) ? c->status_h[1] : -1;
+  info->shift_used = c->shift_used;
   if (c->timing) {
+    // event order: 0 start, 1 jets+J, 8 Gram kernel, 2 Gram epilogue, 3 factor,
+    // 4 solve r, 5 f_vv, 6 solve f_vv, 7 end
+    const int a[7] = {0, 1, 8, 3, 4, 5, 6}, b[7] = {1, 8, 3, 4, 5, 6, 7};
     for (int i = 0; i < 7; ++i) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+      cudaEventElapsedTime(&ms, c->ev[a[i]], c->ev[b[i]]);
       info->phase_ms[i] = ms;
     }
     float tot = 0.f;
@@ -572,6 +599,8 @@ const char* dngd_status_string(dngd_status s) {
 }
 
 const char* dngd_version(void) { return kVersion; }
+
+uint64_t dngd_launch_count(void) { return dngd::g_launches.load(std::memory_order_relaxed); }
 
 int64_t dngd_num_params(const dngd_problem_desc* desc) {
   NetInfo net;

@@ -65,6 +65,10 @@ __host__ __device__ inline const ClassInfo& class_of(const NetInfo& net, int p) 
 
 #define DNGD_LAUNCH_CHECK() DNGD_CUDA_CHECK(cudaGetLastError())
 
+// Host-side count of kernel launches issued by the library (all contexts).
+void note_launch();
+#define DNGD_NOTE_LAUNCH() ::dngd::note_launch()
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------------------

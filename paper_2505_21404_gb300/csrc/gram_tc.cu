@@ -413,8 +413,9 @@ dngd_status gram_tc_set_shift(GramPlan* p, double shift) {
   return DNGD_OK;
 }
 
-dngd_status gram_tc_run(GramPlan* p, int* status, cudaStream_t st) {
+dngd_status gram_tc_run(GramPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_after_mma) {
   dim3 grid(p->ntiles, p->nsplit);
+  DNGD_NOTE_LAUNCH();
   if (p->kind == 0)
     k_gram_tc<0><<<grid, 128, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,
                                                 p->ldp, p->sstride, status);
@@ -422,7 +423,9 @@ dngd_status gram_tc_run(GramPlan* p, int* status, cudaStream_t st) {
     k_gram_tc<1><<<grid, 128, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,
                                                 p->ldp, p->sstride, status);
   DNGD_LAUNCH_CHECK();
+  if (ev_after_mma) cudaEventRecord(ev_after_mma, st);
   const long long tot = (long long)p->m * p->m;
+  DNGD_NOTE_LAUNCH();
   k_gram_reduce<<<(int)((tot + 255) / 256), 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->K,
                                                           p->ldk, p->shift);
   DNGD_LAUNCH_CHECK();

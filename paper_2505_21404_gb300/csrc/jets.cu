@@ -409,16 +409,19 @@ dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, co
     const int w = net.widths[l + 1];
     dim3 grid(net.m, cdiv(w, thr));
     if (l == 0) {
+      DNGD_NOTE_LAUNCH();
       k_first_layer<T><<<grid, thr, 0, st>>>(net, theta, X, Z.p[0], H.p[0]);
     } else {
       dngd_status s = gemm_nt<T>(net.R, w, net.widths[l], T(1), H.p[l - 1], net.widths[l],
                                  theta + net.w_off[l], net.widths[l], T(0), Z.p[l], w, false, st);
       if (s) return s;
+      DNGD_NOTE_LAUNCH();
       k_act_fwd<T><<<grid, thr, 0, st>>>(net, l, theta, Z.p[l], H.p[l]);
     }
     DNGD_LAUNCH_CHECK();
   }
   const T* Hlast = L > 0 ? H.p[L - 1] : nullptr;
+  DNGD_NOTE_LAUNCH();
   k_output<T><<<cdiv((long long)net.m * 32, 256), 256, 0, st>>>(net, theta, X, Hlast, target, r, status);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -433,6 +436,7 @@ dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const dou
   for (int l = L - 1; l >= 0; --l) {
     const int w = net.widths[l + 1];
     dim3 grid(net.m, cdiv(w, thr));
+    DNGD_NOTE_LAUNCH();
     k_act_bwd<T><<<grid, thr, 0, st>>>(net, l, theta, Z.p[l], l == L - 1 ? nullptr : Hbar, D.p[l]);
     DNGD_LAUNCH_CHECK();
     if (l > 0) {
@@ -454,6 +458,7 @@ dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const dou
     cudaFuncSetAttribute(k_jac_write<T, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   dim3 grid(net.m, L + 1);
+  DNGD_NOTE_LAUNCH();
   k_jac_write<T, TJ><<<grid, 256, smem, st>>>(net, theta, X, H, D, J, ldJ, Jb, ldb);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -471,6 +476,7 @@ dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const doubl
     const int w = net.widths[l + 1];
     dim3 grid(net.m, cdiv(w, thr));
     if (l == 0) {
+      DNGD_NOTE_LAUNCH();
       k_first_layer_fvv<T><<<grid, thr, 0, st>>>(net, theta, v, X, Hcur);
     } else {
       const int win = net.widths[l];
@@ -484,6 +490,7 @@ dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const doubl
       if (s) return s;
       s = gemm_nt<T>(net.R, w, win, T(2), Hprev + R * win, win, V, win, T(1), Z3 + 2 * R * w, w, false, st);
       if (s) return s;
+      DNGD_NOTE_LAUNCH();
       k_act_fvv<T><<<grid, thr, 0, st>>>(net, l, theta, v, Z3, Hcur);
     }
     DNGD_LAUNCH_CHECK();
@@ -491,6 +498,7 @@ dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const doubl
     Hprev = Hcur;
     Hcur = tmp;
   }
+  DNGD_NOTE_LAUNCH();
   k_output_fvv<T><<<cdiv((long long)net.m * 32, 256), 256, 0, st>>>(net, theta, v, Hprev, fvv);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;

@@ -80,7 +80,7 @@ dngd_status axpy_dev(int n, double alpha, const double* x, double* y, cudaStream
 struct GramPlan;
 dngd_status gram_tc_plan(GramPlan** plan, int kind, const void* Jlow, int m, int n, long long ld, float* K,
                          long long ldk, float* partials, size_t partial_bytes);
-dngd_status gram_tc_run(GramPlan* plan, int* status, cudaStream_t st);
+dngd_status gram_tc_run(GramPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
 void gram_tc_free(GramPlan* plan);
 size_t gram_tc_partial_bytes(int m, int n);
 

@@ -98,6 +98,7 @@ dngd_status gemm_nt(int M, int N, int K, T alpha, const T* A, long long lda, con
   if (M <= 0 || N <= 0) return DNGD_OK;
   using G = GemmCfg<T>;
   dim3 grid(cdiv(N, G::BN), cdiv(M, G::BM));
+  DNGD_NOTE_LAUNCH();
   k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN, true>
       <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
                                                           lower ? 1 : 0);
@@ -111,6 +112,7 @@ dngd_status gemm_nn(int M, int N, int K, T alpha, const T* A, long long lda, con
   if (M <= 0 || N <= 0) return DNGD_OK;
   using G = GemmCfg<T>;
   dim3 grid(cdiv(N, G::BN), cdiv(M, G::BM));
+  DNGD_NOTE_LAUNCH();
   k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN, false>
       <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0);
   DNGD_LAUNCH_CHECK();
@@ -226,10 +228,12 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
   }
   for (int k0 = 0; k0 < m; k0 += kCholNB) {
     const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
+    DNGD_NOTE_LAUNCH();
     k_potrf_diag<TA><<<1, 256, 0, st>>>(k0, kb, A, lda, status);
     DNGD_LAUNCH_CHECK();
     const int rest = m - k0 - kb;
     if (rest <= 0) break;
+    DNGD_NOTE_LAUNCH();
     k_trsm_panel<TA><<<cdiv(rest, 64), 64, trsm_smem, st>>>(m, k0, kb, A, lda, status);
     DNGD_LAUNCH_CHECK();
     TA* P = A + (long long)(k0 + kb) * lda + k0;
@@ -307,16 +311,24 @@ dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* 
   if (x != b) DNGD_CUDA_CHECK(cudaMemcpyAsync(x, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   for (int k0 = 0; k0 < m; k0 += kTrsvNB) {
     const int kb = (m - k0) < kTrsvNB ? (m - k0) : kTrsvNB;
+    DNGD_NOTE_LAUNCH();
     k_trsv_diag<<<1, 64, 0, st>>>(k0, kb, L, ldl, x, 0);
     const int rest = m - k0 - kb;
-    if (rest > 0) k_trsv_upd_fwd<<<cdiv((long long)rest * 32, 256), 256, 0, st>>>(m, k0, kb, L, ldl, x);
+    if (rest > 0) {
+      DNGD_NOTE_LAUNCH();
+      k_trsv_upd_fwd<<<cdiv((long long)rest * 32, 256), 256, 0, st>>>(m, k0, kb, L, ldl, x);
+    }
   }
   const int nblk = cdiv(m, kTrsvNB);
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int k0 = bi * kTrsvNB;
     const int kb = (m - k0) < kTrsvNB ? (m - k0) : kTrsvNB;
+    DNGD_NOTE_LAUNCH();
     k_trsv_diag<<<1, 64, 0, st>>>(k0, kb, L, ldl, x, 1);
-    if (k0 > 0) k_trsv_upd_bwd<<<cdiv(k0, 128), 128, 0, st>>>(k0, kb, L, ldl, x);
+    if (k0 > 0) {
+      DNGD_NOTE_LAUNCH();
+      k_trsv_upd_bwd<<<cdiv(k0, 128), 128, 0, st>>>(k0, kb, L, ldl, x);
+    }
   }
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -363,6 +375,7 @@ static dngd_status trtri_rec(int k0, int n, const float* L, long long ldl, float
       DNGD_CUDA_CHECK(cudaFuncSetAttribute(k_trtri_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       attr_set = true;
     }
+    DNGD_NOTE_LAUNCH();
     k_trtri_diag<<<1, 64, smem, st>>>(k0, n, L, ldl, Linv, ldi);
     DNGD_LAUNCH_CHECK();
     return DNGD_OK;
@@ -464,7 +477,9 @@ dngd_status gemv_t(int m, int n, const TA* A, long long lda, const double* x, do
                    double* partials, cudaStream_t st) {
   const int splits = m >= kGemvSplits * 8 ? kGemvSplits : 1;
   dim3 grid(cdiv(n, 256), splits);
+  DNGD_NOTE_LAUNCH();
   k_gemv_t<TA><<<grid, 256, 0, st>>>(m, n, A, lda, x, partials);
+  DNGD_NOTE_LAUNCH();
   k_reduce_splits<<<cdiv(n, 256), 256, 0, st>>>(n, splits, partials, alpha, y);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -504,6 +519,7 @@ __global__ void __launch_bounds__(256) k_gemv_n(int m, int n, const TA* __restri
 template <typename TA>
 dngd_status gemv_n(int m, int n, const TA* A, long long lda, const double* x, double alpha, double* y,
                    cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_gemv_n<TA><<<cdiv(m, 4), 256, 0, st>>>(m, n, A, lda, x, alpha, y);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -533,6 +549,7 @@ __global__ void k_add_diag(int m, T* K, long long ldk, double shift) {
 
 template <typename T>
 dngd_status add_diag(int m, T* K, long long ldk, double shift, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_add_diag<T><<<cdiv(m, 256), 256, 0, st>>>(m, K, ldk, shift);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -569,7 +586,9 @@ __global__ void k_dot_final(int nb, const double* __restrict__ partials, double*
 }
 
 dngd_status dot_dev(int n, const double* x, const double* y, double* out, double* partials, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_dot_partial<<<kDotBlocks, 256, 0, st>>>(n, x, y, partials);
+  DNGD_NOTE_LAUNCH();
   k_dot_final<<<1, 32, 0, st>>>(kDotBlocks, partials, out);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -581,6 +600,7 @@ __global__ void k_axpy(int n, double alpha, const double* __restrict__ x, double
 }
 
 dngd_status axpy_dev(int n, double alpha, const double* x, double* y, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_axpy<<<cdiv(n, 256), 256, 0, st>>>(n, alpha, x, y);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;

@@ -13,6 +13,7 @@ __global__ void k_to_float(long long n, const double* __restrict__ x, float* __r
 }
 
 dngd_status to_float(long long n, const double* x, float* y, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_to_float<<<cdiv(n, 256), 256, 0, st>>>(n, x, y);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -26,6 +27,7 @@ __global__ void k_axpy_to(long long n, const double* __restrict__ x, double eta,
 }
 
 dngd_status axpy_to(long long n, const double* x, double eta, const double* d, double* y, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_axpy_to<<<cdiv(n, 256), 256, 0, st>>>(n, x, eta, d, y);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -66,7 +68,9 @@ dngd_status ga_finish(int n, const double* v, const double* a, int use_ga, doubl
   } else {
     DNGD_CUDA_CHECK(cudaMemsetAsync(scal + S_NA2, 0, sizeof(double), st));
   }
+  DNGD_NOTE_LAUNCH();
   k_ga_decide<<<1, 1, 0, st>>>(scal, use_ga, eps_norm, ratio_max);
+  DNGD_NOTE_LAUNCH();
   k_ga_delta<<<cdiv(n, 256), 256, 0, st>>>(n, v, use_ga ? a : v, scal, delta, status);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -115,22 +119,26 @@ __global__ void k_cg_update_p(int m, const double* scal, const double* __restric
 }
 
 dngd_status cg_alpha(double* scal, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_cg_alpha<<<1, 1, 0, st>>>(scal);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
 dngd_status cg_update_x(int m, const double* scal, double* x, double* res, const double* p, const double* Ap,
                         cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_cg_update_x<<<cdiv(m, 256), 256, 0, st>>>(m, scal, x, res, p, Ap);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
 dngd_status cg_beta(double* scal, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_cg_beta<<<1, 1, 0, st>>>(scal);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
 dngd_status cg_update_p(int m, const double* scal, const double* z, double* p, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_cg_update_p<<<cdiv(m, 256), 256, 0, st>>>(m, scal, z, p);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -142,10 +150,36 @@ __global__ void k_axpby(int m, double s, const double* __restrict__ x, double* _
   if (i < m) y[i] += s * x[i];
 }
 dngd_status add_scaled(int m, double s, const double* x, double* y, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
   k_axpby<<<cdiv(m, 256), 256, 0, st>>>(m, s, x, y);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
+
+template <typename T>
+__global__ void k_diag_sum(int m, const T* __restrict__ A, long long lda, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s += (double)A[(long long)i * lda + i];
+  s = warp_sum(s);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+template <typename T>
+dngd_status diag_sum(int m, const T* A, long long lda, double* scal_out, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
+  k_diag_sum<T><<<1, 256, 0, st>>>(m, A, lda, scal_out);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+template dngd_status diag_sum<double>(int, const double*, long long, double*, cudaStream_t);
+template dngd_status diag_sum<float>(int, const float*, long long, double*, cudaStream_t);
 
 // Copy the lower triangle of a [m x m] matrix to float64 (upper = 0).
 template <typename T>
@@ -159,6 +193,7 @@ __global__ void k_lower_to_f64(int m, const T* __restrict__ A, long long lda, do
 template <typename T>
 dngd_status lower_to_f64(int m, const T* A, long long lda, double* out, cudaStream_t st) {
   const long long tot = (long long)m * m;
+  DNGD_NOTE_LAUNCH();
   k_lower_to_f64<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(m, A, lda, out);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
@@ -178,6 +213,7 @@ __global__ void k_rows_to_f64(int m, long long n, const T* __restrict__ A, long 
 template <typename T>
 dngd_status rows_to_f64(int m, long long n, const T* A, long long lda, double* out, cudaStream_t st) {
   const long long tot = (long long)m * n;
+  DNGD_NOTE_LAUNCH();
   k_rows_to_f64<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(m, n, A, lda, out);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;

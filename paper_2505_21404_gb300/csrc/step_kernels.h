@@ -8,7 +8,7 @@ namespace dngd {
 // Slots of the per-context device scalar array.
 enum : int {
   S_NV2 = 0, S_NA2, S_RATIO, S_ACCEPT,
-  S_RHO, S_RHONEW, S_PAP, S_ALPHA, S_BETA, S_BREAK, S_RR, S_BB, S_LOSS,
+  S_RHO, S_RHONEW, S_PAP, S_ALPHA, S_BETA, S_BREAK, S_RR, S_BB, S_LOSS, S_TRACE,
   S_COUNT = 16
 };
 
@@ -21,6 +21,9 @@ dngd_status cg_update_x(int m, const double* scal, double* x, double* res, const
                         cudaStream_t st);
 dngd_status cg_beta(double* scal, cudaStream_t st);
 dngd_status cg_update_p(int m, const double* scal, const double* z, double* p, cudaStream_t st);
+// scal_out = sum_i A[i,i]
+template <typename T>
+dngd_status diag_sum(int m, const T* A, long long lda, double* scal_out, cudaStream_t st);
 dngd_status add_scaled(int m, double s, const double* x, double* y, cudaStream_t st);
 template <typename T>
 dngd_status lower_to_f64(int m, const T* A, long long lda, double* out, cudaStream_t st);

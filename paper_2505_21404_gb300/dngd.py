@@ -53,13 +53,15 @@ class ProblemDesc(C.Structure):
 class StepInfo(C.Structure):
     _fields_ = [("loss", C.c_double), ("norm_v", C.c_double), ("norm_a", C.c_double), ("ga_ratio", C.c_double),
                 ("ga_accepted", C.c_int), ("solve_iters", C.c_int * 2), ("solve_relres", C.c_double * 2),
-                ("not_spd_column", C.c_int), ("device_status", C.c_int), ("phase_ms", C.c_float * 8)]
+                ("not_spd_column", C.c_int), ("device_status", C.c_int), ("phase_ms", C.c_float * 8),
+                ("shift_used", C.c_double)]
 
     def as_dict(self):
         return dict(loss=self.loss, norm_v=self.norm_v, norm_a=self.norm_a, ga_ratio=self.ga_ratio,
                     ga_accepted=bool(self.ga_accepted), solve_iters=list(self.solve_iters),
                     solve_relres=list(self.solve_relres), not_spd_column=self.not_spd_column,
-                    device_status=self.device_status, phase_ms=list(self.phase_ms))
+                    device_status=self.device_status, phase_ms=list(self.phase_ms),
+                    shift_used=self.shift_used)
 
 
 def _load():
@@ -71,6 +73,7 @@ def _load():
     sigs = {
         "dngd_status_string": (C.c_char_p, [C.c_int]),
         "dngd_version": (C.c_char_p, []),
+        "dngd_launch_count": (C.c_uint64, []),
         "dngd_num_params": (C.c_int64, [C.POINTER(ProblemDesc)]),
         "dngd_create": (C.c_int, [C.POINTER(P), C.POINTER(ProblemDesc), P]),
         "dngd_workspace_bytes": (C.c_int, [C.POINTER(ProblemDesc), C.POINTER(C.c_size_t)]),
@@ -94,7 +97,7 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ["dngd_status_string", "dngd_version", "dngd_num_params", "dngd_create", "dngd_workspace_bytes",
+EXPORTED = ["dngd_status_string", "dngd_version", "dngd_launch_count", "dngd_num_params", "dngd_create", "dngd_workspace_bytes",
             "dngd_destroy", "dngd_set_timing", "dngd_set_lambda", "dngd_step", "dngd_solve", "dngd_loss",
             "dngd_line_search", "dngd_residual_jacobian", "dngd_fvv", "dngd_get_stage"]
 
@@ -144,6 +147,10 @@ def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_rati
     d.shift_mu = float(shift_mu)
     d.keep_gram = int(bool(keep_gram))
     return d
+
+
+def dngd_launch_count():
+    return int(lib.dngd_launch_count())
 
 
 def dngd_num_params(desc):
