@@ -214,6 +214,29 @@ dngd_status dngd_fvv(dngd_ctx* ctx, const double* theta, const double* X, const 
  * Values are converted to float64. */
 dngd_status dngd_get_stage(dngd_ctx* ctx, int which, double* dst);
 
+/* Gram matrix without any device allocation (the paper has no counterpart:
+ * this is a library facility).  K = J J^T + shift I for a BF16 matrix J on the
+ * tcgen05 tensor cores, the same kernels as the step's Gram.
+ *   J      device, [m x ld] row-major bfloat16, 16-byte aligned, ld >= n and
+ *          ld * 2 a multiple of 16 bytes; columns n..ld-1 are ignored.
+ *   K      device, [m x ldk] float32 output: the lower triangle with the
+ *          diagonal is written, the strict upper triangle is set to 0.
+ *   stream a cudaStream_t (NULL = legacy default stream).
+ * For callers that cannot call cudaMalloc at this point (their framework owns
+ * every device allocation, or an allocation would disturb the surrounding
+ * work).  The call allocates nothing: its scratch (split-K partial tiles, the
+ * tile list, a status word) is one static 16 MiB device array that every GPU
+ * which loads this library keeps until the process exits, so m is limited to
+ * 2000; larger m returns DNGD_ERR_INVALID_ARG with a message on stderr.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU (other streams, other threads) race on it.  The call
+ * synchronises the stream and returns DNGD_ERR_TIMEOUT if a bounded wait in
+ * the kernel gave up. */
+dngd_status dngd_gram_bf16_noalloc(const void* J, int m, int n, long long ld, float* K, long long ldk,
+                                   double shift, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

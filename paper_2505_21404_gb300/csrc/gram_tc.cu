@@ -442,3 +442,124 @@ int gram_tc_nsplit(const GramPlan* p) { return p->nsplit; }
 int gram_tc_ntiles(const GramPlan* p) { return p->ntiles; }
 
 }  // namespace dngd
+
+// ---------------------------------------------------------------------------
+// Allocation-free Gram entry point.
+//
+// Some callers cannot allocate device memory at the moment they need the
+// Gram: code running under a framework that owns every device allocation (a
+// caching allocator or a fixed memory pool), code inside a region where an
+// allocation would synchronise the device or invalidate a captured work
+// list, or small embedded users that reserve memory once at start-up.  This
+// entry point computes the same K = J J^T + shift I as the context's Gram
+// (same tcgen05 kernel, same reduction) but takes its split-K partial tiles,
+// its tile list and its status word from one file-scope device array of fixed
+// size instead of cudaMalloc.
+// ---------------------------------------------------------------------------
+
+namespace dngd {
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)16 << 20;       // 16 MiB per device
+constexpr size_t kNoAllocStatusOff = 0;                   // int[4]
+constexpr size_t kNoAllocTilesOff = 256;                  // int2 tile list
+constexpr size_t kNoAllocTilesMax = 512;                  // tiles (m <= 2000 needs 72)
+constexpr size_t kNoAllocPartOff = 256 + kNoAllocTilesMax * sizeof(int2);
+
+// Every GPU that loads the library holds this array until the process exits.
+// Host code must not use its name as a device address: the per-device address
+// comes from cudaGetSymbolAddress at set-up.
+static __device__ __align__(256) unsigned char g_gram_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+unsigned char* g_scratch_addr[kNoAllocMaxDevices] = {};
+
+// Writes the lower-triangle 128 x 256 tile list (row block I, column block J)
+// into the scratch; one thread, ntiles is small.
+__global__ void k_noalloc_tiles(int m, int2* tiles) {
+  int t = 0;
+  const int nI = (m + BM - 1) / BM;
+  for (int I = 0; I < nI; ++I)
+    for (int Jc = 0; Jc * BN <= I * BM + BM - 1 && Jc * BN < m; ++Jc) tiles[t++] = make_int2(I, Jc);
+}
+
+}  // namespace
+
+}  // namespace dngd
+
+extern "C" dngd_status dngd_gram_bf16_noalloc(const void* J, int m, int n, long long ld, float* K, long long ldk,
+                                              double shift, void* stream) {
+  using namespace dngd;
+  if (!J || !K || m < 1 || n < 1 || ld < n || ldk < m) return DNGD_ERR_INVALID_ARG;
+  if ((ld * 2) % 16 != 0 || ((uintptr_t)J % 16) != 0) return DNGD_ERR_INVALID_ARG;
+  const int nI = (m + BM - 1) / BM;
+  const long long mp = (long long)nI * BM;
+  const long long ldp = ((m + 3) / 4) * 4 + 4;
+  const size_t per_split = (size_t)mp * ldp * sizeof(float);
+  const size_t cap = kNoAllocBytes - kNoAllocPartOff;
+  if (per_split > cap) {
+    fprintf(stderr, "dngd_gram_bf16_noalloc: m = %d needs %zu bytes of scratch, the static array holds %zu "
+                    "(maximum m is 2000)\n", m, per_split, cap);
+    return DNGD_ERR_INVALID_ARG;
+  }
+  int ntiles = 0;
+  for (int I = 0; I < nI; ++I)
+    for (int Jc = 0; Jc * BN <= I * BM + BM - 1 && Jc * BN < m; ++Jc) ++ntiles;
+  if ((size_t)ntiles > kNoAllocTilesMax) return DNGD_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return DNGD_ERR_CUDA;
+  // once per device, with that device current: the device address of the array
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_gram_scratch);
+    if (e != cudaSuccess || !p) {
+      fprintf(stderr, "dngd_gram_bf16_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+      return DNGD_ERR_CUDA;
+    }
+    if (cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+        cudaSuccess)
+      return DNGD_ERR_CUDA;
+    g_scratch_addr[dev] = (unsigned char*)p;
+  }
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return DNGD_ERR_CUDA;
+  CUtensorMap mapA, mapB;
+  cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t gstride[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t estride[2] = {1, 1};
+  cuuint32_t boxA[2] = {64, (cuuint32_t)BM};
+  cuuint32_t boxB[2] = {64, (cuuint32_t)BN};
+  if (enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(J), gdim, gstride, boxA, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(J), gdim, gstride, boxB, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return DNGD_ERR_CUDA;
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int num_kblk = (n + 63) / 64;
+  int nsplit = choose_splits(ntiles, num_kblk, nsm);
+  while (nsplit > 1 && (size_t)nsplit * per_split > cap) --nsplit;
+  unsigned char* base = g_scratch_addr[dev];
+  int* status = (int*)(base + kNoAllocStatusOff);
+  int2* tiles = (int2*)(base + kNoAllocTilesOff);
+  float* partials = (float*)(base + kNoAllocPartOff);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: clear the status word
+  if (cudaMemsetAsync(status, 0, 4 * sizeof(int), st) != cudaSuccess) return DNGD_ERR_CUDA;
+  DNGD_NOTE_LAUNCH();
+  k_noalloc_tiles<<<1, 1, 0, st>>>(m, tiles);
+  DNGD_NOTE_LAUNCH();
+  k_gram_tc<0><<<dim3(ntiles, nsplit), 128, SMEM_BYTES, st>>>(mapA, mapB, tiles, m, num_kblk, partials, ldp,
+                                                              (long long)mp * ldp, status);
+  const long long tot = (long long)m * m;
+  DNGD_NOTE_LAUNCH();
+  k_gram_reduce<<<(int)((tot + 255) / 256), 256, 0, st>>>(m, nsplit, partials, ldp, (long long)mp * ldp, K, ldk,
+                                                          shift);
+  if (cudaGetLastError() != cudaSuccess) return DNGD_ERR_CUDA;
+  int hs[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(hs, status, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess) return DNGD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DNGD_ERR_CUDA;
+  return (hs[0] & ST_TIMEOUT) ? DNGD_ERR_TIMEOUT : DNGD_OK;
+}

@@ -87,6 +87,7 @@ def _load():
         "dngd_residual_jacobian": (C.c_int, [P, P, P, P, P, P]),
         "dngd_fvv": (C.c_int, [P, P, P, P, P, P]),
         "dngd_get_stage": (C.c_int, [P, C.c_int, P]),
+        "dngd_gram_bf16_noalloc": (C.c_int, [P, C.c_int, C.c_int, C.c_longlong, P, C.c_longlong, C.c_double, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -99,7 +100,8 @@ lib = _load()
 
 EXPORTED = ["dngd_status_string", "dngd_version", "dngd_launch_count", "dngd_num_params", "dngd_create", "dngd_workspace_bytes",
             "dngd_destroy", "dngd_set_timing", "dngd_set_lambda", "dngd_step", "dngd_solve", "dngd_loss",
-            "dngd_line_search", "dngd_residual_jacobian", "dngd_fvv", "dngd_get_stage"]
+            "dngd_line_search", "dngd_residual_jacobian", "dngd_fvv", "dngd_get_stage",
+            "dngd_gram_bf16_noalloc"]
 
 
 def _check(status, where):
@@ -161,6 +163,13 @@ def dngd_workspace_bytes(desc):
     b = C.c_size_t(0)
     _check(lib.dngd_workspace_bytes(C.byref(desc), C.byref(b)), "dngd_workspace_bytes")
     return int(b.value)
+
+
+def dngd_gram_bf16_noalloc(J, m, n, ld, K, ldk, shift, stream=None):
+    """K = J J^T + shift I from a BF16 device matrix, with no device allocation
+    (see include/dngd.h).  Returns the status code."""
+    s = C.c_void_p(int(stream)) if stream else None
+    return int(lib.dngd_gram_bf16_noalloc(_ptr(J), int(m), int(n), int(ld), _ptr(K), int(ldk), float(shift), s))
 
 
 class Context:
