@@ -169,7 +169,8 @@ def main():
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle leg (no step error)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--refine-max-it", type=int, default=200)
+    ap.add_argument("--refine-max-it", type=int, default=400)
+    ap.add_argument("--refine-tol", type=float, default=1e-5)
     ap.add_argument("--workload", default="poisson5d", choices=["poisson5d", "poisson5d_w128"],
                     help="poisson5d_w128: same points, hidden width 128 (profiling case, n=33,537)")
     args = ap.parse_args()
@@ -220,7 +221,8 @@ def main():
     tg = torch.tensor(wl["target"], device=dev)
     etas = _grid()
 
-    ctx = dngd.Context(dngd.make_desc(wl, precision=prec, refine_tol=1e-7, refine_max_it=args.refine_max_it),
+    ctx = dngd.Context(dngd.make_desc(wl, precision=prec, refine_tol=args.refine_tol,
+                                       refine_max_it=args.refine_max_it),
                        stream=stream.cuda_stream)
     ctx.set_timing(True)
     delta = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -345,7 +347,9 @@ def main():
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "gram_tflops": achieved, "fp64": fp64, "step_error": err,
         "speedup_vs_fp64": (value / world) / fp64["steps_per_s"] if fp64 else None,
-        "refine_iters": iters, "phase_ms": phase, "ga_accepted_at_theta0": info0["ga_accepted"],
+        "refine_iters": iters, "phase_ms": phase,
+        "per_step": [{"iters": i["solve_iters"], "shift": i["shift_used"], "factor_attempts": i["factor_attempts"],
+                      "loss": i["loss"], "ms": float(l)} for i, l in zip(infos, lat)], "ga_accepted_at_theta0": info0["ga_accepted"],
         "roofline": {"bound": "tensor", "kernel": "k_gram_tc (tcgen05 BF16 syrk, lower tiles)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"{src} bf16 sustained" + (" / 2 for tf32" if prec != dngd.MIXED_BF16 else ""),

@@ -67,9 +67,9 @@ enum {
 enum dngd_precision {
   DNGD_FP64 = 0,        /* every stage in float64 */
   DNGD_MIXED_BF16 = 1,  /* FP32 jets/J, BF16 tensor-core Gram (FP32 accum),
-                           FP32 Cholesky of K + (lambda+mu) I with FP64
-                           diagonal blocks, PCG refinement on the FP32-J
-                           operator with double-float accumulation */
+                           FP32 Cholesky of K + (lambda+mu) I and its explicit
+                           inverse as the preconditioner of PCG refinement on
+                           the FP32-J operator with double-float accumulation */
   DNGD_MIXED_TF32 = 2   /* as MIXED_BF16 with a TF32 tensor-core Gram */
 };
 
@@ -130,9 +130,10 @@ typedef struct {
   double shift_used;        /* diagonal shift mu of the factored preconditioner
                                (mixed paths).  Starts at max(shift_mu, the
                                shift that factored in the previous step) and
-                               is raised x10 (at least to 1e-8 trace(K)/m) on
-                               a failed low-precision factorisation, up to 8
+                               is raised x3 (at least to 1e-6 trace(K)/m) on
+                               a failed low-precision factorisation, up to 12
                                tries; the refinement keeps the exact lambda. */
+  int factor_attempts;      /* low-precision factorisations this step (mixed) */
 } dngd_step_info;
 
 typedef struct dngd_ctx dngd_ctx;

@@ -35,6 +35,7 @@ struct dngd_ctx {
   double *theta_s = nullptr, *X_s = nullptr, *target_s = nullptr, *nvec_s = nullptr, *mvec_s = nullptr;
   double* theta_tmp = nullptr;  // line search
   float *theta32 = nullptr, *v32 = nullptr;
+  float2* xs = nullptr;  // hi/lo split of the vector of an FP32 GEMV
 
   // jets
   void* Z[kMaxLayers] = {};
@@ -71,6 +72,8 @@ struct dngd_ctx {
   int iters[2] = {0, 0};
   double shift_used = 0.0;
   double mu_sticky = 0.0;  // preconditioner shift that factored last time
+  int factor_attempts = 0;
+  void* K0 = nullptr;      // mixed path: Gram + (lambda + mu0) I before factorisation
   double relres[2] = {0.0, 0.0};
   cudaEvent_t ev[9] = {};
 };
@@ -231,65 +234,45 @@ dngd_status residual_jacobian_T(dngd_ctx* c, const T* thT, const double* X, cons
 // Solves with the factor of the last step
 // ---------------------------------------------------------------------------
 
-// Preconditioner of the mixed path: z = (L L^T)^{-1} q = Linv^T (Linv q).
-dngd_status precond_mixed(dngd_ctx* c, const double* q, double* z) {
-  dngd_status s = gemv_n<float>(c->m, c->m, c->Linv, c->ldk, q, 1.0, c->cg_y, c->st);
-  if (s) return s;
-  return gemv_t<float>(c->m, c->m, c->Linv, c->ldk, c->cg_y, 1.0, z, c->partials, c->st);
+long long partial_cap(const dngd_ctx* c) { return 16LL * (c->n > c->m ? c->n : c->m); }
+
+// y = alpha J^T x in the context's precision
+template <typename T>
+dngd_status jt_x(dngd_ctx* c, const double* x, double alpha, double* y);
+template <>
+dngd_status jt_x<double>(dngd_ctx* c, const double* x, double alpha, double* y) {
+  return gemv_t<double>(c->m, (int)c->n, (const double*)c->J, c->ldJ, x, alpha, y, c->partials, c->st);
+}
+template <>
+dngd_status jt_x<float>(dngd_ctx* c, const double* x, double alpha, double* y) {
+  return gemv_t_f32(c->m, (int)c->n, (const float*)c->J, c->ldJ, x, alpha, y, c->partials, partial_cap(c),
+                    c->xs, c->st);
 }
 
-// A p = J (J^T p) + lambda p with the FP32 J (double-float accumulation).
-dngd_status apply_A_mixed(dngd_ctx* c, const double* p, double* Ap) {
-  dngd_status s = gemv_t<float>(c->m, (int)c->n, (const float*)c->J, c->ldJ, p, 1.0, c->cg_u, c->partials, c->st);
-  if (s) return s;
-  s = gemv_n<float>(c->m, (int)c->n, (const float*)c->J, c->ldJ, c->cg_u, 1.0, Ap, c->st);
-  if (s) return s;
-  return add_scaled(c->m, c->lambda, p, Ap, c->st);
-}
-
-// PCG on (J J^T + lambda I) x = b preconditioned by the low-precision factor
-// (iterative refinement of the mixed path).
 dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
-  const int m = c->m;
-  double* sc = c->scal;
-  dngd_status s;
-  DNGD_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * m, c->st));
-  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->cg_res, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st));
-  DNGD_CUDA_CHECK(cudaMemsetAsync(sc + S_BREAK, 0, sizeof(double), c->st));
-  if ((s = dot_dev(m, b, b, sc + S_BB, c->dot_partials, c->st))) return s;
-  if ((s = precond_mixed(c, c->cg_res, c->cg_z))) return s;
-  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->cg_p, c->cg_z, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st));
-  if ((s = dot_dev(m, c->cg_res, c->cg_z, sc + S_RHO, c->dot_partials, c->st))) return s;
+  PcgMixed P;
+  P.m = c->m;
+  P.n = (int)c->n;
+  P.J = (const float*)c->J;
+  P.ldJ = c->ldJ;
+  P.Linv = c->Linv;
+  P.ldk = c->ldk;
+  P.lambda = c->lambda;
+  P.res = c->cg_res;
+  P.z = c->cg_z;
+  P.p = c->cg_p;
+  P.Ap = c->cg_Ap;
+  P.u = c->cg_u;
+  P.y = c->cg_y;
+  P.xs = c->xs;
+  P.partials = c->partials;
+  P.partial_cap = partial_cap(c);
+  P.dotp = c->dot_partials + 256;
+  P.scal = c->scal;
+  P.scal_h = c->scal_h;
   const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
   const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
-  int it = 0;
-  double rel = 1.0;
-  bool conv = false;
-  for (it = 0; it < maxit;) {
-    if ((s = apply_A_mixed(c, c->cg_p, c->cg_Ap))) return s;
-    if ((s = dot_dev(m, c->cg_p, c->cg_Ap, sc + S_PAP, c->dot_partials, c->st))) return s;
-    if ((s = cg_alpha(sc, c->st))) return s;
-    if ((s = cg_update_x(m, sc, x, c->cg_res, c->cg_p, c->cg_Ap, c->st))) return s;
-    if ((s = dot_dev(m, c->cg_res, c->cg_res, sc + S_RR, c->dot_partials, c->st))) return s;
-    ++it;
-    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
-    DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
-    const double bb = c->scal_h[S_BB];
-    rel = bb > 0 ? sqrt(c->scal_h[S_RR] / bb) : 0.0;
-    if (rel <= tol || bb == 0.0) {
-      conv = true;
-      break;
-    }
-    if (c->scal_h[S_BREAK] != 0.0) break;
-    if ((s = precond_mixed(c, c->cg_res, c->cg_z))) return s;
-    if ((s = dot_dev(m, c->cg_res, c->cg_z, sc + S_RHONEW, c->dot_partials, c->st))) return s;
-    if ((s = cg_beta(sc, c->st))) return s;
-    if ((s = cg_update_p(m, sc, c->cg_z, c->cg_p, c->st))) return s;
-  }
-  c->iters[slot] = it;
-  c->relres[slot] = rel;
-  (void)conv;
-  return DNGD_OK;
+  return pcg_mixed_solve(P, b, x, tol, maxit, 4, &c->iters[slot], &c->relres[slot], c->st);
 }
 
 dngd_status solve_last(dngd_ctx* c, const double* b, double* x, int slot) {
@@ -332,34 +315,49 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     // factorisation is retried with a larger shift mu (it only preconditions
     // the refinement, whose operator keeps the exact lambda)
     double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
+    gram_tc_set_shift(c->gram, c->lambda + mu);
+    if ((s = gram_tc_run(c->gram, c->status, c->st, c->timing ? c->ev[8] : nullptr))) return s;
+    // K0 = K + (lambda + mu0) I is kept, so a failed factorisation is retried
+    // from the copy with a larger shift instead of recomputing the Gram
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->K0, c->K, sizeof(float) * (size_t)m * c->ldk, cudaMemcpyDeviceToDevice,
+                                    c->st));
+    if ((s = diag_sum<float>(m, (const float*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
+    const double mu0 = mu;
+    c->factor_attempts = 0;
     for (int attempt = 0;; ++attempt) {
-      gram_tc_set_shift(c->gram, c->lambda + mu);
-      if ((s = gram_tc_run(c->gram, c->status, c->st, c->timing ? c->ev[8] : nullptr))) return s;
-      if (c->Kcopy)
-        DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(float) * (size_t)m * c->ldk,
-                                        cudaMemcpyDeviceToDevice, c->st));
-      if ((s = diag_sum<float>(m, (const float*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
+      if (attempt > 0) {
+        DNGD_CUDA_CHECK(cudaMemcpyAsync(c->K, c->K0, sizeof(float) * (size_t)m * c->ldk, cudaMemcpyDeviceToDevice,
+                                        c->st));
+        if ((s = add_diag<float>(m, (float*)c->K, c->ldk, mu - mu0, c->st))) return s;
+      }
       evrec(c, 2);
-      if ((s = cholesky<float>(m, (float*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
+      c->factor_attempts++;
+      DNGD_CUDA_CHECK(cudaMemsetAsync(c->Linv, 0, sizeof(float) * (size_t)m * c->ldk, c->st));
+      if ((s = cholesky_f32_inv(m, (float*)c->K, c->ldk, c->Linv, c->ldk, c->status, c->st))) return s;
       const dngd_status fs = read_status(c);
-      if (fs != DNGD_ERR_NOT_SPD || attempt >= 7) break;
+      if (fs != DNGD_ERR_NOT_SPD || attempt >= 15) break;
       DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
       DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
-      const double tr = c->scal_h[S_TRACE] - m * (c->lambda + mu);
-      const double base = 1e-8 * (tr > 0 ? tr : 1.0) / m;
-      mu = mu * 10.0 > base ? mu * 10.0 : base;
+      const double tr = c->scal_h[S_TRACE] - m * (c->lambda + mu0);
+      const double base = 1e-6 * (tr > 0 ? tr : 1.0) / m;
+      mu = mu * 3.0 > base ? mu * 3.0 : base;
       DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+    }
+    if (c->Kcopy) {
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K0, sizeof(float) * (size_t)m * c->ldk, cudaMemcpyDeviceToDevice,
+                                      c->st));
+      if ((s = add_diag<float>(m, (float*)c->Kcopy, c->ldk, mu - mu0, c->st))) return s;
     }
     c->mu_sticky = mu;
     c->shift_used = mu;
-    if ((s = trtri_lower_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
+    if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
   }
   // a failed factorisation stops the step here
   if ((s = read_status(c))) return s;
   evrec(c, 3);
   // alpha = (K + lambda I)^{-1} r ; v = -J^T alpha
   if ((s = solve_last(c, c->r, c->alpha, 0))) return s;
-  if ((s = gemv_t<T>(m, n, (const T*)c->J, c->ldJ, c->alpha, -1.0, c->v, c->partials, c->st))) return s;
+  if ((s = jt_x<T>(c, c->alpha, -1.0, c->v))) return s;
   evrec(c, 4);
   if (c->desc.use_ga) {
     const T* vT;
@@ -372,7 +370,7 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     if ((s = jets_fvv<T>(c->net, thT, vT, X, (T*)c->Z3, (T*)c->H3a, (T*)c->H3b, c->fvv, c->st))) return s;
     evrec(c, 5);
     if ((s = solve_last(c, c->fvv, c->beta, 1))) return s;
-    if ((s = gemv_t<T>(m, n, (const T*)c->J, c->ldJ, c->beta, -1.0, c->a, c->partials, c->st))) return s;
+    if ((s = jt_x<T>(c, c->beta, -1.0, c->a))) return s;
     evrec(c, 6);
   } else {
     evrec(c, 5);
@@ -406,6 +404,7 @@ dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
   info->device_status = c->status_h[0];
   info->not_spd_column = (c->status_h[0] & ST_NOT_SPD) ? c->status_h[1] : -1;
   info->shift_used = c->shift_used;
+  info->factor_attempts = c->factor_attempts;
   if (c->timing) {
     // event order: 0 start, 1 jets+J, 8 Gram kernel, 2 Gram epilogue, 3 factor,
     // 4 solve r, 5 f_vv, 6 solve f_vv, 7 end
@@ -459,6 +458,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   if (c->prec == DNGD_MIXED_BF16) add(sizeof(__nv_bfloat16) * (size_t)m * c->ldb);
   add(es * (size_t)m * c->ldk);
   if (c->desc.keep_gram) add(es * (size_t)m * c->ldk);
+  if (!f64) add(es * (size_t)m * c->ldk);       // K0
   if (!f64) {
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
     add(sizeof(float) * (size_t)m * m);           // trtri work
@@ -467,7 +467,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   add(sizeof(double) * m * 4 + sizeof(double) * n * 3);
   add(sizeof(double) * m * 6 + sizeof(double) * n);
   add(sizeof(double) * (size_t)16 * (n > m ? n : m));
-  add(sizeof(double) * 256 + sizeof(double) * S_COUNT + 16);
+  add(sizeof(double) * (256 + 1024 + (size_t)m / 4 + 64) + sizeof(double) * S_COUNT + 16);
+  add(sizeof(float2) * ((size_t)round_up(n > m ? n : m, 4) + 4));
   if (bytes_out) *bytes_out = tot;
   if (dry) return DNGD_OK;
 
@@ -517,6 +518,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       DNGD_CUDA_CHECK(cudaMemset(c->Jb, 0, sizeof(__nv_bfloat16) * (size_t)m * c->ldb));
     }
     A_(c->K, float, (size_t)m * c->ldk);
+    A_(c->K0, float, (size_t)m * c->ldk);
     if (c->desc.keep_gram) A_(c->Kcopy, float, (size_t)m * c->ldk);
     A_(c->Linv, float, (size_t)m * c->ldk);
     A_(c->trtri_work, float, (size_t)m * m);
@@ -538,7 +540,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   A_(c->xsol, double, m);
   A_(c->cg_u, double, n);
   A_(c->partials, double, (size_t)16 * (n > m ? n : m));
-  A_(c->dot_partials, double, 256);
+  A_(c->dot_partials, double, 256 + 1024 + (size_t)m / 4 + 64);
+  A_(c->xs, float2, (size_t)round_up(n > m ? n : m, 4) + 4);
   A_(c->scal, double, S_COUNT);
   A_(c->status, int, 4);
 #undef A_

@@ -34,7 +34,6 @@ constexpr int A_BYTES = BM * KBLK_BYTES;              // 16 KB
 constexpr int B_BYTES = BN * KBLK_BYTES;              // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;        // 48 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr uint32_t TMEM_COLS = 256;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -139,15 +138,30 @@ __device__ __forceinline__ uint32_t make_idesc() {
 
 // grid.x: tile index into tiles[] (pairs of row-block I, col-block J);
 // grid.y: split index over the K blocks.
+//
+// Accumulation: a tensor-core accumulator that runs over tens of thousands of
+// products loses accuracy (its FP32 additions are not round-to-nearest), and
+// the Gram's error must stay far below lambda relative to ||K|| for the
+// factor to precondition well.  So the MMAs accumulate only CH k-blocks
+// (CH * 64 BF16 / 32 TF32 elements) in one of two TMEM buffers; eight
+// epilogue warps then add that partial tile into round-to-nearest FP32
+// registers (128 columns per thread) while the MMA warp fills the other
+// buffer.  Warps: 0 = TMA producer, 1 = MMA issuer (+ TMEM owner), 2..9 =
+// epilogue (warp w reads TMEM lanes 32*(w%4).., column half (w-2)/4).
+constexpr int CH = 4;
+constexpr int GRAM_THREADS = 320;
+constexpr uint32_t TMEM_COLS2 = 512;
+
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(GRAM_THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           const int2* __restrict__ tiles, int m, int num_kblk, float* __restrict__ out, long long ldo,
           long long split_stride, int* status) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t accf_bar[2];   // MMA -> epilogue: chunk ready in buffer b
+  __shared__ __align__(8) uint64_t acce_bar[2];   // epilogue -> MMA: buffer b drained
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
@@ -159,101 +173,128 @@ k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   const int kb0 = split * kb_per;
   const int kb1 = min(num_kblk, kb0 + kb_per);
   const int nk = max(0, kb1 - kb0);
+  const int nchunk = (nk + CH - 1) / CH;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    mbar_init(smem_u32(&acc_bar), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf_bar[b]), 1);
+      mbar_init(smem_u32(&acce_bar[b]), 8);
+    }
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(TMEM_COLS));
+                 "r"(TMEM_COLS2));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_sh;
-
   volatile int* abort_flag = &abort_sh;
+
   int issued = 0;  // producer: stages issued (for draining on abort)
-  if (warp == 0 && lane == 0) {
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-      if (*abort_flag || !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, status, 1)) {
-        *abort_flag = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+        if (*abort_flag || !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, status, 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        mbar_expect_tx(fb, STAGE_BYTES);
+        const uint32_t sa = smem_base + s * STAGE_BYTES;
+        const int kcoord = (kb0 + it) * (KIND == 0 ? 64 : 32);
+        tma_load_2d(sa, &mapA, fb, kcoord, tile.x * BM);
+        tma_load_2d(sa + A_BYTES, &mapB, fb, kcoord, tile.y * BN);
+        ++issued;
       }
-      const uint32_t fb = smem_u32(&full_bar[s]);
-      mbar_expect_tx(fb, STAGE_BYTES);
-      const uint32_t sa = smem_base + s * STAGE_BYTES;
-      const int kcoord = (kb0 + it) * (KIND == 0 ? 64 : 32);
-      tma_load_2d(sa, &mapA, fb, kcoord, tile.x * BM);
-      tma_load_2d(sa + A_BYTES, &mapB, fb, kcoord, tile.y * BN);
-      ++issued;
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = make_idesc<KIND>();
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-      if (*abort_flag || !mbar_wait(smem_u32(&full_bar[s]), ph, status, 2)) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc<KIND>();
+      for (int c = 0; c < nchunk && !*abort_flag; ++c) {
+        const int b = c & 1, use = c >> 1;
+        if (!mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)((use & 1) ^ 1), status, 5)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t dbuf = tmem + (uint32_t)(b * BN);
+        const int it0 = c * CH, it1 = min(nk, it0 + CH);
+        for (int it = it0; it < it1; ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+          if (*abort_flag || !mbar_wait(smem_u32(&full_bar[s]), ph, status, 2)) {
+            *abort_flag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t sa = smem_base + s * STAGE_BYTES;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            umma<KIND>(dbuf, sw128_desc(sa + 32 * k), sw128_desc(sa + A_BYTES + 32 * k), idesc,
+                       (it > it0 || k > 0) ? 1u : 0u);
+          }
+          umma_commit(smem_u32(&empty_bar[s]));
+        }
+        umma_commit(smem_u32(&accf_bar[b]));  // fires when the chunk's MMAs are done
+      }
+    }
+  } else {
+    // epilogue warps 2..9
+    const int q = warp & 3;             // TMEM lane quadrant this warp may access
+    const int h = (warp - 2) >> 2;      // column half of the 256-column tile
+    float acc[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+    for (int c = 0; c < nchunk; ++c) {
+      const int b = c & 1, use = c >> 1;
+      const bool ok = __all_sync(0xffffffffu,
+                                 (!*abort_flag && mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)(use & 1), status, 3))
+                                     ? 1
+                                     : 0) != 0;
+      if (!ok) {
         *abort_flag = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sa = smem_base + s * STAGE_BYTES;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + h * 128);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        umma<KIND>(tmem, sw128_desc(sa + 32 * k), sw128_desc(sa + A_BYTES + 32 * k), idesc,
-                   (it > 0 || k > 0) ? 1u : 0u);
+      for (int j4 = 0; j4 < 4; ++j4) {
+        uint32_t r[32];
+        TMEM_LD_32(base + (uint32_t)(j4 * 32), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[j4 * 32 + i] += __uint_as_float(r[i]);
       }
-      umma_commit(smem_u32(&empty_bar[s]));
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[b])) : "memory");
     }
-    umma_commit(smem_u32(&acc_bar));  // fires when every MMA above has completed
+    const int row = tile.x * BM + q * 32 + lane;
+    const int col0 = tile.y * BN + h * 128;
+    if (row < m && !*abort_flag) {
+      float* orow = out + (long long)split * split_stride + (long long)row * ldo;
+      if (col0 + 128 <= m) {
+        float4* dst = reinterpret_cast<float4*>(orow + col0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 128; ++j)
+          if (col0 + j < m) orow[col0 + j] = acc[j];
+      }
+    }
   }
   __syncwarp();
-
-  // epilogue: TMEM -> registers -> FP32 tile (rows of this warp's lanes)
-  const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_bar), 0u, status, 3) ? 1 : 0) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const bool aborted = __any_sync(0xffffffffu, *abort_flag) != 0;
-  if (acc_ok && !aborted && nk > 0) {
-    const int row = tile.x * BM + warp * 32 + lane;
-    float* orow = out + (long long)split * split_stride + (long long)row * ldo;
-#pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32);
-      TMEM_LD_32(taddr, r);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int col0 = tile.y * BN + c * 32;
-      if (row < m) {
-        if (col0 + 32 <= m) {
-          float4* dst = reinterpret_cast<float4*>(orow + col0);
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                 __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-        } else {
-#pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (col0 + q < m) orow[col0 + q] = __uint_as_float(r[q]);
-        }
-      }
-    }
-  } else if (nk == 0) {
-    const int row = tile.x * BM + warp * 32 + lane;
-    float* orow = out + (long long)split * split_stride + (long long)row * ldo;
-    if (row < m)
-      for (int q = 0; q < BN; ++q)
-        if (tile.y * BN + q < m) orow[tile.y * BN + q] = 0.f;
-  }
 
   // teardown: on abort, let issued TMA copies land before the CTA exits
   if (warp == 0 && lane == 0 && *abort_flag) {
@@ -266,7 +307,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS2));
   }
 }
 
@@ -417,10 +458,10 @@ dngd_status gram_tc_run(GramPlan* p, int* status, cudaStream_t st, cudaEvent_t e
   dim3 grid(p->ntiles, p->nsplit);
   DNGD_NOTE_LAUNCH();
   if (p->kind == 0)
-    k_gram_tc<0><<<grid, 128, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,
+    k_gram_tc<0><<<grid, GRAM_THREADS, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,
                                                 p->ldp, p->sstride, status);
   else
-    k_gram_tc<1><<<grid, 128, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,
+    k_gram_tc<1><<<grid, GRAM_THREADS, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,
                                                 p->ldp, p->sstride, status);
   DNGD_LAUNCH_CHECK();
   if (ev_after_mma) cudaEventRecord(ev_after_mma, st);
@@ -551,7 +592,7 @@ extern "C" dngd_status dngd_gram_bf16_noalloc(const void* J, int m, int n, long 
   DNGD_NOTE_LAUNCH();
   k_noalloc_tiles<<<1, 1, 0, st>>>(m, tiles);
   DNGD_NOTE_LAUNCH();
-  k_gram_tc<0><<<dim3(ntiles, nsplit), 128, SMEM_BYTES, st>>>(mapA, mapB, tiles, m, num_kblk, partials, ldp,
+  k_gram_tc<0><<<dim3(ntiles, nsplit), GRAM_THREADS, SMEM_BYTES, st>>>(mapA, mapB, tiles, m, num_kblk, partials, ldp,
                                                               (long long)mp * ldp, status);
   const long long tot = (long long)m * m;
   DNGD_NOTE_LAUNCH();

@@ -43,6 +43,14 @@ dngd_status gemm_nn(int M, int N, int K, T alpha, const T* A, long long lda, con
 template <typename TA>
 dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cudaStream_t st);
 
+// FP32 factorisation of the mixed path: A = L L^T in place (lower) and the
+// inverses of the 64 x 64 diagonal blocks of L written into Linv, which the
+// caller zero-initialises; trtri_offdiag_f32 then completes Linv = L^{-1}.
+dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long long ldi, int* status,
+                             cudaStream_t st);
+dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
+                              cudaStream_t st);
+
 // x = (L L^T)^{-1} b with the FP64 factor (two triangular solves).
 dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* b, double* x, cudaStream_t st);
 
@@ -60,9 +68,31 @@ template <typename TA>
 dngd_status gemv_n(int m, int n, const TA* A, long long lda, const double* x, double alpha, double* y,
                    cudaStream_t st);
 
-// y = L x (lower) or y = L^T x for an explicit FP32 lower-triangular matrix.
-dngd_status trmv_f32(int m, const float* L, long long ldl, const double* x, double* y, bool trans,
-                     cudaStream_t st);
+// ---- refine.cu: FP32 matrices with double-float accumulation ---------------
+// y = alpha A^T x (A [m x n] FP32, lda % 4 == 0, padding columns zero).
+// xs: scratch of round_up(max(m, n), 4) + 4 float2; partial_cap: doubles in partials.
+dngd_status gemv_t_f32(int m, int n, const float* A, long long lda, const double* x, double alpha, double* y,
+                       double* partials, long long partial_cap, float2* xs, cudaStream_t st);
+
+// Preconditioned CG on (J J^T + lambda I) x = b with the FP32 J as operator
+// and M^{-1} = Linv^T Linv as preconditioner; all scalars on the device.
+struct PcgMixed {
+  int m, n;
+  const float* J;
+  long long ldJ;
+  const float* Linv;
+  long long ldk;
+  double lambda;
+  double *res, *z, *p, *Ap, *u, *y;   // work vectors (u has n entries)
+  float2* xs;
+  double* partials;
+  long long partial_cap;
+  double* dotp;                       // >= 1024 doubles
+  double* scal;                       // device scalars (S_COUNT)
+  double* scal_h;                     // pinned host copy
+};
+dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, double tol, int maxit, int check_every,
+                            int* iters, double* relres, cudaStream_t st);
 
 // K[i,i] += shift for i < m.
 template <typename T>

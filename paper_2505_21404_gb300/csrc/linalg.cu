@@ -245,7 +245,88 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 }
 
 template dngd_status cholesky<double>(int, double*, long long, int*, double*, cudaStream_t);
-template dngd_status cholesky<float>(int, float*, long long, int*, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// FP32 factorisation for the mixed path (a preconditioner, whose accuracy the
+// refinement restores).  One kernel factors a 64 x 64 diagonal block and,
+// in the same elimination loop, builds its inverse (forward substitution on
+// the identity); the panel solve is then a GEMM with that inverse, and the
+// inverse fills the diagonal blocks of the explicit L^{-1}.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A, long long lda, float* Linv,
+                                                        long long ldi, int* status) {
+  __shared__ float S[kCholNB][kCholNB + 1];
+  __shared__ float X[kCholNB][kCholNB + 1];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  if (status[0] & ST_NOT_SPD) return;
+  for (int e = tid; e < kCholNB * kCholNB; e += blockDim.x) {
+    const int i = e / kCholNB, j = e % kCholNB;
+    S[i][j] = (i < kb && j <= i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.f;
+    X[i][j] = (i == j) ? 1.f : 0.f;
+  }
+  if (tid == 0) bad = -1;
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    const float piv = S[j][j];
+    if (!(piv > 0.f)) {
+      if (tid == 0) bad = j;
+      break;
+    }
+    const float d = sqrtf(piv);
+    const float inv_d = 1.f / d;
+    // phase A: scale column j of L below the diagonal and row j of the inverse
+    if (j + 1 + tid < kb) S[j + 1 + tid][j] *= inv_d;
+    if (tid <= j) X[j][tid] *= inv_d;
+    __syncthreads();
+    if (tid == 0) S[j][j] = d;
+    // phase B: rank-1 update of the trailing block and elimination in X
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      const float lij = S[i][j];
+      for (int c = j + 1 + tx; c <= i; c += 16) S[i][c] -= lij * S[c][j];
+      for (int c = tx; c <= j; c += 16) X[i][c] -= lij * X[j][c];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad >= 0) {
+    if (tid == 0) {
+      const int old = atomicOr(status, ST_NOT_SPD);
+      if (!(old & ST_NOT_SPD)) status[1] = k0 + bad;
+    }
+    return;
+  }
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    if (j <= i) A[(long long)(k0 + i) * lda + k0 + j] = S[i][j];
+    Linv[(long long)(k0 + i) * ldi + k0 + j] = (j <= i) ? X[i][j] : 0.f;
+  }
+}
+
+// A = L L^T (FP32, in place, lower) and the diagonal 64-blocks of L^{-1} in
+// Linv (which must be zero-initialised by the caller).
+dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long long ldi, int* status,
+                             cudaStream_t st) {
+  for (int k0 = 0; k0 < m; k0 += kCholNB) {
+    const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
+    DNGD_NOTE_LAUNCH();
+    k_potrf_inv_f32<<<1, 256, 0, st>>>(k0, kb, A, lda, Linv, ldi, status);
+    DNGD_LAUNCH_CHECK();
+    const int rest = m - k0 - kb;
+    if (rest <= 0) break;
+    float* P = A + (long long)(k0 + kb) * lda + k0;
+    const float* I11 = Linv + (long long)k0 * ldi + k0;
+    // panel: P <- P L11^{-T} = P * (L11^{-1})^T (in place: one column tile)
+    dngd_status s = gemm_nt<float>(rest, kb, kb, 1.0f, P, lda, I11, ldi, 0.0f, P, lda, false, st);
+    if (s) return s;
+    float* A22 = A + (long long)(k0 + kb) * lda + k0 + kb;
+    s = gemm_nt<float>(rest, rest, kb, -1.0f, P, lda, P, lda, 1.0f, A22, lda, true, st);
+    if (s) return s;
+  }
+  return DNGD_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Triangular solves with the FP64 factor, blocked: one small kernel solves a
@@ -367,7 +448,8 @@ __global__ void k_trtri_diag(int k0, int kb, const float* __restrict__ L, long l
 }
 
 static dngd_status trtri_rec(int k0, int n, const float* L, long long ldl, float* Linv, long long ldi, float* work,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool have_diag) {
+  if (n <= kCholNB && have_diag) return DNGD_OK;
   if (n <= kCholNB) {
     const int smem = 2 * kCholNB * (kCholNB + 1) * (int)sizeof(double);
     static bool attr_set = false;
@@ -382,9 +464,9 @@ static dngd_status trtri_rec(int k0, int n, const float* L, long long ldl, float
   }
   const int n1 = ((n / 2 + kCholNB - 1) / kCholNB) * kCholNB;
   const int n2 = n - n1;
-  dngd_status s = trtri_rec(k0, n1, L, ldl, Linv, ldi, work, st);
+  dngd_status s = trtri_rec(k0, n1, L, ldl, Linv, ldi, work, st, have_diag);
   if (s) return s;
-  s = trtri_rec(k0 + n1, n2, L, ldl, Linv, ldi, work, st);
+  s = trtri_rec(k0 + n1, n2, L, ldl, Linv, ldi, work, st, have_diag);
   if (s) return s;
   // T = L21 * Linv11  (n2 x n1), stored in work with ld n1
   const float* L21 = L + (long long)(k0 + n1) * ldl + k0;
@@ -399,7 +481,12 @@ static dngd_status trtri_rec(int k0, int n, const float* L, long long ldl, float
 dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
                             cudaStream_t st) {
   DNGD_CUDA_CHECK(cudaMemsetAsync(Linv, 0, sizeof(float) * (size_t)m * ldi, st));
-  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st);
+  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, false);
+}
+
+dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
+                              cudaStream_t st) {
+  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -527,19 +614,9 @@ dngd_status gemv_n(int m, int n, const TA* A, long long lda, const double* x, do
 
 template dngd_status gemv_t<double>(int, int, const double*, long long, const double*, double, double*, double*,
                                     cudaStream_t);
-template dngd_status gemv_t<float>(int, int, const float*, long long, const double*, double, double*, double*,
-                                   cudaStream_t);
 template dngd_status gemv_n<double>(int, int, const double*, long long, const double*, double, double*,
                                     cudaStream_t);
-template dngd_status gemv_n<float>(int, int, const float*, long long, const double*, double, double*,
-                                   cudaStream_t);
 
-// y = L x or L^T x with an explicit lower-triangular FP32 matrix (zeros above).
-dngd_status trmv_f32(int m, const float* L, long long ldl, const double* x, double* y, bool trans,
-                     cudaStream_t st) {
-  (void)trans;
-  return gemv_n<float>(m, m, L, ldl, x, 1.0, y, st);
-}
 
 template <typename T>
 __global__ void k_add_diag(int m, T* K, long long ldk, double shift) {
