@@ -134,6 +134,9 @@ typedef struct {
                                a failed low-precision factorisation, up to 12
                                tries; the refinement keeps the exact lambda. */
   int factor_attempts;      /* low-precision factorisations this step (mixed) */
+  float jt_ms, j_ms;        /* durations of the first J^T p and J u launches of
+                               the refinement (mixed, timing enabled): each
+                               reads the FP32 J once */
 } dngd_step_info;
 
 typedef struct dngd_ctx dngd_ctx;

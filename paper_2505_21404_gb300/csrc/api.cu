@@ -76,6 +76,7 @@ struct dngd_ctx {
   void* K0 = nullptr;      // mixed path: Gram + (lambda + mu0) I before factorisation
   double relres[2] = {0.0, 0.0};
   cudaEvent_t ev[9] = {};
+  cudaEvent_t kev[4] = {};  // first J^T p / J u launches of the first solve
 };
 
 namespace {
@@ -270,6 +271,7 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
   P.dotp = c->dot_partials + 256;
   P.scal = c->scal;
   P.scal_h = c->scal_h;
+  P.ev = (c->timing && slot == 0) ? c->kev : nullptr;
   const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
   const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
   return pcg_mixed_solve(P, b, x, tol, maxit, 4, &c->iters[slot], &c->relres[slot], c->st);
@@ -417,6 +419,13 @@ dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
     float tot = 0.f;
     cudaEventElapsedTime(&tot, c->ev[0], c->ev[7]);
     info->phase_ms[7] = tot;
+    if (c->prec != DNGD_FP64 && c->iters[0] > 0) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, c->kev[0], c->kev[1]);
+      cudaEventElapsedTime(&b, c->kev[1], c->kev[2]);
+      info->jt_ms = a;
+      info->j_ms = b;
+    }
   }
   return s;
 }
@@ -558,6 +567,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     if (s) return s;
   }
   for (int i = 0; i < 9; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
+  for (int i = 0; i < 4; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->kev[i]));
   return DNGD_OK;
 }
 
@@ -568,6 +578,8 @@ void free_ctx(dngd_ctx* c) {
   if (c->gram) gram_tc_free(c->gram);
   for (int i = 0; i < 9; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  for (int i = 0; i < 4; ++i)
+    if (c->kev[i]) cudaEventDestroy(c->kev[i]);
   delete c;
 }
 

@@ -90,6 +90,8 @@ struct PcgMixed {
   double* dotp;                       // >= 1024 doubles
   double* scal;                       // device scalars (S_COUNT)
   double* scal_h;                     // pinned host copy
+  cudaEvent_t* ev;                    // optional: 4 events bracketing the first
+                                      // J^T p and J u launches of the solve
 };
 dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, double tol, int maxit, int check_every,
                             int* iters, double* relres, cudaStream_t st);

@@ -343,9 +343,13 @@ dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, doubl
     const int chunk = check_every > 0 ? check_every : 4;
     for (int k = 0; k < chunk && it < maxit; ++k, ++it) {
       // Ap = J (J^T p) + lambda p, with the block partials of <p, Ap>
+      const bool tm = P.ev && it == 0;
+      if (tm) cudaEventRecord(P.ev[0], st);
       if ((s = gemv_t_f32_s(m, P.n, P.J, P.ldJ, P.p, 1.0, P.u, P.partials, P.partial_cap, P.xs, sc, st))) return s;
+      if (tm) cudaEventRecord(P.ev[1], st);
       if ((s = gemv_n_f32_s(m, P.n, P.J, P.ldJ, P.u, 1.0, P.Ap, P.p, P.lambda, P.xs, P.p, pap_parts, sc, st)))
         return s;
+      if (tm) cudaEventRecord(P.ev[2], st);
       DNGD_NOTE_LAUNCH();
       k_cg_alpha<<<1, 256, 0, st>>>(nAp, pap_parts, sc);
       DNGD_NOTE_LAUNCH();

@@ -54,14 +54,16 @@ class StepInfo(C.Structure):
     _fields_ = [("loss", C.c_double), ("norm_v", C.c_double), ("norm_a", C.c_double), ("ga_ratio", C.c_double),
                 ("ga_accepted", C.c_int), ("solve_iters", C.c_int * 2), ("solve_relres", C.c_double * 2),
                 ("not_spd_column", C.c_int), ("device_status", C.c_int), ("phase_ms", C.c_float * 8),
-                ("shift_used", C.c_double), ("factor_attempts", C.c_int)]
+                ("shift_used", C.c_double), ("factor_attempts", C.c_int), ("jt_ms", C.c_float),
+                ("j_ms", C.c_float)]
 
     def as_dict(self):
         return dict(loss=self.loss, norm_v=self.norm_v, norm_a=self.norm_a, ga_ratio=self.ga_ratio,
                     ga_accepted=bool(self.ga_accepted), solve_iters=list(self.solve_iters),
                     solve_relres=list(self.solve_relres), not_spd_column=self.not_spd_column,
                     device_status=self.device_status, phase_ms=list(self.phase_ms),
-                    shift_used=self.shift_used, factor_attempts=self.factor_attempts)
+                    shift_used=self.shift_used, factor_attempts=self.factor_attempts, jt_ms=self.jt_ms,
+                    j_ms=self.j_ms)
 
 
 def _load():
