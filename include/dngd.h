@@ -73,7 +73,12 @@ enum dngd_precision {
   DNGD_MIXED_TF32 = 2   /* as MIXED_BF16 with a TF32 tensor-core Gram */
 };
 
-enum dngd_solver { DNGD_DENSE = 0, DNGD_PCG = 1 };
+enum dngd_solver {
+  DNGD_DENSE = 0,  /* form K, factor, solve (Alg. DenseDualSolve) */
+  DNGD_PCG = 1     /* matrix-free: J never formed; Nystrom-preconditioned CG on
+                      K + lambda I (Alg. PCGStep); precision must be a mixed mode
+                      (FP32 jets and FP32 factor-form operator) */
+};
 
 #define DNGD_MAX_LAYERS 12
 #define DNGD_MAX_DIM 8
@@ -107,10 +112,11 @@ typedef struct {
   double shift_mu;                   /* extra diagonal shift of the factored
                                         preconditioner K_lowp + (lambda+mu) I */
   /* matrix-free PCG solver (DNGD_PCG) */
-  int pcg_rank;                      /* landmarks ell */
-  double pcg_tol;
+  int pcg_rank;                      /* landmarks ell (<= m; default 512) */
+  double pcg_tol;                    /* stop at ||rhs - A x|| <= tol ||rhs|| */
   int pcg_max_it;
-  uint64_t pcg_seed;                 /* landmark permutation seed */
+  uint64_t pcg_seed;                 /* reserved (landmarks come from
+                                        dngd_set_landmarks or are evenly spaced) */
   int keep_gram;                     /* keep K + lambda I for dngd_get_stage(6)
                                         (debug; one extra m x m buffer) */
 } dngd_problem_desc;
@@ -214,9 +220,28 @@ dngd_status dngd_fvv(dngd_ctx* ctx, const double* theta, const double* X, const 
  * which = 0 r [m], 1 alpha [m], 2 v [n], 3 f_vv [m], 4 beta [m], 5 a [n],
  *         6 lower triangle of K + lambda I [m x m] row-major (dense, before
  *           factorisation; the upper triangle is left as zero),
- *         7 Cholesky factor L [m x m] row-major (dense solver).
+ *         7 Cholesky factor L [m x m] row-major (dense solver),
+ *         8 landmark columns K_{:,I} [m x ell] row-major (PCG solver).
  * Values are converted to float64. */
 dngd_status dngd_get_stage(dngd_ctx* ctx, int which, double* dst);
+
+/* Landmarks of the Nystrom preconditioner (Sec. 3.3.1: a landmark is one
+ * scalar residual; Alg. "Nystrom construction" picks the set I).  idx [ell]
+ * host array of residual indices in [0, m), ell <= the desc's pcg_rank.
+ * Without this call the context uses ell evenly spaced residuals.
+ * PCG contexts only; INVALID_ARG otherwise. */
+dngd_status dngd_set_landmarks(dngd_ctx* ctx, const int64_t* idx, int ell);
+
+/* Kernel-vector product w = J (J^T v) + lambda v (Def. 3.3) with the stream
+ * factors of the last dngd_step, J never formed.  v [m] -> w_out [m].
+ * PCG contexts only (STATE before the first step). */
+dngd_status dngd_kvp(dngd_ctx* ctx, const double* v, double* w_out);
+
+/* Nystrom preconditioner of the last step: z = P^{-1} x with
+ * P^{-1} = U (Lambda_hat + lambda I)^{-1} U^T + (I - U U^T) / lambda
+ * (Eq. spec_precond_nystrom_main_final), applied as (K_hat + lambda I)^{-1}
+ * through the Woodbury identity.  x [m] -> z_out [m].  PCG contexts only. */
+dngd_status dngd_precond_apply(dngd_ctx* ctx, const double* x, double* z_out);
 
 /* Gram matrix without any device allocation (the paper has no counterpart:
  * this is a library facility).  K = J J^T + shift I for a BF16 matrix J on the

@@ -77,6 +77,18 @@ struct dngd_ctx {
   double relres[2] = {0.0, 0.0};
   cudaEvent_t ev[9] = {};
   cudaEvent_t kev[4] = {};  // first J^T p / J u launches of the first solve
+
+  // matrix-free Nystrom-PCG solver (solver == DNGD_PCG)
+  bool pcg = false;
+  MatFree mf{};
+  std::vector<int> lm_host;             // landmark point indices
+  int* d_lm = nullptr;
+  int* d_lrows = nullptr;
+  int* d_lrow0 = nullptr;
+  int* d_lS = nullptr;
+  int RI_max = 0;
+  double nu_sticky = 0.0;
+  double nu_used = 0.0;
 };
 
 namespace {
@@ -277,7 +289,10 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
   return pcg_mixed_solve(P, b, x, tol, maxit, 4, &c->iters[slot], &c->relres[slot], c->st);
 }
 
+dngd_status pcg_matfree(dngd_ctx* c, const double* b, double* x, int slot);
+
 dngd_status solve_last(dngd_ctx* c, const double* b, double* x, int slot) {
+  if (c->pcg) return pcg_matfree(c, b, x, slot);
   if (c->prec == DNGD_FP64) {
     c->iters[slot] = 0;
     c->relres[slot] = 0.0;
@@ -389,6 +404,255 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
   return DNGD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Matrix-free Nystrom-PCG step (Alg. PCGStep; push-through recovery)
+// ---------------------------------------------------------------------------
+
+dngd_status upload_landmarks(dngd_ctx* c) {
+  const NetInfo& net = c->net;
+  const int ell = (int)c->lm_host.size();
+  std::vector<int> rows, row0(ell), S(ell);
+  for (int j = 0; j < ell; ++j) {
+    const int p = c->lm_host[j];
+    const ClassInfo& ci = class_of(net, p);
+    const int r = ci.row0 + (p - ci.p0) * ci.S;
+    row0[j] = (int)rows.size();
+    S[j] = ci.S;
+    for (int t = 0; t < ci.S; ++t) rows.push_back(r + t);
+  }
+  if ((int)rows.size() > c->RI_max) return DNGD_ERR_INVALID_ARG;
+  c->mf.RI = (int)rows.size();
+  c->mf.ell = ell;
+  DNGD_CUDA_CHECK(cudaMemcpy(c->d_lm, c->lm_host.data(), sizeof(int) * ell, cudaMemcpyHostToDevice));
+  DNGD_CUDA_CHECK(cudaMemcpy(c->d_lrows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice));
+  DNGD_CUDA_CHECK(cudaMemcpy(c->d_lrow0, row0.data(), sizeof(int) * ell, cudaMemcpyHostToDevice));
+  DNGD_CUDA_CHECK(cudaMemcpy(c->d_lS, S.data(), sizeof(int) * ell, cudaMemcpyHostToDevice));
+  return DNGD_OK;
+}
+
+// PCG on (K + lambda I) x = b with the factor-form operator and the Nystrom
+// preconditioner; host-driven loop (one synchronisation per iteration, small
+// next to a kernel-vector product).
+dngd_status pcg_matfree(dngd_ctx* c, const double* b, double* x, int slot) {
+  const int m = c->m;
+  double* sc = c->scal;
+  const MatFree& F = c->mf;
+  dngd_status s;
+  const double tol = c->desc.pcg_tol > 0 ? c->desc.pcg_tol : 1e-6;
+  const int maxit = c->desc.pcg_max_it > 0 ? c->desc.pcg_max_it : 500;
+  DNGD_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * m, c->st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->cg_res, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st));
+  DNGD_CUDA_CHECK(cudaMemsetAsync(sc + S_BREAK, 0, sizeof(double), c->st));
+  if ((s = dot_dev(m, b, b, sc + S_BB, c->dot_partials, c->st))) return s;
+  if ((s = mf_precond(F, c->lambda, c->cg_res, c->cg_z, c->st))) return s;
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->cg_p, c->cg_z, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st));
+  if ((s = dot_dev(m, c->cg_res, c->cg_z, sc + S_RHO, c->dot_partials, c->st))) return s;
+  int it = 0;
+  double rel = 1.0;
+  for (it = 0; it < maxit;) {
+    if ((s = mf_kvp(F, c->cg_p, c->lambda, c->cg_Ap, c->st))) return s;
+    if ((s = dot_dev(m, c->cg_p, c->cg_Ap, sc + S_PAP, c->dot_partials, c->st))) return s;
+    if ((s = cg_alpha(sc, c->st))) return s;
+    if ((s = cg_update_x(m, sc, x, c->cg_res, c->cg_p, c->cg_Ap, c->st))) return s;
+    if ((s = dot_dev(m, c->cg_res, c->cg_res, sc + S_RR, c->dot_partials, c->st))) return s;
+    ++it;
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+    DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+    const double bb = c->scal_h[S_BB];
+    rel = bb > 0 ? sqrt(c->scal_h[S_RR] / bb) : 0.0;
+    if (rel <= tol || bb == 0.0 || c->scal_h[S_BREAK] != 0.0) break;
+    if ((s = mf_precond(F, c->lambda, c->cg_res, c->cg_z, c->st))) return s;
+    if ((s = dot_dev(m, c->cg_res, c->cg_z, sc + S_RHONEW, c->dot_partials, c->st))) return s;
+    if ((s = cg_beta(sc, c->st))) return s;
+    if ((s = cg_update_p(m, sc, c->cg_z, c->cg_p, c->st))) return s;
+  }
+  c->iters[slot] = it;
+  c->relres[slot] = rel;
+  return DNGD_OK;
+}
+
+dngd_status step_pcg(dngd_ctx* c, const double* theta, const double* X, const double* target) {
+  dngd_status s;
+  const int m = c->m;
+  const long long n = c->n;
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+  evrec(c, 0);
+  const float* th = theta_in_T<float>(c, theta);
+  // jets: r, stream activations H and adjoints D (J is not formed)
+  if ((s = jets_forward<float>(c->net, th, X, target, lp<float>(c->Z), lp<float>(c->H), c->r, c->status, c->st)))
+    return s;
+  if ((s = jets_backward_jacobian<float, float>(c->net, th, X, lp<float>(c->Z), lp<float>(c->H), lp<float>(c->D),
+                                                (float*)c->Hbar, (float*)nullptr, 0, nullptr, 0, c->st)))
+    return s;
+  evrec(c, 1);
+  c->mf.X = X;
+  if ((s = mf_input_rows(c->mf, c->st))) return s;
+  if ((s = mf_kci(c->mf, c->st))) return s;
+  evrec(c, 8);
+  // Nystrom factors; K_II + nu I is shifted up only if it does not factor
+  double nu = c->nu_sticky;
+  for (int attempt = 0;; ++attempt) {
+    evrec(c, 2);
+    if ((s = mf_nystrom(c->mf, c->lambda, nu, c->status, c->st))) return s;
+    const dngd_status fs = read_status(c);
+    if (fs != DNGD_ERR_NOT_SPD || attempt >= 15) break;
+    if ((s = mf_kii_trace(c->mf, c->scal + S_TRACE, c->st))) return s;
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+    DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+    const double base = 1e-7 * (c->scal_h[S_TRACE] > 0 ? c->scal_h[S_TRACE] : 1.0) / c->mf.ell;
+    nu = nu * 3.0 > base ? nu * 3.0 : base;
+    DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+  }
+  c->nu_sticky = nu;
+  c->nu_used = nu;
+  if ((s = read_status(c))) return s;
+  evrec(c, 3);
+  if ((s = pcg_matfree(c, c->r, c->alpha, 0))) return s;
+  if ((s = mf_jtv(c->mf, c->alpha, c->mf.g32, c->st))) return s;
+  if ((s = mf_g_to_double(n, c->mf.g32, -1.0, c->v, c->st))) return s;
+  evrec(c, 4);
+  if (c->desc.use_ga) {
+    to_float(n, c->v, c->v32, c->st);
+    if ((s = jets_fvv<float>(c->net, th, c->v32, X, (float*)c->Z3, (float*)c->H3a, (float*)c->H3b, c->fvv,
+                             c->st)))
+      return s;
+    evrec(c, 5);
+    if ((s = pcg_matfree(c, c->fvv, c->beta, 1))) return s;
+    if ((s = mf_jtv(c->mf, c->beta, c->mf.g32, c->st))) return s;
+    if ((s = mf_g_to_double(n, c->mf.g32, -1.0, c->a, c->st))) return s;
+    evrec(c, 6);
+  } else {
+    evrec(c, 5);
+    evrec(c, 6);
+  }
+  if ((s = ga_finish((int)n, c->v, c->a, c->desc.use_ga, c->desc.eps_norm,
+                     c->desc.ga_ratio_max > 0 ? c->desc.ga_ratio_max : 0.5, c->delta, c->scal, c->dot_partials,
+                     c->status, c->st)))
+    return s;
+  if ((s = dot_dev(m, c->r, c->r, c->scal + S_LOSS, c->dot_partials, c->st))) return s;
+  evrec(c, 7);
+  c->have_step = true;
+  return DNGD_OK;
+}
+
+dngd_status alloc_pcg(dngd_ctx* c, bool dry, size_t* bytes_out) {
+  const NetInfo& net = c->net;
+  const int m = net.m;
+  const long long n = net.n;
+  const int L = net.n_layers - 1;
+  const int ell = c->desc.pcg_rank > 0 ? (c->desc.pcg_rank < m ? c->desc.pcg_rank : m) : (m < 512 ? m : 512);
+  int Smax = 1;
+  for (int k = 0; k < net.n_classes; ++k) Smax = net.cls[k].S > Smax ? net.cls[k].S : Smax;
+  c->RI_max = ell * Smax;
+  const int RI = c->RI_max;
+  const int wl = net.widths[L];
+  const int wmax = net.max_w > net.d_in ? net.max_w : net.d_in;
+  size_t tot = 0;
+  auto add = [&](size_t b) { tot += (b + 255) & ~(size_t)255; };
+  const size_t rb = (size_t)net.R * wmax;
+  add(8 * (3 * n + (size_t)m * net.d_in + 2 * m));          // staging
+  add(4 * 2 * n);                                            // theta32, v32
+  for (int l = 0; l < L; ++l) add(4 * 3 * (size_t)net.R * net.widths[l + 1]);
+  add(4 * rb * 10);                                          // Hbar, Z3, H3a, H3b
+  add(4 * ((size_t)net.R + n + rb + (size_t)net.R * net.d_in));  // vrow, g32, Y, Hin
+  add(4 * 2 * (size_t)RI * wmax + 4 * 2 * (size_t)net.R * RI); // DI, HI, P, Q
+  add(4 * ((size_t)m * ell + (size_t)m * wl + (size_t)ell * wl + m));
+  add(4 * (4 * (size_t)ell * ell + (size_t)m * ell + (size_t)ell * ell));
+  add(8 * ((size_t)m * 12 + 3 * n + 16 * (size_t)(n > m ? n : m)));
+  if (bytes_out) *bytes_out = tot;
+  if (dry) return DNGD_OK;
+  dngd_status s;
+#define A_(p, T, cnt) \
+  if ((s = dalloc<T>(c, (T**)&(p), (cnt)))) return s;
+  A_(c->theta_s, double, n);
+  A_(c->X_s, double, (size_t)m * net.d_in);
+  A_(c->target_s, double, m);
+  A_(c->nvec_s, double, n);
+  A_(c->mvec_s, double, m);
+  A_(c->theta_tmp, double, n);
+  A_(c->theta32, float, n);
+  A_(c->v32, float, n);
+  for (int l = 0; l < L; ++l) {
+    const size_t cnt = (size_t)net.R * net.widths[l + 1];
+    A_(c->Z[l], float, cnt);
+    A_(c->H[l], float, cnt);
+    A_(c->D[l], float, cnt);
+  }
+  A_(c->Hbar, float, rb);
+  A_(c->Z3, float, 3 * rb);
+  A_(c->H3a, float, 3 * rb);
+  A_(c->H3b, float, 3 * rb);
+  MatFree& F = c->mf;
+  F.net = &c->net;
+  for (int l = 0; l < kMaxLayers; ++l) {
+    F.H.p[l] = (float*)c->H[l];
+    F.D.p[l] = (float*)c->D[l];
+  }
+  A_(F.vrow, float, net.R);
+  A_(F.g32, float, n);
+  A_(F.Y, float, rb);
+  A_(F.Hin, float, (size_t)net.R * net.d_in);
+  A_(F.DI, float, (size_t)RI * wmax);
+  A_(F.HI, float, (size_t)RI * wmax);
+  A_(F.P, float, (size_t)net.R * RI);
+  A_(F.Q, float, (size_t)net.R * RI);
+  A_(F.KCI, float, (size_t)m * ell);
+  A_(F.Fo, float, (size_t)m * wl);
+  A_(F.FoI, float, (size_t)ell * wl);
+  A_(F.fb, float, m);
+  A_(F.KII, float, (size_t)ell * ell);
+  A_(F.LIIinv, float, (size_t)ell * ell);
+  A_(F.C, float, (size_t)ell * ell);
+  A_(F.LCinv, float, (size_t)ell * ell);
+  A_(F.work, float, (size_t)ell * ell);
+  A_(F.M, float, (size_t)m * ell);
+  A_(F.t1, double, ell > m ? ell : m);
+  A_(F.t2, double, ell > m ? ell : m);
+  A_(F.t3, double, m);
+  A_(c->d_lm, int, ell);
+  A_(c->d_lrows, int, RI);
+  A_(c->d_lrow0, int, ell);
+  A_(c->d_lS, int, ell);
+  F.lm = c->d_lm;
+  F.lrows = c->d_lrows;
+  F.lrow0 = c->d_lrow0;
+  F.lS = c->d_lS;
+  A_(c->r, double, m);
+  A_(c->alpha, double, m);
+  A_(c->fvv, double, m);
+  A_(c->beta, double, m);
+  A_(c->v, double, n);
+  A_(c->a, double, n);
+  A_(c->delta, double, n);
+  A_(c->cg_res, double, m);
+  A_(c->cg_z, double, m);
+  A_(c->cg_p, double, m);
+  A_(c->cg_Ap, double, m);
+  A_(c->cg_y, double, m);
+  A_(c->xsol, double, m);
+  A_(c->cg_u, double, n);
+  A_(c->partials, double, (size_t)16 * (n > m ? n : m));
+  A_(c->dot_partials, double, 256 + 1024 + (size_t)m / 4 + 64);
+  A_(c->xs, float2, (size_t)round_up(n > m ? n : m, 4) + 4);
+  A_(c->scal, double, S_COUNT);
+  A_(c->status, int, 4);
+#undef A_
+  F.xs = c->xs;
+  F.partials = c->partials;
+  F.partial_cap = 16LL * (n > m ? n : m);
+  DNGD_CUDA_CHECK(cudaMemset(c->a, 0, sizeof(double) * n));
+  DNGD_CUDA_CHECK(cudaMemset(c->scal, 0, sizeof(double) * S_COUNT));
+  DNGD_CUDA_CHECK(cudaMemset(c->status, 0, sizeof(int) * 4));
+  DNGD_CUDA_CHECK(cudaMallocHost(&c->scal_h, sizeof(double) * S_COUNT));
+  DNGD_CUDA_CHECK(cudaMallocHost(&c->status_h, sizeof(int) * 4));
+  for (int i = 0; i < 9; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
+  for (int i = 0; i < 4; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->kev[i]));
+  // default landmarks: evenly spaced residual indices
+  c->lm_host.resize(ell);
+  for (int j = 0; j < ell; ++j) c->lm_host[j] = (int)(((long long)j * m) / ell);
+  return upload_landmarks(c);
+}
+
 dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
   DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
   dngd_status s = read_status(c);
@@ -405,7 +669,7 @@ dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
   info->solve_relres[1] = c->relres[1];
   info->device_status = c->status_h[0];
   info->not_spd_column = (c->status_h[0] & ST_NOT_SPD) ? c->status_h[1] : -1;
-  info->shift_used = c->shift_used;
+  info->shift_used = c->pcg ? c->nu_used : c->shift_used;
   info->factor_attempts = c->factor_attempts;
   if (c->timing) {
     // event order: 0 start, 1 jets+J, 8 Gram kernel, 2 Gram epilogue, 3 factor,
@@ -630,6 +894,7 @@ dngd_status dngd_workspace_bytes(const dngd_problem_desc* desc, size_t* bytes) {
   dngd_status s = build_net(desc, &tmp.net);
   if (s) return s;
   tmp.prec = desc->precision;
+  if (desc->solver == DNGD_PCG) return alloc_pcg(&tmp, true, bytes);
   return alloc_workspace(&tmp, true, bytes);
 }
 
@@ -637,7 +902,8 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
   if (!out || !desc) return DNGD_ERR_INVALID_ARG;
   *out = nullptr;
   if (desc->precision < DNGD_FP64 || desc->precision > DNGD_MIXED_TF32) return DNGD_ERR_INVALID_ARG;
-  if (desc->solver != DNGD_DENSE) return DNGD_ERR_INVALID_ARG;
+  if (desc->solver != DNGD_DENSE && desc->solver != DNGD_PCG) return DNGD_ERR_INVALID_ARG;
+  if (desc->solver == DNGD_PCG && desc->precision == DNGD_FP64) return DNGD_ERR_INVALID_ARG;
   if (!(desc->lambda > 0.0)) return DNGD_ERR_INVALID_ARG;
   dngd_ctx* c = new dngd_ctx();
   c->desc = *desc;
@@ -652,7 +918,8 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
   c->R = c->net.R;
   c->prec = desc->precision;
   c->lambda = desc->lambda;
-  if ((s = alloc_workspace(c, false, nullptr))) {
+  c->pcg = desc->solver == DNGD_PCG;
+  if ((s = c->pcg ? alloc_pcg(c, false, nullptr) : alloc_workspace(c, false, nullptr))) {
     free_ctx(c);
     return s;
   }
@@ -686,7 +953,8 @@ dngd_status dngd_step(dngd_ctx* c, const double* theta, const double* X, const d
   const double* x = in_ptr(c, X, c->X_s, (size_t)c->m * c->net.d_in);
   const double* tg = in_ptr(c, target, c->target_s, c->m);
   c->have_step = false;
-  dngd_status s = c->prec == DNGD_FP64 ? step_T<double>(c, th, x, tg, info) : step_T<float>(c, th, x, tg, info);
+  dngd_status s = c->pcg ? step_pcg(c, th, x, tg)
+                         : (c->prec == DNGD_FP64 ? step_T<double>(c, th, x, tg, info) : step_T<float>(c, th, x, tg, info));
   if (s) {
     dngd_status ds = read_status(c);
     if (info) fill_info(c, info);
@@ -714,6 +982,14 @@ dngd_status dngd_residual_jacobian(dngd_ctx* c, const double* theta, const doubl
   const double* tg = in_ptr(c, target, c->target_s, c->m);
   DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
   dngd_status s;
+  if (c->pcg) {
+    if (J_out) return DNGD_ERR_INVALID_ARG;  // the matrix-free context never forms J
+    s = forward_only<float>(c, theta_in_T<float>(c, th), x, tg, c->r);
+    if (s) return s;
+    c->have_step = false;
+    if ((s = out_copy(c, r_out, c->r, c->m))) return s;
+    return read_status(c);
+  }
   if (c->prec == DNGD_FP64) s = residual_jacobian_T<double>(c, theta_in_T<double>(c, th), x, tg);
   else s = residual_jacobian_T<float>(c, theta_in_T<float>(c, th), x, tg);
   if (s) return s;
@@ -829,8 +1105,54 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
       cudaFree(buf);
       return s;
     }
+    case 8: {
+      if (!c->pcg) return DNGD_ERR_STATE;
+      double* buf = nullptr;
+      const long long cnt = (long long)m * c->mf.ell;
+      if (cudaMalloc(&buf, sizeof(double) * cnt) != cudaSuccess) return DNGD_ERR_OOM;
+      dngd_status s = mf_g_to_double(cnt, c->mf.KCI, 1.0, buf, c->st);
+      if (!s) {
+        cudaMemcpyAsync(dst, buf, sizeof(double) * cnt, cudaMemcpyDefault, c->st);
+        cudaStreamSynchronize(c->st);
+      }
+      cudaFree(buf);
+      return s;
+    }
     default: return DNGD_ERR_INVALID_ARG;
   }
+}
+
+dngd_status dngd_set_landmarks(dngd_ctx* c, const int64_t* idx, int ell) {
+  if (!c || !idx || !c->pcg || ell < 1 || ell > c->mf.ell || ell > c->m) return DNGD_ERR_INVALID_ARG;
+  std::vector<int> keep = c->lm_host;
+  c->lm_host.assign(ell, 0);
+  for (int j = 0; j < ell; ++j) {
+    if (idx[j] < 0 || idx[j] >= c->m) {
+      c->lm_host = keep;
+      return DNGD_ERR_INVALID_ARG;
+    }
+    c->lm_host[j] = (int)idx[j];
+  }
+  c->nu_sticky = 0.0;
+  return upload_landmarks(c);
+}
+
+dngd_status dngd_kvp(dngd_ctx* c, const double* v, double* w_out) {
+  if (!c || !v || !w_out) return DNGD_ERR_INVALID_ARG;
+  if (!c->pcg || !c->have_step) return DNGD_ERR_STATE;
+  const double* vv = in_ptr(c, v, c->mvec_s, c->m);
+  dngd_status s = mf_kvp(c->mf, vv, c->lambda, c->xsol, c->st);
+  if (s) return s;
+  return out_copy(c, w_out, c->xsol, c->m);
+}
+
+dngd_status dngd_precond_apply(dngd_ctx* c, const double* x, double* z_out) {
+  if (!c || !x || !z_out) return DNGD_ERR_INVALID_ARG;
+  if (!c->pcg || !c->have_step) return DNGD_ERR_STATE;
+  const double* xx = in_ptr(c, x, c->mvec_s, c->m);
+  dngd_status s = mf_precond(c->mf, c->lambda, xx, c->xsol, c->st);
+  if (s) return s;
+  return out_copy(c, z_out, c->xsol, c->m);
 }
 
 }  // extern "C"

@@ -457,6 +457,7 @@ dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const dou
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_jac_write<T, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
+  if (J == nullptr) return DNGD_OK;  // matrix-free use: stream adjoints only
   dim3 grid(net.m, L + 1);
   DNGD_NOTE_LAUNCH();
   k_jac_write<T, TJ><<<grid, 256, smem, st>>>(net, theta, X, H, D, J, ldJ, Jb, ldb);

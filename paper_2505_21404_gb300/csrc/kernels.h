@@ -36,6 +36,12 @@ template <typename T>
 dngd_status gemm_nn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb,
                     T beta, T* C, long long ldc, cudaStream_t st);
 
+// C[M x N] = alpha * A^T diag(kscale) B + beta * C, A [K x M], B [K x N]
+// row-major; kscale [K] may be null.
+template <typename T>
+dngd_status gemm_tn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb, T beta,
+                    T* C, long long ldc, const T* kscale, cudaStream_t st);
+
 // In-place blocked Cholesky of the lower triangle of A [m x m] (lda).
 // TA = double: everything in FP64.  TA = float: FP32 panels and trailing
 // updates with every diagonal block factored in FP64.
@@ -57,6 +63,10 @@ dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* 
 // Explicit inverse of a lower-triangular FP32 factor: Linv = L^{-1} (lower).
 dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
                             cudaStream_t st);
+
+// y = alpha * A x + add_scale * add  (FP32 A, double-float accumulation)
+dngd_status gemv_n_f32(int m, int n, const float* A, long long lda, const double* x, double alpha, double* y,
+                       const double* add, double add_scale, float2* xs, cudaStream_t st);
 
 // y = alpha * A^T x  (A [m x n] row-major, x [m], y [n]); partials: [splits x n]
 template <typename TA>
@@ -105,6 +115,40 @@ dngd_status dot_dev(int n, const double* x, const double* y, double* out, double
 
 // Device-side vector kernels used by the refinement / PCG loops.
 dngd_status axpy_dev(int n, double alpha, const double* x, double* y, cudaStream_t st);
+
+// ---- matfree.cu: matrix-free operator and Nystrom preconditioner -----------
+struct MatFree {
+  const NetInfo* net;
+  const double* X;
+  LayerPtrs<float> H, D;   // stream activations / adjoints of the hidden layers
+  float* vrow;             // [R]
+  float* g32;              // [n]
+  float* Y;                // [R x max_w]
+  float* Hin;              // [R x d_in] input streams of layer 0
+  int ell, RI;             // landmarks, their stream rows
+  const int* lm;           // [ell] landmark residual (point) indices
+  const int* lrows;        // [RI] stream rows of the landmarks
+  const int* lrow0;        // [ell] first gathered row of landmark j
+  const int* lS;           // [ell] streams of landmark j
+  float *DI, *HI;          // [RI x max_w]
+  float *P, *Q;            // [R x RI]
+  float* KCI;              // [m x ell]
+  float *Fo, *FoI, *fb;    // output-layer features [m x w_L], [ell x w_L], [m]
+  float *KII, *LIIinv, *M, *C, *LCinv, *work;
+  double *t1, *t2, *t3;
+  float2* xs;
+  double* partials;
+  long long partial_cap;
+};
+dngd_status mf_jtv(const MatFree& F, const double* v, float* g, cudaStream_t st);
+dngd_status mf_jv(const MatFree& F, const float* u, double* y, cudaStream_t st);
+dngd_status mf_kvp(const MatFree& F, const double* v, double lambda, double* w, cudaStream_t st);
+dngd_status mf_kci(const MatFree& F, cudaStream_t st);
+dngd_status mf_nystrom(const MatFree& F, double lambda, double nu, int* status, cudaStream_t st);
+dngd_status mf_precond(const MatFree& F, double lambda, const double* x, double* z, cudaStream_t st);
+dngd_status mf_input_rows(const MatFree& F, cudaStream_t st);
+dngd_status mf_g_to_double(long long n, const float* g, double alpha, double* out, cudaStream_t st);
+dngd_status mf_kii_trace(const MatFree& F, double* out, cudaStream_t st);
 
 // ---- gram_tc.cu -----------------------------------------------------------
 // K (FP32, lower 128x256 tiles) = Jlow Jlow^T with tcgen05 tensor cores.

@@ -14,10 +14,10 @@ namespace dngd {
 // BT = true: B is [N x K] (C = A B^T); BT = false: B is [K x N].
 // ---------------------------------------------------------------------------
 
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool BT>
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool BT, bool AT = false>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, const T* __restrict__ B,
-       long long ldb, T beta, T* __restrict__ C, long long ldc, int lower) {
+       long long ldb, T beta, T* __restrict__ C, long long ldc, int lower, const T* __restrict__ kscale = nullptr) {
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
@@ -31,11 +31,23 @@ k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, con
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
   for (int k0 = 0; k0 < K; k0 += BK) {
+    if (AT) {
+      // A is [K x M] row-major (C = A^T op(B)); optional per-k scale of A
 #pragma unroll
-    for (int e = tid; e < BM * BK; e += NT) {
-      const int r = e / BK, kk = e % BK;
-      const int gr = bm + r, gk = k0 + kk;
-      As[kk][r] = (gr < M && gk < K) ? A[(long long)gr * lda + gk] : T(0);
+      for (int e = tid; e < BM * BK; e += NT) {
+        const int kk = e / BM, r = e % BM;
+        const int gr = bm + r, gk = k0 + kk;
+        T v = (gr < M && gk < K) ? A[(long long)gk * lda + gr] : T(0);
+        if (kscale && gk < K) v *= kscale[gk];
+        As[kk][r] = v;
+      }
+    } else {
+#pragma unroll
+      for (int e = tid; e < BM * BK; e += NT) {
+        const int r = e / BK, kk = e % BK;
+        const int gr = bm + r, gk = k0 + kk;
+        As[kk][r] = (gr < M && gk < K) ? A[(long long)gr * lda + gk] : T(0);
+      }
     }
     if (BT) {
 #pragma unroll
@@ -118,6 +130,26 @@ dngd_status gemm_nn(int M, int N, int K, T alpha, const T* A, long long lda, con
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
+
+// C[M x N] = alpha * A^T B + beta * C with A [K x M], B [K x N] row-major and
+// an optional scale of A's rows (the K index): C = A^T diag(kscale) B.
+template <typename T>
+dngd_status gemm_tn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb, T beta,
+                    T* C, long long ldc, const T* kscale, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DNGD_OK;
+  using G = GemmCfg<T>;
+  dim3 grid(cdiv(N, G::BN), cdiv(M, G::BM));
+  DNGD_NOTE_LAUNCH();
+  k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN, false, true>
+      <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0,
+                                                          kscale);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+template dngd_status gemm_tn<float>(int, int, int, float, const float*, long long, const float*, long long, float,
+                                    float*, long long, const float*, cudaStream_t);
+template dngd_status gemm_tn<double>(int, int, int, double, const double*, long long, const double*, long long,
+                                     double, double*, long long, const double*, cudaStream_t);
 
 template dngd_status gemm_nt<double>(int, int, int, double, const double*, long long, const double*, long long,
                                      double, double*, long long, bool, cudaStream_t);

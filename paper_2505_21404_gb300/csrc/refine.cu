@@ -316,6 +316,11 @@ dngd_status gemv_t_f32(int m, int n, const float* A, long long lda, const double
   return gemv_t_f32_s(m, n, A, lda, x, alpha, y, partials, partial_cap, xs, nullptr, st);
 }
 
+dngd_status gemv_n_f32(int m, int n, const float* A, long long lda, const double* x, double alpha, double* y,
+                       const double* add, double add_scale, float2* xs, cudaStream_t st) {
+  return gemv_n_f32_s(m, n, A, lda, x, alpha, y, add, add_scale, xs, nullptr, nullptr, nullptr, st);
+}
+
 dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, double tol, int maxit, int check_every,
                             int* iters, double* relres, cudaStream_t st) {
   const int m = P.m;

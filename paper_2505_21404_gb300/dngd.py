@@ -27,7 +27,7 @@ STATUS = {
     -8: "DNGD_ERR_STATE", -9: "DNGD_ERR_OOM",
 }
 
-STAGES = dict(r=0, alpha=1, v=2, fvv=3, beta=4, a=5, gram=6, chol=7)
+STAGES = dict(r=0, alpha=1, v=2, fvv=3, beta=4, a=5, gram=6, chol=7, kci=8)
 
 
 class DngdError(RuntimeError):
@@ -90,6 +90,9 @@ def _load():
         "dngd_fvv": (C.c_int, [P, P, P, P, P, P]),
         "dngd_get_stage": (C.c_int, [P, C.c_int, P]),
         "dngd_gram_bf16_noalloc": (C.c_int, [P, C.c_int, C.c_int, C.c_longlong, P, C.c_longlong, C.c_double, P]),
+        "dngd_set_landmarks": (C.c_int, [P, P, C.c_int]),
+        "dngd_kvp": (C.c_int, [P, P, P]),
+        "dngd_precond_apply": (C.c_int, [P, P, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -103,7 +106,7 @@ lib = _load()
 EXPORTED = ["dngd_status_string", "dngd_version", "dngd_launch_count", "dngd_num_params", "dngd_create", "dngd_workspace_bytes",
             "dngd_destroy", "dngd_set_timing", "dngd_set_lambda", "dngd_step", "dngd_solve", "dngd_loss",
             "dngd_line_search", "dngd_residual_jacobian", "dngd_fvv", "dngd_get_stage",
-            "dngd_gram_bf16_noalloc"]
+            "dngd_gram_bf16_noalloc", "dngd_set_landmarks", "dngd_kvp", "dngd_precond_apply"]
 
 
 def _check(status, where):
@@ -123,7 +126,8 @@ def _ptr(a):
 
 
 def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_ratio_max=0.5, refine_max_it=200,
-              refine_tol=1e-10, shift_mu=0.0, keep_gram=False):
+              refine_tol=1e-10, shift_mu=0.0, keep_gram=False, solver=DENSE, pcg_rank=512, pcg_tol=1e-6,
+              pcg_max_it=500):
     """Problem descriptor from a workload dict (see workloads.py)."""
     d = ProblemDesc()
     widths = list(spec["widths"])
@@ -141,7 +145,10 @@ def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_rati
         for k, b in enumerate(cl["lap_mask"]):
             cd.lap_mask[k] = int(bool(b))
     d.precision = int(precision)
-    d.solver = DENSE
+    d.solver = int(solver)
+    d.pcg_rank = int(pcg_rank)
+    d.pcg_tol = float(pcg_tol)
+    d.pcg_max_it = int(pcg_max_it)
     d.lam = float(spec["lam"] if lam is None else lam)
     d.use_ga = int(bool(use_ga))
     d.eps_norm = float(eps_norm)
@@ -234,6 +241,16 @@ class Context:
 
     def fvv(self, theta, X, target, v, out):
         _check(lib.dngd_fvv(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(v), _ptr(out)), "dngd_fvv")
+
+    def set_landmarks(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        _check(lib.dngd_set_landmarks(self._h, idx.ctypes.data_as(C.c_void_p), int(idx.size)), "dngd_set_landmarks")
+
+    def kvp(self, v, out):
+        _check(lib.dngd_kvp(self._h, _ptr(v), _ptr(out)), "dngd_kvp")
+
+    def precond_apply(self, x, out):
+        _check(lib.dngd_precond_apply(self._h, _ptr(x), _ptr(out)), "dngd_precond_apply")
 
     def get_stage(self, name, out):
         _check(lib.dngd_get_stage(self._h, STAGES[name], _ptr(out)), "dngd_get_stage")
