@@ -683,13 +683,14 @@ dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
     float tot = 0.f;
     cudaEventElapsedTime(&tot, c->ev[0], c->ev[7]);
     info->phase_ms[7] = tot;
-    if (c->prec != DNGD_FP64 && c->iters[0] > 0) {
+    if (!c->pcg && c->prec != DNGD_FP64 && c->iters[0] > 0) {
       float a = 0.f, b = 0.f;
       cudaEventElapsedTime(&a, c->kev[0], c->kev[1]);
       cudaEventElapsedTime(&b, c->kev[1], c->kev[2]);
       info->jt_ms = a;
       info->j_ms = b;
     }
+    cudaGetLastError();  // an unrecorded event only leaves a timing field at 0
   }
   return s;
 }

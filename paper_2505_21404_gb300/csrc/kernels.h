@@ -42,6 +42,12 @@ template <typename T>
 dngd_status gemm_tn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb, T beta,
                     T* C, long long ldc, const T* kscale, cudaStream_t st);
 
+// FP32 GEMMs with compensated (Kahan over BK-slabs) accumulation.
+dngd_status gemm_nt_comp(int M, int N, int K, float alpha, const float* A, long long lda, const float* B,
+                         long long ldb, float beta, float* C, long long ldc, cudaStream_t st);
+dngd_status gemm_tn_comp(int M, int N, int K, float alpha, const float* A, long long lda, const float* B,
+                         long long ldb, float beta, float* C, long long ldc, const float* kscale, cudaStream_t st);
+
 // In-place blocked Cholesky of the lower triangle of A [m x m] (lda).
 // TA = double: everything in FP64.  TA = float: FP32 panels and trailing
 // updates with every diagonal block factored in FP64.

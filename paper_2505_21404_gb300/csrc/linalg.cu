@@ -14,7 +14,11 @@ namespace dngd {
 // BT = true: B is [N x K] (C = A B^T); BT = false: B is [K x N].
 // ---------------------------------------------------------------------------
 
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool BT, bool AT = false>
+// COMP: compensated accumulation.  Each BK-slab of products is summed in a
+// plain accumulator, then added into (acc, cmp) with Kahan compensation, so
+// the error does not grow with K (used where the operator must stay
+// consistent over thousands of PCG applications).
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool BT, bool AT = false, bool COMP = false>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, const T* __restrict__ B,
        long long ldb, T beta, T* __restrict__ C, long long ldc, int lower, const T* __restrict__ kscale = nullptr) {
@@ -26,10 +30,18 @@ k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, con
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   T acc[TM][TN];
+  T cmp[COMP ? TM : 1][COMP ? TN : 1];
+  T part[COMP ? TM : 1][COMP ? TN : 1];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  if (COMP) {
+#pragma unroll
+    for (int i = 0; i < (COMP ? TM : 1); ++i)
+#pragma unroll
+      for (int j = 0; j < (COMP ? TN : 1); ++j) cmp[i][j] = T(0);
+  }
   for (int k0 = 0; k0 < K; k0 += BK) {
     if (AT) {
       // A is [K x M] row-major (C = A^T op(B)); optional per-k scale of A
@@ -65,6 +77,12 @@ k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, con
       }
     }
     __syncthreads();
+    if (COMP) {
+#pragma unroll
+      for (int i = 0; i < (COMP ? TM : 1); ++i)
+#pragma unroll
+        for (int j = 0; j < (COMP ? TN : 1); ++j) part[i][j] = T(0);
+    }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T a[TM], b[TN];
@@ -72,10 +90,28 @@ k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, con
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
       for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+      if (COMP) {
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+        for (int i = 0; i < (COMP ? TM : 1); ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+          for (int j = 0; j < (COMP ? TN : 1); ++j) part[i][j] += a[i] * b[j];
+      } else {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+      }
+    }
+    if (COMP) {
+#pragma unroll
+      for (int i = 0; i < (COMP ? TM : 1); ++i)
+#pragma unroll
+        for (int j = 0; j < (COMP ? TN : 1); ++j) {
+          const T y = part[i][j] - cmp[i][j];
+          const T t = acc[i][j] + y;
+          cmp[i][j] = (t - acc[i][j]) - y;
+          acc[i][j] = t;
+        }
     }
     __syncthreads();
   }
@@ -148,6 +184,29 @@ dngd_status gemm_tn(int M, int N, int K, T alpha, const T* A, long long lda, con
 }
 template dngd_status gemm_tn<float>(int, int, int, float, const float*, long long, const float*, long long, float,
                                     float*, long long, const float*, cudaStream_t);
+
+// FP32 GEMMs with compensated accumulation (64 x 128 tiles, 4 x 8 per thread).
+dngd_status gemm_nt_comp(int M, int N, int K, float alpha, const float* A, long long lda, const float* B,
+                         long long ldb, float beta, float* C, long long ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DNGD_OK;
+  dim3 grid(cdiv(N, 128), cdiv(M, 64));
+  DNGD_NOTE_LAUNCH();
+  k_gemm<float, 64, 128, 8, 4, 8, true, false, true>
+      <<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, nullptr);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+dngd_status gemm_tn_comp(int M, int N, int K, float alpha, const float* A, long long lda, const float* B,
+                         long long ldb, float beta, float* C, long long ldc, const float* kscale, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DNGD_OK;
+  dim3 grid(cdiv(N, 128), cdiv(M, 64));
+  DNGD_NOTE_LAUNCH();
+  k_gemm<float, 64, 128, 8, 4, 8, false, true, true>
+      <<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, kscale);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
 template dngd_status gemm_tn<double>(int, int, int, double, const double*, long long, const double*, long long,
                                      double, double*, long long, const double*, cudaStream_t);
 

@@ -40,26 +40,26 @@ __global__ void k_jtv_first_and_bias(NetInfo net, const double* __restrict__ v, 
   if (a >= w) return;
   const float* Dl = D.p[l];
   const int din = net.d_in;
-  float gb = 0.f;
-  float gw[kMaxDim];
-  for (int k = 0; k < din; ++k) gw[k] = 0.f;
+  double gb = 0.0;
+  double gw[kMaxDim];
+  for (int k = 0; k < din; ++k) gw[k] = 0.0;
   for (int c = 0; c < net.n_classes; ++c) {
     const ClassInfo& ci = net.cls[c];
     for (int i = 0; i < ci.count; ++i) {
       const int p = ci.p0 + i;
       const long long row = ci.row0 + (long long)i * ci.S;
-      const float vi = (float)v[p];
-      const float dval = Dl[row * w + a];
+      const double vi = v[p];
+      const double dval = Dl[row * w + a];
       gb += vi * dval;
       if (l == 0) {
-        for (int k = 0; k < din; ++k) gw[k] += vi * dval * (float)X[(long long)p * din + k];
-        for (int j = 0; j < ci.nD; ++j) gw[ci.D[j]] += vi * Dl[(row + 1 + j) * w + a];
+        for (int k = 0; k < din; ++k) gw[k] += vi * dval * X[(long long)p * din + k];
+        for (int j = 0; j < ci.nD; ++j) gw[ci.D[j]] += vi * (double)Dl[(row + 1 + j) * w + a];
       }
     }
   }
-  g[net.b_off[l] + a] = gb;
+  g[net.b_off[l] + a] = (float)gb;
   if (l == 0)
-    for (int k = 0; k < din; ++k) g[net.w_off[0] + (long long)a * din + k] = gw[k];
+    for (int k = 0; k < din; ++k) g[net.w_off[0] + (long long)a * din + k] = (float)gw[k];
 }
 
 // Output-layer part of J^T v: g_W[b] = sum_i v_i sum_s ubar_s H_{L-1}[row_s][b],
@@ -71,30 +71,29 @@ __global__ void k_jtv_out(NetInfo net, const double* __restrict__ v, const doubl
   const int w = net.widths[L];
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < w) {
-    float acc = 0.f;
+    double acc = 0.0;
     for (int c = 0; c < net.n_classes; ++c) {
       const ClassInfo& ci = net.cls[c];
-      const float sc = (float)ci.scale;
       for (int i = 0; i < ci.count; ++i) {
         const int p = ci.p0 + i;
-        const float vi = (float)v[p] * sc;
+        const double vi = v[p] * ci.scale;
         if (L == 0) {
-          float hv = (float)X[(long long)p * net.d_in + b] * (float)ci.c_val;
+          double hv = X[(long long)p * net.d_in + b] * ci.c_val;
           for (int j = 0; j < ci.nD; ++j)
-            if (ci.D[j] == b) hv += (float)ci.c_gradD[j];
+            if (ci.D[j] == b) hv += ci.c_gradD[j];
           acc += vi * hv;
         } else {
           const long long row = ci.row0 + (long long)i * ci.S;
-          float hv = 0.f;
+          double hv = 0.0;
           for (int s = 0; s < ci.S; ++s) {
-            const float coef = s == 0 ? (float)ci.c_val : (s <= ci.nD ? (float)ci.c_gradD[s - 1] : (float)ci.c_lap);
-            hv += coef * Hlast[(row + s) * w + b];
+            const double coef = s == 0 ? ci.c_val : (s <= ci.nD ? ci.c_gradD[s - 1] : ci.c_lap);
+            hv += coef * (double)Hlast[(row + s) * w + b];
           }
           acc += vi * hv;
         }
       }
     }
-    g[net.w_off[L] + b] = acc;
+    g[net.w_off[L] + b] = (float)acc;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double acc = 0.0;
@@ -129,22 +128,22 @@ __global__ void k_jv_rowdot(NetInfo net, int l, const float* __restrict__ Dl, co
   const int w = net.widths[l + 1];
   const long long row = ci.row0 + (long long)(p - ci.p0) * ci.S;
   const float* ub = u + net.b_off[l];
-  float acc = 0.f;
+  double acc = 0.0;   // FP32 products are exact in FP64
   if (l == 0) {
     const float* U0 = u + net.w_off[0];
     const int din = net.d_in;
     for (int a = lane; a < w; a += 32) {
-      float yv = ub[a];
-      for (int k = 0; k < din; ++k) yv += U0[(long long)a * din + k] * (float)X[(long long)p * din + k];
-      acc += Dl[row * w + a] * yv;
-      for (int j = 0; j < ci.nD; ++j) acc += Dl[(row + 1 + j) * w + a] * U0[(long long)a * din + ci.D[j]];
+      double yv = ub[a];
+      for (int k = 0; k < din; ++k) yv += (double)U0[(long long)a * din + k] * X[(long long)p * din + k];
+      acc += (double)Dl[row * w + a] * yv;
+      for (int j = 0; j < ci.nD; ++j) acc += (double)Dl[(row + 1 + j) * w + a] * (double)U0[(long long)a * din + ci.D[j]];
     }
   } else {
     for (int s = 0; s < ci.S; ++s)
       for (int a = lane; a < w; a += 32)
-        acc += Dl[(row + s) * w + a] * (Y[(row + s) * w + a] + (s == 0 ? ub[a] : 0.f));
+        acc += (double)Dl[(row + s) * w + a] * ((double)Y[(row + s) * w + a] + (s == 0 ? (double)ub[a] : 0.0));
   }
-  const double t = warp_sum((double)acc);
+  const double t = warp_sum(acc);
   if (lane == 0) y[p] = accumulate ? y[p] + t : t;
 }
 
@@ -310,8 +309,8 @@ dngd_status mf_jtv(const MatFree& F, const double* v, float* g, cudaStream_t st)
   k_expand_rows<<<cdiv(net.m, 256), 256, 0, st>>>(net, v, F.vrow);
   for (int l = 1; l < L; ++l) {
     const int wo = net.widths[l + 1], wi = net.widths[l];
-    dngd_status s = gemm_tn<float>(wo, wi, net.R, 1.0f, F.D.p[l], wo, F.H.p[l - 1], wi, 0.0f, g + net.w_off[l], wi,
-                                   F.vrow, st);
+    dngd_status s = gemm_tn_comp(wo, wi, net.R, 1.0f, F.D.p[l], wo, F.H.p[l - 1], wi, 0.0f, g + net.w_off[l], wi,
+                                 F.vrow, st);
     if (s) return s;
   }
   if (L >= 1) {
@@ -333,8 +332,7 @@ dngd_status mf_jv(const MatFree& F, const float* u, double* y, cudaStream_t st) 
   for (int l = 0; l < L; ++l) {
     const int wo = net.widths[l + 1], wi = net.widths[l];
     if (l > 0) {
-      dngd_status s = gemm_nt<float>(net.R, wo, wi, 1.0f, F.H.p[l - 1], wi, u + net.w_off[l], wi, 0.0f, F.Y, wo,
-                                     false, st);
+      dngd_status s = gemm_nt_comp(net.R, wo, wi, 1.0f, F.H.p[l - 1], wi, u + net.w_off[l], wi, 0.0f, F.Y, wo, st);
       if (s) return s;
     }
     DNGD_NOTE_LAUNCH();
