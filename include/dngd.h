@@ -243,6 +243,50 @@ dngd_status dngd_kvp(dngd_ctx* ctx, const double* v, double* w_out);
  * through the Woodbury identity.  x [m] -> z_out [m].  PCG contexts only. */
 dngd_status dngd_precond_apply(dngd_ctx* ctx, const double* x, double* z_out);
 
+/* ---- asynchronous stepping and batches of independent instances --------
+ * A dense context can step without any host synchronisation: the step reads
+ * its inputs from the context's own staging buffers, runs the refinement for
+ * a fixed budget of refine_max_it iterations (each kernel of an iteration is a
+ * no-op once the device-side convergence flag is set, so results equal the
+ * synchronous step's) and factors the low-precision Gram once with the shift
+ * of the previous synchronous step.  That step is captured once into a CUDA
+ * graph and replayed (re-captured when lambda changes).  The first
+ * asynchronous step of a context, and any step after a failed factorisation,
+ * runs synchronously to choose the shift. */
+
+/* Enqueue one step on the context's stream (inputs are copied first; pointers
+ * may be host or device; delta_out is written when the stream reaches it).
+ * Dense solver only. */
+dngd_status dngd_step_async(dngd_ctx* ctx, const double* theta, const double* X, const double* target,
+                            double* delta_out);
+
+/* Wait for the last dngd_step_async and fill info (may be NULL).  Returns the
+ * step's device status (NOT_SPD means: call again, the next step re-searches
+ * the shift). */
+dngd_status dngd_step_wait(dngd_ctx* ctx, dngd_step_info* info);
+
+/* A batch of independent D-NGD instances of different shapes (e.g. many
+ * small PINNs of uneven m and n).  Every instance has its own context and
+ * stream; one batch step is ONE CUDA-graph launch that forks to all instance
+ * streams (each runs its asynchronous step) and joins.  Instances never
+ * share work, so each result equals the instance stepped alone. */
+typedef struct dngd_batch dngd_batch;
+
+/* descs [count] (dense solver); stream: master stream or NULL (own stream). */
+dngd_status dngd_batch_create(dngd_batch** out, const dngd_problem_desc* descs, int count, void* stream);
+dngd_status dngd_batch_destroy(dngd_batch* batch);
+int dngd_batch_size(const dngd_batch* batch);
+
+/* One step of every instance: arrays of count pointers (host or device), the
+ * same conventions as dngd_step.  infos [count] or NULL.  Synchronises the
+ * master stream; returns the first failing instance's status.  The first call
+ * steps each instance synchronously; later calls launch the batch graph. */
+dngd_status dngd_batch_step(dngd_batch* batch, const double* const* theta, const double* const* X,
+                            const double* const* target, double* const* delta_out, dngd_step_info* infos);
+
+/* The context of instance i (for dngd_get_stage, dngd_line_search, ...). */
+dngd_ctx* dngd_batch_context(dngd_batch* batch, int i);
+
 /* Gram matrix without any device allocation (the paper has no counterpart:
  * this is a library facility).  K = J J^T + shift I for a BF16 matrix J on the
  * tcgen05 tensor cores, the same kernels as the step's Gram.

@@ -78,6 +78,14 @@ struct dngd_ctx {
   cudaEvent_t ev[9] = {};
   cudaEvent_t kev[4] = {};  // first J^T p / J u launches of the first solve
 
+  // asynchronous (graph-capturable) stepping
+  bool async = false;        // current step enqueues without host synchronisation
+  bool async_ok = false;     // a synchronous step has fixed the shift: async allowed
+  cudaGraphExec_t graph = nullptr;
+  double graph_lambda = 0.0;
+  cudaStream_t gst = nullptr;        // private stream for capture / replay
+  cudaEvent_t gev[2] = {};           // fences between st and gst
+
   // matrix-free Nystrom-PCG solver (solver == DNGD_PCG)
   bool pcg = false;
   MatFree mf{};
@@ -286,7 +294,7 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
   P.ev = (c->timing && slot == 0) ? c->kev : nullptr;
   const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
   const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
-  return pcg_mixed_solve(P, b, x, tol, maxit, 4, &c->iters[slot], &c->relres[slot], c->st);
+  return pcg_mixed_solve(P, b, x, tol, maxit, 4, &c->iters[slot], &c->relres[slot], c->st, c->async, slot);
 }
 
 dngd_status pcg_matfree(dngd_ctx* c, const double* b, double* x, int slot);
@@ -332,6 +340,18 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     // factorisation is retried with a larger shift mu (it only preconditions
     // the refinement, whose operator keeps the exact lambda)
     double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
+    if (c->async) {
+      // no host round trip: one factorisation with the shift of the last
+      // synchronous step; a failure is reported by the status word
+      gram_tc_set_shift(c->gram, c->lambda + mu);
+      if ((s = gram_tc_run(c->gram, c->status, c->st, nullptr))) return s;
+      DNGD_CUDA_CHECK(cudaMemsetAsync(c->Linv, 0, sizeof(float) * (size_t)m * c->ldk, c->st));
+      if ((s = cholesky_f32_inv(m, (float*)c->K, c->ldk, c->Linv, c->ldk, c->status, c->st))) return s;
+      if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
+      c->shift_used = mu;
+      c->factor_attempts = 1;
+      goto factored;
+    }
     gram_tc_set_shift(c->gram, c->lambda + mu);
     if ((s = gram_tc_run(c->gram, c->status, c->st, c->timing ? c->ev[8] : nullptr))) return s;
     // K0 = K + (lambda + mu0) I is kept, so a failed factorisation is retried
@@ -369,8 +389,9 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     c->shift_used = mu;
     if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
   }
-  // a failed factorisation stops the step here
-  if ((s = read_status(c))) return s;
+  // a failed factorisation stops the (synchronous) step here
+  if (!c->async && (s = read_status(c))) return s;
+factored:
   evrec(c, 3);
   // alpha = (K + lambda I)^{-1} r ; v = -J^T alpha
   if ((s = solve_last(c, c->r, c->alpha, 0))) return s;
@@ -653,10 +674,39 @@ dngd_status alloc_pcg(dngd_ctx* c, bool dry, size_t* bytes_out) {
   return upload_landmarks(c);
 }
 
+dngd_status status_from_host(const int* h) {
+  const int s = h[0];
+  if (s & ST_TIMEOUT) return DNGD_ERR_TIMEOUT;
+  if (s & ST_NOT_SPD) return DNGD_ERR_NOT_SPD;
+  if (s & ST_NONFINITE) return DNGD_ERR_NONFINITE;
+  if (s & ST_NO_CONVERGE) return DNGD_ERR_NO_CONVERGE;
+  return DNGD_OK;
+}
+
+void info_from_host(dngd_ctx* c, dngd_step_info* info);
+
+// Fill info after an asynchronous step whose graph copied scal/status to the
+// pinned host buffers (the stream must have been synchronised).
+dngd_status finish_async(dngd_ctx* c, dngd_step_info* info) {
+  const double* h = c->scal_h;
+  for (int k = 0; k < 2; ++k) {
+    const int rec = k == 0 ? S_IT0 : S_IT1;
+    c->iters[k] = (int)h[rec];
+    c->relres[k] = h[rec + 2] > 0 ? sqrt(h[rec + 1] / h[rec + 2]) : 0.0;
+  }
+  if (info) info_from_host(c, info);
+  return status_from_host(c->status_h);
+}
+
 dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
   DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
   dngd_status s = read_status(c);
   if (!info) return s;
+  info_from_host(c, info);
+  return s;
+}
+
+void info_from_host(dngd_ctx* c, dngd_step_info* info) {
   memset(info, 0, sizeof(*info));
   info->loss = 0.5 * c->scal_h[S_LOSS];
   info->norm_v = sqrt(c->scal_h[S_NV2]);
@@ -692,7 +742,6 @@ dngd_status fill_info(dngd_ctx* c, dngd_step_info* info) {
     }
     cudaGetLastError();  // an unrecorded event only leaves a timing field at 0
   }
-  return s;
 }
 
 dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
@@ -837,6 +886,10 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
 }
 
 void free_ctx(dngd_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->gst) cudaStreamDestroy(c->gst);
+  for (int i = 0; i < 2; ++i)
+    if (c->gev[i]) cudaEventDestroy(c->gev[i]);
   for (void* p : c->allocs) cudaFree(p);
   if (c->scal_h) cudaFreeHost(c->scal_h);
   if (c->status_h) cudaFreeHost(c->status_h);
@@ -1154,6 +1207,244 @@ dngd_status dngd_precond_apply(dngd_ctx* c, const double* x, double* z_out) {
   dngd_status s = mf_precond(c->mf, c->lambda, xx, c->xsol, c->st);
   if (s) return s;
   return out_copy(c, z_out, c->xsol, c->m);
+}
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Asynchronous, graph-captured stepping and batches of independent instances
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Enqueue one asynchronous step of a dense context on its stream, reading the
+// staging inputs and ending with copies of the status word and scalars to the
+// pinned host buffers.  No host synchronisation: capturable.
+dngd_status enqueue_async(dngd_ctx* c) {
+  c->async = true;
+  const bool timing = c->timing;
+  c->timing = false;
+  dngd_status s = c->prec == DNGD_FP64 ? step_T<double>(c, c->theta_s, c->X_s, c->target_s, nullptr)
+                                       : step_T<float>(c, c->theta_s, c->X_s, c->target_s, nullptr);
+  c->timing = timing;
+  c->async = false;
+  if (s) return s;
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->status_h, c->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  return DNGD_OK;
+}
+
+dngd_status stage_inputs(dngd_ctx* c, const double* theta, const double* X, const double* target,
+                         cudaStream_t st) {
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->theta_s, theta, sizeof(double) * c->n, cudaMemcpyDefault, st));
+  DNGD_CUDA_CHECK(
+      cudaMemcpyAsync(c->X_s, X, sizeof(double) * (size_t)c->m * c->net.d_in, cudaMemcpyDefault, st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->target_s, target, sizeof(double) * c->m, cudaMemcpyDefault, st));
+  return DNGD_OK;
+}
+
+}  // namespace
+
+struct dngd_batch {
+  std::vector<dngd_ctx*> ctx;
+  std::vector<cudaEvent_t> join;
+  cudaStream_t master = nullptr;
+  bool own_master = false;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool first = true;
+};
+
+extern "C" {
+
+dngd_status dngd_step_async(dngd_ctx* c, const double* theta, const double* X, const double* target,
+                            double* delta_out) {
+  if (!c || !theta || !X || !target || !delta_out) return DNGD_ERR_INVALID_ARG;
+  if (c->pcg) return DNGD_ERR_INVALID_ARG;
+  if (!c->async_ok) {
+    // the first step is synchronous: it fixes the preconditioner shift
+    dngd_status s = dngd_step(c, theta, X, target, delta_out, nullptr);
+    if (s) return s;
+    c->async_ok = true;
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->status_h, c->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    return DNGD_OK;
+  }
+  dngd_status s = stage_inputs(c, theta, X, target, c->st);
+  if (s) return s;
+  // the graph is captured and replayed on a private stream (the context's
+  // stream may be the legacy default stream, which cannot be captured);
+  // events keep it ordered with the context's stream
+  if (!c->gst) {
+    DNGD_CUDA_CHECK(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking));
+    DNGD_CUDA_CHECK(cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming));
+    DNGD_CUDA_CHECK(cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
+  }
+  cudaStream_t user = c->st;
+  if (!c->graph || c->graph_lambda != c->lambda) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    c->st = c->gst;
+    cudaError_t e = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      s = enqueue_async(c);
+      e = cudaStreamEndCapture(c->gst, &g);
+    }
+    c->st = user;
+    if (s) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    DNGD_CUDA_CHECK(e);
+    DNGD_CUDA_CHECK(cudaGraphInstantiate(&c->graph, g, 0));
+    cudaGraphDestroy(g);
+    c->graph_lambda = c->lambda;
+  }
+  DNGD_CUDA_CHECK(cudaEventRecord(c->gev[0], user));
+  DNGD_CUDA_CHECK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
+  DNGD_CUDA_CHECK(cudaGraphLaunch(c->graph, c->gst));
+  DNGD_CUDA_CHECK(cudaEventRecord(c->gev[1], c->gst));
+  DNGD_CUDA_CHECK(cudaStreamWaitEvent(user, c->gev[1], 0));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(delta_out, c->delta, sizeof(double) * c->n, cudaMemcpyDefault, user));
+  c->have_step = true;
+  return DNGD_OK;
+}
+
+dngd_status dngd_step_wait(dngd_ctx* c, dngd_step_info* info) {
+  if (!c) return DNGD_ERR_INVALID_ARG;
+  DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+  dngd_status s = finish_async(c, info);
+  if (s == DNGD_ERR_NOT_SPD) c->async_ok = false;  // next step re-runs the shift search
+  return s;
+}
+
+dngd_status dngd_batch_create(dngd_batch** out, const dngd_problem_desc* descs, int count, void* stream) {
+  if (!out || !descs || count < 1) return DNGD_ERR_INVALID_ARG;
+  *out = nullptr;
+  dngd_batch* b = new dngd_batch();
+  for (int i = 0; i < count; ++i) {
+    if (descs[i].solver != DNGD_DENSE) {
+      dngd_batch_destroy(b);
+      return DNGD_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      dngd_batch_destroy(b);
+      return DNGD_ERR_CUDA;
+    }
+    dngd_ctx* c = nullptr;
+    dngd_status s = dngd_create(&c, &descs[i], st);
+    if (s) {
+      cudaStreamDestroy(st);
+      dngd_batch_destroy(b);
+      return s;
+    }
+    b->ctx.push_back(c);
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    b->join.push_back(ev);
+  }
+  if (stream) {
+    b->master = (cudaStream_t)stream;
+  } else {
+    cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking);
+    b->own_master = true;
+  }
+  cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  *out = b;
+  return DNGD_OK;
+}
+
+dngd_status dngd_batch_destroy(dngd_batch* b) {
+  if (!b) return DNGD_ERR_INVALID_ARG;
+  if (b->master) cudaStreamSynchronize(b->master);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    cudaStream_t st = b->ctx[i]->st;
+    dngd_destroy(b->ctx[i]);
+    cudaStreamDestroy(st);
+    cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->own_master) cudaStreamDestroy(b->master);
+  delete b;
+  return DNGD_OK;
+}
+
+int dngd_batch_size(const dngd_batch* b) { return b ? (int)b->ctx.size() : 0; }
+
+dngd_status dngd_batch_step(dngd_batch* b, const double* const* theta, const double* const* X,
+                            const double* const* target, double* const* delta_out, dngd_step_info* infos) {
+  if (!b || !theta || !X || !target || !delta_out) return DNGD_ERR_INVALID_ARG;
+  const int nb = (int)b->ctx.size();
+  dngd_status worst = DNGD_OK;
+  if (b->first) {
+    // synchronous first step per instance (fixes each preconditioner shift)
+    for (int i = 0; i < nb; ++i) {
+      dngd_status s = dngd_step(b->ctx[i], theta[i], X[i], target[i], delta_out[i], infos ? &infos[i] : nullptr);
+      if (s && !worst) worst = s;
+      b->ctx[i]->async_ok = (s == DNGD_OK);
+    }
+    b->first = false;
+    return worst;
+  }
+  for (int i = 0; i < nb; ++i) {
+    dngd_status s = stage_inputs(b->ctx[i], theta[i], X[i], target[i], b->master);
+    if (s) return s;
+  }
+  if (!b->exec) {
+    // one graph: fork to every instance stream, one asynchronous step each, join
+    cudaGraph_t g = nullptr;
+    DNGD_CUDA_CHECK(cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal));
+    dngd_status s = DNGD_OK;
+    if (cudaEventRecord(b->fork, b->master) != cudaSuccess) s = DNGD_ERR_CUDA;
+    for (int i = 0; i < nb && !s; ++i) {
+      dngd_ctx* c = b->ctx[i];
+      if (cudaStreamWaitEvent(c->st, b->fork, 0) != cudaSuccess) s = DNGD_ERR_CUDA;
+      if (!s) s = enqueue_async(c);
+      if (!s && cudaEventRecord(b->join[i], c->st) != cudaSuccess) s = DNGD_ERR_CUDA;
+      if (!s && cudaStreamWaitEvent(b->master, b->join[i], 0) != cudaSuccess) s = DNGD_ERR_CUDA;
+    }
+    const cudaError_t e = cudaStreamEndCapture(b->master, &g);
+    if (s || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return s ? s : DNGD_ERR_CUDA;
+    }
+    DNGD_CUDA_CHECK(cudaGraphInstantiate(&b->exec, g, 0));
+    cudaGraphDestroy(g);
+  }
+  DNGD_CUDA_CHECK(cudaGraphLaunch(b->exec, b->master));
+  for (int i = 0; i < nb; ++i)
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(delta_out[i], b->ctx[i]->delta, sizeof(double) * b->ctx[i]->n,
+                                    cudaMemcpyDefault, b->master));
+  DNGD_CUDA_CHECK(cudaStreamSynchronize(b->master));
+  bool recapture = false;
+  for (int i = 0; i < nb; ++i) {
+    dngd_ctx* c = b->ctx[i];
+    c->have_step = true;
+    dngd_status s = finish_async(c, infos ? &infos[i] : nullptr);
+    if (s == DNGD_ERR_NOT_SPD) {
+      // redo this instance synchronously (the shift search raises mu) and
+      // rebuild the batch graph with the new shift
+      s = dngd_step(c, theta[i], X[i], target[i], delta_out[i], infos ? &infos[i] : nullptr);
+      recapture = true;
+    }
+    if (s && !worst) worst = s;
+  }
+  if (recapture && b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return worst;
+}
+
+dngd_ctx* dngd_batch_context(dngd_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->ctx.size()) return nullptr;
+  return b->ctx[i];
 }
 
 }  // extern "C"

@@ -109,8 +109,11 @@ struct PcgMixed {
   cudaEvent_t* ev;                    // optional: 4 events bracketing the first
                                       // J^T p and J u launches of the solve
 };
+// async: enqueue exactly maxit iterations (kernels become no-ops after
+// convergence) and never synchronise; iters/relres are then left untouched and
+// the per-solve record (S_IT*, S_RR*, S_BB*) holds the result.
 dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, double tol, int maxit, int check_every,
-                            int* iters, double* relres, cudaStream_t st);
+                            int* iters, double* relres, cudaStream_t st, bool async = false, int slot = 0);
 
 // K[i,i] += shift for i < m.
 template <typename T>

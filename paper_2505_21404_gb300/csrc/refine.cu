@@ -322,7 +322,7 @@ dngd_status gemv_n_f32(int m, int n, const float* A, long long lda, const double
 }
 
 dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, double tol, int maxit, int check_every,
-                            int* iters, double* relres, cudaStream_t st) {
+                            int* iters, double* relres, cudaStream_t st, bool async, int slot) {
   const int m = P.m;
   double* sc = P.scal;
   double* part_a = P.dotp;          // kVecBlocks partials
@@ -370,10 +370,20 @@ dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, doubl
       k_cg_update_p<<<cdiv(m, 256), 256, 0, st>>>(m, sc, P.z, P.p);
       DNGD_LAUNCH_CHECK();
     }
+    if (async) {
+      if (it >= maxit) break;
+      continue;
+    }
     DNGD_CUDA_CHECK(cudaMemcpyAsync(P.scal_h, sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
     DNGD_CUDA_CHECK(cudaStreamSynchronize(st));
     if (P.scal_h[S_DONE] != 0.0 || it >= maxit) break;
   }
+  // per-solve record: iterations, ||res||^2, ||b||^2
+  const int rec = slot == 0 ? S_IT0 : S_IT1;
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(sc + rec, sc + S_ITERS, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(sc + rec + 1, sc + S_RR, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(sc + rec + 2, sc + S_BB, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (async) return DNGD_OK;
   const double bb = P.scal_h[S_BB];
   *iters = (int)P.scal_h[S_ITERS];
   *relres = bb > 0 ? sqrt(P.scal_h[S_RR] / bb) : 0.0;

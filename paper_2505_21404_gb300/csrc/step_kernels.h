@@ -10,7 +10,8 @@ enum : int {
   S_NV2 = 0, S_NA2, S_RATIO, S_ACCEPT,
   S_RHO, S_RHONEW, S_PAP, S_ALPHA, S_BETA, S_BREAK, S_RR, S_BB, S_LOSS, S_TRACE,
   S_DONE, S_ITERS, S_TOL2,
-  S_COUNT = 20
+  S_IT0, S_RR0, S_BB0, S_IT1, S_RR1, S_BB1,
+  S_COUNT = 26
 };
 
 dngd_status to_float(long long n, const double* x, float* y, cudaStream_t st);

@@ -91,6 +91,14 @@ def _load():
         "dngd_get_stage": (C.c_int, [P, C.c_int, P]),
         "dngd_gram_bf16_noalloc": (C.c_int, [P, C.c_int, C.c_int, C.c_longlong, P, C.c_longlong, C.c_double, P]),
         "dngd_set_landmarks": (C.c_int, [P, P, C.c_int]),
+        "dngd_step_async": (C.c_int, [P, P, P, P, P]),
+        "dngd_step_wait": (C.c_int, [P, C.POINTER(StepInfo)]),
+        "dngd_batch_create": (C.c_int, [C.POINTER(P), C.POINTER(ProblemDesc), C.c_int, P]),
+        "dngd_batch_destroy": (C.c_int, [P]),
+        "dngd_batch_size": (C.c_int, [P]),
+        "dngd_batch_step": (C.c_int, [P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(P),
+                                      C.POINTER(StepInfo)]),
+        "dngd_batch_context": (P, [P, C.c_int]),
         "dngd_kvp": (C.c_int, [P, P, P]),
         "dngd_precond_apply": (C.c_int, [P, P, P]),
     }
@@ -106,7 +114,9 @@ lib = _load()
 EXPORTED = ["dngd_status_string", "dngd_version", "dngd_launch_count", "dngd_num_params", "dngd_create", "dngd_workspace_bytes",
             "dngd_destroy", "dngd_set_timing", "dngd_set_lambda", "dngd_step", "dngd_solve", "dngd_loss",
             "dngd_line_search", "dngd_residual_jacobian", "dngd_fvv", "dngd_get_stage",
-            "dngd_gram_bf16_noalloc", "dngd_set_landmarks", "dngd_kvp", "dngd_precond_apply"]
+            "dngd_gram_bf16_noalloc", "dngd_set_landmarks", "dngd_kvp", "dngd_precond_apply",
+            "dngd_step_async", "dngd_step_wait", "dngd_batch_create", "dngd_batch_destroy", "dngd_batch_size",
+            "dngd_batch_step", "dngd_batch_context"]
 
 
 def _check(status, where):
@@ -252,5 +262,63 @@ class Context:
     def precond_apply(self, x, out):
         _check(lib.dngd_precond_apply(self._h, _ptr(x), _ptr(out)), "dngd_precond_apply")
 
+    def step_async(self, theta, X, target, delta_out):
+        _check(lib.dngd_step_async(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(delta_out)),
+               "dngd_step_async")
+
+    def step_wait(self):
+        info = StepInfo()
+        _check(lib.dngd_step_wait(self._h, C.byref(info)), "dngd_step_wait")
+        return info.as_dict()
+
     def get_stage(self, name, out):
         _check(lib.dngd_get_stage(self._h, STAGES[name], _ptr(out)), "dngd_get_stage")
+
+
+class _Borrowed(Context):
+    """A context owned by a batch (not destroyed by Python)."""
+
+    def __init__(self, handle, desc):
+        self.desc = desc
+        self._h = C.c_void_p(handle)
+        self.n = dngd_num_params(desc)
+        self.m = sum(desc.classes[c].count for c in range(desc.n_classes))
+
+    def close(self):
+        self._h = C.c_void_p()
+
+
+class Batch:
+    """dngd_batch: independent instances stepped by one CUDA-graph launch."""
+
+    def __init__(self, descs, stream=None):
+        self.descs = list(descs)
+        arr = (ProblemDesc * len(self.descs))(*self.descs)
+        self._h = C.c_void_p()
+        s = C.c_void_p(int(stream)) if stream else None
+        _check(lib.dngd_batch_create(C.byref(self._h), arr, len(self.descs), s), "dngd_batch_create")
+
+    def __len__(self):
+        return int(lib.dngd_batch_size(self._h))
+
+    def close(self):
+        if self._h:
+            lib.dngd_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def context(self, i):
+        return _Borrowed(lib.dngd_batch_context(self._h, int(i)), self.descs[i])
+
+    def step(self, thetas, Xs, targets, deltas):
+        n = len(self.descs)
+        P = C.c_void_p
+        arrs = [(P * n)(*[_ptr(a) for a in lst]) for lst in (thetas, Xs, targets, deltas)]
+        infos = (StepInfo * n)()
+        _check(lib.dngd_batch_step(self._h, arrs[0], arrs[1], arrs[2], arrs[3], infos), "dngd_batch_step")
+        return [i.as_dict() for i in infos]

@@ -1,0 +1,93 @@
+"""Asynchronous (graph-captured) steps and batches of independent instances.
+
+Each instance of a batch must give the same result as the instance stepped
+alone: the batch only overlaps independent work on the device, it never
+changes what an instance computes (no batch-dependent split or reduction
+order)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import residual as ores, step as ostep  # noqa: E402
+from paper_2505_21404_gb300 import workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def dngd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2505_21404_gb300 import dngd as mod
+    return mod
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _instances():
+    out = []
+    for b, (w, m, k) in enumerate([(32, 256, 1), (64, 400, 3), (128, 300, 5), (32, 700, 8), (64, 260, 2),
+                                   (128, 520, 4)]):
+        nb = round(0.2 * m)
+        out.append(workloads.poisson_sine(2, [2, w, w, 1], m - nb, nb, k=k, seed=1000 + b, lam=1e-5))
+    return out
+
+
+def test_async_step_equals_sync_step(dngd):
+    wl = _instances()[1]
+    desc = dngd.make_desc(wl, precision=dngd.MIXED_BF16, refine_tol=1e-8, refine_max_it=120)
+    a = dngd.Context(desc)
+    b = dngd.Context(desc)
+    th, X, tg = _t(wl["theta"]), _t(wl["X"]), _t(wl["target"])
+    da = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    db = torch.zeros(b.n, dtype=torch.float64, device=DEV)
+    for _ in range(3):
+        ia = a.step(th, X, tg, da)
+        b.step_async(th, X, tg, db)
+        ib = b.step_wait()
+        torch.cuda.synchronize()
+        assert torch.equal(da, db)
+        assert ia["solve_iters"] == ib["solve_iters"]
+
+
+def test_batch_equals_each_instance_alone(dngd):
+    wls = _instances()
+    descs = [dngd.make_desc(wl, precision=dngd.MIXED_BF16, refine_tol=1e-8, refine_max_it=120) for wl in wls]
+    batch = dngd.Batch(descs)
+    alone = [dngd.Context(d) for d in descs]
+    ths = [_t(wl["theta"]) for wl in wls]
+    Xs = [_t(wl["X"]) for wl in wls]
+    tgs = [_t(wl["target"]) for wl in wls]
+    db = [torch.zeros(c.n, dtype=torch.float64, device=DEV) for c in alone]
+    da = [torch.zeros(c.n, dtype=torch.float64, device=DEV) for c in alone]
+    for it in range(3):
+        infos = batch.step(ths, Xs, tgs, db)
+        for i, c in enumerate(alone):
+            info = c.step(ths[i], Xs[i], tgs[i], da[i])
+            assert info["solve_iters"] == infos[i]["solve_iters"], (it, i)
+        torch.cuda.synchronize()
+        for i in range(len(wls)):
+            assert torch.equal(da[i], db[i]), (it, i)
+
+
+def test_batch_instance_matches_oracle(dngd):
+    wls = _instances()[:3]
+    descs = [dngd.make_desc(wl, precision=dngd.MIXED_BF16, refine_tol=1e-10, refine_max_it=200) for wl in wls]
+    batch = dngd.Batch(descs)
+    ths = [_t(wl["theta"]) for wl in wls]
+    Xs = [_t(wl["X"]) for wl in wls]
+    tgs = [_t(wl["target"]) for wl in wls]
+    ds = [torch.zeros(len(wl["theta"]), dtype=torch.float64, device=DEV) for wl in wls]
+    for _ in range(2):      # second call runs the captured graph
+        batch.step(ths, Xs, tgs, ds)
+    torch.cuda.synchronize()
+    for wl, d in zip(wls, ds):
+        ref = ostep.dense_step(wl["theta"], ores.problem_from_spec(wl), wl["X"], wl["target"], wl["lam"])
+        err = float(np.linalg.norm(d.cpu().numpy() - ref["delta"]) / np.linalg.norm(ref["delta"]))
+        assert err <= 1e-4, err
