@@ -206,6 +206,13 @@ dngd_status dngd_line_search(dngd_ctx* ctx, const double* theta, const double* X
                              const double* delta, const double* etas, int k, double* theta_out,
                              double* eta_out);
 
+/* The same line search without synchronising: the k losses, the argmin and
+ * theta += eta* delta all stay on the device (theta, X, target, delta must be
+ * device pointers; theta is updated in place; etas is a host array, k <= 64,
+ * copied before the call returns).  The losses are 2x the loss (||r||^2). */
+dngd_status dngd_line_search_async(dngd_ctx* ctx, double* theta, const double* X, const double* target,
+                                   const double* delta, const double* etas, int k);
+
 /* Residuals and Jacobian at theta (Sec. 2.2) through the step's own kernels
  * and precision.  r_out [m] float64; J_out [m x n] row-major float64 or NULL. */
 dngd_status dngd_residual_jacobian(dngd_ctx* ctx, const double* theta, const double* X,
@@ -286,6 +293,62 @@ dngd_status dngd_batch_step(dngd_batch* batch, const double* const* theta, const
 
 /* The context of instance i (for dngd_get_stage, dngd_line_search, ...). */
 dngd_ctx* dngd_batch_context(dngd_batch* batch, int i);
+
+/* ---- serving: a request loop over PINN solve jobs ------------------------
+ * A job is one PINN solve: a problem, initial parameters, collocation data
+ * and a number of D-NGD iterations (step + 31-point line search + update).
+ * Jobs are admitted first come, first served when a slot is free and their
+ * device footprint fits in what is left of the HBM budget (a job that can
+ * never fit is rejected with DNGD_ERR_BUDGET).  Admitted jobs keep their
+ * state on the device and always have their next iteration in flight on their
+ * own stream, so iterations of different jobs overlap on the GPU (continuous
+ * batching); a finished job releases its memory and slot at once.  A failing
+ * job is marked FAILED without affecting others.  One worker thread owns all
+ * device work of the server; submit / poll / cancel / stats are thread-safe. */
+typedef struct dngd_server dngd_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;  /* 0: 80% of the free device memory at creation */
+  int max_slots;            /* jobs running at once (>= 1) */
+  int line_search_points;   /* grid eta_j = 2^-j, j < points (0: 31) */
+} dngd_server_cfg;
+
+typedef struct {
+  dngd_problem_desc desc;   /* dense solver */
+  const double* theta0;     /* [n] host or device; copied at submit */
+  const double* X;          /* [m x d] host or device; copied at submit */
+  const double* target;     /* [m] host or device; copied at submit */
+  int n_steps;              /* D-NGD iterations to run */
+} dngd_job_desc;
+
+enum dngd_job_states { DNGD_JOB_QUEUED = 0, DNGD_JOB_RUNNING = 1, DNGD_JOB_DONE = 2, DNGD_JOB_FAILED = 3,
+                       DNGD_JOB_CANCELLED = 4 };
+
+typedef struct {
+  int state;                /* enum dngd_job_states */
+  int steps_done;
+  dngd_status status;       /* failure reason (FAILED) */
+  double loss;              /* 1/2 ||r||^2 at the start of the last step */
+  double queue_s, run_s;    /* time queued / running so far */
+} dngd_job_state;
+
+typedef struct {
+  double steps_per_s;       /* completed iterations / time since the first submit */
+  double p50_ms, p99_ms;    /* per-iteration latency on the device (step + line search) */
+  long long steps_total;
+  int admitted, rejected, done, failed, running, queued;
+  size_t hbm_used_bytes, hbm_budget_bytes;
+} dngd_serving_stats;
+
+dngd_status dngd_server_create(dngd_server** out, const dngd_server_cfg* cfg);
+dngd_status dngd_server_destroy(dngd_server* server);   /* cancels running jobs */
+dngd_status dngd_submit(dngd_server* server, const dngd_job_desc* job, uint64_t* job_id);
+/* theta_out [n] (host or device, may be NULL) is filled once the job is DONE. */
+dngd_status dngd_poll(dngd_server* server, uint64_t job_id, dngd_job_state* state, double* theta_out);
+dngd_status dngd_cancel(dngd_server* server, uint64_t job_id);
+dngd_status dngd_server_stats(dngd_server* server, dngd_serving_stats* stats);
+/* Block until no job is queued or running (TIMEOUT after timeout_s). */
+dngd_status dngd_server_drain(dngd_server* server, double timeout_s);
 
 /* Gram matrix without any device allocation (the paper has no counterpart:
  * this is a library facility).  K = J J^T + shift I for a BF16 matrix J on the

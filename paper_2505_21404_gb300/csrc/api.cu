@@ -83,7 +83,12 @@ struct dngd_ctx {
   bool async_ok = false;     // a synchronous step has fixed the shift: async allowed
   cudaGraphExec_t graph = nullptr;
   double graph_lambda = 0.0;
+  double* ls_dev = nullptr;          // line search: etas [64], losses [64], result [2]
+  double* ls_host = nullptr;         // pinned copy of the etas
+  int ls_k = 0;
+  double graph_mu = 0.0;
   cudaStream_t gst = nullptr;        // private stream for capture / replay
+  unsigned long long graph_kernels = 0;  // kernel launches captured in the graph
   cudaEvent_t gev[2] = {};           // fences between st and gst
 
   // matrix-free Nystrom-PCG solver (solver == DNGD_PCG)
@@ -886,6 +891,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
 }
 
 void free_ctx(dngd_ctx* c) {
+  if (c->ls_host) cudaFreeHost(c->ls_host);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->gst) cudaStreamDestroy(c->gst);
   for (int i = 0; i < 2; ++i)
@@ -1132,6 +1138,41 @@ dngd_status dngd_line_search(dngd_ctx* c, const double* theta, const double* X, 
   return out_copy(c, theta_out, c->theta_tmp, c->n);
 }
 
+dngd_status dngd_line_search_async(dngd_ctx* c, double* theta, const double* X, const double* target,
+                                   const double* delta, const double* etas, int k) {
+  if (!c || !theta || !X || !target || !delta || !etas || k < 1 || k > 64) return DNGD_ERR_INVALID_ARG;
+  if (!is_device_ptr(theta) || !is_device_ptr(X) || !is_device_ptr(target) || !is_device_ptr(delta))
+    return DNGD_ERR_INVALID_ARG;
+  if (!c->ls_dev) {
+    if (cudaMalloc(&c->ls_dev, sizeof(double) * 132) != cudaSuccess) return DNGD_ERR_OOM;
+    c->allocs.push_back(c->ls_dev);
+    DNGD_CUDA_CHECK(cudaMallocHost(&c->ls_host, sizeof(double) * 64));
+  }
+  // the device grid is reloaded only when it changes (then after the stream
+  // has consumed the previous pinned copy)
+  bool same = c->ls_k == k;
+  for (int j = 0; j < k && same; ++j) same = c->ls_host[j] == etas[j];
+  if (!same) {
+    DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+    for (int j = 0; j < k; ++j) c->ls_host[j] = etas[j];
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->ls_dev, c->ls_host, sizeof(double) * k, cudaMemcpyHostToDevice, c->st));
+    c->ls_k = k;
+  }
+  double* losses = c->ls_dev + 64;
+  // the step's status word, before the trial evaluations add their own flags
+  int* step_flags = (int*)(c->ls_dev + 130);
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(step_flags, c->status, sizeof(int), cudaMemcpyDeviceToDevice, c->st));
+  for (int j = 0; j < k; ++j) {
+    dngd_status s = axpy_to(c->n, theta, etas[j], delta, c->theta_tmp, c->st);
+    if (s) return s;
+    if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, X, target, c->cg_res);
+    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), X, target, c->cg_res);
+    if (s) return s;
+    if ((s = dot_dev(c->m, c->cg_res, c->cg_res, losses + j, c->dot_partials, c->st))) return s;
+  }
+  return ls_finish(c->n, k, losses, c->ls_dev, step_flags, c->ls_dev + 128, delta, theta, c->st);
+}
+
 dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
   if (!c || !dst) return DNGD_ERR_INVALID_ARG;
   if (!c->have_step) return DNGD_ERR_STATE;
@@ -1254,6 +1295,7 @@ struct dngd_batch {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool first = true;
+  unsigned long long graph_kernels = 0;
 };
 
 extern "C" {
@@ -1264,8 +1306,9 @@ dngd_status dngd_step_async(dngd_ctx* c, const double* theta, const double* X, c
   if (c->pcg) return DNGD_ERR_INVALID_ARG;
   if (!c->async_ok) {
     // the first step is synchronous: it fixes the preconditioner shift
+    // (a refinement that stopped at its iteration cap still gives a step)
     dngd_status s = dngd_step(c, theta, X, target, delta_out, nullptr);
-    if (s) return s;
+    if (s && s != DNGD_ERR_NO_CONVERGE) return s;
     c->async_ok = true;
     DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
     DNGD_CUDA_CHECK(cudaMemcpyAsync(c->status_h, c->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1282,7 +1325,10 @@ dngd_status dngd_step_async(dngd_ctx* c, const double* theta, const double* X, c
     DNGD_CUDA_CHECK(cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
   }
   cudaStream_t user = c->st;
-  if (!c->graph || c->graph_lambda != c->lambda) {
+  // the graph bakes in lambda and the preconditioner shift of the last
+  // synchronous step; either changing means a new capture
+  const double mu_now = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
+  if (!c->graph || c->graph_lambda != c->lambda || c->graph_mu != mu_now) {
     if (c->graph) {
       cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
@@ -1290,10 +1336,13 @@ dngd_status dngd_step_async(dngd_ctx* c, const double* theta, const double* X, c
     cudaGraph_t g = nullptr;
     c->st = c->gst;
     cudaError_t e = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal);
+    const unsigned long long k0 = dngd::g_launches.load();
     if (e == cudaSuccess) {
       s = enqueue_async(c);
       e = cudaStreamEndCapture(c->gst, &g);
     }
+    c->graph_kernels = dngd::g_launches.load() - k0;
+    dngd::g_launches.fetch_sub(c->graph_kernels);
     c->st = user;
     if (s) {
       if (g) cudaGraphDestroy(g);
@@ -1303,10 +1352,12 @@ dngd_status dngd_step_async(dngd_ctx* c, const double* theta, const double* X, c
     DNGD_CUDA_CHECK(cudaGraphInstantiate(&c->graph, g, 0));
     cudaGraphDestroy(g);
     c->graph_lambda = c->lambda;
+    c->graph_mu = mu_now;
   }
   DNGD_CUDA_CHECK(cudaEventRecord(c->gev[0], user));
   DNGD_CUDA_CHECK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
   DNGD_CUDA_CHECK(cudaGraphLaunch(c->graph, c->gst));
+  dngd::g_launches.fetch_add(c->graph_kernels);
   DNGD_CUDA_CHECK(cudaEventRecord(c->gev[1], c->gst));
   DNGD_CUDA_CHECK(cudaStreamWaitEvent(user, c->gev[1], 0));
   DNGD_CUDA_CHECK(cudaMemcpyAsync(delta_out, c->delta, sizeof(double) * c->n, cudaMemcpyDefault, user));
@@ -1400,6 +1451,7 @@ dngd_status dngd_batch_step(dngd_batch* b, const double* const* theta, const dou
     // one graph: fork to every instance stream, one asynchronous step each, join
     cudaGraph_t g = nullptr;
     DNGD_CUDA_CHECK(cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long k0 = dngd::g_launches.load();
     dngd_status s = DNGD_OK;
     if (cudaEventRecord(b->fork, b->master) != cudaSuccess) s = DNGD_ERR_CUDA;
     for (int i = 0; i < nb && !s; ++i) {
@@ -1410,6 +1462,8 @@ dngd_status dngd_batch_step(dngd_batch* b, const double* const* theta, const dou
       if (!s && cudaStreamWaitEvent(b->master, b->join[i], 0) != cudaSuccess) s = DNGD_ERR_CUDA;
     }
     const cudaError_t e = cudaStreamEndCapture(b->master, &g);
+    b->graph_kernels = dngd::g_launches.load() - k0;
+    dngd::g_launches.fetch_sub(b->graph_kernels);
     if (s || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return s ? s : DNGD_ERR_CUDA;
@@ -1418,6 +1472,7 @@ dngd_status dngd_batch_step(dngd_batch* b, const double* const* theta, const dou
     cudaGraphDestroy(g);
   }
   DNGD_CUDA_CHECK(cudaGraphLaunch(b->exec, b->master));
+  dngd::g_launches.fetch_add(b->graph_kernels);
   for (int i = 0; i < nb; ++i)
     DNGD_CUDA_CHECK(cudaMemcpyAsync(delta_out[i], b->ctx[i]->delta, sizeof(double) * b->ctx[i]->n,
                                     cudaMemcpyDefault, b->master));

@@ -357,7 +357,7 @@ struct GramPlan {
   double shift = 0.0;
 };
 
-static int choose_splits(int ntiles, int num_kblk, int nsm) {
+int choose_splits(int ntiles, int num_kblk, int nsm) {
   int best = 1;
   double best_eff = 0.0;
   for (int s = 1; s <= 8; ++s) {
@@ -374,9 +374,17 @@ static int choose_splits(int ntiles, int num_kblk, int nsm) {
 }
 
 size_t gram_tc_partial_bytes(int m, int n) {
-  const int mp = ((m + BM - 1) / BM) * BM;
-  (void)n;
-  return (size_t)8 * mp * mp * sizeof(float);
+  // the split count gram_tc_plan will choose for this shape (K blocks of 64)
+  const int nI = (m + BM - 1) / BM;
+  int ntiles = 0;
+  for (int I = 0; I < nI; ++I)
+    for (int Jc = 0; Jc * BN <= I * BM + BM - 1 && Jc * BN < m; ++Jc) ++ntiles;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsplit = choose_splits(ntiles, (n + 31) / 32, nsm);
+  const long long ldp = ((m + 3) / 4) * 4 + 4;
+  return (size_t)nsplit * nI * BM * ldp * sizeof(float);
 }
 
 dngd_status gram_tc_plan(GramPlan** out, int kind, const void* Jlow, int m, int n, long long ld, float* K,

@@ -221,4 +221,35 @@ dngd_status rows_to_f64(int m, long long n, const T* A, long long lda, double* o
 template dngd_status rows_to_f64<double>(int, long long, const double*, long long, double*, cudaStream_t);
 template dngd_status rows_to_f64<float>(int, long long, const float*, long long, double*, cudaStream_t);
 
+// Line search finish (Alg. D-NGD Workflow): eta* = the first minimiser of the
+// k losses (ties go to the earlier grid point), then theta += eta* delta.
+// First minimum of the trial losses over the grid (non-finite trials never
+// win).  A step whose status word reports a failed factorisation, a
+// non-finite value or a timeout is not applied (eta* = 0).
+__global__ void k_ls_argmin(int k, const double* __restrict__ losses, const double* __restrict__ etas,
+                            const int* __restrict__ step_flags, double* __restrict__ out) {
+  int best = -1;
+  for (int j = 0; j < k; ++j)
+    if (isfinite(losses[j]) && (best < 0 || losses[j] < losses[best])) best = j;
+  const bool ok = best >= 0 && (step_flags[0] & (ST_NOT_SPD | ST_NONFINITE | ST_TIMEOUT)) == 0;
+  out[0] = ok ? etas[best] : 0.0;
+  out[1] = ok ? losses[best] : nan("");
+}
+
+__global__ void k_ls_update(long long n, const double* __restrict__ eta, const double* __restrict__ delta,
+                            double* __restrict__ theta) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && eta[0] != 0.0) theta[i] += eta[0] * delta[i];
+}
+
+dngd_status ls_finish(long long n, int k, const double* losses, const double* etas, const int* step_flags,
+                      double* out, const double* delta, double* theta, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
+  k_ls_argmin<<<1, 1, 0, st>>>(k, losses, etas, step_flags, out);
+  DNGD_NOTE_LAUNCH();
+  k_ls_update<<<cdiv(n, 256), 256, 0, st>>>(n, out, delta, theta);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
 }  // namespace dngd

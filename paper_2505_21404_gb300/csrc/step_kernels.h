@@ -32,6 +32,11 @@ dngd_status lower_to_f64(int m, const T* A, long long lda, double* out, cudaStre
 template <typename T>
 dngd_status rows_to_f64(int m, long long n, const T* A, long long lda, double* out, cudaStream_t st);
 
+// theta += eta* delta with eta* the first minimiser of losses[0..k) (out[0] =
+// eta*, out[1] = its loss)
+dngd_status ls_finish(long long n, int k, const double* losses, const double* etas, const int* step_flags,
+                      double* out, const double* delta, double* theta, cudaStream_t st);
+
 dngd_status gram_tc_set_shift(struct GramPlan* p, double shift);
 int gram_tc_nsplit(const struct GramPlan* p);
 int gram_tc_ntiles(const struct GramPlan* p);

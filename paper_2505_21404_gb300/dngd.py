@@ -66,6 +66,32 @@ class StepInfo(C.Structure):
                     j_ms=self.j_ms)
 
 
+class ServerCfg(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("line_search_points", C.c_int)]
+
+
+class JobDesc(C.Structure):
+    _fields_ = [("desc", ProblemDesc), ("theta0", C.c_void_p), ("X", C.c_void_p), ("target", C.c_void_p),
+                ("n_steps", C.c_int)]
+
+
+class JobState(C.Structure):
+    _fields_ = [("state", C.c_int), ("steps_done", C.c_int), ("status", C.c_int), ("loss", C.c_double),
+                ("queue_s", C.c_double), ("run_s", C.c_double)]
+
+
+class ServingStats(C.Structure):
+    _fields_ = [("steps_per_s", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("steps_total", C.c_longlong), ("admitted", C.c_int), ("rejected", C.c_int), ("done", C.c_int),
+                ("failed", C.c_int), ("running", C.c_int), ("queued", C.c_int), ("hbm_used_bytes", C.c_size_t),
+                ("hbm_budget_bytes", C.c_size_t)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELLED = range(5)
+JOB_STATES = {JOB_QUEUED: "queued", JOB_RUNNING: "running", JOB_DONE: "done", JOB_FAILED: "failed",
+              JOB_CANCELLED: "cancelled"}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libdngd.so not built at {LIB_PATH}: run __graft_entry__.build() (no CPU fallback)")
@@ -101,6 +127,14 @@ def _load():
         "dngd_batch_context": (P, [P, C.c_int]),
         "dngd_kvp": (C.c_int, [P, P, P]),
         "dngd_precond_apply": (C.c_int, [P, P, P]),
+        "dngd_line_search_async": (C.c_int, [P, P, P, P, P, D, C.c_int]),
+        "dngd_server_create": (C.c_int, [C.POINTER(P), C.POINTER(ServerCfg)]),
+        "dngd_server_destroy": (C.c_int, [P]),
+        "dngd_submit": (C.c_int, [P, C.POINTER(JobDesc), C.POINTER(C.c_uint64)]),
+        "dngd_poll": (C.c_int, [P, C.c_uint64, C.POINTER(JobState), P]),
+        "dngd_cancel": (C.c_int, [P, C.c_uint64]),
+        "dngd_server_stats": (C.c_int, [P, C.POINTER(ServingStats)]),
+        "dngd_server_drain": (C.c_int, [P, C.c_double]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -116,7 +150,9 @@ EXPORTED = ["dngd_status_string", "dngd_version", "dngd_launch_count", "dngd_num
             "dngd_line_search", "dngd_residual_jacobian", "dngd_fvv", "dngd_get_stage",
             "dngd_gram_bf16_noalloc", "dngd_set_landmarks", "dngd_kvp", "dngd_precond_apply",
             "dngd_step_async", "dngd_step_wait", "dngd_batch_create", "dngd_batch_destroy", "dngd_batch_size",
-            "dngd_batch_step", "dngd_batch_context"]
+            "dngd_batch_step", "dngd_batch_context", "dngd_line_search_async", "dngd_server_create",
+            "dngd_server_destroy", "dngd_submit", "dngd_poll", "dngd_cancel", "dngd_server_stats",
+            "dngd_server_drain"]
 
 
 def _check(status, where):
@@ -245,6 +281,13 @@ class Context:
                                     C.byref(eta)), "dngd_line_search")
         return eta.value
 
+    def line_search_async(self, theta, X, target, delta, etas):
+        """theta += eta* delta on the device (no synchronisation)."""
+        etas = np.ascontiguousarray(etas, dtype=np.float64)
+        _check(lib.dngd_line_search_async(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(delta),
+                                          etas.ctypes.data_as(C.POINTER(C.c_double)), int(etas.size)),
+               "dngd_line_search_async")
+
     def residual_jacobian(self, theta, X, target, r_out, J_out=None):
         _check(lib.dngd_residual_jacobian(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(r_out),
                                           _ptr(J_out)), "dngd_residual_jacobian")
@@ -322,3 +365,58 @@ class Batch:
         infos = (StepInfo * n)()
         _check(lib.dngd_batch_step(self._h, arrs[0], arrs[1], arrs[2], arrs[3], infos), "dngd_batch_step")
         return [i.as_dict() for i in infos]
+
+
+class Server:
+    """dngd_server: PINN solve jobs admitted by HBM budget and slot count,
+    each job's iterations (step + line search + update) kept in flight on its
+    own stream by a native worker thread."""
+
+    def __init__(self, hbm_budget_bytes=0, max_slots=8, line_search_points=31):
+        cfg = ServerCfg(int(hbm_budget_bytes), int(max_slots), int(line_search_points))
+        self._h = C.c_void_p()
+        _check(lib.dngd_server_create(C.byref(self._h), C.byref(cfg)), "dngd_server_create")
+        self._n = {}
+
+    def close(self):
+        if self._h:
+            lib.dngd_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, desc, theta0, X, target, n_steps):
+        """Inputs (numpy or torch float64) are copied before this returns."""
+        keep = [np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a
+                for a in (theta0, X, target)]
+        job = JobDesc(desc, _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2]), int(n_steps))
+        jid = C.c_uint64(0)
+        _check(lib.dngd_submit(self._h, C.byref(job), C.byref(jid)), "dngd_submit")
+        self._n[jid.value] = dngd_num_params(desc)
+        return jid.value
+
+    def poll(self, job_id, theta_out=None):
+        st = JobState()
+        _check(lib.dngd_poll(self._h, C.c_uint64(job_id), C.byref(st), _ptr(theta_out)), "dngd_poll")
+        return dict(state=JOB_STATES[st.state], steps_done=st.steps_done, status=st.status, loss=st.loss,
+                    queue_s=st.queue_s, run_s=st.run_s)
+
+    def result(self, job_id):
+        theta = np.zeros(self._n[job_id])
+        info = self.poll(job_id, theta)
+        return info, (theta if info["state"] == "done" else None)
+
+    def cancel(self, job_id):
+        _check(lib.dngd_cancel(self._h, C.c_uint64(job_id)), "dngd_cancel")
+
+    def stats(self):
+        st = ServingStats()
+        _check(lib.dngd_server_stats(self._h, C.byref(st)), "dngd_server_stats")
+        return {f: getattr(st, f) for f, _ in ServingStats._fields_}
+
+    def drain(self, timeout_s=600.0):
+        _check(lib.dngd_server_drain(self._h, float(timeout_s)), "dngd_server_drain")
