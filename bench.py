@@ -384,7 +384,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lam", type=float, default=1e-5)
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "oz"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle leg (no step error)")
     ap.add_argument("--no-fp64", action="store_true")
@@ -448,7 +448,7 @@ def main():
                          "); line search not included",
                "blas_threads": _threads()}
 
-    prec = dngd.MIXED_BF16 if args.precision == "bf16" else dngd.MIXED_TF32
+    prec = {"bf16": dngd.MIXED_BF16, "tf32": dngd.MIXED_TF32, "oz": dngd.MIXED_OZ}[args.precision]
     m, n = int(wl["X"].shape[0]), dngd.dngd_num_params(dngd.make_desc(wl))
     th0 = torch.tensor(wl["theta"], device=dev)
     X = torch.tensor(wl["X"], device=dev)
@@ -557,9 +557,9 @@ def main():
         ctx64.close()
 
     hbm, bf16_burst, bf16_sust, src = _peaks()
-    gram_flops = float(m) * (m + 1) * n
+    gram_flops = float(m) * (m + 1) * n * (13 if prec == dngd.MIXED_OZ else 1)
     achieved = gram_flops / (gram_ms * 1e-3) / 1e12
-    peak = bf16_sust if prec == dngd.MIXED_BF16 else bf16_sust / 2.0
+    peak = bf16_sust / 2.0 if prec == dngd.MIXED_TF32 else bf16_sust
     # dominant kernel by time: the refinement's J^T p / J u GEMVs over the FP32 J
     jt_ms = float(np.mean([i["jt_ms"] for i in infos]))
     j_ms = float(np.mean([i["j_ms"] for i in infos]))
@@ -598,7 +598,7 @@ def main():
         "roofline_gram": {"bound": "tensor", "kernel": "k_gram_tc (tcgen05 BF16 syrk, lower 128x256 tiles)",
                           "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                           "flops_per_launch": gram_flops, "launch_ms": gram_ms,
-                          "peak_source": f"{src} bf16 sustained" + (" / 2 for tf32" if prec != dngd.MIXED_BF16 else "")},
+                          "peak_source": f"{src} bf16 sustained" + (" / 2 for tf32" if prec == dngd.MIXED_TF32 else "")},
         "cpu_baseline": cpu,
         "e2e": {"value": 1000.0 / e2e_ms * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),

@@ -70,7 +70,14 @@ enum dngd_precision {
                            FP32 Cholesky of K + (lambda+mu) I and its explicit
                            inverse as the preconditioner of PCG refinement on
                            the FP32-J operator with double-float accumulation */
-  DNGD_MIXED_TF32 = 2   /* as MIXED_BF16 with a TF32 tensor-core Gram */
+  DNGD_MIXED_TF32 = 2,  /* as MIXED_BF16 with a TF32 tensor-core Gram */
+  DNGD_MIXED_OZ = 3     /* FP32 jets/J; exact Gram of the FP32 J from four
+                           8-bit integer slices per row on the BF16 tensor
+                           cores (13 slice products, exact FP32 chunks summed
+                           in double-float: K accurate to ~2^-40 of the row
+                           scales); FP64 Cholesky of K + lambda I as the
+                           preconditioner of PCG on the FP32-J operator, which
+                           then converges in one or two iterations */
 };
 
 enum dngd_solver {

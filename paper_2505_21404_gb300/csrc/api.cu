@@ -54,6 +54,11 @@ struct dngd_ctx {
   void* Kcopy = nullptr;
   float* Linv = nullptr;
   float* trtri_work = nullptr;
+  OzPlan* oz = nullptr;       // exact-Gram mode
+  void* oz_slices = nullptr;
+  double* oz_partials = nullptr;
+  double* Dinv = nullptr;     // FP64 diagonal-block inverses of the factor
+  double* tw = nullptr;       // [2 m] triangular-solve work
   float* gram_partials = nullptr;
   size_t gram_partial_bytes = 0;
   GramPlan* gram = nullptr;
@@ -299,6 +304,15 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
   P.ev = (c->timing && slot == 0) ? c->kev : nullptr;
   const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
   const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
+  if (c->prec == DNGD_MIXED_OZ) {
+    // exact Gram + FP64 factor: one or two iterations; captured solves run a
+    // fixed count, so it is kept small
+    P.L64 = (const double*)c->K;
+    P.Dinv = c->Dinv;
+    P.tw = c->tw;
+    const int mi = c->async ? (maxit < 3 ? maxit : 3) : maxit;
+    return pcg_mixed_solve(P, b, x, tol, mi, 1, &c->iters[slot], &c->relres[slot], c->st, c->async, slot);
+  }
   return pcg_mixed_solve(P, b, x, tol, maxit, 4, &c->iters[slot], &c->relres[slot], c->st, c->async, slot);
 }
 
@@ -344,6 +358,39 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     // low-precision Gram + FP32 factor of K + (lambda + mu) I; a failed
     // factorisation is retried with a larger shift mu (it only preconditions
     // the refinement, whose operator keeps the exact lambda)
+    if (c->prec == DNGD_MIXED_OZ) {
+      // exact Gram, FP64 factor; a (rare) failed factorisation is retried
+      // with a shift from the partial tiles (only the reduction re-runs)
+      double mu = c->desc.shift_mu;
+      gram_oz_set_shift(c->oz, c->lambda + mu);
+      if ((s = gram_oz_run(c->oz, c->status, c->st, c->timing ? c->ev[8] : nullptr))) return s;
+      if (c->Kcopy)
+        DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(double) * (size_t)m * c->ldk,
+                                        cudaMemcpyDeviceToDevice, c->st));
+      if (!c->async) {
+        if ((s = diag_sum<double>(m, (const double*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
+      }
+      evrec(c, 2);
+      c->factor_attempts = 0;
+      for (int attempt = 0;; ++attempt) {
+        c->factor_attempts++;
+        if ((s = cholesky<double>(m, (double*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
+        if (c->async) break;
+        const dngd_status fs = read_status(c);
+        if (fs != DNGD_ERR_NOT_SPD || attempt >= 15) break;
+        DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+        DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+        const double tr = c->scal_h[S_TRACE] - m * c->lambda;
+        const double base = 1e-13 * (tr > 0 ? tr : 1.0) / m;
+        mu = mu * 3.0 > base ? mu * 3.0 : base;
+        gram_oz_set_shift(c->oz, c->lambda + mu);
+        if ((s = gram_oz_reduce(c->oz, c->st))) return s;
+        DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+      }
+      c->shift_used = mu;
+      if ((s = trtri_diag64(m, (const double*)c->K, c->ldk, c->Dinv, c->st))) return s;
+      if (c->async) goto factored;
+    } else {
     double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
     if (c->async) {
       // no host round trip: one factorisation with the shift of the last
@@ -393,6 +440,7 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     c->mu_sticky = mu;
     c->shift_used = mu;
     if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
+    }
   }
   // a failed factorisation stops the (synchronous) step here
   if (!c->async && (s = read_status(c))) return s;
@@ -761,6 +809,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   c->ldJ = f64 ? n : round_up(n, 64);
   c->ldb = round_up(n, 64);
   c->ldk = round_up(m, 4);
+  const bool oz = c->prec == DNGD_MIXED_OZ;
+  const bool bf = c->prec == DNGD_MIXED_BF16;
   add(sizeof(double) * n);        // theta_s
   add(sizeof(double) * m * net.d_in);
   add(sizeof(double) * m);        // target_s
@@ -783,11 +833,17 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   add(3 * rowbuf);        // H3a
   add(3 * rowbuf);        // H3b
   add(es * (size_t)m * c->ldJ);
-  if (c->prec == DNGD_MIXED_BF16) add(sizeof(__nv_bfloat16) * (size_t)m * c->ldb);
-  add(es * (size_t)m * c->ldk);
-  if (c->desc.keep_gram) add(es * (size_t)m * c->ldk);
-  if (!f64) add(es * (size_t)m * c->ldk);       // K0
-  if (!f64) {
+  if (bf) add(sizeof(__nv_bfloat16) * (size_t)m * c->ldb);
+  const size_t ks = oz ? sizeof(double) : es;     // K element
+  add(ks * (size_t)m * c->ldk);
+  if (c->desc.keep_gram) add(ks * (size_t)m * c->ldk);
+  if (oz) {
+    add(gram_oz_slice_bytes(m, (int)n));
+    add(gram_oz_partial_bytes(m, (int)n));
+    add(sizeof(double) * (size_t)cdiv(m, 64) * 64 * 64);   // Dinv
+    add(sizeof(double) * 2 * (size_t)m);                   // triangular-solve work
+  } else if (!f64) {
+    add(es * (size_t)m * c->ldk);                 // K0
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
     add(sizeof(float) * (size_t)m * m);           // trtri work
     add(gram_tc_partial_bytes(m, (int)n));
@@ -841,17 +897,27 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->H3b, float, 3 * rb);
     A_(c->J, float, (size_t)m * c->ldJ);
     DNGD_CUDA_CHECK(cudaMemset(c->J, 0, sizeof(float) * (size_t)m * c->ldJ));
-    if (c->prec == DNGD_MIXED_BF16) {
+    if (bf) {
       A_(c->Jb, __nv_bfloat16, (size_t)m * c->ldb);
       DNGD_CUDA_CHECK(cudaMemset(c->Jb, 0, sizeof(__nv_bfloat16) * (size_t)m * c->ldb));
     }
-    A_(c->K, float, (size_t)m * c->ldk);
-    A_(c->K0, float, (size_t)m * c->ldk);
-    if (c->desc.keep_gram) A_(c->Kcopy, float, (size_t)m * c->ldk);
-    A_(c->Linv, float, (size_t)m * c->ldk);
-    A_(c->trtri_work, float, (size_t)m * m);
-    c->gram_partial_bytes = gram_tc_partial_bytes(m, (int)n);
-    A_(c->gram_partials, float, c->gram_partial_bytes / sizeof(float));
+    if (oz) {
+      A_(c->K, double, (size_t)m * c->ldk);
+      if (c->desc.keep_gram) A_(c->Kcopy, double, (size_t)m * c->ldk);
+      A_(c->oz_slices, unsigned char, gram_oz_slice_bytes(m, (int)n));
+      c->gram_partial_bytes = gram_oz_partial_bytes(m, (int)n);
+      A_(c->oz_partials, double, c->gram_partial_bytes / sizeof(double));
+      A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
+      A_(c->tw, double, 2 * (size_t)m);
+    } else {
+      A_(c->K, float, (size_t)m * c->ldk);
+      A_(c->K0, float, (size_t)m * c->ldk);
+      if (c->desc.keep_gram) A_(c->Kcopy, float, (size_t)m * c->ldk);
+      A_(c->Linv, float, (size_t)m * c->ldk);
+      A_(c->trtri_work, float, (size_t)m * m);
+      c->gram_partial_bytes = gram_tc_partial_bytes(m, (int)n);
+      A_(c->gram_partials, float, c->gram_partial_bytes / sizeof(float));
+    }
   }
   A_(c->r, double, m);
   A_(c->alpha, double, m);
@@ -878,11 +944,15 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   DNGD_CUDA_CHECK(cudaMemset(c->status, 0, sizeof(int) * 4));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->scal_h, sizeof(double) * S_COUNT));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->status_h, sizeof(int) * 4));
-  if (!f64) {
-    const void* Jlow = c->prec == DNGD_MIXED_BF16 ? (const void*)c->Jb : (const void*)c->J;
-    const long long ld = c->prec == DNGD_MIXED_BF16 ? c->ldb : c->ldJ;
-    s = gram_tc_plan(&c->gram, c->prec == DNGD_MIXED_BF16 ? 0 : 1, Jlow, m, (int)n, ld, (float*)c->K, c->ldk,
-                     c->gram_partials, c->gram_partial_bytes);
+  if (oz) {
+    s = gram_oz_plan(&c->oz, (const float*)c->J, c->ldJ, m, (int)n, c->oz_slices, (double*)c->K, c->ldk,
+                     c->oz_partials, c->gram_partial_bytes);
+    if (s) return s;
+  } else if (!f64) {
+    const void* Jlow = bf ? (const void*)c->Jb : (const void*)c->J;
+    const long long ld = bf ? c->ldb : c->ldJ;
+    s = gram_tc_plan(&c->gram, bf ? 0 : 1, Jlow, m, (int)n, ld, (float*)c->K, c->ldk, c->gram_partials,
+                     c->gram_partial_bytes);
     if (s) return s;
   }
   for (int i = 0; i < 9; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
@@ -900,6 +970,7 @@ void free_ctx(dngd_ctx* c) {
   if (c->scal_h) cudaFreeHost(c->scal_h);
   if (c->status_h) cudaFreeHost(c->status_h);
   if (c->gram) gram_tc_free(c->gram);
+  if (c->oz) gram_oz_free(c->oz);
   for (int i = 0; i < 9; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (int i = 0; i < 4; ++i)
@@ -961,7 +1032,7 @@ dngd_status dngd_workspace_bytes(const dngd_problem_desc* desc, size_t* bytes) {
 dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* stream) {
   if (!out || !desc) return DNGD_ERR_INVALID_ARG;
   *out = nullptr;
-  if (desc->precision < DNGD_FP64 || desc->precision > DNGD_MIXED_TF32) return DNGD_ERR_INVALID_ARG;
+  if (desc->precision < DNGD_FP64 || desc->precision > DNGD_MIXED_OZ) return DNGD_ERR_INVALID_ARG;
   if (desc->solver != DNGD_DENSE && desc->solver != DNGD_PCG) return DNGD_ERR_INVALID_ARG;
   if (desc->solver == DNGD_PCG && desc->precision == DNGD_FP64) return DNGD_ERR_INVALID_ARG;
   if (!(desc->lambda > 0.0)) return DNGD_ERR_INVALID_ARG;
@@ -1188,10 +1259,11 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
     case 7: {
       const void* src = which == 6 ? c->Kcopy : c->K;
       if (!src) return DNGD_ERR_STATE;
-      if (which == 7 && c->prec != DNGD_FP64) return DNGD_ERR_STATE;
+      const bool k64 = c->prec == DNGD_FP64 || c->prec == DNGD_MIXED_OZ;
+      if (which == 7 && !k64) return DNGD_ERR_STATE;
       double* buf = nullptr;
       if (cudaMalloc(&buf, sizeof(double) * (size_t)m * m) != cudaSuccess) return DNGD_ERR_OOM;
-      dngd_status s = c->prec == DNGD_FP64 ? lower_to_f64<double>(m, (const double*)src, c->ldk, buf, c->st)
+      dngd_status s = k64 ? lower_to_f64<double>(m, (const double*)src, c->ldk, buf, c->st)
                                            : lower_to_f64<float>(m, (const float*)src, c->ldk, buf, c->st);
       if (!s) {
         cudaMemcpyAsync(dst, buf, sizeof(double) * (size_t)m * m, cudaMemcpyDefault, c->st);

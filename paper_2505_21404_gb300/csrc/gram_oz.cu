@@ -1,0 +1,475 @@
+// Exact Gram K = J J^T of an FP32 matrix on the BF16 tensor cores.
+//
+// The dual solve needs K accurate to far below lambda: at lambda = 1e-5 and
+// ||K|| ~ 1e4 (Sec. 3.1's K + lambda I, with cond ~ 1e9 late in training) a
+// BF16 or FP32 Gram is indefinite at the lambda scale, and only an exact
+// Gram factored in FP64 makes the refinement converge in one iteration.
+// GB300's FP64 rate is ~1 TFLOP/s, so the Gram is built from exact integer
+// products instead (an error-free splitting in the spirit of Ozaki et al.):
+//
+//   * each row i of J is scaled by 2^-E_i (E_i = exponent of the row's
+//     largest entry, plus one) and split into four signed 8-bit integers,
+//       J[i,k] = 2^E_i sum_{s<4} sigma_s[i,k] 2^(-8(s+1)) + r,
+//       |sigma_s| <= 128,  |r| <= 2^(E_i - 33);
+//     the slices are exact in BF16;
+//   * with L_g = sum_{s+t=g} sigma_s sigma_t^T (integer matrices),
+//       K[i,j] = 2^(E_i+E_j-48) sum_{g<=4} 2^(8(4-g)) L_g[i,j]
+//     (13 slice products; the dropped s+t >= 5 terms are below 2^-40 of the
+//     row scales);
+//   * products of slices are exact in the tensor cores, and every chunk the
+//     MMAs accumulate in TMEM stays below 2^24 in magnitude (pairs x k-blocks
+//     <= 16), so the FP32 accumulator is exact; the epilogue adds each chunk
+//     into double-float registers (48-bit significand) with a Horner scaling
+//     by 2^8 between levels.
+//
+// Kernel roles (one 128 x 128 lower output tile and one K range per CTA):
+// warp 0 lane 0 streams 128 x 64 slice tiles of A and B rows with TMA
+// (128-byte swizzle) into a 6-stage ring; warp 1 lane 0 issues
+// tcgen05.mma (M = N = 128) into one of two TMEM buffers per chunk; warps
+// 2..9 drain finished chunks (warp w: TMEM lanes 32 (w % 4).., 64 columns).
+// Split-K partial tiles (FP64) are summed in a fixed order by the reduction,
+// which also applies the row scales and the diagonal shift.  Every wait is
+// bounded (ST_TIMEOUT, drain, free TMEM).
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace dngd {
+
+namespace {
+
+using namespace tc;
+
+constexpr int NS = 4;                       // slices per value
+constexpr int NG = 5;                       // levels g = s + t <= 4
+constexpr int TB = 128;                     // output tile rows = columns
+constexpr int OST = 6;                      // pipeline stages
+constexpr int OTILE = TB * 128;             // one operand tile (64 bf16 of K), 16 KB
+constexpr int OSTAGE = 2 * OTILE;           // A + B
+constexpr int OSMEM = OST * OSTAGE + 1024;
+constexpr int OTHREADS = 320;
+// TMEM columns: [0, 256) two 128-column chunk accumulators (MMA), [256, 384)
+// and [384, 512) the hi and lo words of the tile's double-float sum (ten
+// warps share a sub-partition's 16K registers, so the sum cannot stay in
+// registers)
+constexpr uint32_t OTMEM = 512;
+constexpr uint32_t ACC_HI = 256, ACC_LO = 384;
+
+__host__ __device__ __forceinline__ int g_lo(int g) { return g > NS - 1 ? g - (NS - 1) : 0; }
+__host__ __device__ __forceinline__ int g_hi(int g) { return g < NS - 1 ? g : NS - 1; }
+// k blocks per exact chunk: pairs * 64 * kb * 2^14 <= 2^24
+__host__ __device__ __forceinline__ int g_kb(int g) { return 16 / (g_hi(g) - g_lo(g) + 1); }
+
+// BF16 x BF16 -> FP32, both K-major, N = M = 128.
+__device__ __forceinline__ uint32_t oz_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TB >> 3) << 17) | ((uint32_t)(TB >> 4) << 24);
+}
+
+// (hi, lo) += c exactly as long as the sum needs at most ~48 bits.
+__device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
+  const float s = hi + c;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (c - bp);
+  const float l = lo + e;
+  const float t = s + l;
+  lo = l - (t - s);
+  hi = t;
+}
+
+// Row scaling and slicing: one block per row.
+__global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const float* __restrict__ J, long long ldJ,
+                                                  __nv_bfloat16* __restrict__ S, long long ldS, int ldb,
+                                                  int* __restrict__ rowexp) {
+  const int i = blockIdx.x;
+  const float* row = J + (long long)i * ldJ;
+  float amax = 0.f;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) amax = fmaxf(amax, fabsf(row[k]));
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  __shared__ float red[8];
+  __shared__ int E_sh;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f;
+    for (int w = 0; w < 8; ++w) a = fmaxf(a, red[w]);
+    int e = 0;
+    if (a > 0.f && a <= 3.0e38f) frexpf(a, &e);   // a = f 2^e, f in [0.5, 1)
+    E_sh = e + 1;                                 // |J| / 2^E < 0.5
+    rowexp[i] = e + 1;
+  }
+  __syncthreads();
+  const int E = E_sh;
+  __nv_bfloat16* srow = S + (long long)i * ldS;
+  for (int k = threadIdx.x; k < ldb; k += blockDim.x) {
+    float x = k < n ? ldexpf(row[k], -E) : 0.f;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const float t = x * 256.f;
+      const float sg = rintf(t);
+      x = t - sg;
+      srow[(long long)s * ldb + k] = __float2bfloat16_rn(sg);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(OTHREADS, 1)
+k_gram_oz(const __grid_constant__ CUtensorMap map, const int2* __restrict__ tiles, int m, int num_kblk, int ldb,
+          double* __restrict__ out, long long ldo, long long split_stride, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[OST];
+  __shared__ __align__(8) uint64_t empty_bar[OST];
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int2 tile = tiles[blockIdx.x];
+  const int split = blockIdx.y, nsplit = gridDim.y;
+  const int kb_per = (num_kblk + nsplit - 1) / nsplit;
+  const int kb0 = split * kb_per;
+  const int kb1 = min(num_kblk, kb0 + kb_per);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OST; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf_bar[b]), 1);
+      mbar_init(smem_u32(&acce_bar[b]), 8);
+    }
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(OTMEM));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int g = 0; g < NG && !*abort_flag; ++g) {
+        for (int kb = kb0; kb < kb1 && !*abort_flag; ++kb) {
+          for (int sa = g_lo(g); sa <= g_hi(g); ++sa, ++it) {
+            const int st = it % OST;
+            const uint32_t ph = (uint32_t)((it / OST) & 1);
+            if (*abort_flag || !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, status, 11)) {
+              *abort_flag = 1;
+              break;
+            }
+            const uint32_t fb = smem_u32(&full_bar[st]);
+            mbar_expect_tx(fb, OSTAGE);
+            const uint32_t sa_addr = smem_base + st * OSTAGE;
+            tma_load_2d(sa_addr, &map, fb, sa * ldb + kb * 64, tile.x * TB);
+            tma_load_2d(sa_addr + OTILE, &map, fb, (g - sa) * ldb + kb * 64, tile.y * TB);
+            ++issued;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = oz_idesc();
+      int it = 0, c = 0;
+      for (int g = 0; g < NG && !*abort_flag; ++g) {
+        const int ck = g_kb(g);
+        for (int c0 = kb0; c0 < kb1 && !*abort_flag; c0 += ck, ++c) {
+          const int b = c & 1, use = c >> 1;
+          if (!mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)((use & 1) ^ 1), status, 15)) {
+            *abort_flag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t dbuf = tmem + (uint32_t)(b * TB);
+          bool first = true;
+          const int c1 = min(kb1, c0 + ck);
+          for (int kb = c0; kb < c1 && !*abort_flag; ++kb) {
+            for (int sa = g_lo(g); sa <= g_hi(g); ++sa, ++it) {
+              const int st = it % OST;
+              const uint32_t ph = (uint32_t)((it / OST) & 1);
+              if (*abort_flag || !mbar_wait(smem_u32(&full_bar[st]), ph, status, 12)) {
+                *abort_flag = 1;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              const uint32_t sa_addr = smem_base + st * OSTAGE;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                umma<0>(dbuf, sw128_desc(sa_addr + 32 * k), sw128_desc(sa_addr + OTILE + 32 * k), idesc,
+                        (first && k == 0) ? 0u : 1u);
+              }
+              first = false;
+              umma_commit(smem_u32(&empty_bar[st]));
+            }
+          }
+          umma_commit(smem_u32(&accf_bar[b]));
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3;             // TMEM lane quadrant
+    const int h = (warp - 2) >> 2;      // column half (64 columns)
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    int c = 0;
+    for (int g = 0; g < NG && !*abort_flag; ++g) {
+      const int ck = g_kb(g);
+      bool level_start = true;
+      for (int c0 = kb0; c0 < kb1; c0 += ck, ++c) {
+        const int b = c & 1, use = c >> 1;
+        const bool ok = __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&accf_bar[b]),
+                                                                           (uint32_t)(use & 1), status, 13))
+                                                    ? 1
+                                                    : 0) != 0;
+        if (!ok) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+        for (int j2 = 0; j2 < 2; ++j2) {
+          const uint32_t col = (uint32_t)(h * 64 + j2 * 32);
+          uint32_t r[32], hi[32], lo[32];
+          TMEM_LD_32(lane_base + (uint32_t)(b * TB) + col, r);
+          if (c > 0) {
+            TMEM_LD_32(lane_base + ACC_HI + col, hi);
+            TMEM_LD_32(lane_base + ACC_LO + col, lo);
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          // Horner step between levels: the sum so far times 2^8 (exact)
+          const float sc = (level_start && g > 0) ? 256.f : 1.f;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            float a = c > 0 ? __uint_as_float(hi[i]) * sc : 0.f;
+            float l = c > 0 ? __uint_as_float(lo[i]) * sc : 0.f;
+            df_add_exact(a, l, __uint_as_float(r[i]));
+            hi[i] = __float_as_uint(a);
+            lo[i] = __float_as_uint(l);
+          }
+          TMEM_ST_32(lane_base + ACC_HI + col, hi);
+          TMEM_ST_32(lane_base + ACC_LO + col, lo);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        level_start = false;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[b])) : "memory");
+      }
+    }
+    const int row = tile.x * TB + q * 32 + lane;
+    const int col0 = tile.y * TB + h * 64;
+    if (!*abort_flag) {
+#pragma unroll 1
+      for (int j2 = 0; j2 < 2; ++j2) {
+        uint32_t hi[32], lo[32];
+        const uint32_t col = (uint32_t)(h * 64 + j2 * 32);
+        if (c > 0) {
+          TMEM_LD_32(lane_base + ACC_HI + col, hi);
+          TMEM_LD_32(lane_base + ACC_LO + col, lo);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0u;
+        }
+        if (row < m) {
+          double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0 + j2 * 32;
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (col0 + j2 * 32 + i < m) orow[i] = (double)__uint_as_float(hi[i]) + (double)__uint_as_float(lo[i]);
+        }
+      }
+    }
+  }
+  __syncwarp();
+
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (int it = 0; it < issued; ++it) {
+      const int st = it % OST;
+      mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((it / OST) & 1), status, 14);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OTMEM));
+  }
+}
+
+// K[i,j] (j <= i) = 2^(E_i+E_j-48) sum_s P_s[i,j] (+ shift on the diagonal);
+// the upper triangle is set to 0.
+__global__ void k_oz_reduce(int m, int nsplit, const double* __restrict__ P, long long ldp, long long sstride,
+                            const int* __restrict__ rowexp, double shift, double* __restrict__ K, long long ldk) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * m) return;
+  const int i = (int)(idx / m), j = (int)(idx % m);
+  double v = 0.0;
+  if (j <= i) {
+    for (int s = 0; s < nsplit; ++s) v += P[(long long)s * sstride + (long long)i * ldp + j];
+    v = ldexp(v, rowexp[i] + rowexp[j] - 48);
+    if (i == j) v += shift;
+  }
+  K[(long long)i * ldk + j] = v;
+}
+
+int oz_splits(int ntiles, int num_kblk, int nsm) {
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= 4; ++s) {
+    if (num_kblk / s < 16) break;
+    const long long units = (long long)ntiles * s;
+    const long long waves = (units + nsm - 1) / nsm;
+    const double eff = (double)units / (double)(waves * nsm);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
+}
+
+int oz_ntiles(int m) {
+  const int nI = (m + TB - 1) / TB;
+  return nI * (nI + 1) / 2;
+}
+
+}  // namespace
+
+struct OzPlan {
+  int m, n, ldb;
+  long long ldJ, ldS;
+  const float* J;
+  __nv_bfloat16* S;
+  int* rowexp;
+  CUtensorMap map;
+  int2* d_tiles = nullptr;
+  int ntiles = 0, nsplit = 1, num_kblk = 0;
+  double* partials = nullptr;
+  long long ldp = 0, sstride = 0;
+  double* K;
+  long long ldk;
+  double shift = 0.0;
+};
+
+size_t gram_oz_partial_bytes(int m, int n) {
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsplit = oz_splits(oz_ntiles(m), (n + 63) / 64, nsm);
+  const long long mp = (long long)((m + TB - 1) / TB) * TB;
+  return (size_t)nsplit * mp * mp * sizeof(double);
+}
+
+size_t gram_oz_slice_bytes(int m, int n) {
+  const long long ldb = ((n + 63) / 64) * 64;
+  return (size_t)m * NS * ldb * sizeof(__nv_bfloat16) + (size_t)m * sizeof(int) + 256;
+}
+
+dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int n, void* slices, double* K,
+                         long long ldk, double* partials, size_t partial_bytes) {
+  EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
+  if (!enc) return DNGD_ERR_CUDA;
+  OzPlan* p = new OzPlan();
+  p->m = m;
+  p->n = n;
+  p->J = J;
+  p->ldJ = ldJ;
+  p->ldb = ((n + 63) / 64) * 64;
+  p->ldS = (long long)NS * p->ldb;
+  p->S = (__nv_bfloat16*)slices;
+  p->rowexp = (int*)((char*)slices + (size_t)m * p->ldS * sizeof(__nv_bfloat16));
+  p->K = K;
+  p->ldk = ldk;
+  p->num_kblk = p->ldb / 64;
+  cuuint64_t gdim[2] = {(cuuint64_t)p->ldS, (cuuint64_t)m};
+  cuuint64_t gstride[1] = {(cuuint64_t)(p->ldS * 2)};
+  cuuint32_t estride[2] = {1, 1};
+  cuuint32_t box[2] = {64, (cuuint32_t)TB};
+  if (enc(&p->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S, gdim, gstride, box, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    delete p;
+    return DNGD_ERR_CUDA;
+  }
+  std::vector<int2> tiles;
+  const int nI = (m + TB - 1) / TB;
+  for (int I = 0; I < nI; ++I)
+    for (int Jc = 0; Jc <= I; ++Jc) tiles.push_back(make_int2(I, Jc));
+  p->ntiles = (int)tiles.size();
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  p->nsplit = oz_splits(p->ntiles, p->num_kblk, nsm);
+  const long long mp = (long long)nI * TB;
+  p->ldp = mp;
+  p->sstride = mp * mp;
+  if ((size_t)p->nsplit * p->sstride * sizeof(double) > partial_bytes) p->nsplit = 1;
+  if ((size_t)p->sstride * sizeof(double) > partial_bytes) {
+    delete p;
+    return DNGD_ERR_INVALID_ARG;
+  }
+  p->partials = partials;
+  if (cudaMalloc(&p->d_tiles, sizeof(int2) * tiles.size()) != cudaSuccess) {
+    delete p;
+    return DNGD_ERR_OOM;
+  }
+  cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gram_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OSMEM);
+    attr = true;
+  }
+  *out = p;
+  return DNGD_OK;
+}
+
+dngd_status gram_oz_set_shift(OzPlan* p, double shift) {
+  p->shift = shift;
+  return DNGD_OK;
+}
+
+dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_after_mma) {
+  DNGD_NOTE_LAUNCH();
+  k_oz_slice<<<p->m, 256, 0, st>>>(p->m, p->n, p->J, p->ldJ, p->S, p->ldS, p->ldb, p->rowexp);
+  DNGD_LAUNCH_CHECK();
+  DNGD_NOTE_LAUNCH();
+  k_gram_oz<<<dim3(p->ntiles, p->nsplit), OTHREADS, OSMEM, st>>>(p->map, p->d_tiles, p->m, p->num_kblk, p->ldb,
+                                                                  p->partials, p->ldp, p->sstride, status);
+  DNGD_LAUNCH_CHECK();
+  if (ev_after_mma) cudaEventRecord(ev_after_mma, st);
+  return gram_oz_reduce(p, st);
+}
+
+// Re-run only the reduction (e.g. with a new shift): the partial tiles of
+// the last run stay valid.
+dngd_status gram_oz_reduce(OzPlan* p, cudaStream_t st) {
+  const long long tot = (long long)p->m * p->m;
+  DNGD_NOTE_LAUNCH();
+  k_oz_reduce<<<(int)((tot + 255) / 256), 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->rowexp,
+                                                        p->shift, p->K, p->ldk);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+void gram_oz_free(OzPlan* p) {
+  if (!p) return;
+  if (p->d_tiles) cudaFree(p->d_tiles);
+  delete p;
+}
+
+int gram_oz_nsplit(const OzPlan* p) { return p->nsplit; }
+
+}  // namespace dngd

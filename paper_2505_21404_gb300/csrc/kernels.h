@@ -65,6 +65,23 @@ dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv,
 
 // x = (L L^T)^{-1} b with the FP64 factor (two triangular solves).
 dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* b, double* x, cudaStream_t st);
+// Inverses of the 64 x 64 diagonal blocks of an FP64 factor ([ceil(m/64)] x
+// 64 x 64) and the blocked solve that uses them (w, y: work vectors [m]).
+dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cudaStream_t st);
+dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const double* Dinv, const double* b, double* x,
+                                double* w, double* y, cudaStream_t st);
+
+// ---- gram_oz.cu: exact Gram of an FP32 matrix from BF16 integer slices ----
+struct OzPlan;
+size_t gram_oz_partial_bytes(int m, int n);
+size_t gram_oz_slice_bytes(int m, int n);   // slices + row exponents
+dngd_status gram_oz_plan(OzPlan** plan, const float* J, long long ldJ, int m, int n, void* slices, double* K,
+                         long long ldk, double* partials, size_t partial_bytes);
+dngd_status gram_oz_set_shift(OzPlan* plan, double shift);
+dngd_status gram_oz_run(OzPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
+dngd_status gram_oz_reduce(OzPlan* plan, cudaStream_t st);
+void gram_oz_free(OzPlan* plan);
+int gram_oz_nsplit(const OzPlan* plan);
 
 // Explicit inverse of a lower-triangular FP32 factor: Linv = L^{-1} (lower).
 dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
@@ -108,6 +125,10 @@ struct PcgMixed {
   double* scal_h;                     // pinned host copy
   cudaEvent_t* ev;                    // optional: 4 events bracketing the first
                                       // J^T p and J u launches of the solve
+  // FP64 factor preconditioner (exact-Gram mode): M^{-1} = (L L^T)^{-1}
+  const double* L64 = nullptr;
+  const double* Dinv = nullptr;
+  double* tw = nullptr;               // [2 m] triangular-solve work
 };
 // async: enqueue exactly maxit iterations (kernels become no-ops after
 // convergence) and never synchronise; iters/relres are then left untouched and

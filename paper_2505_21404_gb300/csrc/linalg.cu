@@ -507,6 +507,118 @@ dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* 
 }
 
 // ---------------------------------------------------------------------------
+// Faster FP64 triangular solves: the inverses of the 64 x 64 diagonal blocks
+// of L are formed once per factorisation, and each block step is one launch
+// that applies the block inverse (a 64 x 64 GEMV, recomputed by every CTA)
+// and updates the rows still to be solved.
+// ---------------------------------------------------------------------------
+
+// Dinv[b] = inverse of the diagonal block b of L (64 x 64, lower; thread per
+// column, forward substitution on the identity).
+__global__ void __launch_bounds__(64) k_trtri_diag64(int m, const double* __restrict__ L, long long ldl,
+                                                     double* __restrict__ Dinv) {
+  __shared__ double Ls[kTrsvNB][kTrsvNB + 1];
+  __shared__ double Xs[kTrsvNB][kTrsvNB + 1];
+  const int k0 = blockIdx.x * kTrsvNB;
+  const int kb = min(kTrsvNB, m - k0);
+  const int c = threadIdx.x;
+  for (int e = c; e < kTrsvNB * kTrsvNB; e += blockDim.x) {
+    const int i = e / kTrsvNB, j = e % kTrsvNB;
+    Ls[i][j] = (i < kb && j <= i) ? L[(long long)(k0 + i) * ldl + k0 + j] : (i == j ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int i = 0; i < kTrsvNB; ++i) {
+    double s = (i == c) ? 1.0 : 0.0;
+    for (int p = c; p < i; ++p) s -= Ls[i][p] * Xs[p][c];
+    Xs[i][c] = (i >= c) ? s / Ls[i][i] : 0.0;
+  }
+  __syncthreads();
+  double* D = Dinv + (long long)blockIdx.x * kTrsvNB * kTrsvNB;
+  for (int e = c; e < kTrsvNB * kTrsvNB; e += blockDim.x) D[e] = Xs[e / kTrsvNB][e % kTrsvNB];
+}
+
+// Forward block step: y_blk = Dinv_k w_blk; w_i -= L[i, blk] y_blk for the
+// rows i >= k0 + kb this CTA owns (warp per row).  w_blk is only read here.
+__global__ void __launch_bounds__(256) k_trsv_fwd_step(int m, int k0, int kb, const double* __restrict__ L,
+                                                       long long ldl, const double* __restrict__ D,
+                                                       double* __restrict__ w, double* __restrict__ y) {
+  __shared__ double xb[kTrsvNB], yb[kTrsvNB];
+  const int tid = threadIdx.x;
+  if (tid < kTrsvNB) xb[tid] = tid < kb ? w[k0 + tid] : 0.0;
+  __syncthreads();
+  if (tid < kTrsvNB) {
+    double s = 0.0;
+    for (int j = 0; j <= tid; ++j) s += D[tid * kTrsvNB + j] * xb[j];
+    yb[tid] = s;
+    if (blockIdx.x == 0 && tid < kb) y[k0 + tid] = s;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  const int i = k0 + kb + blockIdx.x * 8 + warp;
+  if (i >= m) return;
+  const double* Li = L + (long long)i * ldl + k0;
+  double s = 0.0;
+  for (int j = lane; j < kb; j += 32) s += Li[j] * yb[j];
+  s = warp_sum(s);
+  if (lane == 0) w[i] -= s;
+}
+
+// Backward block step: x_blk = Dinv_k^T w_blk; w_i -= sum_j L[k0+j, i] x_j
+// for i < k0 (thread per i).
+__global__ void __launch_bounds__(256) k_trsv_bwd_step(int k0, int kb, const double* __restrict__ L, long long ldl,
+                                                       const double* __restrict__ D, double* __restrict__ w,
+                                                       double* __restrict__ x) {
+  __shared__ double xb[kTrsvNB], yb[kTrsvNB];
+  const int tid = threadIdx.x;
+  if (tid < kTrsvNB) xb[tid] = tid < kb ? w[k0 + tid] : 0.0;
+  __syncthreads();
+  if (tid < kTrsvNB) {
+    double s = 0.0;
+    for (int j = tid; j < kTrsvNB; ++j) s += D[j * kTrsvNB + tid] * xb[j];
+    yb[tid] = s;
+    if (blockIdx.x == 0 && tid < kb) x[k0 + tid] = s;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + tid;
+  if (i >= k0) return;
+  double s = 0.0;
+  for (int j = 0; j < kb; ++j) s += L[(long long)(k0 + j) * ldl + i] * yb[j];
+  w[i] -= s;
+}
+
+dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
+  k_trtri_diag64<<<cdiv(m, kTrsvNB), kTrsvNB, 0, st>>>(m, L, ldl, Dinv);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// x = (L L^T)^{-1} b with the diagonal-block inverses; w, y: work vectors [m].
+dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const double* Dinv, const double* b, double* x,
+                                double* w, double* y, cudaStream_t st) {
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(w, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+  const int nblk = cdiv(m, kTrsvNB);
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int k0 = bi * kTrsvNB;
+    const int kb = (m - k0) < kTrsvNB ? (m - k0) : kTrsvNB;
+    const int rest = m - k0 - kb;
+    DNGD_NOTE_LAUNCH();
+    k_trsv_fwd_step<<<rest > 0 ? cdiv(rest, 8) : 1, 256, 0, st>>>(m, k0, kb, L, ldl,
+                                                                  Dinv + (long long)bi * kTrsvNB * kTrsvNB, w, y);
+  }
+  // y holds L^{-1} b; solve L^T x = y with y as the working vector
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int k0 = bi * kTrsvNB;
+    const int kb = (m - k0) < kTrsvNB ? (m - k0) : kTrsvNB;
+    DNGD_NOTE_LAUNCH();
+    k_trsv_bwd_step<<<k0 > 0 ? cdiv(k0, 256) : 1, 256, 0, st>>>(k0, kb, L, ldl,
+                                                                Dinv + (long long)bi * kTrsvNB * kTrsvNB, y, x);
+  }
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Explicit inverse of a lower-triangular FP32 factor (recursive 2x2 blocks:
 // inv([[A,0],[B,C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]]); the diagonal blocks
 // are inverted in FP64 in shared memory.  Linv must be zero-initialised.

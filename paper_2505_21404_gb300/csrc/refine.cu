@@ -301,8 +301,9 @@ dngd_status gemv_n_f32_s(int m, int n, const float* A, long long lda, const doub
   return DNGD_OK;
 }
 
-// z = Linv^T (Linv q)
+// z = Linv^T (Linv q), or z = (L L^T)^{-1} q with the FP64 factor
 dngd_status precond(const PcgMixed& P, const double* q, double* z, cudaStream_t st) {
+  if (P.L64) return chol_solve_f64_dinv(P.m, P.L64, P.ldk, P.Dinv, q, z, P.tw, P.tw + P.m, st);
   dngd_status s = gemv_n_f32_s(P.m, P.m, P.Linv, P.ldk, q, 1.0, P.y, nullptr, 0.0, P.xs, nullptr, nullptr, P.scal,
                                st);
   if (s) return s;
