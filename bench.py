@@ -564,7 +564,7 @@ def main():
     jt_ms = float(np.mean([i["jt_ms"] for i in infos]))
     j_ms = float(np.mean([i["j_ms"] for i in infos]))
     gemv_bytes = 4.0 * m * n + 8.0 * (m + n)
-    gemv_gbs = 2 * gemv_bytes / ((jt_ms + j_ms) * 1e-3) / 1e9
+    gemv_gbs = 2 * gemv_bytes / ((jt_ms + j_ms) * 1e-3) / 1e9 if jt_ms + j_ms > 0 else 0.0
     iters_total = float(np.mean([sum(i["solve_iters"]) for i in infos]))
     err = {}
     if ref is not None:

@@ -74,10 +74,11 @@ enum dngd_precision {
   DNGD_MIXED_OZ = 3     /* FP32 jets/J; exact Gram of the FP32 J from four
                            8-bit integer slices per row on the BF16 tensor
                            cores (13 slice products, exact FP32 chunks summed
-                           in double-float: K accurate to ~2^-40 of the row
-                           scales); FP64 Cholesky of K + lambda I as the
-                           preconditioner of PCG on the FP32-J operator, which
-                           then converges in one or two iterations */
+                           in double-float: K accurate to ~2^-33 of the row
+                           scales); the FP32 factor of K + (lambda+mu) I (as
+                           MIXED_BF16) preconditions PCG whose operator is the
+                           exact FP64 Gram (one m x m GEMV per iteration
+                           instead of two over J) */
 };
 
 enum dngd_solver {
@@ -235,7 +236,9 @@ dngd_status dngd_fvv(dngd_ctx* ctx, const double* theta, const double* X, const 
  *         6 lower triangle of K + lambda I [m x m] row-major (dense, before
  *           factorisation; the upper triangle is left as zero),
  *         7 Cholesky factor L [m x m] row-major (dense solver),
- *         8 landmark columns K_{:,I} [m x ell] row-major (PCG solver).
+ *         8 landmark columns K_{:,I} [m x ell] row-major (PCG solver),
+ *         9 exact Gram J J^T [m x m] row-major, full symmetric, no lambda
+ *           (DNGD_MIXED_OZ).
  * Values are converted to float64. */
 dngd_status dngd_get_stage(dngd_ctx* ctx, int which, double* dst);
 

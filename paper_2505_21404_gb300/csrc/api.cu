@@ -57,8 +57,9 @@ struct dngd_ctx {
   OzPlan* oz = nullptr;       // exact-Gram mode
   void* oz_slices = nullptr;
   double* oz_partials = nullptr;
-  double* Dinv = nullptr;     // FP64 diagonal-block inverses of the factor
-  double* tw = nullptr;       // [2 m] triangular-solve work
+  double* K64 = nullptr;      // exact FP64 Gram (full symmetric, no shift)
+  double* Dinv = nullptr;     // FP64 path: inverses of the factor's 64 x 64 diagonal blocks
+  double* tw = nullptr;       // FP64 path: [2 m] triangular-solve work
   float* gram_partials = nullptr;
   size_t gram_partial_bytes = 0;
   GramPlan* gram = nullptr;
@@ -305,13 +306,9 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
   const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
   const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
   if (c->prec == DNGD_MIXED_OZ) {
-    // exact Gram + FP64 factor: one or two iterations; captured solves run a
-    // fixed count, so it is kept small
-    P.L64 = (const double*)c->K;
-    P.Dinv = c->Dinv;
-    P.tw = c->tw;
-    const int mi = c->async ? (maxit < 3 ? maxit : 3) : maxit;
-    return pcg_mixed_solve(P, b, x, tol, mi, 1, &c->iters[slot], &c->relres[slot], c->st, c->async, slot);
+    // the exact FP64 Gram is the operator: one m x m GEMV per iteration
+    P.K64 = c->K64;
+    P.ldk64 = c->ldk;
   }
   return pcg_mixed_solve(P, b, x, tol, maxit, 4, &c->iters[slot], &c->relres[slot], c->st, c->async, slot);
 }
@@ -323,7 +320,7 @@ dngd_status solve_last(dngd_ctx* c, const double* b, double* x, int slot) {
   if (c->prec == DNGD_FP64) {
     c->iters[slot] = 0;
     c->relres[slot] = 0.0;
-    return chol_solve_f64(c->m, (const double*)c->K, c->ldk, b, x, c->st);
+    return chol_solve_f64_dinv(c->m, (const double*)c->K, c->ldk, c->Dinv, b, x, c->tw, c->tw + c->m, c->st);
   }
   return pcg_mixed(c, b, x, slot);
 }
@@ -331,6 +328,18 @@ dngd_status solve_last(dngd_ctx* c, const double* b, double* x, int slot) {
 // ---------------------------------------------------------------------------
 // The step
 // ---------------------------------------------------------------------------
+
+// The low-precision Gram writes K + shift I (FP32 lower) for the factor: the
+// tcgen05 BF16 / TF32 syrk, or the exact sliced Gram (which also writes the
+// FP64 refinement operator).
+void gram_set_shift(dngd_ctx* c, double shift) {
+  if (c->oz) gram_oz_set_shift(c->oz, shift);
+  else gram_tc_set_shift(c->gram, shift);
+}
+dngd_status gram_run(dngd_ctx* c, cudaEvent_t ev_after_mma) {
+  return c->oz ? gram_oz_run(c->oz, c->status, c->st, ev_after_mma)
+               : gram_tc_run(c->gram, c->status, c->st, ev_after_mma);
+}
 
 template <typename T>
 dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const double* target, dngd_step_info* info) {
@@ -354,49 +363,17 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
                                       cudaMemcpyDeviceToDevice, c->st));
     evrec(c, 2);
     if ((s = cholesky<double>(m, (double*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
+    if ((s = trtri_diag64(m, (const double*)c->K, c->ldk, c->Dinv, c->st))) return s;
   } else {
     // low-precision Gram + FP32 factor of K + (lambda + mu) I; a failed
     // factorisation is retried with a larger shift mu (it only preconditions
     // the refinement, whose operator keeps the exact lambda)
-    if (c->prec == DNGD_MIXED_OZ) {
-      // exact Gram, FP64 factor; a (rare) failed factorisation is retried
-      // with a shift from the partial tiles (only the reduction re-runs)
-      double mu = c->desc.shift_mu;
-      gram_oz_set_shift(c->oz, c->lambda + mu);
-      if ((s = gram_oz_run(c->oz, c->status, c->st, c->timing ? c->ev[8] : nullptr))) return s;
-      if (c->Kcopy)
-        DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(double) * (size_t)m * c->ldk,
-                                        cudaMemcpyDeviceToDevice, c->st));
-      if (!c->async) {
-        if ((s = diag_sum<double>(m, (const double*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
-      }
-      evrec(c, 2);
-      c->factor_attempts = 0;
-      for (int attempt = 0;; ++attempt) {
-        c->factor_attempts++;
-        if ((s = cholesky<double>(m, (double*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
-        if (c->async) break;
-        const dngd_status fs = read_status(c);
-        if (fs != DNGD_ERR_NOT_SPD || attempt >= 15) break;
-        DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
-        DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
-        const double tr = c->scal_h[S_TRACE] - m * c->lambda;
-        const double base = 1e-13 * (tr > 0 ? tr : 1.0) / m;
-        mu = mu * 3.0 > base ? mu * 3.0 : base;
-        gram_oz_set_shift(c->oz, c->lambda + mu);
-        if ((s = gram_oz_reduce(c->oz, c->st))) return s;
-        DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
-      }
-      c->shift_used = mu;
-      if ((s = trtri_diag64(m, (const double*)c->K, c->ldk, c->Dinv, c->st))) return s;
-      if (c->async) goto factored;
-    } else {
     double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
     if (c->async) {
       // no host round trip: one factorisation with the shift of the last
       // synchronous step; a failure is reported by the status word
-      gram_tc_set_shift(c->gram, c->lambda + mu);
-      if ((s = gram_tc_run(c->gram, c->status, c->st, nullptr))) return s;
+      gram_set_shift(c, c->lambda + mu);
+      if ((s = gram_run(c, nullptr))) return s;
       DNGD_CUDA_CHECK(cudaMemsetAsync(c->Linv, 0, sizeof(float) * (size_t)m * c->ldk, c->st));
       if ((s = cholesky_f32_inv(m, (float*)c->K, c->ldk, c->Linv, c->ldk, c->status, c->st))) return s;
       if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
@@ -404,8 +381,8 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
       c->factor_attempts = 1;
       goto factored;
     }
-    gram_tc_set_shift(c->gram, c->lambda + mu);
-    if ((s = gram_tc_run(c->gram, c->status, c->st, c->timing ? c->ev[8] : nullptr))) return s;
+    gram_set_shift(c, c->lambda + mu);
+    if ((s = gram_run(c, c->timing ? c->ev[8] : nullptr))) return s;
     // K0 = K + (lambda + mu0) I is kept, so a failed factorisation is retried
     // from the copy with a larger shift instead of recomputing the Gram
     DNGD_CUDA_CHECK(cudaMemcpyAsync(c->K0, c->K, sizeof(float) * (size_t)m * c->ldk, cudaMemcpyDeviceToDevice,
@@ -440,7 +417,6 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     c->mu_sticky = mu;
     c->shift_used = mu;
     if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
-    }
   }
   // a failed factorisation stops the (synchronous) step here
   if (!c->async && (s = read_status(c))) return s;
@@ -834,19 +810,20 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   add(3 * rowbuf);        // H3b
   add(es * (size_t)m * c->ldJ);
   if (bf) add(sizeof(__nv_bfloat16) * (size_t)m * c->ldb);
-  const size_t ks = oz ? sizeof(double) : es;     // K element
-  add(ks * (size_t)m * c->ldk);
-  if (c->desc.keep_gram) add(ks * (size_t)m * c->ldk);
-  if (oz) {
-    add(gram_oz_slice_bytes(m, (int)n));
-    add(gram_oz_partial_bytes(m, (int)n));
-    add(sizeof(double) * (size_t)cdiv(m, 64) * 64 * 64);   // Dinv
-    add(sizeof(double) * 2 * (size_t)m);                   // triangular-solve work
-  } else if (!f64) {
+  add(es * (size_t)m * c->ldk);
+  if (c->desc.keep_gram) add(es * (size_t)m * c->ldk);
+  if (f64) add(sizeof(double) * ((size_t)cdiv(m, 64) * 64 * 64 + 2 * (size_t)m));   // Dinv, tw
+  if (!f64) {
     add(es * (size_t)m * c->ldk);                 // K0
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
     add(sizeof(float) * (size_t)m * m);           // trtri work
-    add(gram_tc_partial_bytes(m, (int)n));
+    if (oz) {
+      add(sizeof(double) * (size_t)m * c->ldk);   // K64
+      add(gram_oz_slice_bytes(m, (int)n));
+      add(gram_oz_partial_bytes(m, (int)n));
+    } else {
+      add(gram_tc_partial_bytes(m, (int)n));
+    }
   }
   add(sizeof(double) * m * 4 + sizeof(double) * n * 3);
   add(sizeof(double) * m * 6 + sizeof(double) * n);
@@ -890,6 +867,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->J, double, (size_t)m * c->ldJ);
     A_(c->K, double, (size_t)m * c->ldk);
     if (c->desc.keep_gram) A_(c->Kcopy, double, (size_t)m * c->ldk);
+    A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
+    A_(c->tw, double, 2 * (size_t)m);
   } else {
     A_(c->Hbar, float, rb);
     A_(c->Z3, float, 3 * rb);
@@ -901,20 +880,17 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       A_(c->Jb, __nv_bfloat16, (size_t)m * c->ldb);
       DNGD_CUDA_CHECK(cudaMemset(c->Jb, 0, sizeof(__nv_bfloat16) * (size_t)m * c->ldb));
     }
+    A_(c->K, float, (size_t)m * c->ldk);
+    A_(c->K0, float, (size_t)m * c->ldk);
+    if (c->desc.keep_gram) A_(c->Kcopy, float, (size_t)m * c->ldk);
+    A_(c->Linv, float, (size_t)m * c->ldk);
+    A_(c->trtri_work, float, (size_t)m * m);
     if (oz) {
-      A_(c->K, double, (size_t)m * c->ldk);
-      if (c->desc.keep_gram) A_(c->Kcopy, double, (size_t)m * c->ldk);
+      A_(c->K64, double, (size_t)m * c->ldk);
       A_(c->oz_slices, unsigned char, gram_oz_slice_bytes(m, (int)n));
       c->gram_partial_bytes = gram_oz_partial_bytes(m, (int)n);
       A_(c->oz_partials, double, c->gram_partial_bytes / sizeof(double));
-      A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
-      A_(c->tw, double, 2 * (size_t)m);
     } else {
-      A_(c->K, float, (size_t)m * c->ldk);
-      A_(c->K0, float, (size_t)m * c->ldk);
-      if (c->desc.keep_gram) A_(c->Kcopy, float, (size_t)m * c->ldk);
-      A_(c->Linv, float, (size_t)m * c->ldk);
-      A_(c->trtri_work, float, (size_t)m * m);
       c->gram_partial_bytes = gram_tc_partial_bytes(m, (int)n);
       A_(c->gram_partials, float, c->gram_partial_bytes / sizeof(float));
     }
@@ -945,8 +921,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   DNGD_CUDA_CHECK(cudaMallocHost(&c->scal_h, sizeof(double) * S_COUNT));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->status_h, sizeof(int) * 4));
   if (oz) {
-    s = gram_oz_plan(&c->oz, (const float*)c->J, c->ldJ, m, (int)n, c->oz_slices, (double*)c->K, c->ldk,
-                     c->oz_partials, c->gram_partial_bytes);
+    s = gram_oz_plan(&c->oz, (const float*)c->J, c->ldJ, m, (int)n, c->oz_slices, (float*)c->K, c->ldk, c->K64,
+                     c->ldk, c->oz_partials, c->gram_partial_bytes);
     if (s) return s;
   } else if (!f64) {
     const void* Jlow = bf ? (const void*)c->Jb : (const void*)c->J;
@@ -1259,7 +1235,7 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
     case 7: {
       const void* src = which == 6 ? c->Kcopy : c->K;
       if (!src) return DNGD_ERR_STATE;
-      const bool k64 = c->prec == DNGD_FP64 || c->prec == DNGD_MIXED_OZ;
+      const bool k64 = c->prec == DNGD_FP64;
       if (which == 7 && !k64) return DNGD_ERR_STATE;
       double* buf = nullptr;
       if (cudaMalloc(&buf, sizeof(double) * (size_t)m * m) != cudaSuccess) return DNGD_ERR_OOM;
@@ -1284,6 +1260,14 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
       }
       cudaFree(buf);
       return s;
+    }
+    case 9: {
+      // the exact FP64 Gram (MIXED_OZ), full symmetric, no shift
+      if (!c->K64) return DNGD_ERR_STATE;
+      DNGD_CUDA_CHECK(cudaMemcpy2DAsync(dst, sizeof(double) * m, c->K64, sizeof(double) * c->ldk,
+                                        sizeof(double) * m, m, cudaMemcpyDefault, c->st));
+      DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+      return DNGD_OK;
     }
     default: return DNGD_ERR_INVALID_ARG;
   }

@@ -3,9 +3,11 @@
 // The dual solve needs K accurate to far below lambda: at lambda = 1e-5 and
 // ||K|| ~ 1e4 (Sec. 3.1's K + lambda I, with cond ~ 1e9 late in training) a
 // BF16 or FP32 Gram is indefinite at the lambda scale, and only an exact
-// Gram factored in FP64 makes the refinement converge in one iteration.
-// GB300's FP64 rate is ~1 TFLOP/s, so the Gram is built from exact integer
-// products instead (an error-free splitting in the spirit of Ozaki et al.):
+// Gram factored in FP64 makes the refinement converge in one iteration; with
+// an exact FP64 Gram the refinement operator is also one m x m GEMV instead
+// of two GEMVs over J.  GB300's FP64 rate is ~1 TFLOP/s, so the Gram is
+// built from exact integer products (an error-free splitting in the spirit
+// of Ozaki et al.):
 //
 //   * each row i of J is scaled by 2^-E_i (E_i = exponent of the row's
 //     largest entry, plus one) and split into four signed 8-bit integers,
@@ -28,7 +30,9 @@
 // tcgen05.mma (M = N = 128) into one of two TMEM buffers per chunk; warps
 // 2..9 drain finished chunks (warp w: TMEM lanes 32 (w % 4).., 64 columns).
 // Split-K partial tiles (FP64) are summed in a fixed order by the reduction,
-// which also applies the row scales and the diagonal shift.  Every wait is
+// which applies the row scales and writes the full FP64 Gram (the
+// refinement operator) and its FP32 lower triangle plus the diagonal shift
+// (the matrix the FP32 preconditioner factors).  Every wait is
 // bounded (ST_TIMEOUT, drain, free TMEM).
 #include <cuda_bf16.h>
 
@@ -309,20 +313,42 @@ k_gram_oz(const __grid_constant__ CUtensorMap map, const int2* __restrict__ tile
   }
 }
 
-// K[i,j] (j <= i) = 2^(E_i+E_j-48) sum_s P_s[i,j] (+ shift on the diagonal);
-// the upper triangle is set to 0.
-__global__ void k_oz_reduce(int m, int nsplit, const double* __restrict__ P, long long ldp, long long sstride,
-                            const int* __restrict__ rowexp, double shift, double* __restrict__ K, long long ldk) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)m * m) return;
-  const int i = (int)(idx / m), j = (int)(idx % m);
-  double v = 0.0;
-  if (j <= i) {
-    for (int s = 0; s < nsplit; ++s) v += P[(long long)s * sstride + (long long)i * ldp + j];
-    v = ldexp(v, rowexp[i] + rowexp[j] - 48);
-    if (i == j) v += shift;
+// Blocks of 32 x 32 entries (bj <= bi): sum the split partials once, scale
+// by 2^(E_i+E_j-48), write the full symmetric FP64 Gram F (both the block
+// and its mirror, through shared memory) and the FP32 lower triangle K with
+// the diagonal shift (its upper triangle zeroed) for the FP32 factorisation.
+__global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const double* __restrict__ P, long long ldp,
+                                                   long long sstride, const int* __restrict__ rowexp, double shift,
+                                                   float* __restrict__ K, long long ldk, double* __restrict__ F,
+                                                   long long ldf) {
+  __shared__ double t[32][33];
+  const int b = blockIdx.x;
+  int bi = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+  while ((bi + 1) * (bi + 2) / 2 <= b) ++bi;
+  while (bi * (bi + 1) / 2 > b) --bi;
+  const int bj = b - bi * (bi + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi * 32 + r, j = bj * 32 + tx;
+    double v = 0.0;
+    if (i < m && j < m && j <= i) {
+      for (int sp = 0; sp < nsplit; ++sp) v += P[(long long)sp * sstride + (long long)i * ldp + j];
+      v = ldexp(v, rowexp[i] + rowexp[j] - 48);
+    }
+    t[r][tx] = v;
+    if (i < m && j < m) {
+      if (j <= i) F[(long long)i * ldf + j] = v;
+      K[(long long)i * ldk + j] = (j <= i) ? (float)(i == j ? v + shift : v) : 0.f;
+    }
   }
-  K[(long long)i * ldk + j] = v;
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bj * 32 + r, j = bi * 32 + tx;   // mirrored block, j > i
+    if (i < m && j < m && j > i) {
+      F[(long long)i * ldf + j] = t[tx][r];
+      if (bi != bj) K[(long long)i * ldk + j] = 0.f;
+    }
+  }
 }
 
 int oz_splits(int ntiles, int num_kblk, int nsm) {
@@ -359,8 +385,10 @@ struct OzPlan {
   int ntiles = 0, nsplit = 1, num_kblk = 0;
   double* partials = nullptr;
   long long ldp = 0, sstride = 0;
-  double* K;
+  float* K;          // FP32 lower + shift (factorisation)
   long long ldk;
+  double* F;         // FP64 full symmetric (refinement operator)
+  long long ldf;
   double shift = 0.0;
 };
 
@@ -378,8 +406,8 @@ size_t gram_oz_slice_bytes(int m, int n) {
   return (size_t)m * NS * ldb * sizeof(__nv_bfloat16) + (size_t)m * sizeof(int) + 256;
 }
 
-dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int n, void* slices, double* K,
-                         long long ldk, double* partials, size_t partial_bytes) {
+dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int n, void* slices, float* K,
+                         long long ldk, double* F, long long ldf, double* partials, size_t partial_bytes) {
   EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
   if (!enc) return DNGD_ERR_CUDA;
   OzPlan* p = new OzPlan();
@@ -393,6 +421,8 @@ dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int
   p->rowexp = (int*)((char*)slices + (size_t)m * p->ldS * sizeof(__nv_bfloat16));
   p->K = K;
   p->ldk = ldk;
+  p->F = F;
+  p->ldf = ldf;
   p->num_kblk = p->ldb / 64;
   cuuint64_t gdim[2] = {(cuuint64_t)p->ldS, (cuuint64_t)m};
   cuuint64_t gstride[1] = {(cuuint64_t)(p->ldS * 2)};
@@ -456,10 +486,10 @@ dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_
 // Re-run only the reduction (e.g. with a new shift): the partial tiles of
 // the last run stay valid.
 dngd_status gram_oz_reduce(OzPlan* p, cudaStream_t st) {
-  const long long tot = (long long)p->m * p->m;
+  const int nb = (p->m + 31) / 32;
   DNGD_NOTE_LAUNCH();
-  k_oz_reduce<<<(int)((tot + 255) / 256), 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->rowexp,
-                                                        p->shift, p->K, p->ldk);
+  k_oz_reduce<<<nb * (nb + 1) / 2, 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->rowexp,
+                                                 p->shift, p->K, p->ldk, p->F, p->ldf);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }

@@ -75,8 +75,9 @@ dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const dou
 struct OzPlan;
 size_t gram_oz_partial_bytes(int m, int n);
 size_t gram_oz_slice_bytes(int m, int n);   // slices + row exponents
-dngd_status gram_oz_plan(OzPlan** plan, const float* J, long long ldJ, int m, int n, void* slices, double* K,
-                         long long ldk, double* partials, size_t partial_bytes);
+// K: FP32 lower triangle + shift; F: full symmetric FP64 Gram (no shift)
+dngd_status gram_oz_plan(OzPlan** plan, const float* J, long long ldJ, int m, int n, void* slices, float* K,
+                         long long ldk, double* F, long long ldf, double* partials, size_t partial_bytes);
 dngd_status gram_oz_set_shift(OzPlan* plan, double shift);
 dngd_status gram_oz_run(OzPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
 dngd_status gram_oz_reduce(OzPlan* plan, cudaStream_t st);
@@ -125,10 +126,9 @@ struct PcgMixed {
   double* scal_h;                     // pinned host copy
   cudaEvent_t* ev;                    // optional: 4 events bracketing the first
                                       // J^T p and J u launches of the solve
-  // FP64 factor preconditioner (exact-Gram mode): M^{-1} = (L L^T)^{-1}
-  const double* L64 = nullptr;
-  const double* Dinv = nullptr;
-  double* tw = nullptr;               // [2 m] triangular-solve work
+  // exact-Gram mode: operator A = K64 (full symmetric FP64 Gram, one GEMV)
+  const double* K64 = nullptr;
+  long long ldk64 = 0;
 };
 // async: enqueue exactly maxit iterations (kernels become no-ops after
 // convergence) and never synchronise; iters/relres are then left untouched and

@@ -146,6 +146,57 @@ __global__ void __launch_bounds__(256) k_gemv_n_f32(int m, int n, const float* _
   }
 }
 
+// FP64 matrix: y[r] = sum_c A[r, c] x[c] + add_scale * add[r] for 4 rows per
+// block, optionally dotp[block] = sum_r dotw[r] y[r].
+__global__ void __launch_bounds__(256) k_gemv_n_f64(int m, int n, const double* __restrict__ A, long long lda,
+                                                     const double* __restrict__ x, const double* __restrict__ add,
+                                                     double add_scale, double* __restrict__ y,
+                                                     const double* __restrict__ dotw, double* __restrict__ dotp,
+                                                     const double* scal) {
+  if (stopped(scal)) return;
+  const int r0 = blockIdx.x * kRows;
+  const int nrow = min(kRows, m - r0);
+  double acc[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) acc[r] = 0.0;
+  for (int c2 = threadIdx.x * 2; c2 < n; c2 += blockDim.x * 2) {
+    const bool pair = c2 + 1 < n;
+    const double x0 = x[c2], x1 = pair ? x[c2 + 1] : 0.0;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      if (r < nrow) {
+        const double* a = A + (long long)(r0 + r) * lda + c2;
+        if (pair) {
+          const double2 v = __ldg(reinterpret_cast<const double2*>(a));
+          acc[r] = fma(v.x, x0, acc[r]);
+          acc[r] = fma(v.y, x1, acc[r]);
+        } else {
+          acc[r] = fma(a[0], x0, acc[r]);
+        }
+      }
+    }
+  }
+  __shared__ double red[kRows][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    const double t = warp_sum(acc[r]);
+    if (lane == 0) red[r][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double d = 0.0;
+    for (int r = 0; r < nrow; ++r) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[r][w];
+      const double yr = t + (add ? add_scale * add[r0 + r] : 0.0);
+      y[r0 + r] = yr;
+      if (dotw) d += dotw[r0 + r] * yr;
+    }
+    if (dotp) dotp[blockIdx.x] = d;
+  }
+}
+
 // Fixed-order reduction of `parts` partial sums by one block of 256 threads.
 __device__ double block_reduce_parts(int parts, const double* __restrict__ p) {
   double s = 0.0;
@@ -301,9 +352,8 @@ dngd_status gemv_n_f32_s(int m, int n, const float* A, long long lda, const doub
   return DNGD_OK;
 }
 
-// z = Linv^T (Linv q), or z = (L L^T)^{-1} q with the FP64 factor
+// z = Linv^T (Linv q)
 dngd_status precond(const PcgMixed& P, const double* q, double* z, cudaStream_t st) {
-  if (P.L64) return chol_solve_f64_dinv(P.m, P.L64, P.ldk, P.Dinv, q, z, P.tw, P.tw + P.m, st);
   dngd_status s = gemv_n_f32_s(P.m, P.m, P.Linv, P.ldk, q, 1.0, P.y, nullptr, 0.0, P.xs, nullptr, nullptr, P.scal,
                                st);
   if (s) return s;
@@ -348,6 +398,13 @@ dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, doubl
   for (;;) {
     const int chunk = check_every > 0 ? check_every : 4;
     for (int k = 0; k < chunk && it < maxit; ++k, ++it) {
+      if (P.K64) {
+        // Ap = K p + lambda p with the exact FP64 Gram, block partials of <p, Ap>
+        DNGD_NOTE_LAUNCH();
+        k_gemv_n_f64<<<cdiv(m, kRows), 256, 0, st>>>(m, m, P.K64, P.ldk64, P.p, P.p, P.lambda, P.Ap, P.p, pap_parts,
+                                                     sc);
+        DNGD_LAUNCH_CHECK();
+      } else {
       // Ap = J (J^T p) + lambda p, with the block partials of <p, Ap>
       const bool tm = P.ev && it == 0;
       if (tm) cudaEventRecord(P.ev[0], st);
@@ -356,6 +413,7 @@ dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, doubl
       if ((s = gemv_n_f32_s(m, P.n, P.J, P.ldJ, P.u, 1.0, P.Ap, P.p, P.lambda, P.xs, P.p, pap_parts, sc, st)))
         return s;
       if (tm) cudaEventRecord(P.ev[2], st);
+      }
       DNGD_NOTE_LAUNCH();
       k_cg_alpha<<<1, 256, 0, st>>>(nAp, pap_parts, sc);
       DNGD_NOTE_LAUNCH();
