@@ -31,6 +31,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D-NGD steps/s mixed vs FP64 at equal step error; Gram TFLOP/s; p99 step latency"
 UNIT = "steps/s"
+DTYPES = {"oz": "bf16 tensor (exact integer slices) / f32 jets and factor / f64 Gram operator",
+          "bf16": "bf16/f32 (double-float accumulation in the refinement)",
+          "tf32": "tf32/f32 (double-float accumulation in the refinement)"}
+L2_NOTE = {"oz": "working set larger than L2 (J: 2.13 GB FP32, slices 4.27 GB BF16, Gram 128 MB FP64 per step)",
+           "bf16": "working set larger than L2 (J: 2.13 GB FP32 + 1.07 GB BF16 per step)",
+           "tf32": "working set larger than L2 (J: 2.13 GB FP32 per step)"}
 WORKLOAD = "poisson5d_dense: -Lap u = f on [0,1]^5, MLP 5-256-256-256-1 (n=133377), 3000+1000 pts (m=4000)"
 
 
@@ -384,7 +390,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lam", type=float, default=1e-5)
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "oz"])
+    ap.add_argument("--precision", default="oz", choices=["oz", "bf16", "tf32"],
+                    help="oz (default): exact Gram from 8-bit slices on BF16 tensor cores, FP32 factor, FP64 Gram "
+                         "operator in the refinement; bf16 / tf32: low-precision Gram, FP32-J operator")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle leg (no step error)")
     ap.add_argument("--no-fp64", action="store_true")
@@ -575,14 +583,34 @@ def main():
     if fp64 is not None:
         err["mixed_vs_fp64_gpu"] = float(np.linalg.norm(d_mixed0 - d64h) / np.linalg.norm(d64h))
 
+    roof_gemv = {"bound": "hbm", "kernel": "k_gemv_t_f32 + k_gemv_n_f32 on the FP32 J (refinement operator / "
+                                           "map-back J^T alpha)",
+                 "achieved": gemv_gbs, "peak": hbm, "unit": "GB/s", "frac": gemv_gbs / hbm,
+                 "bytes_per_launch": gemv_bytes, "launch_ms": [jt_ms, j_ms],
+                 "launches_per_step": 2 * iters_total + 2 if prec != dngd.MIXED_OZ else 2,
+                 "peak_source": f"{src} HBM copy bandwidth (measured)", "traffic": None}
+    if prec == dngd.MIXED_OZ:
+        roof_gram = {"bound": "tensor", "kernel": "k_oz_slice + k_gram_oz (tcgen05 BF16, 13 exact slice products, "
+                                                  "128x96 tiles)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "flops_per_launch": gram_flops, "launch_ms": gram_ms,
+                     "algorithmic": "13 m(m+1)n BF16 tensor flops (the exact Gram's 13 slice products)",
+                     "exact_gram_tflops_fp64_equivalent": gram_flops / 13.0 / (gram_ms * 1e-3) / 1e12,
+                     "peak_source": f"{src} bf16 sustained (measured)", "traffic": None}
+    else:
+        roof_gram = {"bound": "tensor", "kernel": "k_gram_tc (tcgen05 syrk, lower 128x256 tiles)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "flops_per_launch": gram_flops, "launch_ms": gram_ms,
+                     "peak_source": f"{src} bf16 sustained (measured)" + (" / 2 for tf32" if prec == dngd.MIXED_TF32
+                                                                            else ""), "traffic": None}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16/f32 (double-float accumulation in the refinement)",
+        "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == "poisson5d" else args.workload, "lam": args.lam, "precision": f"mixed-{args.precision}",
                    "step": "dngd_step + 31-point line search + update",
-                   "l2": "working set larger than L2 (J: 2.13 GB FP32 + 1.07 GB BF16 per step)",
+                   "l2": L2_NOTE[args.precision],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "gram_tflops": achieved, "fp64": fp64, "step_error": err,
@@ -590,15 +618,8 @@ def main():
         "refine_iters": iters, "phase_ms": phase,
         "per_step": [{"iters": i["solve_iters"], "shift": i["shift_used"], "factor_attempts": i["factor_attempts"],
                       "loss": i["loss"], "ms": float(l)} for i, l in zip(infos, lat)], "ga_accepted_at_theta0": info0["ga_accepted"],
-        "roofline": {"bound": "hbm", "kernel": "k_gemv_t_f32 + k_gemv_n_f32 on the FP32 J (refinement operator)",
-                     "achieved": gemv_gbs, "peak": hbm, "unit": "GB/s", "frac": gemv_gbs / hbm,
-                     "bytes_per_launch": gemv_bytes, "launch_ms": [jt_ms, j_ms],
-                     "launches_per_step": 2 * iters_total + 2,
-                     "peak_source": f"{src} HBM copy bandwidth", "traffic": None},
-        "roofline_gram": {"bound": "tensor", "kernel": "k_gram_tc (tcgen05 BF16 syrk, lower 128x256 tiles)",
-                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                          "flops_per_launch": gram_flops, "launch_ms": gram_ms,
-                          "peak_source": f"{src} bf16 sustained" + (" / 2 for tf32" if prec == dngd.MIXED_TF32 else "")},
+        "roofline": roof_gram if prec == dngd.MIXED_OZ else roof_gemv,
+        "roofline_other": roof_gemv if prec == dngd.MIXED_OZ else roof_gram,
         "cpu_baseline": cpu,
         "e2e": {"value": 1000.0 / e2e_ms * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),

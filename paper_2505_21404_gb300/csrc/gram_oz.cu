@@ -24,16 +24,20 @@
 //     into double-float registers (48-bit significand) with a Horner scaling
 //     by 2^8 between levels.
 //
-// Kernel roles (one 128 x 128 lower output tile and one K range per CTA):
-// warp 0 lane 0 streams 128 x 64 slice tiles of A and B rows with TMA
-// (128-byte swizzle) into a 6-stage ring; warp 1 lane 0 issues
-// tcgen05.mma (M = N = 128) into one of two TMEM buffers per chunk; warps
-// 2..9 drain finished chunks (warp w: TMEM lanes 32 (w % 4).., 64 columns).
+// Kernel roles (one 128 x 96 output tile touching the lower triangle and one
+// K range per CTA): warp 0 lane 0 streams, per 64-wide K block, all four A
+// slices (128 rows) and all four B slices (96 rows) with TMA (128-byte
+// swizzle) into a 2-stage ring of 112 KB stages, so one stage feeds all 13
+// slice products; warp 1 lane 0 issues tcgen05.mma (M = 128, N = 96) into
+// five per-level TMEM accumulators (480 columns) and commits a level every
+// 4 K blocks (the exactness period); warps 2..13 drain a level as soon as it
+// is committed (warp w: TMEM lanes 32 (w % 4).., 32 columns), release it to
+// the MMA warp, and add it times 2^(8(4-g)) into double-float registers.
 // Split-K partial tiles (FP64) are summed in a fixed order by the reduction,
 // which applies the row scales and writes the full FP64 Gram (the
 // refinement operator) and its FP32 lower triangle plus the diagonal shift
-// (the matrix the FP32 preconditioner factors).  Every wait is
-// bounded (ST_TIMEOUT, drain, free TMEM).
+// (the matrix the FP32 preconditioner factors).  Every wait is bounded
+// (ST_TIMEOUT, drain, free TMEM).
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -50,27 +54,24 @@ using namespace tc;
 
 constexpr int NS = 4;                       // slices per value
 constexpr int NG = 5;                       // levels g = s + t <= 4
-constexpr int TB = 128;                     // output tile rows = columns
-constexpr int OST = 6;                      // pipeline stages
-constexpr int OTILE = TB * 128;             // one operand tile (64 bf16 of K), 16 KB
-constexpr int OSTAGE = 2 * OTILE;           // A + B
+constexpr int TM = 128, TN = 96;            // output tile rows x columns
+constexpr int OST = 4;                      // pipeline stages
+constexpr int KS = 32;                      // K per stage (64-byte rows, 64-byte swizzle)
+constexpr int A_TILE = TM * 64;             // 8 KB
+constexpr int B_TILE = TN * 64;             // 6 KB
+constexpr int OSTAGE = NS * (A_TILE + B_TILE);   // 56 KB
 constexpr int OSMEM = OST * OSTAGE + 1024;
-constexpr int OTHREADS = 320;
-// TMEM columns: [0, 256) two 128-column chunk accumulators (MMA), [256, 384)
-// and [384, 512) the hi and lo words of the tile's double-float sum (ten
-// warps share a sub-partition's 16K registers, so the sum cannot stay in
-// registers)
-constexpr uint32_t OTMEM = 512;
-constexpr uint32_t ACC_HI = 256, ACC_LO = 384;
+constexpr int OTHREADS = 448;               // TMA warp, MMA warp, 12 epilogue warps
+constexpr int EPI_WARPS = 12;
+constexpr uint32_t OTMEM = 512;             // five 96-column level accumulators
+constexpr int PERIOD = 8;                   // stages per exact chunk (4 pairs x 8 x 32 x 2^14 = 2^24)
 
 __host__ __device__ __forceinline__ int g_lo(int g) { return g > NS - 1 ? g - (NS - 1) : 0; }
 __host__ __device__ __forceinline__ int g_hi(int g) { return g < NS - 1 ? g : NS - 1; }
-// k blocks per exact chunk: pairs * 64 * kb * 2^14 <= 2^24
-__host__ __device__ __forceinline__ int g_kb(int g) { return 16 / (g_hi(g) - g_lo(g) + 1); }
 
-// BF16 x BF16 -> FP32, both K-major, N = M = 128.
+// BF16 x BF16 -> FP32, both K-major, N = 96, M = 128.
 __device__ __forceinline__ uint32_t oz_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TB >> 3) << 17) | ((uint32_t)(TB >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
 // (hi, lo) += c exactly as long as the sum needs at most ~48 bits.
@@ -121,13 +122,14 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const float* __r
 }
 
 __global__ void __launch_bounds__(OTHREADS, 1)
-k_gram_oz(const __grid_constant__ CUtensorMap map, const int2* __restrict__ tiles, int m, int num_kblk, int ldb,
-          double* __restrict__ out, long long ldo, long long split_stride, int* status) {
+k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+          const int2* __restrict__ tiles, int m, int num_kblk, int ldb, double* __restrict__ out, long long ldo,
+          long long split_stride, int* status) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[OST];
   __shared__ __align__(8) uint64_t empty_bar[OST];
-  __shared__ __align__(8) uint64_t accf_bar[2];
-  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t accf_bar[NG];   // MMA -> epilogue: level g committed
+  __shared__ __align__(8) uint64_t acce_bar[NG];   // epilogue -> MMA: level g drained
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
@@ -138,15 +140,17 @@ k_gram_oz(const __grid_constant__ CUtensorMap map, const int2* __restrict__ tile
   const int kb_per = (num_kblk + nsplit - 1) / nsplit;
   const int kb0 = split * kb_per;
   const int kb1 = min(num_kblk, kb0 + kb_per);
+  const int nk = max(0, kb1 - kb0);
+  const int nper = (nk + PERIOD - 1) / PERIOD;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OST; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&accf_bar[b]), 1);
-      mbar_init(smem_u32(&acce_bar[b]), 8);
+    for (int g = 0; g < NG; ++g) {
+      mbar_init(smem_u32(&accf_bar[g]), 1);
+      mbar_init(smem_u32(&acce_bar[g]), EPI_WARPS);
     }
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -165,77 +169,82 @@ k_gram_oz(const __grid_constant__ CUtensorMap map, const int2* __restrict__ tile
   int issued = 0;
   if (warp == 0) {
     if (lane == 0) {
-      int it = 0;
-      for (int g = 0; g < NG && !*abort_flag; ++g) {
-        for (int kb = kb0; kb < kb1 && !*abort_flag; ++kb) {
-          for (int sa = g_lo(g); sa <= g_hi(g); ++sa, ++it) {
-            const int st = it % OST;
-            const uint32_t ph = (uint32_t)((it / OST) & 1);
-            if (*abort_flag || !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, status, 11)) {
-              *abort_flag = 1;
-              break;
-            }
-            const uint32_t fb = smem_u32(&full_bar[st]);
-            mbar_expect_tx(fb, OSTAGE);
-            const uint32_t sa_addr = smem_base + st * OSTAGE;
-            tma_load_2d(sa_addr, &map, fb, sa * ldb + kb * 64, tile.x * TB);
-            tma_load_2d(sa_addr + OTILE, &map, fb, (g - sa) * ldb + kb * 64, tile.y * TB);
-            ++issued;
-          }
+      for (int it = 0; it < nk; ++it) {
+        const int st = it % OST;
+        const uint32_t ph = (uint32_t)((it / OST) & 1);
+        if (*abort_flag || !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, status, 11)) {
+          *abort_flag = 1;
+          break;
         }
+        const uint32_t fb = smem_u32(&full_bar[st]);
+        mbar_expect_tx(fb, OSTAGE);
+        const uint32_t sbase = smem_base + st * OSTAGE;
+        const int kc = (kb0 + it) * KS;
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) {
+          tma_load_2d(sbase + sl * A_TILE, &mapA, fb, sl * ldb + kc, tile.x * TM);
+          tma_load_2d(sbase + NS * A_TILE + sl * B_TILE, &mapB, fb, sl * ldb + kc, tile.y * TN);
+        }
+        ++issued;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = oz_idesc();
-      int it = 0, c = 0;
-      for (int g = 0; g < NG && !*abort_flag; ++g) {
-        const int ck = g_kb(g);
-        for (int c0 = kb0; c0 < kb1 && !*abort_flag; c0 += ck, ++c) {
-          const int b = c & 1, use = c >> 1;
-          if (!mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)((use & 1) ^ 1), status, 15)) {
-            *abort_flag = 1;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t dbuf = tmem + (uint32_t)(b * TB);
-          bool first = true;
-          const int c1 = min(kb1, c0 + ck);
-          for (int kb = c0; kb < c1 && !*abort_flag; ++kb) {
-            for (int sa = g_lo(g); sa <= g_hi(g); ++sa, ++it) {
-              const int st = it % OST;
-              const uint32_t ph = (uint32_t)((it / OST) & 1);
-              if (*abort_flag || !mbar_wait(smem_u32(&full_bar[st]), ph, status, 12)) {
-                *abort_flag = 1;
-                break;
-              }
-              asm volatile("tcgen05.fence::after_thread_sync;");
-              const uint32_t sa_addr = smem_base + st * OSTAGE;
+      for (int it = 0; it < nk && !*abort_flag; ++it) {
+        const int st = it % OST;
+        const uint32_t ph = (uint32_t)((it / OST) & 1);
+        const int per = it / PERIOD;
+        const bool first = (it % PERIOD) == 0;
+        const bool last = (it % PERIOD) == PERIOD - 1 || it == nk - 1;
+        if (!mbar_wait(smem_u32(&full_bar[st]), ph, status, 12)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sbase = smem_base + st * OSTAGE;
+        // descriptors of the stage's first A and B tiles; the others differ
+        // only in the start-address field (byte offset / 16, no carry out)
+        const uint64_t da0 = sw64_desc(sbase), db0 = sw64_desc(sbase + NS * A_TILE);
 #pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                umma<0>(dbuf, sw128_desc(sa_addr + 32 * k), sw128_desc(sa_addr + OTILE + 32 * k), idesc,
-                        (first && k == 0) ? 0u : 1u);
-              }
-              first = false;
-              umma_commit(smem_u32(&empty_bar[st]));
+        for (int g = 0; g < NG; ++g) {
+          if (first) {
+            // level g's accumulator must have been drained (period per - 1)
+            if (!mbar_wait(smem_u32(&acce_bar[g]), (uint32_t)((per & 1) ^ 1), status, 15)) {
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+          }
+          const uint32_t dbuf = tmem + (uint32_t)(g * TN);
+#pragma unroll
+          for (int sa = g_lo(g); sa <= g_hi(g); ++sa) {
+#pragma unroll
+            for (int k = 0; k < KS / 16; ++k) {
+              umma<0>(dbuf, da0 + (uint64_t)((sa * A_TILE + 32 * k) >> 4),
+                      db0 + (uint64_t)(((g - sa) * B_TILE + 32 * k) >> 4), idesc,
+                      (first && sa == g_lo(g) && k == 0) ? 0u : 1u);
             }
           }
-          umma_commit(smem_u32(&accf_bar[b]));
+          if (last) umma_commit(smem_u32(&accf_bar[g]));
         }
+        umma_commit(smem_u32(&empty_bar[st]));
       }
     }
   } else {
-    const int q = warp & 3;             // TMEM lane quadrant
-    const int h = (warp - 2) >> 2;      // column half (64 columns)
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    int c = 0;
-    for (int g = 0; g < NG && !*abort_flag; ++g) {
-      const int ck = g_kb(g);
-      bool level_start = true;
-      for (int c0 = kb0; c0 < kb1; c0 += ck, ++c) {
-        const int b = c & 1, use = c >> 1;
-        const bool ok = __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&accf_bar[b]),
-                                                                           (uint32_t)(use & 1), status, 13))
+    const int q = warp & 3;             // TMEM lane quadrant this warp may access
+    const int cg = (warp - 2) >> 2;     // column group (32 of the 96 columns)
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * 32);
+    float hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      hi[j] = 0.f;
+      lo[j] = 0.f;
+    }
+    for (int per = 0; per < nper && !*abort_flag; ++per) {
+      for (int g = 0; g < NG; ++g) {
+        const bool ok = __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&accf_bar[g]),
+                                                                           (uint32_t)(per & 1), status, 13))
                                                     ? 1
                                                     : 0) != 0;
         if (!ok) {
@@ -243,58 +252,25 @@ k_gram_oz(const __grid_constant__ CUtensorMap map, const int2* __restrict__ tile
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll 1
-        for (int j2 = 0; j2 < 2; ++j2) {
-          const uint32_t col = (uint32_t)(h * 64 + j2 * 32);
-          uint32_t r[32], hi[32], lo[32];
-          TMEM_LD_32(lane_base + (uint32_t)(b * TB) + col, r);
-          if (c > 0) {
-            TMEM_LD_32(lane_base + ACC_HI + col, hi);
-            TMEM_LD_32(lane_base + ACC_LO + col, lo);
-          }
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          // Horner step between levels: the sum so far times 2^8 (exact)
-          const float sc = (level_start && g > 0) ? 256.f : 1.f;
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            float a = c > 0 ? __uint_as_float(hi[i]) * sc : 0.f;
-            float l = c > 0 ? __uint_as_float(lo[i]) * sc : 0.f;
-            df_add_exact(a, l, __uint_as_float(r[i]));
-            hi[i] = __float_as_uint(a);
-            lo[i] = __float_as_uint(l);
-          }
-          TMEM_ST_32(lane_base + ACC_HI + col, hi);
-          TMEM_ST_32(lane_base + ACC_LO + col, lo);
-          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        }
-        level_start = false;
+        uint32_t r[32];
+        TMEM_LD_32(lane_base + (uint32_t)(g * TN), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[b])) : "memory");
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[g])) : "memory");
+        // the level's exact chunk times 2^(8 (4 - g)) (a power of two: exact)
+        const float sc = __int_as_float((127 + 8 * (NG - 1 - g)) << 23);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) df_add_exact(hi[i], lo[i], __uint_as_float(r[i]) * sc);
       }
     }
-    const int row = tile.x * TB + q * 32 + lane;
-    const int col0 = tile.y * TB + h * 64;
-    if (!*abort_flag) {
-#pragma unroll 1
-      for (int j2 = 0; j2 < 2; ++j2) {
-        uint32_t hi[32], lo[32];
-        const uint32_t col = (uint32_t)(h * 64 + j2 * 32);
-        if (c > 0) {
-          TMEM_LD_32(lane_base + ACC_HI + col, hi);
-          TMEM_LD_32(lane_base + ACC_LO + col, lo);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        } else {
+    const int row = tile.x * TM + q * 32 + lane;
+    const int col0 = tile.y * TN + cg * 32;
+    if (row < m && !*abort_flag) {
+      double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0u;
-        }
-        if (row < m) {
-          double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0 + j2 * 32;
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (col0 + j2 * 32 + i < m) orow[i] = (double)__uint_as_float(hi[i]) + (double)__uint_as_float(lo[i]);
-        }
-      }
+      for (int j = 0; j < 32; ++j)
+        if (col0 + j < m) orow[j] = (double)hi[j] + (double)lo[j];
     }
   }
   __syncwarp();
@@ -367,10 +343,17 @@ int oz_splits(int ntiles, int num_kblk, int nsm) {
   return best;
 }
 
-int oz_ntiles(int m) {
-  const int nI = (m + TB - 1) / TB;
-  return nI * (nI + 1) / 2;
+// Output tiles (I: 128-row block, J: 96-column block) touching the lower
+// triangle; partial tiles are stored [split][mp rows][lp columns].
+std::vector<int2> oz_tiles(int m) {
+  std::vector<int2> t;
+  const int nI = (m + TM - 1) / TM, nJ = (m + TN - 1) / TN;
+  for (int I = 0; I < nI; ++I)
+    for (int Jc = 0; Jc < nJ && Jc * TN <= I * TM + TM - 1; ++Jc) t.push_back(make_int2(I, Jc));
+  return t;
 }
+long long oz_mp(int m) { return (long long)((m + TM - 1) / TM) * TM; }
+long long oz_lp(int m) { return (long long)((m + TN - 1) / TN) * TN; }
 
 }  // namespace
 
@@ -380,7 +363,7 @@ struct OzPlan {
   const float* J;
   __nv_bfloat16* S;
   int* rowexp;
-  CUtensorMap map;
+  CUtensorMap mapA, mapB;
   int2* d_tiles = nullptr;
   int ntiles = 0, nsplit = 1, num_kblk = 0;
   double* partials = nullptr;
@@ -396,9 +379,8 @@ size_t gram_oz_partial_bytes(int m, int n) {
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int nsplit = oz_splits(oz_ntiles(m), (n + 63) / 64, nsm);
-  const long long mp = (long long)((m + TB - 1) / TB) * TB;
-  return (size_t)nsplit * mp * mp * sizeof(double);
+  const int nsplit = oz_splits((int)oz_tiles(m).size(), (n + KS - 1) / KS, nsm);
+  return (size_t)nsplit * oz_mp(m) * oz_lp(m) * sizeof(double);
 }
 
 size_t gram_oz_slice_bytes(int m, int n) {
@@ -423,29 +405,29 @@ dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int
   p->ldk = ldk;
   p->F = F;
   p->ldf = ldf;
-  p->num_kblk = p->ldb / 64;
+  p->num_kblk = p->ldb / KS;   // K stages
   cuuint64_t gdim[2] = {(cuuint64_t)p->ldS, (cuuint64_t)m};
   cuuint64_t gstride[1] = {(cuuint64_t)(p->ldS * 2)};
   cuuint32_t estride[2] = {1, 1};
-  cuuint32_t box[2] = {64, (cuuint32_t)TB};
-  if (enc(&p->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S, gdim, gstride, box, estride,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  cuuint32_t boxA[2] = {(cuuint32_t)KS, (cuuint32_t)TM};
+  cuuint32_t boxB[2] = {(cuuint32_t)KS, (cuuint32_t)TN};
+  if (enc(&p->mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S, gdim, gstride, boxA, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&p->mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S, gdim, gstride, boxB, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
     delete p;
     return DNGD_ERR_CUDA;
   }
-  std::vector<int2> tiles;
-  const int nI = (m + TB - 1) / TB;
-  for (int I = 0; I < nI; ++I)
-    for (int Jc = 0; Jc <= I; ++Jc) tiles.push_back(make_int2(I, Jc));
+  std::vector<int2> tiles = oz_tiles(m);
   p->ntiles = (int)tiles.size();
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   p->nsplit = oz_splits(p->ntiles, p->num_kblk, nsm);
-  const long long mp = (long long)nI * TB;
-  p->ldp = mp;
-  p->sstride = mp * mp;
+  p->ldp = oz_lp(m);
+  p->sstride = oz_mp(m) * p->ldp;
   if ((size_t)p->nsplit * p->sstride * sizeof(double) > partial_bytes) p->nsplit = 1;
   if ((size_t)p->sstride * sizeof(double) > partial_bytes) {
     delete p;
@@ -476,7 +458,8 @@ dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_
   k_oz_slice<<<p->m, 256, 0, st>>>(p->m, p->n, p->J, p->ldJ, p->S, p->ldS, p->ldb, p->rowexp);
   DNGD_LAUNCH_CHECK();
   DNGD_NOTE_LAUNCH();
-  k_gram_oz<<<dim3(p->ntiles, p->nsplit), OTHREADS, OSMEM, st>>>(p->map, p->d_tiles, p->m, p->num_kblk, p->ldb,
+  k_gram_oz<<<dim3(p->ntiles, p->nsplit), OTHREADS, OSMEM, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk,
+                                                                  p->ldb,
                                                                   p->partials, p->ldp, p->sstride, status);
   DNGD_LAUNCH_CHECK();
   if (ev_after_mma) cudaEventRecord(ev_after_mma, st);
