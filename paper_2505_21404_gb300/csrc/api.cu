@@ -57,7 +57,7 @@ struct dngd_ctx {
   OzPlan* oz = nullptr;       // exact-Gram mode
   void* oz_slices = nullptr;
   double* oz_partials = nullptr;
-  double* K64 = nullptr;      // exact FP64 Gram (full symmetric, no shift)
+  float2* K64 = nullptr;      // exact Gram as double-float pairs (full symmetric, no shift)
   double* Dinv = nullptr;     // FP64 path: inverses of the factor's 64 x 64 diagonal blocks
   double* tw = nullptr;       // FP64 path: [2 m] triangular-solve work
   float* gram_partials = nullptr;
@@ -818,7 +818,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
     add(sizeof(float) * (size_t)m * m);           // trtri work
     if (oz) {
-      add(sizeof(double) * (size_t)m * c->ldk);   // K64
+      add(sizeof(float2) * (size_t)m * c->ldk);   // K64
       add(gram_oz_slice_bytes(m, (int)n));
       add(gram_oz_partial_bytes(m, (int)n));
     } else {
@@ -886,7 +886,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->Linv, float, (size_t)m * c->ldk);
     A_(c->trtri_work, float, (size_t)m * m);
     if (oz) {
-      A_(c->K64, double, (size_t)m * c->ldk);
+      A_(c->K64, float2, (size_t)m * c->ldk);
       A_(c->oz_slices, unsigned char, gram_oz_slice_bytes(m, (int)n));
       c->gram_partial_bytes = gram_oz_partial_bytes(m, (int)n);
       A_(c->oz_partials, double, c->gram_partial_bytes / sizeof(double));
@@ -1263,11 +1263,17 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
     }
     case 9: {
       // the exact FP64 Gram (MIXED_OZ), full symmetric, no shift
-      if (!c->K64) return DNGD_ERR_STATE;
-      DNGD_CUDA_CHECK(cudaMemcpy2DAsync(dst, sizeof(double) * m, c->K64, sizeof(double) * c->ldk,
-                                        sizeof(double) * m, m, cudaMemcpyDefault, c->st));
-      DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
-      return DNGD_OK;
+      if (!c->oz) return DNGD_ERR_STATE;
+      double* buf = nullptr;
+      if (cudaMalloc(&buf, sizeof(double) * (size_t)m * c->ldk) != cudaSuccess) return DNGD_ERR_OOM;
+      dngd_status s = gram_oz_read(c->oz, buf, c->st);
+      if (!s) {
+        cudaMemcpy2DAsync(dst, sizeof(double) * m, buf, sizeof(double) * c->ldk, sizeof(double) * m, m,
+                          cudaMemcpyDefault, c->st);
+        cudaStreamSynchronize(c->st);
+      }
+      cudaFree(buf);
+      return s;
     }
     default: return DNGD_ERR_INVALID_ARG;
   }

@@ -85,14 +85,19 @@ __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
   hi = t;
 }
 
-// Row scaling and slicing: one block per row.
+// Row scaling and slicing: one block per row, float4 loads and 8-byte
+// stores (ldJ and ldb are multiples of 4; the row's pad columns are zero).
 __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const float* __restrict__ J, long long ldJ,
                                                   __nv_bfloat16* __restrict__ S, long long ldS, int ldb,
                                                   int* __restrict__ rowexp) {
   const int i = blockIdx.x;
-  const float* row = J + (long long)i * ldJ;
+  const float4* row = reinterpret_cast<const float4*>(J + (long long)i * ldJ);
+  const int n4 = (n + 3) / 4, b4 = ldb / 4;
   float amax = 0.f;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) amax = fmaxf(amax, fabsf(row[k]));
+  for (int k = threadIdx.x; k < n4; k += blockDim.x) {
+    const float4 v = __ldg(row + k);
+    amax = fmaxf(fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y))), fmaxf(fabsf(v.z), fabsf(v.w)));
+  }
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   __shared__ float red[8];
   __shared__ int E_sh;
@@ -109,14 +114,30 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const float* __r
   __syncthreads();
   const int E = E_sh;
   __nv_bfloat16* srow = S + (long long)i * ldS;
-  for (int k = threadIdx.x; k < ldb; k += blockDim.x) {
-    float x = k < n ? ldexpf(row[k], -E) : 0.f;
+  for (int k = threadIdx.x; k < b4; k += blockDim.x) {
+    float x[4];
+    if (k < n4) {
+      const float4 v = __ldg(row + k);
+      x[0] = v.x;
+      x[1] = v.y;
+      x[2] = v.z;
+      x[3] = v.w;
+    } else {
+      x[0] = x[1] = x[2] = x[3] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = (4 * k + c < n) ? ldexpf(x[c], -E) : 0.f;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const float t = x * 256.f;
-      const float sg = rintf(t);
-      x = t - sg;
-      srow[(long long)s * ldb + k] = __float2bfloat16_rn(sg);
+      __nv_bfloat16 q[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float t = x[c] * 256.f;
+        const float sg = rintf(t);
+        x[c] = t - sg;
+        q[c] = __float2bfloat16_rn(sg);
+      }
+      *reinterpret_cast<uint2*>(srow + (long long)s * ldb + 4 * k) = *reinterpret_cast<const uint2*>(q);
     }
   }
 }
@@ -289,13 +310,24 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   }
 }
 
+// v as an unevaluated sum of two floats (48 significant bits)
+__device__ __forceinline__ float2 df_split(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+__global__ void k_df_to_double(long long cnt, const float2* __restrict__ F, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) out[i] = (double)F[i].x + (double)F[i].y;
+}
+
 // Blocks of 32 x 32 entries (bj <= bi): sum the split partials once, scale
-// by 2^(E_i+E_j-48), write the full symmetric FP64 Gram F (both the block
+// by 2^(E_i+E_j-48), write the full symmetric double-float Gram F (both the block
 // and its mirror, through shared memory) and the FP32 lower triangle K with
 // the diagonal shift (its upper triangle zeroed) for the FP32 factorisation.
 __global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const double* __restrict__ P, long long ldp,
                                                    long long sstride, const int* __restrict__ rowexp, double shift,
-                                                   float* __restrict__ K, long long ldk, double* __restrict__ F,
+                                                   float* __restrict__ K, long long ldk, float2* __restrict__ F,
                                                    long long ldf) {
   __shared__ double t[32][33];
   const int b = blockIdx.x;
@@ -313,7 +345,7 @@ __global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const doub
     }
     t[r][tx] = v;
     if (i < m && j < m) {
-      if (j <= i) F[(long long)i * ldf + j] = v;
+      if (j <= i) F[(long long)i * ldf + j] = df_split(v);
       K[(long long)i * ldk + j] = (j <= i) ? (float)(i == j ? v + shift : v) : 0.f;
     }
   }
@@ -321,7 +353,7 @@ __global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const doub
   for (int r = ty; r < 32; r += 8) {
     const int i = bj * 32 + r, j = bi * 32 + tx;   // mirrored block, j > i
     if (i < m && j < m && j > i) {
-      F[(long long)i * ldf + j] = t[tx][r];
+      F[(long long)i * ldf + j] = df_split(t[tx][r]);
       if (bi != bj) K[(long long)i * ldk + j] = 0.f;
     }
   }
@@ -370,7 +402,7 @@ struct OzPlan {
   long long ldp = 0, sstride = 0;
   float* K;          // FP32 lower + shift (factorisation)
   long long ldk;
-  double* F;         // FP64 full symmetric (refinement operator)
+  float2* F;         // double-float full symmetric (refinement operator)
   long long ldf;
   double shift = 0.0;
 };
@@ -389,7 +421,7 @@ size_t gram_oz_slice_bytes(int m, int n) {
 }
 
 dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int n, void* slices, float* K,
-                         long long ldk, double* F, long long ldf, double* partials, size_t partial_bytes) {
+                         long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes) {
   EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
   if (!enc) return DNGD_ERR_CUDA;
   OzPlan* p = new OzPlan();
@@ -473,6 +505,15 @@ dngd_status gram_oz_reduce(OzPlan* p, cudaStream_t st) {
   DNGD_NOTE_LAUNCH();
   k_oz_reduce<<<nb * (nb + 1) / 2, 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->rowexp,
                                                  p->shift, p->K, p->ldk, p->F, p->ldf);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// The exact Gram (rows of ldf float2) as FP64 [m x m] row-major on the device.
+dngd_status gram_oz_read(const OzPlan* p, double* out, cudaStream_t st) {
+  const long long cnt = (long long)p->m * p->ldf;
+  DNGD_NOTE_LAUNCH();
+  k_df_to_double<<<(int)((cnt + 255) / 256), 256, 0, st>>>(cnt, p->F, out);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }

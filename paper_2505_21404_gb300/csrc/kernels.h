@@ -75,9 +75,11 @@ dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const dou
 struct OzPlan;
 size_t gram_oz_partial_bytes(int m, int n);
 size_t gram_oz_slice_bytes(int m, int n);   // slices + row exponents
-// K: FP32 lower triangle + shift; F: full symmetric FP64 Gram (no shift)
+// K: FP32 lower triangle + shift; F: full symmetric Gram as double-float
+// pairs (no shift)
 dngd_status gram_oz_plan(OzPlan** plan, const float* J, long long ldJ, int m, int n, void* slices, float* K,
-                         long long ldk, double* F, long long ldf, double* partials, size_t partial_bytes);
+                         long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes);
+dngd_status gram_oz_read(const OzPlan* plan, double* out, cudaStream_t st);  // F as FP64 [m x ldf]
 dngd_status gram_oz_set_shift(OzPlan* plan, double shift);
 dngd_status gram_oz_run(OzPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
 dngd_status gram_oz_reduce(OzPlan* plan, cudaStream_t st);
@@ -126,8 +128,8 @@ struct PcgMixed {
   double* scal_h;                     // pinned host copy
   cudaEvent_t* ev;                    // optional: 4 events bracketing the first
                                       // J^T p and J u launches of the solve
-  // exact-Gram mode: operator A = K64 (full symmetric FP64 Gram, one GEMV)
-  const double* K64 = nullptr;
+  // exact-Gram mode: operator A = K64 (full symmetric double-float Gram, one GEMV)
+  const float2* K64 = nullptr;
   long long ldk64 = 0;
 };
 // async: enqueue exactly maxit iterations (kernels become no-ops after

@@ -146,33 +146,40 @@ __global__ void __launch_bounds__(256) k_gemv_n_f32(int m, int n, const float* _
   }
 }
 
-// FP64 matrix: y[r] = sum_c A[r, c] x[c] + add_scale * add[r] for 4 rows per
-// block, optionally dotp[block] = sum_r dotw[r] y[r].
-__global__ void __launch_bounds__(256) k_gemv_n_f64(int m, int n, const double* __restrict__ A, long long lda,
-                                                     const double* __restrict__ x, const double* __restrict__ add,
-                                                     double add_scale, double* __restrict__ y,
-                                                     const double* __restrict__ dotw, double* __restrict__ dotp,
-                                                     const double* scal) {
+// Double-float matrix (pairs hi + lo): y[r] = sum_c A[r, c] x[c] +
+// add_scale * add[r] for 4 rows per block with double-float products and
+// accumulation (x split on the fly), optionally dotp[block] = sum_r dotw[r] y[r].
+__global__ void __launch_bounds__(256) k_gemv_n_df(int m, int n, const float2* __restrict__ A, long long lda,
+                                                    const double* __restrict__ x, const double* __restrict__ add,
+                                                    double add_scale, double* __restrict__ y,
+                                                    const double* __restrict__ dotw, double* __restrict__ dotp,
+                                                    const double* scal) {
   if (stopped(scal)) return;
   const int r0 = blockIdx.x * kRows;
   const int nrow = min(kRows, m - r0);
-  double acc[kRows];
+  dfloat acc[kRows];
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) acc[r] = 0.0;
+  for (int r = 0; r < kRows; ++r) acc[r] = {0.f, 0.f};
   for (int c2 = threadIdx.x * 2; c2 < n; c2 += blockDim.x * 2) {
     const bool pair = c2 + 1 < n;
     const double x0 = x[c2], x1 = pair ? x[c2 + 1] : 0.0;
+    const float x0h = (float)x0, x1h = (float)x1;
+    const float x0l = (float)(x0 - (double)x0h), x1l = (float)(x1 - (double)x1h);
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       if (r < nrow) {
-        const double* a = A + (long long)(r0 + r) * lda + c2;
+        const float2* a = A + (long long)(r0 + r) * lda + c2;
+        float4 v;
         if (pair) {
-          const double2 v = __ldg(reinterpret_cast<const double2*>(a));
-          acc[r] = fma(v.x, x0, acc[r]);
-          acc[r] = fma(v.y, x1, acc[r]);
+          v = __ldg(reinterpret_cast<const float4*>(a));
         } else {
-          acc[r] = fma(a[0], x0, acc[r]);
+          const float2 t = a[0];
+          v = make_float4(t.x, t.y, 0.f, 0.f);
         }
+        acc[r] = df_fma(acc[r], v.x, x0h);
+        acc[r].lo = fmaf(v.x, x0l, fmaf(v.y, x0h, acc[r].lo));
+        acc[r] = df_fma(acc[r], v.z, x1h);
+        acc[r].lo = fmaf(v.z, x1l, fmaf(v.w, x1h, acc[r].lo));
       }
     }
   }
@@ -180,8 +187,8 @@ __global__ void __launch_bounds__(256) k_gemv_n_f64(int m, int n, const double* 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
-    const double t = warp_sum(acc[r]);
-    if (lane == 0) red[r][warp] = t;
+    const dfloat t = df_warp_sum(acc[r]);
+    if (lane == 0) red[r][warp] = (double)t.hi + (double)t.lo;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -399,9 +406,9 @@ dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, doubl
     const int chunk = check_every > 0 ? check_every : 4;
     for (int k = 0; k < chunk && it < maxit; ++k, ++it) {
       if (P.K64) {
-        // Ap = K p + lambda p with the exact FP64 Gram, block partials of <p, Ap>
+        // Ap = K p + lambda p with the exact Gram, block partials of <p, Ap>
         DNGD_NOTE_LAUNCH();
-        k_gemv_n_f64<<<cdiv(m, kRows), 256, 0, st>>>(m, m, P.K64, P.ldk64, P.p, P.p, P.lambda, P.Ap, P.p, pap_parts,
+        k_gemv_n_df<<<cdiv(m, kRows), 256, 0, st>>>(m, m, P.K64, P.ldk64, P.p, P.p, P.lambda, P.Ap, P.p, pap_parts,
                                                      sc);
         DNGD_LAUNCH_CHECK();
       } else {
