@@ -336,11 +336,11 @@ def run_serving(args, rank, world, local_rank):
         ids = []
         t0 = time.perf_counter()
         for (t_arr, wl, n_steps), desc in zip(jobs, descs):
+            if t_arr >= args.window:
+                break
             dt = t0 + t_arr - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            if time.perf_counter() - t0 >= args.window:
-                break
             ids.append((srv.submit(desc, wl["theta"], wl["X"], wl["target"], n_steps), wl))
         rest = t0 + args.window - time.perf_counter()
         if rest > 0:
