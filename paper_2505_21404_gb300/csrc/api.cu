@@ -58,6 +58,7 @@ struct dngd_ctx {
   void* oz_slices = nullptr;
   double* oz_partials = nullptr;
   float2* K64 = nullptr;      // exact Gram as double-float pairs (full symmetric, no shift)
+  Tc3Scratch tc3;             // split operands of the TF32 tensor-core GEMMs (mixed paths)
   double* Dinv = nullptr;     // FP64 path: inverses of the factor's 64 x 64 diagonal blocks
   double* tw = nullptr;       // FP64 path: [2 m] triangular-solve work
   float* gram_partials = nullptr;
@@ -249,8 +250,10 @@ const float* theta_in_T<float>(dngd_ctx* c, const double* theta) {
 }
 
 template <typename T>
-dngd_status forward_only(dngd_ctx* c, const T* thT, const double* X, const double* target, double* r) {
-  return jets_forward<T>(c->net, thT, X, target, lp<T>(c->Z), lp<T>(c->H), r, c->status, c->st);
+dngd_status forward_only(dngd_ctx* c, const T* thT, const double* X, const double* target, double* r,
+                         bool tensor = false) {
+  return jets_forward<T>(c->net, thT, X, target, lp<T>(c->Z), lp<T>(c->H), r, c->status, c->st,
+                         tensor && c->tc3.buf ? &c->tc3 : nullptr);
 }
 
 template <typename T>
@@ -329,6 +332,21 @@ dngd_status solve_last(dngd_ctx* c, const double* b, double* x, int slot) {
 // The step
 // ---------------------------------------------------------------------------
 
+const Tc3Scratch* tc3p(dngd_ctx* c) { return c->tc3.buf ? &c->tc3 : nullptr; }
+
+// Scratch for the largest TF32 tensor-core GEMM of the context: a line-search
+// forward layer (R x w x w), a factor update (m x m x 64) or the top level
+// of the recursive inverse (m/2 x m/2 x m/2).
+size_t tc3_bytes(const dngd_ctx* c) {
+  const int m = c->net.m, w = c->net.max_w;
+  size_t b = tc3_scratch_bytes(c->net.R, w, w);
+  const size_t f = tc3_scratch_bytes(m, m, 64);
+  const size_t t = tc3_scratch_bytes(m, 0, m / 2 + 64);
+  if (f > b) b = f;
+  if (t > b) b = t;
+  return b;
+}
+
 // The low-precision Gram writes K + shift I (FP32 lower) for the factor: the
 // tcgen05 BF16 / TF32 syrk, or the exact sliced Gram (which also writes the
 // FP64 refinement operator).
@@ -375,8 +393,10 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
       gram_set_shift(c, c->lambda + mu);
       if ((s = gram_run(c, nullptr))) return s;
       DNGD_CUDA_CHECK(cudaMemsetAsync(c->Linv, 0, sizeof(float) * (size_t)m * c->ldk, c->st));
-      if ((s = cholesky_f32_inv(m, (float*)c->K, c->ldk, c->Linv, c->ldk, c->status, c->st))) return s;
-      if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
+      if ((s = cholesky_f32_inv(m, (float*)c->K, c->ldk, c->Linv, c->ldk, c->status, c->st, tc3p(c)))) return s;
+      if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st, tc3p(c),
+                                 c->status)))
+        return s;
       c->shift_used = mu;
       c->factor_attempts = 1;
       goto factored;
@@ -399,7 +419,7 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
       evrec(c, 2);
       c->factor_attempts++;
       DNGD_CUDA_CHECK(cudaMemsetAsync(c->Linv, 0, sizeof(float) * (size_t)m * c->ldk, c->st));
-      if ((s = cholesky_f32_inv(m, (float*)c->K, c->ldk, c->Linv, c->ldk, c->status, c->st))) return s;
+      if ((s = cholesky_f32_inv(m, (float*)c->K, c->ldk, c->Linv, c->ldk, c->status, c->st, tc3p(c)))) return s;
       const dngd_status fs = read_status(c);
       if (fs != DNGD_ERR_NOT_SPD || attempt >= 15) break;
       DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
@@ -416,7 +436,9 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     }
     c->mu_sticky = mu;
     c->shift_used = mu;
-    if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st))) return s;
+    if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st, tc3p(c),
+                               c->status)))
+      return s;
   }
   // a failed factorisation stops the (synchronous) step here
   if (!c->async && (s = read_status(c))) return s;
@@ -817,6 +839,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     add(es * (size_t)m * c->ldk);                 // K0
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
     add(sizeof(float) * (size_t)m * m);           // trtri work
+    add(tc3_bytes(c));                            // TF32 tensor-core GEMM splits
     if (oz) {
       add(sizeof(float2) * (size_t)m * c->ldk);   // K64
       add(gram_oz_slice_bytes(m, (int)n));
@@ -885,6 +908,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     if (c->desc.keep_gram) A_(c->Kcopy, float, (size_t)m * c->ldk);
     A_(c->Linv, float, (size_t)m * c->ldk);
     A_(c->trtri_work, float, (size_t)m * m);
+    c->tc3.bytes = tc3_bytes(c);
+    A_(c->tc3.buf, float, c->tc3.bytes / sizeof(float));
     if (oz) {
       A_(c->K64, float2, (size_t)m * c->ldk);
       A_(c->oz_slices, unsigned char, gram_oz_slice_bytes(m, (int)n));
@@ -1156,7 +1181,7 @@ dngd_status dngd_loss(dngd_ctx* c, const double* theta, const double* X, const d
     dngd_status s = axpy_to(c->n, th, etas[j], dl, c->theta_tmp, c->st);
     if (s) return s;
     if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, x, tg, c->cg_res);
-    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), x, tg, c->cg_res);
+    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), x, tg, c->cg_res, true);
     if (s) return s;
     if ((s = dot_dev(c->m, c->cg_res, c->cg_res, c->scal + S_LOSS, c->dot_partials, c->st))) return s;
     DNGD_CUDA_CHECK(cudaMemcpyAsync(&c->scal_h[S_LOSS], c->scal + S_LOSS, sizeof(double), cudaMemcpyDeviceToHost,
@@ -1213,7 +1238,7 @@ dngd_status dngd_line_search_async(dngd_ctx* c, double* theta, const double* X, 
     dngd_status s = axpy_to(c->n, theta, etas[j], delta, c->theta_tmp, c->st);
     if (s) return s;
     if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, X, target, c->cg_res);
-    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), X, target, c->cg_res);
+    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), X, target, c->cg_res, true);
     if (s) return s;
     if ((s = dot_dev(c->m, c->cg_res, c->cg_res, losses + j, c->dot_partials, c->st))) return s;
   }

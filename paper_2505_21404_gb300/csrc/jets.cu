@@ -16,6 +16,8 @@
 // parameter direction t of theta + t v: (q, q', q'') with
 //     z' = W h' + V h + b_v,   z'' = W h'' + 2 V h'
 // and the chain rules of tanh, s and t*s up to second order.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -402,7 +404,8 @@ __global__ void k_output_fvv(NetInfo net, const T* __restrict__ theta, const T* 
 
 template <typename T>
 dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, const double* target,
-                         LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st) {
+                         LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st,
+                         const Tc3Scratch* tc3) {
   const int L = net.n_layers - 1;
   const int thr = 128;
   for (int l = 0; l < L; ++l) {
@@ -412,8 +415,15 @@ dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, co
       DNGD_NOTE_LAUNCH();
       k_first_layer<T><<<grid, thr, 0, st>>>(net, theta, X, Z.p[0], H.p[0]);
     } else {
-      dngd_status s = gemm_nt<T>(net.R, w, net.widths[l], T(1), H.p[l - 1], net.widths[l],
-                                 theta + net.w_off[l], net.widths[l], T(0), Z.p[l], w, false, st);
+      dngd_status s = DNGD_ERR_INVALID_ARG;
+      if constexpr (std::is_same<T, float>::value) {
+        if (tc3)
+          s = gemm_tc3(net.R, w, net.widths[l], 1.0f, H.p[l - 1], net.widths[l], false, theta + net.w_off[l],
+                       net.widths[l], false, 0.0f, Z.p[l], w, false, *tc3, status, st);
+      }
+      if (s == DNGD_ERR_INVALID_ARG)
+        s = gemm_nt<T>(net.R, w, net.widths[l], T(1), H.p[l - 1], net.widths[l], theta + net.w_off[l],
+                       net.widths[l], T(0), Z.p[l], w, false, st);
       if (s) return s;
       DNGD_NOTE_LAUNCH();
       k_act_fwd<T><<<grid, thr, 0, st>>>(net, l, theta, Z.p[l], H.p[l]);
@@ -506,9 +516,11 @@ dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const doubl
 }
 
 template dngd_status jets_forward<double>(const NetInfo&, const double*, const double*, const double*,
-                                          LayerPtrs<double>, LayerPtrs<double>, double*, int*, cudaStream_t);
+                                          LayerPtrs<double>, LayerPtrs<double>, double*, int*, cudaStream_t,
+                                          const Tc3Scratch*);
 template dngd_status jets_forward<float>(const NetInfo&, const float*, const double*, const double*,
-                                         LayerPtrs<float>, LayerPtrs<float>, double*, int*, cudaStream_t);
+                                         LayerPtrs<float>, LayerPtrs<float>, double*, int*, cudaStream_t,
+                                         const Tc3Scratch*);
 template dngd_status jets_backward_jacobian<double, double>(const NetInfo&, const double*, const double*,
                                                             LayerPtrs<double>, LayerPtrs<double>,
                                                             LayerPtrs<double>, double*, double*, long long,

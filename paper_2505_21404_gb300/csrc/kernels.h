@@ -11,9 +11,13 @@ struct LayerPtrs {
 };
 
 // ---- jets.cu --------------------------------------------------------------
+struct Tc3Scratch;
+// tc3 (FP32 only, optional): hidden-layer GEMMs on the TF32 tensor cores
+// (3xTF32, ~2^-21 per product) instead of FP32 SIMT.
 template <typename T>
 dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, const double* target,
-                         LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st);
+                         LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st,
+                         const Tc3Scratch* tc3 = nullptr);
 
 template <typename T, typename TJ>
 dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
@@ -58,10 +62,12 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 // FP32 factorisation of the mixed path: A = L L^T in place (lower) and the
 // inverses of the 64 x 64 diagonal blocks of L written into Linv, which the
 // caller zero-initialises; trtri_offdiag_f32 then completes Linv = L^{-1}.
+// tc3 (optional): the panel / trailing / inverse GEMMs on the TF32 tensor
+// cores (3xTF32) — the factor only preconditions the refinement.
 dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long long ldi, int* status,
-                             cudaStream_t st);
+                             cudaStream_t st, const Tc3Scratch* tc3 = nullptr);
 dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
-                              cudaStream_t st);
+                              cudaStream_t st, const Tc3Scratch* tc3 = nullptr, int* status = nullptr);
 
 // x = (L L^T)^{-1} b with the FP64 factor (two triangular solves).
 dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* b, double* x, cudaStream_t st);
@@ -70,6 +76,20 @@ dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* 
 dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cudaStream_t st);
 dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const double* Dinv, const double* b, double* x,
                                 double* w, double* y, cudaStream_t st);
+
+// ---- tc3.cu: FP32 GEMM on TF32 tensor cores with hi/lo splits -----------
+struct Tc3Scratch {
+  float* buf = nullptr;
+  size_t bytes = 0;
+};
+size_t tc3_scratch_bytes(int M, int N, int K);
+// C = alpha A_op B_op^T + beta C; A_op = A [M x K] (or A^T with transA,
+// A then [K x M]), B_op = B [N x K] (or B^T with transB); lower: only
+// C[i][j], j <= i.  INVALID_ARG when the scratch is too small (callers then
+// use the SIMT GEMM).
+dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long lda, bool transA, const float* B,
+                     long long ldb, bool transB, float beta, float* C, long long ldc, bool lower, const Tc3Scratch& sc,
+                     int* status, cudaStream_t st);
 
 // ---- gram_oz.cu: exact Gram of an FP32 matrix from BF16 integer slices ----
 struct OzPlan;

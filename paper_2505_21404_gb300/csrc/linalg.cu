@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A,
 // A = L L^T (FP32, in place, lower) and the diagonal 64-blocks of L^{-1} in
 // Linv (which must be zero-initialised by the caller).
 dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long long ldi, int* status,
-                             cudaStream_t st) {
+                             cudaStream_t st, const Tc3Scratch* tc3) {
   for (int k0 = 0; k0 < m; k0 += kCholNB) {
     const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
     DNGD_NOTE_LAUNCH();
@@ -409,11 +409,17 @@ dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long l
     if (rest <= 0) break;
     float* P = A + (long long)(k0 + kb) * lda + k0;
     const float* I11 = Linv + (long long)k0 * ldi + k0;
-    // panel: P <- P L11^{-T} = P * (L11^{-1})^T (in place: one column tile)
-    dngd_status s = gemm_nt<float>(rest, kb, kb, 1.0f, P, lda, I11, ldi, 0.0f, P, lda, false, st);
+    // panel: P <- P L11^{-T} = P * (L11^{-1})^T (in place: one column tile;
+    // the tensor-core form reads P from its split copy)
+    dngd_status s = tc3 ? gemm_tc3(rest, kb, kb, 1.0f, P, lda, false, I11, ldi, false, 0.0f, P, lda, false, *tc3,
+                                   status, st)
+                        : DNGD_ERR_INVALID_ARG;
+    if (s == DNGD_ERR_INVALID_ARG) s = gemm_nt<float>(rest, kb, kb, 1.0f, P, lda, I11, ldi, 0.0f, P, lda, false, st);
     if (s) return s;
     float* A22 = A + (long long)(k0 + kb) * lda + k0 + kb;
-    s = gemm_nt<float>(rest, rest, kb, -1.0f, P, lda, P, lda, 1.0f, A22, lda, true, st);
+    s = tc3 ? gemm_tc3(rest, rest, kb, -1.0f, P, lda, false, P, lda, false, 1.0f, A22, lda, true, *tc3, status, st)
+            : DNGD_ERR_INVALID_ARG;
+    if (s == DNGD_ERR_INVALID_ARG) s = gemm_nt<float>(rest, rest, kb, -1.0f, P, lda, P, lda, 1.0f, A22, lda, true, st);
     if (s) return s;
   }
   return DNGD_OK;
@@ -651,7 +657,7 @@ __global__ void k_trtri_diag(int k0, int kb, const float* __restrict__ L, long l
 }
 
 static dngd_status trtri_rec(int k0, int n, const float* L, long long ldl, float* Linv, long long ldi, float* work,
-                             cudaStream_t st, bool have_diag) {
+                             cudaStream_t st, bool have_diag, const Tc3Scratch* tc3, int* status) {
   if (n <= kCholNB && have_diag) return DNGD_OK;
   if (n <= kCholNB) {
     const int smem = 2 * kCholNB * (kCholNB + 1) * (int)sizeof(double);
@@ -667,15 +673,21 @@ static dngd_status trtri_rec(int k0, int n, const float* L, long long ldl, float
   }
   const int n1 = ((n / 2 + kCholNB - 1) / kCholNB) * kCholNB;
   const int n2 = n - n1;
-  dngd_status s = trtri_rec(k0, n1, L, ldl, Linv, ldi, work, st, have_diag);
+  dngd_status s = trtri_rec(k0, n1, L, ldl, Linv, ldi, work, st, have_diag, tc3, status);
   if (s) return s;
-  s = trtri_rec(k0 + n1, n2, L, ldl, Linv, ldi, work, st, have_diag);
+  s = trtri_rec(k0 + n1, n2, L, ldl, Linv, ldi, work, st, have_diag, tc3, status);
   if (s) return s;
   // T = L21 * Linv11  (n2 x n1), stored in work with ld n1
   const float* L21 = L + (long long)(k0 + n1) * ldl + k0;
   const float* I11 = Linv + (long long)k0 * ldi + k0;
   const float* I22 = Linv + (long long)(k0 + n1) * ldi + k0 + n1;
   float* I21 = Linv + (long long)(k0 + n1) * ldi + k0;
+  if (tc3 && status) {
+    s = gemm_tc3(n2, n1, n1, 1.0f, L21, ldl, false, I11, ldi, true, 0.0f, work, n1, false, *tc3, status, st);
+    if (s == DNGD_OK)
+      s = gemm_tc3(n2, n1, n2, -1.0f, I22, ldi, false, work, n1, true, 0.0f, I21, ldi, false, *tc3, status, st);
+    if (s != DNGD_ERR_INVALID_ARG) return s;
+  }
   s = gemm_nn<float>(n2, n1, n1, 1.0f, L21, ldl, I11, ldi, 0.0f, work, n1, st);
   if (s) return s;
   return gemm_nn<float>(n2, n1, n2, -1.0f, I22, ldi, work, n1, 0.0f, I21, ldi, st);
@@ -684,12 +696,12 @@ static dngd_status trtri_rec(int k0, int n, const float* L, long long ldl, float
 dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
                             cudaStream_t st) {
   DNGD_CUDA_CHECK(cudaMemsetAsync(Linv, 0, sizeof(float) * (size_t)m * ldi, st));
-  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, false);
+  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, false, nullptr, nullptr);
 }
 
 dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
-                              cudaStream_t st) {
-  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, true);
+                              cudaStream_t st, const Tc3Scratch* tc3, int* status) {
+  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, true, tc3, status);
 }
 
 // ---------------------------------------------------------------------------

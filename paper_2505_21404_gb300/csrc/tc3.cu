@@ -1,0 +1,302 @@
+// FP32 GEMM on the TF32 tensor cores with FP32-like accuracy ("3xTF32"):
+// C = alpha * A_op B_op^T + beta * C, A_op [M x K], B_op [N x K].
+//
+// Every operand x is split into x_hi = tf32(x) and x_lo = tf32(x - x_hi)
+// (both rounded to nearest, so the tensor cores see exact TF32 values), and
+// A_op B_op^T ~= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T; the dropped
+// A_lo B_lo^T and the rounding of x_lo leave ~2^-21 relative error per
+// product (FP32 SIMT: 2^-24).  It serves the products that need no more: the
+// 31 trial forwards of the line search and the FP32 preconditioning factor.
+//
+// The split copies (and, for a transposed operand, the transpose) go to a
+// caller-owned scratch as [rows x 2 Kp] FP32 (hi in columns [0, Kp), lo in
+// [Kp, 2 Kp), Kp = K rounded up to 32, zero tails), so TMA needs no
+// alignment from the caller's matrices.  Kernel: one 128 x 128 output tile
+// per CTA (lower-triangle tiles only when asked), a 3-stage TMA ring of
+// 64 KB stages (A_hi, A_lo, B_hi, B_lo for 32 K), warp 1 issuing 12
+// tcgen05.mma kind::tf32 per stage into one TMEM accumulator, warps 2..5
+// draining it once.  Waits are bounded (ST_TIMEOUT).
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace dngd {
+
+namespace {
+
+using namespace tc;
+
+constexpr int T3 = 128;                     // tile rows = columns
+constexpr int KB3 = 32;                     // K per stage (128-byte rows)
+constexpr int ST3 = 3;
+constexpr int TILE3 = T3 * 128;             // 16 KB
+constexpr int STAGE3 = 4 * TILE3;           // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM3 = ST3 * STAGE3 + 1024;
+constexpr int THREADS3 = 192;
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;   // inf / nan unchanged
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  return __uint_as_float(u);
+}
+
+// dst[r, 0:Kp] = hi, dst[r, Kp:2Kp] = lo of op[r, k]; op = src (row-major
+// [rows x K], ld) or, with trans, src^T (src row-major [K x rows]).
+__global__ void k_tc3_split(int rows, int K, int Kp, const float* __restrict__ src, long long ld, int trans,
+                            float* __restrict__ dst) {
+  __shared__ float t[32][33];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    float v = 0.f;
+    if (trans) {
+      const int k = k0 + i, r = r0 + tx;
+      if (k < K && r < rows) v = src[(long long)k * ld + r];
+      t[tx][i] = v;   // t[r][k]
+    } else {
+      const int r = r0 + i, k = k0 + tx;
+      if (k < K && r < rows) v = src[(long long)r * ld + k];
+      t[i][tx] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, k = k0 + tx;
+    if (r < rows && k < Kp) {
+      const float x = t[i][tx];
+      const float hi = tf32_rn(x);
+      float* row = dst + (long long)r * 2 * Kp;
+      row[k] = hi;
+      row[Kp + k] = tf32_rn(x - hi);
+    }
+  }
+}
+
+// TF32 x TF32 -> FP32, both K-major, N = M = 128.
+__device__ __forceinline__ uint32_t tc3_idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(T3 >> 3) << 17) | ((uint32_t)(T3 >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(THREADS3, 1)
+k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int Kp,
+      float alpha, float beta, float* __restrict__ C, long long ldc, int lower, int* status) {
+  const int bn = blockIdx.x, bm = blockIdx.y;
+  if (lower && bn * T3 > bm * T3 + T3 - 1) return;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[ST3];
+  __shared__ __align__(8) uint64_t empty_bar[ST3];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int nk = Kp / KB3;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST3; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&acc_bar), 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < nk; ++it) {
+        const int st = it % ST3;
+        const uint32_t ph = (uint32_t)((it / ST3) & 1);
+        if (*abort_flag || !mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, status, 21)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t fb = smem_u32(&full_bar[st]);
+        mbar_expect_tx(fb, STAGE3);
+        const uint32_t sb = smem_base + st * STAGE3;
+        const int kc = it * KB3;
+        tma_load_2d(sb, &mapA, fb, kc, bm * T3);
+        tma_load_2d(sb + TILE3, &mapA, fb, Kp + kc, bm * T3);
+        tma_load_2d(sb + 2 * TILE3, &mapB, fb, kc, bn * T3);
+        tma_load_2d(sb + 3 * TILE3, &mapB, fb, Kp + kc, bn * T3);
+        ++issued;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc3_idesc();
+      for (int it = 0; it < nk && !*abort_flag; ++it) {
+        const int st = it % ST3;
+        const uint32_t ph = (uint32_t)((it / ST3) & 1);
+        if (!mbar_wait(smem_u32(&full_bar[st]), ph, status, 22)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sb = smem_base + st * STAGE3;
+        const uint64_t ahi = sw128_desc(sb), alo = sw128_desc(sb + TILE3);
+        const uint64_t bhi = sw128_desc(sb + 2 * TILE3), blo = sw128_desc(sb + 3 * TILE3);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t dk = (uint64_t)((32 * k) >> 4);
+          umma<1>(tmem, ahi + dk, bhi + dk, idesc, (it > 0 || k > 0) ? 1u : 0u);
+          umma<1>(tmem, ahi + dk, blo + dk, idesc, 1u);
+          umma<1>(tmem, alo + dk, bhi + dk, idesc, 1u);
+        }
+        umma_commit(smem_u32(&empty_bar[st]));
+      }
+      umma_commit(smem_u32(&acc_bar));
+    }
+  } else {
+    const int q = warp & 3;
+    const bool ok = __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&acc_bar), 0u, status, 23)) ? 1 : 0) != 0;
+    if (!ok) {
+      *abort_flag = 1;
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      // all MMAs (hence all TMA stages) are done: stage 0 holds each warp's
+      // 32 x 33 transpose buffer, so C is written row by row, coalesced
+      float* tb = reinterpret_cast<float*>(smem_raw + (smem_base - smem_u32(smem_raw))) + (warp - 2) * 32 * 33;
+      const int row0 = bm * T3 + q * 32;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int j4 = 0; j4 < 4; ++j4) {
+        uint32_t r[32];
+        TMEM_LD_32(base + (uint32_t)(j4 * 32), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) tb[lane * 33 + i] = __uint_as_float(r[i]);
+        __syncwarp();
+        const int col = bn * T3 + j4 * 32 + lane;
+        if (col < N && nk > 0) {
+          for (int i = 0; i < 32; ++i) {
+            const int row = row0 + i;
+            if (row < M && (!lower || col <= row)) {
+              float* cp = C + (long long)row * ldc + col;
+              const float v = alpha * tb[i * 33 + lane];
+              *cp = beta == 0.f ? v : v + beta * *cp;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (int it = 0; it < issued; ++it) {
+      const int st = it % ST3;
+      mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((it / ST3) & 1), status, 24);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  }
+}
+
+bool encode_split_map(CUtensorMap* map, float* base, int rows, int Kp) {
+  EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)(2 * Kp), (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)(2 * Kp) * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)KB3, (cuuint32_t)T3};
+  cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// The scratch is used as two fixed halves (A split, B split), so a tensor map
+// depends only on the half's base and Kp and is encoded once: rows past the
+// operand's size are read but their results are never stored.
+size_t tc3_scratch_bytes(int M, int N, int K) {
+  const long long Kp = ((K + KB3 - 1) / KB3) * KB3;
+  const long long rows = M > N ? M : N;
+  return (size_t)2 * rows * 2 * Kp * sizeof(float) + 1024;
+}
+
+namespace {
+
+struct MapEntry {
+  const float* base;
+  int Kp, rows;
+  CUtensorMap map;
+};
+std::mutex g_map_mu;
+std::vector<MapEntry> g_maps;
+
+bool cached_map(float* base, int rows, int Kp, CUtensorMap* out) {
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  // the key includes the row capacity, so a new scratch at a reused address
+  // never inherits a map with a larger extent
+  for (const MapEntry& e : g_maps)
+    if (e.base == base && e.Kp == Kp && e.rows == rows) {
+      *out = e.map;
+      return true;
+    }
+  MapEntry e;
+  e.base = base;
+  e.Kp = Kp;
+  e.rows = rows;
+  if (!encode_split_map(&e.map, base, rows, Kp)) return false;
+  if (g_maps.size() > 256) g_maps.clear();
+  g_maps.push_back(e);
+  *out = e.map;
+  return true;
+}
+
+}  // namespace
+
+dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long lda, bool transA, const float* B,
+                     long long ldb, bool transB, float beta, float* C, long long ldc, bool lower, const Tc3Scratch& sc,
+                     int* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DNGD_OK;
+  if (!sc.buf || tc3_scratch_bytes(M, N, K) > sc.bytes || K <= 0) return DNGD_ERR_INVALID_ARG;
+  const int Kp = ((K + KB3 - 1) / KB3) * KB3;
+  const size_t half = ((sc.bytes - 1024) / 2) / sizeof(float) / 32 * 32;   // floats per half
+  const int cap_rows = (int)(half / (2 * (size_t)Kp));
+  float* Ab = sc.buf;
+  float* Bh = sc.buf + half;
+  const bool same = A == B && lda == ldb && transA == transB && M == N;
+  float* Bb = same ? Ab : Bh;
+  DNGD_NOTE_LAUNCH();
+  k_tc3_split<<<dim3(Kp / 32, cdiv(M, 32)), 256, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, Ab);
+  if (!same) {
+    DNGD_NOTE_LAUNCH();
+    k_tc3_split<<<dim3(Kp / 32, cdiv(N, 32)), 256, 0, st>>>(N, K, Kp, B, ldb, transB ? 1 : 0, Bb);
+  }
+  DNGD_LAUNCH_CHECK();
+  CUtensorMap mapA, mapB;
+  if (!cached_map(Ab, cap_rows, Kp, &mapA) || !cached_map(Bb, cap_rows, Kp, &mapB)) return DNGD_ERR_CUDA;
+  static bool attr = false;
+  if (!attr) {
+    DNGD_CUDA_CHECK(cudaFuncSetAttribute(k_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM3));
+    attr = true;
+  }
+  DNGD_NOTE_LAUNCH();
+  k_tc3<<<dim3(cdiv(N, T3), cdiv(M, T3)), THREADS3, SMEM3, st>>>(mapA, mapB, M, N, Kp, alpha, beta, C, ldc,
+                                                                 lower ? 1 : 0, status);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+}  // namespace dngd

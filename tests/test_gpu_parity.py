@@ -16,7 +16,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import residual as ores, step as ostep  # noqa: E402
+from oracle import linesearch as olin, residual as ores, step as ostep  # noqa: E402
 from paper_2505_21404_gb300 import workloads  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -202,3 +202,27 @@ def test_dense_step_mixed_oz(dngd, case):
     err = _rel(delta, ref["delta"])
     assert err <= 1e-4, (err, info)
     assert max(info["solve_relres"]) <= 1e-10, info
+
+
+@pytest.mark.parametrize("prec", ["MIXED_OZ", "MIXED_BF16"])
+def test_line_search_losses_mixed(dngd, prec):
+    """Trial losses of the line search (their hidden layers run on the TF32
+    tensor cores with hi/lo splits, ~2^-21 per product) against the oracle's
+    FP64 losses, on a case whose stream matrix spans several 128-row tiles."""
+    wl = workloads.poisson_sine(5, [5, 64, 64, 64, 1], 481, 120, k=1, seed=6, lam=1e-5)
+    prob = ores.problem_from_spec(wl)
+    ctx = dngd.Context(dngd.make_desc(wl, precision=getattr(dngd, prec), refine_tol=1e-8, refine_max_it=300))
+    delta = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
+    ctx.step(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), delta)
+    d = delta.cpu().numpy()
+    etas = olin.grid()
+    got = ctx.loss(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), delta, etas)
+    ref = np.array([ores.loss(wl["theta"] + e * d, prob, wl["X"], wl["target"]) for e in etas])
+    rel = np.abs(got - ref) / ref
+    near = ref <= 10 * ref.min()
+    # near the minimum (where the choice is made) the losses agree to FP32
+    # level; far out (eta ~ 1 here: loss 1e10, saturated units) the FP32 jets
+    # lose a few more digits
+    assert np.max(rel[near]) <= 1e-6, rel
+    assert np.max(rel) <= 2e-4, rel
+    assert int(np.argmin(got)) == int(np.argmin(ref))
