@@ -86,6 +86,9 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
       float alpha, float beta, float* __restrict__ C, long long ldc, int lower, int* status) {
   const int bn = blockIdx.x, bm = blockIdx.y;
   if (lower && bn * T3 > bm * T3 + T3 - 1) return;
+  // a factorisation that already failed (the host retries it with a larger
+  // shift) needs no further updates
+  if (status[0] & ST_NOT_SPD) return;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[ST3];
   __shared__ __align__(8) uint64_t empty_bar[ST3];

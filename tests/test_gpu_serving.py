@@ -63,10 +63,17 @@ def test_server_job_equals_manual_async_loop(dngd):
     th, X, tg = _t(wl["theta"]), _t(wl["X"]), _t(wl["target"])
     d = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
     etas = olin.grid()
-    for _ in range(n_steps):
+    done = 0
+    while done < n_steps:
+        # as the server does: a failed factorisation leaves theta unchanged
+        # and the iteration is re-run with the synchronous shift search
         ctx.step_async(th, X, tg, d)
         ctx.line_search_async(th, X, tg, d, etas)
-        ctx.step_wait()
+        try:
+            ctx.step_wait()
+            done += 1
+        except dngd.DngdError as e:
+            assert "NOT_SPD" in str(e)
     torch.cuda.synchronize()
     assert np.array_equal(theta_srv, th.cpu().numpy())
 
