@@ -59,6 +59,9 @@ struct dngd_ctx {
   double* oz_partials = nullptr;
   float2* K64 = nullptr;      // exact Gram as double-float pairs (full symmetric, no shift)
   Tc3Scratch tc3;             // split operands of the TF32 tensor-core GEMMs (mixed paths)
+  cudaStream_t cap_st = nullptr;                 // capture stream of the PCG chunk graphs
+  cudaGraphExec_t pcg_chunk[2] = {nullptr, nullptr};
+  double pcg_chunk_key[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};   // lambda, chunk, kernels, x
   double* Dinv = nullptr;     // FP64 path: inverses of the factor's 64 x 64 diagonal blocks
   double* tw = nullptr;       // FP64 path: [2 m] triangular-solve work
   float* gram_partials = nullptr;
@@ -312,6 +315,12 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
     // the exact FP64 Gram is the operator: one m x m GEMV per iteration
     P.K64 = c->K64;
     P.ldk64 = c->ldk;
+  }
+  if (!c->async) {
+    if (!c->cap_st) DNGD_CUDA_CHECK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+    P.chunk_exec = &c->pcg_chunk[slot];
+    P.chunk_key = c->pcg_chunk_key[slot];
+    P.cap = c->cap_st;
   }
   return pcg_mixed_solve(P, b, x, tol, maxit, 4, &c->iters[slot], &c->relres[slot], c->st, c->async, slot);
 }
@@ -962,6 +971,9 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
 }
 
 void free_ctx(dngd_ctx* c) {
+  for (int i = 0; i < 2; ++i)
+    if (c->pcg_chunk[i]) cudaGraphExecDestroy(c->pcg_chunk[i]);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->ls_host) cudaFreeHost(c->ls_host);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->gst) cudaStreamDestroy(c->gst);

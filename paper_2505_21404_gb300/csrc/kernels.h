@@ -151,6 +151,12 @@ struct PcgMixed {
   // exact-Gram mode: operator A = K64 (full symmetric double-float Gram, one GEMV)
   const float2* K64 = nullptr;
   long long ldk64 = 0;
+  // synchronous solves: chunks of iterations captured once into a graph on
+  // the stream cap and replayed (key: lambda, chunk size, kernels per chunk,
+  // solution pointer)
+  cudaGraphExec_t* chunk_exec = nullptr;
+  double* chunk_key = nullptr;
+  cudaStream_t cap = nullptr;
 };
 // async: enqueue exactly maxit iterations (kernels become no-ops after
 // convergence) and never synchronise; iters/relres are then left untouched and

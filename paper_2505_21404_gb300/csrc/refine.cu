@@ -379,6 +379,50 @@ dngd_status gemv_n_f32(int m, int n, const float* A, long long lda, const double
   return gemv_n_f32_s(m, n, A, lda, x, alpha, y, add, add_scale, xs, nullptr, nullptr, nullptr, st);
 }
 
+namespace {
+
+// One PCG iteration (no-ops once the device "done" flag is set).
+dngd_status pcg_iteration(const PcgMixed& P, double* x, bool timed, cudaStream_t st) {
+  const int m = P.m;
+  double* sc = P.scal;
+  double* part_a = P.dotp;
+  double* part_b = P.dotp + 512;
+  double* pap_parts = P.dotp + 1024;
+  const int nAp = cdiv(m, kRows);
+  dngd_status s;
+  if (P.K64) {
+    // Ap = K p + lambda p with the exact Gram, block partials of <p, Ap>
+    DNGD_NOTE_LAUNCH();
+    k_gemv_n_df<<<cdiv(m, kRows), 256, 0, st>>>(m, m, P.K64, P.ldk64, P.p, P.p, P.lambda, P.Ap, P.p, pap_parts, sc);
+    DNGD_LAUNCH_CHECK();
+  } else {
+    // Ap = J (J^T p) + lambda p, with the block partials of <p, Ap>
+    if (timed) cudaEventRecord(P.ev[0], st);
+    if ((s = gemv_t_f32_s(m, P.n, P.J, P.ldJ, P.p, 1.0, P.u, P.partials, P.partial_cap, P.xs, sc, st))) return s;
+    if (timed) cudaEventRecord(P.ev[1], st);
+    if ((s = gemv_n_f32_s(m, P.n, P.J, P.ldJ, P.u, 1.0, P.Ap, P.p, P.lambda, P.xs, P.p, pap_parts, sc, st)))
+      return s;
+    if (timed) cudaEventRecord(P.ev[2], st);
+  }
+  DNGD_NOTE_LAUNCH();
+  k_cg_alpha<<<1, 256, 0, st>>>(nAp, pap_parts, sc);
+  DNGD_NOTE_LAUNCH();
+  k_cg_update_x<<<kVecBlocks, 256, 0, st>>>(m, sc, x, P.res, P.p, P.Ap, part_a);
+  DNGD_NOTE_LAUNCH();
+  k_cg_check<<<1, 256, 0, st>>>(kVecBlocks, part_a, sc);
+  if ((s = precond(P, P.res, P.z, st))) return s;
+  DNGD_NOTE_LAUNCH();
+  k_dot_parts<<<kVecBlocks, 256, 0, st>>>(m, P.res, P.z, part_b, sc);
+  DNGD_NOTE_LAUNCH();
+  k_cg_beta<<<1, 256, 0, st>>>(kVecBlocks, part_b, sc);
+  DNGD_NOTE_LAUNCH();
+  k_cg_update_p<<<cdiv(m, 256), 256, 0, st>>>(m, sc, P.z, P.p);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+}  // namespace
+
 dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, double tol, int maxit, int check_every,
                             int* iters, double* relres, cudaStream_t st, bool async, int slot) {
   const int m = P.m;
@@ -404,37 +448,40 @@ dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, doubl
   int it = 0;
   for (;;) {
     const int chunk = check_every > 0 ? check_every : 4;
-    for (int k = 0; k < chunk && it < maxit; ++k, ++it) {
-      if (P.K64) {
-        // Ap = K p + lambda p with the exact Gram, block partials of <p, Ap>
-        DNGD_NOTE_LAUNCH();
-        k_gemv_n_df<<<cdiv(m, kRows), 256, 0, st>>>(m, m, P.K64, P.ldk64, P.p, P.p, P.lambda, P.Ap, P.p, pap_parts,
-                                                     sc);
-        DNGD_LAUNCH_CHECK();
-      } else {
-      // Ap = J (J^T p) + lambda p, with the block partials of <p, Ap>
-      const bool tm = P.ev && it == 0;
-      if (tm) cudaEventRecord(P.ev[0], st);
-      if ((s = gemv_t_f32_s(m, P.n, P.J, P.ldJ, P.p, 1.0, P.u, P.partials, P.partial_cap, P.xs, sc, st))) return s;
-      if (tm) cudaEventRecord(P.ev[1], st);
-      if ((s = gemv_n_f32_s(m, P.n, P.J, P.ldJ, P.u, 1.0, P.Ap, P.p, P.lambda, P.xs, P.p, pap_parts, sc, st)))
-        return s;
-      if (tm) cudaEventRecord(P.ev[2], st);
+    const bool timed = P.ev && it == 0;
+    if (!async && P.chunk_exec && !timed && it + chunk <= maxit) {
+      // the chunk of iterations as one captured graph (cached per solve
+      // slot and lambda): one launch instead of ~12 per iteration
+      const double xkey = (double)(uintptr_t)x;
+      if (!*P.chunk_exec || P.chunk_key[0] != P.lambda || P.chunk_key[1] != (double)chunk || P.chunk_key[3] != xkey) {
+        if (*P.chunk_exec) {
+          cudaGraphExecDestroy(*P.chunk_exec);
+          *P.chunk_exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        const unsigned long long n0 = dngd_launch_count();
+        DNGD_CUDA_CHECK(cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal));
+        dngd_status cs = DNGD_OK;
+        for (int k = 0; k < chunk && !cs; ++k) cs = pcg_iteration(P, x, false, P.cap);
+        const cudaError_t e = cudaStreamEndCapture(P.cap, &g);
+        P.chunk_key[2] = (double)(dngd_launch_count() - n0);
+        if (cs) {
+          if (g) cudaGraphDestroy(g);
+          return cs;
+        }
+        DNGD_CUDA_CHECK(e);
+        DNGD_CUDA_CHECK(cudaGraphInstantiate(P.chunk_exec, g, 0));
+        cudaGraphDestroy(g);
+        P.chunk_key[0] = P.lambda;
+        P.chunk_key[1] = (double)chunk;
+        P.chunk_key[3] = xkey;
       }
-      DNGD_NOTE_LAUNCH();
-      k_cg_alpha<<<1, 256, 0, st>>>(nAp, pap_parts, sc);
-      DNGD_NOTE_LAUNCH();
-      k_cg_update_x<<<kVecBlocks, 256, 0, st>>>(m, sc, x, P.res, P.p, P.Ap, part_a);
-      DNGD_NOTE_LAUNCH();
-      k_cg_check<<<1, 256, 0, st>>>(kVecBlocks, part_a, sc);
-      if ((s = precond(P, P.res, P.z, st))) return s;
-      DNGD_NOTE_LAUNCH();
-      k_dot_parts<<<kVecBlocks, 256, 0, st>>>(m, P.res, P.z, part_b, sc);
-      DNGD_NOTE_LAUNCH();
-      k_cg_beta<<<1, 256, 0, st>>>(kVecBlocks, part_b, sc);
-      DNGD_NOTE_LAUNCH();
-      k_cg_update_p<<<cdiv(m, 256), 256, 0, st>>>(m, sc, P.z, P.p);
-      DNGD_LAUNCH_CHECK();
+      DNGD_CUDA_CHECK(cudaGraphLaunch(*P.chunk_exec, st));
+      for (int k = 0; k < (int)P.chunk_key[2]; ++k) note_launch();
+      it += chunk;
+    } else {
+      for (int k = 0; k < chunk && it < maxit; ++k, ++it)
+        if ((s = pcg_iteration(P, x, P.ev && it == 0, st))) return s;
     }
     if (async) {
       if (it >= maxit) break;
