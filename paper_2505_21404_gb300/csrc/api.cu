@@ -58,6 +58,9 @@ struct dngd_ctx {
   void* oz_slices = nullptr;
   double* oz_partials = nullptr;
   float2* K64 = nullptr;      // exact Gram as double-float pairs (full symmetric, no shift)
+  float* LinvT = nullptr;     // transpose of Linv (exact-Gram persistent PCG)
+  void* pstate = nullptr;     // grid-barrier state of the persistent PCG
+  double* pwork = nullptr;    // [7 m] vectors of the persistent PCG
   Tc3Scratch tc3;             // split operands of the TF32 tensor-core GEMMs (mixed paths)
   cudaStream_t cap_st = nullptr;                 // capture stream of the PCG chunk graphs
   cudaGraphExec_t pcg_chunk[2] = {nullptr, nullptr};
@@ -312,9 +315,14 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
   const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
   const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
   if (c->prec == DNGD_MIXED_OZ) {
-    // the exact FP64 Gram is the operator: one m x m GEMV per iteration
+    // the exact FP64 Gram is the operator: one m x m GEMV per iteration; the
+    // synchronous solve is one persistent cooperative kernel
     P.K64 = c->K64;
     P.ldk64 = c->ldk;
+    P.LinvT = c->LinvT;
+    P.pstate = c->pstate;
+    P.pwork = c->pwork;
+    P.status = c->status;
   }
   if (!c->async) {
     if (!c->cap_st) DNGD_CUDA_CHECK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
@@ -448,6 +456,8 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st, tc3p(c),
                                c->status)))
       return s;
+    // row-oriented access to Linv^T for the persistent solve
+    if (c->LinvT && (s = transpose_f32(m, c->Linv, c->ldk, c->LinvT, c->ldk, c->st))) return s;
   }
   // a failed factorisation stops the (synchronous) step here
   if (!c->async && (s = read_status(c))) return s;
@@ -851,6 +861,9 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     add(tc3_bytes(c));                            // TF32 tensor-core GEMM splits
     if (oz) {
       add(sizeof(float2) * (size_t)m * c->ldk);   // K64
+      add(sizeof(float) * (size_t)m * c->ldk);    // LinvT
+      add(256);                                   // persistent-PCG barrier state
+      add(sizeof(double) * 7 * (size_t)m);        // persistent-PCG vectors
       add(gram_oz_slice_bytes(m, (int)n));
       add(gram_oz_partial_bytes(m, (int)n));
     } else {
@@ -921,6 +934,9 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->tc3.buf, float, c->tc3.bytes / sizeof(float));
     if (oz) {
       A_(c->K64, float2, (size_t)m * c->ldk);
+      A_(c->LinvT, float, (size_t)m * c->ldk);
+      A_(c->pstate, unsigned char, 256);
+      A_(c->pwork, double, 7 * (size_t)m);
       A_(c->oz_slices, unsigned char, gram_oz_slice_bytes(m, (int)n));
       c->gram_partial_bytes = gram_oz_partial_bytes(m, (int)n);
       A_(c->oz_partials, double, c->gram_partial_bytes / sizeof(double));

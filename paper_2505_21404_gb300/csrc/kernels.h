@@ -77,6 +77,17 @@ dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cu
 dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const double* Dinv, const double* b, double* x,
                                 double* w, double* y, cudaStream_t st);
 
+// ---- pcg_persist.cu: one cooperative kernel per exact-Gram PCG solve ------
+size_t pcg_persist_state_bytes();
+dngd_status transpose_f32(int m, const float* A, long long lda, float* T, long long ldt, cudaStream_t st);
+// INVALID_ARG when the cooperative grid cannot be formed (callers then use
+// the per-kernel loop).  Results in scal (S_ITERS, S_RR, S_BB, ...).
+// work: [7 m] doubles.
+dngd_status pcg_persist_solve(int m, const float2* K, long long ldk, double lambda, const float* Linv,
+                              const float* LinvT, long long ldi, const double* b, double* x, double* work,
+                              double* parts, long long parts_cap, double* scal, double tol, int maxit, void* state,
+                              int* status, cudaStream_t st);
+
 // ---- tc3.cu: FP32 GEMM on TF32 tensor cores with hi/lo splits -----------
 struct Tc3Scratch {
   float* buf = nullptr;
@@ -151,6 +162,12 @@ struct PcgMixed {
   // exact-Gram mode: operator A = K64 (full symmetric double-float Gram, one GEMV)
   const float2* K64 = nullptr;
   long long ldk64 = 0;
+  // exact-Gram synchronous solves: the persistent cooperative PCG kernel
+  // (needs Linv^T and a barrier state word)
+  const float* LinvT = nullptr;
+  void* pstate = nullptr;
+  double* pwork = nullptr;            // [7 m]
+  int* status = nullptr;
   // synchronous solves: chunks of iterations captured once into a graph on
   // the stream cap and replayed (key: lambda, chunk size, kernels per chunk,
   // solution pointer)

@@ -1,0 +1,447 @@
+// Persistent PCG for the exact-Gram path: the whole solve of
+// (K + lambda I) x = b (Alg. DenseDualSolve's refinement, preconditioned by
+// the FP32 factor M^{-1} = Linv^T Linv) is one cooperative kernel.
+//
+// Every block owns a contiguous range of rows; each phase of an iteration is
+// a row-parallel GEMV (warp per row, the input vector staged in shared memory,
+// double-float accumulation) followed by a grid barrier; block partial sums
+// are reduced by every block in the same order, so all blocks take the same
+// decisions and the result is deterministic.  Vectors written during the
+// kernel are read with L2-only loads (another SM may have written them).
+// p and r are double-buffered, so each iteration needs three barriers:
+//   p = z + beta p_prev (staged whole by every block), Ap = K p + lambda p,
+//     <p, Ap>                                                    | barrier
+//   r_new = r - alpha Ap staged whole by every block (each forms the same
+//     ||r_new||^2: the stop test needs no barrier), x += alpha p on owned
+//     rows, y = Linv r_new (lower triangle only)                 | barrier
+//   z = Linv^T y (upper triangle of the stored transpose), <r_new, z> | barrier
+// The grid barrier is an arrival counter plus a generation word; every wait
+// is bounded by a global-timer deadline after which the kernel records
+// ST_TIMEOUT and all blocks leave.  The launch is cooperative, so all blocks
+// are co-resident.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "step_kernels.h"
+
+namespace dngd {
+
+namespace {
+
+constexpr int PT = 256;                         // threads per block
+constexpr unsigned long long kBarrierNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct PcgState {
+  unsigned int count;       // arrivals at the current barrier
+  unsigned int gen;         // barrier generation
+  int abort;                // set by a block whose wait ran out
+  int pad;
+};
+
+// Returns false (all threads) if the barrier timed out or another block did.
+__device__ bool grid_barrier(PcgState* gs, unsigned nblocks, int* status) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &gs->gen;
+    volatile int* ab = &gs->abort;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gs->count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == nblocks) {
+      gs->count = 0;
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      const unsigned long long t0 = gtime();
+      while (*gen == g) {
+        if (*ab) {
+          ok = 0;
+          break;
+        }
+        if (gtime() - t0 > kBarrierNs) {
+          atomicOr(status, ST_TIMEOUT);
+          atomicExch(&gs->abort, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_sh = ok && !*ab;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// Fixed-order sum of nb block partials (valid in every thread).
+__device__ double sum_parts(const double* parts, int nb) {
+  __shared__ double red[PT / 32];
+  __shared__ double tot;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += PT) s += __ldcg(parts + i);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < PT / 32; ++w) t += red[w];
+    tot = t;
+  }
+  __syncthreads();
+  const double v = tot;
+  __syncthreads();
+  return v;
+}
+
+// Block sum of v (valid in thread 0).
+__device__ double block_sum(double v) {
+  __shared__ double red[PT / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < PT / 32; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// Stage v[0, m) in shared memory as (hi, lo) float pairs.
+__device__ void stage(const double* __restrict__ v, float2* __restrict__ sv, int m) {
+  __syncthreads();
+  for (int j0 = threadIdx.x; j0 < m; j0 += 8 * PT) {
+    double x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + u * PT;
+      x[u] = j < m ? __ldcg(v + j) : 0.0;   // written by other blocks: bypass L1
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + u * PT;
+      if (j < m) {
+        const float h = (float)x[u];
+        sv[j] = make_float2(h, (float)(x[u] - (double)h));
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Row of an FP32 matrix (columns [c0, c1)) times the staged vector; eight
+// loads in flight per lane, two double-float accumulators.
+__device__ double row_dot_f32(const float* __restrict__ A, int c0, int c1, const float2* __restrict__ sv) {
+  const int lane = threadIdx.x & 31;
+  dfloat acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+  int j = c0 + lane;
+  for (; j + 7 * 32 < c1; j += 8 * 32) {
+    float a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = __ldg(A + j + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      const float2 x0 = sv[j + 32 * u], x1 = sv[j + 32 * (u + 1)];
+      acc0 = df_fma(acc0, a[u], x0.x);
+      acc0.lo = fmaf(a[u], x0.y, acc0.lo);
+      acc1 = df_fma(acc1, a[u + 1], x1.x);
+      acc1.lo = fmaf(a[u + 1], x1.y, acc1.lo);
+    }
+  }
+  for (; j < c1; j += 32) {
+    const float a = __ldg(A + j);
+    const float2 x = sv[j];
+    acc0 = df_fma(acc0, a, x.x);
+    acc0.lo = fmaf(a, x.y, acc0.lo);
+  }
+  dfloat acc = df_warp_sum(df_add(acc0, acc1));
+  return (double)acc.hi + (double)acc.lo;
+}
+
+// Row of the double-float Gram times the staged vector (same scheme).
+__device__ double row_dot_df(const float2* __restrict__ A, int m, const float2* __restrict__ sv) {
+  const int lane = threadIdx.x & 31;
+  dfloat acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+  int j = lane;
+  for (; j + 7 * 32 < m; j += 8 * 32) {
+    float2 a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = __ldg(A + j + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      const float2 x0 = sv[j + 32 * u], x1 = sv[j + 32 * (u + 1)];
+      acc0 = df_fma(acc0, a[u].x, x0.x);
+      acc0.lo = fmaf(a[u].x, x0.y, fmaf(a[u].y, x0.x, acc0.lo));
+      acc1 = df_fma(acc1, a[u + 1].x, x1.x);
+      acc1.lo = fmaf(a[u + 1].x, x1.y, fmaf(a[u + 1].y, x1.x, acc1.lo));
+    }
+  }
+  for (; j < m; j += 32) {
+    const float2 a = __ldg(A + j);
+    const float2 x = sv[j];
+    acc0 = df_fma(acc0, a.x, x.x);
+    acc0.lo = fmaf(a.x, x.y, fmaf(a.y, x.x, acc0.lo));
+  }
+  dfloat acc = df_warp_sum(df_add(acc0, acc1));
+  return (double)acc.hi + (double)acc.lo;
+}
+
+__global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restrict__ K, long long ldk, double lambda,
+                                                    const float* __restrict__ Linv, const float* __restrict__ LinvT,
+                                                    long long ldi, const double* __restrict__ b,
+                                                    double* __restrict__ x, double* __restrict__ r0b,
+                                                    double* __restrict__ r1b, double* __restrict__ p0b,
+                                                    double* __restrict__ p1b, double* __restrict__ z,
+                                                    double* __restrict__ Ap, double* __restrict__ y,
+                                                    double* __restrict__ parts, double* scal, double tol, int maxit,
+                                                    PcgState* gs, int* status) {
+  extern __shared__ float2 sv[];   // [m]
+  __shared__ double red_sh[PT / 32];
+  const unsigned nb = gridDim.x;
+  const int per = (m + (int)nb - 1) / (int)nb;
+  const int ra = min(m, (int)blockIdx.x * per), rb = min(m, ra + per);   // rows this block updates
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = PT / 32;
+  // GEMV rows go round-robin over all warps of the grid (the triangular
+  // factor's rows differ in length)
+  const int gw = (int)blockIdx.x * nw + warp, GW = (int)nb * nw;
+  double* p_pap = parts;           // [nb] per quantity, rewritten once per iteration
+  double* p_rz = parts + nb;
+  double* p_bb = parts + 2 * nb;
+  double* rbuf[2] = {r0b, r1b};
+  double* pbuf[2] = {p0b, p1b};
+
+  // x = 0, r = b; z = M^{-1} r
+  for (int i = ra + threadIdx.x; i < rb; i += PT) {
+    x[i] = 0.0;
+    r0b[i] = b[i];
+  }
+  if (!grid_barrier(gs, nb, status)) return;
+  stage(r0b, sv, m);
+  for (int i = gw; i < m; i += GW) {
+    const double v = row_dot_f32(Linv + (long long)i * ldi, 0, i + 1, sv);
+    if (lane == 0) y[i] = v;
+  }
+  if (!grid_barrier(gs, nb, status)) return;
+  stage(y, sv, m);
+  {
+    double rz = 0.0, bb = 0.0;
+    for (int i = gw; i < m; i += GW) {
+      const double v = row_dot_f32(LinvT + (long long)i * ldi, i, m, sv);
+      if (lane == 0) {
+        z[i] = v;
+        rz += __ldcg(r0b + i) * v;
+        bb += b[i] * b[i];
+      }
+    }
+    rz = block_sum(rz);
+    bb = block_sum(bb);
+    if (threadIdx.x == 0) {
+      p_rz[blockIdx.x] = rz;
+      p_bb[blockIdx.x] = bb;
+    }
+  }
+  if (!grid_barrier(gs, nb, status)) return;
+  double rho = sum_parts(p_rz, nb);
+  const double bbt = sum_parts(p_bb, nb);
+  const double tol2 = tol * tol * bbt;
+  double rr = bbt, beta = 0.0;
+  int it = 0;
+  bool done = bbt == 0.0, brk = false;
+  while (!done && it < maxit) {
+    double* pc = pbuf[it & 1];
+    const double* pp = pbuf[(it + 1) & 1];
+    const double* rc = rbuf[it & 1];
+    double* rn = rbuf[(it + 1) & 1];
+    // A: p = z + beta p_prev (every block stages all of it, the owners store
+    //    their rows); Ap = K p + lambda p with the block partials of <p, Ap>
+    __syncthreads();
+    for (int j0 = threadIdx.x; j0 < m; j0 += 8 * PT) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u * PT;
+        v[u] = j < m ? (it == 0 ? __ldcg(z + j) : __ldcg(z + j) + beta * __ldcg(pp + j)) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u * PT;
+        if (j < m) {
+          const float h = (float)v[u];
+          sv[j] = make_float2(h, (float)(v[u] - (double)h));
+          if (j >= ra && j < rb) pc[j] = v[u];
+        }
+      }
+    }
+    __syncthreads();
+    double pap = 0.0;
+    for (int i = gw; i < m; i += GW) {
+      const double pi = (double)sv[i].x + (double)sv[i].y;
+      const double v = row_dot_df(K + (long long)i * ldk, m, sv) + lambda * pi;
+      if (lane == 0) {
+        Ap[i] = v;
+        pap += pi * v;
+      }
+    }
+    pap = block_sum(pap);
+    if (threadIdx.x == 0) p_pap[blockIdx.x] = pap;
+    if (!grid_barrier(gs, nb, status)) return;
+    const double pAp = sum_parts(p_pap, nb);
+    if (!(pAp > 1e-300)) {
+      brk = true;
+      break;
+    }
+    const double alpha = rho / pAp;
+    // B: r_new = r - alpha Ap for all rows (staged; every block forms the same
+    //    ||r_new||^2 in the same order), x += alpha p on the owned rows, stop
+    //    test, y = Linv r_new
+    __syncthreads();
+    double rrl = 0.0;
+    for (int j0 = threadIdx.x; j0 < m; j0 += 8 * PT) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u * PT;
+        v[u] = j < m ? __ldcg(rc + j) - alpha * __ldcg(Ap + j) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u * PT;
+        if (j < m) {
+          rrl += v[u] * v[u];
+          const float h = (float)v[u];
+          sv[j] = make_float2(h, (float)(v[u] - (double)h));
+          if (j >= ra && j < rb) {
+            rn[j] = v[u];
+            x[j] = __ldcg(x + j) + alpha * __ldcg(pc + j);
+          }
+        }
+      }
+    }
+    rrl = warp_sum(rrl);
+    if (lane == 0) red_sh[warp] = rrl;
+    __syncthreads();
+    rr = 0.0;
+    for (int w = 0; w < nw; ++w) rr += red_sh[w];
+    ++it;
+    if (rr <= tol2) {
+      done = true;
+      break;
+    }
+    for (int i = gw; i < m; i += GW) {
+      const double v = row_dot_f32(Linv + (long long)i * ldi, 0, i + 1, sv);
+      if (lane == 0) y[i] = v;
+    }
+    if (!grid_barrier(gs, nb, status)) return;
+    // C: z = Linv^T y with the block partials of <r_new, z>
+    stage(y, sv, m);
+    double rz = 0.0;
+    for (int i = gw; i < m; i += GW) {
+      const double v = row_dot_f32(LinvT + (long long)i * ldi, i, m, sv);
+      if (lane == 0) {
+        z[i] = v;
+        rz += __ldcg(rn + i) * v;
+      }
+    }
+    rz = block_sum(rz);
+    if (threadIdx.x == 0) p_rz[blockIdx.x] = rz;
+    if (!grid_barrier(gs, nb, status)) return;
+    const double rho_new = sum_parts(p_rz, nb);
+    if (rho_new == 0.0 || rho == 0.0) {
+      brk = true;
+      break;
+    }
+    beta = rho_new / rho;
+    rho = rho_new;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scal[S_ITERS] = (double)it;
+    scal[S_RR] = rr;
+    scal[S_BB] = bbt;
+    scal[S_TOL2] = tol2;
+    scal[S_RHO] = rho;
+    scal[S_BREAK] = brk ? 1.0 : 0.0;
+    scal[S_DONE] = 1.0;
+  }
+}
+
+// Linv^T, tile-transposed (ld of both: ldi).
+__global__ void k_transpose_f32(int m, const float* __restrict__ A, long long lda, float* __restrict__ T,
+                                long long ldt) {
+  __shared__ float t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = by + i, c = bx + tx;
+    t[i][tx] = (r < m && c < m) ? A[(long long)r * lda + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int r = bx + i, c = by + tx;
+    if (r < m && c < m) T[(long long)r * ldt + c] = t[tx][i];
+  }
+}
+
+}  // namespace
+
+dngd_status transpose_f32(int m, const float* A, long long lda, float* T, long long ldt, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
+  k_transpose_f32<<<dim3(cdiv(m, 32), cdiv(m, 32)), 256, 0, st>>>(m, A, lda, T, ldt);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+size_t pcg_persist_state_bytes() { return sizeof(PcgState); }
+
+// Blocks of the cooperative grid (co-resident), or 0 if the launch cannot fit.
+static int persist_blocks(int m) {
+  static int cached = -1, cached_m = -1;
+  if (cached >= 0 && cached_m == m) return cached;
+  int dev = 0, nsm = 0, per = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  const size_t smem = sizeof(float2) * (size_t)m;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_pcg_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persist, PT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per = 0;
+  }
+  if (per > 2) per = 2;
+  cached = coop ? per * nsm : 0;
+  cached_m = m;
+  return cached;
+}
+
+dngd_status pcg_persist_solve(int m, const float2* K, long long ldk, double lambda, const float* Linv,
+                              const float* LinvT, long long ldi, const double* b, double* x, double* work,
+                              double* parts, long long parts_cap, double* scal, double tol, int maxit, void* state,
+                              int* status, cudaStream_t st) {
+  const int nb = persist_blocks(m);
+  if (nb <= 0 || 3LL * nb > parts_cap || sizeof(float2) * (size_t)m > 200 * 1024) return DNGD_ERR_INVALID_ARG;
+  DNGD_CUDA_CHECK(cudaMemsetAsync(state, 0, sizeof(PcgState), st));
+  PcgState* gs = (PcgState*)state;
+  double* r0b = work;
+  double* r1b = work + m;
+  double* p0b = work + 2 * (size_t)m;
+  double* p1b = work + 3 * (size_t)m;
+  double* z = work + 4 * (size_t)m;
+  double* Ap = work + 5 * (size_t)m;
+  double* y = work + 6 * (size_t)m;
+  void* args[] = {&m,  &K,  &ldk, &lambda, &Linv, &LinvT, &ldi,  &b,   &x,      &r0b,   &r1b, &p0b,
+                  &p1b, &z, &Ap,  &y,      &parts, &scal, &tol, &maxit, &gs, &status};
+  DNGD_NOTE_LAUNCH();
+  DNGD_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persist, dim3(nb), dim3(PT), args,
+                                              sizeof(float2) * (size_t)m, st));
+  return DNGD_OK;
+}
+
+}  // namespace dngd

@@ -425,6 +425,24 @@ dngd_status pcg_iteration(const PcgMixed& P, double* x, bool timed, cudaStream_t
 
 dngd_status pcg_mixed_solve(const PcgMixed& P, const double* b, double* x, double tol, int maxit, int check_every,
                             int* iters, double* relres, cudaStream_t st, bool async, int slot) {
+  if (!async && P.K64 && P.LinvT && P.pstate && P.pwork) {
+    const dngd_status ps = pcg_persist_solve(P.m, P.K64, P.ldk64, P.lambda, P.Linv, P.LinvT, P.ldk, b, x, P.pwork,
+                                             P.partials, P.partial_cap, P.scal, tol, maxit, P.pstate, P.status, st);
+    if (ps == DNGD_OK) {
+      double* sc = P.scal;
+      const int rec = slot == 0 ? S_IT0 : S_IT1;
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(sc + rec, sc + S_ITERS, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(sc + rec + 1, sc + S_RR, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(sc + rec + 2, sc + S_BB, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(P.scal_h, sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+      DNGD_CUDA_CHECK(cudaStreamSynchronize(st));
+      const double bb = P.scal_h[S_BB];
+      *iters = (int)P.scal_h[S_ITERS];
+      *relres = bb > 0 ? sqrt(P.scal_h[S_RR] / bb) : 0.0;
+      return DNGD_OK;
+    }
+    if (ps != DNGD_ERR_INVALID_ARG) return ps;
+  }
   const int m = P.m;
   double* sc = P.scal;
   double* part_a = P.dotp;          // kVecBlocks partials
