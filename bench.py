@@ -596,7 +596,11 @@ def main():
                      "flops_per_launch": gram_flops, "launch_ms": gram_ms,
                      "algorithmic": "13 m(m+1)n BF16 tensor flops (the exact Gram's 13 slice products)",
                      "exact_gram_tflops_fp64_equivalent": gram_flops / 13.0 / (gram_ms * 1e-3) / 1e12,
-                     "peak_source": f"{src} bf16 sustained (measured)", "traffic": None}
+                     "peak_source": f"{src} bf16 sustained (measured)",
+                     # dram read + write of one launch from the ncu capture of the same kernel on the
+                     # width-128 case (n = 33,921), scaled by n to this workload (same m and tiles)
+                     "traffic": (4.429785e9 * n / 33921.0 + 0.33452e9) if args.workload == "poisson5d" else None,
+                     "traffic_source": "profiles/k_gram_oz_poisson5d_w128.md (scaled by n)"}
     else:
         roof_gram = {"bound": "tensor", "kernel": "k_gram_tc (tcgen05 syrk, lower 128x256 tiles)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
