@@ -304,6 +304,15 @@ dngd_status dngd_batch_step(dngd_batch* batch, const double* const* theta, const
 /* The context of instance i (for dngd_get_stage, dngd_line_search, ...). */
 dngd_ctx* dngd_batch_context(dngd_batch* batch, int i);
 
+/* Failure detection check (no counterpart in the paper): runs one bounded
+ * device-side wait that cannot be satisfied (a grid barrier missing one
+ * arrival) with a limit of limit_ms (0 < limit_ms <= 1000).  The wait runs
+ * out, the kernel records its timeout and returns, and the call reports
+ * DNGD_ERR_TIMEOUT; the context stays usable.  The same bounded waits guard
+ * every device-side wait of the library (TMA / MMA / epilogue mbarriers, the
+ * persistent PCG's grid barriers). */
+dngd_status dngd_check_wait_expiry(dngd_ctx* ctx, double limit_ms);
+
 /* ---- serving: a request loop over PINN solve jobs ------------------------
  * A job is one PINN solve: a problem, initial parameters, collocation data
  * and a number of D-NGD iterations (step + 31-point line search + update).

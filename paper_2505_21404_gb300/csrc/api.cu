@@ -1332,6 +1332,21 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
   }
 }
 
+dngd_status dngd_check_wait_expiry(dngd_ctx* c, double limit_ms) {
+  if (!c || !(limit_ms > 0.0) || limit_ms > 1000.0) return DNGD_ERR_INVALID_ARG;
+  void* state = c->pstate;
+  bool own = false;
+  if (!state) {
+    if (cudaMalloc(&state, 256) != cudaSuccess) return DNGD_ERR_OOM;
+    own = true;
+  }
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+  dngd_status s = barrier_expiry(state, c->status, limit_ms, c->st);
+  if (!s) s = read_status(c);
+  if (own) cudaFree(state);
+  return s;
+}
+
 dngd_status dngd_set_landmarks(dngd_ctx* c, const int64_t* idx, int ell) {
   if (!c || !idx || !c->pcg || ell < 1 || ell > c->mf.ell || ell > c->m) return DNGD_ERR_INVALID_ARG;
   std::vector<int> keep = c->lm_host;

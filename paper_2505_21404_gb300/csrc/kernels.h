@@ -79,6 +79,9 @@ dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const dou
 
 // ---- pcg_persist.cu: one cooperative kernel per exact-Gram PCG solve ------
 size_t pcg_persist_state_bytes();
+// Runs the grid barrier with one arrival missing, so its bounded wait
+// expires after limit_ms (records ST_TIMEOUT).
+dngd_status barrier_expiry(void* state, int* status, double limit_ms, cudaStream_t st);
 dngd_status transpose_f32(int m, const float* A, long long lda, float* T, long long ldt, cudaStream_t st);
 // INVALID_ARG when the cooperative grid cannot be formed (callers then use
 // the per-kernel loop).  Results in scal (S_ITERS, S_RR, S_BB, ...).

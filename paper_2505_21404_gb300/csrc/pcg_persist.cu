@@ -46,7 +46,8 @@ struct PcgState {
 };
 
 // Returns false (all threads) if the barrier timed out or another block did.
-__device__ bool grid_barrier(PcgState* gs, unsigned nblocks, int* status) {
+__device__ bool grid_barrier(PcgState* gs, unsigned nblocks, int* status,
+                             unsigned long long limit_ns = kBarrierNs) {
   __shared__ int ok_sh;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -67,7 +68,7 @@ __device__ bool grid_barrier(PcgState* gs, unsigned nblocks, int* status) {
           ok = 0;
           break;
         }
-        if (gtime() - t0 > kBarrierNs) {
+        if (gtime() - t0 > limit_ns) {
           atomicOr(status, ST_TIMEOUT);
           atomicExch(&gs->abort, 1);
           ok = 0;
@@ -372,6 +373,13 @@ __global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restr
   }
 }
 
+// Expiry of the bounded grid barrier: the blocks wait for one more arrival
+// than there are blocks, so the wait runs out after limit_ns and the kernel
+// records ST_TIMEOUT and returns (the check that a stuck wait ends cleanly).
+__global__ void k_barrier_expiry(PcgState* gs, int* status, unsigned long long limit_ns) {
+  grid_barrier(gs, gridDim.x + 1, status, limit_ns);
+}
+
 // Linv^T, tile-transposed (ld of both: ldi).
 __global__ void k_transpose_f32(int m, const float* __restrict__ A, long long lda, float* __restrict__ T,
                                 long long ldt) {
@@ -399,6 +407,14 @@ dngd_status transpose_f32(int m, const float* A, long long lda, float* T, long l
 }
 
 size_t pcg_persist_state_bytes() { return sizeof(PcgState); }
+
+dngd_status barrier_expiry(void* state, int* status, double limit_ms, cudaStream_t st) {
+  DNGD_CUDA_CHECK(cudaMemsetAsync(state, 0, sizeof(PcgState), st));
+  DNGD_NOTE_LAUNCH();
+  k_barrier_expiry<<<2, PT, 0, st>>>((PcgState*)state, status, (unsigned long long)(limit_ms * 1e6));
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
 
 // Blocks of the cooperative grid (co-resident), or 0 if the launch cannot fit.
 static int persist_blocks(int m) {

@@ -128,6 +128,7 @@ def _load():
         "dngd_kvp": (C.c_int, [P, P, P]),
         "dngd_precond_apply": (C.c_int, [P, P, P]),
         "dngd_line_search_async": (C.c_int, [P, P, P, P, P, D, C.c_int]),
+        "dngd_check_wait_expiry": (C.c_int, [P, C.c_double]),
         "dngd_server_create": (C.c_int, [C.POINTER(P), C.POINTER(ServerCfg)]),
         "dngd_server_destroy": (C.c_int, [P]),
         "dngd_submit": (C.c_int, [P, C.POINTER(JobDesc), C.POINTER(C.c_uint64)]),
@@ -152,7 +153,7 @@ EXPORTED = ["dngd_status_string", "dngd_version", "dngd_launch_count", "dngd_num
             "dngd_step_async", "dngd_step_wait", "dngd_batch_create", "dngd_batch_destroy", "dngd_batch_size",
             "dngd_batch_step", "dngd_batch_context", "dngd_line_search_async", "dngd_server_create",
             "dngd_server_destroy", "dngd_submit", "dngd_poll", "dngd_cancel", "dngd_server_stats",
-            "dngd_server_drain"]
+            "dngd_server_drain", "dngd_check_wait_expiry"]
 
 
 def _check(status, where):
@@ -287,6 +288,10 @@ class Context:
         _check(lib.dngd_line_search_async(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(delta),
                                           etas.ctypes.data_as(C.POINTER(C.c_double)), int(etas.size)),
                "dngd_line_search_async")
+
+    def check_wait_expiry(self, limit_ms=5.0):
+        """Status of one deliberately unsatisfiable bounded device wait."""
+        return int(lib.dngd_check_wait_expiry(self._h, float(limit_ms)))
 
     def residual_jacobian(self, theta, X, target, r_out, J_out=None):
         _check(lib.dngd_residual_jacobian(self._h, _ptr(theta), _ptr(X), _ptr(target), _ptr(r_out),
