@@ -100,6 +100,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms, dist, device):
+    """The job's time is the slowest rank's (replicas run independently)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, ms_per_step):
+    """Whole-job steps/s: every rank advances its own replica one step per ms_per_step."""
+    return world * 1000.0 / ms_per_step
+
+
 def oracle_full_step(wl, lam):
     """One full FP64 oracle step (stage timings in seconds)."""
     from oracle import residual as ores, step as ostep
@@ -507,14 +522,10 @@ def main():
     torch.cuda.synchronize(dev)
     launches = dngd.dngd_launch_count() - launches0
     clk = clocks.stop()
-    total_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_per_step = total_ms / args.steps
     lat = np.array([a.elapsed_time(b) for a, b in step_ev])
-    value = world * 1000.0 / ms_per_step
+    value = job_value(world, ms_per_step)
     gram_ms = float(np.mean([i["phase_ms"][1] for i in infos]))
     phase = np.mean(np.array([i["phase_ms"] for i in infos]), axis=0).tolist()
     iters = np.mean(np.array([i["solve_iters"] for i in infos]), axis=0).tolist()
