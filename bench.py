@@ -188,8 +188,8 @@ def run_batch(args, rank, world, local_rank):
     dev = torch.device(f"cuda:{local_rank}")
     lam = args.lam
     wls = workloads.poisson2d_batch(64, seed=0, lam=lam)
-    descs = [dngd.make_desc(wl, precision=dngd.MIXED_BF16, refine_tol=args.refine_tol, refine_max_it=60)
-             for wl in wls]
+    bprec = dngd.MIXED_OZ if args.precision == "oz" else dngd.MIXED_BF16
+    descs = [dngd.make_desc(wl, precision=bprec, refine_tol=args.refine_tol, refine_max_it=60) for wl in wls]
     ths = [torch.tensor(wl["theta"], device=dev) for wl in wls]
     Xs = [torch.tensor(wl["X"], device=dev) for wl in wls]
     tgs = [torch.tensor(wl["target"], device=dev) for wl in wls]
@@ -223,15 +223,18 @@ def run_batch(args, rank, world, local_rank):
     t_batch = (time.perf_counter() - t0) / args.steps
     launches = dngd.dngd_launch_count() - l0
     clk = clocks.stop()
-    # the same 64 instances stepped alone, one after another (synchronous API)
+    # the same 64 instances stepped alone, one after another, through the same
+    # captured-graph API (the first call of a context is its synchronous step)
     alone = [dngd.Context(d) for d in descs]
     da = [torch.zeros_like(d) for d in ds]
     for i, c in enumerate(alone):
-        c.step(ths[i], Xs[i], tgs[i], da[i])
+        c.step_async(ths[i], Xs[i], tgs[i], da[i])
+        c.step_wait()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for i, c in enumerate(alone):
-        c.step(ths[i], Xs[i], tgs[i], da[i])
+        c.step_async(ths[i], Xs[i], tgs[i], da[i])
+        c.step_wait()
     torch.cuda.synchronize(dev)
     t_alone = time.perf_counter() - t0
     same = sum(int(torch.equal(a, b)) for a, b in zip(da, ds))
@@ -345,7 +348,8 @@ def run_serving(args, rank, world, local_rank):
     for rate in rates:
         n_jobs = int(min(args.max_jobs, max(4, rate * args.window * 1.2 + 2)))
         jobs = workloads.serving_jobs(n_jobs, rate_per_s=rate, seed=7, lam=args.lam)
-        descs = [dngd.make_desc(wl, precision=dngd.MIXED_BF16, refine_tol=args.refine_tol, refine_max_it=60)
+        sprec = dngd.MIXED_OZ if args.precision == "oz" else dngd.MIXED_BF16
+        descs = [dngd.make_desc(wl, precision=sprec, refine_tol=args.refine_tol, refine_max_it=60)
                  for _, wl, _ in jobs]
         srv = dngd.Server(hbm_budget_bytes=0, max_slots=args.slots)
         ids = []
