@@ -97,13 +97,23 @@ struct Tc3Scratch {
   size_t bytes = 0;
 };
 size_t tc3_scratch_bytes(int M, int N, int K);
+// The scratch's two halves: the A operand's split [M x 2 Kp] and the B
+// operand's split [N x 2 Kp] (row r: tf32 hi in [0, Kp), lo in [Kp, 2 Kp),
+// Kp = K rounded up to 32, zero tails).
+void tc3_halves(const Tc3Scratch& sc, float** a_half, float** b_half);
+enum : unsigned {
+  TC3_A_PRESPLIT = 1u,   // the A half already holds A_op's split (no split launch)
+  TC3_B_PRESPLIT = 2u,   // the B half already holds B_op's split
+  TC3_C_SPLIT = 4u,      // the epilogue also writes the result's split into the A half,
+                         // as the A operand of a following GEMM with K = N (N <= 128, not lower)
+};
 // C = alpha A_op B_op^T + beta C; A_op = A [M x K] (or A^T with transA,
 // A then [K x M]), B_op = B [N x K] (or B^T with transB); lower: only
 // C[i][j], j <= i.  INVALID_ARG when the scratch is too small (callers then
 // use the SIMT GEMM).
 dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long lda, bool transA, const float* B,
                      long long ldb, bool transB, float beta, float* C, long long ldc, bool lower, const Tc3Scratch& sc,
-                     int* status, cudaStream_t st);
+                     int* status, cudaStream_t st, unsigned flags = 0u);
 
 // ---- gram_oz.cu: exact Gram of an FP32 matrix from BF16 integer slices ----
 struct OzPlan;

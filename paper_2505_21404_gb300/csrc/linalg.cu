@@ -343,45 +343,112 @@ template dngd_status cholesky<double>(int, double*, long long, int*, double*, cu
 // in the same elimination loop, builds its inverse (forward substitution on
 // the identity); the panel solve is then a GEMM with that inverse, and the
 // inverse fills the diagonal blocks of the explicit L^{-1}.
+//
+// Register-blocked: thread (tr, tc) of a 16 x 16 grid holds rows 4tr..4tr+3 x
+// columns 4tc..4tc+3 of both the block S (becoming L) and the inverse X.  Per
+// column j one barrier: the owners of column j of S publish it (rows >= j)
+// and the owners of row j-1 of X publish that row, each into a
+// double-buffered shared vector; every thread then applies the rank-1 update
+// of column j to its S block and the elimination of column j-1 to its X block
+// (X's row j-1 was final after column j-1).  Per element the operations and
+// their order are those of the unblocked column loop.
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  return __uint_as_float(u);
+}
+
+// bsplit (optional): the inverse block also goes out as the B operand split
+// of the tensor-core panel GEMM, row i: tf32 hi of X[i][0..Kp) then lo
+// (Kp = kb rounded up to 32, zero beyond kb).
 __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A, long long lda, float* Linv,
-                                                        long long ldi, int* status) {
-  __shared__ float S[kCholNB][kCholNB + 1];
-  __shared__ float X[kCholNB][kCholNB + 1];
-  __shared__ int bad;
-  const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+                                                        long long ldi, float* bsplit, int* status) {
+  __shared__ float colbuf[2][kCholNB];
+  __shared__ float rowbuf[2][kCholNB];
   if (status[0] & ST_NOT_SPD) return;
-  for (int e = tid; e < kCholNB * kCholNB; e += blockDim.x) {
-    const int i = e / kCholNB, j = e % kCholNB;
-    S[i][j] = (i < kb && j <= i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.f;
-    X[i][j] = (i == j) ? 1.f : 0.f;
-  }
-  if (tid == 0) bad = -1;
-  __syncthreads();
-  for (int j = 0; j < kb; ++j) {
-    const float piv = S[j][j];
-    if (!(piv > 0.f)) {
-      if (tid == 0) bad = j;
-      break;
+  const int tid = threadIdx.x;
+  const int tc = tid & 15, tr = tid >> 4;
+  const int i0 = 4 * tr, c0 = 4 * tc;
+  float S[4][4], X[4][4], Lprev[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    Lprev[r] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + r, c = c0 + q;
+      S[r][q] = (i < kb && c <= i) ? A[(long long)(k0 + i) * lda + k0 + c] : 0.f;
+      X[r][q] = (i == c) ? 1.f : 0.f;
     }
-    const float d = sqrtf(piv);
-    const float inv_d = 1.f / d;
-    // phase A: scale column j of L below the diagonal and row j of the inverse
-    if (j + 1 + tid < kb) S[j + 1 + tid][j] *= inv_d;
-    if (tid <= j) X[j][tid] *= inv_d;
-    __syncthreads();
-    if (tid == 0) S[j][j] = d;
-    // phase B: rank-1 update of the trailing block and elimination in X
-    for (int i = j + 1 + ty; i < kb; i += 16) {
-      const float lij = S[i][j];
-      for (int c = j + 1 + tx; c <= i; c += 16) S[i][c] -= lij * S[c][j];
-      for (int c = tx; c <= j; c += 16) X[i][c] -= lij * X[j][c];
-    }
-    __syncthreads();
   }
-  __syncthreads();
+  int bad = -1;
+  for (int jb = 0; jb < kCholNB / 4 && bad < 0; ++jb) {
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = 4 * jb + jj;
+      if (j >= kb || bad >= 0) break;
+      // publish column j of S (rows >= j) and the final row j-1 of X
+      if (tc == jb) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (i0 + r >= j) colbuf[j & 1][i0 + r] = S[r][jj];
+      }
+      if (j > 0 && tr == (j - 1) >> 2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c0 + q <= j - 1) rowbuf[(j - 1) & 1][c0 + q] = X[(jj + 3) & 3][q];
+      }
+      __syncthreads();
+      const float piv = colbuf[j & 1][j];
+      if (!(piv > 0.f)) {   // the same value in every thread: a uniform exit
+        bad = j;
+        break;
+      }
+      const float d = sqrtf(piv);
+      const float inv_d = 1.f / d;
+      // elimination of column j-1 in X: X[i][c] -= L[i][j-1] X[j-1][c], i >= j
+      if (j > 0) {
+        float xr[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xr[q] = (c0 + q <= j - 1) ? rowbuf[(j - 1) & 1][c0 + q] : 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (i0 + r >= j) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (c0 + q <= j - 1) X[r][q] -= Lprev[r] * xr[q];
+          }
+      }
+      // column j of L and the rank-1 update of the trailing block
+      float Li[4], Lc[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) Li[r] = (i0 + r > j) ? colbuf[j & 1][i0 + r] * inv_d : 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Lc[q] = (c0 + q > j) ? colbuf[j & 1][c0 + q] * inv_d : 0.f;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c0 + q > j && c0 + q <= i0 + r) S[r][q] -= Li[r] * Lc[q];
+        Lprev[r] = Li[r];
+      }
+      if (tc == jb) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (i0 + r > j) S[r][jj] = Li[r];
+          if (i0 + r == j) S[r][jj] = d;
+        }
+      }
+      // row j of X is final after its scaling
+      if (tr == jb) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c0 + q <= j) X[jj][q] *= inv_d;
+      }
+    }
+  }
   if (bad >= 0) {
     if (tid == 0) {
       const int old = atomicOr(status, ST_NOT_SPD);
@@ -389,38 +456,62 @@ __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A,
     }
     return;
   }
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
-    const int i = e / kb, j = e % kb;
-    if (j <= i) A[(long long)(k0 + i) * lda + k0 + j] = S[i][j];
-    Linv[(long long)(k0 + i) * ldi + k0 + j] = (j <= i) ? X[i][j] : 0.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + r, c = c0 + q;
+      if (i < kb && c < kb) {
+        if (c <= i) A[(long long)(k0 + i) * lda + k0 + c] = S[r][q];
+        Linv[(long long)(k0 + i) * ldi + k0 + c] = (c <= i) ? X[r][q] : 0.f;
+      }
+      const int kp = (kb + 31) & ~31;
+      if (bsplit && i < kb && c < kp) {
+        const float x = (c <= i && c < kb) ? X[r][q] : 0.f;
+        const float hi = tf32_round(x);
+        bsplit[(long long)i * 2 * kp + c] = hi;
+        bsplit[(long long)i * 2 * kp + kp + c] = tf32_round(x - hi);
+      }
+    }
   }
 }
 
 // A = L L^T (FP32, in place, lower) and the diagonal 64-blocks of L^{-1} in
 // Linv (which must be zero-initialised by the caller).
+// With the tensor-core GEMMs a 64-column step is four launches: the block
+// factor (which also writes its inverse's split as the panel GEMM's B
+// operand), the split of the panel, the panel GEMM (whose epilogue writes the
+// split of the solved panel) and the trailing update reading that split.
 dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long long ldi, int* status,
                              cudaStream_t st, const Tc3Scratch* tc3) {
+  const bool tc = tc3 && tc3->buf && tc3_scratch_bytes(m, m, kCholNB) <= tc3->bytes;
+  float *a_half = nullptr, *b_half = nullptr;
+  if (tc) tc3_halves(*tc3, &a_half, &b_half);
   for (int k0 = 0; k0 < m; k0 += kCholNB) {
     const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
-    DNGD_NOTE_LAUNCH();
-    k_potrf_inv_f32<<<1, 256, 0, st>>>(k0, kb, A, lda, Linv, ldi, status);
-    DNGD_LAUNCH_CHECK();
     const int rest = m - k0 - kb;
+    DNGD_NOTE_LAUNCH();
+    k_potrf_inv_f32<<<1, 256, 0, st>>>(k0, kb, A, lda, Linv, ldi, (tc && rest > 0) ? b_half : nullptr, status);
+    DNGD_LAUNCH_CHECK();
     if (rest <= 0) break;
     float* P = A + (long long)(k0 + kb) * lda + k0;
     const float* I11 = Linv + (long long)k0 * ldi + k0;
+    float* A22 = A + (long long)(k0 + kb) * lda + k0 + kb;
     // panel: P <- P L11^{-T} = P * (L11^{-1})^T (in place: one column tile;
     // the tensor-core form reads P from its split copy)
-    dngd_status s = tc3 ? gemm_tc3(rest, kb, kb, 1.0f, P, lda, false, I11, ldi, false, 0.0f, P, lda, false, *tc3,
-                                   status, st)
-                        : DNGD_ERR_INVALID_ARG;
-    if (s == DNGD_ERR_INVALID_ARG) s = gemm_nt<float>(rest, kb, kb, 1.0f, P, lda, I11, ldi, 0.0f, P, lda, false, st);
-    if (s) return s;
-    float* A22 = A + (long long)(k0 + kb) * lda + k0 + kb;
-    s = tc3 ? gemm_tc3(rest, rest, kb, -1.0f, P, lda, false, P, lda, false, 1.0f, A22, lda, true, *tc3, status, st)
-            : DNGD_ERR_INVALID_ARG;
-    if (s == DNGD_ERR_INVALID_ARG) s = gemm_nt<float>(rest, rest, kb, -1.0f, P, lda, P, lda, 1.0f, A22, lda, true, st);
-    if (s) return s;
+    if (tc) {
+      dngd_status s = gemm_tc3(rest, kb, kb, 1.0f, P, lda, false, I11, ldi, false, 0.0f, P, lda, false, *tc3, status,
+                               st, TC3_B_PRESPLIT | TC3_C_SPLIT);
+      if (s) return s;
+      s = gemm_tc3(rest, rest, kb, -1.0f, P, lda, false, P, lda, false, 1.0f, A22, lda, true, *tc3, status, st,
+                   TC3_A_PRESPLIT);
+      if (s) return s;
+    } else {
+      dngd_status s = gemm_nt<float>(rest, kb, kb, 1.0f, P, lda, I11, ldi, 0.0f, P, lda, false, st);
+      if (s) return s;
+      s = gemm_nt<float>(rest, rest, kb, -1.0f, P, lda, P, lda, 1.0f, A22, lda, true, st);
+      if (s) return s;
+    }
   }
   return DNGD_OK;
 }

@@ -83,7 +83,8 @@ __device__ __forceinline__ uint32_t tc3_idesc() {
 
 __global__ void __launch_bounds__(THREADS3, 1)
 k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int Kp,
-      float alpha, float beta, float* __restrict__ C, long long ldc, int lower, int* status) {
+      float alpha, float beta, float* __restrict__ C, long long ldc, int lower, float* __restrict__ csplit, int kpc,
+      int* status) {
   const int bn = blockIdx.x, bm = blockIdx.y;
   if (lower && bn * T3 > bm * T3 + T3 - 1) return;
   // a factorisation that already failed (the host retries it with a larger
@@ -186,12 +187,37 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
         __syncwarp();
         const int col = bn * T3 + j4 * 32 + lane;
         if (col < N && nk > 0) {
+          // all 32 reads of C are issued before the first write, so the
+          // read-modify-write costs one memory latency per 32 rows
+          float cv[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int row = row0 + i;
+            cv[i] = (beta != 0.f && row < M && (!lower || col <= row)) ? C[(long long)row * ldc + col] : 0.f;
+          }
+#pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int row = row0 + i;
             if (row < M && (!lower || col <= row)) {
-              float* cp = C + (long long)row * ldc + col;
-              const float v = alpha * tb[i * 33 + lane];
-              *cp = beta == 0.f ? v : v + beta * *cp;
+              const float v = alpha * tb[i * 33 + lane] + beta * cv[i];
+              C[(long long)row * ldc + col] = v;
+              if (csplit) {
+                // this tile's rows of the A half were read by this CTA alone
+                // (one column tile) and every MMA reading them has completed
+                const float hi = tf32_rn(v);
+                float* sp = csplit + (long long)row * 2 * kpc;
+                sp[col] = hi;
+                sp[kpc + col] = tf32_rn(v - hi);
+              }
+            }
+          }
+        } else if (csplit && col < kpc && nk > 0) {
+          for (int i = 0; i < 32; ++i) {
+            const int row = row0 + i;
+            if (row < M) {
+              float* sp = csplit + (long long)row * 2 * kpc;
+              sp[col] = 0.f;
+              sp[kpc + col] = 0.f;
             }
           }
         }
@@ -237,6 +263,12 @@ size_t tc3_scratch_bytes(int M, int N, int K) {
   return (size_t)2 * rows * 2 * Kp * sizeof(float) + 1024;
 }
 
+void tc3_halves(const Tc3Scratch& sc, float** a_half, float** b_half) {
+  const size_t half = sc.bytes > 1024 ? ((sc.bytes - 1024) / 2) / sizeof(float) / 32 * 32 : 0;   // floats per half
+  *a_half = sc.buf;
+  *b_half = sc.buf + half;
+}
+
 namespace {
 
 struct MapEntry {
@@ -271,19 +303,23 @@ bool cached_map(float* base, int rows, int Kp, CUtensorMap* out) {
 
 dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long lda, bool transA, const float* B,
                      long long ldb, bool transB, float beta, float* C, long long ldc, bool lower, const Tc3Scratch& sc,
-                     int* status, cudaStream_t st) {
+                     int* status, cudaStream_t st, unsigned flags) {
   if (M <= 0 || N <= 0) return DNGD_OK;
   if (!sc.buf || tc3_scratch_bytes(M, N, K) > sc.bytes || K <= 0) return DNGD_ERR_INVALID_ARG;
+  if ((flags & TC3_C_SPLIT) && (lower || N > T3)) return DNGD_ERR_INVALID_ARG;
   const int Kp = ((K + KB3 - 1) / KB3) * KB3;
-  const size_t half = ((sc.bytes - 1024) / 2) / sizeof(float) / 32 * 32;   // floats per half
-  const int cap_rows = (int)(half / (2 * (size_t)Kp));
-  float* Ab = sc.buf;
-  float* Bh = sc.buf + half;
+  const int kpc = ((N + KB3 - 1) / KB3) * KB3;
+  if ((flags & TC3_C_SPLIT) && tc3_scratch_bytes(M, 0, N) > sc.bytes) return DNGD_ERR_INVALID_ARG;
+  float *Ab, *Bh;
+  tc3_halves(sc, &Ab, &Bh);
+  const int cap_rows = (int)((size_t)(Bh - Ab) / (2 * (size_t)Kp));
   const bool same = A == B && lda == ldb && transA == transB && M == N;
   float* Bb = same ? Ab : Bh;
-  DNGD_NOTE_LAUNCH();
-  k_tc3_split<<<dim3(Kp / 32, cdiv(M, 32)), 256, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, Ab);
-  if (!same) {
+  if (!(flags & TC3_A_PRESPLIT)) {
+    DNGD_NOTE_LAUNCH();
+    k_tc3_split<<<dim3(Kp / 32, cdiv(M, 32)), 256, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, Ab);
+  }
+  if (!same && !(flags & TC3_B_PRESPLIT)) {
     DNGD_NOTE_LAUNCH();
     k_tc3_split<<<dim3(Kp / 32, cdiv(N, 32)), 256, 0, st>>>(N, K, Kp, B, ldb, transB ? 1 : 0, Bb);
   }
@@ -297,7 +333,8 @@ dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long
   }
   DNGD_NOTE_LAUNCH();
   k_tc3<<<dim3(cdiv(N, T3), cdiv(M, T3)), THREADS3, SMEM3, st>>>(mapA, mapB, M, N, Kp, alpha, beta, C, ldc,
-                                                                 lower ? 1 : 0, status);
+                                                                 lower ? 1 : 0,
+                                                                 (flags & TC3_C_SPLIT) ? Ab : nullptr, kpc, status);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
