@@ -339,19 +339,15 @@ template dngd_status cholesky<double>(int, double*, long long, int*, double*, cu
 
 // ---------------------------------------------------------------------------
 // FP32 factorisation for the mixed path (a preconditioner, whose accuracy the
-// refinement restores).  One kernel factors a 64 x 64 diagonal block and,
-// in the same elimination loop, builds its inverse (forward substitution on
-// the identity); the panel solve is then a GEMM with that inverse, and the
-// inverse fills the diagonal blocks of the explicit L^{-1}.
+// refinement restores).  One kernel factors a 64 x 64 diagonal block and
+// builds its inverse; the panel solve is then a GEMM with that inverse, and
+// the inverse fills the diagonal blocks of the explicit L^{-1}.
 //
-// Register-blocked: thread (tr, tc) of a 16 x 16 grid holds rows 4tr..4tr+3 x
-// columns 4tc..4tc+3 of both the block S (becoming L) and the inverse X.  Per
-// column j one barrier: the owners of column j of S publish it (rows >= j)
-// and the owners of row j-1 of X publish that row, each into a
-// double-buffered shared vector; every thread then applies the rank-1 update
-// of column j to its S block and the elimination of column j-1 to its X block
-// (X's row j-1 was final after column j-1).  Per element the operations and
-// their order are those of the unblocked column loop.
+// The 64-block is taken as 2 x 2 blocks of 32: one warp factors a 32 x 32
+// diagonal block in registers (lane i holds row i of the block and of its
+// inverse; column j's entries travel by warp shuffles, so no block barrier
+// per column), and the rest are 32 x 32 products over the whole CTA:
+// L10 = S10 Y00^T, S11 -= L10 L10^T, and (L^{-1})10 = -Y11 (L10 Y00).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ float tf32_round(float x) {
@@ -361,123 +357,187 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(u);
 }
 
+// Cholesky of a 32 x 32 SPD block held by one warp (a[c] = S[lane][c] for
+// c <= lane, zero above): on return a holds row `lane` of L and y row `lane`
+// of L^{-1}.  Column J: the pivot, column J of L, row J of the inverse
+// (scaled), the rank-1 update of the trailing rows, and the elimination of
+// column J from the inverse rows below.  A non-positive pivot is recorded in
+// `bad` (the same in every lane) and the remaining columns run on, their
+// values unused.  The column index is a template parameter so that every
+// register index is static.
+template <int J>
+__device__ __forceinline__ void chol32_col(float (&a)[32], float (&y)[32], int lane, int& bad) {
+  const unsigned full = 0xffffffffu;
+  const float piv = __shfl_sync(full, a[J], J);
+  if (!(piv > 0.f) && bad < 0) bad = J;
+  const float d = sqrtf(piv);
+  const float inv_d = 1.f / d;
+  if (lane > J) a[J] *= inv_d;
+  if (lane == J) {
+    a[J] = d;
+#pragma unroll
+    for (int c = 0; c <= J; ++c) y[c] *= inv_d;
+  }
+#pragma unroll
+  for (int c = J + 1; c < 32; ++c) {
+    const float lc = __shfl_sync(full, a[J], c);
+    if (lane >= c) a[c] -= a[J] * lc;
+  }
+#pragma unroll
+  for (int c = 0; c <= J; ++c) {
+    const float yc = __shfl_sync(full, y[c], J);
+    if (lane > J) y[c] -= a[J] * yc;
+  }
+  if constexpr (J + 1 < 32) chol32_col<J + 1>(a, y, lane, bad);
+}
+
+// Returns -1, or the first column whose pivot is not positive.
+__device__ __forceinline__ int warp_chol32_inv(float (&a)[32], float (&y)[32], int lane) {
+  int bad = -1;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) y[c] = (c == lane) ? 1.f : 0.f;
+  chol32_col<0>(a, y, lane, bad);
+  return bad;
+}
+
 // bsplit (optional): the inverse block also goes out as the B operand split
 // of the tensor-core panel GEMM, row i: tf32 hi of X[i][0..Kp) then lo
 // (Kp = kb rounded up to 32, zero beyond kb).
 __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A, long long lda, float* Linv,
                                                         long long ldi, float* bsplit, int* status) {
-  __shared__ float colbuf[2][kCholNB];
-  __shared__ float rowbuf[2][kCholNB];
+  __shared__ float S[kCholNB][kCholNB + 1];
+  __shared__ float X[kCholNB][kCholNB + 1];
+  __shared__ float T[32][33];
+  __shared__ int bad;
   if (status[0] & ST_NOT_SPD) return;
-  const int tid = threadIdx.x;
-  const int tc = tid & 15, tr = tid >> 4;
-  const int i0 = 4 * tr, c0 = 4 * tc;
-  float S[4][4], X[4][4], Lprev[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    Lprev[r] = 0.f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = i0 + r, c = c0 + q;
-      S[r][q] = (i < kb && c <= i) ? A[(long long)(k0 + i) * lda + k0 + c] : 0.f;
-      X[r][q] = (i == c) ? 1.f : 0.f;
-    }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // lower triangle of the block; rows past kb are identity rows
+  for (int e = tid; e < kCholNB * kCholNB; e += blockDim.x) {
+    const int i = e / kCholNB, j = e % kCholNB;
+    S[i][j] = (i < kb && j <= i) ? A[(long long)(k0 + i) * lda + k0 + j] : (i == j ? 1.f : 0.f);
+    X[i][j] = 0.f;
   }
-  int bad = -1;
-  for (int jb = 0; jb < kCholNB / 4 && bad < 0; ++jb) {
+  if (tid == 0) bad = -1;
+  __syncthreads();
+  // 2 x 2 output elements per thread in the 32 x 32 products
+  const int r0 = 2 * (tid >> 4), c0 = 2 * (tid & 15);
+  for (int half = 0; half < 2; ++half) {
+    const int o = 32 * half;
+    if (warp == 0) {
+      float a[32], y[32];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int j = 4 * jb + jj;
-      if (j >= kb || bad >= 0) break;
-      // publish column j of S (rows >= j) and the final row j-1 of X
-      if (tc == jb) {
+      for (int c = 0; c < 32; ++c) a[c] = (c <= lane) ? S[o + lane][o + c] : 0.f;
+      const int b = warp_chol32_inv(a, y, lane);
+      if (b >= 0) {
+        if (lane == 0) bad = o + b;
+      } else {
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (i0 + r >= j) colbuf[j & 1][i0 + r] = S[r][jj];
-      }
-      if (j > 0 && tr == (j - 1) >> 2) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (c0 + q <= j - 1) rowbuf[(j - 1) & 1][c0 + q] = X[(jj + 3) & 3][q];
-      }
-      __syncthreads();
-      const float piv = colbuf[j & 1][j];
-      if (!(piv > 0.f)) {   // the same value in every thread: a uniform exit
-        bad = j;
-        break;
-      }
-      const float d = sqrtf(piv);
-      const float inv_d = 1.f / d;
-      // elimination of column j-1 in X: X[i][c] -= L[i][j-1] X[j-1][c], i >= j
-      if (j > 0) {
-        float xr[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) xr[q] = (c0 + q <= j - 1) ? rowbuf[(j - 1) & 1][c0 + q] : 0.f;
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (i0 + r >= j) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (c0 + q <= j - 1) X[r][q] -= Lprev[r] * xr[q];
-          }
-      }
-      // column j of L and the rank-1 update of the trailing block
-      float Li[4], Lc[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) Li[r] = (i0 + r > j) ? colbuf[j & 1][i0 + r] * inv_d : 0.f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) Lc[q] = (c0 + q > j) ? colbuf[j & 1][c0 + q] * inv_d : 0.f;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (c0 + q > j && c0 + q <= i0 + r) S[r][q] -= Li[r] * Lc[q];
-        Lprev[r] = Li[r];
-      }
-      if (tc == jb) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          if (i0 + r > j) S[r][jj] = Li[r];
-          if (i0 + r == j) S[r][jj] = d;
+        for (int c = 0; c < 32; ++c) {
+          S[o + lane][o + c] = (c <= lane) ? a[c] : 0.f;
+          X[o + lane][o + c] = (c <= lane) ? y[c] : 0.f;
         }
       }
-      // row j of X is final after its scaling
-      if (tr == jb) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (c0 + q <= j) X[jj][q] *= inv_d;
-      }
     }
+    __syncthreads();
+    if (bad >= 0) break;
+    if (half == 1) break;
+    // L10 = S10 Y00^T
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float s0 = S[32 + r0][k], s1 = S[33 + r0][k];
+      const float y0 = X[c0][k], y1 = X[c0 + 1][k];
+      acc[0][0] += s0 * y0;
+      acc[0][1] += s0 * y1;
+      acc[1][0] += s1 * y0;
+      acc[1][1] += s1 * y1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) S[32 + r0 + p][c0 + q] = acc[p][q];
+    __syncthreads();
+    // S11 -= L10 L10^T (lower triangle)
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) acc[p][q] = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float l0 = S[32 + r0][k], l1 = S[33 + r0][k];
+      const float m0 = S[32 + c0][k], m1 = S[33 + c0][k];
+      acc[0][0] += l0 * m0;
+      acc[0][1] += l0 * m1;
+      acc[1][0] += l1 * m0;
+      acc[1][1] += l1 * m1;
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (c0 + q <= r0 + p) S[32 + r0 + p][32 + c0 + q] -= acc[p][q];
+    __syncthreads();
   }
   if (bad >= 0) {
-    if (tid == 0) {
+    if (tid == 0 && bad < kb) {
       const int old = atomicOr(status, ST_NOT_SPD);
       if (!(old & ST_NOT_SPD)) status[1] = k0 + bad;
     }
     return;
   }
+  // (L^{-1})10 = -Y11 (L10 Y00)
+  {
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float l0 = S[32 + r0][k], l1 = S[33 + r0][k];
+      const float y0 = X[k][c0], y1 = X[k][c0 + 1];
+      acc[0][0] += l0 * y0;
+      acc[0][1] += l0 * y1;
+      acc[1][0] += l1 * y0;
+      acc[1][1] += l1 * y1;
+    }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+    for (int p = 0; p < 2; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = i0 + r, c = c0 + q;
-      if (i < kb && c < kb) {
-        if (c <= i) A[(long long)(k0 + i) * lda + k0 + c] = S[r][q];
-        Linv[(long long)(k0 + i) * ldi + k0 + c] = (c <= i) ? X[r][q] : 0.f;
-      }
-      const int kp = (kb + 31) & ~31;
-      if (bsplit && i < kb && c < kp) {
-        const float x = (c <= i && c < kb) ? X[r][q] : 0.f;
-        const float hi = tf32_round(x);
-        bsplit[(long long)i * 2 * kp + c] = hi;
-        bsplit[(long long)i * 2 * kp + kp + c] = tf32_round(x - hi);
-      }
+      for (int q = 0; q < 2; ++q) T[r0 + p][c0 + q] = acc[p][q];
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) acc[p][q] = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float y0 = X[32 + r0][32 + k], y1 = X[33 + r0][32 + k];
+      const float t0 = T[k][c0], t1 = T[k][c0 + 1];
+      acc[0][0] += y0 * t0;
+      acc[0][1] += y0 * t1;
+      acc[1][0] += y1 * t0;
+      acc[1][1] += y1 * t1;
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) X[32 + r0 + p][c0 + q] = -acc[p][q];
+    __syncthreads();
+  }
+  const int kp = (kb + 31) & ~31;
+  for (int e = tid; e < kCholNB * kCholNB; e += blockDim.x) {
+    const int i = e / kCholNB, c = e % kCholNB;
+    if (i < kb && c < kb) {
+      if (c <= i) A[(long long)(k0 + i) * lda + k0 + c] = S[i][c];
+      Linv[(long long)(k0 + i) * ldi + k0 + c] = (c <= i) ? X[i][c] : 0.f;
+    }
+    if (bsplit && i < kb && c < kp) {
+      const float x = (c <= i && c < kb) ? X[i][c] : 0.f;
+      const float hi = tf32_round(x);
+      bsplit[(long long)i * 2 * kp + c] = hi;
+      bsplit[(long long)i * 2 * kp + kp + c] = tf32_round(x - hi);
     }
   }
 }
 
-// A = L L^T (FP32, in place, lower) and the diagonal 64-blocks of L^{-1} in
-// Linv (which must be zero-initialised by the caller).
 // With the tensor-core GEMMs a 64-column step is four launches: the block
 // factor (which also writes its inverse's split as the panel GEMM's B
 // operand), the split of the panel, the panel GEMM (whose epilogue writes the
