@@ -3,8 +3,9 @@
 // the FP32 factor M^{-1} = Linv^T Linv) is one cooperative kernel.
 //
 // Every block owns a contiguous range of rows; each phase of an iteration is
-// a row-parallel GEMV (warp per row, the input vector staged in shared memory,
-// double-float accumulation) followed by a grid barrier; block partial sums
+// a row-parallel GEMV (warp per row, 16-byte loads with eight in flight per
+// lane, the input vector staged in shared memory as separate hi and lo float
+// arrays, double-float accumulation) followed by a grid barrier; block partial sums
 // are reduced by every block in the same order, so all blocks take the same
 // decisions and the result is deterministic.  Vectors written during the
 // kernel are read with L2-only loads (another SM may have written them).
@@ -116,8 +117,8 @@ __device__ double block_sum(double v) {
   return t;
 }
 
-// Stage v[0, m) in shared memory as (hi, lo) float pairs.
-__device__ void stage(const double* __restrict__ v, float2* __restrict__ sv, int m) {
+// Stage v[0, m) in shared memory as hi and lo floats (sh[j], sl[j]).
+__device__ void stage(const double* __restrict__ v, float* __restrict__ sh, float* __restrict__ sl, int m) {
   __syncthreads();
   for (int j0 = threadIdx.x; j0 < m; j0 += 8 * PT) {
     double x[8];
@@ -131,71 +132,104 @@ __device__ void stage(const double* __restrict__ v, float2* __restrict__ sv, int
       const int j = j0 + u * PT;
       if (j < m) {
         const float h = (float)x[u];
-        sv[j] = make_float2(h, (float)(x[u] - (double)h));
+        sh[j] = h;
+        sl[j] = (float)(x[u] - (double)h);
       }
     }
   }
   __syncthreads();
 }
 
-// Row of an FP32 matrix (columns [c0, c1)) times the staged vector; eight
-// loads in flight per lane, two double-float accumulators.
-__device__ double row_dot_f32(const float* __restrict__ A, int c0, int c1, const float2* __restrict__ sv) {
+__device__ __forceinline__ void acc_f32(dfloat& acc, float a, float xh, float xl) {
+  acc = df_fma(acc, a, xh);
+  acc.lo = fmaf(a, xl, acc.lo);
+}
+
+// Row of an FP32 matrix (columns [c0, c1)) times the staged vector: a scalar
+// head up to a 4-aligned column, float4 loads (eight in flight per lane),
+// a scalar tail; two double-float accumulators.  The row must start on a
+// 16-byte boundary (the caller checks base and leading dimension).
+__device__ double row_dot_f32(const float* __restrict__ A, int c0, int c1, const float* __restrict__ sh,
+                              const float* __restrict__ sl) {
   const int lane = threadIdx.x & 31;
   dfloat acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
-  int j = c0 + lane;
-  for (; j + 7 * 32 < c1; j += 8 * 32) {
-    float a[8];
+  const int a0 = min(c1, (c0 + 3) & ~3);
+  if (c0 + lane < a0) acc_f32(acc0, __ldg(A + c0 + lane), sh[c0 + lane], sl[c0 + lane]);
+  const int n4 = (c1 - a0) >> 2;
+  const float4* A4 = reinterpret_cast<const float4*>(A + a0);
+  const float4* h4 = reinterpret_cast<const float4*>(sh + a0);
+  const float4* l4 = reinterpret_cast<const float4*>(sl + a0);
+  int q = lane;
+  for (; q + 7 * 32 < n4; q += 8 * 32) {
+    float4 a[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = __ldg(A + j + 32 * u);
+    for (int u = 0; u < 8; ++u) a[u] = __ldg(A4 + q + 32 * u);
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      const float2 x0 = sv[j + 32 * u], x1 = sv[j + 32 * (u + 1)];
-      acc0 = df_fma(acc0, a[u], x0.x);
-      acc0.lo = fmaf(a[u], x0.y, acc0.lo);
-      acc1 = df_fma(acc1, a[u + 1], x1.x);
-      acc1.lo = fmaf(a[u + 1], x1.y, acc1.lo);
+    for (int u = 0; u < 8; ++u) {
+      const float4 xh = h4[q + 32 * u], xl = l4[q + 32 * u];
+      acc_f32(acc0, a[u].x, xh.x, xl.x);
+      acc_f32(acc1, a[u].y, xh.y, xl.y);
+      acc_f32(acc0, a[u].z, xh.z, xl.z);
+      acc_f32(acc1, a[u].w, xh.w, xl.w);
     }
   }
-  for (; j < c1; j += 32) {
-    const float a = __ldg(A + j);
-    const float2 x = sv[j];
-    acc0 = df_fma(acc0, a, x.x);
-    acc0.lo = fmaf(a, x.y, acc0.lo);
+  for (; q < n4; q += 32) {
+    const float4 a = __ldg(A4 + q);
+    const float4 xh = h4[q], xl = l4[q];
+    acc_f32(acc0, a.x, xh.x, xl.x);
+    acc_f32(acc1, a.y, xh.y, xl.y);
+    acc_f32(acc0, a.z, xh.z, xl.z);
+    acc_f32(acc1, a.w, xh.w, xl.w);
+  }
+  const int b0 = a0 + 4 * n4;
+  if (b0 + lane < c1) acc_f32(acc1, __ldg(A + b0 + lane), sh[b0 + lane], sl[b0 + lane]);
+  dfloat acc = df_warp_sum(df_add(acc0, acc1));
+  return (double)acc.hi + (double)acc.lo;
+}
+
+__device__ __forceinline__ void acc_df(dfloat& acc, float ah, float al, float xh, float xl) {
+  acc = df_fma(acc, ah, xh);
+  acc.lo = fmaf(ah, xl, fmaf(al, xh, acc.lo));
+}
+
+// Row of the double-float Gram (float2 (hi, lo) per entry) times the staged
+// vector: float4 loads = two entries, eight in flight per lane.  The row must
+// start on a 16-byte boundary.
+__device__ double row_dot_df(const float2* __restrict__ A, int m, const float* __restrict__ sh,
+                             const float* __restrict__ sl) {
+  const int lane = threadIdx.x & 31;
+  dfloat acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+  const float4* A4 = reinterpret_cast<const float4*>(A);
+  const float2* h2 = reinterpret_cast<const float2*>(sh);
+  const float2* l2 = reinterpret_cast<const float2*>(sl);
+  const int m2 = m >> 1;
+  int q = lane;
+  for (; q + 7 * 32 < m2; q += 8 * 32) {
+    float4 a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = __ldg(A4 + q + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float2 xh = h2[q + 32 * u], xl = l2[q + 32 * u];
+      acc_df(acc0, a[u].x, a[u].y, xh.x, xl.x);
+      acc_df(acc1, a[u].z, a[u].w, xh.y, xl.y);
+    }
+  }
+  for (; q < m2; q += 32) {
+    const float4 a = __ldg(A4 + q);
+    const float2 xh = h2[q], xl = l2[q];
+    acc_df(acc0, a.x, a.y, xh.x, xl.x);
+    acc_df(acc1, a.z, a.w, xh.y, xl.y);
+  }
+  if ((m & 1) && lane == 0) {
+    const float2 a = __ldg(A + m - 1);
+    acc_df(acc0, a.x, a.y, sh[m - 1], sl[m - 1]);
   }
   dfloat acc = df_warp_sum(df_add(acc0, acc1));
   return (double)acc.hi + (double)acc.lo;
 }
 
-// Row of the double-float Gram times the staged vector (same scheme).
-__device__ double row_dot_df(const float2* __restrict__ A, int m, const float2* __restrict__ sv) {
-  const int lane = threadIdx.x & 31;
-  dfloat acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
-  int j = lane;
-  for (; j + 7 * 32 < m; j += 8 * 32) {
-    float2 a[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = __ldg(A + j + 32 * u);
-#pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      const float2 x0 = sv[j + 32 * u], x1 = sv[j + 32 * (u + 1)];
-      acc0 = df_fma(acc0, a[u].x, x0.x);
-      acc0.lo = fmaf(a[u].x, x0.y, fmaf(a[u].y, x0.x, acc0.lo));
-      acc1 = df_fma(acc1, a[u + 1].x, x1.x);
-      acc1.lo = fmaf(a[u + 1].x, x1.y, fmaf(a[u + 1].y, x1.x, acc1.lo));
-    }
-  }
-  for (; j < m; j += 32) {
-    const float2 a = __ldg(A + j);
-    const float2 x = sv[j];
-    acc0 = df_fma(acc0, a.x, x.x);
-    acc0.lo = fmaf(a.x, x.y, fmaf(a.y, x.x, acc0.lo));
-  }
-  dfloat acc = df_warp_sum(df_add(acc0, acc1));
-  return (double)acc.hi + (double)acc.lo;
-}
-
-__global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restrict__ K, long long ldk, double lambda,
+__global__ void __launch_bounds__(PT, 2) k_pcg_persist(int m, const float2* __restrict__ K, long long ldk, double lambda,
                                                     const float* __restrict__ Linv, const float* __restrict__ LinvT,
                                                     long long ldi, const double* __restrict__ b,
                                                     double* __restrict__ x, double* __restrict__ r0b,
@@ -204,7 +238,10 @@ __global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restr
                                                     double* __restrict__ Ap, double* __restrict__ y,
                                                     double* __restrict__ parts, double* scal, double tol, int maxit,
                                                     PcgState* gs, int* status) {
-  extern __shared__ float2 sv[];   // [m]
+  extern __shared__ float4 sv_raw[];
+  const int mpad = (m + 3) & ~3;
+  float* sh = reinterpret_cast<float*>(sv_raw);   // [mpad] hi
+  float* sl = sh + mpad;                          // [mpad] lo
   __shared__ double red_sh[PT / 32];
   const unsigned nb = gridDim.x;
   const int per = (m + (int)nb - 1) / (int)nb;
@@ -225,17 +262,17 @@ __global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restr
     r0b[i] = b[i];
   }
   if (!grid_barrier(gs, nb, status)) return;
-  stage(r0b, sv, m);
+  stage(r0b, sh, sl, m);
   for (int i = gw; i < m; i += GW) {
-    const double v = row_dot_f32(Linv + (long long)i * ldi, 0, i + 1, sv);
+    const double v = row_dot_f32(Linv + (long long)i * ldi, 0, i + 1, sh, sl);
     if (lane == 0) y[i] = v;
   }
   if (!grid_barrier(gs, nb, status)) return;
-  stage(y, sv, m);
+  stage(y, sh, sl, m);
   {
     double rz = 0.0, bb = 0.0;
     for (int i = gw; i < m; i += GW) {
-      const double v = row_dot_f32(LinvT + (long long)i * ldi, i, m, sv);
+      const double v = row_dot_f32(LinvT + (long long)i * ldi, i, m, sh, sl);
       if (lane == 0) {
         z[i] = v;
         rz += __ldcg(r0b + i) * v;
@@ -276,7 +313,8 @@ __global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restr
         const int j = j0 + u * PT;
         if (j < m) {
           const float h = (float)v[u];
-          sv[j] = make_float2(h, (float)(v[u] - (double)h));
+          sh[j] = h;
+          sl[j] = (float)(v[u] - (double)h);
           if (j >= ra && j < rb) pc[j] = v[u];
         }
       }
@@ -284,8 +322,8 @@ __global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restr
     __syncthreads();
     double pap = 0.0;
     for (int i = gw; i < m; i += GW) {
-      const double pi = (double)sv[i].x + (double)sv[i].y;
-      const double v = row_dot_df(K + (long long)i * ldk, m, sv) + lambda * pi;
+      const double pi = (double)sh[i] + (double)sl[i];
+      const double v = row_dot_df(K + (long long)i * ldk, m, sh, sl) + lambda * pi;
       if (lane == 0) {
         Ap[i] = v;
         pap += pi * v;
@@ -318,7 +356,8 @@ __global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restr
         if (j < m) {
           rrl += v[u] * v[u];
           const float h = (float)v[u];
-          sv[j] = make_float2(h, (float)(v[u] - (double)h));
+          sh[j] = h;
+          sl[j] = (float)(v[u] - (double)h);
           if (j >= ra && j < rb) {
             rn[j] = v[u];
             x[j] = __ldcg(x + j) + alpha * __ldcg(pc + j);
@@ -337,15 +376,15 @@ __global__ void __launch_bounds__(PT) k_pcg_persist(int m, const float2* __restr
       break;
     }
     for (int i = gw; i < m; i += GW) {
-      const double v = row_dot_f32(Linv + (long long)i * ldi, 0, i + 1, sv);
+      const double v = row_dot_f32(Linv + (long long)i * ldi, 0, i + 1, sh, sl);
       if (lane == 0) y[i] = v;
     }
     if (!grid_barrier(gs, nb, status)) return;
     // C: z = Linv^T y with the block partials of <r_new, z>
-    stage(y, sv, m);
+    stage(y, sh, sl, m);
     double rz = 0.0;
     for (int i = gw; i < m; i += GW) {
-      const double v = row_dot_f32(LinvT + (long long)i * ldi, i, m, sv);
+      const double v = row_dot_f32(LinvT + (long long)i * ldi, i, m, sh, sl);
       if (lane == 0) {
         z[i] = v;
         rz += __ldcg(rn + i) * v;
@@ -416,6 +455,8 @@ dngd_status barrier_expiry(void* state, int* status, double limit_ms, cudaStream
   return DNGD_OK;
 }
 
+static size_t persist_smem(int m) { return 2 * sizeof(float) * (size_t)((m + 3) & ~3); }
+
 // Blocks of the cooperative grid (co-resident), or 0 if the launch cannot fit.
 static int persist_blocks(int m) {
   static int cached = -1, cached_m = -1;
@@ -424,7 +465,7 @@ static int persist_blocks(int m) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  const size_t smem = sizeof(float2) * (size_t)m;
+  const size_t smem = persist_smem(m);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_pcg_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persist, PT, smem) != cudaSuccess) {
@@ -442,7 +483,12 @@ dngd_status pcg_persist_solve(int m, const float2* K, long long ldk, double lamb
                               double* parts, long long parts_cap, double* scal, double tol, int maxit, void* state,
                               int* status, cudaStream_t st) {
   const int nb = persist_blocks(m);
-  if (nb <= 0 || 3LL * nb > parts_cap || sizeof(float2) * (size_t)m > 200 * 1024) return DNGD_ERR_INVALID_ARG;
+  if (nb <= 0 || 3LL * nb > parts_cap || persist_smem(m) > 200 * 1024) return DNGD_ERR_INVALID_ARG;
+  // the row products use 16-byte loads: every row of K (float2) and of the
+  // factor (float) must start on a 16-byte boundary
+  if ((reinterpret_cast<uintptr_t>(K) & 15) || (ldk & 1) || (reinterpret_cast<uintptr_t>(Linv) & 15) ||
+      (reinterpret_cast<uintptr_t>(LinvT) & 15) || (ldi & 3))
+    return DNGD_ERR_INVALID_ARG;
   DNGD_CUDA_CHECK(cudaMemsetAsync(state, 0, sizeof(PcgState), st));
   PcgState* gs = (PcgState*)state;
   double* r0b = work;
@@ -456,7 +502,7 @@ dngd_status pcg_persist_solve(int m, const float2* K, long long ldk, double lamb
                   &p1b, &z, &Ap,  &y,      &parts, &scal, &tol, &maxit, &gs, &status};
   DNGD_NOTE_LAUNCH();
   DNGD_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persist, dim3(nb), dim3(PT), args,
-                                              sizeof(float2) * (size_t)m, st));
+                                              persist_smem(m), st));
   return DNGD_OK;
 }
 
