@@ -19,26 +19,30 @@
 //     (13 slice products; the dropped s+t >= 5 terms are below 2^-40 of the
 //     row scales);
 //   * products of slices are exact in the tensor cores, and every chunk the
-//     MMAs accumulate in TMEM stays below 2^24 in magnitude (pairs x k-blocks
-//     <= 16), so the FP32 accumulator is exact; the epilogue adds each chunk
-//     into double-float registers (48-bit significand) with a Horner scaling
-//     by 2^8 between levels.
+//     MMAs accumulate in TMEM stays within 2^24 in magnitude (level g with
+//     n_g products is drained every 2^10 / n_g K columns), so the FP32
+//     accumulator is exact; the epilogue adds each chunk into double-float
+//     registers (48-bit significand) times 2^(8(4-g)).
 //
 // Kernel roles (one 128 x 96 output tile touching the lower triangle and one
-// K range per CTA): warp 0 lane 0 streams, per 64-wide K block, all four A
-// slices (128 rows) and all four B slices (96 rows) with TMA (128-byte
-// swizzle) into a 2-stage ring of 112 KB stages, so one stage feeds all 13
+// K range per CTA): warp 0 lane 0 streams, per 32-wide K block, all four A
+// slices (128 rows) and all four B slices (96 rows) with TMA (64-byte
+// swizzle) into a 4-stage ring of 56 KB stages, so one stage feeds all 13
 // slice products; warp 1 lane 0 issues tcgen05.mma (M = 128, N = 96) into
-// five per-level TMEM accumulators (480 columns) and commits a level every
-// 4 K blocks (the exactness period); warps 2..13 drain a level as soon as it
-// is committed (warp w: TMEM lanes 32 (w % 4).., 32 columns), release it to
-// the MMA warp, and add it times 2^(8(4-g)) into double-float registers.
+// five per-level TMEM accumulators (480 columns) and commits a level at the
+// end of its chunk; the levels' chunk boundaries are staggered and a level
+// that starts a chunk is issued last in its stage, so its drain overlaps the
+// other levels' MMAs; warps 2..13 drain a level as soon as it is committed
+// (warp w: TMEM lanes 32 (w % 4).., 32 columns), release it to the MMA warp,
+// and add it times 2^(8(4-g)) into double-float registers.
 // Split-K partial tiles (FP64) are summed in a fixed order by the reduction,
 // which applies the row scales and writes the full FP64 Gram (the
 // refinement operator) and its FP32 lower triangle plus the diagonal shift
 // (the matrix the FP32 preconditioner factors).  Every wait is bounded
 // (ST_TIMEOUT, drain, free TMEM).
 #include <cuda_bf16.h>
+
+#include <climits>
 
 #include <vector>
 
@@ -64,10 +68,24 @@ constexpr int OSMEM = OST * OSTAGE + 1024;
 constexpr int OTHREADS = 448;               // TMA warp, MMA warp, 12 epilogue warps
 constexpr int EPI_WARPS = 12;
 constexpr uint32_t OTMEM = 512;             // five 96-column level accumulators
-constexpr int PERIOD = 8;                   // stages per exact chunk (4 pairs x 8 x 32 x 2^14 = 2^24)
 
 __host__ __device__ __forceinline__ int g_lo(int g) { return g > NS - 1 ? g - (NS - 1) : 0; }
 __host__ __device__ __forceinline__ int g_hi(int g) { return g < NS - 1 ? g : NS - 1; }
+
+// Stages per exact chunk of level g: n_g = g_hi - g_lo + 1 products of
+// |sigma| <= 128 over period x 32 columns stay within 2^24
+// (1 x 32 x 32, 2 x 16 x 32, 3 x 10 x 32, 4 x 8 x 32, 3 x 10 x 32, times 2^14).
+__host__ __device__ constexpr int period_of(int g) { return g == 0 ? 32 : g == 1 ? 16 : g == 3 ? 8 : 10; }
+// Offsets that stagger the levels' chunk boundaries (the first chunk of level
+// g is period - offset stages long).
+__host__ __device__ constexpr int offset_of(int g) { return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 4 : 7; }
+static_assert(32 * 32 * 1 <= 1024 && 16 * 32 * 2 <= 1024 && 10 * 32 * 3 <= 1024 && 8 * 32 * 4 <= 1024,
+              "a chunk must stay within 2^24 = 2^10 x 2^14");
+// Chunk c of level g covers stages [start, end]: start = 0 for c = 0, else
+// c period - offset; end = (c + 1) period - offset - 1, clamped to nk - 1.
+__device__ __forceinline__ int chunk_end(int g, int c, int nk) {
+  return min(nk - 1, (c + 1) * period_of(g) - offset_of(g) - 1);
+}
 
 // BF16 x BF16 -> FP32, both K-major, N = 96, M = 128.
 __device__ __forceinline__ uint32_t oz_idesc() {
@@ -162,7 +180,6 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   const int kb0 = split * kb_per;
   const int kb1 = min(num_kblk, kb0 + kb_per);
   const int nk = max(0, kb1 - kb0);
-  const int nper = (nk + PERIOD - 1) / PERIOD;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OST; ++s) {
@@ -212,12 +229,17 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = oz_idesc();
+      // per level: current chunk, its first and last stage
+      int cidx[NG], cstart[NG], cend[NG];
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        cidx[g] = 0;
+        cstart[g] = 0;
+        cend[g] = chunk_end(g, 0, nk);
+      }
       for (int it = 0; it < nk && !*abort_flag; ++it) {
         const int st = it % OST;
         const uint32_t ph = (uint32_t)((it / OST) & 1);
-        const int per = it / PERIOD;
-        const bool first = (it % PERIOD) == 0;
-        const bool last = (it % PERIOD) == PERIOD - 1 || it == nk - 1;
         if (!mbar_wait(smem_u32(&full_bar[st]), ph, status, 12)) {
           *abort_flag = 1;
           break;
@@ -227,28 +249,42 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         // descriptors of the stage's first A and B tiles; the others differ
         // only in the start-address field (byte offset / 16, no carry out)
         const uint64_t da0 = sw64_desc(sbase), db0 = sw64_desc(sbase + NS * A_TILE);
+        // pass 0: levels inside a chunk; pass 1: levels starting one, which
+        // first wait until their previous chunk has been drained
+        bool stop = false;
 #pragma unroll
-        for (int g = 0; g < NG; ++g) {
-          if (first) {
-            // level g's accumulator must have been drained (period per - 1)
-            if (!mbar_wait(smem_u32(&acce_bar[g]), (uint32_t)((per & 1) ^ 1), status, 15)) {
-              *abort_flag = 1;
-              break;
+        for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+          for (int g = 0; g < NG; ++g) {
+            const bool first = cstart[g] == it;
+            if (first != (pass == 1) || stop) continue;
+            if (first) {
+              if (!mbar_wait(smem_u32(&acce_bar[g]), (uint32_t)((cidx[g] & 1) ^ 1), status, 15)) {
+                *abort_flag = 1;
+                stop = true;
+                continue;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-          }
-          const uint32_t dbuf = tmem + (uint32_t)(g * TN);
+            const uint32_t dbuf = tmem + (uint32_t)(g * TN);
 #pragma unroll
-          for (int sa = g_lo(g); sa <= g_hi(g); ++sa) {
+            for (int sa = g_lo(g); sa <= g_hi(g); ++sa) {
 #pragma unroll
-            for (int k = 0; k < KS / 16; ++k) {
-              umma<0>(dbuf, da0 + (uint64_t)((sa * A_TILE + 32 * k) >> 4),
-                      db0 + (uint64_t)(((g - sa) * B_TILE + 32 * k) >> 4), idesc,
-                      (first && sa == g_lo(g) && k == 0) ? 0u : 1u);
+              for (int k = 0; k < KS / 16; ++k) {
+                umma<0>(dbuf, da0 + (uint64_t)((sa * A_TILE + 32 * k) >> 4),
+                        db0 + (uint64_t)(((g - sa) * B_TILE + 32 * k) >> 4), idesc,
+                        (first && sa == g_lo(g) && k == 0) ? 0u : 1u);
+              }
+            }
+            if (cend[g] == it) {
+              umma_commit(smem_u32(&accf_bar[g]));
+              ++cidx[g];
+              cstart[g] = it + 1;
+              cend[g] = chunk_end(g, cidx[g], nk);
             }
           }
-          if (last) umma_commit(smem_u32(&accf_bar[g]));
         }
+        if (stop) break;
         umma_commit(smem_u32(&empty_bar[st]));
       }
     }
@@ -262,28 +298,58 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       hi[j] = 0.f;
       lo[j] = 0.f;
     }
-    for (int per = 0; per < nper && !*abort_flag; ++per) {
-      for (int g = 0; g < NG; ++g) {
-        const bool ok = __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&accf_bar[g]),
-                                                                           (uint32_t)(per & 1), status, 13))
-                                                    ? 1
-                                                    : 0) != 0;
-        if (!ok) {
-          *abort_flag = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        uint32_t r[32];
-        TMEM_LD_32(lane_base + (uint32_t)(g * TN), r);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[g])) : "memory");
-        // the level's exact chunk times 2^(8 (4 - g)) (a power of two: exact)
-        const float sc = __int_as_float((127 + 8 * (NG - 1 - g)) << 23);
+    // the chunks in the order the MMA warp commits them: by last stage, a
+    // chunk of one stage (issued in the second pass) after the others, then
+    // by level
+    int cidx[NG], cstart[NG], cend[NG];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) df_add_exact(hi[i], lo[i], __uint_as_float(r[i]) * sc);
+    for (int g = 0; g < NG; ++g) {
+      cidx[g] = 0;
+      cstart[g] = 0;
+      cend[g] = nk > 0 ? chunk_end(g, 0, nk) : INT_MAX;
+    }
+    while (!*abort_flag) {
+      int gsel = -1, kbest = INT_MAX;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        if (cend[g] == INT_MAX) continue;
+        const int key = cend[g] * 2 + (cstart[g] == cend[g] ? 1 : 0);
+        if (key < kbest) {
+          kbest = key;
+          gsel = g;
+        }
       }
+      if (gsel < 0) break;
+      const bool ok =
+          __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&accf_bar[gsel]), (uint32_t)(cidx[gsel] & 1),
+                                                             status, 13))
+                                      ? 1
+                                      : 0) != 0;
+      if (!ok) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t r[32];
+      TMEM_LD_32(lane_base + (uint32_t)(gsel * TN), r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[gsel])) : "memory");
+      // the level's exact chunk times 2^(8 (4 - g)) (a power of two: exact)
+      const float sc = __int_as_float((127 + 8 * (NG - 1 - gsel)) << 23);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) df_add_exact(hi[i], lo[i], __uint_as_float(r[i]) * sc);
+      // next chunk of this level
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+        if (g == gsel) {
+          const int e = cend[g];
+          ++cidx[g];
+          cstart[g] = e + 1;
+          cend[g] = e + 1 < nk ? chunk_end(g, cidx[g], nk) : INT_MAX;
+        }
     }
     const int row = tile.x * TM + q * 32 + lane;
     const int col0 = tile.y * TN + cg * 32;
