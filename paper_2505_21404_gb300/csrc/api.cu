@@ -98,6 +98,8 @@ struct dngd_ctx {
   double graph_lambda = 0.0;
   double* ls_dev = nullptr;          // line search: etas [64], losses [64], result [2]
   double* ls_host = nullptr;         // pinned copy of the etas
+  double* loss_dev = nullptr;        // trial losses of dngd_loss [64]
+  double* loss_host = nullptr;       // pinned copy [64]
   int ls_k = 0;
   double graph_mu = 0.0;
   cudaStream_t gst = nullptr;        // private stream for capture / replay
@@ -991,6 +993,7 @@ void free_ctx(dngd_ctx* c) {
     if (c->pcg_chunk[i]) cudaGraphExecDestroy(c->pcg_chunk[i]);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->ls_host) cudaFreeHost(c->ls_host);
+  if (c->loss_host) cudaFreeHost(c->loss_host);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->gst) cudaStreamDestroy(c->gst);
   for (int i = 0; i < 2; ++i)
@@ -1204,21 +1207,28 @@ dngd_status dngd_loss(dngd_ctx* c, const double* theta, const double* X, const d
   const double* tg = in_ptr(c, target, c->target_s, c->m);
   const double* dl = delta ? in_ptr(c, delta, c->nvec_s, c->n) : nullptr;
   DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
-  std::vector<double> out(k);
-  for (int j = 0; j < k; ++j) {
-    dngd_status s = axpy_to(c->n, th, etas[j], dl, c->theta_tmp, c->st);
-    if (s) return s;
-    if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, x, tg, c->cg_res);
-    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), x, tg, c->cg_res, true);
-    if (s) return s;
-    if ((s = dot_dev(c->m, c->cg_res, c->cg_res, c->scal + S_LOSS, c->dot_partials, c->st))) return s;
-    DNGD_CUDA_CHECK(cudaMemcpyAsync(&c->scal_h[S_LOSS], c->scal + S_LOSS, sizeof(double), cudaMemcpyDeviceToHost,
-                                    c->st));
+  // the trial losses stay on the device (64 per round trip), so the trials'
+  // kernels queue back to back
+  if (!c->loss_dev) {
+    if (cudaMalloc(&c->loss_dev, sizeof(double) * 64) != cudaSuccess) return DNGD_ERR_OOM;
+    c->allocs.push_back(c->loss_dev);
+    DNGD_CUDA_CHECK(cudaMallocHost(&c->loss_host, sizeof(double) * 64));
+  }
+  for (int j0 = 0; j0 < k; j0 += 64) {
+    const int kk = (k - j0) < 64 ? (k - j0) : 64;
+    for (int j = 0; j < kk; ++j) {
+      dngd_status s = axpy_to(c->n, th, etas[j0 + j], dl, c->theta_tmp, c->st);
+      if (s) return s;
+      if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, x, tg, c->cg_res);
+      else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), x, tg, c->cg_res, true);
+      if (s) return s;
+      if ((s = dot_dev(c->m, c->cg_res, c->cg_res, c->loss_dev + j, c->dot_partials, c->st))) return s;
+    }
+    DNGD_CUDA_CHECK(cudaMemcpyAsync(c->loss_host, c->loss_dev, sizeof(double) * kk, cudaMemcpyDeviceToHost, c->st));
     DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
-    loss_out[j] = 0.5 * c->scal_h[S_LOSS];
+    for (int j = 0; j < kk; ++j) loss_out[j0 + j] = 0.5 * c->loss_host[j];
   }
   c->have_step = false;
-  (void)out;
   return read_status(c);
 }
 

@@ -27,57 +27,88 @@ namespace dngd {
 // Forward sweep
 // ---------------------------------------------------------------------------
 
+// Where a forward-only sweep feeds the next layer's 3xTF32 GEMM, the
+// activations go out directly as that GEMM's A operand split (row r:
+// tf32 hi of h[r][0..kp) then lo, zero beyond w) instead of as H, and the
+// pre-activations (needed only by the reverse sweep) are not stored.
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  return __uint_as_float(u);
+}
+
+template <typename T>
+__device__ __forceinline__ void put_h(T* __restrict__ H, float* __restrict__ hs, int kp, long long row, int w, int a,
+                                      T v) {
+  if (hs) {
+    const float x = (float)v, hi = tf32_hi(x);
+    hs[row * 2 * kp + a] = hi;
+    hs[row * 2 * kp + kp + a] = tf32_hi(x - hi);
+  } else {
+    H[row * w + a] = v;
+  }
+}
+
 template <typename T>
 __global__ void k_first_layer(NetInfo net, const T* __restrict__ theta, const double* __restrict__ X,
-                              T* __restrict__ Z, T* __restrict__ H) {
+                              T* __restrict__ Z, T* __restrict__ H, float* __restrict__ hs, int kp) {
   const int p = blockIdx.x;
   const int a = blockIdx.y * blockDim.x + threadIdx.x;
   const int w = net.widths[1], din = net.d_in;
-  if (a >= w) return;
   const ClassInfo& c = class_of(net, p);
+  const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+  if (a >= w) {
+    if (hs && a < kp)
+      for (int j = 0; j < c.S; ++j) put_h<T>(H, hs, kp, row + j, w, a, T(0));
+    return;
+  }
   const T* W = theta + net.w_off[0];
   T z = theta[net.b_off[0] + a];
   for (int k = 0; k < din; ++k) z += W[(long long)a * din + k] * (T)X[(long long)p * din + k];
-  const long long row = c.row0 + (long long)(p - c.p0) * c.S;
   const T t = tanh_t(z), s = T(1) - t * t;
-  Z[row * w + a] = z;
-  H[row * w + a] = t;
+  if (!hs) Z[row * w + a] = z;
+  put_h<T>(H, hs, kp, row, w, a, t);
   T Q = 0;
   for (int j = 0; j < c.nD; ++j) {
     const T zk = W[(long long)a * din + c.D[j]];
-    Z[(row + 1 + j) * w + a] = zk;
-    H[(row + 1 + j) * w + a] = s * zk;
+    if (!hs) Z[(row + 1 + j) * w + a] = zk;
+    put_h<T>(H, hs, kp, row + 1 + j, w, a, s * zk);
     if (c.lapD[j]) Q += zk * zk;
   }
   if (c.has_lap) {
-    Z[(row + 1 + c.nD) * w + a] = T(0);
-    H[(row + 1 + c.nD) * w + a] = T(-2) * t * s * Q;
+    if (!hs) Z[(row + 1 + c.nD) * w + a] = T(0);
+    put_h<T>(H, hs, kp, row + 1 + c.nD, w, a, T(-2) * t * s * Q);
   }
 }
 
 // Hidden layer l >= 1: Z already holds W_l h_{l-1} for every stream row.
 template <typename T>
 __global__ void k_act_fwd(NetInfo net, int l, const T* __restrict__ theta, T* __restrict__ Z,
-                          T* __restrict__ H) {
+                          T* __restrict__ H, float* __restrict__ hs, int kp) {
   const int p = blockIdx.x;
   const int a = blockIdx.y * blockDim.x + threadIdx.x;
   const int w = net.widths[l + 1];
-  if (a >= w) return;
   const ClassInfo& c = class_of(net, p);
   const long long row = c.row0 + (long long)(p - c.p0) * c.S;
+  if (a >= w) {
+    if (hs && a < kp)
+      for (int j = 0; j < c.S; ++j) put_h<T>(H, hs, kp, row + j, w, a, T(0));
+    return;
+  }
   const T z = Z[row * w + a] + theta[net.b_off[l] + a];
   const T t = tanh_t(z), s = T(1) - t * t;
-  Z[row * w + a] = z;
-  H[row * w + a] = t;
+  if (!hs) Z[row * w + a] = z;
+  put_h<T>(H, hs, kp, row, w, a, t);
   T Q = 0;
   for (int j = 0; j < c.nD; ++j) {
     const T zk = Z[(row + 1 + j) * w + a];
-    H[(row + 1 + j) * w + a] = s * zk;
+    put_h<T>(H, hs, kp, row + 1 + j, w, a, s * zk);
     if (c.lapD[j]) Q += zk * zk;
   }
   if (c.has_lap) {
     const T L = Z[(row + 1 + c.nD) * w + a];
-    H[(row + 1 + c.nD) * w + a] = s * L - T(2) * t * s * Q;
+    put_h<T>(H, hs, kp, row + 1 + c.nD, w, a, s * L - T(2) * t * s * Q);
   }
 }
 
@@ -408,25 +439,44 @@ dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, co
                          const Tc3Scratch* tc3) {
   const int L = net.n_layers - 1;
   const int thr = 128;
+  // forward-only sweep on the TF32 tensor cores: every hidden GEMM fits the
+  // scratch, so each layer but the last hands its activations over as the
+  // next GEMM's A operand split
+  bool presplit = false;
+  float *a_half = nullptr, *b_half = nullptr;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc3 && tc3->buf) {
+      presplit = true;
+      for (int l = 1; l < L; ++l)
+        presplit = presplit && tc3_scratch_bytes(net.R, net.widths[l + 1], net.widths[l]) <= tc3->bytes;
+      if (presplit) tc3_halves(*tc3, &a_half, &b_half);
+    }
+  }
   for (int l = 0; l < L; ++l) {
     const int w = net.widths[l + 1];
-    dim3 grid(net.m, cdiv(w, thr));
+    const bool split_out = presplit && l + 1 < L;
+    const int kp = (w + 31) & ~31;
+    float* hs = split_out ? a_half : nullptr;
+    dim3 grid(net.m, cdiv(split_out ? kp : w, thr));
     if (l == 0) {
       DNGD_NOTE_LAUNCH();
-      k_first_layer<T><<<grid, thr, 0, st>>>(net, theta, X, Z.p[0], H.p[0]);
+      k_first_layer<T><<<grid, thr, 0, st>>>(net, theta, X, Z.p[0], H.p[0], hs, kp);
     } else {
       dngd_status s = DNGD_ERR_INVALID_ARG;
       if constexpr (std::is_same<T, float>::value) {
-        if (tc3)
+        if (presplit)
+          s = gemm_tc3(net.R, w, net.widths[l], 1.0f, H.p[l - 1], net.widths[l], false, theta + net.w_off[l],
+                       net.widths[l], false, 0.0f, Z.p[l], w, false, *tc3, status, st, TC3_A_PRESPLIT);
+        else if (tc3)
           s = gemm_tc3(net.R, w, net.widths[l], 1.0f, H.p[l - 1], net.widths[l], false, theta + net.w_off[l],
                        net.widths[l], false, 0.0f, Z.p[l], w, false, *tc3, status, st);
       }
-      if (s == DNGD_ERR_INVALID_ARG)
+      if (s == DNGD_ERR_INVALID_ARG && !presplit)
         s = gemm_nt<T>(net.R, w, net.widths[l], T(1), H.p[l - 1], net.widths[l], theta + net.w_off[l],
                        net.widths[l], T(0), Z.p[l], w, false, st);
       if (s) return s;
       DNGD_NOTE_LAUNCH();
-      k_act_fwd<T><<<grid, thr, 0, st>>>(net, l, theta, Z.p[l], H.p[l]);
+      k_act_fwd<T><<<grid, thr, 0, st>>>(net, l, theta, Z.p[l], H.p[l], hs, kp);
     }
     DNGD_LAUNCH_CHECK();
   }
