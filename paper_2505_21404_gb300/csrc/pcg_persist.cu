@@ -2,12 +2,16 @@
 // (K + lambda I) x = b (Alg. DenseDualSolve's refinement, preconditioned by
 // the FP32 factor M^{-1} = Linv^T Linv) is one cooperative kernel.
 //
-// Every block owns a contiguous range of rows; each phase of an iteration is
-// a row-parallel GEMV (warp per row, 16-byte loads with eight in flight per
-// lane, the input vector staged in shared memory as separate hi and lo float
-// arrays, double-float accumulation) followed by a grid barrier; block partial sums
-// are reduced by every block in the same order, so all blocks take the same
-// decisions and the result is deterministic.  Vectors written during the
+// One 512-thread block per SM (the vector every block stages is read from L2
+// by half as many blocks as with two smaller ones).  Every block owns a
+// contiguous range of rows; each phase of an iteration is a row-parallel
+// GEMV (warp per row, rows taken in pairs (p, m-1-p) so that every warp's
+// share of the triangular factor is the same; 16-byte loads with eight in
+// flight per lane; the input vector staged in shared memory as separate hi
+// and lo float arrays; double-float accumulation) followed by a grid
+// barrier; block partial sums are reduced by every block in the same order,
+// so all blocks take the same decisions and the result is deterministic.
+// Vectors written during the
 // kernel are read with L2-only loads (another SM may have written them).
 // p and r are double-buffered, so each iteration needs three barriers:
 //   p = z + beta p_prev (staged whole by every block), Ap = K p + lambda p,
@@ -30,7 +34,7 @@ namespace dngd {
 
 namespace {
 
-constexpr int PT = 256;                         // threads per block
+constexpr int PT = 512;                         // threads per block (one block per SM)
 constexpr unsigned long long kBarrierNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long gtime() {
@@ -229,7 +233,7 @@ __device__ double row_dot_df(const float2* __restrict__ A, int m, const float* _
   return (double)acc.hi + (double)acc.lo;
 }
 
-__global__ void __launch_bounds__(PT, 2) k_pcg_persist(int m, const float2* __restrict__ K, long long ldk, double lambda,
+__global__ void __launch_bounds__(PT, 1) k_pcg_persist(int m, const float2* __restrict__ K, long long ldk, double lambda,
                                                     const float* __restrict__ Linv, const float* __restrict__ LinvT,
                                                     long long ldi, const double* __restrict__ b,
                                                     double* __restrict__ x, double* __restrict__ r0b,
@@ -263,7 +267,9 @@ __global__ void __launch_bounds__(PT, 2) k_pcg_persist(int m, const float2* __re
   }
   if (!grid_barrier(gs, nb, status)) return;
   stage(r0b, sh, sl, m);
-  for (int i = gw; i < m; i += GW) {
+  for (int p = gw; p < (m + 1) / 2; p += GW)
+      for (int h = 0; h < 2 && (h == 0 || m - 1 - p != p); ++h) {
+        const int i = h ? m - 1 - p : p;
     const double v = row_dot_f32(Linv + (long long)i * ldi, 0, i + 1, sh, sl);
     if (lane == 0) y[i] = v;
   }
@@ -271,7 +277,9 @@ __global__ void __launch_bounds__(PT, 2) k_pcg_persist(int m, const float2* __re
   stage(y, sh, sl, m);
   {
     double rz = 0.0, bb = 0.0;
-    for (int i = gw; i < m; i += GW) {
+    for (int p = gw; p < (m + 1) / 2; p += GW)
+      for (int h = 0; h < 2 && (h == 0 || m - 1 - p != p); ++h) {
+        const int i = h ? m - 1 - p : p;
       const double v = row_dot_f32(LinvT + (long long)i * ldi, i, m, sh, sl);
       if (lane == 0) {
         z[i] = v;
@@ -321,7 +329,9 @@ __global__ void __launch_bounds__(PT, 2) k_pcg_persist(int m, const float2* __re
     }
     __syncthreads();
     double pap = 0.0;
-    for (int i = gw; i < m; i += GW) {
+    for (int p = gw; p < (m + 1) / 2; p += GW)
+      for (int h = 0; h < 2 && (h == 0 || m - 1 - p != p); ++h) {
+        const int i = h ? m - 1 - p : p;
       const double pi = (double)sh[i] + (double)sl[i];
       const double v = row_dot_df(K + (long long)i * ldk, m, sh, sl) + lambda * pi;
       if (lane == 0) {
@@ -375,7 +385,9 @@ __global__ void __launch_bounds__(PT, 2) k_pcg_persist(int m, const float2* __re
       done = true;
       break;
     }
-    for (int i = gw; i < m; i += GW) {
+    for (int p = gw; p < (m + 1) / 2; p += GW)
+      for (int h = 0; h < 2 && (h == 0 || m - 1 - p != p); ++h) {
+        const int i = h ? m - 1 - p : p;
       const double v = row_dot_f32(Linv + (long long)i * ldi, 0, i + 1, sh, sl);
       if (lane == 0) y[i] = v;
     }
@@ -383,7 +395,9 @@ __global__ void __launch_bounds__(PT, 2) k_pcg_persist(int m, const float2* __re
     // C: z = Linv^T y with the block partials of <r_new, z>
     stage(y, sh, sl, m);
     double rz = 0.0;
-    for (int i = gw; i < m; i += GW) {
+    for (int p = gw; p < (m + 1) / 2; p += GW)
+      for (int h = 0; h < 2 && (h == 0 || m - 1 - p != p); ++h) {
+        const int i = h ? m - 1 - p : p;
       const double v = row_dot_f32(LinvT + (long long)i * ldi, i, m, sh, sl);
       if (lane == 0) {
         z[i] = v;
@@ -472,7 +486,7 @@ static int persist_blocks(int m) {
     cudaGetLastError();
     per = 0;
   }
-  if (per > 2) per = 2;
+  if (per > 1) per = 1;
   cached = coop ? per * nsm : 0;
   cached_m = m;
   return cached;
