@@ -11,8 +11,8 @@
 // and lo float arrays; double-float accumulation) followed by a grid
 // barrier; block partial sums are reduced by every block in the same order,
 // so all blocks take the same decisions and the result is deterministic.
-// Vectors written during the
-// kernel are read with L2-only loads (another SM may have written them).
+// Vectors written during the kernel are read with L2-only loads (another SM
+// may have written them).
 // p and r are double-buffered, so each iteration needs three barriers:
 //   p = z + beta p_prev (staged whole by every block), Ap = K p + lambda p,
 //     <p, Ap>                                                    | barrier
