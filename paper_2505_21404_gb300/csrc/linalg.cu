@@ -370,8 +370,10 @@ __device__ __forceinline__ void chol32_col(float (&a)[32], float (&y)[32], int l
   const unsigned full = 0xffffffffu;
   const float piv = __shfl_sync(full, a[J], J);
   if (!(piv > 0.f) && bad < 0) bad = J;
-  const float d = sqrtf(piv);
-  const float inv_d = 1.f / d;
+  // the column's chain runs through this pivot: one hardware reciprocal
+  // square root (a preconditioner needs no correctly rounded sqrt)
+  const float inv_d = rsqrtf(piv);
+  const float d = piv * inv_d;
   if (lane > J) a[J] *= inv_d;
   if (lane == J) {
     a[J] = d;
