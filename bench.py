@@ -614,7 +614,10 @@ def main():
                      "peak_source": f"{src} bf16 sustained (measured)",
                      # dram read + write of one launch from the ncu capture of the same kernel on the
                      # width-128 case (n = 33,921), scaled by n to this workload (same m and tiles)
-                     "traffic": (4.429785e9 * n / 33921.0 + 0.33452e9) if args.workload == "poisson5d" else None,
+                     # ncu capture on the width-128 case (n = 33,921): DRAM read scales with the K
+                     # extent n, the partial-tile writes do not
+                     "traffic": ((4.627013e9 * n / 33921.0 + 0.285605e9)
+                                 if args.workload in ("poisson5d", "poisson5d_w128") else None),
                      "traffic_source": "profiles/k_gram_oz_poisson5d_w128.md (scaled by n)"}
     else:
         roof_gram = {"bound": "tensor", "kernel": "k_gram_tc (tcgen05 syrk, lower 128x256 tiles)",
