@@ -264,13 +264,19 @@ dngd_status forward_only(dngd_ctx* c, const T* thT, const double* X, const doubl
                          tensor && c->tc3.buf ? &c->tc3 : nullptr);
 }
 
+// FP32 paths: the hidden-layer GEMMs of the jets, J's reverse sweep and f_vv
+// run on the TF32 tensor cores (3xTF32) when the context has the scratch.
+const Tc3Scratch* tc3p(dngd_ctx* c);
+
 template <typename T>
 dngd_status residual_jacobian_T(dngd_ctx* c, const T* thT, const double* X, const double* target) {
-  dngd_status s = forward_only<T>(c, thT, X, target, c->r);
+  const Tc3Scratch* t3 = std::is_same<T, float>::value ? tc3p(c) : nullptr;
+  dngd_status s = jets_forward<T>(c->net, thT, X, target, lp<T>(c->Z), lp<T>(c->H), c->r, c->status, c->st, t3,
+                                  true);
   if (s) return s;
   return jets_backward_jacobian<T, T>(c->net, thT, X, lp<T>(c->Z), lp<T>(c->H), lp<T>(c->D), (T*)c->Hbar,
                                       (T*)c->J, c->ldJ, c->prec == DNGD_MIXED_BF16 ? c->Jb : nullptr, c->ldb,
-                                      c->st);
+                                      c->st, t3, c->status);
 }
 
 // ---------------------------------------------------------------------------
@@ -353,12 +359,13 @@ dngd_status solve_last(dngd_ctx* c, const double* b, double* x, int slot) {
 
 const Tc3Scratch* tc3p(dngd_ctx* c) { return c->tc3.buf ? &c->tc3 : nullptr; }
 
-// Scratch for the largest TF32 tensor-core GEMM of the context: a line-search
-// forward layer (R x w x w), a factor update (m x m x 64) or the top level
-// of the recursive inverse (m/2 x m/2 x m/2).
+// Scratch for the largest TF32 tensor-core GEMM of the context: a jets layer
+// (R x w x w; the f_vv sweep's three stacked streams 3R x w x w), a factor
+// update (m x m x 64) or the top level of the recursive inverse
+// (m/2 x m/2 x m/2).
 size_t tc3_bytes(const dngd_ctx* c) {
   const int m = c->net.m, w = c->net.max_w;
-  size_t b = tc3_scratch_bytes(c->net.R, w, w);
+  size_t b = tc3_scratch_bytes(3 * c->net.R, w, w);
   const size_t f = tc3_scratch_bytes(m, m, 64);
   const size_t t = tc3_scratch_bytes(m, 0, m / 2 + 64);
   if (f > b) b = f;
@@ -477,7 +484,9 @@ factored:
       to_float(n, c->v, c->v32, c->st);
       vT = (const T*)c->v32;
     }
-    if ((s = jets_fvv<T>(c->net, thT, vT, X, (T*)c->Z3, (T*)c->H3a, (T*)c->H3b, c->fvv, c->st))) return s;
+    if ((s = jets_fvv<T>(c->net, thT, vT, X, (T*)c->Z3, (T*)c->H3a, (T*)c->H3b, c->fvv, c->st,
+                         std::is_same<T, float>::value ? tc3p(c) : nullptr, c->status)))
+      return s;
     evrec(c, 5);
     if ((s = solve_last(c, c->fvv, c->beta, 1))) return s;
     if ((s = jt_x<T>(c, c->beta, -1.0, c->a))) return s;
@@ -1192,7 +1201,8 @@ dngd_status dngd_fvv(dngd_ctx* c, const double* theta, const double* X, const do
   } else {
     const float* t32 = theta_in_T<float>(c, th);
     to_float(c->n, vv, c->v32, c->st);
-    s = jets_fvv<float>(c->net, t32, c->v32, x, (float*)c->Z3, (float*)c->H3a, (float*)c->H3b, c->fvv, c->st);
+    s = jets_fvv<float>(c->net, t32, c->v32, x, (float*)c->Z3, (float*)c->H3a, (float*)c->H3b, c->fvv, c->st,
+                        tc3p(c), c->status);
   }
   if (s) return s;
   c->have_step = false;

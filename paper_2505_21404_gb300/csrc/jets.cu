@@ -433,10 +433,27 @@ __global__ void k_output_fvv(NetInfo net, const T* __restrict__ theta, const T* 
 // Launchers
 // ---------------------------------------------------------------------------
 
+// C = alpha A B^T + beta C (A [M x K], B [N x K]) or, with b_kn, B given as
+// [K x N]: on the TF32 tensor cores (3xTF32) when a scratch is given and
+// fits, else on the FP32 / FP64 SIMT GEMM.
+template <typename T>
+static dngd_status layer_gemm(int M, int N, int K, T alpha, const T* A, int lda, const T* B, int ldb, bool b_kn,
+                              T beta, T* C, int ldc, const Tc3Scratch* tc3, int* status, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc3 && status) {
+      const dngd_status s =
+          gemm_tc3(M, N, K, alpha, A, lda, false, B, ldb, b_kn, beta, C, ldc, false, *tc3, status, st);
+      if (s != DNGD_ERR_INVALID_ARG) return s;
+    }
+  }
+  return b_kn ? gemm_nn<T>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st)
+              : gemm_nt<T>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, false, st);
+}
+
 template <typename T>
 dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, const double* target,
                          LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st,
-                         const Tc3Scratch* tc3) {
+                         const Tc3Scratch* tc3, bool streams) {
   const int L = net.n_layers - 1;
   const int thr = 128;
   // forward-only sweep on the TF32 tensor cores: every hidden GEMM fits the
@@ -445,7 +462,7 @@ dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, co
   bool presplit = false;
   float *a_half = nullptr, *b_half = nullptr;
   if constexpr (std::is_same<T, float>::value) {
-    if (tc3 && tc3->buf) {
+    if (tc3 && tc3->buf && !streams) {
       presplit = true;
       for (int l = 1; l < L; ++l)
         presplit = presplit && tc3_scratch_bytes(net.R, net.widths[l + 1], net.widths[l]) <= tc3->bytes;
@@ -490,7 +507,8 @@ dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, co
 template <typename T, typename TJ>
 dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
                                    LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
-                                   __nv_bfloat16* Jb, long long ldb, cudaStream_t st) {
+                                   __nv_bfloat16* Jb, long long ldb, cudaStream_t st, const Tc3Scratch* tc3,
+                                   int* status) {
   const int L = net.n_layers - 1;
   const int thr = 128;
   for (int l = L - 1; l >= 0; --l) {
@@ -501,8 +519,8 @@ dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const dou
     DNGD_LAUNCH_CHECK();
     if (l > 0) {
       // Hbar_{l-1} = D_l W_l  (rows x w_l)
-      dngd_status s = gemm_nn<T>(net.R, net.widths[l], w, T(1), D.p[l], w, theta + net.w_off[l],
-                                 net.widths[l], T(0), Hbar, net.widths[l], st);
+      dngd_status s = layer_gemm<T>(net.R, net.widths[l], w, T(1), D.p[l], w, theta + net.w_off[l],
+                                    net.widths[l], true, T(0), Hbar, net.widths[l], tc3, status, st);
       if (s) return s;
     }
   }
@@ -527,7 +545,7 @@ dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const dou
 
 template <typename T>
 dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const double* X, T* Z3, T* H3a,
-                     T* H3b, double* fvv, cudaStream_t st) {
+                     T* H3b, double* fvv, cudaStream_t st, const Tc3Scratch* tc3, int* status) {
   const int L = net.n_layers - 1;
   const int thr = 128;
   const long long R = net.R;
@@ -544,12 +562,13 @@ dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const doubl
       const T* W = theta + net.w_off[l];
       const T* V = v + net.w_off[l];
       // blocks 0..2: W h^(j)
-      dngd_status s = gemm_nt<T>(3 * net.R, w, win, T(1), Hprev, win, W, win, T(0), Z3, w, false, st);
+      dngd_status s = layer_gemm<T>(3 * net.R, w, win, T(1), Hprev, win, W, win, false, T(0), Z3, w, tc3, status, st);
       if (s) return s;
       // block 1 += V h ; block 2 += 2 V h'
-      s = gemm_nt<T>(net.R, w, win, T(1), Hprev, win, V, win, T(1), Z3 + R * w, w, false, st);
+      s = layer_gemm<T>(net.R, w, win, T(1), Hprev, win, V, win, false, T(1), Z3 + R * w, w, tc3, status, st);
       if (s) return s;
-      s = gemm_nt<T>(net.R, w, win, T(2), Hprev + R * win, win, V, win, T(1), Z3 + 2 * R * w, w, false, st);
+      s = layer_gemm<T>(net.R, w, win, T(2), Hprev + R * win, win, V, win, false, T(1), Z3 + 2 * R * w, w, tc3,
+                        status, st);
       if (s) return s;
       DNGD_NOTE_LAUNCH();
       k_act_fvv<T><<<grid, thr, 0, st>>>(net, l, theta, v, Z3, Hcur);
@@ -567,21 +586,23 @@ dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const doubl
 
 template dngd_status jets_forward<double>(const NetInfo&, const double*, const double*, const double*,
                                           LayerPtrs<double>, LayerPtrs<double>, double*, int*, cudaStream_t,
-                                          const Tc3Scratch*);
+                                          const Tc3Scratch*, bool);
 template dngd_status jets_forward<float>(const NetInfo&, const float*, const double*, const double*,
                                          LayerPtrs<float>, LayerPtrs<float>, double*, int*, cudaStream_t,
-                                         const Tc3Scratch*);
+                                         const Tc3Scratch*, bool);
 template dngd_status jets_backward_jacobian<double, double>(const NetInfo&, const double*, const double*,
                                                             LayerPtrs<double>, LayerPtrs<double>,
                                                             LayerPtrs<double>, double*, double*, long long,
-                                                            __nv_bfloat16*, long long, cudaStream_t);
+                                                            __nv_bfloat16*, long long, cudaStream_t,
+                                                            const Tc3Scratch*, int*);
 template dngd_status jets_backward_jacobian<float, float>(const NetInfo&, const float*, const double*,
                                                           LayerPtrs<float>, LayerPtrs<float>,
                                                           LayerPtrs<float>, float*, float*, long long,
-                                                          __nv_bfloat16*, long long, cudaStream_t);
+                                                          __nv_bfloat16*, long long, cudaStream_t,
+                                                          const Tc3Scratch*, int*);
 template dngd_status jets_fvv<double>(const NetInfo&, const double*, const double*, const double*, double*,
-                                      double*, double*, double*, cudaStream_t);
+                                      double*, double*, double*, cudaStream_t, const Tc3Scratch*, int*);
 template dngd_status jets_fvv<float>(const NetInfo&, const float*, const float*, const double*, float*,
-                                     float*, float*, double*, cudaStream_t);
+                                     float*, float*, double*, cudaStream_t, const Tc3Scratch*, int*);
 
 }  // namespace dngd

@@ -13,20 +13,24 @@ struct LayerPtrs {
 // ---- jets.cu --------------------------------------------------------------
 struct Tc3Scratch;
 // tc3 (FP32 only, optional): hidden-layer GEMMs on the TF32 tensor cores
-// (3xTF32, ~2^-21 per product) instead of FP32 SIMT.
+// (3xTF32, ~2^-21 per product) instead of FP32 SIMT.  Without `streams` the
+// sweep is forward-only (losses): the activations are handed to the next
+// GEMM as its split operand and Z / H are not kept for a reverse sweep.
 template <typename T>
 dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, const double* target,
                          LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st,
-                         const Tc3Scratch* tc3 = nullptr);
+                         const Tc3Scratch* tc3 = nullptr, bool streams = false);
 
 template <typename T, typename TJ>
 dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
                                    LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
-                                   __nv_bfloat16* Jb, long long ldb, cudaStream_t st);
+                                   __nv_bfloat16* Jb, long long ldb, cudaStream_t st,
+                                   const Tc3Scratch* tc3 = nullptr, int* status = nullptr);
 
 template <typename T>
 dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const double* X, T* Z3, T* H3a,
-                     T* H3b, double* fvv, cudaStream_t st);
+                     T* H3b, double* fvv, cudaStream_t st, const Tc3Scratch* tc3 = nullptr,
+                     int* status = nullptr);
 
 // ---- linalg.cu ------------------------------------------------------------
 // C[M x N] = alpha * A[M x K] * B^T + beta * C, B is [N x K] (both row-major).
