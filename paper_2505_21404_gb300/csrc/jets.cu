@@ -251,11 +251,42 @@ __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const doub
   __nv_bfloat16* Jbrow = Jb ? Jb + (long long)p * ldb : nullptr;
   const long long wo = net.w_off[l], bo = net.b_off[l];
   for (int b = threadIdx.x; b < win; b += blockDim.x) {
+    // the stream loops are unrolled to the largest S so hreg stays in registers
     T hreg[2 + kMaxDim];
-    for (int s = 0; s < S; ++s) hreg[s] = hsh[s * win + b];
-    for (int a = 0; a < wout; ++a) {
+#pragma unroll
+    for (int s = 0; s < 2 + kMaxDim; ++s) hreg[s] = s < S ? hsh[s * win + b] : T(0);
+    int a = 0;
+    if constexpr (std::is_same<T, float>::value) {
+      // four outputs per pass: one 16-byte broadcast load of the adjoints per
+      // stream instead of four (the loop is bound by shared-memory loads)
+      if ((wout & 3) == 0) {
+        for (; a < wout; a += 4) {
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int s = 0; s < 2 + kMaxDim; ++s) {
+            if (s >= S) break;
+            const float4 d = *reinterpret_cast<const float4*>(dsh + s * wout + a);
+            acc.x += d.x * hreg[s];
+            acc.y += d.y * hreg[s];
+            acc.z += d.z * hreg[s];
+            acc.w += d.w * hreg[s];
+          }
+          const float o[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            Jrow[wo + (long long)(a + q) * win + b] = (TJ)o[q];
+            if (Jbrow) Jbrow[wo + (long long)(a + q) * win + b] = __float2bfloat16_rn(o[q]);
+          }
+        }
+      }
+    }
+    for (; a < wout; ++a) {
       T acc = 0;
-      for (int s = 0; s < S; ++s) acc += dsh[s * wout + a] * hreg[s];
+#pragma unroll
+      for (int s = 0; s < 2 + kMaxDim; ++s) {
+        if (s >= S) break;
+        acc += dsh[s * wout + a] * hreg[s];
+      }
       Jrow[wo + (long long)a * win + b] = (TJ)acc;
       if (Jbrow) Jbrow[wo + (long long)a * win + b] = __float2bfloat16_rn((float)acc);
     }
