@@ -602,9 +602,22 @@ def main():
                                            "map-back J^T alpha)",
                  "achieved": gemv_gbs, "peak": hbm, "unit": "GB/s", "frac": gemv_gbs / hbm,
                  "bytes_per_launch": gemv_bytes, "launch_ms": [jt_ms, j_ms],
-                 "launches_per_step": 2 * iters_total + 2 if prec != dngd.MIXED_OZ else 2,
+                 "launches_per_step": 2 * iters_total + 2,
                  "peak_source": f"{src} HBM copy bandwidth (measured)", "traffic": None}
     if prec == dngd.MIXED_OZ:
+        # the two refinement solves (persistent PCG: per iteration the double-float
+        # Gram, 8 m^2 B, and both triangles of the FP32 inverse factor, 2 x 2 m^2 B)
+        # plus each solve's map-back J^T x over the FP32 J (4 m n B), against the
+        # solve phases' CUDA-event time
+        solve_ms = float(np.mean([i["phase_ms"][3] + i["phase_ms"][5] for i in infos]))
+        solve_bytes = iters_total * 12.0 * m * m + 2 * gemv_bytes
+        solve_gbs = solve_bytes / (solve_ms * 1e-3) / 1e9 if solve_ms > 0 else 0.0
+        roof_gemv = {"bound": "hbm", "kernel": "k_pcg_persist (both solves) + k_gemv_t_f32 (map-back J^T x)",
+                     "achieved": solve_gbs, "peak": hbm, "unit": "GB/s", "frac": solve_gbs / hbm,
+                     "bytes_per_step": solve_bytes, "solve_ms": solve_ms,
+                     "algorithmic": "per PCG iteration 8 m^2 + 4 m^2 B (exact Gram operator, L^-1 and L^-T "
+                                    "triangles); per solve 4 m n B (J^T x)",
+                     "peak_source": f"{src} HBM copy bandwidth (measured)", "traffic": None}
         roof_gram = {"bound": "tensor", "kernel": "k_oz_slice + k_gram_oz (tcgen05 BF16, 13 exact slice products, "
                                                   "128x96 tiles)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
