@@ -4,6 +4,9 @@
 //
 // All reductions use a fixed order (no atomics on floating point), so every
 // result is bitwise reproducible run to run.
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -852,9 +855,201 @@ dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, l
   return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, false, nullptr, nullptr);
 }
 
+// ---------------------------------------------------------------------------
+// Off-diagonal blocks of L^{-1} level by level.  The recursion splits a block
+// of n rows at n1 = n/2 rounded up to 64: with L = [L11 0; L21 L22] and the
+// inverses I11, I22 of the halves, (L^{-1})21 = -I22 (L21 I11).  Nodes of one
+// depth are independent, so all small nodes of a depth (n <= 512) go into
+// one batched FP32 SIMT GEMM launch for T = L21 I11 and one for
+// -I22 T; the few large nodes at the top use the 3xTF32 tensor-core GEMMs.
+// ---------------------------------------------------------------------------
+
+struct GemmNode {
+  const float* A;
+  const float* B;
+  float* C;
+  int M, N, K, lda, ldb, ldc;
+  float alpha;
+  int pad;
+};
+
+// C = alpha A B for every node (A [M x K], B [K x N], row-major), 64 x 64
+// tiles, blockIdx.z = node.
+__global__ void __launch_bounds__(256) k_gemm_nodes(const GemmNode* __restrict__ nodes) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const GemmNode nd = nodes[blockIdx.z];
+  const int bm = blockIdx.y * 64, bn = blockIdx.x * 64;
+  if (bm >= nd.M || bn >= nd.N) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < nd.K; k0 += 16) {
+    for (int e = tid; e < 64 * 16; e += 256) {
+      const int r = e >> 4, kk = e & 15;
+      const int gr = bm + r, gk = k0 + kk;
+      As[kk][r] = (gr < nd.M && gk < nd.K) ? nd.A[(long long)gr * nd.lda + gk] : 0.f;
+    }
+    for (int e = tid; e < 16 * 64; e += 256) {
+      const int kk = e >> 6, c = e & 63;
+      const int gc = bn + c, gk = k0 + kk;
+      Bs[kk][c] = (gc < nd.N && gk < nd.K) ? nd.B[(long long)gk * nd.ldb + gc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = bm + ty * 4 + i;
+    if (gr >= nd.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = bn + tx * 4 + j;
+      if (gc < nd.N) nd.C[(long long)gr * nd.ldc + gc] = nd.alpha * acc[i][j];
+    }
+  }
+}
+
+namespace {
+
+constexpr int kSmallNode = 512;   // nodes up to this size go into the batched launches
+
+struct TrtriNode {
+  int k0, n1, n2;
+};
+
+void trtri_tree(int k0, int n, int depth, std::vector<std::vector<TrtriNode>>& levels) {
+  if (n <= kCholNB) return;   // the factor's 64-blocks are the leaves
+  const int n1 = ((n / 2 + kCholNB - 1) / kCholNB) * kCholNB;
+  const int n2 = n - n1;
+  trtri_tree(k0, n1, depth + 1, levels);
+  trtri_tree(k0 + n1, n2, depth + 1, levels);
+  if ((int)levels.size() <= depth) levels.resize(depth + 1);
+  levels[depth].push_back({k0, n1, n2});
+}
+
+// Device node tables of one (m, L, Linv, work) layout, built once.
+struct TrtriPlan {
+  int m;
+  const float* L;
+  long long ldl;
+  float* Linv;
+  long long ldi;
+  float* work;
+  std::vector<std::vector<TrtriNode>> levels;
+  GemmNode* d_nodes = nullptr;          // per depth: [count] T nodes then [count] I21 nodes
+  std::vector<int> first, count, maxM, maxN1;
+};
+std::mutex g_trtri_mu;
+std::vector<TrtriPlan*> g_trtri_plans;
+
+TrtriPlan* trtri_plan(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
+                      cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_trtri_mu);
+  for (TrtriPlan* p : g_trtri_plans)
+    if (p->m == m && p->L == L && p->ldl == ldl && p->Linv == Linv && p->ldi == ldi && p->work == work) return p;
+  // building a plan allocates and copies: not inside a stream capture
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+  TrtriPlan* p = new TrtriPlan();
+  p->m = m;
+  p->L = L;
+  p->ldl = ldl;
+  p->Linv = Linv;
+  p->ldi = ldi;
+  p->work = work;
+  trtri_tree(0, m, 0, p->levels);
+  std::vector<GemmNode> h;
+  for (size_t d = 0; d < p->levels.size(); ++d) {
+    std::vector<GemmNode> t, u;
+    long long woff = 0;
+    int mm = 0, mn = 0;
+    for (const TrtriNode& nd : p->levels[d]) {
+      if (nd.n1 + nd.n2 > kSmallNode) continue;
+      float* T = work + woff;   // n2 x n1, ld n1
+      woff += (long long)nd.n1 * nd.n2;
+      const float* L21 = L + (long long)(nd.k0 + nd.n1) * ldl + nd.k0;
+      const float* I11 = Linv + (long long)nd.k0 * ldi + nd.k0;
+      const float* I22 = Linv + (long long)(nd.k0 + nd.n1) * ldi + nd.k0 + nd.n1;
+      float* I21 = Linv + (long long)(nd.k0 + nd.n1) * ldi + nd.k0;
+      t.push_back({L21, I11, T, nd.n2, nd.n1, nd.n1, (int)ldl, (int)ldi, nd.n1, 1.0f, 0});
+      u.push_back({I22, T, I21, nd.n2, nd.n1, nd.n2, (int)ldi, nd.n1, (int)ldi, -1.0f, 0});
+      mm = nd.n2 > mm ? nd.n2 : mm;
+      mn = nd.n1 > mn ? nd.n1 : mn;
+    }
+    p->first.push_back((int)h.size());
+    p->count.push_back((int)t.size());
+    p->maxM.push_back(mm);
+    p->maxN1.push_back(mn);
+    h.insert(h.end(), t.begin(), t.end());
+    h.insert(h.end(), u.begin(), u.end());
+  }
+  if (!h.empty()) {
+    if (cudaMalloc(&p->d_nodes, sizeof(GemmNode) * h.size()) != cudaSuccess ||
+        cudaMemcpy(p->d_nodes, h.data(), sizeof(GemmNode) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      delete p;
+      return nullptr;
+    }
+  }
+  // plans are kept for the process (a few KB each; a released workspace's
+  // plan may still be read by work in flight on another stream)
+  g_trtri_plans.push_back(p);
+  return p;
+}
+
+}  // namespace
+
 dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
                               cudaStream_t st, const Tc3Scratch* tc3, int* status) {
-  return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, true, tc3, status);
+  TrtriPlan* p = (tc3 && status) ? trtri_plan(m, L, ldl, Linv, ldi, work, st) : nullptr;
+  if (!p) return trtri_rec(0, m, L, ldl, Linv, ldi, work, st, true, tc3, status);
+  for (int d = (int)p->levels.size() - 1; d >= 0; --d) {
+    // small nodes of this depth: two batched launches
+    const int cnt = p->count[d];
+    if (cnt > 0) {
+      const dim3 gT(cdiv(p->maxN1[d], 64), cdiv(p->maxM[d], 64), cnt);
+      DNGD_NOTE_LAUNCH();
+      k_gemm_nodes<<<gT, 256, 0, st>>>(p->d_nodes + p->first[d]);
+      DNGD_NOTE_LAUNCH();
+      k_gemm_nodes<<<gT, 256, 0, st>>>(p->d_nodes + p->first[d] + cnt);
+      DNGD_LAUNCH_CHECK();
+    }
+    // large nodes: 3xTF32 tensor-core GEMMs, one node at a time
+    for (const TrtriNode& nd : p->levels[d]) {
+      if (nd.n1 + nd.n2 <= kSmallNode) continue;
+      const float* L21 = L + (long long)(nd.k0 + nd.n1) * ldl + nd.k0;
+      const float* I11 = Linv + (long long)nd.k0 * ldi + nd.k0;
+      const float* I22 = Linv + (long long)(nd.k0 + nd.n1) * ldi + nd.k0 + nd.n1;
+      float* I21 = Linv + (long long)(nd.k0 + nd.n1) * ldi + nd.k0;
+      dngd_status s = gemm_tc3(nd.n2, nd.n1, nd.n1, 1.0f, L21, ldl, false, I11, ldi, true, 0.0f, work, nd.n1, false,
+                               *tc3, status, st);
+      if (s == DNGD_OK)
+        s = gemm_tc3(nd.n2, nd.n1, nd.n2, -1.0f, I22, ldi, false, work, nd.n1, true, 0.0f, I21, ldi, false, *tc3,
+                     status, st);
+      if (s == DNGD_ERR_INVALID_ARG) {
+        s = gemm_nn<float>(nd.n2, nd.n1, nd.n1, 1.0f, L21, ldl, I11, ldi, 0.0f, work, nd.n1, st);
+        if (s == DNGD_OK) s = gemm_nn<float>(nd.n2, nd.n1, nd.n2, -1.0f, I22, ldi, work, nd.n1, 0.0f, I21, ldi, st);
+      }
+      if (s) return s;
+    }
+  }
+  return DNGD_OK;
 }
 
 // ---------------------------------------------------------------------------
