@@ -101,6 +101,8 @@ struct dngd_ctx {
   double* loss_dev = nullptr;        // trial losses of dngd_loss [64]
   double* loss_host = nullptr;       // pinned copy [64]
   int ls_k = 0;
+  float* ls_th32 = nullptr;          // FP32 parameters of kTrials line-search trials
+  double* ls_r = nullptr;            // their residuals [kTrials m]
   double graph_mu = 0.0;
   cudaStream_t gst = nullptr;        // private stream for capture / replay
   unsigned long long graph_kernels = 0;  // kernel launches captured in the graph
@@ -122,6 +124,7 @@ struct dngd_ctx {
 namespace {
 
 constexpr const char* kVersion = "dngd-gb300 0.1 (sm_103a)";
+constexpr int kTrials = 3;  // line-search trials per batched forward sweep
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -870,6 +873,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
     add(sizeof(float) * (size_t)m * m);           // trtri work
     add(tc3_bytes(c));                            // TF32 tensor-core GEMM splits
+    add(sizeof(float) * kTrials * n);             // line-search trial parameters
+    add(sizeof(double) * kTrials * m);            // line-search trial residuals
     if (oz) {
       add(sizeof(float2) * (size_t)m * c->ldk);   // K64
       add(sizeof(float) * (size_t)m * c->ldk);    // LinvT
@@ -943,6 +948,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->trtri_work, float, (size_t)m * m);
     c->tc3.bytes = tc3_bytes(c);
     A_(c->tc3.buf, float, c->tc3.bytes / sizeof(float));
+    A_(c->ls_th32, float, kTrials * n);
+    A_(c->ls_r, double, kTrials * m);
     if (oz) {
       A_(c->K64, float2, (size_t)m * c->ldk);
       A_(c->LinvT, float, (size_t)m * c->ldk);
@@ -1209,6 +1216,33 @@ dngd_status dngd_fvv(dngd_ctx* c, const double* theta, const double* X, const do
   return out_copy(c, fvv_out, c->fvv, c->m);
 }
 
+// ||r(theta + etas[j] delta)||^2 into sq[j] for j < k: in the FP32 modes
+// kTrials trials share each launch of the forward sweep, otherwise one trial
+// at a time.
+dngd_status trial_sqnorms(dngd_ctx* c, const double* theta, const double* X, const double* target,
+                          const double* delta, const double* etas, int k, double* sq) {
+  dngd_status s;
+  if (c->prec != DNGD_FP64 && c->ls_th32 && c->tc3.buf) {
+    for (int j = 0; j < k; j += kTrials) {
+      const int G = k - j < kTrials ? k - j : kTrials;
+      if ((s = axpy_to_float_batch(c->n, G, theta, etas + j, delta, c->ls_th32, c->st))) return s;
+      if ((s = jets_forward_trials(c->net, G, c->ls_th32, c->n, X, target, (float*)c->Z3, (float*)c->H3a, c->ls_r,
+                                   c->status, c->st, c->tc3)))
+        return s;
+      if ((s = sqnorm_batch(c->m, G, c->ls_r, sq + j, c->st))) return s;
+    }
+    return DNGD_OK;
+  }
+  for (int j = 0; j < k; ++j) {
+    if ((s = axpy_to(c->n, theta, etas[j], delta, c->theta_tmp, c->st))) return s;
+    if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, X, target, c->cg_res);
+    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), X, target, c->cg_res, true);
+    if (s) return s;
+    if ((s = dot_dev(c->m, c->cg_res, c->cg_res, sq + j, c->dot_partials, c->st))) return s;
+  }
+  return DNGD_OK;
+}
+
 dngd_status dngd_loss(dngd_ctx* c, const double* theta, const double* X, const double* target, const double* delta,
                       const double* etas, int k, double* loss_out) {
   if (!c || !theta || !X || !target || !etas || !loss_out || k < 1) return DNGD_ERR_INVALID_ARG;
@@ -1226,14 +1260,8 @@ dngd_status dngd_loss(dngd_ctx* c, const double* theta, const double* X, const d
   }
   for (int j0 = 0; j0 < k; j0 += 64) {
     const int kk = (k - j0) < 64 ? (k - j0) : 64;
-    for (int j = 0; j < kk; ++j) {
-      dngd_status s = axpy_to(c->n, th, etas[j0 + j], dl, c->theta_tmp, c->st);
-      if (s) return s;
-      if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, x, tg, c->cg_res);
-      else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), x, tg, c->cg_res, true);
-      if (s) return s;
-      if ((s = dot_dev(c->m, c->cg_res, c->cg_res, c->loss_dev + j, c->dot_partials, c->st))) return s;
-    }
+    dngd_status s = trial_sqnorms(c, th, x, tg, dl, etas + j0, kk, c->loss_dev);
+    if (s) return s;
     DNGD_CUDA_CHECK(cudaMemcpyAsync(c->loss_host, c->loss_dev, sizeof(double) * kk, cudaMemcpyDeviceToHost, c->st));
     DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
     for (int j = 0; j < kk; ++j) loss_out[j0 + j] = 0.5 * c->loss_host[j];
@@ -1282,14 +1310,8 @@ dngd_status dngd_line_search_async(dngd_ctx* c, double* theta, const double* X, 
   // the step's status word, before the trial evaluations add their own flags
   int* step_flags = (int*)(c->ls_dev + 130);
   DNGD_CUDA_CHECK(cudaMemcpyAsync(step_flags, c->status, sizeof(int), cudaMemcpyDeviceToDevice, c->st));
-  for (int j = 0; j < k; ++j) {
-    dngd_status s = axpy_to(c->n, theta, etas[j], delta, c->theta_tmp, c->st);
-    if (s) return s;
-    if (c->prec == DNGD_FP64) s = forward_only<double>(c, c->theta_tmp, X, target, c->cg_res);
-    else s = forward_only<float>(c, theta_in_T<float>(c, c->theta_tmp), X, target, c->cg_res, true);
-    if (s) return s;
-    if ((s = dot_dev(c->m, c->cg_res, c->cg_res, losses + j, c->dot_partials, c->st))) return s;
-  }
+  dngd_status s = trial_sqnorms(c, theta, X, target, delta, etas, k, losses);
+  if (s) return s;
   return ls_finish(c->n, k, losses, c->ls_dev, step_flags, c->ls_dev + 128, delta, theta, c->st);
 }
 

@@ -38,6 +38,12 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(u);
 }
 
+// Per-trial strides of the line search's batched forward sweep (grid.z =
+// trial): every pointer of trial z is offset by z times its stride.
+struct TrialStride {
+  long long theta = 0, z = 0, h = 0, hs = 0, r = 0;
+};
+
 template <typename T>
 __device__ __forceinline__ void put_h(T* __restrict__ H, float* __restrict__ hs, int kp, long long row, int w, int a,
                                       T v) {
@@ -52,7 +58,12 @@ __device__ __forceinline__ void put_h(T* __restrict__ H, float* __restrict__ hs,
 
 template <typename T>
 __global__ void k_first_layer(NetInfo net, const T* __restrict__ theta, const double* __restrict__ X,
-                              T* __restrict__ Z, T* __restrict__ H, float* __restrict__ hs, int kp) {
+                              T* __restrict__ Z, T* __restrict__ H, float* __restrict__ hs, int kp,
+                              TrialStride zs = TrialStride()) {
+  theta += blockIdx.z * zs.theta;
+  Z += blockIdx.z * zs.z;
+  H += blockIdx.z * zs.h;
+  if (hs) hs += blockIdx.z * zs.hs;
   const int p = blockIdx.x;
   const int a = blockIdx.y * blockDim.x + threadIdx.x;
   const int w = net.widths[1], din = net.d_in;
@@ -85,7 +96,11 @@ __global__ void k_first_layer(NetInfo net, const T* __restrict__ theta, const do
 // Hidden layer l >= 1: Z already holds W_l h_{l-1} for every stream row.
 template <typename T>
 __global__ void k_act_fwd(NetInfo net, int l, const T* __restrict__ theta, T* __restrict__ Z,
-                          T* __restrict__ H, float* __restrict__ hs, int kp) {
+                          T* __restrict__ H, float* __restrict__ hs, int kp, TrialStride zs = TrialStride()) {
+  theta += blockIdx.z * zs.theta;
+  Z += blockIdx.z * zs.z;
+  H += blockIdx.z * zs.h;
+  if (hs) hs += blockIdx.z * zs.hs;
   const int p = blockIdx.x;
   const int a = blockIdx.y * blockDim.x + threadIdx.x;
   const int w = net.widths[l + 1];
@@ -116,7 +131,10 @@ __global__ void k_act_fwd(NetInfo net, int l, const T* __restrict__ theta, T* __
 template <typename T>
 __global__ void k_output(NetInfo net, const T* __restrict__ theta, const double* __restrict__ X,
                          const T* __restrict__ Hlast, const double* __restrict__ target,
-                         double* __restrict__ r, int* __restrict__ status) {
+                         double* __restrict__ r, int* __restrict__ status, TrialStride zs = TrialStride()) {
+  theta += blockIdx.z * zs.theta;
+  if (Hlast) Hlast += blockIdx.z * zs.h;
+  r += blockIdx.z * zs.r;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= net.m) return;
@@ -531,6 +549,59 @@ dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, co
   const T* Hlast = L > 0 ? H.p[L - 1] : nullptr;
   DNGD_NOTE_LAUNCH();
   k_output<T><<<cdiv((long long)net.m * 32, 256), 256, 0, st>>>(net, theta, X, Hlast, target, r, status);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// Forward-only sweeps of G line-search trials at once (grid.z = trial): the
+// trials' FP32 parameters are theta_b + g n; each layer's activations go to
+// the next 3xTF32 GEMM as split operands stacked by trial in the scratch's A
+// half, every hidden GEMM is one launch for all trials, the pre-activations
+// of trial g sit at Zb + g R w, the last activations at Hb + g R w_L and the
+// residuals at rb + g m.  INVALID_ARG when the scratch cannot hold G trials.
+dngd_status jets_forward_trials(const NetInfo& net, int G, const float* theta_b, long long n, const double* X,
+                                const double* target, float* Zb, float* Hb, double* rb, int* status, cudaStream_t st,
+                                const Tc3Scratch& tc3) {
+  const int L = net.n_layers - 1;
+  const int thr = 128;
+  const long long R = net.R;
+  if (L < 2 || !tc3.buf) return DNGD_ERR_INVALID_ARG;
+  float *a_half, *b_half;
+  tc3_halves(tc3, &a_half, &b_half);
+  for (int l = 1; l < L; ++l) {
+    const long long kp = (net.widths[l] + 31) & ~31;
+    if ((long long)G * R * 2 * kp > (long long)(b_half - a_half)) return DNGD_ERR_INVALID_ARG;
+    if ((long long)G * net.widths[l + 1] * 2 * kp > (long long)(b_half - a_half)) return DNGD_ERR_INVALID_ARG;
+  }
+  for (int l = 0; l < L; ++l) {
+    const int w = net.widths[l + 1];
+    const bool split_out = l + 1 < L;
+    const int kp = (w + 31) & ~31;
+    TrialStride zs;
+    zs.theta = n;
+    zs.z = R * w;
+    zs.h = R * w;
+    zs.hs = R * 2 * kp;
+    dim3 grid(net.m, cdiv(split_out ? kp : w, thr), G);
+    if (l == 0) {
+      DNGD_NOTE_LAUNCH();
+      k_first_layer<float><<<grid, thr, 0, st>>>(net, theta_b, X, Zb, Hb, a_half, kp, zs);
+    } else {
+      dngd_status s = gemm_tc3_trials(G, (int)R, w, net.widths[l], theta_b + net.w_off[l], net.widths[l], n, Zb, w,
+                                      R * w, tc3, status, st);
+      if (s) return s;
+      DNGD_NOTE_LAUNCH();
+      k_act_fwd<float><<<grid, thr, 0, st>>>(net, l, theta_b, Zb, Hb, split_out ? a_half : nullptr, kp, zs);
+    }
+    DNGD_LAUNCH_CHECK();
+  }
+  TrialStride zo;
+  zo.theta = n;
+  zo.h = R * net.widths[L];
+  zo.r = net.m;
+  DNGD_NOTE_LAUNCH();
+  k_output<float><<<dim3(cdiv((long long)net.m * 32, 256), 1, G), 256, 0, st>>>(net, theta_b, X, Hb, target, rb, status,
+                                                                                 zo);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }

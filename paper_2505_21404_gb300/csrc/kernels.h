@@ -21,6 +21,12 @@ dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, co
                          LayerPtrs<T> Z, LayerPtrs<T> H, double* r, int* status, cudaStream_t st,
                          const Tc3Scratch* tc3 = nullptr, bool streams = false);
 
+// G forward-only sweeps of line-search trials at once (FP32, 3xTF32 hidden
+// layers; see jets.cu).
+dngd_status jets_forward_trials(const NetInfo& net, int G, const float* theta_b, long long n, const double* X,
+                                const double* target, float* Zb, float* Hb, double* rb, int* status, cudaStream_t st,
+                                const Tc3Scratch& tc3);
+
 template <typename T, typename TJ>
 dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
                                    LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
@@ -119,6 +125,9 @@ dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long
                      long long ldb, bool transB, float beta, float* C, long long ldc, bool lower, const Tc3Scratch& sc,
                      int* status, cudaStream_t st, unsigned flags = 0u);
 
+dngd_status gemm_tc3_trials(int G, int M, int N, int K, const float* B0, long long ldb, long long b_z, float* C,
+                            long long ldc, long long c_z, const Tc3Scratch& sc, int* status, cudaStream_t st);
+
 // ---- gram_oz.cu: exact Gram of an FP32 matrix from BF16 integer slices ----
 struct OzPlan;
 size_t gram_oz_partial_bytes(int m, int n);
@@ -204,6 +213,8 @@ dngd_status add_diag(int m, T* K, long long ldk, double shift, cudaStream_t st);
 
 // Deterministic dot products / norms into a device scalar.
 dngd_status dot_dev(int n, const double* x, const double* y, double* out, double* partials, cudaStream_t st);
+// out[g] = <x_g, x_g> for G vectors x_g = x + g n (one block each, fixed order).
+dngd_status sqnorm_batch(int n, int G, const double* x, double* out, cudaStream_t st);
 
 // Device-side vector kernels used by the refinement / PCG loops.
 dngd_status axpy_dev(int n, double alpha, const double* x, double* y, cudaStream_t st);

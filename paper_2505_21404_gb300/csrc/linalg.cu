@@ -1234,6 +1234,28 @@ dngd_status dot_dev(int n, const double* x, const double* y, double* out, double
   return DNGD_OK;
 }
 
+__global__ void k_sqnorm_batch(int n, const double* __restrict__ x, double* __restrict__ out) {
+  const double* v = x + (long long)blockIdx.x * n;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i] * v[i];
+  s = warp_sum(s);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    out[blockIdx.x] = t;
+  }
+}
+
+dngd_status sqnorm_batch(int n, int G, const double* x, double* out, cudaStream_t st) {
+  DNGD_NOTE_LAUNCH();
+  k_sqnorm_batch<<<G, 256, 0, st>>>(n, x, out);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
 __global__ void k_axpy(int n, double alpha, const double* __restrict__ x, double* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += alpha * x[i];

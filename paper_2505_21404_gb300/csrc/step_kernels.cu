@@ -33,6 +33,28 @@ dngd_status axpy_to(long long n, const double* x, double eta, const double* d, d
   return DNGD_OK;
 }
 
+// theta32_g = fl32(theta + eta_g delta) for up to 4 line-search trials
+// (grid.y = trial, outputs n apart)
+struct Etas4 {
+  double e[4];
+};
+__global__ void k_axpy_to_float_batch(long long n, const double* __restrict__ x, Etas4 eta,
+                                      const double* __restrict__ d, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[(long long)blockIdx.y * n + i] = (float)(x[i] + eta.e[blockIdx.y] * (d ? d[i] : 0.0));
+}
+
+dngd_status axpy_to_float_batch(long long n, int G, const double* x, const double* etas, const double* d, float* y,
+                                cudaStream_t st) {
+  if (G < 1 || G > 4) return DNGD_ERR_INVALID_ARG;
+  Etas4 e = {{0.0, 0.0, 0.0, 0.0}};
+  for (int g = 0; g < G; ++g) e.e[g] = etas[g];
+  DNGD_NOTE_LAUNCH();
+  k_axpy_to_float_batch<<<dim3(cdiv(n, 256), G), 256, 0, st>>>(n, x, e, d, y);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
 // GA acceptance (Alg. DenseDualSolve): scal[S_NV2], scal[S_NA2] hold ||v||^2,
 // ||a||^2.  Writes ratio / accepted to scal and delta = v (+ a/2).
 __global__ void k_ga_decide(double* scal, int use_ga, double eps_norm, double ratio_max) {

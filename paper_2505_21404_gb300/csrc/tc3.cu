@@ -47,7 +47,11 @@ __device__ __forceinline__ float tf32_rn(float x) {
 // dst[r, 0:Kp] = hi, dst[r, Kp:2Kp] = lo of op[r, k]; op = src (row-major
 // [rows x K], ld) or, with trans, src^T (src row-major [K x rows]).
 __global__ void k_tc3_split(int rows, int K, int Kp, const float* __restrict__ src, long long ld, int trans,
-                            float* __restrict__ dst) {
+                            float* __restrict__ dst, long long src_z = 0) {
+  // grid.z: independent operands (line-search trials), src + z src_z, dst
+  // z rows further on
+  src += blockIdx.z * src_z;
+  dst += (long long)blockIdx.z * rows * 2 * Kp;
   __shared__ float t[32][33];
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -84,8 +88,12 @@ __device__ __forceinline__ uint32_t tc3_idesc() {
 __global__ void __launch_bounds__(THREADS3, 1)
 k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int Kp,
       float alpha, float beta, float* __restrict__ C, long long ldc, int lower, float* __restrict__ csplit, int kpc,
-      int* status) {
+      int* status, int a_zrows = 0, int b_zrows = 0, long long c_z = 0) {
+  // grid.z: independent products (line-search trials) whose operands are
+  // stacked by rows in the split buffers and whose outputs are c_z apart
   const int bn = blockIdx.x, bm = blockIdx.y;
+  const int ay = (int)blockIdx.z * a_zrows + bm * T3, by = (int)blockIdx.z * b_zrows + bn * T3;
+  C += blockIdx.z * c_z;
   if (lower && bn * T3 > bm * T3 + T3 - 1) return;
   // a factorisation that already failed (the host retries it with a larger
   // shift) needs no further updates
@@ -133,10 +141,10 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
         mbar_expect_tx(fb, STAGE3);
         const uint32_t sb = smem_base + st * STAGE3;
         const int kc = it * KB3;
-        tma_load_2d(sb, &mapA, fb, kc, bm * T3);
-        tma_load_2d(sb + TILE3, &mapA, fb, Kp + kc, bm * T3);
-        tma_load_2d(sb + 2 * TILE3, &mapB, fb, kc, bn * T3);
-        tma_load_2d(sb + 3 * TILE3, &mapB, fb, Kp + kc, bn * T3);
+        tma_load_2d(sb, &mapA, fb, kc, ay);
+        tma_load_2d(sb + TILE3, &mapA, fb, Kp + kc, ay);
+        tma_load_2d(sb + 2 * TILE3, &mapB, fb, kc, by);
+        tma_load_2d(sb + 3 * TILE3, &mapB, fb, Kp + kc, by);
         ++issued;
       }
     }
@@ -335,6 +343,36 @@ dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long
   k_tc3<<<dim3(cdiv(N, T3), cdiv(M, T3)), THREADS3, SMEM3, st>>>(mapA, mapB, M, N, Kp, alpha, beta, C, ldc,
                                                                  lower ? 1 : 0,
                                                                  (flags & TC3_C_SPLIT) ? Ab : nullptr, kpc, status);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// G independent products C_g = A_g B_g^T (line-search trials): A_g is
+// already split in the scratch's A half as rows [g M, (g+1) M) of a
+// [G M x 2 Kp] stack; B_g = B0 + g b_z ([N x K], ld ldb) is split here into
+// the B half; C_g = C + g c_z.  One launch per operand kind.
+dngd_status gemm_tc3_trials(int G, int M, int N, int K, const float* B0, long long ldb, long long b_z, float* C,
+                            long long ldc, long long c_z, const Tc3Scratch& sc, int* status, cudaStream_t st) {
+  if (G <= 0 || M <= 0 || N <= 0) return DNGD_OK;
+  if (!sc.buf || K <= 0) return DNGD_ERR_INVALID_ARG;
+  const int Kp = ((K + KB3 - 1) / KB3) * KB3;
+  float *Ab, *Bh;
+  tc3_halves(sc, &Ab, &Bh);
+  const long long cap_rows = (long long)(Bh - Ab) / (2 * (long long)Kp);
+  if ((long long)G * M > cap_rows || (long long)G * N > cap_rows) return DNGD_ERR_INVALID_ARG;
+  DNGD_NOTE_LAUNCH();
+  k_tc3_split<<<dim3(Kp / 32, cdiv(N, 32), G), 256, 0, st>>>(N, K, Kp, B0, ldb, 0, Bh, b_z);
+  DNGD_LAUNCH_CHECK();
+  CUtensorMap mapA, mapB;
+  if (!cached_map(Ab, (int)cap_rows, Kp, &mapA) || !cached_map(Bh, (int)cap_rows, Kp, &mapB)) return DNGD_ERR_CUDA;
+  static bool attr = false;
+  if (!attr) {
+    DNGD_CUDA_CHECK(cudaFuncSetAttribute(k_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM3));
+    attr = true;
+  }
+  DNGD_NOTE_LAUNCH();
+  k_tc3<<<dim3(cdiv(N, T3), cdiv(M, T3), G), THREADS3, SMEM3, st>>>(mapA, mapB, M, N, Kp, 1.0f, 0.0f, C, ldc, 0,
+                                                                    nullptr, 0, status, M, N, c_z);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
