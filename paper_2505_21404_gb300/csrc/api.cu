@@ -101,8 +101,10 @@ struct dngd_ctx {
   double* loss_dev = nullptr;        // trial losses of dngd_loss [64]
   double* loss_host = nullptr;       // pinned copy [64]
   int ls_k = 0;
-  float* ls_th32 = nullptr;          // FP32 parameters of kTrials line-search trials
-  double* ls_r = nullptr;            // their residuals [kTrials m]
+  float* ls_th32 = nullptr;          // FP32 parameters of the batched line-search trials
+  double* ls_r = nullptr;            // their residuals [G m]
+  float *ls_Z = nullptr, *ls_H = nullptr;  // their pre-activations / activations [G R max_w]
+  int ls_G = 0;                            // trials per batched sweep
   double graph_mu = 0.0;
   cudaStream_t gst = nullptr;        // private stream for capture / replay
   unsigned long long graph_kernels = 0;  // kernel launches captured in the graph
@@ -124,7 +126,15 @@ struct dngd_ctx {
 namespace {
 
 constexpr const char* kVersion = "dngd-gb300 0.1 (sm_103a)";
-constexpr int kTrials = 3;  // line-search trials per batched forward sweep
+constexpr int kTrials = 8;  // most line-search trials per batched forward sweep
+
+// trials per batched sweep: up to kTrials while their activations stay
+// within 2^26 floats per buffer (at least 2)
+int trials_of(const NetInfo& net) {
+  const long long per = (long long)net.R * net.max_w;
+  long long g = per > 0 ? (1LL << 26) / per : kTrials;
+  return (int)(g > kTrials ? kTrials : (g < 2 ? 2 : g));
+}
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -368,7 +378,7 @@ const Tc3Scratch* tc3p(dngd_ctx* c) { return c->tc3.buf ? &c->tc3 : nullptr; }
 // (m/2 x m/2 x m/2).
 size_t tc3_bytes(const dngd_ctx* c) {
   const int m = c->net.m, w = c->net.max_w;
-  size_t b = tc3_scratch_bytes(3 * c->net.R, w, w);
+  size_t b = tc3_scratch_bytes(trials_of(c->net) * c->net.R, w, w);   // line-search trials stacked by rows
   const size_t f = tc3_scratch_bytes(m, m, 64);
   const size_t t = tc3_scratch_bytes(m, 0, m / 2 + 64);
   if (f > b) b = f;
@@ -873,8 +883,9 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
     add(sizeof(float) * (size_t)m * m);           // trtri work
     add(tc3_bytes(c));                            // TF32 tensor-core GEMM splits
-    add(sizeof(float) * kTrials * n);             // line-search trial parameters
-    add(sizeof(double) * kTrials * m);            // line-search trial residuals
+    add(sizeof(float) * trials_of(net) * n);      // line-search trial parameters
+    add(sizeof(double) * trials_of(net) * m);     // line-search trial residuals
+    add(2 * sizeof(float) * trials_of(net) * (size_t)net.R * net.max_w);   // their activations
     if (oz) {
       add(sizeof(float2) * (size_t)m * c->ldk);   // K64
       add(sizeof(float) * (size_t)m * c->ldk);    // LinvT
@@ -948,8 +959,11 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->trtri_work, float, (size_t)m * m);
     c->tc3.bytes = tc3_bytes(c);
     A_(c->tc3.buf, float, c->tc3.bytes / sizeof(float));
-    A_(c->ls_th32, float, kTrials * n);
-    A_(c->ls_r, double, kTrials * m);
+    c->ls_G = trials_of(net);
+    A_(c->ls_th32, float, c->ls_G * n);
+    A_(c->ls_r, double, c->ls_G * m);
+    A_(c->ls_Z, float, c->ls_G * (size_t)net.R * net.max_w);
+    A_(c->ls_H, float, c->ls_G * (size_t)net.R * net.max_w);
     if (oz) {
       A_(c->K64, float2, (size_t)m * c->ldk);
       A_(c->LinvT, float, (size_t)m * c->ldk);
@@ -1217,16 +1231,16 @@ dngd_status dngd_fvv(dngd_ctx* c, const double* theta, const double* X, const do
 }
 
 // ||r(theta + etas[j] delta)||^2 into sq[j] for j < k: in the FP32 modes
-// kTrials trials share each launch of the forward sweep, otherwise one trial
-// at a time.
+// up to kTrials trials share each launch of the forward sweep, otherwise one
+// trial at a time.
 dngd_status trial_sqnorms(dngd_ctx* c, const double* theta, const double* X, const double* target,
                           const double* delta, const double* etas, int k, double* sq) {
   dngd_status s;
   if (c->prec != DNGD_FP64 && c->ls_th32 && c->tc3.buf) {
-    for (int j = 0; j < k; j += kTrials) {
-      const int G = k - j < kTrials ? k - j : kTrials;
+    for (int j = 0; j < k; j += c->ls_G) {
+      const int G = k - j < c->ls_G ? k - j : c->ls_G;
       if ((s = axpy_to_float_batch(c->n, G, theta, etas + j, delta, c->ls_th32, c->st))) return s;
-      if ((s = jets_forward_trials(c->net, G, c->ls_th32, c->n, X, target, (float*)c->Z3, (float*)c->H3a, c->ls_r,
+      if ((s = jets_forward_trials(c->net, G, c->ls_th32, c->n, X, target, c->ls_Z, c->ls_H, c->ls_r,
                                    c->status, c->st, c->tc3)))
         return s;
       if ((s = sqnorm_batch(c->m, G, c->ls_r, sq + j, c->st))) return s;

@@ -33,12 +33,12 @@ dngd_status axpy_to(long long n, const double* x, double eta, const double* d, d
   return DNGD_OK;
 }
 
-// theta32_g = fl32(theta + eta_g delta) for up to 4 line-search trials
+// theta32_g = fl32(theta + eta_g delta) for up to 8 line-search trials
 // (grid.y = trial, outputs n apart)
-struct Etas4 {
-  double e[4];
+struct Etas8 {
+  double e[8];
 };
-__global__ void k_axpy_to_float_batch(long long n, const double* __restrict__ x, Etas4 eta,
+__global__ void k_axpy_to_float_batch(long long n, const double* __restrict__ x, Etas8 eta,
                                       const double* __restrict__ d, float* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[(long long)blockIdx.y * n + i] = (float)(x[i] + eta.e[blockIdx.y] * (d ? d[i] : 0.0));
@@ -46,8 +46,8 @@ __global__ void k_axpy_to_float_batch(long long n, const double* __restrict__ x,
 
 dngd_status axpy_to_float_batch(long long n, int G, const double* x, const double* etas, const double* d, float* y,
                                 cudaStream_t st) {
-  if (G < 1 || G > 4) return DNGD_ERR_INVALID_ARG;
-  Etas4 e = {{0.0, 0.0, 0.0, 0.0}};
+  if (G < 1 || G > 8) return DNGD_ERR_INVALID_ARG;
+  Etas8 e = {};
   for (int g = 0; g < G; ++g) e.e[g] = etas[g];
   DNGD_NOTE_LAUNCH();
   k_axpy_to_float_batch<<<dim3(cdiv(n, 256), G), 256, 0, st>>>(n, x, e, d, y);

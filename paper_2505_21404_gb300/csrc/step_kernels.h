@@ -16,7 +16,7 @@ enum : int {
 
 dngd_status to_float(long long n, const double* x, float* y, cudaStream_t st);
 dngd_status axpy_to(long long n, const double* x, double eta, const double* d, double* y, cudaStream_t st);
-// y_g = fl32(x + etas[g] d) for g < G <= 4 (etas on the host), y_g = y + g n.
+// y_g = fl32(x + etas[g] d) for g < G <= 8 (etas on the host), y_g = y + g n.
 dngd_status axpy_to_float_batch(long long n, int G, const double* x, const double* etas, const double* d, float* y,
                                 cudaStream_t st);
 dngd_status ga_finish(int n, const double* v, const double* a, int use_ga, double eps_norm, double ratio_max,
