@@ -18,11 +18,17 @@
 //       K[i,j] = 2^(E_i+E_j-48) sum_{g<=4} 2^(8(4-g)) L_g[i,j]
 //     (13 slice products; the dropped s+t >= 5 terms are below 2^-40 of the
 //     row scales);
-//   * products of slices are exact in the tensor cores, and every chunk the
-//     MMAs accumulate in TMEM stays within 2^24 in magnitude (level g with
-//     n_g products is drained every 2^10 / n_g K columns), so the FP32
-//     accumulator is exact; the epilogue adds each chunk into double-float
-//     registers (48-bit significand) times 2^(8(4-g)).
+//   * products of slices are exact in the tensor cores; for levels 0-2 every
+//     chunk the MMAs accumulate in TMEM stays within 2^24 in magnitude
+//     (level g with n_g products is drained every 2^10 / n_g K columns), so
+//     the FP32 accumulator is exact; levels 3 and 4 (weights 2^-24 and
+//     2^-32 of level 0) are drained every 1024 columns and round in FP32
+//     (chunks below 2^26, so a unit is at most 4): even with each of a
+//     chunk's 256 (level 3) or 192 (level 4) MMA additions off by a full
+//     unit in the same direction this adds at most 2^-40 of the row scales
+//     times n (2^-40 = 256 x 4 x 2^8 x 2^-48 / 1024), below the slicing's
+//     own 2^-32; the epilogue adds each chunk into double-float registers
+//     (48-bit significand) times 2^(8(4-g)).
 //
 // Kernel roles (one 128 x 96 output tile touching the lower triangle and one
 // K range per CTA): warp 0 lane 0 streams, per 32-wide K block, all four A
@@ -72,15 +78,17 @@ constexpr uint32_t OTMEM = 512;             // five 96-column level accumulators
 __host__ __device__ __forceinline__ int g_lo(int g) { return g > NS - 1 ? g - (NS - 1) : 0; }
 __host__ __device__ __forceinline__ int g_hi(int g) { return g < NS - 1 ? g : NS - 1; }
 
-// Stages per exact chunk of level g: n_g = g_hi - g_lo + 1 products of
-// |sigma| <= 128 over period x 32 columns stay within 2^24
-// (1 x 32 x 32, 2 x 16 x 32, 3 x 10 x 32, 4 x 8 x 32, 3 x 10 x 32, times 2^14).
-__host__ __device__ constexpr int period_of(int g) { return g == 0 ? 32 : g == 1 ? 16 : g == 3 ? 8 : 10; }
+// Stages per chunk of level g.  Levels 0-2 are exact: n_g = g_hi - g_lo + 1
+// products of |sigma| <= 128 over period x 32 columns stay within 2^24
+// (1 x 32 x 32, 2 x 16 x 32, 3 x 10 x 32, times 2^14).  Levels 3 and 4 run
+// 32 stages and round (their error bound is in the header).
+__host__ __device__ constexpr int period_of(int g) { return g == 1 ? 16 : g == 2 ? 10 : 32; }
 // Offsets that stagger the levels' chunk boundaries (the first chunk of level
-// g is period - offset stages long).
-__host__ __device__ constexpr int offset_of(int g) { return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 4 : 7; }
-static_assert(32 * 32 * 1 <= 1024 && 16 * 32 * 2 <= 1024 && 10 * 32 * 3 <= 1024 && 8 * 32 * 4 <= 1024,
-              "a chunk must stay within 2^24 = 2^10 x 2^14");
+// g is period - offset stages long): chunk ends fall on stages 31, 10/26,
+// 7 + 10 i, 20 and 6 modulo 32.
+__host__ __device__ constexpr int offset_of(int g) { return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 11 : 25; }
+static_assert(32 * 32 * 1 <= 1024 && 16 * 32 * 2 <= 1024 && 10 * 32 * 3 <= 1024,
+              "an exact chunk must stay within 2^24 = 2^10 x 2^14");
 // Chunk c of level g covers stages [start, end]: start = 0 for c = 0, else
 // c period - offset; end = (c + 1) period - offset - 1, clamped to nk - 1.
 __device__ __forceinline__ int chunk_end(int g, int c, int nk) {
@@ -337,7 +345,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       __syncwarp();
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[gsel])) : "memory");
-      // the level's exact chunk times 2^(8 (4 - g)) (a power of two: exact)
+      // the level's chunk times 2^(8 (4 - g)) (a power of two: exact)
       const float sc = __int_as_float((127 + 8 * (NG - 1 - gsel)) << 23);
 #pragma unroll
       for (int i = 0; i < 32; ++i) df_add_exact(hi[i], lo[i], __uint_as_float(r[i]) * sc);
