@@ -22,11 +22,11 @@
 //     chunk the MMAs accumulate in TMEM stays within 2^24 in magnitude
 //     (level g with n_g products is drained every 2^10 / n_g K columns), so
 //     the FP32 accumulator is exact; levels 3 and 4 (weights 2^-24 and
-//     2^-32 of level 0) are drained every 1024 columns and round in FP32
-//     (chunks below 2^26, so a unit is at most 4): even with each of a
-//     chunk's 256 (level 3) or 192 (level 4) MMA additions off by a full
-//     unit in the same direction this adds at most 2^-40 of the row scales
-//     times n (2^-40 = 256 x 4 x 2^8 x 2^-48 / 1024), below the slicing's
+//     2^-32 of level 0) are drained every 2048 columns and round in FP32
+//     (chunks below 2^27, so a unit is at most 8): even with each of a
+//     chunk's 512 (level 3) or 384 (level 4) MMA additions off by a full
+//     unit in the same direction this adds at most 2^-39 of the row scales
+//     times n (2^-39 = 512 x 8 x 2^8 x 2^-48 / 2048), below the slicing's
 //     own 2^-32; the epilogue adds each chunk into double-float registers
 //     (48-bit significand) times 2^(8(4-g)).
 //
@@ -81,11 +81,11 @@ __host__ __device__ __forceinline__ int g_hi(int g) { return g < NS - 1 ? g : NS
 // Stages per chunk of level g.  Levels 0-2 are exact: n_g = g_hi - g_lo + 1
 // products of |sigma| <= 128 over period x 32 columns stay within 2^24
 // (1 x 32 x 32, 2 x 16 x 32, 3 x 10 x 32, times 2^14).  Levels 3 and 4 run
-// 32 stages and round (their error bound is in the header).
-__host__ __device__ constexpr int period_of(int g) { return g == 1 ? 16 : g == 2 ? 10 : 32; }
+// 64 stages and round (their error bound is in the header).
+__host__ __device__ constexpr int period_of(int g) { return g == 0 ? 32 : g == 1 ? 16 : g == 2 ? 10 : 64; }
 // Offsets that stagger the levels' chunk boundaries (the first chunk of level
 // g is period - offset stages long): chunk ends fall on stages 31, 10/26,
-// 7 + 10 i, 20 and 6 modulo 32.
+// 7 + 10 i (modulo 32), 52 and 38 (modulo 64).
 __host__ __device__ constexpr int offset_of(int g) { return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 11 : 25; }
 static_assert(32 * 32 * 1 <= 1024 && 16 * 32 * 2 <= 1024 && 10 * 32 * 3 <= 1024,
               "an exact chunk must stay within 2^24 = 2^10 x 2^14");
