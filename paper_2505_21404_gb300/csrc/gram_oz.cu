@@ -113,32 +113,18 @@ __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
 
 // Row scaling and slicing: one block per row, float4 loads and 8-byte
 // stores (ldJ and ldb are multiples of 4; the row's pad columns are zero).
+// The row's largest |J| comes from the Jacobian's writer, so J is read once.
 __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const float* __restrict__ J, long long ldJ,
                                                   __nv_bfloat16* __restrict__ S, long long ldS, int ldb,
-                                                  int* __restrict__ rowexp) {
+                                                  const unsigned* __restrict__ rowmax, int* __restrict__ rowexp) {
   const int i = blockIdx.x;
   const float4* row = reinterpret_cast<const float4*>(J + (long long)i * ldJ);
   const int n4 = (n + 3) / 4, b4 = ldb / 4;
-  float amax = 0.f;
-  for (int k = threadIdx.x; k < n4; k += blockDim.x) {
-    const float4 v = __ldg(row + k);
-    amax = fmaxf(fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y))), fmaxf(fabsf(v.z), fabsf(v.w)));
-  }
-  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  __shared__ float red[8];
-  __shared__ int E_sh;
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float a = 0.f;
-    for (int w = 0; w < 8; ++w) a = fmaxf(a, red[w]);
-    int e = 0;
-    if (a > 0.f && a <= 3.0e38f) frexpf(a, &e);   // a = f 2^e, f in [0.5, 1)
-    E_sh = e + 1;                                 // |J| / 2^E < 0.5
-    rowexp[i] = e + 1;
-  }
-  __syncthreads();
-  const int E = E_sh;
+  const float a = __uint_as_float(rowmax[i]);
+  int e = 0;
+  if (a > 0.f && a <= 3.0e38f) frexpf(a, &e);   // a = f 2^e, f in [0.5, 1)
+  const int E = e + 1;                          // |J| / 2^E < 0.5
+  if (threadIdx.x == 0) rowexp[i] = E;
   __nv_bfloat16* srow = S + (long long)i * ldS;
   for (int k = threadIdx.x; k < b4; k += blockDim.x) {
     float x[4];
@@ -469,6 +455,7 @@ struct OzPlan {
   const float* J;
   __nv_bfloat16* S;
   int* rowexp;
+  unsigned* rowmax;
   CUtensorMap mapA, mapB;
   int2* d_tiles = nullptr;
   int ntiles = 0, nsplit = 1, num_kblk = 0;
@@ -491,7 +478,7 @@ size_t gram_oz_partial_bytes(int m, int n) {
 
 size_t gram_oz_slice_bytes(int m, int n) {
   const long long ldb = ((n + 63) / 64) * 64;
-  return (size_t)m * NS * ldb * sizeof(__nv_bfloat16) + (size_t)m * sizeof(int) + 256;
+  return (size_t)m * NS * ldb * sizeof(__nv_bfloat16) + 2 * (size_t)m * sizeof(int) + 256;
 }
 
 dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int n, void* slices, float* K,
@@ -507,6 +494,7 @@ dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int
   p->ldS = (long long)NS * p->ldb;
   p->S = (__nv_bfloat16*)slices;
   p->rowexp = (int*)((char*)slices + (size_t)m * p->ldS * sizeof(__nv_bfloat16));
+  p->rowmax = (unsigned*)(p->rowexp + m);
   p->K = K;
   p->ldk = ldk;
   p->F = F;
@@ -561,7 +549,7 @@ dngd_status gram_oz_set_shift(OzPlan* p, double shift) {
 
 dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_after_mma) {
   DNGD_NOTE_LAUNCH();
-  k_oz_slice<<<p->m, 256, 0, st>>>(p->m, p->n, p->J, p->ldJ, p->S, p->ldS, p->ldb, p->rowexp);
+  k_oz_slice<<<p->m, 256, 0, st>>>(p->m, p->n, p->J, p->ldJ, p->S, p->ldS, p->ldb, p->rowmax, p->rowexp);
   DNGD_LAUNCH_CHECK();
   DNGD_NOTE_LAUNCH();
   k_gram_oz<<<dim3(p->ntiles, p->nsplit), OTHREADS, OSMEM, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk,
@@ -599,5 +587,7 @@ void gram_oz_free(OzPlan* p) {
 }
 
 int gram_oz_nsplit(const OzPlan* p) { return p->nsplit; }
+
+unsigned* gram_oz_rowmax(OzPlan* p) { return p->rowmax; }
 
 }  // namespace dngd

@@ -227,7 +227,7 @@ __global__ void k_act_bwd(NetInfo net, int l, const T* __restrict__ theta, const
 template <typename T, typename TJ>
 __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const double* __restrict__ X,
                             LayerPtrs<T> Hs, LayerPtrs<T> Ds, TJ* __restrict__ J, long long ldJ,
-                            __nv_bfloat16* __restrict__ Jb, long long ldb) {
+                            __nv_bfloat16* __restrict__ Jb, long long ldb, unsigned* __restrict__ rowmax) {
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int p = blockIdx.x;
@@ -268,6 +268,7 @@ __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const doub
   TJ* Jrow = J + (long long)p * ldJ;
   __nv_bfloat16* Jbrow = Jb ? Jb + (long long)p * ldb : nullptr;
   const long long wo = net.w_off[l], bo = net.b_off[l];
+  float amax = 0.f;   // largest |J| this block writes (as stored)
   for (int b = threadIdx.x; b < win; b += blockDim.x) {
     // the stream loops are unrolled to the largest S so hreg stays in registers
     T hreg[2 + kMaxDim];
@@ -294,6 +295,7 @@ __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const doub
           for (int q = 0; q < 4; ++q) {
             Jrow[wo + (long long)(a + q) * win + b] = (TJ)o[q];
             if (Jbrow) Jbrow[wo + (long long)(a + q) * win + b] = __float2bfloat16_rn(o[q]);
+            amax = fmaxf(amax, fabsf(o[q]));
           }
         }
       }
@@ -307,11 +309,26 @@ __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const doub
       }
       Jrow[wo + (long long)a * win + b] = (TJ)acc;
       if (Jbrow) Jbrow[wo + (long long)a * win + b] = __float2bfloat16_rn((float)acc);
+      amax = fmaxf(amax, fabsf((float)(TJ)acc));
     }
   }
   for (int a = threadIdx.x; a < wout; a += blockDim.x) {
     Jrow[bo + a] = (TJ)dsh[a];
     if (Jbrow) Jbrow[bo + a] = __float2bfloat16_rn((float)dsh[a]);
+    amax = fmaxf(amax, fabsf((float)(TJ)dsh[a]));
+  }
+  if (rowmax) {
+    // the row's largest magnitude over all layer blocks (non-negative floats
+    // order like their bit patterns)
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float a = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmaxf(a, red[w]);
+      atomicMax(rowmax + p, __float_as_uint(a));
+    }
   }
 }
 
@@ -610,7 +627,7 @@ template <typename T, typename TJ>
 dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
                                    LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
                                    __nv_bfloat16* Jb, long long ldb, cudaStream_t st, const Tc3Scratch* tc3,
-                                   int* status) {
+                                   int* status, unsigned* rowmax) {
   const int L = net.n_layers - 1;
   const int thr = 128;
   for (int l = L - 1; l >= 0; --l) {
@@ -639,8 +656,9 @@ dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const dou
   }
   if (J == nullptr) return DNGD_OK;  // matrix-free use: stream adjoints only
   dim3 grid(net.m, L + 1);
+  if (rowmax) DNGD_CUDA_CHECK(cudaMemsetAsync(rowmax, 0, sizeof(unsigned) * net.m, st));
   DNGD_NOTE_LAUNCH();
-  k_jac_write<T, TJ><<<grid, 256, smem, st>>>(net, theta, X, H, D, J, ldJ, Jb, ldb);
+  k_jac_write<T, TJ><<<grid, 256, smem, st>>>(net, theta, X, H, D, J, ldJ, Jb, ldb, rowmax);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
@@ -696,12 +714,12 @@ template dngd_status jets_backward_jacobian<double, double>(const NetInfo&, cons
                                                             LayerPtrs<double>, LayerPtrs<double>,
                                                             LayerPtrs<double>, double*, double*, long long,
                                                             __nv_bfloat16*, long long, cudaStream_t,
-                                                            const Tc3Scratch*, int*);
+                                                            const Tc3Scratch*, int*, unsigned*);
 template dngd_status jets_backward_jacobian<float, float>(const NetInfo&, const float*, const double*,
                                                           LayerPtrs<float>, LayerPtrs<float>,
                                                           LayerPtrs<float>, float*, float*, long long,
                                                           __nv_bfloat16*, long long, cudaStream_t,
-                                                          const Tc3Scratch*, int*);
+                                                          const Tc3Scratch*, int*, unsigned*);
 template dngd_status jets_fvv<double>(const NetInfo&, const double*, const double*, const double*, double*,
                                       double*, double*, double*, cudaStream_t, const Tc3Scratch*, int*);
 template dngd_status jets_fvv<float>(const NetInfo&, const float*, const float*, const double*, float*,

@@ -31,7 +31,8 @@ template <typename T, typename TJ>
 dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
                                    LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
                                    __nv_bfloat16* Jb, long long ldb, cudaStream_t st,
-                                   const Tc3Scratch* tc3 = nullptr, int* status = nullptr);
+                                   const Tc3Scratch* tc3 = nullptr, int* status = nullptr,
+                                   unsigned* rowmax = nullptr);
 
 template <typename T>
 dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const double* X, T* Z3, T* H3a,
@@ -139,6 +140,9 @@ dngd_status gram_oz_plan(OzPlan** plan, const float* J, long long ldJ, int m, in
 dngd_status gram_oz_read(const OzPlan* plan, double* out, cudaStream_t st);  // F as FP64 [m x ldf]
 dngd_status gram_oz_set_shift(OzPlan* plan, double shift);
 dngd_status gram_oz_run(OzPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
+// Per-row largest |J| (float bits) that the writer of J fills for the slicing
+// (jets_backward_jacobian's rowmax); gram_oz_run reads it.
+unsigned* gram_oz_rowmax(OzPlan* plan);
 dngd_status gram_oz_reduce(OzPlan* plan, cudaStream_t st);
 void gram_oz_free(OzPlan* plan);
 int gram_oz_nsplit(const OzPlan* plan);
