@@ -409,7 +409,7 @@ __device__ __forceinline__ int warp_chol32_inv(float (&a)[32], float (&y)[32], i
 // of the tensor-core panel GEMM, row i: tf32 hi of X[i][0..Kp) then lo
 // (Kp = kb rounded up to 32, zero beyond kb).
 __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A, long long lda, float* Linv,
-                                                        long long ldi, float* bsplit, int* status) {
+                                                        long long ldi, int rest, float* asplit, int* status) {
   __shared__ float S[kCholNB][kCholNB + 1];
   __shared__ float X[kCholNB][kCholNB + 1];
   __shared__ float T[32][33];
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A,
     __syncthreads();
   }
   if (bad >= 0) {
-    if (tid == 0 && bad < kb) {
+    if (blockIdx.x == 0 && tid == 0 && bad < kb) {
       const int old = atomicOr(status, ST_NOT_SPD);
       if (!(old & ST_NOT_SPD)) status[1] = k0 + bad;
     }
@@ -527,26 +527,71 @@ __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A,
       for (int q = 0; q < 2; ++q) X[32 + r0 + p][c0 + q] = -acc[p][q];
     __syncthreads();
   }
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < kCholNB * kCholNB; e += blockDim.x) {
+      const int i = e / kCholNB, c = e % kCholNB;
+      if (i < kb && c < kb) {
+        if (c <= i) A[(long long)(k0 + i) * lda + k0 + c] = S[i][c];
+        Linv[(long long)(k0 + i) * ldi + k0 + c] = (c <= i) ? X[i][c] : 0.f;
+      }
+    }
+    return;
+  }
+  // CTA b >= 1: panel rows k0 + kb + 64 (b - 1) .. (+64): P <- P L11^{-T}
+  // (P[r][c] = sum_{k <= c} P[r][k] X[c][k]), written back into A and, for
+  // the trailing update, as its split A operand (rows from the panel's first
+  // row, 2 kp floats each: TF32 hi, then lo)
   const int kp = (kb + 31) & ~31;
+  const int rb0 = (blockIdx.x - 1) * kCholNB;
+  const int nr = min(kCholNB, rest - rb0);
+  const long long grow0 = (long long)k0 + kb + rb0;
   for (int e = tid; e < kCholNB * kCholNB; e += blockDim.x) {
     const int i = e / kCholNB, c = e % kCholNB;
-    if (i < kb && c < kb) {
-      if (c <= i) A[(long long)(k0 + i) * lda + k0 + c] = S[i][c];
-      Linv[(long long)(k0 + i) * ldi + k0 + c] = (c <= i) ? X[i][c] : 0.f;
-    }
-    if (bsplit && i < kb && c < kp) {
-      const float x = (c <= i && c < kb) ? X[i][c] : 0.f;
-      const float hi = tf32_round(x);
-      bsplit[(long long)i * 2 * kp + c] = hi;
-      bsplit[(long long)i * 2 * kp + kp + c] = tf32_round(x - hi);
+    S[i][c] = (i < nr && c < kb) ? A[(grow0 + i) * lda + k0 + c] : 0.f;
+  }
+  __syncthreads();
+  // 4 x 4 outputs per thread: rows 4 (tid / 16) .., columns (tid % 16) + 16 q
+  const int rr = 4 * (tid >> 4), cc = tid & 15;
+  float acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < kCholNB; ++k) {
+    float pv[4], xv[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) pv[p] = S[rr + p][k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xv[q] = X[cc + 16 * q][k];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] += pv[p] * xv[q];
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int i = rr + p;
+    if (i >= nr) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = cc + 16 * q;
+      if (c < kb) A[(grow0 + i) * lda + k0 + c] = acc[p][q];
+      if (asplit && c < kp) {
+        const float x = c < kb ? acc[p][q] : 0.f;
+        const float hi = tf32_round(x);
+        float* sp = asplit + (long long)(rb0 + i) * 2 * kp;
+        sp[c] = hi;
+        sp[kp + c] = tf32_round(x - hi);
+      }
     }
   }
 }
 
-// With the tensor-core GEMMs a 64-column step is four launches: the block
-// factor (which also writes its inverse's split as the panel GEMM's B
-// operand), the split of the panel, the panel GEMM (whose epilogue writes the
-// split of the solved panel) and the trailing update reading that split.
+// A 64-column step is two launches: the block factor with the panel solve
+// (every CTA factors the 64 x 64 diagonal block and its inverse, CTA 0 stores
+// them, CTA b >= 1 solves 64 panel rows in FP32 and also writes them as the
+// trailing update's split operand), then the trailing update.
 dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long long ldi, int* status,
                              cudaStream_t st, const Tc3Scratch* tc3) {
   const bool tc = tc3 && tc3->buf && tc3_scratch_bytes(m, m, kCholNB) <= tc3->bytes;
@@ -556,27 +601,18 @@ dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long l
     const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
     const int rest = m - k0 - kb;
     DNGD_NOTE_LAUNCH();
-    k_potrf_inv_f32<<<1, 256, 0, st>>>(k0, kb, A, lda, Linv, ldi, (tc && rest > 0) ? b_half : nullptr, status);
+    k_potrf_inv_f32<<<1 + cdiv(rest, kCholNB), 256, 0, st>>>(k0, kb, A, lda, Linv, ldi, rest,
+                                                              (tc && rest > 0) ? a_half : nullptr, status);
     DNGD_LAUNCH_CHECK();
     if (rest <= 0) break;
     float* P = A + (long long)(k0 + kb) * lda + k0;
-    const float* I11 = Linv + (long long)k0 * ldi + k0;
     float* A22 = A + (long long)(k0 + kb) * lda + k0 + kb;
-    // panel: P <- P L11^{-T} = P * (L11^{-1})^T (in place: one column tile;
-    // the tensor-core form reads P from its split copy)
-    if (tc) {
-      dngd_status s = gemm_tc3(rest, kb, kb, 1.0f, P, lda, false, I11, ldi, false, 0.0f, P, lda, false, *tc3, status,
-                               st, TC3_B_PRESPLIT | TC3_C_SPLIT);
-      if (s) return s;
-      s = gemm_tc3(rest, rest, kb, -1.0f, P, lda, false, P, lda, false, 1.0f, A22, lda, true, *tc3, status, st,
-                   TC3_A_PRESPLIT);
-      if (s) return s;
-    } else {
-      dngd_status s = gemm_nt<float>(rest, kb, kb, 1.0f, P, lda, I11, ldi, 0.0f, P, lda, false, st);
-      if (s) return s;
-      s = gemm_nt<float>(rest, rest, kb, -1.0f, P, lda, P, lda, 1.0f, A22, lda, true, st);
-      if (s) return s;
-    }
+    // trailing update A22 -= P P^T (lower); the tensor-core form reads P from
+    // the split the panel solve wrote
+    dngd_status s = tc ? gemm_tc3(rest, rest, kb, -1.0f, P, lda, false, P, lda, false, 1.0f, A22, lda, true, *tc3,
+                                  status, st, TC3_A_PRESPLIT)
+                       : gemm_nt<float>(rest, rest, kb, -1.0f, P, lda, P, lda, 1.0f, A22, lda, true, st);
+    if (s) return s;
   }
   return DNGD_OK;
 }
