@@ -625,11 +625,10 @@ def main():
                      "algorithmic": "13 m(m+1)n BF16 tensor flops (the exact Gram's 13 slice products)",
                      "exact_gram_tflops_fp64_equivalent": gram_flops / 13.0 / (gram_ms * 1e-3) / 1e12,
                      "peak_source": f"{src} bf16 sustained (measured)",
-                     # dram read + write of one launch from the ncu capture of the same kernel on the
-                     # width-128 case (n = 33,921), scaled by n to this workload (same m and tiles)
-                     # ncu capture on the width-128 case (n = 33,921): DRAM read scales with the K
-                     # extent n, the partial-tile writes do not
-                     "traffic": ((4.627013e9 * n / 33921.0 + 0.285605e9)
+                     # DRAM read + write of one launch from the ncu capture of the same kernel on
+                     # the width-128 case (n = 33,921, same m and tiles): the reads scale with the
+                     # K extent n, the partial-tile writes do not
+                     "traffic": ((4.784785e9 * n / 33921.0 + 0.303845e9)
                                  if args.workload in ("poisson5d", "poisson5d_w128") else None),
                      "traffic_source": "profiles/k_gram_oz_poisson5d_w128.md (scaled by n)"}
     else:
