@@ -618,7 +618,7 @@ def main():
                      "algorithmic": "per PCG iteration 8 m^2 + 4 m^2 B (exact Gram operator, L^-1 and L^-T "
                                     "triangles); per solve 4 m n B (J^T x)",
                      "peak_source": f"{src} HBM copy bandwidth (measured)", "traffic": None}
-        roof_gram = {"bound": "tensor", "kernel": "k_oz_slice + k_gram_oz (tcgen05 BF16, 13 exact slice products, "
+        roof_gram = {"bound": "tensor", "kernel": "k_oz_slice + k_gram_oz (tcgen05 BF16, 13 integer slice products, "
                                                   "128x96 tiles)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "flops_per_launch": gram_flops, "launch_ms": gram_ms,
