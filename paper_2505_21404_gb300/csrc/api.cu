@@ -1099,6 +1099,7 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
   if (desc->solver != DNGD_DENSE && desc->solver != DNGD_PCG) return DNGD_ERR_INVALID_ARG;
   if (desc->solver == DNGD_PCG && desc->precision == DNGD_FP64) return DNGD_ERR_INVALID_ARG;
   if (!(desc->lambda > 0.0)) return DNGD_ERR_INVALID_ARG;
+  gemv_init();
   dngd_ctx* c = new dngd_ctx();
   c->desc = *desc;
   dngd_status s = build_net(desc, &c->net);

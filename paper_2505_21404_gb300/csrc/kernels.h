@@ -168,6 +168,8 @@ dngd_status gemv_n(int m, int n, const TA* A, long long lda, const double* x, do
 // ---- refine.cu: FP32 matrices with double-float accumulation ---------------
 // y = alpha A^T x (A [m x n] FP32, lda % 4 == 0, padding columns zero).
 // xs: scratch of round_up(max(m, n), 4) + 4 float2; partial_cap: doubles in partials.
+// Queries the GEMV launch shape once (outside any stream capture).
+void gemv_init();
 dngd_status gemv_t_f32(int m, int n, const float* A, long long lda, const double* x, double alpha, double* y,
                        double* partials, long long partial_cap, float2* xs, cudaStream_t st);
 

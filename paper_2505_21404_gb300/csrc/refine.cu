@@ -327,14 +327,30 @@ __global__ void k_cg_init(int parts, const double* __restrict__ rz_parts, const 
 
 constexpr int kVecBlocks = 64;
 
+// Resident blocks of k_gemv_t_f32 on the whole device (one wave).
+int gemv_t_wave() {
+  static int wave = 0;
+  if (!wave) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 152;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gemv_t_f32, 256, 0) != cudaSuccess || per < 1) per = 4;
+    cudaGetLastError();
+    wave = nsm * per;
+  }
+  return wave;
+}
+
 dngd_status gemv_t_f32_s(int m, int n, const float* A, long long lda, const double* x, double alpha, double* y,
                          double* partials, long long partial_cap, float2* xs, const double* scal,
                          cudaStream_t st) {
   const int mpad = (m + 3) & ~3;
   DNGD_NOTE_LAUNCH();
   k_split_vec<<<cdiv(mpad, 256), 256, 0, st>>>(m, mpad, x, xs, scal);
+  // row splits: as many as fill one wave of resident blocks (a second, partly
+  // filled wave would leave the memory system idle at its end)
   const int gx = cdiv(n, 1024);
-  int splits = cdiv(8 * 152, gx);
+  int splits = max(1, gemv_t_wave() / gx);
   splits = min(splits, max(1, m / 16));
   while (splits > 1 && (long long)splits * n > partial_cap) --splits;
   const int rows = cdiv(m, splits);
@@ -368,6 +384,8 @@ dngd_status precond(const PcgMixed& P, const double* q, double* z, cudaStream_t 
 }
 
 }  // namespace
+
+void gemv_init() { gemv_t_wave(); }
 
 dngd_status gemv_t_f32(int m, int n, const float* A, long long lda, const double* x, double alpha, double* y,
                        double* partials, long long partial_cap, float2* xs, cudaStream_t st) {
