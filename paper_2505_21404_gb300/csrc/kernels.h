@@ -73,8 +73,10 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 // FP32 factorisation of the mixed path: A = L L^T in place (lower) and the
 // inverses of the 64 x 64 diagonal blocks of L written into Linv, which the
 // caller zero-initialises; trtri_offdiag_f32 then completes Linv = L^{-1}.
-// tc3 (optional): the panel / trailing / inverse GEMMs on the TF32 tensor
-// cores (3xTF32) — the factor only preconditions the refinement.
+// tc3 (optional): the trailing / inverse GEMMs on the TF32 tensor cores
+// (3xTF32) — the factor only preconditions the refinement.  status: the
+// context's four status words; status[3] counts the block-factor CTAs within
+// a launch and is zero outside one.
 dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long long ldi, int* status,
                              cudaStream_t st, const Tc3Scratch* tc3 = nullptr);
 dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,

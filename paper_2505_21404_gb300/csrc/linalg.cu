@@ -424,6 +424,16 @@ __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A,
   }
   if (tid == 0) bad = -1;
   __syncthreads();
+  // every CTA computes the same factor; the diagonal block of A is
+  // overwritten with it only by the last CTA to have read the block, so no
+  // CTA that starts late reads a half-written block (status[3] counts the
+  // arrivals and is zero again once the last one has arrived)
+  __shared__ int writer;
+  if (tid == 0) {
+    const int old = atomicAdd(status + 3, 1);
+    writer = (old == (int)gridDim.x - 1) ? 1 : 0;
+    if (writer) status[3] = 0;
+  }
   // 2 x 2 output elements per thread in the 32 x 32 products
   const int r0 = 2 * (tid >> 4), c0 = 2 * (tid & 15);
   for (int half = 0; half < 2; ++half) {
@@ -527,16 +537,20 @@ __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A,
       for (int q = 0; q < 2; ++q) X[32 + r0 + p][c0 + q] = -acc[p][q];
     __syncthreads();
   }
+  if (writer) {
+    for (int e = tid; e < kCholNB * kCholNB; e += blockDim.x) {
+      const int i = e / kCholNB, c = e % kCholNB;
+      if (i < kb && c <= i) A[(long long)(k0 + i) * lda + k0 + c] = S[i][c];
+    }
+  }
   if (blockIdx.x == 0) {
     for (int e = tid; e < kCholNB * kCholNB; e += blockDim.x) {
       const int i = e / kCholNB, c = e % kCholNB;
-      if (i < kb && c < kb) {
-        if (c <= i) A[(long long)(k0 + i) * lda + k0 + c] = S[i][c];
-        Linv[(long long)(k0 + i) * ldi + k0 + c] = (c <= i) ? X[i][c] : 0.f;
-      }
+      if (i < kb && c < kb) Linv[(long long)(k0 + i) * ldi + k0 + c] = (c <= i) ? X[i][c] : 0.f;
     }
     return;
   }
+  __syncthreads();   // S is reused for the panel rows below
   // CTA b >= 1: panel rows k0 + kb + 64 (b - 1) .. (+64): P <- P L11^{-T}
   // (P[r][c] = sum_{k <= c} P[r][k] X[c][k]), written back into A and, for
   // the trailing update, as its split A operand (rows from the panel's first

@@ -91,3 +91,37 @@ def test_batch_instance_matches_oracle(dngd):
         ref = ostep.dense_step(wl["theta"], ores.problem_from_spec(wl), wl["X"], wl["target"], wl["lam"])
         err = float(np.linalg.norm(d.cpu().numpy() - ref["delta"]) / np.linalg.norm(ref["delta"]))
         assert err <= 1e-4, err
+
+
+def test_crowded_batch_equals_alone(dngd):
+    """Many larger instances at once, so that the CTAs of one instance's
+    kernels start at different times on a busy device: every instance of the
+    captured batch step still equals the same instance stepped alone, bit for
+    bit, and no factorisation fails (a failed one would be redone
+    synchronously and recaptured)."""
+    rng = np.random.default_rng(77)
+    wls = []
+    for b in range(24):
+        m = int(rng.integers(1000, 2001))
+        w = int(rng.choice([32, 64]))
+        nb = round(0.2 * m)
+        wls.append(workloads.poisson_sine(2, [2, w, w, 1], m - nb, nb, k=int(rng.integers(1, 9)), seed=2000 + b,
+                                          lam=1e-5))
+    descs = [dngd.make_desc(wl, precision=dngd.MIXED_OZ, refine_tol=1e-8, refine_max_it=60) for wl in wls]
+    batch = dngd.Batch(descs)
+    ths = [_t(wl["theta"]) for wl in wls]
+    Xs = [_t(wl["X"]) for wl in wls]
+    tgs = [_t(wl["target"]) for wl in wls]
+    db = [torch.zeros(len(wl["theta"]), dtype=torch.float64, device=DEV) for wl in wls]
+    for _ in range(3):      # synchronous first step, then the captured graph twice
+        batch.step(ths, Xs, tgs, db)
+    torch.cuda.synchronize()
+    alone = [dngd.Context(d) for d in descs]
+    da = [torch.zeros_like(d) for d in db]
+    for i, c in enumerate(alone):
+        for _ in range(2):      # the first call is synchronous and fixes the shift, as in the batch
+            c.step_async(ths[i], Xs[i], tgs[i], da[i])
+            c.step_wait()
+    torch.cuda.synchronize()
+    for i in range(len(wls)):
+        assert torch.equal(da[i], db[i]), i
