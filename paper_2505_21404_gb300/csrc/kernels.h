@@ -75,8 +75,10 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 // caller zero-initialises; trtri_offdiag_f32 then completes Linv = L^{-1}.
 // tc3 (optional): the trailing / inverse GEMMs on the TF32 tensor cores
 // (3xTF32) — the factor only preconditions the refinement.  status: the
-// context's four status words; status[3] counts the block-factor CTAs within
-// a launch and is zero outside one.
+// context's four status words, all zero on entry; status[3] counts the
+// block-factor CTAs within a launch and is zero again after it, except after
+// a failed factorisation (ST_NOT_SPD), which the caller clears with the other
+// words before the next one.
 dngd_status cholesky_f32_inv(int m, float* A, long long lda, float* Linv, long long ldi, int* status,
                              cudaStream_t st, const Tc3Scratch* tc3 = nullptr);
 dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
