@@ -396,11 +396,26 @@ __global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const doub
   while (bi * (bi + 1) / 2 > b) --bi;
   const int bj = b - bi * (bi + 1) / 2;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
+  // every partial this thread needs is loaded before the first sum (up to 16
+  // loads in flight); the sums keep the split order (nsplit <= 4)
+  double pv[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = bi * 32 + ty + 8 * q, j = bj * 32 + tx;
+    const bool in = i < m && j < m && j <= i;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+      pv[q][sp] = (in && sp < nsplit) ? P[(long long)sp * sstride + (long long)i * ldp + j] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = ty + 8 * q;
     const int i = bi * 32 + r, j = bj * 32 + tx;
     double v = 0.0;
     if (i < m && j < m && j <= i) {
-      for (int sp = 0; sp < nsplit; ++sp) v += P[(long long)sp * sstride + (long long)i * ldp + j];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+        if (sp < nsplit) v += pv[q][sp];
       v = ldexp(v, rowexp[i] + rowexp[j] - 48);
     }
     t[r][tx] = v;
@@ -563,6 +578,7 @@ dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_
 // Re-run only the reduction (e.g. with a new shift): the partial tiles of
 // the last run stay valid.
 dngd_status gram_oz_reduce(OzPlan* p, cudaStream_t st) {
+  if (p->nsplit > 4) return DNGD_ERR_INVALID_ARG;   // the reduction sums at most four partial tiles
   const int nb = (p->m + 31) / 32;
   DNGD_NOTE_LAUNCH();
   k_oz_reduce<<<nb * (nb + 1) / 2, 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->rowexp,
