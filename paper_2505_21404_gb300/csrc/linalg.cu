@@ -405,9 +405,12 @@ __device__ __forceinline__ int warp_chol32_inv(float (&a)[32], float (&y)[32], i
   return bad;
 }
 
-// bsplit (optional): the inverse block also goes out as the B operand split
-// of the tensor-core panel GEMM, row i: tf32 hi of X[i][0..Kp) then lo
-// (Kp = kb rounded up to 32, zero beyond kb).
+// Grid: 1 + ceil(rest / 64) CTAs.  CTA 0 stores the block's inverse into
+// Linv; CTA b >= 1 solves panel rows k0 + kb + 64 (b - 1) .. (+64) and, with
+// asplit given, also writes them as the trailing update's split A operand
+// (row r of the panel: TF32 hi of its kp = kb rounded up to 32 values, then
+// lo; zero beyond kb).  The factored block itself goes back into A from the
+// last CTA to have read it (status[3] counts the arrivals).
 __global__ void __launch_bounds__(256) k_potrf_inv_f32(int k0, int kb, float* A, long long lda, float* Linv,
                                                         long long ldi, int rest, float* asplit, int* status) {
   __shared__ float S[kCholNB][kCholNB + 1];
