@@ -73,9 +73,11 @@ enum dngd_precision {
   DNGD_MIXED_TF32 = 2,  /* as MIXED_BF16 with a TF32 tensor-core Gram */
   DNGD_MIXED_OZ = 3     /* FP32 jets/J; exact Gram of the FP32 J from four
                            8-bit integer slices per row on the BF16 tensor
-                           cores (13 slice products, exact FP32 chunks summed
-                           in double-float: K accurate to ~2^-33 of the row
-                           scales); the FP32 factor of K + (lambda+mu) I (as
+                           cores (13 slice products; the three leading levels
+                           in exact FP32 chunks, the two trailing ones rounded
+                           within 2^-39 of the row scales times n; chunks
+                           summed in double-float: K accurate to ~2^-33 of the
+                           row scales); the FP32 factor of K + (lambda+mu) I (as
                            MIXED_BF16) preconditions PCG whose operator is the
                            exact FP64 Gram (one m x m GEMV per iteration
                            instead of two over J) */
