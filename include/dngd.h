@@ -112,7 +112,12 @@ typedef struct {
   dngd_class_desc classes[DNGD_MAX_CLASSES];
   int precision;                     /* enum dngd_precision */
   int solver;                        /* enum dngd_solver */
-  double lambda;                     /* Levenberg-Marquardt damping, > 0 */
+  double lambda;                     /* Levenberg-Marquardt damping, > 0;
+                                        FP64 contexts also accept a finite
+                                        lambda <= 0, with which K + lambda I
+                                        may be indefinite: the factorisation
+                                        then reports DNGD_ERR_NOT_SPD and the
+                                        failing column */
   int use_ga;                        /* geodesic acceleration on/off */
   double eps_norm;                   /* GA guard: accept only if ||v|| > eps_norm */
   double ga_ratio_max;               /* GA threshold on 2||a||/||v|| (paper: 0.5) */
@@ -129,6 +134,18 @@ typedef struct {
                                         dngd_set_landmarks or are evenly spaced) */
   int keep_gram;                     /* keep K + lambda I for dngd_get_stage(6)
                                         (debug; one extra m x m buffer) */
+  double lambda_cap;                 /* > 0: the damping rule of the paper's
+                                        experiments (App. A.3 tables),
+                                        lambda_k = min(L(theta_k), lambda_cap)
+                                        with L = 1/2 ||r(theta_k)||^2, taken by
+                                        every synchronous step (dngd_step)
+                                        right after the residuals; lambda (or
+                                        dngd_set_lambda) is then ignored by
+                                        those steps.  A loss that is zero or
+                                        not finite gives lambda_cap.  The
+                                        asynchronous and batched steps keep
+                                        the lambda of the last synchronous
+                                        step.  0: fixed lambda. */
 } dngd_problem_desc;
 
 typedef struct {
@@ -153,6 +170,7 @@ typedef struct {
   float jt_ms, j_ms;        /* durations of the first J^T p and J u launches of
                                the refinement (mixed, timing enabled): each
                                reads the FP32 J once */
+  double lambda_used;       /* the damping this step solved with */
 } dngd_step_info;
 
 typedef struct dngd_ctx dngd_ctx;
@@ -184,8 +202,10 @@ dngd_status dngd_destroy(dngd_ctx* ctx);
 /* Enable (1) or disable (0) per-phase CUDA-event timing in dngd_step_info. */
 dngd_status dngd_set_timing(dngd_ctx* ctx, int enable);
 
-/* Override the damping lambda for the following calls (the paper's rule
- * lambda_k = min(L, cap) changes it every step). */
+/* Override the damping lambda for the following calls (> 0; FP64 contexts
+ * also accept a finite lambda <= 0, as dngd_create).  A context whose
+ * descriptor sets lambda_cap applies the paper's rule lambda_k = min(L, cap)
+ * in each synchronous step instead. */
 dngd_status dngd_set_lambda(dngd_ctx* ctx, double lambda);
 
 /* One D-NGD step (Alg. DenseDualSolve or PCGStep; push-through recovery).

@@ -23,6 +23,8 @@ Scalable Training of Physics-Informed Neural Networks", TMLR 2025):
                   preconditioner (Eq. spec_precond_nystrom, Sec. 3.3.1) and
                   PCG (Alg. PCGStep, App. A.2).
 * ``linesearch``- grid line search of the D-NGD workflow (Alg. D-NGD Workflow).
+* ``evaluate``  - relative L2 error of u_theta against the manufactured
+                  solution on a midpoint grid (the error columns of Sec. 5).
 
 Every function cites the passage it follows.  The oracle shares no code with
 the CUDA path; inputs come from the seeded generators in

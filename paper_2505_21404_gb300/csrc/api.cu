@@ -161,6 +161,12 @@ dngd_status dalloc(dngd_ctx* c, T** p, size_t count) {
 
 long long round_up(long long a, long long b) { return ((a + b - 1) / b) * b; }
 
+// lambda > 0 everywhere; an FP64 context also takes a finite lambda <= 0
+// (K + lambda I may then be indefinite, which its Cholesky reports)
+bool lambda_ok(int prec, double lambda) {
+  return prec == DNGD_FP64 ? isfinite(lambda) != 0 : lambda > 0.0 && isfinite(lambda) != 0;
+}
+
 dngd_status build_net(const dngd_problem_desc* d, NetInfo* net) {
   memset(net, 0, sizeof(*net));
   if (d->n_layers < 1 || d->n_layers > kMaxLayers) return DNGD_ERR_INVALID_ARG;
@@ -243,6 +249,22 @@ dngd_status read_status(dngd_ctx* c) {
   if (s & ST_NOT_SPD) return DNGD_ERR_NOT_SPD;
   if (s & ST_NONFINITE) return DNGD_ERR_NONFINITE;
   if (s & ST_NO_CONVERGE) return DNGD_ERR_NO_CONVERGE;
+  return DNGD_OK;
+}
+
+// The damping rule lambda_k = min(L(theta_k), cap) of the paper's experiments
+// (App. A.3), L = 1/2 ||r||^2 of the residuals just computed: one reduction
+// and one read-back before K + lambda I is formed.
+dngd_status apply_lambda_rule(dngd_ctx* c) {
+  const double cap = c->desc.lambda_cap;
+  if (!(cap > 0.0) || c->async) return DNGD_OK;
+  dngd_status s = dot_dev(c->m, c->r, c->r, c->scal + S_LOSS, c->dot_partials, c->st);
+  if (s) return s;
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h + S_LOSS, c->scal + S_LOSS, sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->st));
+  DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+  const double loss = 0.5 * c->scal_h[S_LOSS];
+  c->lambda = (loss > 0.0 && isfinite(loss) && loss < cap) ? loss : cap;
   return DNGD_OK;
 }
 
@@ -408,6 +430,7 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
   evrec(c, 0);
   const T* thT = theta_in_T<T>(c, theta);
   if ((s = residual_jacobian_T<T>(c, thT, X, target))) return s;
+  if ((s = apply_lambda_rule(c))) return s;
   evrec(c, 1);
   // K + lambda I (lower)
   if (c->prec == DNGD_FP64) {
@@ -600,6 +623,7 @@ dngd_status step_pcg(dngd_ctx* c, const double* theta, const double* X, const do
   if ((s = jets_backward_jacobian<float, float>(c->net, th, X, lp<float>(c->Z), lp<float>(c->H), lp<float>(c->D),
                                                 (float*)c->Hbar, (float*)nullptr, 0, nullptr, 0, c->st)))
     return s;
+  if ((s = apply_lambda_rule(c))) return s;
   evrec(c, 1);
   c->mf.X = X;
   if ((s = mf_input_rows(c->mf, c->st))) return s;
@@ -816,6 +840,7 @@ void info_from_host(dngd_ctx* c, dngd_step_info* info) {
   info->not_spd_column = (c->status_h[0] & ST_NOT_SPD) ? c->status_h[1] : -1;
   info->shift_used = c->pcg ? c->nu_used : c->shift_used;
   info->factor_attempts = c->factor_attempts;
+  info->lambda_used = c->lambda;
   if (c->timing) {
     // event order: 0 start, 1 jets+J, 8 Gram kernel, 2 Gram epilogue, 3 factor,
     // 4 solve r, 5 f_vv, 6 solve f_vv, 7 end
@@ -1098,7 +1123,8 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
   if (desc->precision < DNGD_FP64 || desc->precision > DNGD_MIXED_OZ) return DNGD_ERR_INVALID_ARG;
   if (desc->solver != DNGD_DENSE && desc->solver != DNGD_PCG) return DNGD_ERR_INVALID_ARG;
   if (desc->solver == DNGD_PCG && desc->precision == DNGD_FP64) return DNGD_ERR_INVALID_ARG;
-  if (!(desc->lambda > 0.0)) return DNGD_ERR_INVALID_ARG;
+  if (!lambda_ok(desc->precision, desc->lambda) || !(desc->lambda_cap >= 0.0) || !isfinite(desc->lambda_cap))
+    return DNGD_ERR_INVALID_ARG;
   gemv_init();
   dngd_ctx* c = new dngd_ctx();
   c->desc = *desc;
@@ -1136,7 +1162,7 @@ dngd_status dngd_set_timing(dngd_ctx* c, int enable) {
 }
 
 dngd_status dngd_set_lambda(dngd_ctx* c, double lambda) {
-  if (!c || !(lambda > 0.0)) return DNGD_ERR_INVALID_ARG;
+  if (!c || !lambda_ok(c->prec, lambda)) return DNGD_ERR_INVALID_ARG;
   c->lambda = lambda;
   return DNGD_OK;
 }

@@ -163,6 +163,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   __shared__ __align__(8) uint64_t empty_bar[OST];
   __shared__ __align__(8) uint64_t accf_bar[NG];   // MMA -> epilogue: level g committed
   __shared__ __align__(8) uint64_t acce_bar[NG];   // epilogue -> MMA: level g drained
+  __shared__ __align__(8) uint64_t fin_bar;    // teardown: every issued MMA retired
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
@@ -184,6 +185,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       mbar_init(smem_u32(&accf_bar[g]), 1);
       mbar_init(smem_u32(&acce_bar[g]), EPI_WARPS);
     }
+    mbar_init(smem_u32(&fin_bar), 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -362,6 +364,11 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((it / OST) & 1), status, 14);
     }
   }
+  // on abort, the MMAs already issued must retire before TMEM is freed
+  if (warp == 1 && lane == 0 && *abort_flag) {
+    umma_commit(smem_u32(&fin_bar));
+    mbar_wait(smem_u32(&fin_bar), 0u, status, 16);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 1) {
@@ -451,12 +458,21 @@ int oz_splits(int ntiles, int num_kblk, int nsm) {
 }
 
 // Output tiles (I: 128-row block, J: 96-column block) touching the lower
-// triangle; partial tiles are stored [split][mp rows][lp columns].
+// triangle; partial tiles are stored [split][mp rows][lp columns].  CTAs run
+// roughly in tile-list order, one per SM, so the list goes by super-blocks of
+// kSB x kSB tiles: the ~one wave of CTAs working at a time reads the slice
+// rows of kSB row blocks and kSB column blocks (which L2 then serves to the
+// other tiles of the super-block) instead of every column block of a few
+// row blocks.
+constexpr int kSB = 12;
 std::vector<int2> oz_tiles(int m) {
   std::vector<int2> t;
   const int nI = (m + TM - 1) / TM, nJ = (m + TN - 1) / TN;
-  for (int I = 0; I < nI; ++I)
-    for (int Jc = 0; Jc < nJ && Jc * TN <= I * TM + TM - 1; ++Jc) t.push_back(make_int2(I, Jc));
+  for (int I0 = 0; I0 < nI; I0 += kSB)
+    for (int J0 = 0; J0 < nJ && J0 * TN <= (I0 + kSB) * TM - 1; J0 += kSB)
+      for (int I = I0; I < I0 + kSB && I < nI; ++I)
+        for (int Jc = J0; Jc < J0 + kSB && Jc < nJ && Jc * TN <= I * TM + TM - 1; ++Jc)
+          t.push_back(make_int2(I, Jc));
   return t;
 }
 long long oz_mp(int m) { return (long long)((m + TM - 1) / TM) * TM; }

@@ -72,6 +72,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
   __shared__ __align__(8) uint64_t accf_bar[2];   // MMA -> epilogue: chunk ready in buffer b
   __shared__ __align__(8) uint64_t acce_bar[2];   // epilogue -> MMA: buffer b drained
+  __shared__ __align__(8) uint64_t fin_bar;   // teardown: every issued MMA retired
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
@@ -94,6 +95,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       mbar_init(smem_u32(&accf_bar[b]), 1);
       mbar_init(smem_u32(&acce_bar[b]), 8);
     }
+    mbar_init(smem_u32(&fin_bar), 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -212,6 +214,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int s = it % STAGES;
       mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / STAGES) & 1), status, 4);
     }
+  }
+  // on abort, the MMAs already issued must retire before TMEM is freed
+  if (warp == 1 && lane == 0 && *abort_flag) {
+    umma_commit(smem_u32(&fin_bar));
+    mbar_wait(smem_u32(&fin_bar), 0u, status, 6);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -408,8 +415,8 @@ int gram_tc_ntiles(const GramPlan* p) { return p->ntiles; }
 // Some callers cannot allocate device memory at the moment they need the
 // Gram: code running under a framework that owns every device allocation (a
 // caching allocator or a fixed memory pool), code inside a region where an
-// allocation would synchronise the device or invalidate a captured work
-// list, or small embedded users that reserve memory once at start-up.  This
+// allocation would synchronise the device and stall the surrounding work, or
+// small embedded users that reserve memory once at start-up.  This
 // entry point computes the same K = J J^T + shift I as the context's Gram
 // (same tcgen05 kernel, same reduction) but takes its split-K partial tiles,
 // its tile list and its status word from one file-scope device array of fixed
@@ -423,6 +430,7 @@ constexpr size_t kNoAllocBytes = (size_t)16 << 20;       // 16 MiB per device
 constexpr size_t kNoAllocStatusOff = 0;                   // int[4]
 constexpr size_t kNoAllocTilesOff = 256;                  // int2 tile list
 constexpr size_t kNoAllocTilesMax = 512;                  // tiles (m <= 2000 needs 72)
+constexpr int kNoAllocMaxM = 2000;                        // largest m accepted
 constexpr size_t kNoAllocPartOff = 256 + kNoAllocTilesMax * sizeof(int2);
 
 // Every GPU that loads the library holds this array until the process exits.
@@ -451,16 +459,21 @@ extern "C" dngd_status dngd_gram_bf16_noalloc(const void* J, int m, int n, long 
   using namespace dngd;
   if (!J || !K || m < 1 || n < 1 || ld < n || ldk < m) return DNGD_ERR_INVALID_ARG;
   if ((ld * 2) % 16 != 0 || ((uintptr_t)J % 16) != 0) return DNGD_ERR_INVALID_ARG;
+  if (m > kNoAllocMaxM) {
+    fprintf(stderr, "dngd_gram_bf16_noalloc: m = %d is above the maximum m = %d that its static scratch "
+                    "array holds\n", m, kNoAllocMaxM);
+    return DNGD_ERR_INVALID_ARG;
+  }
   const int nI = (m + BM - 1) / BM;
   const long long mp = (long long)nI * BM;
   const long long ldp = ((m + 3) / 4) * 4 + 4;
   const size_t per_split = (size_t)mp * ldp * sizeof(float);
   const size_t cap = kNoAllocBytes - kNoAllocPartOff;
-  if (per_split > cap) {
-    fprintf(stderr, "dngd_gram_bf16_noalloc: m = %d needs %zu bytes of scratch, the static array holds %zu "
-                    "(maximum m is 2000)\n", m, per_split, cap);
-    return DNGD_ERR_INVALID_ARG;
-  }
+  // m <= 2000 needs at most 2048 x 2008 floats (16.4 MB) of one split
+  static_assert((size_t)((kNoAllocMaxM + BM - 1) / BM) * BM * (((kNoAllocMaxM + 3) / 4) * 4 + 4) * sizeof(float) <=
+                    kNoAllocBytes - kNoAllocPartOff,
+                "the static scratch must hold one split of the largest accepted m");
+  if (per_split > cap) return DNGD_ERR_INVALID_ARG;
   int ntiles = 0;
   for (int I = 0; I < nI; ++I)
     for (int Jc = 0; Jc * BN <= I * BM + BM - 1 && Jc * BN < m; ++Jc) ++ntiles;

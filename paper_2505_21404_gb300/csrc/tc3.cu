@@ -102,6 +102,7 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
   __shared__ __align__(8) uint64_t full_bar[ST3];
   __shared__ __align__(8) uint64_t empty_bar[ST3];
   __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t fin_bar;   // teardown: every issued MMA retired
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -113,6 +114,7 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     mbar_init(smem_u32(&acc_bar), 1);
+    mbar_init(smem_u32(&fin_bar), 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -239,6 +241,11 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
       const int st = it % ST3;
       mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((it / ST3) & 1), status, 24);
     }
+  }
+  // on abort, the MMAs already issued must retire before TMEM is freed
+  if (warp == 1 && lane == 0 && *abort_flag) {
+    umma_commit(smem_u32(&fin_bar));
+    mbar_wait(smem_u32(&fin_bar), 0u, status, 25);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();

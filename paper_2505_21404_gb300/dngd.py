@@ -47,7 +47,8 @@ class ProblemDesc(C.Structure):
                 ("lam", C.c_double), ("use_ga", C.c_int), ("eps_norm", C.c_double),
                 ("ga_ratio_max", C.c_double), ("refine_max_it", C.c_int), ("refine_tol", C.c_double),
                 ("shift_mu", C.c_double), ("pcg_rank", C.c_int), ("pcg_tol", C.c_double),
-                ("pcg_max_it", C.c_int), ("pcg_seed", C.c_uint64), ("keep_gram", C.c_int)]
+                ("pcg_max_it", C.c_int), ("pcg_seed", C.c_uint64), ("keep_gram", C.c_int),
+                ("lambda_cap", C.c_double)]
 
 
 class StepInfo(C.Structure):
@@ -55,7 +56,7 @@ class StepInfo(C.Structure):
                 ("ga_accepted", C.c_int), ("solve_iters", C.c_int * 2), ("solve_relres", C.c_double * 2),
                 ("not_spd_column", C.c_int), ("device_status", C.c_int), ("phase_ms", C.c_float * 8),
                 ("shift_used", C.c_double), ("factor_attempts", C.c_int), ("jt_ms", C.c_float),
-                ("j_ms", C.c_float)]
+                ("j_ms", C.c_float), ("lambda_used", C.c_double)]
 
     def as_dict(self):
         return dict(loss=self.loss, norm_v=self.norm_v, norm_a=self.norm_a, ga_ratio=self.ga_ratio,
@@ -63,7 +64,7 @@ class StepInfo(C.Structure):
                     solve_relres=list(self.solve_relres), not_spd_column=self.not_spd_column,
                     device_status=self.device_status, phase_ms=list(self.phase_ms),
                     shift_used=self.shift_used, factor_attempts=self.factor_attempts, jt_ms=self.jt_ms,
-                    j_ms=self.j_ms)
+                    j_ms=self.j_ms, lambda_used=self.lambda_used)
 
 
 class ServerCfg(C.Structure):
@@ -174,8 +175,9 @@ def _ptr(a):
 
 def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_ratio_max=0.5, refine_max_it=200,
               refine_tol=1e-10, shift_mu=0.0, keep_gram=False, solver=DENSE, pcg_rank=512, pcg_tol=1e-6,
-              pcg_max_it=500):
-    """Problem descriptor from a workload dict (see workloads.py)."""
+              pcg_max_it=500, lambda_cap=0.0):
+    """Problem descriptor from a workload dict (see workloads.py).
+    lambda_cap > 0 selects the damping rule lambda_k = min(L(theta_k), cap)."""
     d = ProblemDesc()
     widths = list(spec["widths"])
     d.n_layers = len(widths) - 1
@@ -204,6 +206,7 @@ def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_rati
     d.refine_tol = float(refine_tol)
     d.shift_mu = float(shift_mu)
     d.keep_gram = int(bool(keep_gram))
+    d.lambda_cap = float(lambda_cap)
     return d
 
 

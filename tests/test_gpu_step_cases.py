@@ -1,0 +1,270 @@
+"""GPU parity of the D-NGD step on the cases the basic parity tests leave out.
+
+* The geodesic-acceleration branch taken: delta = v + a/2 (Alg.
+  DenseDualSolve), on inputs where the oracle accepts (2||a||/||v|| <= 0.5),
+  and with the threshold raised so that a case that rejects is accepted.
+* The exact-Gram (MIXED_OZ) step at m = 2,000, n = 33,921 (5-128^3-1 net, 16
+  row tiles and a 1,060-stage K extent) and at the 5-D benchmark size
+  (m = 4,000, n = 133,377): the Gram against the FP64 product of the
+  context's own FP32 Jacobian, entry by entry within the slicing bound, and
+  alpha, v, a, delta against the FP64 oracle.
+* dngd_solve against the oracle's triangular solves with the factor of the
+  same step.
+* An indefinite K + lambda I (FP64, lambda < 0, a residual class whose
+  operator is zero so its Jacobian rows vanish): DNGD_ERR_NOT_SPD at the
+  oracle's failing column.
+* The 2-D benchmark at lambda = 1e-8 entry by entry.
+
+Every call goes through the C ABI on cuda:0.  Errors are normwise, entrywise
+(relative to the entry plus the RMS of the reference) and per block (each
+layer's W and b; each residual class), see tests/_parity.py.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import residual as ores, step as ostep  # noqa: E402
+from paper_2505_21404_gb300 import workloads  # noqa: E402
+
+from _parity import check, class_blocks, layer_blocks, rel  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def dngd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2505_21404_gb300 import dngd as mod
+    return mod
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _stages(ctx, names):
+    out = {}
+    for name in names:
+        size = ctx.n if name in ("v", "a") else ctx.m
+        buf = torch.zeros(size, dtype=torch.float64, device=DEV)
+        ctx.get_stage(name, buf)
+        out[name] = buf
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+# (workload, GA threshold): the oracle accepts the GA correction on each
+GA_CASES = {
+    # heat, lambda = 0.1: ratio 0.35
+    "heat_lam0.1": (lambda: workloads.heat_1d([2, 24, 24, 1], 40, 12, 12, kappa=0.1, seed=0, lam=0.1), 0.5),
+    # 2-D Poisson, lambda = 10: ratio 0.14
+    "poisson2d_lam10": (lambda: workloads.poisson_sine(2, [2, 20, 20, 1], 70, 26, k=2, seed=3, lam=10.0), 0.5),
+    # 5-D Poisson, lambda = 1e-5: ratio ~300, accepted with the threshold raised
+    "poisson5d_forced": (lambda: workloads.poisson_sine(5, [5, 33, 17, 9, 1], 61, 19, k=1, seed=4, lam=1e-5),
+                         1e9),
+}
+
+
+@pytest.mark.parametrize("prec,tol", [("FP64", 1e-10), ("MIXED_OZ", 1e-4), ("MIXED_BF16", 1e-4)])
+@pytest.mark.parametrize("case", list(GA_CASES))
+def test_ga_accepted_step(dngd, case, prec, tol):
+    make, ratio_max = GA_CASES[case]
+    wl = make()
+    prob = ores.problem_from_spec(wl)
+    ref = ostep.dense_step(wl["theta"], prob, wl["X"], wl["target"], wl["lam"], use_ga=True, ratio_max=ratio_max)
+    assert ref["accepted"], ref["ratio"]
+    ctx = dngd.Context(dngd.make_desc(wl, precision=getattr(dngd, prec), ga_ratio_max=ratio_max, refine_tol=1e-12,
+                                      refine_max_it=300))
+    delta = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
+    info = ctx.step(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), delta)
+    st = _stages(ctx, ["v", "a", "alpha", "beta"])
+    d = delta.cpu().numpy()
+    assert info["ga_accepted"], info
+    assert abs(info["ga_ratio"] - ref["ratio"]) <= 1e-3 * ref["ratio"] + (1e-8 if prec == "FP64" else 1e-4)
+    # the accepted step is exactly v + a/2 of the step's own v and a
+    assert np.array_equal(d, st["v"] + 0.5 * st["a"])
+    lb = layer_blocks(wl["widths"])
+    cb = class_blocks(wl["classes"])
+    check("delta", d, ref["delta"], tol, lb)
+    check("v", st["v"], ref["v"], tol, lb)
+
+    check("a", st["a"], ref["a"], tol, lb)
+    check("alpha", st["alpha"], ref["alpha"], tol, cb)
+    ctx.close()
+
+
+def _oz_gram_bound(J):
+    """Entry bound of the exact Gram of an FP32 matrix J (rows scaled by 2^E_i,
+    E_i = exponent of the row's largest |J| plus one, four 8-bit slices):
+    each entry of J is kept to 2^(E_i - 33), so
+      |K_ij - (J J^T)_ij| <= 2^-33 (||J_i||_1 2^E_j + ||J_j||_1 2^E_i)
+                              + n 2^(E_i + E_j) 2^-38
+    (the last term covers the dropped slice products s + t >= 5, 2^-40, and
+    the rounded trailing levels, 2^-39)."""
+    amax = np.abs(J).max(axis=1)
+    E = np.where(amax > 0, np.frexp(amax)[1] + 1, 0).astype(np.float64)
+    s = 2.0 ** E
+    l1 = np.abs(J).sum(axis=1)
+    n = J.shape[1]
+    return 2.0 ** -33 * (np.outer(l1, s) + np.outer(s, l1)) + n * 2.0 ** -38 * np.outer(s, s)
+
+
+def _oz_case(dngd, wl, sample=None, seed=0):
+    prob = ores.problem_from_spec(wl)
+    ref = ostep.dense_step(wl["theta"], prob, wl["X"], wl["target"], wl["lam"], use_ga=True)
+    ctx = dngd.Context(dngd.make_desc(wl, precision=dngd.MIXED_OZ, refine_tol=1e-10, refine_max_it=400))
+    delta = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
+    info = ctx.step(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), delta)
+    st = _stages(ctx, ["v", "a", "alpha", "beta"])
+    m, n = ctx.m, ctx.n
+    K = torch.zeros(m, m, dtype=torch.float64, device=DEV)
+    ctx.get_stage("gram64", K)
+    J32 = torch.zeros(m, n, dtype=torch.float64, device=DEV)
+    ctx.residual_jacobian(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]),
+                          torch.zeros(m, dtype=torch.float64, device=DEV), J32)
+    torch.cuda.synchronize()
+    Kh = K.cpu().numpy()
+    assert np.array_equal(Kh, Kh.T)
+    if sample is None:
+        J = J32.cpu().numpy()
+        Kx = J @ J.T
+        assert rel(Kh, Kx) <= 2.0 ** -33
+        B = _oz_gram_bound(J)
+        assert np.all(np.abs(Kh - Kx) <= B), float(np.max(np.abs(Kh - Kx) / B))
+        assert rel(J, ref["J"]) <= 1e-5
+    else:
+        # sampled rows: the exact Gram's rows against FP64 products of the
+        # context's FP32 rows with the whole FP32 Jacobian
+        rows = np.sort(np.random.default_rng(seed).choice(m, size=sample, replace=False))
+        Jr = J32[rows].cpu().numpy()
+        Kx = (J32[rows] @ J32.T).cpu().numpy()
+        Jall = J32.cpu().numpy()
+        B = _oz_gram_bound(Jall)[rows]
+        assert np.all(np.abs(Kh[rows] - Kx) <= B), float(np.max(np.abs(Kh[rows] - Kx) / B))
+        assert rel(Kh[rows], Kx) <= 2.0 ** -33
+        assert rel(Jr, ref["J"][rows]) <= 1e-5
+        del Jall
+    assert max(info["solve_relres"]) <= 1e-10, info
+    lb = layer_blocks(wl["widths"])
+    cb = class_blocks(wl["classes"])
+    check("delta", delta, ref["delta"], 1e-4, lb)
+    check("v", st["v"], ref["v"], 1e-4, lb)
+    check("alpha", st["alpha"], ref["alpha"], 1e-4, cb)
+    check("a", st["a"], ref["a"], 1e-4, lb)
+    assert info["ga_accepted"] == ref["accepted"]
+    ctx.close()
+    return info
+
+
+def test_dense_step_oz_m2000(dngd):
+    """5-D Poisson, MLP 5-128-128-128-1 (n = 33,921), 1,500 + 500 points."""
+    wl = workloads.poisson_sine(5, [5, 128, 128, 128, 1], 1500, 500, k=1, seed=8, lam=1e-5)
+    _oz_case(dngd, wl)
+
+
+def test_dense_step_oz_benchmark_size(dngd):
+    """The 5-D benchmark workload itself (m = 4,000, n = 133,377, lambda =
+    1e-5, theta_0), in the launch configuration the benchmark times: Gram rows
+    sampled, every stage against a full oracle step."""
+    wl = workloads.poisson5d_dense(seed=0, lam=1e-5)
+    _oz_case(dngd, wl, sample=48, seed=1)
+
+
+@pytest.mark.parametrize("prec,tol", [("FP64", 1e-10), ("MIXED_OZ", 1e-6), ("MIXED_BF16", 1e-6)])
+def test_dngd_solve_matches_triangular_solves(dngd, prec, tol):
+    """dngd_solve reuses the last step's factor (FP64) or preconditioned
+    refinement (mixed) for a new right-hand side: against the oracle's two
+    triangular solves with the Cholesky factor of the same K + lambda I (for
+    the mixed paths, the Gram of the context's own FP32 Jacobian)."""
+    wl = workloads.poisson_sine(2, [2, 20, 20, 1], 70, 26, k=2, seed=3, lam=1e-3)
+    ctx = dngd.Context(dngd.make_desc(wl, precision=getattr(dngd, prec), refine_tol=1e-13, refine_max_it=400))
+    m, n = ctx.m, ctx.n
+    delta = torch.zeros(n, dtype=torch.float64, device=DEV)
+    with pytest.raises(dngd.DngdError) as e:
+        ctx.solve(_t(np.ones(m)), torch.zeros(m, dtype=torch.float64, device=DEV))
+    assert e.value.status == -8   # DNGD_ERR_STATE before any step
+    ctx.step(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), delta)
+    rng = np.random.default_rng(3)
+    bs = [rng.normal(size=m) for _ in range(2)]
+    xs = []
+    for b in bs:
+        x = torch.zeros(m, dtype=torch.float64, device=DEV)
+        ctx.solve(_t(b), x)
+        xs.append(x)
+    # the step's own Jacobian (FP32 on the mixed paths), read after the solves
+    # (a new Jacobian evaluation ends the step's state)
+    J = torch.zeros(m, n, dtype=torch.float64, device=DEV)
+    ctx.residual_jacobian(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]),
+                          torch.zeros(m, dtype=torch.float64, device=DEV), J)
+    torch.cuda.synchronize()
+    L = ostep.cholesky(ostep.gram(J.cpu().numpy(), wl["lam"]))
+    for k, (b, x) in enumerate(zip(bs, xs)):
+        check(f"x{k}", x, ostep.chol_solve(L, b), tol, class_blocks(wl["classes"]))
+    ctx.close()
+
+
+def test_not_spd_reports_oracle_column(dngd):
+    """FP64, lambda = -1e-12, classes: six boundary value points, then three
+    points whose operator is zero (their Jacobian rows are zero, so their
+    pivots are lambda < 0).  The oracle's Cholesky fails at column 6; the
+    step must return DNGD_ERR_NOT_SPD with the same column."""
+    wl = workloads.poisson_sine(2, [2, 8, 8, 1], 3, 6, k=1, seed=11, lam=-1e-12)
+    wl["classes"] = [dict(count=6, c_val=1.0, c_grad=[0.0, 0.0], c_lap=0.0, lap_mask=[0, 0]),
+                     dict(count=3, c_val=0.0, c_grad=[0.0, 0.0], c_lap=0.0, lap_mask=[0, 0])]
+    wl["X"] = np.ascontiguousarray(np.concatenate([wl["X"][3:], wl["X"][:3]]))
+    prob = ores.problem_from_spec(wl)
+    r, J = ores.residual_and_jacobian(wl["theta"], prob, wl["X"], wl["target"])
+    with pytest.raises(ostep.NotSPD) as e:
+        ostep.cholesky(ostep.gram(J, wl["lam"]))
+    col = e.value.column
+    assert col == 6
+    # a mixed-precision context refuses lambda <= 0
+    with pytest.raises(dngd.DngdError):
+        dngd.Context(dngd.make_desc(wl, precision=dngd.MIXED_OZ))
+    ctx = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64))
+    # the context's Jacobian is the oracle's (the zero-operator rows included)
+    Jg = torch.zeros(ctx.m, ctx.n, dtype=torch.float64, device=DEV)
+    rg = torch.zeros(ctx.m, dtype=torch.float64, device=DEV)
+    ctx.residual_jacobian(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), rg, Jg)
+    torch.cuda.synchronize()
+    assert rel(Jg, J) <= 1e-12 and not np.any(Jg.cpu().numpy()[6:]), (Jg.cpu().numpy(), J)
+    assert rel(rg, r) <= 1e-12
+    info = dngd.StepInfo()
+    d = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
+    s = dngd.lib.dngd_step(ctx._h, dngd._ptr(_t(wl["theta"])), dngd._ptr(_t(wl["X"])), dngd._ptr(_t(wl["target"])),
+                           dngd._ptr(d), dngd.C.byref(info))
+    assert dngd.STATUS[s] == "DNGD_ERR_NOT_SPD"
+    assert info.not_spd_column == col
+    # the same context steps normally once lambda is positive again
+    ctx.set_lambda(1e-3)
+    ref = ostep.dense_step(wl["theta"], prob, wl["X"], wl["target"], 1e-3, use_ga=True)
+    ctx.step(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), d)
+    torch.cuda.synchronize()
+    check("delta", d, ref["delta"], 1e-10)
+    ctx.close()
+
+
+def test_poisson2d_benchmark_entrywise(dngd):
+    """The 2-D benchmark (m = 500, n = 1,185, lambda = 1e-8, FP64) entry by
+    entry and per block.  The bound 1e-7 on v and delta is ~50x the oracle's
+    own FP64 rounding spread at this lambda (about 2e-9 on v against an
+    extended-precision solve of the same J; test_oracle_step.py pins it)."""
+    wl = workloads.poisson2d_fp64()
+    prob = ores.problem_from_spec(wl)
+    ref = ostep.dense_step(wl["theta"], prob, wl["X"], wl["target"], wl["lam"], use_ga=True)
+    ctx = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64))
+    delta = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
+    info = ctx.step(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), delta)
+    st = _stages(ctx, ["v", "a", "alpha"])
+    lb = layer_blocks(wl["widths"])
+    check("delta", delta, ref["delta"], 1e-7, lb)
+    check("v", st["v"], ref["v"], 1e-7, lb)
+    check("alpha", st["alpha"], ref["alpha"], 1e-6, class_blocks(wl["classes"]))
+    check("a", st["a"], ref["a"], 1e-6, lb)
+    assert info["ga_accepted"] == ref["accepted"]
+    ctx.close()

@@ -1,5 +1,6 @@
 """The allocation-free Gram entry point (dngd_gram_bf16_noalloc) against the
-Gram that a mixed-precision step computes through the regular context.
+Gram that a mixed-precision step computes through the regular context, and
+against the FP64 product of the same BF16 operand computed on the host.
 
 The no-alloc call exists for callers that cannot allocate device memory when
 they need the Gram (their framework owns all device memory, or an allocation
@@ -51,6 +52,9 @@ def test_gram_noalloc_matches_context_gram_twice(dngd):
     K = torch.empty(m, m, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream().cuda_stream
     Kd = K_ref.cpu().numpy()
+    # the FP64 product of the BF16 operand, on the host
+    Jh = Jb[:, :n].double().cpu().numpy()
+    K64 = np.tril(Jh @ Jh.T + shift * np.eye(m))
     for call in range(2):
         K.fill_(float("nan"))
         st = dngd.dngd_gram_bf16_noalloc(Jb, m, n, ld, K, m, shift, stream)
@@ -61,13 +65,31 @@ def test_gram_noalloc_matches_context_gram_twice(dngd):
         assert np.allclose(np.triu(Kh, 1), 0.0), call
         err = np.linalg.norm(Kh - Kd) / np.linalg.norm(Kd)
         assert err <= 1e-5, (call, err)
+        err64 = np.linalg.norm(Kh - K64) / np.linalg.norm(K64)
+        assert err64 <= 1e-5, (call, err64)
     ctx.close()
 
 
-def test_gram_noalloc_rejects_sizes_beyond_its_scratch(dngd):
+def test_gram_noalloc_largest_size_and_one_beyond(dngd):
+    """m = 2000 (the stated maximum) is accepted and agrees with the host FP64
+    product of its BF16 operand on two calls in a row; m = 2001 is rejected."""
     dev = "cuda:0"
-    m, n = 2500, 64
-    Jb = torch.zeros(m, n, dtype=torch.bfloat16, device=dev)
-    K = torch.zeros(1, dtype=torch.float32, device=dev)
-    st = dngd.dngd_gram_bf16_noalloc(Jb, m, n, n, K, m, 0.0, None)
+    m, n = 2000, 1000
+    g = torch.Generator(device="cpu").manual_seed(5)
+    Jb = (torch.randn(m, n, generator=g, dtype=torch.float64) / 32.0).to(torch.bfloat16).to(dev)
+    Jh = Jb.double().cpu().numpy()
+    K64 = np.tril(Jh @ Jh.T + 0.25 * np.eye(m))
+    K = torch.empty(m, m, dtype=torch.float32, device=dev)
+    for call in range(2):
+        K.fill_(float("nan"))
+        st = dngd.dngd_gram_bf16_noalloc(Jb, m, n, n, K, m, 0.25, None)
+        assert st == 0, dngd.STATUS.get(st, st)
+        torch.cuda.synchronize()
+        Kh = K.double().cpu().numpy()
+        assert np.all(np.isfinite(Kh)), call
+        err = np.linalg.norm(Kh - K64) / np.linalg.norm(K64)
+        assert err <= 1e-5, (call, err)
+    Jb1 = torch.zeros(m + 1, n, dtype=torch.bfloat16, device=dev)
+    K1 = torch.zeros(1, dtype=torch.float32, device=dev)
+    st = dngd.dngd_gram_bf16_noalloc(Jb1, m + 1, n, n, K1, m + 1, 0.0, None)
     assert dngd.STATUS[st] == "DNGD_ERR_INVALID_ARG"
