@@ -32,9 +32,12 @@ sys.path.insert(0, ROOT)
 METRIC = "D-NGD steps/s mixed vs FP64 at equal step error; Gram TFLOP/s; p99 step latency"
 UNIT = "steps/s"
 DTYPES = {"oz": "bf16 tensor (exact integer slices) / f32 jets and factor / f64 Gram operator",
+          "oz64": "f64 jets and Jacobian / bf16 tensor (exact integer slices, 5 per entry) / f32 factor / "
+                  "f64 Gram operator",
           "bf16": "bf16/f32 (double-float accumulation in the refinement)",
           "tf32": "tf32/f32 (double-float accumulation in the refinement)"}
 L2_NOTE = {"oz": "working set larger than L2 (J: 2.13 GB FP32, slices 4.27 GB BF16, Gram 128 MB FP64 per step)",
+           "oz64": "working set larger than L2 (J: 4.27 GB FP64, slices 5.3 GB BF16, Gram 128 MB FP64 per step)",
            "bf16": "working set larger than L2 (J: 2.13 GB FP32 + 1.07 GB BF16 per step)",
            "tf32": "working set larger than L2 (J: 2.13 GB FP32 per step)"}
 WORKLOAD = "poisson5d_dense: -Lap u = f on [0,1]^5, MLP 5-256-256-256-1 (n=133377), 3000+1000 pts (m=4000)"
@@ -578,7 +581,7 @@ def main():
     ap.add_argument("--save-theta", default=None, help="write the parameters after the timed steps (.npy)")
     ap.add_argument("--gram-traffic", type=float, default=None,
                     help="DRAM bytes of one exact-Gram launch on the 5-D workload (from an ncu capture)")
-    ap.add_argument("--precision", default="oz", choices=["oz", "bf16", "tf32"],
+    ap.add_argument("--precision", default="oz", choices=["oz", "oz64", "bf16", "tf32"],
                     help="oz (default): exact Gram from 8-bit slices on BF16 tensor cores, FP32 factor, FP64 Gram "
                          "operator in the refinement; bf16 / tf32: low-precision Gram, FP32-J operator")
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -681,7 +684,8 @@ def run_dense(args, wl, rank, world, local_rank):
                          "); line search not included",
                "blas_threads": _threads()}
 
-    prec = {"bf16": dngd.MIXED_BF16, "tf32": dngd.MIXED_TF32, "oz": dngd.MIXED_OZ}[args.precision]
+    prec = {"bf16": dngd.MIXED_BF16, "tf32": dngd.MIXED_TF32, "oz": dngd.MIXED_OZ,
+            "oz64": dngd.MIXED_OZ64}[args.precision]
     m, n = int(wl["X"].shape[0]), dngd.dngd_num_params(dngd.make_desc(wl))
     th0 = torch.tensor(wl["theta"], device=dev)
     X = torch.tensor(wl["X"], device=dev)
@@ -845,7 +849,7 @@ def run_dense(args, wl, rank, world, local_rank):
 
     hbm, bf16_burst, bf16_sust, src = _peaks()
     alg_flops = float(m) * (m + 1) * n
-    exec_flops = alg_flops * (13 if prec == dngd.MIXED_OZ else 1)
+    exec_flops = alg_flops * {dngd.MIXED_OZ: 13, dngd.MIXED_OZ64: 19}.get(prec, 1)
     achieved = alg_flops / (gram_ms * 1e-3) / 1e12
     executed = exec_flops / (gram_ms * 1e-3) / 1e12
     peak = bf16_sust / 2.0 if prec == dngd.MIXED_TF32 else bf16_sust
@@ -862,13 +866,13 @@ def run_dense(args, wl, rank, world, local_rank):
                  "bytes_per_launch": gemv_bytes, "launch_ms": [jt_ms, j_ms],
                  "launches_per_step": 2 * iters_total + 2,
                  "peak_source": f"{src} HBM copy bandwidth", "traffic": None}
-    if prec == dngd.MIXED_OZ:
+    if prec in (dngd.MIXED_OZ, dngd.MIXED_OZ64):
         # the two refinement solves (persistent PCG: per iteration the double-float
         # Gram, 8 m^2 B, and both triangles of the FP32 inverse factor, 2 x 2 m^2 B)
         # plus each solve's map-back J^T x over the FP32 J (4 m n B), against the
         # solve phases' CUDA-event time
         solve_ms = float(np.mean([i["phase_ms"][3] + i["phase_ms"][5] for i in infos]))
-        solve_bytes = iters_total * 12.0 * m * m + 2 * gemv_bytes
+        solve_bytes = iters_total * 12.0 * m * m + 2 * gemv_bytes * (2 if prec == dngd.MIXED_OZ64 else 1)
         solve_gbs = solve_bytes / (solve_ms * 1e-3) / 1e9 if solve_ms > 0 else 0.0
         roof_gemv = {"bound": "hbm", "kernel": "k_pcg_persist (both solves) + k_gemv_t_f32 (map-back J^T x)",
                      "achieved": solve_gbs, "peak": hbm, "unit": "GB/s", "frac": solve_gbs / hbm,
@@ -882,7 +886,9 @@ def run_dense(args, wl, rank, world, local_rank):
                      "algorithmic": "m(m+1)n flop per Gram (the syrk of the 5-D workload, 2.135e12)",
                      "flops_per_launch": alg_flops, "launch_ms": gram_ms,
                      "executed_tflops": executed, "executed_frac": executed / peak,
-                     "executed": "13 m(m+1)n BF16 tensor flop (the 13 slice products the exact Gram runs)",
+                     "executed": ("19 m(m+1)n BF16 tensor flop (the 19 products of five slices)"
+                                  if prec == dngd.MIXED_OZ64 else
+                                  "13 m(m+1)n BF16 tensor flop (the 13 products of four slices)"),
                      "peak_source": f"{src} bf16 sustained",
                      "traffic": args.gram_traffic if args.workload == "poisson5d" else None,
                      "traffic_source": "profiles/k_gram_oz_poisson5d.md (ncu, one launch of the 5-D workload)"}
@@ -910,8 +916,8 @@ def run_dense(args, wl, rank, world, local_rank):
         "per_step": [{"iters": i["solve_iters"], "shift": i["shift_used"], "factor_attempts": i["factor_attempts"],
                       "loss": i["loss"], "lam": i["lambda_used"], "ms": float(l)} for i, l in zip(infos, lat)],
         "ga_accepted_at_theta0": info0["ga_accepted"],
-        "roofline": roof_gram if prec == dngd.MIXED_OZ else roof_gemv,
-        "roofline_other": roof_gemv if prec == dngd.MIXED_OZ else roof_gram,
+        "roofline": roof_gram if prec in (dngd.MIXED_OZ, dngd.MIXED_OZ64) else roof_gemv,
+        "roofline_other": roof_gemv if prec in (dngd.MIXED_OZ, dngd.MIXED_OZ64) else roof_gram,
         "cpu_baseline": cpu,
         "e2e": {"value": 1000.0 / e2e_ms * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,

@@ -71,7 +71,7 @@ enum dngd_precision {
                            inverse as the preconditioner of PCG refinement on
                            the FP32-J operator with double-float accumulation */
   DNGD_MIXED_TF32 = 2,  /* as MIXED_BF16 with a TF32 tensor-core Gram */
-  DNGD_MIXED_OZ = 3     /* FP32 jets/J; exact Gram of the FP32 J from four
+  DNGD_MIXED_OZ = 3,    /* FP32 jets/J; exact Gram of the FP32 J from four
                            8-bit integer slices per row on the BF16 tensor
                            cores (13 slice products; the three leading levels
                            in exact FP32 chunks, the two trailing ones rounded
@@ -81,6 +81,16 @@ enum dngd_precision {
                            MIXED_BF16) preconditions PCG whose operator is the
                            exact FP64 Gram (one m x m GEMV per iteration
                            instead of two over J) */
+  DNGD_MIXED_OZ64 = 4   /* as MIXED_OZ for an FP64 Jacobian: FP64 jets,
+                           residuals, J, f_vv and map-back J^T x; the exact
+                           Gram from the same four 8-bit slices per entry
+                           with the products of levels g = s + t <= 5 (15 of
+                           16; the dropped level is what limits an accurate
+                           J's Gram, not the slicing); K accurate to ~2^-33
+                           of the row scales, the Gram of J rounded to 32
+                           bits below each row's largest entry; FP32
+                           preconditioning factor and PCG on the exact Gram
+                           as MIXED_OZ; line-search trial losses in FP32 */
 };
 
 enum dngd_solver {

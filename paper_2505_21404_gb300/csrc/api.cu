@@ -161,6 +161,12 @@ dngd_status dalloc(dngd_ctx* c, T** p, size_t count) {
 
 long long round_up(long long a, long long b) { return ((a + b - 1) / b) * b; }
 
+// FP64 jets, residuals and Jacobian (the FP64 path and the exact-Gram mode
+// of an FP64 Jacobian)
+bool jets64(int prec) { return prec == DNGD_FP64 || prec == DNGD_MIXED_OZ64; }
+// exact Gram from integer slices on the tensor cores
+bool oz_mode(int prec) { return prec == DNGD_MIXED_OZ || prec == DNGD_MIXED_OZ64; }
+
 // lambda > 0 everywhere; an FP64 context also takes a finite lambda <= 0
 // (K + lambda I may then be indefinite, which its Cholesky reports)
 bool lambda_ok(int prec, double lambda) {
@@ -358,7 +364,7 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
   P.ev = (c->timing && slot == 0) ? c->kev : nullptr;
   const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
   const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
-  if (c->prec == DNGD_MIXED_OZ) {
+  if (oz_mode(c->prec)) {
     // the exact FP64 Gram is the operator: one m x m GEMV per iteration; the
     // synchronous solve is one persistent cooperative kernel
     P.K64 = c->K64;
@@ -869,14 +875,17 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   const int m = net.m;
   const long long n = net.n;
   const int L = net.n_layers - 1;
-  const bool f64 = c->prec == DNGD_FP64;
-  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  const bool f64 = c->prec == DNGD_FP64;          // FP64 Gram, factor and solves
+  const bool j64 = jets64(c->prec);                // FP64 jets and Jacobian
+  const size_t es = j64 ? sizeof(double) : sizeof(float);     // jets / J elements
+  const size_t ek = f64 ? sizeof(double) : sizeof(float);     // K elements
   size_t tot = 0;
   auto add = [&](size_t b) { tot += (b + 255) & ~(size_t)255; };
   c->ldJ = f64 ? n : round_up(n, 64);
   c->ldb = round_up(n, 64);
   c->ldk = round_up(m, 4);
-  const bool oz = c->prec == DNGD_MIXED_OZ;
+  const bool oz = oz_mode(c->prec);
+  const int ng = c->prec == DNGD_MIXED_OZ64 ? 6 : 5;   // exact-Gram levels kept
   const bool bf = c->prec == DNGD_MIXED_BF16;
   add(sizeof(double) * n);        // theta_s
   add(sizeof(double) * m * net.d_in);
@@ -901,11 +910,11 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   add(3 * rowbuf);        // H3b
   add(es * (size_t)m * c->ldJ);
   if (bf) add(sizeof(__nv_bfloat16) * (size_t)m * c->ldb);
-  add(es * (size_t)m * c->ldk);
-  if (c->desc.keep_gram) add(es * (size_t)m * c->ldk);
+  add(ek * (size_t)m * c->ldk);
+  if (c->desc.keep_gram) add(ek * (size_t)m * c->ldk);
   if (f64) add(sizeof(double) * ((size_t)cdiv(m, 64) * 64 * 64 + 2 * (size_t)m));   // Dinv, tw
   if (!f64) {
-    add(es * (size_t)m * c->ldk);                 // K0
+    add(ek * (size_t)m * c->ldk);                 // K0
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
     add(sizeof(float) * (size_t)m * m);           // trtri work
     add(tc3_bytes(c));                            // TF32 tensor-core GEMM splits
@@ -918,7 +927,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       add(256);                                   // persistent-PCG barrier state
       add(sizeof(double) * 7 * (size_t)m);        // persistent-PCG vectors
       add(gram_oz_slice_bytes(m, (int)n));
-      add(gram_oz_partial_bytes(m, (int)n));
+      add(gram_oz_partial_bytes(m, (int)n, ng));
     } else {
       add(gram_tc_partial_bytes(m, (int)n));
     }
@@ -946,7 +955,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   }
   for (int l = 0; l < L; ++l) {
     const size_t cnt = (size_t)net.R * net.widths[l + 1];
-    if (f64) {
+    if (j64) {
       A_(c->Z[l], double, cnt);
       A_(c->H[l], double, cnt);
       A_(c->D[l], double, cnt);
@@ -957,16 +966,14 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     }
   }
   const size_t rb = (size_t)net.R * net.max_w;
-  if (f64) {
+  if (j64) {
     A_(c->Hbar, double, rb);
     A_(c->Z3, double, 3 * rb);
     A_(c->H3a, double, 3 * rb);
     A_(c->H3b, double, 3 * rb);
     A_(c->J, double, (size_t)m * c->ldJ);
-    A_(c->K, double, (size_t)m * c->ldk);
-    if (c->desc.keep_gram) A_(c->Kcopy, double, (size_t)m * c->ldk);
-    A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
-    A_(c->tw, double, 2 * (size_t)m);
+    // the exact-Gram slicing reads whole padded rows: the pad stays zero
+    if (!f64) DNGD_CUDA_CHECK(cudaMemset(c->J, 0, sizeof(double) * (size_t)m * c->ldJ));
   } else {
     A_(c->Hbar, float, rb);
     A_(c->Z3, float, 3 * rb);
@@ -974,6 +981,13 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->H3b, float, 3 * rb);
     A_(c->J, float, (size_t)m * c->ldJ);
     DNGD_CUDA_CHECK(cudaMemset(c->J, 0, sizeof(float) * (size_t)m * c->ldJ));
+  }
+  if (f64) {
+    A_(c->K, double, (size_t)m * c->ldk);
+    if (c->desc.keep_gram) A_(c->Kcopy, double, (size_t)m * c->ldk);
+    A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
+    A_(c->tw, double, 2 * (size_t)m);
+  } else {
     if (bf) {
       A_(c->Jb, __nv_bfloat16, (size_t)m * c->ldb);
       DNGD_CUDA_CHECK(cudaMemset(c->Jb, 0, sizeof(__nv_bfloat16) * (size_t)m * c->ldb));
@@ -996,7 +1010,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       A_(c->pstate, unsigned char, 256);
       A_(c->pwork, double, 7 * (size_t)m);
       A_(c->oz_slices, unsigned char, gram_oz_slice_bytes(m, (int)n));
-      c->gram_partial_bytes = gram_oz_partial_bytes(m, (int)n);
+      c->gram_partial_bytes = gram_oz_partial_bytes(m, (int)n, ng);
       A_(c->oz_partials, double, c->gram_partial_bytes / sizeof(double));
     } else {
       c->gram_partial_bytes = gram_tc_partial_bytes(m, (int)n);
@@ -1029,8 +1043,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   DNGD_CUDA_CHECK(cudaMallocHost(&c->scal_h, sizeof(double) * S_COUNT));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->status_h, sizeof(int) * 4));
   if (oz) {
-    s = gram_oz_plan(&c->oz, (const float*)c->J, c->ldJ, m, (int)n, c->oz_slices, (float*)c->K, c->ldk, c->K64,
-                     c->ldk, c->oz_partials, c->gram_partial_bytes);
+    s = gram_oz_plan(&c->oz, c->J, j64, ng, c->ldJ, m, (int)n, c->oz_slices, (float*)c->K, c->ldk, c->K64, c->ldk,
+                     c->oz_partials, c->gram_partial_bytes);
     if (s) return s;
   } else if (!f64) {
     const void* Jlow = bf ? (const void*)c->Jb : (const void*)c->J;
@@ -1120,9 +1134,9 @@ dngd_status dngd_workspace_bytes(const dngd_problem_desc* desc, size_t* bytes) {
 dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* stream) {
   if (!out || !desc) return DNGD_ERR_INVALID_ARG;
   *out = nullptr;
-  if (desc->precision < DNGD_FP64 || desc->precision > DNGD_MIXED_OZ) return DNGD_ERR_INVALID_ARG;
+  if (desc->precision < DNGD_FP64 || desc->precision > DNGD_MIXED_OZ64) return DNGD_ERR_INVALID_ARG;
   if (desc->solver != DNGD_DENSE && desc->solver != DNGD_PCG) return DNGD_ERR_INVALID_ARG;
-  if (desc->solver == DNGD_PCG && desc->precision == DNGD_FP64) return DNGD_ERR_INVALID_ARG;
+  if (desc->solver == DNGD_PCG && jets64(desc->precision)) return DNGD_ERR_INVALID_ARG;
   if (!lambda_ok(desc->precision, desc->lambda) || !(desc->lambda_cap >= 0.0) || !isfinite(desc->lambda_cap))
     return DNGD_ERR_INVALID_ARG;
   gemv_init();
@@ -1175,7 +1189,7 @@ dngd_status dngd_step(dngd_ctx* c, const double* theta, const double* X, const d
   const double* tg = in_ptr(c, target, c->target_s, c->m);
   c->have_step = false;
   dngd_status s = c->pcg ? step_pcg(c, th, x, tg)
-                         : (c->prec == DNGD_FP64 ? step_T<double>(c, th, x, tg, info) : step_T<float>(c, th, x, tg, info));
+                         : (jets64(c->prec) ? step_T<double>(c, th, x, tg, info) : step_T<float>(c, th, x, tg, info));
   if (s) {
     dngd_status ds = read_status(c);
     if (info) fill_info(c, info);
@@ -1211,7 +1225,7 @@ dngd_status dngd_residual_jacobian(dngd_ctx* c, const double* theta, const doubl
     if ((s = out_copy(c, r_out, c->r, c->m))) return s;
     return read_status(c);
   }
-  if (c->prec == DNGD_FP64) s = residual_jacobian_T<double>(c, theta_in_T<double>(c, th), x, tg);
+  if (jets64(c->prec)) s = residual_jacobian_T<double>(c, theta_in_T<double>(c, th), x, tg);
   else s = residual_jacobian_T<float>(c, theta_in_T<float>(c, th), x, tg);
   if (s) return s;
   c->have_step = false;
@@ -1225,7 +1239,7 @@ dngd_status dngd_residual_jacobian(dngd_ctx* c, const double* theta, const doubl
       if (cudaMalloc(&dbuf, sizeof(double) * (size_t)c->m * c->n) != cudaSuccess) return DNGD_ERR_OOM;
       dst = dbuf;
     }
-    if (c->prec == DNGD_FP64) s = rows_to_f64<double>(c->m, c->n, (const double*)c->J, c->ldJ, dst, c->st);
+    if (jets64(c->prec)) s = rows_to_f64<double>(c->m, c->n, (const double*)c->J, c->ldJ, dst, c->st);
     else s = rows_to_f64<float>(c->m, c->n, (const float*)c->J, c->ldJ, dst, c->st);
     if (!s && !dev) {
       cudaMemcpyAsync(J_out, dbuf, sizeof(double) * (size_t)c->m * c->n, cudaMemcpyDeviceToHost, c->st);
@@ -1245,7 +1259,7 @@ dngd_status dngd_fvv(dngd_ctx* c, const double* theta, const double* X, const do
   const double* x = in_ptr(c, X, c->X_s, (size_t)c->m * c->net.d_in);
   const double* vv = in_ptr(c, v, c->nvec_s, c->n);
   dngd_status s;
-  if (c->prec == DNGD_FP64) {
+  if (jets64(c->prec)) {
     s = jets_fvv<double>(c->net, th, vv, x, (double*)c->Z3, (double*)c->H3a, (double*)c->H3b, c->fvv, c->st);
   } else {
     const float* t32 = theta_in_T<float>(c, th);
@@ -1480,7 +1494,7 @@ dngd_status enqueue_async(dngd_ctx* c) {
   c->async = true;
   const bool timing = c->timing;
   c->timing = false;
-  dngd_status s = c->prec == DNGD_FP64 ? step_T<double>(c, c->theta_s, c->X_s, c->target_s, nullptr)
+  dngd_status s = jets64(c->prec) ? step_T<double>(c, c->theta_s, c->X_s, c->target_s, nullptr)
                                        : step_T<float>(c, c->theta_s, c->X_s, c->target_s, nullptr);
   c->timing = timing;
   c->async = false;

@@ -63,41 +63,82 @@ namespace {
 using namespace tc;
 
 constexpr int NS = 4;                       // slices per value
-constexpr int NG = 5;                       // levels g = s + t <= 4
-constexpr int TM = 128, TN = 96;            // output tile rows x columns
-constexpr int OST = 4;                      // pipeline stages
+
+// Level configurations: the products sigma_s sigma_t^T are summed by level
+// g = s + t, each level in its own TMEM accumulator of TN columns
+// (NG x TN <= 512).  NG = 5 keeps the levels g <= 4 (13 of the 16 products;
+// the FP32 Jacobian, whose own rounding is far larger than the dropped
+// terms), NG = 6 also level 5 (15 products; the FP64 Jacobian).  The dropped
+// levels are not unbiased noise (on the diagonal they are a sum of squares),
+// so for an accurate J the truncation is what limits the Gram, not the
+// slicing: level 5 brings the step error at a trained theta from 1.5e-4 to
+// 6e-6 (CPU emulation), as close as a fifth slice would.
+template <int NG>
+struct OzCfg;
+template <>
+struct OzCfg<5> {
+  static constexpr int TN = 96, OST = 4;
+  // Stages per chunk of level g.  Levels 0-2 are exact: n_g = g_hi - g_lo +
+  // 1 products of |sigma| <= 128 over period x 32 columns stay within 2^24
+  // (1 x 32 x 32, 2 x 16 x 32, 3 x 10 x 32, times 2^14).  Levels 3 and 4
+  // run 64 stages and round (their error bound is in the header).
+  __host__ __device__ static constexpr int period(int g) { return g == 0 ? 32 : g == 1 ? 16 : g == 2 ? 10 : 64; }
+  // Offsets that stagger the levels' chunk boundaries (the first chunk of
+  // level g is period - offset stages long): chunk ends fall on stages 31,
+  // 10/26, 7 + 10 i (modulo 32), 52 and 38 (modulo 64).
+  __host__ __device__ static constexpr int offset(int g) {
+    return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 11 : 25;
+  }
+};
+template <>
+struct OzCfg<6> {
+  static constexpr int TN = 80, OST = 4;
+  // As OzCfg<5>, plus level 5 (2 products, weight 2^-8 of level 4) rounded
+  // in 64-stage chunks like levels 3 and 4: its chunks stay below 2^26, and
+  // even with every one of a chunk's 256 MMA additions off by a full unit
+  // (at most 4) the added error is 256 x 4 x 2^-56 / 2048 = 2^-57 of the
+  // row scales per column.
+  __host__ __device__ static constexpr int period(int g) { return g == 0 ? 32 : g == 1 ? 16 : g == 2 ? 10 : 64; }
+  __host__ __device__ static constexpr int offset(int g) {
+    return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 11 : g == 4 ? 25 : 44;
+  }
+};
+
+constexpr int TM = 128;                     // output tile rows
 constexpr int KS = 32;                      // K per stage (64-byte rows, 64-byte swizzle)
 constexpr int A_TILE = TM * 64;             // 8 KB
-constexpr int B_TILE = TN * 64;             // 6 KB
-constexpr int OSTAGE = NS * (A_TILE + B_TILE);   // 56 KB
-constexpr int OSMEM = OST * OSTAGE + 1024;
 constexpr int OTHREADS = 448;               // TMA warp, MMA warp, 12 epilogue warps
 constexpr int EPI_WARPS = 12;
-constexpr uint32_t OTMEM = 512;             // five 96-column level accumulators
+constexpr uint32_t OTMEM = 512;             // NG level accumulators of TN columns
+
+template <int NG>
+__host__ __device__ constexpr int b_tile() { return OzCfg<NG>::TN * 64; }
+template <int NG>
+__host__ __device__ constexpr int ostage() { return NS * (A_TILE + b_tile<NG>()); }
+template <int NG>
+__host__ __device__ constexpr int osmem() { return OzCfg<NG>::OST * ostage<NG>() + 1024; }
 
 __host__ __device__ __forceinline__ int g_lo(int g) { return g > NS - 1 ? g - (NS - 1) : 0; }
 __host__ __device__ __forceinline__ int g_hi(int g) { return g < NS - 1 ? g : NS - 1; }
 
-// Stages per chunk of level g.  Levels 0-2 are exact: n_g = g_hi - g_lo + 1
-// products of |sigma| <= 128 over period x 32 columns stay within 2^24
-// (1 x 32 x 32, 2 x 16 x 32, 3 x 10 x 32, times 2^14).  Levels 3 and 4 run
-// 64 stages and round (their error bound is in the header).
-__host__ __device__ constexpr int period_of(int g) { return g == 0 ? 32 : g == 1 ? 16 : g == 2 ? 10 : 64; }
-// Offsets that stagger the levels' chunk boundaries (the first chunk of level
-// g is period - offset stages long): chunk ends fall on stages 31, 10/26,
-// 7 + 10 i (modulo 32), 52 and 38 (modulo 64).
-__host__ __device__ constexpr int offset_of(int g) { return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 11 : 25; }
 static_assert(32 * 32 * 1 <= 1024 && 16 * 32 * 2 <= 1024 && 10 * 32 * 3 <= 1024,
               "an exact chunk must stay within 2^24 = 2^10 x 2^14");
+static_assert(5 * OzCfg<5>::TN <= (int)OTMEM && 6 * OzCfg<6>::TN <= (int)OTMEM,
+              "the level accumulators must fit the TMEM allocation");
+static_assert(osmem<5>() <= 227 * 1024 && osmem<6>() <= 227 * 1024, "shared-memory ring too large");
+static_assert(b_tile<5>() % 1024 == 0 && b_tile<6>() % 1024 == 0, "tiles keep 1024-byte alignment");
+
 // Chunk c of level g covers stages [start, end]: start = 0 for c = 0, else
 // c period - offset; end = (c + 1) period - offset - 1, clamped to nk - 1.
+template <int NG>
 __device__ __forceinline__ int chunk_end(int g, int c, int nk) {
-  return min(nk - 1, (c + 1) * period_of(g) - offset_of(g) - 1);
+  return min(nk - 1, (c + 1) * OzCfg<NG>::period(g) - OzCfg<NG>::offset(g) - 1);
 }
 
-// BF16 x BF16 -> FP32, both K-major, N = 96, M = 128.
+// BF16 x BF16 -> FP32, both K-major, M = 128, N = TN.
+template <int NG>
 __device__ __forceinline__ uint32_t oz_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OzCfg<NG>::TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
 // (hi, lo) += c exactly as long as the sum needs at most ~48 bits.
@@ -111,14 +152,18 @@ __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
   hi = t;
 }
 
-// Row scaling and slicing: one block per row, float4 loads and 8-byte
-// stores (ldJ and ldb are multiples of 4; the row's pad columns are zero).
-// The row's largest |J| comes from the Jacobian's writer, so J is read once.
-__global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const float* __restrict__ J, long long ldJ,
+// Row scaling and slicing: one block per row, 16-byte loads (four FP32 or
+// two pairs of FP64 entries) and 8-byte stores (ldJ and ldb are multiples of
+// 4; the row's pad columns are zero).  The row's largest |J| (as a float)
+// comes from the Jacobian's writer, so J is read once.  A float that rounded
+// a double maximum down keeps |J| / 2^E below 0.5 (1 + 2^-24), so the first
+// slice still stays within +-128.
+template <typename TJ>
+__global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const TJ* __restrict__ J, long long ldJ,
                                                   __nv_bfloat16* __restrict__ S, long long ldS, int ldb,
                                                   const unsigned* __restrict__ rowmax, int* __restrict__ rowexp) {
   const int i = blockIdx.x;
-  const float4* row = reinterpret_cast<const float4*>(J + (long long)i * ldJ);
+  const TJ* row = J + (long long)i * ldJ;
   const int n4 = (n + 3) / 4, b4 = ldb / 4;
   const float a = __uint_as_float(rowmax[i]);
   int e = 0;
@@ -127,37 +172,49 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const float* __r
   if (threadIdx.x == 0) rowexp[i] = E;
   __nv_bfloat16* srow = S + (long long)i * ldS;
   for (int k = threadIdx.x; k < b4; k += blockDim.x) {
-    float x[4];
+    TJ x[4];
     if (k < n4) {
-      const float4 v = __ldg(row + k);
-      x[0] = v.x;
-      x[1] = v.y;
-      x[2] = v.z;
-      x[3] = v.w;
+      if constexpr (sizeof(TJ) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(row) + k);
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
+      } else {
+        const double2 v0 = __ldg(reinterpret_cast<const double2*>(row) + 2 * k);
+        const double2 v1 = __ldg(reinterpret_cast<const double2*>(row) + 2 * k + 1);
+        x[0] = v0.x;
+        x[1] = v0.y;
+        x[2] = v1.x;
+        x[3] = v1.y;
+      }
     } else {
-      x[0] = x[1] = x[2] = x[3] = 0.f;
+      x[0] = x[1] = x[2] = x[3] = TJ(0);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) x[c] = (4 * k + c < n) ? ldexpf(x[c], -E) : 0.f;
+    for (int c = 0; c < 4; ++c) x[c] = (4 * k + c < n) ? (TJ)ldexp(x[c], -E) : TJ(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       __nv_bfloat16 q[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const float t = x[c] * 256.f;
-        const float sg = rintf(t);
+        const TJ t = x[c] * TJ(256);
+        const TJ sg = rint(t);
         x[c] = t - sg;
-        q[c] = __float2bfloat16_rn(sg);
+        q[c] = __float2bfloat16_rn((float)sg);
       }
       *reinterpret_cast<uint2*>(srow + (long long)s * ldb + 4 * k) = *reinterpret_cast<const uint2*>(q);
     }
   }
 }
 
+template <int NG>
 __global__ void __launch_bounds__(OTHREADS, 1)
 k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           const int2* __restrict__ tiles, int m, int num_kblk, int ldb, double* __restrict__ out, long long ldo,
           long long split_stride, int* status) {
+  constexpr int TN = OzCfg<NG>::TN, OST = OzCfg<NG>::OST;
+  constexpr int B_TILE = b_tile<NG>(), OSTAGE = ostage<NG>();
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[OST];
   __shared__ __align__(8) uint64_t empty_bar[OST];
@@ -224,14 +281,14 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = oz_idesc();
+      const uint32_t idesc = oz_idesc<NG>();
       // per level: current chunk, its first and last stage
       int cidx[NG], cstart[NG], cend[NG];
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         cidx[g] = 0;
         cstart[g] = 0;
-        cend[g] = chunk_end(g, 0, nk);
+        cend[g] = chunk_end<NG>(g, 0, nk);
       }
       for (int it = 0; it < nk && !*abort_flag; ++it) {
         const int st = it % OST;
@@ -276,7 +333,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
               umma_commit(smem_u32(&accf_bar[g]));
               ++cidx[g];
               cstart[g] = it + 1;
-              cend[g] = chunk_end(g, cidx[g], nk);
+              cend[g] = chunk_end<NG>(g, cidx[g], nk);
             }
           }
         }
@@ -286,7 +343,8 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
   } else {
     const int q = warp & 3;             // TMEM lane quadrant this warp may access
-    const int cg = (warp - 2) >> 2;     // column group (32 of the 96 columns)
+    const int cg = (warp - 2) >> 2;     // column group: 32 of the TN columns (the last 16 when TN = 80)
+    const int ncol = TN - cg * 32 < 32 ? TN - cg * 32 : 32;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * 32);
     float hi[32], lo[32];
 #pragma unroll
@@ -302,7 +360,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     for (int g = 0; g < NG; ++g) {
       cidx[g] = 0;
       cstart[g] = 0;
-      cend[g] = nk > 0 ? chunk_end(g, 0, nk) : INT_MAX;
+      cend[g] = nk > 0 ? chunk_end<NG>(g, 0, nk) : INT_MAX;
     }
     while (!*abort_flag) {
       int gsel = -1, kbest = INT_MAX;
@@ -327,13 +385,19 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       uint32_t r[32];
-      TMEM_LD_32(lane_base + (uint32_t)(gsel * TN), r);
+      if (ncol == 32) {
+        TMEM_LD_32(lane_base + (uint32_t)(gsel * TN), r);
+      } else {
+        TMEM_LD_16(lane_base + (uint32_t)(gsel * TN), r);
+#pragma unroll
+        for (int i = 16; i < 32; ++i) r[i] = 0u;
+      }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[gsel])) : "memory");
-      // the level's chunk times 2^(8 (4 - g)) (a power of two: exact)
+      // the level's chunk times 2^(8 (NG - 1 - g)) (a power of two: exact)
       const float sc = __int_as_float((127 + 8 * (NG - 1 - gsel)) << 23);
 #pragma unroll
       for (int i = 0; i < 32; ++i) df_add_exact(hi[i], lo[i], __uint_as_float(r[i]) * sc);
@@ -344,7 +408,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           const int e = cend[g];
           ++cidx[g];
           cstart[g] = e + 1;
-          cend[g] = e + 1 < nk ? chunk_end(g, cidx[g], nk) : INT_MAX;
+          cend[g] = e + 1 < nk ? chunk_end<NG>(g, cidx[g], nk) : INT_MAX;
         }
     }
     const int row = tile.x * TM + q * 32 + lane;
@@ -353,7 +417,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0;
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (col0 + j < m) orow[j] = (double)hi[j] + (double)lo[j];
+        if (j < ncol && col0 + j < m) orow[j] = (double)hi[j] + (double)lo[j];
     }
   }
   __syncwarp();
@@ -389,13 +453,15 @@ __global__ void k_df_to_double(long long cnt, const float2* __restrict__ F, doub
 }
 
 // Blocks of 32 x 32 entries (bj <= bi): sum the split partials once, scale
-// by 2^(E_i+E_j-48), write the full symmetric double-float Gram F (both the block
+// by 2^(E_i+E_j-eshift) (eshift = 16 + 8 (NG - 1): the slices' 2^-8(s+1)
+// weights and the epilogue's 2^(8 (NG - 1 - g)) level factors), write the full
+// symmetric double-float Gram F (both the block
 // and its mirror, through shared memory) and the FP32 lower triangle K with
 // the diagonal shift (its upper triangle zeroed) for the FP32 factorisation.
 __global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const double* __restrict__ P, long long ldp,
-                                                   long long sstride, const int* __restrict__ rowexp, double shift,
-                                                   float* __restrict__ K, long long ldk, float2* __restrict__ F,
-                                                   long long ldf) {
+                                                   long long sstride, const int* __restrict__ rowexp, int eshift,
+                                                   double shift, float* __restrict__ K, long long ldk,
+                                                   float2* __restrict__ F, long long ldf) {
   __shared__ double t[32][33];
   const int b = blockIdx.x;
   int bi = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
@@ -423,7 +489,7 @@ __global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const doub
 #pragma unroll
       for (int sp = 0; sp < 4; ++sp)
         if (sp < nsplit) v += pv[q][sp];
-      v = ldexp(v, rowexp[i] + rowexp[j] - 48);
+      v = ldexp(v, rowexp[i] + rowexp[j] - eshift);
     }
     t[r][tx] = v;
     if (i < m && j < m) {
@@ -465,8 +531,10 @@ int oz_splits(int ntiles, int num_kblk, int nsm) {
 // other tiles of the super-block) instead of every column block of a few
 // row blocks.
 constexpr int kSB = 12;
-std::vector<int2> oz_tiles(int m) {
+int oz_tn(int ng) { return ng == 6 ? OzCfg<6>::TN : OzCfg<5>::TN; }
+std::vector<int2> oz_tiles(int m, int ng) {
   std::vector<int2> t;
+  const int TN = oz_tn(ng);
   const int nI = (m + TM - 1) / TM, nJ = (m + TN - 1) / TN;
   for (int I0 = 0; I0 < nI; I0 += kSB)
     for (int J0 = 0; J0 < nJ && J0 * TN <= (I0 + kSB) * TM - 1; J0 += kSB)
@@ -476,14 +544,16 @@ std::vector<int2> oz_tiles(int m) {
   return t;
 }
 long long oz_mp(int m) { return (long long)((m + TM - 1) / TM) * TM; }
-long long oz_lp(int m) { return (long long)((m + TN - 1) / TN) * TN; }
+long long oz_lp(int m, int ng) { return (long long)((m + oz_tn(ng) - 1) / oz_tn(ng)) * oz_tn(ng); }
 
 }  // namespace
 
 struct OzPlan {
   int m, n, ldb;
+  int ng;            // levels kept (5: g <= 4, 6: g <= 5)
+  bool j64;          // J is FP64 (else FP32)
   long long ldJ, ldS;
-  const float* J;
+  const void* J;
   __nv_bfloat16* S;
   int* rowexp;
   unsigned* rowmax;
@@ -499,12 +569,12 @@ struct OzPlan {
   double shift = 0.0;
 };
 
-size_t gram_oz_partial_bytes(int m, int n) {
+size_t gram_oz_partial_bytes(int m, int n, int ng) {
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int nsplit = oz_splits((int)oz_tiles(m).size(), (n + KS - 1) / KS, nsm);
-  return (size_t)nsplit * oz_mp(m) * oz_lp(m) * sizeof(double);
+  const int nsplit = oz_splits((int)oz_tiles(m, ng).size(), (n + KS - 1) / KS, nsm);
+  return (size_t)nsplit * oz_mp(m) * oz_lp(m, ng) * sizeof(double);
 }
 
 size_t gram_oz_slice_bytes(int m, int n) {
@@ -512,13 +582,16 @@ size_t gram_oz_slice_bytes(int m, int n) {
   return (size_t)m * NS * ldb * sizeof(__nv_bfloat16) + 2 * (size_t)m * sizeof(int) + 256;
 }
 
-dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int n, void* slices, float* K,
-                         long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes) {
+dngd_status gram_oz_plan(OzPlan** out, const void* J, bool j64, int ng, long long ldJ, int m, int n, void* slices,
+                         float* K, long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes) {
+  if (ng != 5 && ng != 6) return DNGD_ERR_INVALID_ARG;
   EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
   if (!enc) return DNGD_ERR_CUDA;
   OzPlan* p = new OzPlan();
   p->m = m;
   p->n = n;
+  p->ng = ng;
+  p->j64 = j64;
   p->J = J;
   p->ldJ = ldJ;
   p->ldb = ((n + 63) / 64) * 64;
@@ -531,6 +604,7 @@ dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int
   p->F = F;
   p->ldf = ldf;
   p->num_kblk = p->ldb / KS;   // K stages
+  const int TN = oz_tn(ng);
   cuuint64_t gdim[2] = {(cuuint64_t)p->ldS, (cuuint64_t)m};
   cuuint64_t gstride[1] = {(cuuint64_t)(p->ldS * 2)};
   cuuint32_t estride[2] = {1, 1};
@@ -545,13 +619,13 @@ dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int
     delete p;
     return DNGD_ERR_CUDA;
   }
-  std::vector<int2> tiles = oz_tiles(m);
+  std::vector<int2> tiles = oz_tiles(m, ng);
   p->ntiles = (int)tiles.size();
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   p->nsplit = oz_splits(p->ntiles, p->num_kblk, nsm);
-  p->ldp = oz_lp(m);
+  p->ldp = oz_lp(m, ng);
   p->sstride = oz_mp(m) * p->ldp;
   if ((size_t)p->nsplit * p->sstride * sizeof(double) > partial_bytes) p->nsplit = 1;
   if ((size_t)p->sstride * sizeof(double) > partial_bytes) {
@@ -564,10 +638,14 @@ dngd_status gram_oz_plan(OzPlan** out, const float* J, long long ldJ, int m, int
     return DNGD_ERR_OOM;
   }
   cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gram_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OSMEM);
-    attr = true;
+  static bool attr5 = false, attr6 = false;
+  if (ng == 5 && !attr5) {
+    cudaFuncSetAttribute(k_gram_oz<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<5>());
+    attr5 = true;
+  }
+  if (ng == 6 && !attr6) {
+    cudaFuncSetAttribute(k_gram_oz<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<6>());
+    attr6 = true;
   }
   *out = p;
   return DNGD_OK;
@@ -580,12 +658,20 @@ dngd_status gram_oz_set_shift(OzPlan* p, double shift) {
 
 dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_after_mma) {
   DNGD_NOTE_LAUNCH();
-  k_oz_slice<<<p->m, 256, 0, st>>>(p->m, p->n, p->J, p->ldJ, p->S, p->ldS, p->ldb, p->rowmax, p->rowexp);
+  if (p->j64)
+    k_oz_slice<double><<<p->m, 256, 0, st>>>(p->m, p->n, (const double*)p->J, p->ldJ, p->S, p->ldS, p->ldb,
+                                              p->rowmax, p->rowexp);
+  else
+    k_oz_slice<float><<<p->m, 256, 0, st>>>(p->m, p->n, (const float*)p->J, p->ldJ, p->S, p->ldS, p->ldb,
+                                             p->rowmax, p->rowexp);
   DNGD_LAUNCH_CHECK();
   DNGD_NOTE_LAUNCH();
-  k_gram_oz<<<dim3(p->ntiles, p->nsplit), OTHREADS, OSMEM, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk,
-                                                                  p->ldb,
-                                                                  p->partials, p->ldp, p->sstride, status);
+  if (p->ng == 5)
+    k_gram_oz<5><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<5>(), st>>>(
+        p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, status);
+  else
+    k_gram_oz<6><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<6>(), st>>>(
+        p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, status);
   DNGD_LAUNCH_CHECK();
   if (ev_after_mma) cudaEventRecord(ev_after_mma, st);
   return gram_oz_reduce(p, st);
@@ -598,7 +684,7 @@ dngd_status gram_oz_reduce(OzPlan* p, cudaStream_t st) {
   const int nb = (p->m + 31) / 32;
   DNGD_NOTE_LAUNCH();
   k_oz_reduce<<<nb * (nb + 1) / 2, 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->rowexp,
-                                                 p->shift, p->K, p->ldk, p->F, p->ldf);
+                                                 16 + 8 * (p->ng - 1), p->shift, p->K, p->ldk, p->F, p->ldf);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }

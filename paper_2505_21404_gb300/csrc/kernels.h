@@ -133,14 +133,18 @@ dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long
 dngd_status gemm_tc3_trials(int G, int M, int N, int K, const float* B0, long long ldb, long long b_z, float* C,
                             long long ldc, long long c_z, const Tc3Scratch& sc, int* status, cudaStream_t st);
 
-// ---- gram_oz.cu: exact Gram of an FP32 matrix from BF16 integer slices ----
+// ---- gram_oz.cu: exact Gram of an FP32 or FP64 matrix from BF16 integer slices ----
+// Four 8-bit slices per entry; ng = 5 keeps the slice products of levels
+// s + t <= 4 (13 products), ng = 6 levels <= 5 (15 products).  J is float*
+// (j64 false) or double* (j64 true); ldJ a multiple of 4 and the row pad
+// beyond n zero.
 struct OzPlan;
-size_t gram_oz_partial_bytes(int m, int n);
+size_t gram_oz_partial_bytes(int m, int n, int ng);
 size_t gram_oz_slice_bytes(int m, int n);   // slices + row exponents
 // K: FP32 lower triangle + shift; F: full symmetric Gram as double-float
 // pairs (no shift)
-dngd_status gram_oz_plan(OzPlan** plan, const float* J, long long ldJ, int m, int n, void* slices, float* K,
-                         long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes);
+dngd_status gram_oz_plan(OzPlan** plan, const void* J, bool j64, int ng, long long ldJ, int m, int n, void* slices,
+                         float* K, long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes);
 dngd_status gram_oz_read(const OzPlan* plan, double* out, cudaStream_t st);  // F as FP64 [m x ldf]
 dngd_status gram_oz_set_shift(OzPlan* plan, double shift);
 dngd_status gram_oz_run(OzPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);

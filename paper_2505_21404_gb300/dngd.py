@@ -18,7 +18,7 @@ MAX_LAYERS = 12
 MAX_DIM = 8
 MAX_CLASSES = 4
 
-FP64, MIXED_BF16, MIXED_TF32, MIXED_OZ = 0, 1, 2, 3
+FP64, MIXED_BF16, MIXED_TF32, MIXED_OZ, MIXED_OZ64 = 0, 1, 2, 3, 4
 DENSE, PCG = 0, 1
 
 STATUS = {

@@ -78,7 +78,9 @@ def test_poisson2d_twenty_iterations_step_parity(dngd):
         assert err <= bound, rows[-1]
         assert blk <= bound, rows[-1]
         assert info["ga_accepted"] == ref["accepted"], rows[-1]
-        assert abs(info["loss"] - 0.5 * float(ref["r"] @ ref["r"])) <= 1e-11 * info["loss"] + 1e-300
+        # the residuals are small differences of O(10) jets terms late in the
+        # run: their FP64 values carry ~1e-15 absolute, i.e. ~1e-9 relative
+        assert abs(info["loss"] - 0.5 * float(ref["r"] @ ref["r"])) <= 1e-9 * info["loss"] + 1e-300
         # the oracle's line search along the GPU's step picks the same eta
         eta_ref, ls = olin.line_search(th, prob, X, tg, d, etas)
         assert eta == eta_ref, (k, eta, eta_ref, ls)
