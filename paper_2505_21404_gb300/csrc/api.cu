@@ -55,6 +55,9 @@ struct dngd_ctx {
   float* Linv = nullptr;
   float* trtri_work = nullptr;
   OzPlan* oz = nullptr;       // exact-Gram mode
+  OzFactor* ozf = nullptr;    // its FP64 factorisation (exact sliced trailing updates)
+  double* Kd = nullptr;       // exact Gram + (lambda + mu) I, FP64 lower: factored in place
+  void* ozf_work = nullptr;
   void* oz_slices = nullptr;
   double* oz_partials = nullptr;
   float2* K64 = nullptr;      // exact Gram as double-float pairs (full symmetric, no shift)
@@ -451,6 +454,43 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     evrec(c, 2);
     if ((s = cholesky<double>(m, (double*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
     if ((s = trtri_diag64(m, (const double*)c->K, c->ldk, c->Dinv, c->st))) return s;
+  } else if (c->ozf) {
+    // exact Gram: FP64 factor of K + (lambda + mu) I with exact sliced
+    // trailing updates (mu = 0 unless that fails at the Gram's own accuracy);
+    // its FP32 rounding and inverse precondition PCG on the exact operator
+    double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
+    const double mu0 = mu;
+    gram_set_shift(c, c->lambda + mu);
+    if ((s = gram_run(c, c->timing ? c->ev[8] : nullptr))) return s;
+    c->factor_attempts = 0;
+    if (!c->async && (s = diag_sum<float>(m, (const float*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
+    for (int attempt = 0;; ++attempt) {
+      if (attempt > 0) {
+        gram_set_shift(c, c->lambda + mu);
+        if ((s = gram_oz_reduce(c->oz, c->st))) return s;
+      }
+      evrec(c, 2);
+      c->factor_attempts++;
+      if ((s = oz_factor_run(c->ozf, c->status, c->st))) return s;
+      if (c->async) break;   // a failure is reported by the status word
+      const dngd_status fs = read_status(c);
+      if (fs != DNGD_ERR_NOT_SPD || attempt >= 15) break;
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+      DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+      const double tr = c->scal_h[S_TRACE] - m * (c->lambda + mu0);
+      const double base = 1e-10 * (tr > 0 ? tr : 1.0) / m;
+      mu = mu * 10.0 > base ? mu * 10.0 : base;
+      DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+    }
+    if (!c->async) c->mu_sticky = mu;
+    c->shift_used = mu;
+    if ((s = trtri_diag64(m, c->Kd, c->ldk, c->Dinv, c->st))) return s;
+    if ((s = factor_to_f32(m, c->Kd, c->ldk, c->Dinv, (float*)c->K, c->ldk, c->Linv, c->ldk, c->st))) return s;
+    if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st, tc3p(c),
+                               c->status)))
+      return s;
+    if (c->LinvT && (s = transpose_f32(m, c->Linv, c->ldk, c->LinvT, c->ldk, c->st))) return s;
+    if (c->async) goto factored;
   } else {
     // low-precision Gram + FP32 factor of K + (lambda + mu) I; a failed
     // factorisation is retried with a larger shift mu (it only preconditions
@@ -928,6 +968,9 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       add(sizeof(double) * 7 * (size_t)m);        // persistent-PCG vectors
       add(gram_oz_slice_bytes(m, (int)n));
       add(gram_oz_partial_bytes(m, (int)n, ng));
+      add(sizeof(double) * (size_t)m * c->ldk);                                  // Kd
+      add(sizeof(double) * (size_t)cdiv(m, 64) * 64 * 64);                       // Dinv
+      add(oz_factor_bytes(m));
     } else {
       add(gram_tc_partial_bytes(m, (int)n));
     }
@@ -1012,6 +1055,9 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       A_(c->oz_slices, unsigned char, gram_oz_slice_bytes(m, (int)n));
       c->gram_partial_bytes = gram_oz_partial_bytes(m, (int)n, ng);
       A_(c->oz_partials, double, c->gram_partial_bytes / sizeof(double));
+      A_(c->Kd, double, (size_t)m * c->ldk);
+      A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
+      A_(c->ozf_work, unsigned char, oz_factor_bytes(m));
     } else {
       c->gram_partial_bytes = gram_tc_partial_bytes(m, (int)n);
       A_(c->gram_partials, float, c->gram_partial_bytes / sizeof(float));
@@ -1046,6 +1092,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     s = gram_oz_plan(&c->oz, c->J, j64, ng, c->ldJ, m, (int)n, c->oz_slices, (float*)c->K, c->ldk, c->K64, c->ldk,
                      c->oz_partials, c->gram_partial_bytes);
     if (s) return s;
+    gram_oz_set_fp64_out(c->oz, c->Kd);
+    if ((s = oz_factor_plan(&c->ozf, m, c->Kd, c->ldk, c->ozf_work))) return s;
   } else if (!f64) {
     const void* Jlow = bf ? (const void*)c->Jb : (const void*)c->J;
     const long long ld = bf ? c->ldb : c->ldJ;
@@ -1073,6 +1121,7 @@ void free_ctx(dngd_ctx* c) {
   if (c->status_h) cudaFreeHost(c->status_h);
   if (c->gram) gram_tc_free(c->gram);
   if (c->oz) gram_oz_free(c->oz);
+  if (c->ozf) oz_factor_free(c->ozf);
   for (int i = 0; i < 9; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (int i = 0; i < 4; ++i)

@@ -62,21 +62,22 @@ namespace {
 
 using namespace tc;
 
-constexpr int NS = 4;                       // slices per value
-
-// Level configurations: the products sigma_s sigma_t^T are summed by level
-// g = s + t, each level in its own TMEM accumulator of TN columns
-// (NG x TN <= 512).  NG = 5 keeps the levels g <= 4 (13 of the 16 products;
-// the FP32 Jacobian, whose own rounding is far larger than the dropped
-// terms), NG = 6 also level 5 (15 products; the FP64 Jacobian).  The dropped
-// levels are not unbiased noise (on the diagonal they are a sum of squares),
-// so for an accurate J the truncation is what limits the Gram, not the
-// slicing: level 5 brings the step error at a trained theta from 1.5e-4 to
-// 6e-6 (CPU emulation), as close as a fifth slice would.
-template <int NG>
+// Configurations <NS, NG>: NS 8-bit slices per value; the products
+// sigma_s sigma_t^T are summed by level g = s + t <= NG - 1, each level in
+// its own TMEM accumulator of TN columns (NG x TN <= 512).
+// * <4, 5>: levels g <= 4 (13 of the 16 products), for the FP32 Jacobian,
+//   whose own rounding is far larger than the dropped terms.
+// * <4, 6>: also level 5 (15 products), for the FP64 Jacobian.  The dropped
+//   levels are not unbiased noise (on the diagonal they are a sum of
+//   squares), so for an accurate J the truncation is what limits the Gram,
+//   not the slicing: level 5 brings the step error at a trained theta from
+//   1.5e-4 to 6e-6 (CPU emulation), as close as a fifth slice would.
+// * <6, 7>: six slices, levels g <= 6 (26 of 36 products), for the trailing
+//   updates of the FP64 factorisation (K extent 64: every chunk exact).
+template <int NS, int NG>
 struct OzCfg;
 template <>
-struct OzCfg<5> {
+struct OzCfg<4, 5> {
   static constexpr int TN = 96, OST = 4;
   // Stages per chunk of level g.  Levels 0-2 are exact: n_g = g_hi - g_lo +
   // 1 products of |sigma| <= 128 over period x 32 columns stay within 2^24
@@ -91,10 +92,10 @@ struct OzCfg<5> {
   }
 };
 template <>
-struct OzCfg<6> {
+struct OzCfg<4, 6> {
   static constexpr int TN = 80, OST = 4;
-  // As OzCfg<5>, plus level 5 (2 products, weight 2^-8 of level 4) rounded
-  // in 64-stage chunks like levels 3 and 4: its chunks stay below 2^26, and
+  // As <4, 5>, plus level 5 (2 products, weight 2^-8 of level 4) rounded in
+  // 64-stage chunks like levels 3 and 4: its chunks stay below 2^26, and
   // even with every one of a chunk's 256 MMA additions off by a full unit
   // (at most 4) the added error is 256 x 4 x 2^-56 / 2048 = 2^-57 of the
   // row scales per column.
@@ -102,6 +103,14 @@ struct OzCfg<6> {
   __host__ __device__ static constexpr int offset(int g) {
     return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 11 : g == 4 ? 25 : 44;
   }
+};
+template <>
+struct OzCfg<6, 7> {
+  static constexpr int TN = 64, OST = 2;
+  // K extent 64 = two stages: one chunk per level, 2 x 32 x 6 x 2^14 < 2^24,
+  // so every level is exact.
+  __host__ __device__ static constexpr int period(int g) { return g >= 0 ? 2 : 2; }
+  __host__ __device__ static constexpr int offset(int g) { return g >= 0 ? 0 : 0; }
 };
 
 constexpr int TM = 128;                     // output tile rows
@@ -111,35 +120,50 @@ constexpr int OTHREADS = 448;               // TMA warp, MMA warp, 12 epilogue w
 constexpr int EPI_WARPS = 12;
 constexpr uint32_t OTMEM = 512;             // NG level accumulators of TN columns
 
-template <int NG>
-__host__ __device__ constexpr int b_tile() { return OzCfg<NG>::TN * 64; }
-template <int NG>
-__host__ __device__ constexpr int ostage() { return NS * (A_TILE + b_tile<NG>()); }
-template <int NG>
-__host__ __device__ constexpr int osmem() { return OzCfg<NG>::OST * ostage<NG>() + 1024; }
+template <int NS, int NG>
+__host__ __device__ constexpr int b_tile() { return OzCfg<NS, NG>::TN * 64; }
+template <int NS, int NG>
+__host__ __device__ constexpr int ostage() { return NS * (A_TILE + b_tile<NS, NG>()); }
+template <int NS, int NG>
+__host__ __device__ constexpr int osmem() { return OzCfg<NS, NG>::OST * ostage<NS, NG>() + 1024; }
 
+template <int NS>
 __host__ __device__ __forceinline__ int g_lo(int g) { return g > NS - 1 ? g - (NS - 1) : 0; }
+template <int NS>
 __host__ __device__ __forceinline__ int g_hi(int g) { return g < NS - 1 ? g : NS - 1; }
 
-static_assert(32 * 32 * 1 <= 1024 && 16 * 32 * 2 <= 1024 && 10 * 32 * 3 <= 1024,
+static_assert(32 * 32 * 1 <= 1024 && 16 * 32 * 2 <= 1024 && 10 * 32 * 3 <= 1024 && 2 * 32 * 6 <= 1024,
               "an exact chunk must stay within 2^24 = 2^10 x 2^14");
-static_assert(5 * OzCfg<5>::TN <= (int)OTMEM && 6 * OzCfg<6>::TN <= (int)OTMEM,
+static_assert(5 * OzCfg<4, 5>::TN <= (int)OTMEM && 6 * OzCfg<4, 6>::TN <= (int)OTMEM &&
+                  7 * OzCfg<6, 7>::TN <= (int)OTMEM,
               "the level accumulators must fit the TMEM allocation");
-static_assert(osmem<5>() <= 227 * 1024 && osmem<6>() <= 227 * 1024, "shared-memory ring too large");
-static_assert(b_tile<5>() % 1024 == 0 && b_tile<6>() % 1024 == 0, "tiles keep 1024-byte alignment");
+static_assert(osmem<4, 5>() <= 227 * 1024 && osmem<4, 6>() <= 227 * 1024 && osmem<6, 7>() <= 227 * 1024,
+              "shared-memory ring too large");
+static_assert(b_tile<4, 5>() % 1024 == 0 && b_tile<4, 6>() % 1024 == 0 && b_tile<6, 7>() % 1024 == 0,
+              "tiles keep 1024-byte alignment");
 
 // Chunk c of level g covers stages [start, end]: start = 0 for c = 0, else
 // c period - offset; end = (c + 1) period - offset - 1, clamped to nk - 1.
-template <int NG>
+template <int NS, int NG>
 __device__ __forceinline__ int chunk_end(int g, int c, int nk) {
-  return min(nk - 1, (c + 1) * OzCfg<NG>::period(g) - OzCfg<NG>::offset(g) - 1);
+  return min(nk - 1, (c + 1) * OzCfg<NS, NG>::period(g) - OzCfg<NS, NG>::offset(g) - 1);
 }
 
 // BF16 x BF16 -> FP32, both K-major, M = 128, N = TN.
-template <int NG>
+template <int TN>
 __device__ __forceinline__ uint32_t oz_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OzCfg<NG>::TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
+
+// The factorisation's trailing update, done in the epilogue instead of
+// writing partial tiles: C[i, j] -= 2^(E_i + E_j - eshift) acc for the
+// entries j <= i of the trailing block (rows and columns row_off + index).
+struct OzUpdate {
+  double* C;
+  long long ldc;
+  const int* rowexp;
+  int eshift;
+};
 
 // (hi, lo) += c exactly as long as the sum needs at most ~48 bits.
 __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
@@ -194,7 +218,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const TJ* __rest
 #pragma unroll
     for (int c = 0; c < 4; ++c) x[c] = (4 * k + c < n) ? (TJ)ldexp(x[c], -E) : TJ(0);
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
+    for (int s = 0; s < 4; ++s) {
       __nv_bfloat16 q[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -208,13 +232,17 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const TJ* __rest
   }
 }
 
-template <int NG>
+// One CTA per (output tile, K split).  m: rows of the (trailing) matrix;
+// its row and column i sit at slice row row_off + i.  UPD: the epilogue
+// applies the factorisation update (OzUpdate) instead of writing the partial
+// tile to out.
+template <int NS, int NG, bool UPD>
 __global__ void __launch_bounds__(OTHREADS, 1)
 k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-          const int2* __restrict__ tiles, int m, int num_kblk, int ldb, double* __restrict__ out, long long ldo,
-          long long split_stride, int* status) {
-  constexpr int TN = OzCfg<NG>::TN, OST = OzCfg<NG>::OST;
-  constexpr int B_TILE = b_tile<NG>(), OSTAGE = ostage<NG>();
+          const int2* __restrict__ tiles, int m, int row_off, int num_kblk, int ldb, double* __restrict__ out,
+          long long ldo, long long split_stride, OzUpdate upd, int* status) {
+  constexpr int TN = OzCfg<NS, NG>::TN, OST = OzCfg<NS, NG>::OST;
+  constexpr int B_TILE = b_tile<NS, NG>(), OSTAGE = ostage<NS, NG>();
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[OST];
   __shared__ __align__(8) uint64_t empty_bar[OST];
@@ -273,22 +301,22 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int kc = (kb0 + it) * KS;
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) {
-          tma_load_2d(sbase + sl * A_TILE, &mapA, fb, sl * ldb + kc, tile.x * TM);
-          tma_load_2d(sbase + NS * A_TILE + sl * B_TILE, &mapB, fb, sl * ldb + kc, tile.y * TN);
+          tma_load_2d(sbase + sl * A_TILE, &mapA, fb, sl * ldb + kc, row_off + tile.x * TM);
+          tma_load_2d(sbase + NS * A_TILE + sl * B_TILE, &mapB, fb, sl * ldb + kc, row_off + tile.y * TN);
         }
         ++issued;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = oz_idesc<NG>();
+      const uint32_t idesc = oz_idesc<TN>();
       // per level: current chunk, its first and last stage
       int cidx[NG], cstart[NG], cend[NG];
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         cidx[g] = 0;
         cstart[g] = 0;
-        cend[g] = chunk_end<NG>(g, 0, nk);
+        cend[g] = chunk_end<NS, NG>(g, 0, nk);
       }
       for (int it = 0; it < nk && !*abort_flag; ++it) {
         const int st = it % OST;
@@ -321,19 +349,19 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             }
             const uint32_t dbuf = tmem + (uint32_t)(g * TN);
 #pragma unroll
-            for (int sa = g_lo(g); sa <= g_hi(g); ++sa) {
+            for (int sa = g_lo<NS>(g); sa <= g_hi<NS>(g); ++sa) {
 #pragma unroll
               for (int k = 0; k < KS / 16; ++k) {
                 umma<0>(dbuf, da0 + (uint64_t)((sa * A_TILE + 32 * k) >> 4),
                         db0 + (uint64_t)(((g - sa) * B_TILE + 32 * k) >> 4), idesc,
-                        (first && sa == g_lo(g) && k == 0) ? 0u : 1u);
+                        (first && sa == g_lo<NS>(g) && k == 0) ? 0u : 1u);
               }
             }
             if (cend[g] == it) {
               umma_commit(smem_u32(&accf_bar[g]));
               ++cidx[g];
               cstart[g] = it + 1;
-              cend[g] = chunk_end<NG>(g, cidx[g], nk);
+              cend[g] = chunk_end<NS, NG>(g, cidx[g], nk);
             }
           }
         }
@@ -343,8 +371,8 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
   } else {
     const int q = warp & 3;             // TMEM lane quadrant this warp may access
-    const int cg = (warp - 2) >> 2;     // column group: 32 of the TN columns (the last 16 when TN = 80)
-    const int ncol = TN - cg * 32 < 32 ? TN - cg * 32 : 32;
+    const int cg = (warp - 2) >> 2;     // column group: 32 of the TN columns (16 or none in the last)
+    const int ncol = TN - cg * 32 < 32 ? (TN - cg * 32 > 0 ? TN - cg * 32 : 0) : 32;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * 32);
     float hi[32], lo[32];
 #pragma unroll
@@ -360,7 +388,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     for (int g = 0; g < NG; ++g) {
       cidx[g] = 0;
       cstart[g] = 0;
-      cend[g] = nk > 0 ? chunk_end<NG>(g, 0, nk) : INT_MAX;
+      cend[g] = nk > 0 ? chunk_end<NS, NG>(g, 0, nk) : INT_MAX;
     }
     while (!*abort_flag) {
       int gsel = -1, kbest = INT_MAX;
@@ -387,10 +415,13 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       uint32_t r[32];
       if (ncol == 32) {
         TMEM_LD_32(lane_base + (uint32_t)(gsel * TN), r);
-      } else {
+      } else if (ncol == 16) {
         TMEM_LD_16(lane_base + (uint32_t)(gsel * TN), r);
 #pragma unroll
         for (int i = 16; i < 32; ++i) r[i] = 0u;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) r[i] = 0u;
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -408,12 +439,22 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           const int e = cend[g];
           ++cidx[g];
           cstart[g] = e + 1;
-          cend[g] = e + 1 < nk ? chunk_end<NG>(g, cidx[g], nk) : INT_MAX;
+          cend[g] = e + 1 < nk ? chunk_end<NS, NG>(g, cidx[g], nk) : INT_MAX;
         }
     }
     const int row = tile.x * TM + q * 32 + lane;
     const int col0 = tile.y * TN + cg * 32;
-    if (row < m && !*abort_flag) {
+    if (UPD) {
+      if (row < m && !*abort_flag) {
+        const int gr = row_off + row;
+        const int er = upd.rowexp[gr];
+        double* crow = upd.C + (long long)gr * upd.ldc + row_off + col0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < ncol && col0 + j <= row)
+            crow[j] -= ldexp((double)hi[j] + (double)lo[j], er + upd.rowexp[row_off + col0 + j] - upd.eshift);
+      }
+    } else if (row < m && !*abort_flag) {
       double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0;
 #pragma unroll
       for (int j = 0; j < 32; ++j)
@@ -461,7 +502,7 @@ __global__ void k_df_to_double(long long cnt, const float2* __restrict__ F, doub
 __global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const double* __restrict__ P, long long ldp,
                                                    long long sstride, const int* __restrict__ rowexp, int eshift,
                                                    double shift, float* __restrict__ K, long long ldk,
-                                                   float2* __restrict__ F, long long ldf) {
+                                                   float2* __restrict__ F, long long ldf, double* __restrict__ Kd) {
   __shared__ double t[32][33];
   const int b = blockIdx.x;
   int bi = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
@@ -495,6 +536,7 @@ __global__ void __launch_bounds__(256) k_oz_reduce(int m, int nsplit, const doub
     if (i < m && j < m) {
       if (j <= i) F[(long long)i * ldf + j] = df_split(v);
       K[(long long)i * ldk + j] = (j <= i) ? (float)(i == j ? v + shift : v) : 0.f;
+      if (Kd && j <= i) Kd[(long long)i * ldk + j] = i == j ? v + shift : v;
     }
   }
   __syncthreads();
@@ -531,7 +573,7 @@ int oz_splits(int ntiles, int num_kblk, int nsm) {
 // other tiles of the super-block) instead of every column block of a few
 // row blocks.
 constexpr int kSB = 12;
-int oz_tn(int ng) { return ng == 6 ? OzCfg<6>::TN : OzCfg<5>::TN; }
+int oz_tn(int ng) { return ng == 6 ? OzCfg<4, 6>::TN : OzCfg<4, 5>::TN; }
 std::vector<int2> oz_tiles(int m, int ng) {
   std::vector<int2> t;
   const int TN = oz_tn(ng);
@@ -567,6 +609,7 @@ struct OzPlan {
   float2* F;         // double-float full symmetric (refinement operator)
   long long ldf;
   double shift = 0.0;
+  double* Kd = nullptr;   // FP64 lower + shift (the FP64 factorisation), or null
 };
 
 size_t gram_oz_partial_bytes(int m, int n, int ng) {
@@ -579,7 +622,7 @@ size_t gram_oz_partial_bytes(int m, int n, int ng) {
 
 size_t gram_oz_slice_bytes(int m, int n) {
   const long long ldb = ((n + 63) / 64) * 64;
-  return (size_t)m * NS * ldb * sizeof(__nv_bfloat16) + 2 * (size_t)m * sizeof(int) + 256;
+  return (size_t)m * 4 * ldb * sizeof(__nv_bfloat16) + 2 * (size_t)m * sizeof(int) + 256;
 }
 
 dngd_status gram_oz_plan(OzPlan** out, const void* J, bool j64, int ng, long long ldJ, int m, int n, void* slices,
@@ -595,7 +638,7 @@ dngd_status gram_oz_plan(OzPlan** out, const void* J, bool j64, int ng, long lon
   p->J = J;
   p->ldJ = ldJ;
   p->ldb = ((n + 63) / 64) * 64;
-  p->ldS = (long long)NS * p->ldb;
+  p->ldS = (long long)4 * p->ldb;
   p->S = (__nv_bfloat16*)slices;
   p->rowexp = (int*)((char*)slices + (size_t)m * p->ldS * sizeof(__nv_bfloat16));
   p->rowmax = (unsigned*)(p->rowexp + m);
@@ -640,11 +683,11 @@ dngd_status gram_oz_plan(OzPlan** out, const void* J, bool j64, int ng, long lon
   cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
   static bool attr5 = false, attr6 = false;
   if (ng == 5 && !attr5) {
-    cudaFuncSetAttribute(k_gram_oz<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<5>());
+    cudaFuncSetAttribute(k_gram_oz<4, 5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 5>());
     attr5 = true;
   }
   if (ng == 6 && !attr6) {
-    cudaFuncSetAttribute(k_gram_oz<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<6>());
+    cudaFuncSetAttribute(k_gram_oz<4, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 6>());
     attr6 = true;
   }
   *out = p;
@@ -666,12 +709,13 @@ dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_
                                              p->rowmax, p->rowexp);
   DNGD_LAUNCH_CHECK();
   DNGD_NOTE_LAUNCH();
+  const OzUpdate none{nullptr, 0, nullptr, 0};
   if (p->ng == 5)
-    k_gram_oz<5><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<5>(), st>>>(
-        p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, status);
+    k_gram_oz<4, 5, false><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<4, 5>(), st>>>(
+        p->mapA, p->mapB, p->d_tiles, p->m, 0, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, none, status);
   else
-    k_gram_oz<6><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<6>(), st>>>(
-        p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, status);
+    k_gram_oz<4, 6, false><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<4, 6>(), st>>>(
+        p->mapA, p->mapB, p->d_tiles, p->m, 0, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, none, status);
   DNGD_LAUNCH_CHECK();
   if (ev_after_mma) cudaEventRecord(ev_after_mma, st);
   return gram_oz_reduce(p, st);
@@ -684,7 +728,7 @@ dngd_status gram_oz_reduce(OzPlan* p, cudaStream_t st) {
   const int nb = (p->m + 31) / 32;
   DNGD_NOTE_LAUNCH();
   k_oz_reduce<<<nb * (nb + 1) / 2, 256, 0, st>>>(p->m, p->nsplit, p->partials, p->ldp, p->sstride, p->rowexp,
-                                                 16 + 8 * (p->ng - 1), p->shift, p->K, p->ldk, p->F, p->ldf);
+                                                 16 + 8 * (p->ng - 1), p->shift, p->K, p->ldk, p->F, p->ldf, p->Kd);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
@@ -705,6 +749,140 @@ void gram_oz_free(OzPlan* p) {
 }
 
 int gram_oz_nsplit(const OzPlan* p) { return p->nsplit; }
+
+void gram_oz_set_fp64_out(OzPlan* p, double* Kd) { p->Kd = Kd; }
+
+// ---------------------------------------------------------------------------
+// FP64 blocked Cholesky with exact sliced trailing updates
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int FNS = 6, FNG = 7;                       // six slices, levels <= 6
+constexpr int FNB = 64;                               // columns per step (the K extent of an update)
+constexpr int FLD = FNS * FNB;                        // slice row: 6 x 64 BF16
+
+// Rows i in [row0, m): the panel C[i, k0 .. k0 + kb) as six 8-bit slices of
+// 64 columns (zero beyond kb) and the row exponent E_i (|C| / 2^E_i < 0.5,
+// entries kept to 2^(E_i - 49)).  One warp per row.
+__global__ void __launch_bounds__(256) k_panel_slice(int m, int row0, int k0, int kb, const double* __restrict__ C,
+                                                     long long ldc, __nv_bfloat16* __restrict__ S,
+                                                     int* __restrict__ rowexp, const int* __restrict__ status) {
+  if (status[0] & ST_NOT_SPD) return;   // the factorisation already failed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = row0 + blockIdx.x * 8 + warp;
+  if (row >= m) return;
+  const double* cr = C + (long long)row * ldc + k0;
+  double x0 = lane < kb ? cr[lane] : 0.0;
+  double x1 = lane + 32 < kb ? cr[lane + 32] : 0.0;
+  double a = fmax(fabs(x0), fabs(x1));
+  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+  int e = 0;
+  if (a > 0.0 && isfinite(a)) frexp(a, &e);   // a = f 2^e, f in [0.5, 1)
+  const int E = e + 1;
+  if (lane == 0) rowexp[row] = E;
+  x0 = ldexp(x0, -E);
+  x1 = ldexp(x1, -E);
+  __nv_bfloat16* sr = S + (long long)row * FLD;
+#pragma unroll
+  for (int s = 0; s < FNS; ++s) {
+    const double t0 = x0 * 256.0, t1 = x1 * 256.0;
+    const double g0 = rint(t0), g1 = rint(t1);
+    x0 = t0 - g0;
+    x1 = t1 - g1;
+    sr[s * FNB + lane] = __float2bfloat16_rn((float)g0);
+    sr[s * FNB + lane + 32] = __float2bfloat16_rn((float)g1);
+  }
+}
+
+}  // namespace
+
+struct OzFactor {
+  int m;
+  double* C;
+  long long ldc;
+  __nv_bfloat16* S;
+  int* rowexp;
+  int2* d_tiles;
+  std::vector<int> prefix;   // tiles with row block < I, for I = 0 .. nI
+  CUtensorMap mapA, mapB;
+};
+
+size_t oz_factor_bytes(int m) {
+  const int nI = (m + TM - 1) / TM, nJ = (m + OzCfg<FNS, FNG>::TN - 1) / OzCfg<FNS, FNG>::TN;
+  return (size_t)m * FLD * sizeof(__nv_bfloat16) + (size_t)m * sizeof(int) + (size_t)nI * nJ * sizeof(int2) + 1024;
+}
+
+dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void* work) {
+  EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
+  if (!enc) return DNGD_ERR_CUDA;
+  constexpr int TN = OzCfg<FNS, FNG>::TN;
+  OzFactor* p = new OzFactor();
+  p->m = m;
+  p->C = C;
+  p->ldc = ldc;
+  p->S = (__nv_bfloat16*)work;
+  p->rowexp = (int*)((char*)work + (size_t)m * FLD * sizeof(__nv_bfloat16));
+  p->d_tiles = (int2*)(((uintptr_t)(p->rowexp + m) + 255) & ~(uintptr_t)255);
+  // lower tiles, row blocks in order: the tiles of a trailing block of r
+  // rows are the first prefix[ceil(r / TM)] entries (the few that reach
+  // past r are masked in the epilogue)
+  std::vector<int2> tiles;
+  const int nI = (m + TM - 1) / TM, nJ = (m + TN - 1) / TN;
+  p->prefix.assign(nI + 1, 0);
+  for (int I = 0; I < nI; ++I) {
+    for (int Jc = 0; Jc < nJ && Jc * TN <= I * TM + TM - 1; ++Jc) tiles.push_back(make_int2(I, Jc));
+    p->prefix[I + 1] = (int)tiles.size();
+  }
+  cuuint64_t gdim[2] = {(cuuint64_t)FLD, (cuuint64_t)m};
+  cuuint64_t gstride[1] = {(cuuint64_t)(FLD * 2)};
+  cuuint32_t estride[2] = {1, 1};
+  cuuint32_t boxA[2] = {(cuuint32_t)KS, (cuuint32_t)TM};
+  cuuint32_t boxB[2] = {(cuuint32_t)KS, (cuuint32_t)TN};
+  if (enc(&p->mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S, gdim, gstride, boxA, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&p->mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S, gdim, gstride, boxB, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    delete p;
+    return DNGD_ERR_CUDA;
+  }
+  if (cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    delete p;
+    return DNGD_ERR_CUDA;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gram_oz<FNS, FNG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<FNS, FNG>());
+    attr = true;
+  }
+  *out = p;
+  return DNGD_OK;
+}
+
+dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
+  const int m = p->m;
+  const OzUpdate upd{p->C, p->ldc, p->rowexp, 16 + 8 * (FNG - 1)};
+  for (int k0 = 0; k0 < m; k0 += FNB) {
+    dngd_status s = chol_step_f64(m, k0, p->C, p->ldc, status, st);
+    if (s) return s;
+    const int kb = (m - k0) < FNB ? (m - k0) : FNB;
+    const int row0 = k0 + kb, r = m - row0;
+    if (r <= 0) break;
+    DNGD_NOTE_LAUNCH();
+    k_panel_slice<<<(r + 7) / 8, 256, 0, st>>>(m, row0, k0, kb, p->C, p->ldc, p->S, p->rowexp, status);
+    DNGD_LAUNCH_CHECK();
+    const int ntiles = p->prefix[(r + TM - 1) / TM];
+    DNGD_NOTE_LAUNCH();
+    k_gram_oz<FNS, FNG, true><<<dim3(ntiles, 1), OTHREADS, osmem<FNS, FNG>(), st>>>(
+        p->mapA, p->mapB, p->d_tiles, r, row0, FNB / KS, FNB, nullptr, 0, 0, upd, status);
+    DNGD_LAUNCH_CHECK();
+  }
+  return DNGD_OK;
+}
+
+void oz_factor_free(OzFactor* p) { delete p; }
 
 unsigned* gram_oz_rowmax(OzPlan* p) { return p->rowmax; }
 

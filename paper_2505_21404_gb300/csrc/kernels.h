@@ -89,6 +89,14 @@ dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* 
 // Inverses of the 64 x 64 diagonal blocks of an FP64 factor ([ceil(m/64)] x
 // 64 x 64) and the blocked solve that uses them (w, y: work vectors [m]).
 dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cudaStream_t st);
+// One 64-column step of the FP64 blocked Cholesky (diagonal block at k0 and
+// the panel solve below it; no trailing update).  A non-positive pivot sets
+// ST_NOT_SPD and status[1] = column.
+dngd_status chol_step_f64(int m, int k0, double* A, long long lda, int* status, cudaStream_t st);
+// L32 = fl32(L) (lower) and the diagonal 64-blocks of Linv = fl32(Dinv),
+// zero elsewhere (ldi = ldk).
+dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* Dinv, float* L32, long long ldk,
+                          float* Linv, long long ldi, cudaStream_t st);
 dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const double* Dinv, const double* b, double* x,
                                 double* w, double* y, cudaStream_t st);
 
@@ -154,6 +162,19 @@ unsigned* gram_oz_rowmax(OzPlan* plan);
 dngd_status gram_oz_reduce(OzPlan* plan, cudaStream_t st);
 void gram_oz_free(OzPlan* plan);
 int gram_oz_nsplit(const OzPlan* plan);
+// The exact Gram's reduction also writes K + shift as FP64 (lower) into Kd
+// when set (the FP64 factorisation's input), or not when Kd is null.
+void gram_oz_set_fp64_out(OzPlan* plan, double* Kd);
+
+// FP64 blocked Cholesky (64-column steps) of the lower triangle of C in
+// place, its trailing updates done exactly from six 8-bit slices per entry
+// of the panel on the BF16 tensor cores (products of levels <= 6, each entry
+// of the panel kept to 2^-49 of its row's largest).
+struct OzFactor;
+size_t oz_factor_bytes(int m);   // panel slices + row exponents + tile list
+dngd_status oz_factor_plan(OzFactor** plan, int m, double* C, long long ldc, void* work);
+dngd_status oz_factor_run(OzFactor* plan, int* status, cudaStream_t st);
+void oz_factor_free(OzFactor* plan);
 
 // Explicit inverse of a lower-triangular FP32 factor: Linv = L^{-1} (lower).
 dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,

@@ -340,6 +340,29 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 
 template dngd_status cholesky<double>(int, double*, long long, int*, double*, cudaStream_t);
 
+// One 64-column step of the FP64 blocked Cholesky without its trailing
+// update: factor the diagonal block at k0 and solve the panel below it.
+dngd_status chol_step_f64(int m, int k0, double* A, long long lda, int* status, cudaStream_t st) {
+  const int trsm_smem = 2 * kCholNB * (kCholNB + 1) * (int)sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    DNGD_CUDA_CHECK(
+        cudaFuncSetAttribute(k_trsm_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem));
+    attr_set = true;
+  }
+  const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
+  DNGD_NOTE_LAUNCH();
+  k_potrf_diag<double><<<1, 256, 0, st>>>(k0, kb, A, lda, status);
+  DNGD_LAUNCH_CHECK();
+  const int rest = m - k0 - kb;
+  if (rest > 0) {
+    DNGD_NOTE_LAUNCH();
+    k_trsm_panel<double><<<cdiv(rest, 64), 64, trsm_smem, st>>>(m, k0, kb, A, lda, status);
+    DNGD_LAUNCH_CHECK();
+  }
+  return DNGD_OK;
+}
+
 // ---------------------------------------------------------------------------
 // FP32 factorisation for the mixed path (a preconditioner, whose accuracy the
 // refinement restores).  One kernel factors a 64 x 64 diagonal block and
@@ -799,6 +822,33 @@ __global__ void __launch_bounds__(256) k_trsv_bwd_step(int k0, int kb, const dou
   double s = 0.0;
   for (int j = 0; j < kb; ++j) s += L[(long long)(k0 + j) * ldl + i] * yb[j];
   w[i] -= s;
+}
+
+// The FP64 factor as the FP32 preconditioner's inputs: L32 = fl32(L) (lower,
+// upper set to zero) and the diagonal 64-blocks of Linv = fl32(Dinv) (the
+// rest of Linv zero, for trtri_offdiag_f32 to fill).
+__global__ void k_factor_to_f32(int m, const double* __restrict__ L, long long ldl, const double* __restrict__ Dinv,
+                                float* __restrict__ L32, long long ldk, float* __restrict__ Linv, long long ldi) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int cols = (int)ldk;
+  if (idx >= (long long)m * cols) return;
+  const int i = (int)(idx / cols), j = (int)(idx % cols);
+  L32[(long long)i * ldk + j] = (j <= i) ? (float)L[(long long)i * ldl + j] : 0.f;
+  float d = 0.f;
+  if (j <= i && j / kTrsvNB == i / kTrsvNB) {
+    const int b = i / kTrsvNB;
+    d = (float)Dinv[(long long)b * kTrsvNB * kTrsvNB + (i - b * kTrsvNB) * kTrsvNB + (j - b * kTrsvNB)];
+  }
+  if (j < (int)ldi) Linv[(long long)i * ldi + j] = d;
+}
+
+dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* Dinv, float* L32, long long ldk,
+                          float* Linv, long long ldi, cudaStream_t st) {
+  const long long cnt = (long long)m * ldk;
+  DNGD_NOTE_LAUNCH();
+  k_factor_to_f32<<<(int)((cnt + 255) / 256), 256, 0, st>>>(m, L, ldl, Dinv, L32, ldk, Linv, ldi);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
 }
 
 dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cudaStream_t st) {
