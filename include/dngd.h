@@ -270,7 +270,11 @@ dngd_status dngd_fvv(dngd_ctx* ctx, const double* theta, const double* X, const 
  *         7 Cholesky factor L [m x m] row-major (dense solver),
  *         8 landmark columns K_{:,I} [m x ell] row-major (PCG solver),
  *         9 exact Gram J J^T [m x m] row-major, full symmetric, no lambda
- *           (DNGD_MIXED_OZ).
+ *           (DNGD_MIXED_OZ, DNGD_MIXED_OZ64),
+ *        10 the preconditioner's explicit inverse factor L^{-1} [m x m]
+ *           row-major lower (mixed paths, FP32 values),
+ *        11 the FP64 Cholesky factor of the exact Gram + (lambda + mu) I
+ *           [m x m] row-major lower (DNGD_MIXED_OZ, DNGD_MIXED_OZ64).
  * Values are converted to float64. */
 dngd_status dngd_get_stage(dngd_ctx* ctx, int which, double* dst);
 

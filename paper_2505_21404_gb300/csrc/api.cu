@@ -56,6 +56,9 @@ struct dngd_ctx {
   float* trtri_work = nullptr;
   OzPlan* oz = nullptr;       // exact-Gram mode
   OzFactor* ozf = nullptr;    // its FP64 factorisation (exact sliced trailing updates)
+  OzGemm* ozg = nullptr;      // FP64 jets' layer GEMMs from exact slice products (MIXED_OZ64)
+  void* ozg_work = nullptr;
+  Tc3Scratch ozs;             // hands ozg to the FP64 jets
   double* Kd = nullptr;       // exact Gram + (lambda + mu) I, FP64 lower: factored in place
   void* ozf_work = nullptr;
   void* oz_slices = nullptr;
@@ -312,9 +315,17 @@ dngd_status forward_only(dngd_ctx* c, const T* thT, const double* X, const doubl
 // run on the TF32 tensor cores (3xTF32) when the context has the scratch.
 const Tc3Scratch* tc3p(dngd_ctx* c);
 
+// The tensor-core GEMM handle of the jets: 3xTF32 (FP32 jets) or the FP64
+// GEMM from slice products (FP64 jets of MIXED_OZ64); null: SIMT GEMMs.
+template <typename T>
+const Tc3Scratch* jets_tc(dngd_ctx* c) {
+  if (std::is_same<T, float>::value) return tc3p(c);
+  return c->ozg ? &c->ozs : nullptr;
+}
+
 template <typename T>
 dngd_status residual_jacobian_T(dngd_ctx* c, const T* thT, const double* X, const double* target) {
-  const Tc3Scratch* t3 = std::is_same<T, float>::value ? tc3p(c) : nullptr;
+  const Tc3Scratch* t3 = jets_tc<T>(c);
   dngd_status s = jets_forward<T>(c->net, thT, X, target, lp<T>(c->Z), lp<T>(c->H), c->r, c->status, c->st, t3,
                                   true);
   if (s) return s;
@@ -567,8 +578,8 @@ factored:
       to_float(n, c->v, c->v32, c->st);
       vT = (const T*)c->v32;
     }
-    if ((s = jets_fvv<T>(c->net, thT, vT, X, (T*)c->Z3, (T*)c->H3a, (T*)c->H3b, c->fvv, c->st,
-                         std::is_same<T, float>::value ? tc3p(c) : nullptr, c->status)))
+    if ((s = jets_fvv<T>(c->net, thT, vT, X, (T*)c->Z3, (T*)c->H3a, (T*)c->H3b, c->fvv, c->st, jets_tc<T>(c),
+                         c->status)))
       return s;
     evrec(c, 5);
     if ((s = solve_last(c, c->fvv, c->beta, 1))) return s;
@@ -971,6 +982,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       add(sizeof(double) * (size_t)m * c->ldk);                                  // Kd
       add(sizeof(double) * (size_t)cdiv(m, 64) * 64 * 64);                       // Dinv
       add(oz_factor_bytes(m));
+      if (j64) add(oz_gemm_bytes(3 * net.R, net.max_w, net.max_w));              // FP64 jets' GEMMs
     } else {
       add(gram_tc_partial_bytes(m, (int)n));
     }
@@ -1058,6 +1070,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       A_(c->Kd, double, (size_t)m * c->ldk);
       A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
       A_(c->ozf_work, unsigned char, oz_factor_bytes(m));
+      if (j64) A_(c->ozg_work, unsigned char, oz_gemm_bytes(3 * net.R, net.max_w, net.max_w));
     } else {
       c->gram_partial_bytes = gram_tc_partial_bytes(m, (int)n);
       A_(c->gram_partials, float, c->gram_partial_bytes / sizeof(float));
@@ -1094,6 +1107,10 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     if (s) return s;
     gram_oz_set_fp64_out(c->oz, c->Kd);
     if ((s = oz_factor_plan(&c->ozf, m, c->Kd, c->ldk, c->ozf_work))) return s;
+    if (c->ozg_work) {
+      if ((s = oz_gemm_plan(&c->ozg, 3 * net.R, net.max_w, net.max_w, c->ozg_work))) return s;
+      c->ozs.ozg = c->ozg;
+    }
   } else if (!f64) {
     const void* Jlow = bf ? (const void*)c->Jb : (const void*)c->J;
     const long long ld = bf ? c->ldb : c->ldJ;
@@ -1122,6 +1139,7 @@ void free_ctx(dngd_ctx* c) {
   if (c->gram) gram_tc_free(c->gram);
   if (c->oz) gram_oz_free(c->oz);
   if (c->ozf) oz_factor_free(c->ozf);
+  if (c->ozg) oz_gemm_free(c->ozg);
   for (int i = 0; i < 9; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (int i = 0; i < 4; ++i)
@@ -1309,7 +1327,8 @@ dngd_status dngd_fvv(dngd_ctx* c, const double* theta, const double* X, const do
   const double* vv = in_ptr(c, v, c->nvec_s, c->n);
   dngd_status s;
   if (jets64(c->prec)) {
-    s = jets_fvv<double>(c->net, th, vv, x, (double*)c->Z3, (double*)c->H3a, (double*)c->H3b, c->fvv, c->st);
+    s = jets_fvv<double>(c->net, th, vv, x, (double*)c->Z3, (double*)c->H3a, (double*)c->H3b, c->fvv, c->st,
+                         jets_tc<double>(c), c->status);
   } else {
     const float* t32 = theta_in_T<float>(c, th);
     to_float(c->n, vv, c->v32, c->st);
@@ -1432,10 +1451,14 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
     case 4: return out_copy(c, dst, c->beta, m);
     case 5: return out_copy(c, dst, c->a, c->n);
     case 6:
-    case 7: {
-      const void* src = which == 6 ? c->Kcopy : c->K;
+    case 7:
+    case 10:
+    case 11: {
+      // 7: the FP64 path's factor; 10: the explicit inverse factor of the
+      // mixed paths (FP32); 11: the exact-Gram modes' FP64 factor
+      const void* src = which == 6 ? c->Kcopy : which == 7 ? c->K : which == 10 ? (void*)c->Linv : (void*)c->Kd;
       if (!src) return DNGD_ERR_STATE;
-      const bool k64 = c->prec == DNGD_FP64;
+      const bool k64 = which == 11 || (which != 10 && c->prec == DNGD_FP64);
       if (which == 7 && !k64) return DNGD_ERR_STATE;
       double* buf = nullptr;
       if (cudaMalloc(&buf, sizeof(double) * (size_t)m * m) != cudaSuccess) return DNGD_ERR_OOM;

@@ -155,14 +155,22 @@ __device__ __forceinline__ uint32_t oz_idesc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
-// The factorisation's trailing update, done in the epilogue instead of
-// writing partial tiles: C[i, j] -= 2^(E_i + E_j - eshift) acc for the
-// entries j <= i of the trailing block (rows and columns row_off + index).
-struct OzUpdate {
+// Epilogue modes of the sliced product kernel:
+//   OZ_PARTIAL  the tile's raw level sum into the split-K partial tiles;
+//   OZ_UPDATE   the factorisation's trailing update C[i, j] -= 2^(E_i + E_j -
+//               eshift) acc for the entries j <= i of the trailing block
+//               (rows and columns row_off + index, exponents rexpA);
+//   OZ_GEMM     C[i, j] = alpha 2^(EA_i + EB_j - eshift) acc + beta C[i, j]
+//               (i < m, j < ncols; tiles from blockIdx, ntn column tiles).
+enum { OZ_PARTIAL = 0, OZ_UPDATE = 1, OZ_GEMM = 2 };
+struct OzEpi {
   double* C;
   long long ldc;
-  const int* rowexp;
+  const int* rexpA;
+  const int* rexpB;
   int eshift;
+  int ncols, ntn;
+  double alpha, beta;
 };
 
 // (hi, lo) += c exactly as long as the sum needs at most ~48 bits.
@@ -232,15 +240,14 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const TJ* __rest
   }
 }
 
-// One CTA per (output tile, K split).  m: rows of the (trailing) matrix;
-// its row and column i sit at slice row row_off + i.  UPD: the epilogue
-// applies the factorisation update (OzUpdate) instead of writing the partial
-// tile to out.
-template <int NS, int NG, bool UPD>
+// One CTA per (output tile, K split).  m: rows of the output (for the
+// Gram and the update also its columns); its row i sits at slice row
+// row_off + i.  MODE: the epilogue (OZ_PARTIAL, OZ_UPDATE, OZ_GEMM).
+template <int NS, int NG, int MODE>
 __global__ void __launch_bounds__(OTHREADS, 1)
 k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           const int2* __restrict__ tiles, int m, int row_off, int num_kblk, int ldb, double* __restrict__ out,
-          long long ldo, long long split_stride, OzUpdate upd, int* status) {
+          long long ldo, long long split_stride, OzEpi epi, int* status) {
   constexpr int TN = OzCfg<NS, NG>::TN, OST = OzCfg<NS, NG>::OST;
   constexpr int B_TILE = b_tile<NS, NG>(), OSTAGE = ostage<NS, NG>();
   extern __shared__ unsigned char smem_raw[];
@@ -254,7 +261,8 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const int2 tile = tiles[blockIdx.x];
+  const int2 tile = MODE == OZ_GEMM ? make_int2((int)blockIdx.x / epi.ntn, (int)blockIdx.x % epi.ntn)
+                                    : tiles[blockIdx.x];
   const int split = blockIdx.y, nsplit = gridDim.y;
   const int kb_per = (num_kblk + nsplit - 1) / nsplit;
   const int kb0 = split * kb_per;
@@ -444,15 +452,26 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
     const int row = tile.x * TM + q * 32 + lane;
     const int col0 = tile.y * TN + cg * 32;
-    if (UPD) {
+    if (MODE == OZ_UPDATE) {
       if (row < m && !*abort_flag) {
         const int gr = row_off + row;
-        const int er = upd.rowexp[gr];
-        double* crow = upd.C + (long long)gr * upd.ldc + row_off + col0;
+        const int er = epi.rexpA[gr];
+        double* crow = epi.C + (long long)gr * epi.ldc + row_off + col0;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if (j < ncol && col0 + j <= row)
-            crow[j] -= ldexp((double)hi[j] + (double)lo[j], er + upd.rowexp[row_off + col0 + j] - upd.eshift);
+            crow[j] -= ldexp((double)hi[j] + (double)lo[j], er + epi.rexpA[row_off + col0 + j] - epi.eshift);
+      }
+    } else if (MODE == OZ_GEMM) {
+      if (row < m && !*abort_flag) {
+        const int er = epi.rexpA[row];
+        double* crow = epi.C + (long long)row * epi.ldc + col0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < ncol && col0 + j < epi.ncols) {
+            const double v = epi.alpha * ldexp((double)hi[j] + (double)lo[j], er + epi.rexpB[col0 + j] - epi.eshift);
+            crow[j] = epi.beta == 0.0 ? v : v + epi.beta * crow[j];
+          }
       }
     } else if (row < m && !*abort_flag) {
       double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0;
@@ -683,11 +702,11 @@ dngd_status gram_oz_plan(OzPlan** out, const void* J, bool j64, int ng, long lon
   cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
   static bool attr5 = false, attr6 = false;
   if (ng == 5 && !attr5) {
-    cudaFuncSetAttribute(k_gram_oz<4, 5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 5>());
+    cudaFuncSetAttribute(k_gram_oz<4, 5, OZ_PARTIAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 5>());
     attr5 = true;
   }
   if (ng == 6 && !attr6) {
-    cudaFuncSetAttribute(k_gram_oz<4, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 6>());
+    cudaFuncSetAttribute(k_gram_oz<4, 6, OZ_PARTIAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 6>());
     attr6 = true;
   }
   *out = p;
@@ -709,12 +728,12 @@ dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_
                                              p->rowmax, p->rowexp);
   DNGD_LAUNCH_CHECK();
   DNGD_NOTE_LAUNCH();
-  const OzUpdate none{nullptr, 0, nullptr, 0};
+  const OzEpi none{nullptr, 0, nullptr, nullptr, 0, 0, 0, 0.0, 0.0};
   if (p->ng == 5)
-    k_gram_oz<4, 5, false><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<4, 5>(), st>>>(
+    k_gram_oz<4, 5, OZ_PARTIAL><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<4, 5>(), st>>>(
         p->mapA, p->mapB, p->d_tiles, p->m, 0, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, none, status);
   else
-    k_gram_oz<4, 6, false><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<4, 6>(), st>>>(
+    k_gram_oz<4, 6, OZ_PARTIAL><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<4, 6>(), st>>>(
         p->mapA, p->mapB, p->d_tiles, p->m, 0, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, none, status);
   DNGD_LAUNCH_CHECK();
   if (ev_after_mma) cudaEventRecord(ev_after_mma, st);
@@ -854,7 +873,8 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gram_oz<FNS, FNG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<FNS, FNG>());
+    cudaFuncSetAttribute(k_gram_oz<FNS, FNG, OZ_UPDATE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         osmem<FNS, FNG>());
     attr = true;
   }
   *out = p;
@@ -863,7 +883,7 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
 
 dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
   const int m = p->m;
-  const OzUpdate upd{p->C, p->ldc, p->rowexp, 16 + 8 * (FNG - 1)};
+  const OzEpi upd{p->C, p->ldc, p->rowexp, nullptr, 16 + 8 * (FNG - 1), 0, 0, 0.0, 0.0};
   for (int k0 = 0; k0 < m; k0 += FNB) {
     dngd_status s = chol_step_f64(m, k0, p->C, p->ldc, status, st);
     if (s) return s;
@@ -875,7 +895,7 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
     DNGD_LAUNCH_CHECK();
     const int ntiles = p->prefix[(r + TM - 1) / TM];
     DNGD_NOTE_LAUNCH();
-    k_gram_oz<FNS, FNG, true><<<dim3(ntiles, 1), OTHREADS, osmem<FNS, FNG>(), st>>>(
+    k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(ntiles, 1), OTHREADS, osmem<FNS, FNG>(), st>>>(
         p->mapA, p->mapB, p->d_tiles, r, row0, FNB / KS, FNB, nullptr, 0, 0, upd, status);
     DNGD_LAUNCH_CHECK();
   }
@@ -883,6 +903,113 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
 }
 
 void oz_factor_free(OzFactor* p) { delete p; }
+
+// ---------------------------------------------------------------------------
+// FP64 GEMM from exact slice products: C = alpha A B^T + beta C
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Rows of A [M x K] (ld lda), or with cols the columns of a [K x M] matrix,
+// as four 8-bit slices of kp columns (zero beyond K) and the row exponent.
+// One warp per row; two passes over the row (its largest |A|, then slices).
+__global__ void __launch_bounds__(256) k_slice_rows_f64(int M, int K, int kp, const double* __restrict__ A,
+                                                        long long lda, bool cols, __nv_bfloat16* __restrict__ S,
+                                                        int* __restrict__ rexp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  if (row >= M) return;
+  auto at = [&](int k) -> double { return cols ? A[(long long)k * lda + row] : A[(long long)row * lda + k]; };
+  double a = 0.0;
+  for (int k = lane; k < K; k += 32) a = fmax(a, fabs(at(k)));
+  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+  int e = 0;
+  if (a > 0.0 && isfinite(a)) frexp(a, &e);
+  const int E = e + 1;
+  if (lane == 0) rexp[row] = E;
+  __nv_bfloat16* sr = S + (long long)row * 4 * kp;
+  for (int k = lane; k < kp; k += 32) {
+    double x = k < K ? ldexp(at(k), -E) : 0.0;
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+      const double t = x * 256.0;
+      const double g = rint(t);
+      x = t - g;
+      sr[sl * kp + k] = __float2bfloat16_rn((float)g);
+    }
+  }
+}
+
+}  // namespace
+
+struct OzGemm {
+  int max_m, max_n, kp;
+  __nv_bfloat16 *SA, *SB;
+  int *ea, *eb;
+  CUtensorMap mapA, mapB;
+};
+
+size_t oz_gemm_bytes(int max_m, int max_n, int max_k) {
+  const size_t kp = (size_t)((max_k + 63) / 64) * 64;
+  return ((size_t)max_m + max_n) * 4 * kp * sizeof(__nv_bfloat16) + ((size_t)max_m + max_n) * sizeof(int) + 1024;
+}
+
+dngd_status oz_gemm_plan(OzGemm** out, int max_m, int max_n, int max_k, void* work) {
+  EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
+  if (!enc) return DNGD_ERR_CUDA;
+  OzGemm* p = new OzGemm();
+  p->max_m = max_m;
+  p->max_n = max_n;
+  p->kp = ((max_k + 63) / 64) * 64;
+  p->SA = (__nv_bfloat16*)work;
+  p->SB = p->SA + (size_t)max_m * 4 * p->kp;
+  p->ea = (int*)(p->SB + (size_t)max_n * 4 * p->kp);
+  p->eb = p->ea + max_m;
+  constexpr int TN = OzCfg<4, 5>::TN;
+  cuuint64_t gA[2] = {(cuuint64_t)(4 * p->kp), (cuuint64_t)max_m};
+  cuuint64_t gB[2] = {(cuuint64_t)(4 * p->kp), (cuuint64_t)max_n};
+  cuuint64_t stride[1] = {(cuuint64_t)(4 * p->kp * 2)};
+  cuuint32_t estride[2] = {1, 1};
+  cuuint32_t boxA[2] = {(cuuint32_t)KS, (cuuint32_t)TM};
+  cuuint32_t boxB[2] = {(cuuint32_t)KS, (cuuint32_t)TN};
+  if (enc(&p->mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->SA, gA, stride, boxA, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&p->mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->SB, gB, stride, boxB, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    delete p;
+    return DNGD_ERR_CUDA;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gram_oz<4, 5, OZ_GEMM>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 5>());
+    attr = true;
+  }
+  *out = p;
+  return DNGD_OK;
+}
+
+dngd_status oz_gemm(OzGemm* p, int M, int N, int K, double alpha, const double* A, long long lda, const double* B,
+                    long long ldb, bool b_kn, double beta, double* C, long long ldc, int* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DNGD_OK;
+  if (M > p->max_m || N > p->max_n || K > p->kp || K <= 0) return DNGD_ERR_INVALID_ARG;
+  constexpr int TN = OzCfg<4, 5>::TN;
+  DNGD_NOTE_LAUNCH();
+  k_slice_rows_f64<<<(M + 7) / 8, 256, 0, st>>>(M, K, p->kp, A, lda, false, p->SA, p->ea);
+  DNGD_NOTE_LAUNCH();
+  k_slice_rows_f64<<<(N + 7) / 8, 256, 0, st>>>(N, K, p->kp, B, ldb, b_kn, p->SB, p->eb);
+  DNGD_LAUNCH_CHECK();
+  const int ntn = (N + TN - 1) / TN, ntm = (M + TM - 1) / TM;
+  const OzEpi epi{C, ldc, p->ea, p->eb, 16 + 8 * 4, N, ntn, alpha, beta};
+  DNGD_NOTE_LAUNCH();
+  k_gram_oz<4, 5, OZ_GEMM><<<dim3(ntm * ntn, 1), OTHREADS, osmem<4, 5>(), st>>>(
+      p->mapA, p->mapB, nullptr, M, 0, (K + KS - 1) / KS, p->kp, nullptr, 0, 0, epi, status);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+void oz_gemm_free(OzGemm* p) { delete p; }
 
 unsigned* gram_oz_rowmax(OzPlan* p) { return p->rowmax; }
 

@@ -511,6 +511,11 @@ static dngd_status layer_gemm(int M, int N, int K, T alpha, const T* A, int lda,
           gemm_tc3(M, N, K, alpha, A, lda, false, B, ldb, b_kn, beta, C, ldc, false, *tc3, status, st);
       if (s != DNGD_ERR_INVALID_ARG) return s;
     }
+  } else {
+    if (tc3 && tc3->ozg && status) {
+      const dngd_status s = oz_gemm(tc3->ozg, M, N, K, alpha, A, lda, B, ldb, b_kn, beta, C, ldc, status, st);
+      if (s != DNGD_ERR_INVALID_ARG) return s;
+    }
   }
   return b_kn ? gemm_nn<T>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st)
               : gemm_nt<T>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, false, st);
@@ -555,8 +560,9 @@ dngd_status jets_forward(const NetInfo& net, const T* theta, const double* X, co
                        net.widths[l], false, 0.0f, Z.p[l], w, false, *tc3, status, st);
       }
       if (s == DNGD_ERR_INVALID_ARG && !presplit)
-        s = gemm_nt<T>(net.R, w, net.widths[l], T(1), H.p[l - 1], net.widths[l], theta + net.w_off[l],
-                       net.widths[l], T(0), Z.p[l], w, false, st);
+        s = layer_gemm<T>(net.R, w, net.widths[l], T(1), H.p[l - 1], net.widths[l], theta + net.w_off[l],
+                          net.widths[l], false, T(0), Z.p[l], w, std::is_same<T, float>::value ? nullptr : tc3,
+                          status, st);
       if (s) return s;
       DNGD_NOTE_LAUNCH();
       k_act_fwd<T><<<grid, thr, 0, st>>>(net, l, theta, Z.p[l], H.p[l], hs, kp);

@@ -115,9 +115,11 @@ dngd_status pcg_persist_solve(int m, const float2* K, long long ldk, double lamb
                               int* status, cudaStream_t st);
 
 // ---- tc3.cu: FP32 GEMM on TF32 tensor cores with hi/lo splits -----------
+struct OzGemm;
 struct Tc3Scratch {
   float* buf = nullptr;
   size_t bytes = 0;
+  OzGemm* ozg = nullptr;   // FP64 layer GEMMs from exact slice products (FP64 jets)
 };
 size_t tc3_scratch_bytes(int M, int N, int K);
 // The scratch's two halves: the A operand's split [M x 2 Kp] and the B
@@ -175,6 +177,17 @@ size_t oz_factor_bytes(int m);   // panel slices + row exponents + tile list
 dngd_status oz_factor_plan(OzFactor** plan, int m, double* C, long long ldc, void* work);
 dngd_status oz_factor_run(OzFactor* plan, int* status, cudaStream_t st);
 void oz_factor_free(OzFactor* plan);
+
+// C = alpha A B^T + beta C in FP64 (A [M x K] ld lda; B [N x K] ld ldb, or
+// with b_kn B given as [K x N]) from four 8-bit slices of every row of A and
+// of B^T on the BF16 tensor cores (13 slice products): each entry of A and B
+// kept to 2^-33 of its row's largest, the products exact, so C is accurate
+// to ~2^-33 of the row scales times K.  M, N, K within the plan's capacity.
+size_t oz_gemm_bytes(int max_m, int max_n, int max_k);
+dngd_status oz_gemm_plan(OzGemm** plan, int max_m, int max_n, int max_k, void* work);
+dngd_status oz_gemm(OzGemm* plan, int M, int N, int K, double alpha, const double* A, long long lda, const double* B,
+                    long long ldb, bool b_kn, double beta, double* C, long long ldc, int* status, cudaStream_t st);
+void oz_gemm_free(OzGemm* plan);
 
 // Explicit inverse of a lower-triangular FP32 factor: Linv = L^{-1} (lower).
 dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,

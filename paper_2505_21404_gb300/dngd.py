@@ -27,7 +27,7 @@ STATUS = {
     -8: "DNGD_ERR_STATE", -9: "DNGD_ERR_OOM",
 }
 
-STAGES = dict(r=0, alpha=1, v=2, fvv=3, beta=4, a=5, gram=6, chol=7, kci=8, gram64=9)
+STAGES = dict(r=0, alpha=1, v=2, fvv=3, beta=4, a=5, gram=6, chol=7, kci=8, gram64=9, linv=10, chol64=11)
 
 
 class DngdError(RuntimeError):
