@@ -497,8 +497,11 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     c->shift_used = mu;
     if ((s = trtri_diag64(m, c->Kd, c->ldk, c->Dinv, c->st))) return s;
     if ((s = factor_to_f32(m, c->Kd, c->ldk, c->Dinv, (float*)c->K, c->ldk, c->Linv, c->ldk, c->st))) return s;
-    if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st, tc3p(c),
-                               c->status)))
+    // the inverse of this factor (cond ~ sqrt of K's, up to ~1e5) on FP32
+    // SIMT GEMMs with round-to-nearest accumulation: the 3xTF32 products
+    // accumulate in TMEM over up to m/2 terms and lose too much here
+    if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st, nullptr,
+                               nullptr)))
       return s;
     if (c->LinvT && (s = transpose_f32(m, c->Linv, c->ldk, c->LinvT, c->ldk, c->st))) return s;
     if (c->async) goto factored;

@@ -184,6 +184,40 @@ __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
   hi = t;
 }
 
+// The ND balanced base-256 digits of v = round(x 2^(8 ND - E)) for a double
+// x with |x| < 2^(E - 1), from x's bits with integer operations only (FP64
+// arithmetic is slow on this GPU): x 2^-E = sum_s d_s 2^-8(s+1) to within
+// 2^-(8 ND + 1), every |d_s| <= 128 (so exact in BF16).  Zero and
+// subnormal x give zero digits (subnormals lie far below that bound).
+template <int ND>
+__device__ __forceinline__ void oz_digits(double x, int E, float (&d)[ND]) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long v = 0;
+  if (ex != 0 && ex != 0x7FF) {
+    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+    const int sh = 1075 - ex - 8 * ND + E;   // >= 6 for |x| < 2^(E - 1) and ND <= 6
+    v = (sh >= 1 && sh < 64) ? (mant + (1LL << (sh - 1))) >> sh : 0;
+    if (bits < 0) v = -v;
+  }
+#pragma unroll
+  for (int s = ND - 1; s >= 1; --s) {
+    long long r = v & 255;     // v mod 256 (two's complement)
+    if (r >= 128) r -= 256;    // balanced digit in [-128, 127]
+    d[s] = (float)r;
+    v = (v - r) >> 8;          // exact
+  }
+  d[0] = (float)v;             // |v| <= 128
+}
+
+// |x| as ordered integer bits (non-negative doubles compare like their bits)
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
+// E with |x| / 2^E < 0.5 for the largest |x| given by its bits (1 for zero)
+__device__ __forceinline__ int exp_of_abs_bits(long long b) {
+  const int ex = (int)(b >> 52);
+  return ex == 0 ? 1 : ex - 1021;   // |x| = f 2^(ex - 1022), f in [0.5, 1)
+}
+
 // Row scaling and slicing: one block per row, 16-byte loads (four FP32 or
 // two pairs of FP64 entries) and 8-byte stores (ldJ and ldb are multiples of
 // 4; the row's pad columns are zero).  The row's largest |J| (as a float)
@@ -223,19 +257,32 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const TJ* __rest
     } else {
       x[0] = x[1] = x[2] = x[3] = TJ(0);
     }
+    if constexpr (sizeof(TJ) == 4) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) x[c] = (4 * k + c < n) ? (TJ)ldexp(x[c], -E) : TJ(0);
+      for (int c = 0; c < 4; ++c) x[c] = (4 * k + c < n) ? ldexpf(x[c], -E) : 0.f;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      __nv_bfloat16 q[4];
+      for (int s = 0; s < 4; ++s) {
+        __nv_bfloat16 q[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const TJ t = x[c] * TJ(256);
-        const TJ sg = rint(t);
-        x[c] = t - sg;
-        q[c] = __float2bfloat16_rn((float)sg);
+        for (int c = 0; c < 4; ++c) {
+          const float t = x[c] * 256.f;
+          const float sg = rintf(t);
+          x[c] = t - sg;
+          q[c] = __float2bfloat16_rn(sg);
+        }
+        *reinterpret_cast<uint2*>(srow + (long long)s * ldb + 4 * k) = *reinterpret_cast<const uint2*>(q);
       }
-      *reinterpret_cast<uint2*>(srow + (long long)s * ldb + 4 * k) = *reinterpret_cast<const uint2*>(q);
+    } else {
+      float d[4][4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) oz_digits<4>(4 * k + c < n ? (double)x[c] : 0.0, E, d[c]);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        __nv_bfloat16 q[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q[c] = __float2bfloat16_rn(d[c][s]);
+        *reinterpret_cast<uint2*>(srow + (long long)s * ldb + 4 * k) = *reinterpret_cast<const uint2*>(q);
+      }
     }
   }
 }
@@ -792,25 +839,21 @@ __global__ void __launch_bounds__(256) k_panel_slice(int m, int row0, int k0, in
   const int row = row0 + blockIdx.x * 8 + warp;
   if (row >= m) return;
   const double* cr = C + (long long)row * ldc + k0;
-  double x0 = lane < kb ? cr[lane] : 0.0;
-  double x1 = lane + 32 < kb ? cr[lane + 32] : 0.0;
-  double a = fmax(fabs(x0), fabs(x1));
-  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-  int e = 0;
-  if (a > 0.0 && isfinite(a)) frexp(a, &e);   // a = f 2^e, f in [0.5, 1)
-  const int E = e + 1;
+  const double x0 = lane < kb ? cr[lane] : 0.0;
+  const double x1 = lane + 32 < kb ? cr[lane + 32] : 0.0;
+  long long a = max(abs_bits(x0), abs_bits(x1));
+  for (int o = 16; o > 0; o >>= 1) a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+  // a non-finite entry (a failed factorisation upstream) slices as zero
+  const int E = a >= 0x7FF0000000000000LL ? 1 : exp_of_abs_bits(a);
   if (lane == 0) rowexp[row] = E;
-  x0 = ldexp(x0, -E);
-  x1 = ldexp(x1, -E);
+  float d0[FNS], d1[FNS];
+  oz_digits<FNS>(a >= 0x7FF0000000000000LL ? 0.0 : x0, E, d0);
+  oz_digits<FNS>(a >= 0x7FF0000000000000LL ? 0.0 : x1, E, d1);
   __nv_bfloat16* sr = S + (long long)row * FLD;
 #pragma unroll
   for (int s = 0; s < FNS; ++s) {
-    const double t0 = x0 * 256.0, t1 = x1 * 256.0;
-    const double g0 = rint(t0), g1 = rint(t1);
-    x0 = t0 - g0;
-    x1 = t1 - g1;
-    sr[s * FNB + lane] = __float2bfloat16_rn((float)g0);
-    sr[s * FNB + lane + 32] = __float2bfloat16_rn((float)g1);
+    sr[s * FNB + lane] = __float2bfloat16_rn(d0[s]);
+    sr[s * FNB + lane + 32] = __float2bfloat16_rn(d1[s]);
   }
 }
 
@@ -920,23 +963,18 @@ __global__ void __launch_bounds__(256) k_slice_rows_f64(int M, int K, int kp, co
   const int row = blockIdx.x * 8 + warp;
   if (row >= M) return;
   auto at = [&](int k) -> double { return cols ? A[(long long)k * lda + row] : A[(long long)row * lda + k]; };
-  double a = 0.0;
-  for (int k = lane; k < K; k += 32) a = fmax(a, fabs(at(k)));
-  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-  int e = 0;
-  if (a > 0.0 && isfinite(a)) frexp(a, &e);
-  const int E = e + 1;
+  long long a = 0;
+  for (int k = lane; k < K; k += 32) a = max(a, abs_bits(at(k)));
+  for (int o = 16; o > 0; o >>= 1) a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+  const bool bad = a >= 0x7FF0000000000000LL;   // a non-finite row slices as zero
+  const int E = bad ? 1 : exp_of_abs_bits(a);
   if (lane == 0) rexp[row] = E;
   __nv_bfloat16* sr = S + (long long)row * 4 * kp;
   for (int k = lane; k < kp; k += 32) {
-    double x = k < K ? ldexp(at(k), -E) : 0.0;
+    float d[4];
+    oz_digits<4>(k < K && !bad ? at(k) : 0.0, E, d);
 #pragma unroll
-    for (int sl = 0; sl < 4; ++sl) {
-      const double t = x * 256.0;
-      const double g = rint(t);
-      x = t - g;
-      sr[sl * kp + k] = __float2bfloat16_rn((float)g);
-    }
+    for (int sl = 0; sl < 4; ++sl) sr[sl * kp + k] = __float2bfloat16_rn(d[sl]);
   }
 }
 

@@ -90,9 +90,9 @@ dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* 
 // 64 x 64) and the blocked solve that uses them (w, y: work vectors [m]).
 dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cudaStream_t st);
 // One 64-column step of the FP64 blocked Cholesky (diagonal block at k0 and
-// the panel solve below it; no trailing update).  A non-positive pivot sets
-// ST_NOT_SPD and status[1] = column.
-dngd_status chol_step_f64(int m, int k0, double* A, long long lda, int* status, cudaStream_t st);
+// the panel solve below it; no trailing update; rdiag [64] device scratch).
+// A non-positive pivot sets ST_NOT_SPD and status[1] = column.
+dngd_status chol_step_f64(int m, int k0, double* A, long long lda, double* rdiag, int* status, cudaStream_t st);
 // L32 = fl32(L) (lower) and the diagonal 64-blocks of Linv = fl32(Dinv),
 // zero elsewhere (ldi = ldk).
 dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* Dinv, float* L32, long long ldk,

@@ -340,24 +340,113 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 
 template dngd_status cholesky<double>(int, double*, long long, int*, double*, cudaStream_t);
 
-// One 64-column step of the FP64 blocked Cholesky without its trailing
-// update: factor the diagonal block at k0 and solve the panel below it.
-dngd_status chol_step_f64(int m, int k0, double* A, long long lda, int* status, cudaStream_t st) {
-  const int trsm_smem = 2 * kCholNB * (kCholNB + 1) * (int)sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    DNGD_CUDA_CHECK(
-        cudaFuncSetAttribute(k_trsm_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem));
-    attr_set = true;
+// FP64 diagonal block of one factorisation step, organised for GB300's slow
+// FP64 pipe: one reciprocal per column (the panel below multiplies by it
+// instead of dividing), the rank-1 update spread over a 16 x 16 thread grid.
+// The block's L and the reciprocals of its diagonal (rdiag[kb]) go to
+// global memory.
+__global__ void __launch_bounds__(256) k_potrf_diag_rcp(int k0, int kb, double* A, long long lda,
+                                                        double* __restrict__ rdiag, int* status) {
+  __shared__ double S[kCholNB][kCholNB + 1];
+  __shared__ double rcp[kCholNB];
+  __shared__ int bad;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    S[i][j] = (j <= i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
   }
+  if (tid == 0) bad = -1;
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      const double piv = S[j][j];
+      if (!(piv > 0.0)) {
+        bad = j;
+      } else {
+        const double d = sqrt(piv);
+        S[j][j] = d;
+        rcp[j] = 1.0 / d;
+      }
+    }
+    __syncthreads();
+    if (bad >= 0) break;
+    const double r = rcp[j];
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] *= r;
+    __syncthreads();
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      const double lij = S[i][j];
+      for (int c = j + 1 + tx; c <= i; c += 16) S[i][c] -= lij * S[c][j];
+    }
+    __syncthreads();
+  }
+  if (bad >= 0) {
+    if (tid == 0) {
+      const int old = atomicOr(status, ST_NOT_SPD);
+      if (!(old & ST_NOT_SPD)) status[1] = k0 + bad;
+    }
+    return;
+  }
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    if (j <= i) A[(long long)(k0 + i) * lda + k0 + j] = S[i][j];
+  }
+  if (tid < kb) rdiag[tid] = rcp[tid];
+}
+
+// Panel rows [k0 + kb, m): x L11^T = a by forward substitution, one thread
+// per row, 32 rows per CTA (so the rows spread over the SMs), multiplying by
+// the diagonal's reciprocals.
+__global__ void __launch_bounds__(32) k_trsm_panel_rcp(int m, int k0, int kb, double* A, long long lda,
+                                                       const double* __restrict__ rdiag, const int* status) {
+  if (status[0] & ST_NOT_SPD) return;
+  __shared__ double Lsh[kCholNB][kCholNB + 1];
+  __shared__ double X[32][kCholNB + 1];
+  __shared__ double rc[kCholNB];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    Lsh[i][j] = (j < i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
+  }
+  for (int j = tid; j < kb; j += blockDim.x) rc[j] = rdiag[j];
+  const int r0 = k0 + kb + blockIdx.x * 32;
+  for (int e = tid; e < 32 * kb; e += blockDim.x) {
+    const int rr = e / kb, j = e % kb;
+    const int gr = r0 + rr;
+    X[rr][j] = (gr < m) ? A[(long long)gr * lda + k0 + j] : 0.0;
+  }
+  __syncwarp();
+  if (r0 + tid < m) {
+    for (int j = 0; j < kb; ++j) {
+      double s0 = X[tid][j], s1 = 0.0;
+      int p = 0;
+      for (; p + 1 < j; p += 2) {   // two independent chains
+        s0 -= X[tid][p] * Lsh[j][p];
+        s1 -= X[tid][p + 1] * Lsh[j][p + 1];
+      }
+      if (p < j) s0 -= X[tid][p] * Lsh[j][p];
+      X[tid][j] = (s0 + s1) * rc[j];
+    }
+  }
+  __syncwarp();
+  for (int e = tid; e < 32 * kb; e += blockDim.x) {
+    const int rr = e / kb, j = e % kb;
+    const int g = r0 + rr;
+    if (g < m) A[(long long)g * lda + k0 + j] = X[rr][j];
+  }
+}
+
+// One 64-column step of the FP64 blocked Cholesky without its trailing
+// update: factor the diagonal block at k0 and solve the panel below it
+// (rdiag: [64] scratch for the diagonal's reciprocals).
+dngd_status chol_step_f64(int m, int k0, double* A, long long lda, double* rdiag, int* status, cudaStream_t st) {
   const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
   DNGD_NOTE_LAUNCH();
-  k_potrf_diag<double><<<1, 256, 0, st>>>(k0, kb, A, lda, status);
+  k_potrf_diag_rcp<<<1, 256, 0, st>>>(k0, kb, A, lda, rdiag, status);
   DNGD_LAUNCH_CHECK();
   const int rest = m - k0 - kb;
   if (rest > 0) {
     DNGD_NOTE_LAUNCH();
-    k_trsm_panel<double><<<cdiv(rest, 64), 64, trsm_smem, st>>>(m, k0, kb, A, lda, status);
+    k_trsm_panel_rcp<<<cdiv(rest, 32), 32, 0, st>>>(m, k0, kb, A, lda, rdiag, status);
     DNGD_LAUNCH_CHECK();
   }
   return DNGD_OK;
