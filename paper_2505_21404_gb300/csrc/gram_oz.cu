@@ -139,6 +139,8 @@ static_assert(5 * OzCfg<4, 5>::TN <= (int)OTMEM && 6 * OzCfg<4, 6>::TN <= (int)O
               "the level accumulators must fit the TMEM allocation");
 static_assert(osmem<4, 5>() <= 227 * 1024 && osmem<4, 6>() <= 227 * 1024 && osmem<6, 7>() <= 227 * 1024,
               "shared-memory ring too large");
+static_assert(EPI_WARPS * 32 * 33 * (int)sizeof(double) <= OzCfg<6, 7>::OST * ostage<6, 7>(),
+              "the update epilogue stages its sub-tiles in the operand ring");
 static_assert(b_tile<4, 5>() % 1024 == 0 && b_tile<4, 6>() % 1024 == 0 && b_tile<6, 7>() % 1024 == 0,
               "tiles keep 1024-byte alignment");
 
@@ -500,14 +502,26 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     const int row = tile.x * TM + q * 32 + lane;
     const int col0 = tile.y * TN + cg * 32;
     if (MODE == OZ_UPDATE) {
-      if (row < m && !*abort_flag) {
-        const int gr = row_off + row;
-        const int er = epi.rexpA[gr];
-        double* crow = epi.C + (long long)gr * epi.ldc + row_off + col0;
+      // every MMA has completed, so the operand ring is idle: the warp's 32 x
+      // 32 sub-tile (lane = row), scaled by 2^(E_row + E_col - eshift), goes
+      // through shared memory and is subtracted row by row, coalesced
+      double* tb = reinterpret_cast<double*>(smem_raw + (smem_base - smem_u32(smem_raw))) + (warp - 2) * 32 * 33;
+      const int er = row < m ? epi.rexpA[row_off + row] : 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < ncol && col0 + j <= row)
-            crow[j] -= ldexp((double)hi[j] + (double)lo[j], er + epi.rexpA[row_off + col0 + j] - epi.eshift);
+      for (int j = 0; j < 32; ++j) {
+        const int cj = col0 + j;
+        const int ec = (j < ncol && cj < m) ? epi.rexpA[row_off + cj] : 0;
+        int e = er + ec - epi.eshift;
+        e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+        tb[lane * 33 + j] = __longlong_as_double((long long)(e + 1023) << 52) * ((double)hi[j] + (double)lo[j]);
+      }
+      __syncwarp();
+      if (!*abort_flag && lane < ncol) {
+        const int col = col0 + lane;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int rw = tile.x * TM + q * 32 + rr;
+          if (rw < m && col <= rw) epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] -= tb[rr * 33 + lane];
+        }
       }
     } else if (MODE == OZ_GEMM) {
       if (row < m && !*abort_flag) {
@@ -866,13 +880,15 @@ struct OzFactor {
   __nv_bfloat16* S;
   int* rowexp;
   int2* d_tiles;
+  double* rdiag;             // reciprocals of the current diagonal block's pivots
   std::vector<int> prefix;   // tiles with row block < I, for I = 0 .. nI
   CUtensorMap mapA, mapB;
 };
 
 size_t oz_factor_bytes(int m) {
   const int nI = (m + TM - 1) / TM, nJ = (m + OzCfg<FNS, FNG>::TN - 1) / OzCfg<FNS, FNG>::TN;
-  return (size_t)m * FLD * sizeof(__nv_bfloat16) + (size_t)m * sizeof(int) + (size_t)nI * nJ * sizeof(int2) + 1024;
+  return (size_t)m * FLD * sizeof(__nv_bfloat16) + (size_t)m * sizeof(int) + (size_t)nI * nJ * sizeof(int2) +
+         FNB * sizeof(double) + 1024;
 }
 
 dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void* work) {
@@ -891,6 +907,7 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
   // past r are masked in the epilogue)
   std::vector<int2> tiles;
   const int nI = (m + TM - 1) / TM, nJ = (m + TN - 1) / TN;
+  p->rdiag = (double*)(((uintptr_t)(p->d_tiles + (size_t)nI * nJ) + 255) & ~(uintptr_t)255);
   p->prefix.assign(nI + 1, 0);
   for (int I = 0; I < nI; ++I) {
     for (int Jc = 0; Jc < nJ && Jc * TN <= I * TM + TM - 1; ++Jc) tiles.push_back(make_int2(I, Jc));
@@ -928,7 +945,7 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
   const int m = p->m;
   const OzEpi upd{p->C, p->ldc, p->rowexp, nullptr, 16 + 8 * (FNG - 1), 0, 0, 0.0, 0.0};
   for (int k0 = 0; k0 < m; k0 += FNB) {
-    dngd_status s = chol_step_f64(m, k0, p->C, p->ldc, status, st);
+    dngd_status s = chol_step_f64(m, k0, p->C, p->ldc, p->rdiag, status, st);
     if (s) return s;
     const int kb = (m - k0) < FNB ? (m - k0) : FNB;
     const int row0 = k0 + kb, r = m - row0;

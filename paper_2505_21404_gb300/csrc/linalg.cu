@@ -399,9 +399,10 @@ __global__ void __launch_bounds__(256) k_potrf_diag_rcp(int k0, int kb, double* 
 __global__ void __launch_bounds__(32) k_trsm_panel_rcp(int m, int k0, int kb, double* A, long long lda,
                                                        const double* __restrict__ rdiag, const int* status) {
   if (status[0] & ST_NOT_SPD) return;
-  __shared__ double Lsh[kCholNB][kCholNB + 1];
-  __shared__ double X[32][kCholNB + 1];
-  __shared__ double rc[kCholNB];
+  extern __shared__ double panel_smem[];
+  double(*Lsh)[kCholNB] = reinterpret_cast<double(*)[kCholNB]>(panel_smem);         // read by broadcast
+  double(*X)[kCholNB + 1] = reinterpret_cast<double(*)[kCholNB + 1]>(panel_smem + kCholNB * kCholNB);
+  double* rc = panel_smem + kCholNB * kCholNB + 32 * (kCholNB + 1);
   const int tid = threadIdx.x;
   for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int i = e / kb, j = e % kb;
@@ -445,8 +446,14 @@ dngd_status chol_step_f64(int m, int k0, double* A, long long lda, double* rdiag
   DNGD_LAUNCH_CHECK();
   const int rest = m - k0 - kb;
   if (rest > 0) {
+    const int smem = (kCholNB * kCholNB + 32 * (kCholNB + 1) + kCholNB) * (int)sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+      DNGD_CUDA_CHECK(cudaFuncSetAttribute(k_trsm_panel_rcp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      attr_set = true;
+    }
     DNGD_NOTE_LAUNCH();
-    k_trsm_panel_rcp<<<cdiv(rest, 32), 32, 0, st>>>(m, k0, kb, A, lda, rdiag, status);
+    k_trsm_panel_rcp<<<cdiv(rest, 32), 32, smem, st>>>(m, k0, kb, A, lda, rdiag, status);
     DNGD_LAUNCH_CHECK();
   }
   return DNGD_OK;
