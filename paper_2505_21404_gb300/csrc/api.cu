@@ -56,6 +56,9 @@ struct dngd_ctx {
   float* trtri_work = nullptr;
   OzPlan* oz = nullptr;       // exact-Gram mode
   OzFactor* ozf = nullptr;    // its FP64 factorisation (exact sliced trailing updates)
+  OzGemm* ozi = nullptr;      // FP64 GEMMs of the factor's inverse (exact-Gram modes)
+  void* ozi_work = nullptr;
+  double *Li64 = nullptr, *LiT64 = nullptr;   // the factor's FP64 inverse and its transpose
   OzGemm* ozg = nullptr;      // FP64 jets' layer GEMMs from exact slice products (MIXED_OZ64)
   void* ozg_work = nullptr;
   Tc3Scratch ozs;             // hands ozg to the FP64 jets
@@ -495,15 +498,17 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     }
     if (!c->async) c->mu_sticky = mu;
     c->shift_used = mu;
+    // the factor's inverse in FP64 from sliced products (its condition number
+    // is the square root of K's, up to ~1e5 late in training, so an inverse
+    // formed in FP32 arithmetic is off by far more than FP32 rounding), then
+    // rounded to FP32: a relative perturbation of 2^-24 cond(L) of the ideal
+    // preconditioner
     if ((s = trtri_diag64(m, c->Kd, c->ldk, c->Dinv, c->st))) return s;
-    if ((s = factor_to_f32(m, c->Kd, c->ldk, c->Dinv, (float*)c->K, c->ldk, c->Linv, c->ldk, c->st))) return s;
-    // the inverse of this factor (cond ~ sqrt of K's, up to ~1e5) on FP32
-    // SIMT GEMMs with round-to-nearest accumulation: the 3xTF32 products
-    // accumulate in TMEM over up to m/2 terms and lose too much here
-    if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st, nullptr,
-                               nullptr)))
+    if ((s = oz_trtri(c->ozi, m, c->Kd, c->ldk, c->Dinv, c->Li64, c->LiT64, c->ldk, (double*)c->trtri_work,
+                      c->status, c->st)))
       return s;
-    if (c->LinvT && (s = transpose_f32(m, c->Linv, c->ldk, c->LinvT, c->ldk, c->st))) return s;
+    if ((s = to_float((long long)m * c->ldk, c->Li64, c->Linv, c->st))) return s;
+    if (c->LinvT && (s = to_float((long long)m * c->ldk, c->LiT64, c->LinvT, c->st))) return s;
     if (c->async) goto factored;
   } else {
     // low-precision Gram + FP32 factor of K + (lambda + mu) I; a failed
@@ -985,6 +990,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       add(sizeof(double) * (size_t)m * c->ldk);                                  // Kd
       add(sizeof(double) * (size_t)cdiv(m, 64) * 64 * 64);                       // Dinv
       add(oz_factor_bytes(m));
+      add(oz_gemm_bytes(m, m, m));                                               // inverse's GEMMs
+      add(2 * sizeof(double) * (size_t)m * c->ldk);                              // Li64, LiT64
       if (j64) add(oz_gemm_bytes(3 * net.R, net.max_w, net.max_w));              // FP64 jets' GEMMs
     } else {
       add(gram_tc_partial_bytes(m, (int)n));
@@ -1073,6 +1080,9 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
       A_(c->Kd, double, (size_t)m * c->ldk);
       A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
       A_(c->ozf_work, unsigned char, oz_factor_bytes(m));
+      A_(c->ozi_work, unsigned char, oz_gemm_bytes(m, m, m));
+      A_(c->Li64, double, (size_t)m * c->ldk);
+      A_(c->LiT64, double, (size_t)m * c->ldk);
       if (j64) A_(c->ozg_work, unsigned char, oz_gemm_bytes(3 * net.R, net.max_w, net.max_w));
     } else {
       c->gram_partial_bytes = gram_tc_partial_bytes(m, (int)n);
@@ -1110,6 +1120,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     if (s) return s;
     gram_oz_set_fp64_out(c->oz, c->Kd);
     if ((s = oz_factor_plan(&c->ozf, m, c->Kd, c->ldk, c->ozf_work))) return s;
+    if ((s = oz_gemm_plan(&c->ozi, m, m, m, c->ozi_work))) return s;
     if (c->ozg_work) {
       if ((s = oz_gemm_plan(&c->ozg, 3 * net.R, net.max_w, net.max_w, c->ozg_work))) return s;
       c->ozs.ozg = c->ozg;
@@ -1143,6 +1154,7 @@ void free_ctx(dngd_ctx* c) {
   if (c->oz) gram_oz_free(c->oz);
   if (c->ozf) oz_factor_free(c->ozf);
   if (c->ozg) oz_gemm_free(c->ozg);
+  if (c->ozi) oz_gemm_free(c->ozi);
   for (int i = 0; i < 9; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (int i = 0; i < 4; ++i)

@@ -1066,6 +1066,69 @@ dngd_status oz_gemm(OzGemm* p, int M, int N, int K, double alpha, const double* 
 
 void oz_gemm_free(OzGemm* p) { delete p; }
 
+// ---------------------------------------------------------------------------
+// Inverse of a lower-triangular FP64 factor from exact slice products
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Diagonal 64-blocks of Li = L^{-1} and of LiT = L^{-T} from the blocks'
+// inverses (Dinv [blocks x 64 x 64], row-major); everything else zero.
+__global__ void k_inv_diag_blocks(int m, const double* __restrict__ Dinv, double* __restrict__ Li,
+                                  double* __restrict__ LiT, long long ld) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * ld) return;
+  const int i = (int)(idx / ld), j = (int)(idx % ld);
+  double v = 0.0, vt = 0.0;
+  if (j < m && i / 64 == j / 64) {
+    const int b = i / 64;
+    const double* D = Dinv + (long long)b * 64 * 64;
+    if (j <= i) v = D[(i - b * 64) * 64 + (j - b * 64)];
+    if (i <= j) vt = D[(j - b * 64) * 64 + (i - b * 64)];
+  }
+  Li[idx] = v;
+  LiT[idx] = vt;
+}
+
+// Recursion on [k0, k0 + n): with L = [L11 0; L21 L22] and the halves'
+// inverses I11, I22 (and their transposes),
+//   T^T = I11^T L21^T,  I21 = -I22 T,  I21^T = -T^T I22^T,
+// each an FP64 product C = A B^T of row-major operands.
+dngd_status oz_trtri_rec(OzGemm* g, int k0, int n, const double* L, long long ldl, double* Li, double* LiT,
+                         long long ld, double* work, int* status, cudaStream_t st) {
+  if (n <= 64) return DNGD_OK;
+  const int n1 = ((n / 2 + 63) / 64) * 64, n2 = n - n1;
+  dngd_status s = oz_trtri_rec(g, k0, n1, L, ldl, Li, LiT, ld, work, status, st);
+  if (!s) s = oz_trtri_rec(g, k0 + n1, n2, L, ldl, Li, LiT, ld, work, status, st);
+  if (s) return s;
+  const double* L21 = L + (long long)(k0 + n1) * ldl + k0;      // [n2 x n1]
+  const double* I11T = LiT + (long long)k0 * ld + k0;           // [n1 x n1] (upper)
+  const double* I22 = Li + (long long)(k0 + n1) * ld + k0 + n1; // [n2 x n2] (lower)
+  const double* I22T = LiT + (long long)(k0 + n1) * ld + k0 + n1;
+  double* TT = work;                                            // T^T [n1 x n2]
+  // T^T[i, j] = sum_k I11^T[i, k] L21[j, k]
+  if ((s = oz_gemm(g, n1, n2, n1, 1.0, I11T, ld, L21, ldl, false, 0.0, TT, n2, status, st))) return s;
+  // I21[i, j] = -sum_k I22[i, k] T[k, j] = -sum_k I22[i, k] T^T[j, k]
+  if ((s = oz_gemm(g, n2, n1, n2, -1.0, I22, ld, TT, n2, false, 0.0, Li + (long long)(k0 + n1) * ld + k0, ld,
+                   status, st)))
+    return s;
+  // I21^T[i, j] = -sum_k T^T[i, k] I22^T[k, j] = -sum_k T^T[i, k] I22[j, k]
+  return oz_gemm(g, n1, n2, n2, -1.0, TT, n2, I22, ld, false, 0.0, LiT + (long long)k0 * ld + k0 + n1, ld, status,
+                 st);
+  (void)I22T;
+}
+
+}  // namespace
+
+dngd_status oz_trtri(OzGemm* g, int m, const double* L, long long ldl, const double* Dinv, double* Li, double* LiT,
+                     long long ld, double* work, int* status, cudaStream_t st) {
+  const long long cnt = (long long)m * ld;
+  DNGD_NOTE_LAUNCH();
+  k_inv_diag_blocks<<<(int)((cnt + 255) / 256), 256, 0, st>>>(m, Dinv, Li, LiT, ld);
+  DNGD_LAUNCH_CHECK();
+  return oz_trtri_rec(g, 0, m, L, ldl, Li, LiT, ld, work, status, st);
+}
+
 unsigned* gram_oz_rowmax(OzPlan* p) { return p->rowmax; }
 
 }  // namespace dngd

@@ -93,10 +93,6 @@ dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cu
 // the panel solve below it; no trailing update; rdiag [64] device scratch).
 // A non-positive pivot sets ST_NOT_SPD and status[1] = column.
 dngd_status chol_step_f64(int m, int k0, double* A, long long lda, double* rdiag, int* status, cudaStream_t st);
-// L32 = fl32(L) (lower) and the diagonal 64-blocks of Linv = fl32(Dinv),
-// zero elsewhere (ldi = ldk).
-dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* Dinv, float* L32, long long ldk,
-                          float* Linv, long long ldi, cudaStream_t st);
 dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const double* Dinv, const double* b, double* x,
                                 double* w, double* y, cudaStream_t st);
 
@@ -188,6 +184,12 @@ dngd_status oz_gemm_plan(OzGemm** plan, int max_m, int max_n, int max_k, void* w
 dngd_status oz_gemm(OzGemm* plan, int M, int N, int K, double alpha, const double* A, long long lda, const double* B,
                     long long ldb, bool b_kn, double beta, double* C, long long ldc, int* status, cudaStream_t st);
 void oz_gemm_free(OzGemm* plan);
+// Li = L^{-1} and LiT = L^{-T} (both [m x ld] row-major, FP64) of a lower
+// FP64 factor from its diagonal blocks' inverses Dinv (trtri_diag64) and
+// sliced products (three per recursion node); work >= (m/2 + 64)^2 doubles;
+// the plan's capacity >= (m, m, m).
+dngd_status oz_trtri(OzGemm* plan, int m, const double* L, long long ldl, const double* Dinv, double* Li,
+                     double* LiT, long long ld, double* work, int* status, cudaStream_t st);
 
 // Explicit inverse of a lower-triangular FP32 factor: Linv = L^{-1} (lower).
 dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,

@@ -920,33 +920,6 @@ __global__ void __launch_bounds__(256) k_trsv_bwd_step(int k0, int kb, const dou
   w[i] -= s;
 }
 
-// The FP64 factor as the FP32 preconditioner's inputs: L32 = fl32(L) (lower,
-// upper set to zero) and the diagonal 64-blocks of Linv = fl32(Dinv) (the
-// rest of Linv zero, for trtri_offdiag_f32 to fill).
-__global__ void k_factor_to_f32(int m, const double* __restrict__ L, long long ldl, const double* __restrict__ Dinv,
-                                float* __restrict__ L32, long long ldk, float* __restrict__ Linv, long long ldi) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int cols = (int)ldk;
-  if (idx >= (long long)m * cols) return;
-  const int i = (int)(idx / cols), j = (int)(idx % cols);
-  L32[(long long)i * ldk + j] = (j <= i) ? (float)L[(long long)i * ldl + j] : 0.f;
-  float d = 0.f;
-  if (j <= i && j / kTrsvNB == i / kTrsvNB) {
-    const int b = i / kTrsvNB;
-    d = (float)Dinv[(long long)b * kTrsvNB * kTrsvNB + (i - b * kTrsvNB) * kTrsvNB + (j - b * kTrsvNB)];
-  }
-  if (j < (int)ldi) Linv[(long long)i * ldi + j] = d;
-}
-
-dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* Dinv, float* L32, long long ldk,
-                          float* Linv, long long ldi, cudaStream_t st) {
-  const long long cnt = (long long)m * ldk;
-  DNGD_NOTE_LAUNCH();
-  k_factor_to_f32<<<(int)((cnt + 255) / 256), 256, 0, st>>>(m, L, ldl, Dinv, L32, ldk, Linv, ldi);
-  DNGD_LAUNCH_CHECK();
-  return DNGD_OK;
-}
-
 dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cudaStream_t st) {
   DNGD_NOTE_LAUNCH();
   k_trtri_diag64<<<cdiv(m, kTrsvNB), kTrsvNB, 0, st>>>(m, L, ldl, Dinv);

