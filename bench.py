@@ -540,12 +540,16 @@ def run_serving(args, rank, world, local_rank):
         flops = sum(p["steps_done"] * wl["X"].shape[0] * (wl["X"].shape[0] + 1) * len(wl["theta"])
                     for p, wl in polls)
         qd = [p["queue_s"] for p, _ in polls if p["state"] != "queued"]
+        # completed jobs: time from submission to the last iteration
+        lat = [p["queue_s"] + p["run_s"] for p, _ in polls if p["state"] == "done"]
         srv.close()
         results.append({
             "rate_jobs_per_s": rate, "window_s": elapsed, "submitted": len(ids),
             "steps_per_s": st["steps_total"] / elapsed, "steps_total": st["steps_total"],
             "p50_step_ms": st["p50_ms"], "p99_step_ms": st["p99_ms"],
             "queue_delay_p50_s": float(np.percentile(qd, 50)) if qd else None,
+            "job_latency_p50_s": float(np.percentile(lat, 50)) if lat else None,
+            "job_latency_p99_s": float(np.percentile(lat, 99)) if lat else None,
             "admitted": st["admitted"], "queued": st["queued"], "rejected": st["rejected"],
             "done": st["done"], "failed": st["failed"], "running_at_end": st["running"],
             "gram_tflops": flops / elapsed / 1e12,

@@ -504,11 +504,9 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     // rounded to FP32: a relative perturbation of 2^-24 cond(L) of the ideal
     // preconditioner
     if ((s = trtri_diag64(m, c->Kd, c->ldk, c->Dinv, c->st))) return s;
-    if ((s = oz_trtri(c->ozi, m, c->Kd, c->ldk, c->Dinv, c->Li64, c->LiT64, c->ldk, (double*)c->trtri_work,
-                      c->status, c->st)))
+    if ((s = oz_trtri(c->ozi, m, c->Kd, c->ldk, c->Dinv, (float*)c->K, c->Linv, c->LinvT, c->Li64, c->LiT64, c->ldk,
+                      c->trtri_work, (double*)c->K0, c->status, c->st)))
       return s;
-    if ((s = to_float((long long)m * c->ldk, c->Li64, c->Linv, c->st))) return s;
-    if (c->LinvT && (s = to_float((long long)m * c->ldk, c->LiT64, c->LinvT, c->st))) return s;
     if (c->async) goto factored;
   } else {
     // low-precision Gram + FP32 factor of K + (lambda + mu) I; a failed

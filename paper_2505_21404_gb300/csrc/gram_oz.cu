@@ -54,6 +54,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "step_kernels.h"
 #include "tc_ptx.cuh"
 
 namespace dngd {
@@ -1067,68 +1068,72 @@ dngd_status oz_gemm(OzGemm* p, int M, int N, int K, double alpha, const double* 
 void oz_gemm_free(OzGemm* p) { delete p; }
 
 // ---------------------------------------------------------------------------
-// Inverse of a lower-triangular FP64 factor from exact slice products
+// Inverse of a lower-triangular FP64 factor (the exact-Gram preconditioner)
 // ---------------------------------------------------------------------------
+//
+// The recursion (L^{-1})21 = -I22 (L21 I11) over halves rounded to 64.  Its
+// small nodes (n1 + n2 <= 512: products over at most 448 terms) run as the
+// batched FP32 launches of trtri_offdiag_f32; a large node's products run
+// over up to m/2 terms, where FP32 accumulation ruins the preconditioner at
+// cond(L) ~ 1e5 (preconditioned condition number ~1e4 instead of ~2 on the
+// 5-D benchmark late in training, CPU emulation), so they are FP64 products
+// from exact slices: keeping L^{-1} and L^{-T},
+//   T^T = I11^T L21^T,  I21 = -I22 T,  I21^T = -T^T I22^T,
+// each a row-major C = A B^T.
 
 namespace {
 
-// Diagonal 64-blocks of Li = L^{-1} and of LiT = L^{-T} from the blocks'
-// inverses (Dinv [blocks x 64 x 64], row-major); everything else zero.
-__global__ void k_inv_diag_blocks(int m, const double* __restrict__ Dinv, double* __restrict__ Li,
-                                  double* __restrict__ LiT, long long ld) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)m * ld) return;
-  const int i = (int)(idx / ld), j = (int)(idx % ld);
-  double v = 0.0, vt = 0.0;
-  if (j < m && i / 64 == j / 64) {
-    const int b = i / 64;
-    const double* D = Dinv + (long long)b * 64 * 64;
-    if (j <= i) v = D[(i - b * 64) * 64 + (j - b * 64)];
-    if (i <= j) vt = D[(j - b * 64) * 64 + (i - b * 64)];
+// Li = double(Linv) and LiT = its transpose (both [m x ld]).
+__global__ void k_widen_inv(int m, const float* __restrict__ Linv, double* __restrict__ Li,
+                            double* __restrict__ LiT, long long ld) {
+  __shared__ float t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int i = by + r, j = bx + tx;
+    const float v = (i < m && j < ld) ? Linv[(long long)i * ld + j] : 0.f;
+    t[r][tx] = v;
+    if (i < m && j < ld) Li[(long long)i * ld + j] = v;
   }
-  Li[idx] = v;
-  LiT[idx] = vt;
-}
-
-// Recursion on [k0, k0 + n): with L = [L11 0; L21 L22] and the halves'
-// inverses I11, I22 (and their transposes),
-//   T^T = I11^T L21^T,  I21 = -I22 T,  I21^T = -T^T I22^T,
-// each an FP64 product C = A B^T of row-major operands.
-dngd_status oz_trtri_rec(OzGemm* g, int k0, int n, const double* L, long long ldl, double* Li, double* LiT,
-                         long long ld, double* work, int* status, cudaStream_t st) {
-  if (n <= 64) return DNGD_OK;
-  const int n1 = ((n / 2 + 63) / 64) * 64, n2 = n - n1;
-  dngd_status s = oz_trtri_rec(g, k0, n1, L, ldl, Li, LiT, ld, work, status, st);
-  if (!s) s = oz_trtri_rec(g, k0 + n1, n2, L, ldl, Li, LiT, ld, work, status, st);
-  if (s) return s;
-  const double* L21 = L + (long long)(k0 + n1) * ldl + k0;      // [n2 x n1]
-  const double* I11T = LiT + (long long)k0 * ld + k0;           // [n1 x n1] (upper)
-  const double* I22 = Li + (long long)(k0 + n1) * ld + k0 + n1; // [n2 x n2] (lower)
-  const double* I22T = LiT + (long long)(k0 + n1) * ld + k0 + n1;
-  double* TT = work;                                            // T^T [n1 x n2]
-  // T^T[i, j] = sum_k I11^T[i, k] L21[j, k]
-  if ((s = oz_gemm(g, n1, n2, n1, 1.0, I11T, ld, L21, ldl, false, 0.0, TT, n2, status, st))) return s;
-  // I21[i, j] = -sum_k I22[i, k] T[k, j] = -sum_k I22[i, k] T^T[j, k]
-  if ((s = oz_gemm(g, n2, n1, n2, -1.0, I22, ld, TT, n2, false, 0.0, Li + (long long)(k0 + n1) * ld + k0, ld,
-                   status, st)))
-    return s;
-  // I21^T[i, j] = -sum_k T^T[i, k] I22^T[k, j] = -sum_k T^T[i, k] I22[j, k]
-  return oz_gemm(g, n1, n2, n2, -1.0, TT, n2, I22, ld, false, 0.0, LiT + (long long)k0 * ld + k0 + n1, ld, status,
-                 st);
-  (void)I22T;
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bx + r, j = by + tx;   // LiT[i][j] = Linv[j][i]
+    if (i < m && j < ld) LiT[(long long)i * ld + j] = (j < m) ? t[tx][r] : 0.f;
+  }
 }
 
 }  // namespace
 
-dngd_status oz_trtri(OzGemm* g, int m, const double* L, long long ldl, const double* Dinv, double* Li, double* LiT,
-                     long long ld, double* work, int* status, cudaStream_t st) {
-  const long long cnt = (long long)m * ld;
-  DNGD_NOTE_LAUNCH();
-  k_inv_diag_blocks<<<(int)((cnt + 255) / 256), 256, 0, st>>>(m, Dinv, Li, LiT, ld);
-  DNGD_LAUNCH_CHECK();
-  return oz_trtri_rec(g, 0, m, L, ldl, Li, LiT, ld, work, status, st);
+dngd_status oz_trtri(OzGemm* g, int m, const double* L, long long ldl, const double* Dinv, float* L32, float* Linv,
+                     float* LinvT, double* Li, double* LiT, long long ld, float* work32, double* work, int* status,
+                     cudaStream_t st) {
+  dngd_status s = factor_to_f32(m, L, ldl, Dinv, L32, Linv, ld, st);
+  if (s) return s;
+  std::vector<int3> large;
+  if ((s = trtri_small_nodes_f32(m, L32, ld, Linv, ld, work32, st, &large))) return s;
+  if (!large.empty()) {
+    DNGD_NOTE_LAUNCH();
+    k_widen_inv<<<dim3((unsigned)((ld + 31) / 32), (unsigned)((m + 31) / 32)), 256, 0, st>>>(m, Linv, Li, LiT, ld);
+    DNGD_LAUNCH_CHECK();
+    for (const int3& nd : large) {
+      const int k0 = nd.x, n1 = nd.y, n2 = nd.z;
+      const double* L21 = L + (long long)(k0 + n1) * ldl + k0;        // [n2 x n1]
+      const double* I11T = LiT + (long long)k0 * ld + k0;             // [n1 x n1]
+      const double* I22 = Li + (long long)(k0 + n1) * ld + k0 + n1;   // [n2 x n2]
+      double* TT = work;                                              // T^T [n1 x n2]
+      if ((s = oz_gemm(g, n1, n2, n1, 1.0, I11T, ld, L21, ldl, false, 0.0, TT, n2, status, st))) return s;
+      if ((s = oz_gemm(g, n2, n1, n2, -1.0, I22, ld, TT, n2, false, 0.0, Li + (long long)(k0 + n1) * ld + k0, ld,
+                       status, st)))
+        return s;
+      if ((s = oz_gemm(g, n1, n2, n2, -1.0, TT, n2, I22, ld, false, 0.0, LiT + (long long)k0 * ld + k0 + n1, ld,
+                       status, st)))
+        return s;
+    }
+    if ((s = to_float((long long)m * ld, Li, Linv, st))) return s;
+    if ((s = to_float((long long)m * ld, LiT, LinvT, st))) return s;
+    return DNGD_OK;
+  }
+  return transpose_f32(m, Linv, ld, LinvT, ld, st);
 }
-
-unsigned* gram_oz_rowmax(OzPlan* p) { return p->rowmax; }
 
 }  // namespace dngd

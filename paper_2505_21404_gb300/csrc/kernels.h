@@ -1,6 +1,8 @@
 // Internal kernel launchers of the D-NGD library.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace dngd {
@@ -89,6 +91,14 @@ dngd_status chol_solve_f64(int m, const double* L, long long ldl, const double* 
 // Inverses of the 64 x 64 diagonal blocks of an FP64 factor ([ceil(m/64)] x
 // 64 x 64) and the blocked solve that uses them (w, y: work vectors [m]).
 dngd_status trtri_diag64(int m, const double* L, long long ldl, double* Dinv, cudaStream_t st);
+// L32 = fl32(L) (lower) and the diagonal 64-blocks of Linv = fl32(Dinv),
+// zero elsewhere (both [m x ldk]).
+dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* Dinv, float* L32, float* Linv,
+                          long long ldk, cudaStream_t st);
+// The small nodes (n1 + n2 <= 512) of trtri_offdiag_f32's recursion only,
+// bottom-up; the large nodes (k0, n1, n2) are returned bottom-up.
+dngd_status trtri_small_nodes_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
+                                  cudaStream_t st, std::vector<int3>* large_out);
 // One 64-column step of the FP64 blocked Cholesky (diagonal block at k0 and
 // the panel solve below it; no trailing update; rdiag [64] device scratch).
 // A non-positive pivot sets ST_NOT_SPD and status[1] = column.
@@ -184,12 +194,15 @@ dngd_status oz_gemm_plan(OzGemm** plan, int max_m, int max_n, int max_k, void* w
 dngd_status oz_gemm(OzGemm* plan, int M, int N, int K, double alpha, const double* A, long long lda, const double* B,
                     long long ldb, bool b_kn, double beta, double* C, long long ldc, int* status, cudaStream_t st);
 void oz_gemm_free(OzGemm* plan);
-// Li = L^{-1} and LiT = L^{-T} (both [m x ld] row-major, FP64) of a lower
-// FP64 factor from its diagonal blocks' inverses Dinv (trtri_diag64) and
-// sliced products (three per recursion node); work >= (m/2 + 64)^2 doubles;
-// the plan's capacity >= (m, m, m).
-dngd_status oz_trtri(OzGemm* plan, int m, const double* L, long long ldl, const double* Dinv, double* Li,
-                     double* LiT, long long ld, double* work, int* status, cudaStream_t st);
+// The preconditioner's inverse factor: Linv = fl32(L^{-1}) and LinvT =
+// fl32(L^{-T}) (FP32, [m x ld]) of a lower FP64 factor L, from its diagonal
+// blocks' inverses Dinv (trtri_diag64); small recursion nodes in FP32, large
+// ones as FP64 sliced products through Li, LiT ([m x ld] FP64).  Scratch:
+// L32 [m x ld] FP32, work32 >= m^2 / 4 floats, work >= (m/2 + 64)^2
+// doubles; the plan's capacity >= (m, m, m).
+dngd_status oz_trtri(OzGemm* plan, int m, const double* L, long long ldl, const double* Dinv, float* L32, float* Linv,
+                     float* LinvT, double* Li, double* LiT, long long ld, float* work32, double* work, int* status,
+                     cudaStream_t st);
 
 // Explicit inverse of a lower-triangular FP32 factor: Linv = L^{-1} (lower).
 dngd_status trtri_lower_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,

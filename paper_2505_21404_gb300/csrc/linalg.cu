@@ -1187,6 +1187,56 @@ TrtriPlan* trtri_plan(int m, const float* L, long long ldl, float* Linv, long lo
 
 }  // namespace
 
+// Only the small nodes (two batched FP32 launches per depth, products
+// accumulated in FP32 over at most 448 terms), bottom-up; the large nodes are
+// the caller's, listed (k0, n1, n2) bottom-up in large_out.
+dngd_status trtri_small_nodes_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
+                                  cudaStream_t st, std::vector<int3>* large_out) {
+  TrtriPlan* p = trtri_plan(m, L, ldl, Linv, ldi, work, st);
+  if (!p) return DNGD_ERR_INVALID_ARG;
+  large_out->clear();
+  for (int d = (int)p->levels.size() - 1; d >= 0; --d) {
+    const int cnt = p->count[d];
+    if (cnt > 0) {
+      const dim3 gT(cdiv(p->maxN1[d], 64), cdiv(p->maxM[d], 64), cnt);
+      DNGD_NOTE_LAUNCH();
+      k_gemm_nodes<<<gT, 256, 0, st>>>(p->d_nodes + p->first[d]);
+      DNGD_NOTE_LAUNCH();
+      k_gemm_nodes<<<gT, 256, 0, st>>>(p->d_nodes + p->first[d] + cnt);
+      DNGD_LAUNCH_CHECK();
+    }
+    for (const TrtriNode& nd : p->levels[d])
+      if (nd.n1 + nd.n2 > kSmallNode) large_out->push_back(make_int3(nd.k0, nd.n1, nd.n2));
+  }
+  return DNGD_OK;
+}
+
+// The FP64 factor as FP32 inputs of the inverse: L32 = fl32(L) (lower,
+// upper zero) and the diagonal 64-blocks of Linv = fl32(Dinv), zero
+// elsewhere (ldi = ldk).
+__global__ void k_factor_to_f32(int m, const double* __restrict__ L, long long ldl, const double* __restrict__ Dinv,
+                                float* __restrict__ L32, long long ldk, float* __restrict__ Linv) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * ldk) return;
+  const int i = (int)(idx / ldk), j = (int)(idx % ldk);
+  L32[idx] = (j <= i) ? (float)L[(long long)i * ldl + j] : 0.f;
+  float d = 0.f;
+  if (j <= i && j / kTrsvNB == i / kTrsvNB) {
+    const int b = i / kTrsvNB;
+    d = (float)Dinv[(long long)b * kTrsvNB * kTrsvNB + (i - b * kTrsvNB) * kTrsvNB + (j - b * kTrsvNB)];
+  }
+  Linv[idx] = d;
+}
+
+dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* Dinv, float* L32, float* Linv,
+                          long long ldk, cudaStream_t st) {
+  const long long cnt = (long long)m * ldk;
+  DNGD_NOTE_LAUNCH();
+  k_factor_to_f32<<<(int)((cnt + 255) / 256), 256, 0, st>>>(m, L, ldl, Dinv, L32, ldk, Linv);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
 dngd_status trtri_offdiag_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
                               cudaStream_t st, const Tc3Scratch* tc3, int* status) {
   TrtriPlan* p = (tc3 && status) ? trtri_plan(m, L, ldl, Linv, ldi, work, st) : nullptr;
