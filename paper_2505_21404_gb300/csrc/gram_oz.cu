@@ -1136,4 +1136,6 @@ dngd_status oz_trtri(OzGemm* g, int m, const double* L, long long ldl, const dou
   return transpose_f32(m, Linv, ld, LinvT, ld, st);
 }
 
+unsigned* gram_oz_rowmax(OzPlan* p) { return p->rowmax; }
+
 }  // namespace dngd
