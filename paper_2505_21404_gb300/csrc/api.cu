@@ -680,11 +680,14 @@ dngd_status step_pcg(dngd_ctx* c, const double* theta, const double* X, const do
   DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
   evrec(c, 0);
   const float* th = theta_in_T<float>(c, theta);
-  // jets: r, stream activations H and adjoints D (J is not formed)
-  if ((s = jets_forward<float>(c->net, th, X, target, lp<float>(c->Z), lp<float>(c->H), c->r, c->status, c->st)))
+  // jets: r, stream activations H and adjoints D (J is not formed); their
+  // layer GEMMs on the TF32 tensor cores
+  if ((s = jets_forward<float>(c->net, th, X, target, lp<float>(c->Z), lp<float>(c->H), c->r, c->status, c->st,
+                               tc3p(c), true)))
     return s;
   if ((s = jets_backward_jacobian<float, float>(c->net, th, X, lp<float>(c->Z), lp<float>(c->H), lp<float>(c->D),
-                                                (float*)c->Hbar, (float*)nullptr, 0, nullptr, 0, c->st)))
+                                                (float*)c->Hbar, (float*)nullptr, 0, nullptr, 0, c->st, tc3p(c),
+                                                c->status)))
     return s;
   if ((s = apply_lambda_rule(c))) return s;
   evrec(c, 1);
@@ -716,8 +719,8 @@ dngd_status step_pcg(dngd_ctx* c, const double* theta, const double* X, const do
   evrec(c, 4);
   if (c->desc.use_ga) {
     to_float(n, c->v, c->v32, c->st);
-    if ((s = jets_fvv<float>(c->net, th, c->v32, X, (float*)c->Z3, (float*)c->H3a, (float*)c->H3b, c->fvv,
-                             c->st)))
+    if ((s = jets_fvv<float>(c->net, th, c->v32, X, (float*)c->Z3, (float*)c->H3a, (float*)c->H3b, c->fvv, c->st,
+                             tc3p(c), c->status)))
       return s;
     evrec(c, 5);
     if ((s = pcg_matfree(c, c->fvv, c->beta, 1))) return s;
@@ -762,11 +765,22 @@ dngd_status alloc_pcg(dngd_ctx* c, bool dry, size_t* bytes_out) {
   add(4 * ((size_t)m * ell + (size_t)m * wl + (size_t)ell * wl + m));
   add(4 * (4 * (size_t)ell * ell + (size_t)m * ell + (size_t)ell * ell));
   add(8 * ((size_t)m * 12 + 3 * n + 16 * (size_t)(n > m ? n : m)));
+  // split operands of the 3xTF32 GEMMs: the jets' layers (R x w x w), J u
+  // (R x w_out x w_in), the landmark columns (R x RI x w) and the chunks of
+  // J^T v (w_out x w_in x 1024)
+  size_t t3 = tc3_scratch_bytes(net.R, net.max_w, net.max_w);
+  const size_t t3b = tc3_scratch_bytes(net.R, RI, wmax);
+  const size_t t3c = tc3_scratch_bytes(3 * net.R, net.max_w, net.max_w);   // the f_vv sweep's stacked streams
+  t3 = t3 > t3b ? t3 : t3b;
+  t3 = t3 > t3c ? t3 : t3c;
+  add(t3);
   if (bytes_out) *bytes_out = tot;
   if (dry) return DNGD_OK;
   dngd_status s;
 #define A_(p, T, cnt) \
   if ((s = dalloc<T>(c, (T**)&(p), (cnt)))) return s;
+  c->tc3.bytes = t3;
+  A_(c->tc3.buf, float, t3 / sizeof(float));
   A_(c->theta_s, double, n);
   A_(c->X_s, double, (size_t)m * net.d_in);
   A_(c->target_s, double, m);
@@ -843,6 +857,8 @@ dngd_status alloc_pcg(dngd_ctx* c, bool dry, size_t* bytes_out) {
   F.xs = c->xs;
   F.partials = c->partials;
   F.partial_cap = 16LL * (n > m ? n : m);
+  F.tc3 = &c->tc3;
+  F.status = c->status;
   DNGD_CUDA_CHECK(cudaMemset(c->a, 0, sizeof(double) * n));
   DNGD_CUDA_CHECK(cudaMemset(c->scal, 0, sizeof(double) * S_COUNT));
   DNGD_CUDA_CHECK(cudaMemset(c->status, 0, sizeof(int) * 4));

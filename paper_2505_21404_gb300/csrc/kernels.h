@@ -142,9 +142,11 @@ enum : unsigned {
 // A then [K x M]), B_op = B [N x K] (or B^T with transB); lower: only
 // C[i][j], j <= i.  INVALID_ARG when the scratch is too small (callers then
 // use the SIMT GEMM).
+// kscale_a (optional, [K]): op(A)'s columns scaled by it (a diagonal in the
+// product) as A is split.
 dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long lda, bool transA, const float* B,
                      long long ldb, bool transB, float beta, float* C, long long ldc, bool lower, const Tc3Scratch& sc,
-                     int* status, cudaStream_t st, unsigned flags = 0u);
+                     int* status, cudaStream_t st, unsigned flags = 0u, const float* kscale_a = nullptr);
 
 dngd_status gemm_tc3_trials(int G, int M, int N, int K, const float* B0, long long ldb, long long b_z, float* C,
                             long long ldc, long long c_z, const Tc3Scratch& sc, int* status, cudaStream_t st);
@@ -305,6 +307,8 @@ struct MatFree {
   float2* xs;
   double* partials;
   long long partial_cap;
+  const Tc3Scratch* tc3;   // the factor-form GEMMs on the TF32 tensor cores (3xTF32), or null: SIMT
+  int* status;
 };
 dngd_status mf_jtv(const MatFree& F, const double* v, float* g, cudaStream_t st);
 dngd_status mf_jv(const MatFree& F, const float* u, double* y, cudaStream_t st);

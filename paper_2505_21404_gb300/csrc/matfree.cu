@@ -29,6 +29,8 @@ namespace dngd {
 
 namespace {
 
+constexpr int kJtvChunk = 1024;   // point-stream rows per TMEM accumulation of J^T v
+
 // Layer-0 and bias parts of J^T v.  Thread = one output unit a of layer l.
 // Writes g[w_off[l] ...] and g[b_off[l] ...] for l = 0 (weights from the
 // input streams) and the biases of every hidden layer.
@@ -309,6 +311,19 @@ dngd_status mf_jtv(const MatFree& F, const double* v, float* g, cudaStream_t st)
   k_expand_rows<<<cdiv(net.m, 256), 256, 0, st>>>(net, v, F.vrow);
   for (int l = 1; l < L; ++l) {
     const int wo = net.widths[l + 1], wi = net.widths[l];
+    if (F.tc3) {
+      // G_l = D_l^T diag(v) H_{l-1} in chunks of kJtvChunk point-stream rows:
+      // each chunk accumulates in TMEM, the chunks add in round-to-nearest
+      // FP32 (beta = 1), so no accumulator runs over all R rows
+      for (int r0 = 0; r0 < net.R; r0 += kJtvChunk) {
+        const int cr = net.R - r0 < kJtvChunk ? net.R - r0 : kJtvChunk;
+        dngd_status s = gemm_tc3(wo, wi, cr, 1.0f, F.D.p[l] + (long long)r0 * wo, wo, true,
+                                 F.H.p[l - 1] + (long long)r0 * wi, wi, true, r0 ? 1.0f : 0.0f, g + net.w_off[l], wi,
+                                 false, *F.tc3, F.status, st, 0u, F.vrow + r0);
+        if (s) return s;
+      }
+      continue;
+    }
     dngd_status s = gemm_tn_comp(wo, wi, net.R, 1.0f, F.D.p[l], wo, F.H.p[l - 1], wi, 0.0f, g + net.w_off[l], wi,
                                  F.vrow, st);
     if (s) return s;
@@ -332,7 +347,11 @@ dngd_status mf_jv(const MatFree& F, const float* u, double* y, cudaStream_t st) 
   for (int l = 0; l < L; ++l) {
     const int wo = net.widths[l + 1], wi = net.widths[l];
     if (l > 0) {
-      dngd_status s = gemm_nt_comp(net.R, wo, wi, 1.0f, F.H.p[l - 1], wi, u + net.w_off[l], wi, 0.0f, F.Y, wo, st);
+      // Y = H_{l-1} U_l^T (K = the layer width)
+      dngd_status s = F.tc3 ? gemm_tc3(net.R, wo, wi, 1.0f, F.H.p[l - 1], wi, false, u + net.w_off[l], wi, false, 0.0f,
+                                       F.Y, wo, false, *F.tc3, F.status, st)
+                            : gemm_nt_comp(net.R, wo, wi, 1.0f, F.H.p[l - 1], wi, u + net.w_off[l], wi, 0.0f, F.Y,
+                                           wo, st);
       if (s) return s;
     }
     DNGD_NOTE_LAUNCH();
@@ -369,9 +388,13 @@ dngd_status mf_kci(const MatFree& F, cudaStream_t st) {
     k_gather_rows<<<cdiv((long long)F.RI * wo, 256), 256, 0, st>>>(F.RI, wo, F.lrows, F.D.p[l], F.DI);
     DNGD_NOTE_LAUNCH();
     k_gather_rows<<<cdiv((long long)F.RI * wi, 256), 256, 0, st>>>(F.RI, wi, F.lrows, Hin, F.HI);
-    dngd_status s = gemm_nt<float>(net.R, F.RI, wo, 1.0f, F.D.p[l], wo, F.DI, wo, 0.0f, F.P, F.RI, false, st);
+    dngd_status s = F.tc3 ? gemm_tc3(net.R, F.RI, wo, 1.0f, F.D.p[l], wo, false, F.DI, wo, false, 0.0f, F.P, F.RI,
+                                     false, *F.tc3, F.status, st)
+                          : gemm_nt<float>(net.R, F.RI, wo, 1.0f, F.D.p[l], wo, F.DI, wo, 0.0f, F.P, F.RI, false, st);
     if (s) return s;
-    s = gemm_nt<float>(net.R, F.RI, wi, 1.0f, Hin, wi, F.HI, wi, 0.0f, F.Q, F.RI, false, st);
+    s = F.tc3 ? gemm_tc3(net.R, F.RI, wi, 1.0f, Hin, wi, false, F.HI, wi, false, 0.0f, F.Q, F.RI, false, *F.tc3,
+                         F.status, st)
+              : gemm_nt<float>(net.R, F.RI, wi, 1.0f, Hin, wi, F.HI, wi, 0.0f, F.Q, F.RI, false, st);
     if (s) return s;
     DNGD_NOTE_LAUNCH();
     k_ghost_accum<<<cdiv(tot, 256), 256, 0, st>>>(net, ell, F.lrow0, F.lS, F.P, F.Q, F.RI, 1, F.KCI, first ? 0 : 1);

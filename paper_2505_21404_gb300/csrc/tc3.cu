@@ -47,7 +47,7 @@ __device__ __forceinline__ float tf32_rn(float x) {
 // dst[r, 0:Kp] = hi, dst[r, Kp:2Kp] = lo of op[r, k]; op = src (row-major
 // [rows x K], ld) or, with trans, src^T (src row-major [K x rows]).
 __global__ void k_tc3_split(int rows, int K, int Kp, const float* __restrict__ src, long long ld, int trans,
-                            float* __restrict__ dst, long long src_z = 0) {
+                            float* __restrict__ dst, long long src_z = 0, const float* __restrict__ kscale = nullptr) {
   // grid.z: independent operands (line-search trials), src + z src_z, dst
   // z rows further on
   src += blockIdx.z * src_z;
@@ -59,11 +59,11 @@ __global__ void k_tc3_split(int rows, int K, int Kp, const float* __restrict__ s
     float v = 0.f;
     if (trans) {
       const int k = k0 + i, r = r0 + tx;
-      if (k < K && r < rows) v = src[(long long)k * ld + r];
+      if (k < K && r < rows) v = src[(long long)k * ld + r] * (kscale ? kscale[k] : 1.f);
       t[tx][i] = v;   // t[r][k]
     } else {
       const int r = r0 + i, k = k0 + tx;
-      if (k < K && r < rows) v = src[(long long)r * ld + k];
+      if (k < K && r < rows) v = src[(long long)r * ld + k] * (kscale ? kscale[k] : 1.f);
       t[i][tx] = v;
     }
   }
@@ -318,7 +318,7 @@ bool cached_map(float* base, int rows, int Kp, CUtensorMap* out) {
 
 dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long lda, bool transA, const float* B,
                      long long ldb, bool transB, float beta, float* C, long long ldc, bool lower, const Tc3Scratch& sc,
-                     int* status, cudaStream_t st, unsigned flags) {
+                     int* status, cudaStream_t st, unsigned flags, const float* kscale_a) {
   if (M <= 0 || N <= 0) return DNGD_OK;
   if (!sc.buf || tc3_scratch_bytes(M, N, K) > sc.bytes || K <= 0) return DNGD_ERR_INVALID_ARG;
   if ((flags & TC3_C_SPLIT) && (lower || N > T3)) return DNGD_ERR_INVALID_ARG;
@@ -332,7 +332,7 @@ dngd_status gemm_tc3(int M, int N, int K, float alpha, const float* A, long long
   float* Bb = same ? Ab : Bh;
   if (!(flags & TC3_A_PRESPLIT)) {
     DNGD_NOTE_LAUNCH();
-    k_tc3_split<<<dim3(Kp / 32, cdiv(M, 32)), 256, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, Ab);
+    k_tc3_split<<<dim3(Kp / 32, cdiv(M, 32)), 256, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, Ab, 0, kscale_a);
   }
   if (!same && !(flags & TC3_B_PRESPLIT)) {
     DNGD_NOTE_LAUNCH();
