@@ -625,10 +625,10 @@ dngd_status upload_landmarks(dngd_ctx* c) {
   if ((int)rows.size() > c->RI_max) return DNGD_ERR_INVALID_ARG;
   c->mf.RI = (int)rows.size();
   c->mf.ell = ell;
-  DNGD_CUDA_CHECK(cudaMemcpy(c->d_lm, c->lm_host.data(), sizeof(int) * ell, cudaMemcpyHostToDevice));
-  DNGD_CUDA_CHECK(cudaMemcpy(c->d_lrows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice));
-  DNGD_CUDA_CHECK(cudaMemcpy(c->d_lrow0, row0.data(), sizeof(int) * ell, cudaMemcpyHostToDevice));
-  DNGD_CUDA_CHECK(cudaMemcpy(c->d_lS, S.data(), sizeof(int) * ell, cudaMemcpyHostToDevice));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->d_lm, c->lm_host.data(), sizeof(int) * ell, cudaMemcpyHostToDevice, c->st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->d_lrows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, c->st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->d_lrow0, row0.data(), sizeof(int) * ell, cudaMemcpyHostToDevice, c->st));
+  DNGD_CUDA_CHECK(cudaMemcpyAsync(c->d_lS, S.data(), sizeof(int) * ell, cudaMemcpyHostToDevice, c->st));
   return DNGD_OK;
 }
 
@@ -859,9 +859,9 @@ dngd_status alloc_pcg(dngd_ctx* c, bool dry, size_t* bytes_out) {
   F.partial_cap = 16LL * (n > m ? n : m);
   F.tc3 = &c->tc3;
   F.status = c->status;
-  DNGD_CUDA_CHECK(cudaMemset(c->a, 0, sizeof(double) * n));
-  DNGD_CUDA_CHECK(cudaMemset(c->scal, 0, sizeof(double) * S_COUNT));
-  DNGD_CUDA_CHECK(cudaMemset(c->status, 0, sizeof(int) * 4));
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->a, 0, sizeof(double) * n, c->st));
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->scal, 0, sizeof(double) * S_COUNT, c->st));
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->scal_h, sizeof(double) * S_COUNT));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->status_h, sizeof(int) * 4));
   for (int i = 0; i < 9; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
@@ -1052,14 +1052,14 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->H3b, double, 3 * rb);
     A_(c->J, double, (size_t)m * c->ldJ);
     // the exact-Gram slicing reads whole padded rows: the pad stays zero
-    if (!f64) DNGD_CUDA_CHECK(cudaMemset(c->J, 0, sizeof(double) * (size_t)m * c->ldJ));
+    if (!f64) DNGD_CUDA_CHECK(cudaMemsetAsync(c->J, 0, sizeof(double) * (size_t)m * c->ldJ, c->st));
   } else {
     A_(c->Hbar, float, rb);
     A_(c->Z3, float, 3 * rb);
     A_(c->H3a, float, 3 * rb);
     A_(c->H3b, float, 3 * rb);
     A_(c->J, float, (size_t)m * c->ldJ);
-    DNGD_CUDA_CHECK(cudaMemset(c->J, 0, sizeof(float) * (size_t)m * c->ldJ));
+    DNGD_CUDA_CHECK(cudaMemsetAsync(c->J, 0, sizeof(float) * (size_t)m * c->ldJ, c->st));
   }
   if (f64) {
     A_(c->K, double, (size_t)m * c->ldk);
@@ -1069,7 +1069,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   } else {
     if (bf) {
       A_(c->Jb, __nv_bfloat16, (size_t)m * c->ldb);
-      DNGD_CUDA_CHECK(cudaMemset(c->Jb, 0, sizeof(__nv_bfloat16) * (size_t)m * c->ldb));
+      DNGD_CUDA_CHECK(cudaMemsetAsync(c->Jb, 0, sizeof(__nv_bfloat16) * (size_t)m * c->ldb, c->st));
     }
     A_(c->K, float, (size_t)m * c->ldk);
     A_(c->K0, float, (size_t)m * c->ldk);
@@ -1123,17 +1123,17 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   A_(c->scal, double, S_COUNT);
   A_(c->status, int, 4);
 #undef A_
-  DNGD_CUDA_CHECK(cudaMemset(c->a, 0, sizeof(double) * n));
-  DNGD_CUDA_CHECK(cudaMemset(c->scal, 0, sizeof(double) * S_COUNT));
-  DNGD_CUDA_CHECK(cudaMemset(c->status, 0, sizeof(int) * 4));
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->a, 0, sizeof(double) * n, c->st));
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->scal, 0, sizeof(double) * S_COUNT, c->st));
+  DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->scal_h, sizeof(double) * S_COUNT));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->status_h, sizeof(int) * 4));
   if (oz) {
     s = gram_oz_plan(&c->oz, c->J, j64, ng, c->ldJ, m, (int)n, c->oz_slices, (float*)c->K, c->ldk, c->K64, c->ldk,
-                     c->oz_partials, c->gram_partial_bytes);
+                     c->oz_partials, c->gram_partial_bytes, c->st);
     if (s) return s;
     gram_oz_set_fp64_out(c->oz, c->Kd);
-    if ((s = oz_factor_plan(&c->ozf, m, c->Kd, c->ldk, c->ozf_work))) return s;
+    if ((s = oz_factor_plan(&c->ozf, m, c->Kd, c->ldk, c->ozf_work, c->st))) return s;
     if ((s = oz_gemm_plan(&c->ozi, m, m, m, c->ozi_work))) return s;
     if (c->ozg_work) {
       if ((s = oz_gemm_plan(&c->ozg, 3 * net.R, net.max_w, net.max_w, c->ozg_work))) return s;
@@ -1143,7 +1143,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     const void* Jlow = bf ? (const void*)c->Jb : (const void*)c->J;
     const long long ld = bf ? c->ldb : c->ldJ;
     s = gram_tc_plan(&c->gram, bf ? 0 : 1, Jlow, m, (int)n, ld, (float*)c->K, c->ldk, c->gram_partials,
-                     c->gram_partial_bytes);
+                     c->gram_partial_bytes, c->st);
     if (s) return s;
   }
   for (int i = 0; i < 9; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));

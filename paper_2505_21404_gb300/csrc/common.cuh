@@ -71,6 +71,23 @@ void note_launch();
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Lets func take up to the device's opt-in maximum of dynamic shared memory
+// (less its static shared memory).  Called once per kernel whose dynamic
+// size depends on the problem: the limit belongs to the function, shared by
+// every context and stream of the process, so it is raised once to the
+// maximum and never set per problem (which would lower it under launches of
+// a larger problem still queued on another stream).
+inline cudaError_t allow_max_dynamic_smem(const void* func) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------

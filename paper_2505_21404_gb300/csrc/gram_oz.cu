@@ -707,7 +707,8 @@ size_t gram_oz_slice_bytes(int m, int n) {
 }
 
 dngd_status gram_oz_plan(OzPlan** out, const void* J, bool j64, int ng, long long ldJ, int m, int n, void* slices,
-                         float* K, long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes) {
+                         float* K, long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes,
+                         cudaStream_t st) {
   if (ng != 5 && ng != 6) return DNGD_ERR_INVALID_ARG;
   EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
   if (!enc) return DNGD_ERR_CUDA;
@@ -761,7 +762,12 @@ dngd_status gram_oz_plan(OzPlan** out, const void* J, bool j64, int ng, long lon
     delete p;
     return DNGD_ERR_OOM;
   }
-  cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
+  if (cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess) {
+    cudaFree(p->d_tiles);
+    delete p;
+    return DNGD_ERR_CUDA;
+  }
   static bool attr5 = false, attr6 = false;
   if (ng == 5 && !attr5) {
     cudaFuncSetAttribute(k_gram_oz<4, 5, OZ_PARTIAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 5>());
@@ -892,7 +898,7 @@ size_t oz_factor_bytes(int m) {
          FNB * sizeof(double) + 1024;
 }
 
-dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void* work) {
+dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void* work, cudaStream_t st) {
   EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
   if (!enc) return DNGD_ERR_CUDA;
   constexpr int TN = OzCfg<FNS, FNG>::TN;
@@ -928,7 +934,8 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
     delete p;
     return DNGD_ERR_CUDA;
   }
-  if (cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess) {
     delete p;
     return DNGD_ERR_CUDA;
   }
@@ -1078,10 +1085,27 @@ void oz_gemm_free(OzGemm* p) { delete p; }
 // cond(L) ~ 1e5 (preconditioned condition number ~1e4 instead of ~2 on the
 // 5-D benchmark late in training, CPU emulation), so they are FP64 products
 // from exact slices: keeping L^{-1} and L^{-T},
-//   T^T = I11^T L21^T,  I21 = -I22 T,  I21^T = -T^T I22^T,
-// each a row-major C = A B^T.
+//   T^T = I11^T L21^T,  I21 = -I22 T  (row-major products C = A B^T)
+// and I21^T by a transpose.
 
 namespace {
+
+// B [cols x rows] = A^T for A [rows x cols] (FP64, 32 x 32 tiles).
+__global__ void k_transpose_f64(int rows, int cols, const double* __restrict__ A, long long lda,
+                                double* __restrict__ B, long long ldb) {
+  __shared__ double t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int i = by + r, j = bx + tx;
+    if (i < rows && j < cols) t[r][tx] = A[(long long)i * lda + j];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bx + r, j = by + tx;   // B[i][j] = A[j][i]
+    if (i < cols && j < rows) B[(long long)i * ldb + j] = t[tx][r];
+  }
+}
 
 // Li = double(Linv) and LiT = its transpose (both [m x ld]).
 __global__ void k_widen_inv(int m, const float* __restrict__ Linv, double* __restrict__ Li,
@@ -1125,9 +1149,11 @@ dngd_status oz_trtri(OzGemm* g, int m, const double* L, long long ldl, const dou
       if ((s = oz_gemm(g, n2, n1, n2, -1.0, I22, ld, TT, n2, false, 0.0, Li + (long long)(k0 + n1) * ld + k0, ld,
                        status, st)))
         return s;
-      if ((s = oz_gemm(g, n1, n2, n2, -1.0, TT, n2, I22, ld, false, 0.0, LiT + (long long)k0 * ld + k0 + n1, ld,
-                       status, st)))
-        return s;
+      // I21^T: the transpose of the block just formed
+      DNGD_NOTE_LAUNCH();
+      k_transpose_f64<<<dim3((unsigned)((n1 + 31) / 32), (unsigned)((n2 + 31) / 32)), 256, 0, st>>>(
+          n2, n1, Li + (long long)(k0 + n1) * ld + k0, ld, LiT + (long long)k0 * ld + k0 + n1, ld);
+      DNGD_LAUNCH_CHECK();
     }
     if ((s = to_float((long long)m * ld, Li, Linv, st))) return s;
     if ((s = to_float((long long)m * ld, LiT, LinvT, st))) return s;

@@ -305,7 +305,7 @@ size_t gram_tc_partial_bytes(int m, int n) {
 }
 
 dngd_status gram_tc_plan(GramPlan** out, int kind, const void* Jlow, int m, int n, long long ld, float* K,
-                         long long ldk, float* partials, size_t partial_bytes) {
+                         long long ldk, float* partials, size_t partial_bytes, cudaStream_t st) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return DNGD_ERR_CUDA;
   GramPlan* p = new GramPlan();
@@ -360,7 +360,13 @@ dngd_status gram_tc_plan(GramPlan** out, int kind, const void* Jlow, int m, int 
     delete p;
     return DNGD_ERR_OOM;
   }
-  cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
+  // stream-ordered before the runs (the host list is staged before return)
+  if (cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess) {
+    cudaFree(p->d_tiles);
+    delete p;
+    return DNGD_ERR_CUDA;
+  }
   static bool attr0 = false, attr1 = false;
   if (kind == 0 && !attr0) {
     cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);

@@ -658,7 +658,11 @@ dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const dou
   }
   const size_t smem = (size_t)maxS * maxw * sizeof(T);
   if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(k_jac_write<T, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool attr = false;
+    if (!attr) {
+      DNGD_CUDA_CHECK(allow_max_dynamic_smem((const void*)k_jac_write<T, TJ>));
+      attr = true;
+    }
   }
   if (J == nullptr) return DNGD_OK;  // matrix-free use: stream adjoints only
   dim3 grid(net.m, L + 1);

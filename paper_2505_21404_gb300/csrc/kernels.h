@@ -161,8 +161,10 @@ size_t gram_oz_partial_bytes(int m, int n, int ng);
 size_t gram_oz_slice_bytes(int m, int n);   // slices + row exponents
 // K: FP32 lower triangle + shift; F: full symmetric Gram as double-float
 // pairs (no shift)
+// Its tile list is uploaded on st (the stream its runs are issued on).
 dngd_status gram_oz_plan(OzPlan** plan, const void* J, bool j64, int ng, long long ldJ, int m, int n, void* slices,
-                         float* K, long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes);
+                         float* K, long long ldk, float2* F, long long ldf, double* partials, size_t partial_bytes,
+                         cudaStream_t st);
 dngd_status gram_oz_read(const OzPlan* plan, double* out, cudaStream_t st);  // F as FP64 [m x ldf]
 dngd_status gram_oz_set_shift(OzPlan* plan, double shift);
 dngd_status gram_oz_run(OzPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
@@ -182,7 +184,7 @@ void gram_oz_set_fp64_out(OzPlan* plan, double* Kd);
 // of the panel kept to 2^-49 of its row's largest).
 struct OzFactor;
 size_t oz_factor_bytes(int m);   // panel slices + row exponents + tile list
-dngd_status oz_factor_plan(OzFactor** plan, int m, double* C, long long ldc, void* work);
+dngd_status oz_factor_plan(OzFactor** plan, int m, double* C, long long ldc, void* work, cudaStream_t st);
 dngd_status oz_factor_run(OzFactor* plan, int* status, cudaStream_t st);
 void oz_factor_free(OzFactor* plan);
 
@@ -324,8 +326,11 @@ dngd_status mf_kii_trace(const MatFree& F, double* out, cudaStream_t st);
 // K (FP32, lower 128x256 tiles) = Jlow Jlow^T with tcgen05 tensor cores.
 // kind: 0 = BF16 operands (Jlow is bf16 [rows x ld]), 1 = TF32 (float).
 struct GramPlan;
+// The tile list is uploaded on st, the stream the runs are issued on (a copy
+// on the legacy stream would not be ordered before work on a non-blocking
+// stream).
 dngd_status gram_tc_plan(GramPlan** plan, int kind, const void* Jlow, int m, int n, long long ld, float* K,
-                         long long ldk, float* partials, size_t partial_bytes);
+                         long long ldk, float* partials, size_t partial_bytes, cudaStream_t st);
 dngd_status gram_tc_run(GramPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
 void gram_tc_free(GramPlan* plan);
 size_t gram_tc_partial_bytes(int m, int n);

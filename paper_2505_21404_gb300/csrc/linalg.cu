@@ -360,12 +360,20 @@ __global__ void __launch_bounds__(256) k_potrf_diag_rcp(int k0, int kb, double* 
   for (int j = 0; j < kb; ++j) {
     if (tid == 0) {
       const double piv = S[j][j];
-      if (!(piv > 0.0)) {
+      if (!(piv > 0.0) || !(piv < 1e300)) {
         bad = j;
       } else {
-        const double d = sqrt(piv);
-        S[j][j] = d;
-        rcp[j] = 1.0 / d;
+        // y = 1 / sqrt(piv) by Newton-Raphson on f(y) = 1/y^2 - piv from a
+        // single-precision start: each step y <- y (3 - piv y^2) / 2 doubles
+        // the correct bits (24 -> 48 -> 53); a few FP64 multiplies instead
+        // of FP64 square root and division sequences
+        const float pf = (float)piv;
+        double y = (double)rsqrtf(pf > 1e-37f ? pf : 1e-37f);
+        if (!(pf > 1e-37f)) y = 1.0 / sqrt(piv);   // outside the float range
+        y = y * (1.5 - 0.5 * piv * y * y);
+        y = y * (1.5 - 0.5 * piv * y * y);
+        S[j][j] = piv * y;   // sqrt(piv)
+        rcp[j] = y;          // 1 / sqrt(piv)
       }
     }
     __syncthreads();
@@ -417,15 +425,13 @@ __global__ void __launch_bounds__(32) k_trsm_panel_rcp(int m, int k0, int kb, do
   }
   __syncwarp();
   if (r0 + tid < m) {
+    // right-looking: once x_j is known it updates the row's remaining
+    // entries, independent multiply-adds the pipe overlaps (a left-looking
+    // dot product would chain them)
     for (int j = 0; j < kb; ++j) {
-      double s0 = X[tid][j], s1 = 0.0;
-      int p = 0;
-      for (; p + 1 < j; p += 2) {   // two independent chains
-        s0 -= X[tid][p] * Lsh[j][p];
-        s1 -= X[tid][p + 1] * Lsh[j][p + 1];
-      }
-      if (p < j) s0 -= X[tid][p] * Lsh[j][p];
-      X[tid][j] = (s0 + s1) * rc[j];
+      const double x = X[tid][j] * rc[j];
+      X[tid][j] = x;
+      for (int k = j + 1; k < kb; ++k) X[tid][k] -= x * Lsh[k][j];
     }
   }
   __syncwarp();
@@ -1135,7 +1141,11 @@ TrtriPlan* trtri_plan(int m, const float* L, long long ldl, float* Linv, long lo
   std::lock_guard<std::mutex> lk(g_trtri_mu);
   for (TrtriPlan* p : g_trtri_plans)
     if (p->m == m && p->L == L && p->ldl == ldl && p->Linv == Linv && p->ldi == ldi && p->work == work) return p;
-  // building a plan allocates and copies: not inside a stream capture
+  // building a plan allocates and copies: not inside a stream capture.  The
+  // node table is uploaded on st, ahead of the launches that read it there
+  // (a copy on the legacy stream would not be ordered before them when st is
+  // a non-blocking stream); a later context can match the plan only once the
+  // buffers it names were released, which synchronised the device
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
   TrtriPlan* p = new TrtriPlan();
@@ -1173,7 +1183,8 @@ TrtriPlan* trtri_plan(int m, const float* L, long long ldl, float* Linv, long lo
   }
   if (!h.empty()) {
     if (cudaMalloc(&p->d_nodes, sizeof(GemmNode) * h.size()) != cudaSuccess ||
-        cudaMemcpy(p->d_nodes, h.data(), sizeof(GemmNode) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpyAsync(p->d_nodes, h.data(), sizeof(GemmNode) * h.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess) {
       cudaGetLastError();
       delete p;
       return nullptr;

@@ -26,6 +26,8 @@
 // are co-resident.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "step_kernels.h"
@@ -473,23 +475,28 @@ static size_t persist_smem(int m) { return 2 * sizeof(float) * (size_t)((m + 3) 
 
 // Blocks of the cooperative grid (co-resident), or 0 if the launch cannot fit.
 static int persist_blocks(int m) {
-  static int cached = -1, cached_m = -1;
-  if (cached >= 0 && cached_m == m) return cached;
+  // one block per SM, so the grid only depends on whether a block with this
+  // m's shared memory fits on an SM at all
+  static std::mutex mu;
+  static bool attr = false;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!attr) {
+    if (allow_max_dynamic_smem((const void*)k_pcg_persist) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    attr = true;
+  }
   int dev = 0, nsm = 0, per = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  const size_t smem = persist_smem(m);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_pcg_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persist, PT, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persist, PT, persist_smem(m)) != cudaSuccess) {
     cudaGetLastError();
     per = 0;
   }
   if (per > 1) per = 1;
-  cached = coop ? per * nsm : 0;
-  cached_m = m;
-  return cached;
+  return coop ? per * nsm : 0;
 }
 
 dngd_status pcg_persist_solve(int m, const float2* K, long long ldk, double lambda, const float* Linv,

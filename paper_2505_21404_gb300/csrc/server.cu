@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -56,6 +57,35 @@ struct Job {
   int m = 0;
 };
 
+// Host copy of a caller's buffer: a plain memcpy from host memory (so a
+// submission never waits behind work queued on the legacy stream), a
+// synchronous device-to-host copy from device memory.
+bool copy_in(void* dst, const void* src, size_t bytes) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, src) != cudaSuccess) {
+    cudaGetLastError();
+    a.type = cudaMemoryTypeUnregistered;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess;
+  memcpy(dst, src, bytes);
+  return false;
+}
+
+// The converse for results: memcpy into host memory, a synchronous
+// host-to-device copy into device memory.
+bool copy_out(void* dst, const void* src, size_t bytes) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, dst) != cudaSuccess) {
+    cudaGetLastError();
+    a.type = cudaMemoryTypeUnregistered;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess;
+  memcpy(dst, src, bytes);
+  return false;
+}
+
 }  // namespace
 
 struct dngd_server {
@@ -86,7 +116,8 @@ void dngd_server::release(Job* j, int state, dngd_status st) {
   if (j->ctx) {
     cudaStreamSynchronize(j->st);
     if (state == DNGD_JOB_DONE) {
-      cudaMemcpy(j->theta.data(), j->d_theta, sizeof(double) * j->n, cudaMemcpyDeviceToHost);
+      cudaMemcpyAsync(j->theta.data(), j->d_theta, sizeof(double) * j->n, cudaMemcpyDeviceToHost, j->st);
+      cudaStreamSynchronize(j->st);
     }
     dngd_destroy(j->ctx);
     j->ctx = nullptr;
@@ -155,9 +186,12 @@ bool dngd_server::admit_one() {
   dal(&j->d_X, j->X.size());
   dal(&j->d_target, j->m);
   dal(&j->d_delta, j->n);
-  if (!s && (cudaMemcpy(j->d_theta, j->theta.data(), sizeof(double) * j->n, cudaMemcpyHostToDevice) ||
-             cudaMemcpy(j->d_X, j->X.data(), sizeof(double) * j->X.size(), cudaMemcpyHostToDevice) ||
-             cudaMemcpy(j->d_target, j->target.data(), sizeof(double) * j->m, cudaMemcpyHostToDevice)))
+  // the inputs go up on the job's own stream, ahead of its first step there
+  // (the job streams are non-blocking: a copy on the legacy stream would not
+  // be ordered before that step)
+  if (!s && (cudaMemcpyAsync(j->d_theta, j->theta.data(), sizeof(double) * j->n, cudaMemcpyHostToDevice, j->st) ||
+             cudaMemcpyAsync(j->d_X, j->X.data(), sizeof(double) * j->X.size(), cudaMemcpyHostToDevice, j->st) ||
+             cudaMemcpyAsync(j->d_target, j->target.data(), sizeof(double) * j->m, cudaMemcpyHostToDevice, j->st)))
     s = DNGD_ERR_CUDA;
   if (!s && (cudaEventCreate(&j->ev0) || cudaEventCreate(&j->ev1))) s = DNGD_ERR_CUDA;
   if (s) release(j, DNGD_JOB_FAILED, s);
@@ -292,9 +326,8 @@ dngd_status dngd_submit(dngd_server* s, const dngd_job_desc* job, uint64_t* job_
   j->theta.resize(n);
   j->X.resize((size_t)m * d);
   j->target.resize(m);
-  if (cudaMemcpy(j->theta.data(), job->theta0, sizeof(double) * n, cudaMemcpyDefault) ||
-      cudaMemcpy(j->X.data(), job->X, sizeof(double) * m * d, cudaMemcpyDefault) ||
-      cudaMemcpy(j->target.data(), job->target, sizeof(double) * m, cudaMemcpyDefault)) {
+  if (copy_in(j->theta.data(), job->theta0, sizeof(double) * n) ||
+      copy_in(j->X.data(), job->X, sizeof(double) * m * d) || copy_in(j->target.data(), job->target, sizeof(double) * m)) {
     delete j;
     return DNGD_ERR_CUDA;
   }
@@ -324,8 +357,7 @@ dngd_status dngd_poll(dngd_server* s, uint64_t job_id, dngd_job_state* out, doub
   out->queue_s = (j->start_t > 0 ? j->start_t : now_s()) - j->submit_t;
   out->run_s = j->start_t > 0 ? ((j->end_t > 0 ? j->end_t : now_s()) - j->start_t) : 0.0;
   if (theta_out && j->state == DNGD_JOB_DONE)
-    if (cudaMemcpy(theta_out, j->theta.data(), sizeof(double) * j->n, cudaMemcpyDefault) != cudaSuccess)
-      return DNGD_ERR_CUDA;
+    if (copy_out(theta_out, j->theta.data(), sizeof(double) * j->n)) return DNGD_ERR_CUDA;
   return DNGD_OK;
 }
 

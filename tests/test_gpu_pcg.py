@@ -118,3 +118,38 @@ def test_all_landmarks_converge_in_one_iteration(dngd):
     prob = ores.problem_from_spec(wl)
     dense = ostep.dense_step(wl["theta"], prob, wl["X"], wl["target"], wl["lam"])
     assert _rel(delta, dense["delta"]) <= 1e-3
+
+
+def test_operator_and_dual_solve_several_row_chunks(dngd):
+    """The matrix-free J^T v runs over the point-stream rows in chunks of 1024
+    on the tensor cores.  Here R = 4 * 400 + 64 + 64 = 1,728 rows (two
+    chunks) and width 256: K v against (J J^T + lambda I) v from the FP64
+    Jacobian of a dense context at the same theta, and the converged dual
+    solve's true residual ||r - (K + lambda I) alpha|| / ||r|| against the
+    PCG tolerance."""
+    wl = workloads.heat_1d([2, 256, 256, 256, 1], 400, 64, 64, kappa=0.1, seed=2, lam=1e-3)
+    th, X, tg = _t(wl["theta"]), _t(wl["X"]), _t(wl["target"])
+    dense = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64))
+    m = dense.m
+    r = torch.zeros(m, dtype=torch.float64, device=DEV)
+    J = torch.zeros(m, dense.n, dtype=torch.float64, device=DEV)
+    dense.residual_jacobian(th, X, tg, r, J)
+    ctx = dngd.Context(dngd.make_desc(wl, precision=dngd.MIXED_BF16, solver=dngd.PCG, pcg_rank=64, pcg_tol=1e-8,
+                                      pcg_max_it=400))
+    ctx.set_landmarks(workloads.landmarks(m, 64, seed=3))
+    delta = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
+    info = ctx.step(th, X, tg, delta)
+    lam = wl["lam"]
+    v = torch.tensor(np.random.default_rng(7).normal(size=m), device=DEV)
+    w = torch.zeros_like(v)
+    ctx.kvp(v, w)
+    ref = J @ (J.T @ v) + lam * v
+    torch.cuda.synchronize()
+    assert _rel(w, ref.cpu().numpy()) <= 1e-5
+    alpha = torch.zeros(m, dtype=torch.float64, device=DEV)
+    ctx.get_stage("alpha", alpha)
+    true_res = float(((r - (J @ (J.T @ alpha) + lam * alpha)).norm() / r.norm()).item())
+    assert info["solve_relres"][0] <= 1e-8, info
+    assert true_res <= 1e-5, (true_res, info)
+    dense.close()
+    ctx.close()

@@ -161,3 +161,24 @@ def test_cancel(dngd):
     i0, th0 = srv.result(j0)
     assert i0["state"] == "done" and np.array_equal(th0, ref)
     srv.close()
+
+
+def test_job_setup_ordered_on_its_stream_while_legacy_stream_busy(dngd):
+    """Jobs run on non-blocking streams, which are not ordered after work on
+    the legacy default stream.  A job admitted while that stream is still
+    busy (one spinning block queued there first) must still see its zeroed
+    buffers, tile lists and inputs: its set-up is issued on its own stream,
+    so it ends exactly as when it runs alone on an idle device."""
+    wls = _jobs()
+    ref = [_run_alone(dngd, wls[i], 3) for i in (3, 5)]
+    srv = dngd.Server(max_slots=2)
+    torch.cuda.synchronize()
+    torch.cuda._sleep(int(3e9))   # ~1.5 s of one block on the legacy stream
+    ids = [srv.submit(_desc(dngd, wls[i]), wls[i]["theta"], wls[i]["X"], wls[i]["target"], 3) for i in (3, 5)]
+    srv.drain(300)
+    for jid, r in zip(ids, ref):
+        info, theta = srv.result(jid)
+        assert info["state"] == "done", info
+        assert np.array_equal(theta, r)
+    srv.close()
+    torch.cuda.synchronize()
