@@ -31,13 +31,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D-NGD steps/s mixed vs FP64 at equal step error; Gram TFLOP/s; p99 step latency"
 UNIT = "steps/s"
-DTYPES = {"oz": "bf16 tensor (exact integer slices) / f32 jets and factor / f64 Gram operator",
-          "oz64": "f64 jets and Jacobian / bf16 tensor (exact integer slices, 5 per entry) / f32 factor / "
-                  "f64 Gram operator",
+DTYPES = {"oz": "f32 jets and Jacobian / bf16 tensor (exact integer slices, 4 per entry, 13 products) / f64 "
+                "factor, f32 preconditioner / f64 Gram operator",
+          "oz64": "f64 jets and Jacobian / bf16 tensor (exact integer slices, 4 per entry, 15 products) / f64 "
+                  "factor, f32 preconditioner / f64 Gram operator",
           "bf16": "bf16/f32 (double-float accumulation in the refinement)",
           "tf32": "tf32/f32 (double-float accumulation in the refinement)"}
 L2_NOTE = {"oz": "working set larger than L2 (J: 2.13 GB FP32, slices 4.27 GB BF16, Gram 128 MB FP64 per step)",
-           "oz64": "working set larger than L2 (J: 4.27 GB FP64, slices 5.3 GB BF16, Gram 128 MB FP64 per step)",
+           "oz64": "working set larger than L2 (J: 4.27 GB FP64, slices 4.27 GB BF16, Gram 128 MB FP64 per step)",
            "bf16": "working set larger than L2 (J: 2.13 GB FP32 + 1.07 GB BF16 per step)",
            "tf32": "working set larger than L2 (J: 2.13 GB FP32 per step)"}
 WORKLOAD = "poisson5d_dense: -Lap u = f on [0,1]^5, MLP 5-256-256-256-1 (n=133377), 3000+1000 pts (m=4000)"
@@ -855,7 +856,7 @@ def run_dense(args, wl, rank, world, local_rank):
 
     hbm, bf16_burst, bf16_sust, src = _peaks()
     alg_flops = float(m) * (m + 1) * n
-    exec_flops = alg_flops * {dngd.MIXED_OZ: 13, dngd.MIXED_OZ64: 19}.get(prec, 1)
+    exec_flops = alg_flops * {dngd.MIXED_OZ: 13, dngd.MIXED_OZ64: 15}.get(prec, 1)
     achieved = alg_flops / (gram_ms * 1e-3) / 1e12
     executed = exec_flops / (gram_ms * 1e-3) / 1e12
     peak = bf16_sust / 2.0 if prec == dngd.MIXED_TF32 else bf16_sust
@@ -892,8 +893,8 @@ def run_dense(args, wl, rank, world, local_rank):
                      "algorithmic": "m(m+1)n flop per Gram (the syrk of the 5-D workload, 2.135e12)",
                      "flops_per_launch": alg_flops, "launch_ms": gram_ms,
                      "executed_tflops": executed, "executed_frac": executed / peak,
-                     "executed": ("19 m(m+1)n BF16 tensor flop (the 19 products of five slices)"
-                                  if prec == dngd.MIXED_OZ64 else
+                     "executed": ("15 m(m+1)n BF16 tensor flop (the 15 slice products of levels <= 5 of four "
+                                  "slices)" if prec == dngd.MIXED_OZ64 else
                                   "13 m(m+1)n BF16 tensor flop (the 13 products of four slices)"),
                      "peak_source": f"{src} bf16 sustained",
                      "traffic": args.gram_traffic if args.workload == "poisson5d" else None,

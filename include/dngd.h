@@ -100,6 +100,12 @@ enum dngd_solver {
                       (FP32 jets and FP32 factor-form operator) */
 };
 
+/* GEMMs of the matrix-free operator (dngd_problem_desc.pcg_operator) */
+enum dngd_pcg_operator {
+  DNGD_PCG_OP_TC3 = 0,          /* 3xTF32 on the tensor cores */
+  DNGD_PCG_OP_COMPENSATED = 1   /* FP32 SIMT, compensated accumulation */
+};
+
 #define DNGD_MAX_LAYERS 12
 #define DNGD_MAX_DIM 8
 #define DNGD_MAX_CLASSES 4
@@ -156,6 +162,17 @@ typedef struct {
                                         asynchronous and batched steps keep
                                         the lambda of the last synchronous
                                         step.  0: fixed lambda. */
+  int pcg_operator;                  /* enum dngd_pcg_operator (DNGD_PCG): the
+                                        GEMMs of the factor-form operator
+                                        K v = J (J^T v) and of the landmark
+                                        columns.  0: 3xTF32 on the
+                                        tensor cores (operands split into two
+                                        TF32 terms, three products, FP32
+                                        accumulation in 1,024-row chunks);
+                                        1: FP32 SIMT with compensated
+                                        (Kahan) accumulation and FP64 row
+                                        reductions, slower and more
+                                        accurate (see dngd_kvp). */
 } dngd_problem_desc;
 
 typedef struct {
@@ -287,7 +304,13 @@ dngd_status dngd_set_landmarks(dngd_ctx* ctx, const int64_t* idx, int ell);
 
 /* Kernel-vector product w = J (J^T v) + lambda v (Def. 3.3) with the stream
  * factors of the last dngd_step, J never formed.  v [m] -> w_out [m].
- * PCG contexts only (STATE before the first step). */
+ * PCG contexts only (STATE before the first step).  Accuracy: the 3xTF32
+ * operator's products keep about 2^-22 of each FP32 operand (the split drops
+ * the third TF32 term) and sum in FP32 chunks; the compensated operator
+ * rounds each FP32 product once and sums with Kahan compensation.  CG with
+ * an inexact product converges on its recursive residual, while the true
+ * residual ||rhs - (K + lambda I) x|| stalls near the product's error times
+ * cond(K + lambda I). */
 dngd_status dngd_kvp(dngd_ctx* ctx, const double* v, double* w_out);
 
 /* Nystrom preconditioner of the last step: z = P^{-1} x with

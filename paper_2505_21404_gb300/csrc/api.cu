@@ -857,7 +857,9 @@ dngd_status alloc_pcg(dngd_ctx* c, bool dry, size_t* bytes_out) {
   F.xs = c->xs;
   F.partials = c->partials;
   F.partial_cap = 16LL * (n > m ? n : m);
-  F.tc3 = &c->tc3;
+  // the factor-form operator's GEMMs: 3xTF32 tensor cores, or compensated
+  // FP32 SIMT (null)
+  F.tc3 = c->desc.pcg_operator == DNGD_PCG_OP_COMPENSATED ? nullptr : &c->tc3;
   F.status = c->status;
   DNGD_CUDA_CHECK(cudaMemsetAsync(c->a, 0, sizeof(double) * n, c->st));
   DNGD_CUDA_CHECK(cudaMemsetAsync(c->scal, 0, sizeof(double) * S_COUNT, c->st));
@@ -1234,6 +1236,8 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
   if (desc->solver != DNGD_DENSE && desc->solver != DNGD_PCG) return DNGD_ERR_INVALID_ARG;
   if (desc->solver == DNGD_PCG && jets64(desc->precision)) return DNGD_ERR_INVALID_ARG;
   if (!lambda_ok(desc->precision, desc->lambda) || !(desc->lambda_cap >= 0.0) || !isfinite(desc->lambda_cap))
+    return DNGD_ERR_INVALID_ARG;
+  if (desc->pcg_operator != DNGD_PCG_OP_TC3 && desc->pcg_operator != DNGD_PCG_OP_COMPENSATED)
     return DNGD_ERR_INVALID_ARG;
   gemv_init();
   dngd_ctx* c = new dngd_ctx();
