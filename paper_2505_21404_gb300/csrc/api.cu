@@ -332,10 +332,14 @@ dngd_status residual_jacobian_T(dngd_ctx* c, const T* thT, const double* X, cons
   dngd_status s = jets_forward<T>(c->net, thT, X, target, lp<T>(c->Z), lp<T>(c->H), c->r, c->status, c->st, t3,
                                   true);
   if (s) return s;
-  // the exact Gram's slicing takes each row's largest |J| from the writer
+  // the exact Gram's slicing takes each row's largest |J| from the writer;
+  // its FP64 Jacobian is written in double-float arithmetic: ~46 bits,
+  // where the slices keep 33 of each row's largest entry and the map-back
+  // J^T x needs no more)
   return jets_backward_jacobian<T, T>(c->net, thT, X, lp<T>(c->Z), lp<T>(c->H), lp<T>(c->D), (T*)c->Hbar,
                                       (T*)c->J, c->ldJ, c->prec == DNGD_MIXED_BF16 ? c->Jb : nullptr, c->ldb,
-                                      c->st, t3, c->status, c->oz ? gram_oz_rowmax(c->oz) : nullptr);
+                                      c->st, t3, c->status, c->oz ? gram_oz_rowmax(c->oz) : nullptr,
+                                      c->prec == DNGD_MIXED_OZ64);
 }
 
 // ---------------------------------------------------------------------------

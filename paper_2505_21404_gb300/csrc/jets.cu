@@ -224,7 +224,12 @@ __global__ void k_act_bwd(NetInfo net, int l, const T* __restrict__ theta, const
 }
 
 // Jacobian rows: block (point p, layer l) writes dr_p/dW_l and dr_p/db_l.
-template <typename T, typename TJ>
+// DF (FP64 data only): each entry sum_s d_s h_s is formed in double-float
+// arithmetic on the FP32 pipes (both factors split into FP32 hi + lo, the
+// hi products exact by fma, the cross terms added, the sum carried as an
+// unevaluated hi + lo pair) and rounded to FP64 once: ~2^-46 of the sum of
+// the terms' magnitudes, at FP32 instead of FP64 throughput.
+template <typename T, typename TJ, bool DF = false>
 __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const double* __restrict__ X,
                             LayerPtrs<T> Hs, LayerPtrs<T> Ds, TJ* __restrict__ J, long long ldJ,
                             __nv_bfloat16* __restrict__ Jb, long long ldb, unsigned* __restrict__ rowmax) {
@@ -269,6 +274,44 @@ __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const doub
   __nv_bfloat16* Jbrow = Jb ? Jb + (long long)p * ldb : nullptr;
   const long long wo = net.w_off[l], bo = net.b_off[l];
   float amax = 0.f;   // largest |J| this block writes (as stored)
+  if constexpr (DF && std::is_same<T, double>::value) {
+    // adjoints as FP32 pairs after the two FP64 tiles
+    float2* d2 = reinterpret_cast<float2*>(sm + S * wout + S * win);
+    for (int e = threadIdx.x; e < S * wout; e += blockDim.x) {
+      const double v = dsh[e];
+      const float h = (float)v;
+      d2[e] = make_float2(h, (float)(v - (double)h));
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < win; b += blockDim.x) {
+      float hh[2 + kMaxDim], hl[2 + kMaxDim];
+#pragma unroll
+      for (int s = 0; s < 2 + kMaxDim; ++s) {
+        const double v = s < S ? hsh[s * win + b] : 0.0;
+        hh[s] = (float)v;
+        hl[s] = (float)(v - (double)hh[s]);
+      }
+      for (int a = 0; a < wout; ++a) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int s = 0; s < 2 + kMaxDim; ++s) {
+          if (s >= S) break;
+          const float2 d = d2[s * wout + a];
+          const float pr = d.x * hh[s];
+          float e = fmaf(d.x, hh[s], -pr);   // exact residual of the hi product
+          e = fmaf(d.x, hl[s], e);
+          e = fmaf(d.y, hh[s], e);
+          float t, te;
+          two_sum(hi, pr, t, te);
+          hi = t;
+          lo += te + e;
+        }
+        const double v = (double)hi + (double)lo;
+        Jrow[wo + (long long)a * win + b] = (TJ)v;
+        amax = fmaxf(amax, fabsf((float)v));
+      }
+    }
+  } else
   for (int b = threadIdx.x; b < win; b += blockDim.x) {
     // the stream loops are unrolled to the largest S so hreg stays in registers
     T hreg[2 + kMaxDim];
@@ -633,7 +676,7 @@ template <typename T, typename TJ>
 dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
                                    LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
                                    __nv_bfloat16* Jb, long long ldb, cudaStream_t st, const Tc3Scratch* tc3,
-                                   int* status, unsigned* rowmax) {
+                                   int* status, unsigned* rowmax, bool df64) {
   const int L = net.n_layers - 1;
   const int thr = 128;
   for (int l = L - 1; l >= 0; --l) {
@@ -656,19 +699,29 @@ dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const dou
     const int ws = net.widths[l + 1] + net.widths[l];
     maxw = ws > maxw ? ws : maxw;
   }
-  const size_t smem = (size_t)maxS * maxw * sizeof(T);
+  int maxwo = 1;
+  for (int l = 0; l <= L; ++l) maxwo = net.widths[l + 1] > maxwo ? net.widths[l + 1] : maxwo;
+  const bool df = df64 && std::is_same<T, double>::value;
+  const size_t smem = (size_t)maxS * maxw * sizeof(T) + (df ? (size_t)maxS * maxwo * sizeof(float2) : 0);
   if (smem > 48 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      DNGD_CUDA_CHECK(allow_max_dynamic_smem((const void*)k_jac_write<T, TJ>));
+    static bool attr = false, attr_df = false;
+    if (!df && !attr) {
+      DNGD_CUDA_CHECK(allow_max_dynamic_smem((const void*)k_jac_write<T, TJ, false>));
       attr = true;
+    }
+    if (df && !attr_df) {
+      DNGD_CUDA_CHECK(allow_max_dynamic_smem((const void*)k_jac_write<T, TJ, true>));
+      attr_df = true;
     }
   }
   if (J == nullptr) return DNGD_OK;  // matrix-free use: stream adjoints only
   dim3 grid(net.m, L + 1);
   if (rowmax) DNGD_CUDA_CHECK(cudaMemsetAsync(rowmax, 0, sizeof(unsigned) * net.m, st));
   DNGD_NOTE_LAUNCH();
-  k_jac_write<T, TJ><<<grid, 256, smem, st>>>(net, theta, X, H, D, J, ldJ, Jb, ldb, rowmax);
+  if (df)
+    k_jac_write<T, TJ, true><<<grid, 256, smem, st>>>(net, theta, X, H, D, J, ldJ, Jb, ldb, rowmax);
+  else
+    k_jac_write<T, TJ, false><<<grid, 256, smem, st>>>(net, theta, X, H, D, J, ldJ, Jb, ldb, rowmax);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
@@ -724,12 +777,12 @@ template dngd_status jets_backward_jacobian<double, double>(const NetInfo&, cons
                                                             LayerPtrs<double>, LayerPtrs<double>,
                                                             LayerPtrs<double>, double*, double*, long long,
                                                             __nv_bfloat16*, long long, cudaStream_t,
-                                                            const Tc3Scratch*, int*, unsigned*);
+                                                            const Tc3Scratch*, int*, unsigned*, bool);
 template dngd_status jets_backward_jacobian<float, float>(const NetInfo&, const float*, const double*,
                                                           LayerPtrs<float>, LayerPtrs<float>,
                                                           LayerPtrs<float>, float*, float*, long long,
                                                           __nv_bfloat16*, long long, cudaStream_t,
-                                                          const Tc3Scratch*, int*, unsigned*);
+                                                          const Tc3Scratch*, int*, unsigned*, bool);
 template dngd_status jets_fvv<double>(const NetInfo&, const double*, const double*, const double*, double*,
                                       double*, double*, double*, cudaStream_t, const Tc3Scratch*, int*);
 template dngd_status jets_fvv<float>(const NetInfo&, const float*, const float*, const double*, float*,

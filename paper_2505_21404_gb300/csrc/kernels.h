@@ -29,12 +29,14 @@ dngd_status jets_forward_trials(const NetInfo& net, int G, const float* theta_b,
                                 const double* target, float* Zb, float* Hb, double* rb, int* status, cudaStream_t st,
                                 const Tc3Scratch& tc3);
 
+// df64 (FP64 data): J's entries in double-float arithmetic (k_jac_write,
+// ~2^-46 relative), for Jacobians whose consumer keeps fewer bits.
 template <typename T, typename TJ>
 dngd_status jets_backward_jacobian(const NetInfo& net, const T* theta, const double* X, LayerPtrs<T> Z,
                                    LayerPtrs<T> H, LayerPtrs<T> D, T* Hbar, TJ* J, long long ldJ,
                                    __nv_bfloat16* Jb, long long ldb, cudaStream_t st,
                                    const Tc3Scratch* tc3 = nullptr, int* status = nullptr,
-                                   unsigned* rowmax = nullptr);
+                                   unsigned* rowmax = nullptr, bool df64 = false);
 
 template <typename T>
 dngd_status jets_fvv(const NetInfo& net, const T* theta, const T* v, const double* X, T* Z3, T* H3a,

@@ -341,46 +341,51 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 template dngd_status cholesky<double>(int, double*, long long, int*, double*, cudaStream_t);
 
 // FP64 diagonal block of one factorisation step, organised for GB300's slow
-// FP64 pipe: one reciprocal per column (the panel below multiplies by it
-// instead of dividing), the rank-1 update spread over a 16 x 16 thread grid.
-// The block's L and the reciprocals of its diagonal (rdiag[kb]) go to
-// global memory.
+// FP64 pipe: one reciprocal square root per column (Newton-Raphson from a
+// single-precision estimate; the panel below multiplies by it instead of
+// dividing), warp 0 scales the column, the rank-1 update is spread over a
+// 16 x 16 thread grid: two barriers per column.  The block's L and the
+// reciprocals of its diagonal (rdiag[kb]) go to global memory.
 __global__ void __launch_bounds__(256) k_potrf_diag_rcp(int k0, int kb, double* A, long long lda,
                                                         double* __restrict__ rdiag, int* status) {
   __shared__ double S[kCholNB][kCholNB + 1];
   __shared__ double rcp[kCholNB];
   __shared__ int bad;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
-    const int i = e / kb, j = e % kb;
-    S[i][j] = (j <= i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+#pragma unroll 4
+  for (int e = tid; e < kCholNB * kCholNB; e += 256) {
+    const int i = e >> 6, j = e & (kCholNB - 1);
+    S[i][j] = (i < kb && j <= i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
   }
   if (tid == 0) bad = -1;
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    if (tid == 0) {
+    if (tid < 32) {
+      // y = 1 / sqrt(piv) by Newton-Raphson on f(y) = 1/y^2 - piv from a
+      // single-precision start: each step y <- y (3 - piv y^2) / 2 doubles
+      // the correct bits (24 -> 48 -> 53)
       const double piv = S[j][j];
-      if (!(piv > 0.0) || !(piv < 1e300)) {
-        bad = j;
-      } else {
-        // y = 1 / sqrt(piv) by Newton-Raphson on f(y) = 1/y^2 - piv from a
-        // single-precision start: each step y <- y (3 - piv y^2) / 2 doubles
-        // the correct bits (24 -> 48 -> 53); a few FP64 multiplies instead
-        // of FP64 square root and division sequences
+      const bool ok = piv > 0.0 && piv < 1e300;
+      double y = 0.0;
+      if (ok) {
         const float pf = (float)piv;
-        double y = (double)rsqrtf(pf > 1e-37f ? pf : 1e-37f);
+        y = (double)rsqrtf(pf > 1e-37f ? pf : 1e-37f);
         if (!(pf > 1e-37f)) y = 1.0 / sqrt(piv);   // outside the float range
         y = y * (1.5 - 0.5 * piv * y * y);
         y = y * (1.5 - 0.5 * piv * y * y);
-        S[j][j] = piv * y;   // sqrt(piv)
-        rcp[j] = y;          // 1 / sqrt(piv)
+        for (int i = j + 1 + lane; i < kb; i += 32) S[i][j] *= y;
+      }
+      if (lane == 0) {
+        if (ok) {
+          S[j][j] = piv * y;   // sqrt(piv)
+          rcp[j] = y;
+        } else {
+          bad = j;
+        }
       }
     }
     __syncthreads();
     if (bad >= 0) break;
-    const double r = rcp[j];
-    for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] *= r;
-    __syncthreads();
     for (int i = j + 1 + ty; i < kb; i += 16) {
       const double lij = S[i][j];
       for (int c = j + 1 + tx; c <= i; c += 16) S[i][c] -= lij * S[c][j];
@@ -394,51 +399,62 @@ __global__ void __launch_bounds__(256) k_potrf_diag_rcp(int k0, int kb, double* 
     }
     return;
   }
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
-    const int i = e / kb, j = e % kb;
-    if (j <= i) A[(long long)(k0 + i) * lda + k0 + j] = S[i][j];
+#pragma unroll 4
+  for (int e = tid; e < kCholNB * kCholNB; e += 256) {
+    const int i = e >> 6, j = e & (kCholNB - 1);
+    if (i < kb && j <= i) A[(long long)(k0 + i) * lda + k0 + j] = S[i][j];
   }
   if (tid < kb) rdiag[tid] = rcp[tid];
 }
 
-// Panel rows [k0 + kb, m): x L11^T = a by forward substitution, one thread
-// per row, 32 rows per CTA (so the rows spread over the SMs), multiplying by
-// the diagonal's reciprocals.
-__global__ void __launch_bounds__(32) k_trsm_panel_rcp(int m, int k0, int kb, double* A, long long lda,
-                                                       const double* __restrict__ rdiag, const int* status) {
+// Panel rows [k0 + kb, m): X L11^T = A_panel by forward substitution, with
+// the diagonal's reciprocals.  A CTA takes 32 rows with 256 threads, eight
+// per row: thread (row r, q) keeps columns q, q + 8, ... of its row in
+// registers; once x_j is final its owner scales it and a width-8 shuffle
+// hands it to the row's other threads, which update their later columns.
+// Loads and stores use every thread, so the CTA keeps many in flight (the
+// kernel is latency-bound on GB300's FP64 pipe otherwise).
+constexpr int kPanelRows = 32;
+__global__ void __launch_bounds__(256) k_trsm_panel_rcp(int m, int k0, int kb, double* A, long long lda,
+                                                        const double* __restrict__ rdiag, const int* status) {
   if (status[0] & ST_NOT_SPD) return;
-  extern __shared__ double panel_smem[];
-  double(*Lsh)[kCholNB] = reinterpret_cast<double(*)[kCholNB]>(panel_smem);         // read by broadcast
-  double(*X)[kCholNB + 1] = reinterpret_cast<double(*)[kCholNB + 1]>(panel_smem + kCholNB * kCholNB);
-  double* rc = panel_smem + kCholNB * kCholNB + 32 * (kCholNB + 1);
+  __shared__ double Lsh[kCholNB][kCholNB + 1];   // strictly lower part of L11, zero elsewhere
+  __shared__ double rc[kCholNB];
   const int tid = threadIdx.x;
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
-    const int i = e / kb, j = e % kb;
-    Lsh[i][j] = (j < i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
+#pragma unroll 4
+  for (int e = tid; e < kCholNB * kCholNB; e += 256) {
+    const int i = e >> 6, j = e & (kCholNB - 1);
+    Lsh[i][j] = (i < kb && j < i) ? A[(long long)(k0 + i) * lda + k0 + j] : 0.0;
   }
-  for (int j = tid; j < kb; j += blockDim.x) rc[j] = rdiag[j];
-  const int r0 = k0 + kb + blockIdx.x * 32;
-  for (int e = tid; e < 32 * kb; e += blockDim.x) {
-    const int rr = e / kb, j = e % kb;
-    const int gr = r0 + rr;
-    X[rr][j] = (gr < m) ? A[(long long)gr * lda + k0 + j] : 0.0;
+  if (tid < kCholNB) rc[tid] = tid < kb ? rdiag[tid] : 0.0;
+  const int q = tid & 7;
+  const long long g = (long long)k0 + kb + (long long)blockIdx.x * kPanelRows + (tid >> 3);
+  const bool live = g < m;
+  double x[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int j = q + 8 * t;
+    x[t] = (live && j < kb) ? A[g * lda + k0 + j] : 0.0;
   }
-  __syncwarp();
-  if (r0 + tid < m) {
-    // right-looking: once x_j is known it updates the row's remaining
-    // entries, independent multiply-adds the pipe overlaps (a left-looking
-    // dot product would chain them)
-    for (int j = 0; j < kb; ++j) {
-      const double x = X[tid][j] * rc[j];
-      X[tid][j] = x;
-      for (int k = j + 1; k < kb; ++k) X[tid][k] -= x * Lsh[k][j];
+  __syncthreads();
+  const int base = (tid & 31) & ~7;   // first lane of this row's group
+#pragma unroll
+  for (int j = 0; j < kCholNB; ++j) {
+    const int t = j >> 3, owner = j & 7;
+    double xj = 0.0;
+    if (q == owner) {
+      x[t] *= rc[j];
+      xj = x[t];
     }
+    xj = __shfl_sync(0xffffffffu, xj, base + owner);
+#pragma unroll
+    for (int u = t; u < 8; ++u)
+      if (q + 8 * u > j) x[u] -= xj * Lsh[q + 8 * u][j];
   }
-  __syncwarp();
-  for (int e = tid; e < 32 * kb; e += blockDim.x) {
-    const int rr = e / kb, j = e % kb;
-    const int g = r0 + rr;
-    if (g < m) A[(long long)g * lda + k0 + j] = X[rr][j];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int j = q + 8 * t;
+    if (live && j < kb) A[g * lda + k0 + j] = x[t];
   }
 }
 
@@ -452,14 +468,8 @@ dngd_status chol_step_f64(int m, int k0, double* A, long long lda, double* rdiag
   DNGD_LAUNCH_CHECK();
   const int rest = m - k0 - kb;
   if (rest > 0) {
-    const int smem = (kCholNB * kCholNB + 32 * (kCholNB + 1) + kCholNB) * (int)sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
-      DNGD_CUDA_CHECK(cudaFuncSetAttribute(k_trsm_panel_rcp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      attr_set = true;
-    }
     DNGD_NOTE_LAUNCH();
-    k_trsm_panel_rcp<<<cdiv(rest, 32), 32, smem, st>>>(m, k0, kb, A, lda, rdiag, status);
+    k_trsm_panel_rcp<<<cdiv(rest, kPanelRows), 256, 0, st>>>(m, k0, kb, A, lda, rdiag, status);
     DNGD_LAUNCH_CHECK();
   }
   return DNGD_OK;
