@@ -270,6 +270,51 @@ dngd_status dngd_line_search(dngd_ctx* ctx, const double* theta, const double* X
 dngd_status dngd_line_search_async(dngd_ctx* ctx, double* theta, const double* X, const double* target,
                                    const double* delta, const double* etas, int k);
 
+/* ---- the optimizer loop ------------------------------------------------------
+ * D-NGD training (Alg. "D-NGD Workflow"): each iteration takes one step
+ * (dngd_step, so the descriptor's damping rule lambda_k = min(L, cap) of
+ * App. A.3 applies) and the grid line search with the update of theta, until
+ * max_iters iterations, the wall-clock budget or the loss target.  Between
+ * iterations the collocation points may be resampled (the paper redraws them
+ * for several problems): the callback rewrites X [m x d] and target [m] in
+ * place, every `resample_every` iterations, and must have finished its writes
+ * when it returns.  A step that reports NO_CONVERGE is still taken; any other
+ * failure ends the loop with that status (theta then holds the last iterate).
+ */
+typedef dngd_status (*dngd_resample_fn)(void* user, int iteration, double* X, double* target);
+
+typedef struct {
+  int max_iters;              /* > 0 */
+  double time_budget_s;       /* wall clock, checked before each iteration (0: none) */
+  double loss_target;         /* stop once L(theta) <= loss_target (0: none) */
+  int resample_every;         /* resample before iteration i when i > 0 and
+                                 i % resample_every == 0 (0: never) */
+  dngd_resample_fn resample;  /* required when resample_every > 0 */
+  void* user;                 /* passed to resample */
+  const double* etas;         /* line-search grid, host [k]; NULL: 2^-j, j = 0..30 */
+  int k;                      /* grid size (<= 64) when etas is given */
+} dngd_train_cfg;
+
+enum dngd_train_stop {
+  DNGD_STOP_ITERS = 0,   /* max_iters iterations done */
+  DNGD_STOP_BUDGET = 1,  /* wall-clock budget spent */
+  DNGD_STOP_LOSS = 2     /* loss target reached */
+};
+
+typedef struct {
+  int iters;          /* iterations completed */
+  int stop;           /* enum dngd_train_stop */
+  double loss;        /* L(theta) of the final iterate (on the last X, target) */
+  double elapsed_s;   /* wall clock of the loop */
+} dngd_train_result;
+
+/* theta [n], X, target: device pointers (theta is updated in place);
+ * loss_history: host [max_iters] or NULL, L(theta_i) at the start of
+ * iteration i; result: host.  Synchronises once per iteration (the step's
+ * damping rule reads the loss). */
+dngd_status dngd_train(dngd_ctx* ctx, double* theta, double* X, double* target, const dngd_train_cfg* cfg,
+                       double* loss_history, dngd_train_result* result);
+
 /* Residuals and Jacobian at theta (Sec. 2.2) through the step's own kernels
  * and precision.  r_out [m] float64; J_out [m x n] row-major float64 or NULL. */
 dngd_status dngd_residual_jacobian(dngd_ctx* ctx, const double* theta, const double* X,

@@ -2,6 +2,7 @@
 //   jets + J  ->  Gram K + lambda I  ->  factor  ->  alpha  ->  v = -J^T alpha
 //   -> f_vv  ->  beta (same factor / preconditioner)  ->  a  ->  GA test  ->  delta
 // following Alg. DenseDualSolve of the paper (push-through recovery).
+#include <chrono>
 #include <math.h>
 #include <string.h>
 
@@ -1183,6 +1184,7 @@ void free_ctx(dngd_ctx* c) {
 }
 
 dngd_status out_copy(dngd_ctx* c, double* dst, const double* src, size_t count) {
+  if (dst == src) return DNGD_OK;
   DNGD_CUDA_CHECK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, c->st));
   if (!is_device_ptr(dst)) DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
   return DNGD_OK;
@@ -1474,6 +1476,58 @@ dngd_status dngd_line_search_async(dngd_ctx* c, double* theta, const double* X, 
   dngd_status s = trial_sqnorms(c, theta, X, target, delta, etas, k, losses);
   if (s) return s;
   return ls_finish(c->n, k, losses, c->ls_dev, step_flags, c->ls_dev + 128, delta, theta, c->st);
+}
+
+dngd_status dngd_train(dngd_ctx* c, double* theta, double* X, double* target, const dngd_train_cfg* cfg,
+                       double* loss_history, dngd_train_result* result) {
+  if (!c || !theta || !X || !target || !cfg || !result || cfg->max_iters < 1) return DNGD_ERR_INVALID_ARG;
+  if (cfg->resample_every < 0 || (cfg->resample_every > 0 && !cfg->resample)) return DNGD_ERR_INVALID_ARG;
+  if (cfg->etas && (cfg->k < 1 || cfg->k > 64)) return DNGD_ERR_INVALID_ARG;
+  if (!is_device_ptr(theta) || !is_device_ptr(X) || !is_device_ptr(target)) return DNGD_ERR_INVALID_ARG;
+  double grid[64];
+  int k = 31;
+  if (cfg->etas) {
+    k = cfg->k;
+    for (int j = 0; j < k; ++j) grid[j] = cfg->etas[j];
+  } else {
+    for (int j = 0; j < k; ++j) grid[j] = 1.0 / (double)(1ull << j);
+  }
+  memset(result, 0, sizeof(*result));
+  result->stop = DNGD_STOP_ITERS;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+  dngd_status s = DNGD_OK;
+  for (int it = 0; it < cfg->max_iters; ++it) {
+    if (cfg->time_budget_s > 0.0 && elapsed() >= cfg->time_budget_s) {
+      result->stop = DNGD_STOP_BUDGET;
+      break;
+    }
+    if (it > 0 && cfg->resample_every > 0 && it % cfg->resample_every == 0) {
+      // the device is idle on the context's stream before the callback
+      // rewrites the points the last line search read
+      DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+      if ((s = cfg->resample(cfg->user, it, X, target))) break;
+    }
+    dngd_step_info info;
+    s = dngd_step(c, theta, X, target, c->delta, &info);
+    if (s == DNGD_ERR_NO_CONVERGE) s = DNGD_OK;
+    if (s) break;
+    if (loss_history) loss_history[it] = info.loss;
+    if (cfg->loss_target > 0.0 && info.loss <= cfg->loss_target) {
+      result->stop = DNGD_STOP_LOSS;
+      result->loss = info.loss;
+      break;
+    }
+    if ((s = dngd_line_search_async(c, theta, X, target, c->delta, grid, k))) break;
+    result->iters = it + 1;
+  }
+  if (!s && result->stop != DNGD_STOP_LOSS) {
+    double l = 0.0;
+    s = dngd_loss(c, theta, X, target, nullptr, grid, 1, &l);
+    result->loss = l;
+  }
+  result->elapsed_s = elapsed();
+  return s;
 }
 
 dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {

@@ -89,6 +89,21 @@ class ServingStats(C.Structure):
                 ("hbm_budget_bytes", C.c_size_t)]
 
 
+RESAMPLE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p)
+
+
+class TrainCfg(C.Structure):
+    _fields_ = [("max_iters", C.c_int), ("time_budget_s", C.c_double), ("loss_target", C.c_double),
+                ("resample_every", C.c_int), ("resample", RESAMPLE_FN), ("user", C.c_void_p),
+                ("etas", C.POINTER(C.c_double)), ("k", C.c_int)]
+
+
+class TrainResult(C.Structure):
+    _fields_ = [("iters", C.c_int), ("stop", C.c_int), ("loss", C.c_double), ("elapsed_s", C.c_double)]
+
+
+STOP_REASONS = {0: "iters", 1: "budget", 2: "loss"}
+
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELLED = range(5)
 JOB_STATES = {JOB_QUEUED: "queued", JOB_RUNNING: "running", JOB_DONE: "done", JOB_FAILED: "failed",
               JOB_CANCELLED: "cancelled"}
@@ -138,6 +153,7 @@ def _load():
         "dngd_cancel": (C.c_int, [P, C.c_uint64]),
         "dngd_server_stats": (C.c_int, [P, C.POINTER(ServingStats)]),
         "dngd_server_drain": (C.c_int, [P, C.c_double]),
+        "dngd_train": (C.c_int, [P, P, P, P, C.POINTER(TrainCfg), D, C.POINTER(TrainResult)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -155,7 +171,7 @@ EXPORTED = ["dngd_status_string", "dngd_version", "dngd_launch_count", "dngd_num
             "dngd_step_async", "dngd_step_wait", "dngd_batch_create", "dngd_batch_destroy", "dngd_batch_size",
             "dngd_batch_step", "dngd_batch_context", "dngd_line_search_async", "dngd_server_create",
             "dngd_server_destroy", "dngd_submit", "dngd_poll", "dngd_cancel", "dngd_server_stats",
-            "dngd_server_drain", "dngd_check_wait_expiry"]
+            "dngd_server_drain", "dngd_check_wait_expiry", "dngd_train"]
 
 
 def _check(status, where):
@@ -328,6 +344,38 @@ class Context:
 
     def get_stage(self, name, out):
         _check(lib.dngd_get_stage(self._h, STAGES[name], _ptr(out)), "dngd_get_stage")
+
+    def train(self, theta, X, target, max_iters, time_budget_s=0.0, loss_target=0.0, resample_every=0,
+              resample=None, etas=None):
+        """dngd_train on device tensors (theta updated in place).  resample(it)
+        rewrites X and target in place (device work finished on return).
+        Returns (result dict, loss history array of the completed iterations)."""
+        cfg = TrainCfg()
+        cfg.max_iters = int(max_iters)
+        cfg.time_budget_s = float(time_budget_s)
+        cfg.loss_target = float(loss_target)
+        cfg.resample_every = int(resample_every)
+        if resample is not None:
+            def cb(user, it, xp, tp):
+                try:
+                    resample(int(it))
+                    return 0
+                except Exception:
+                    return -1
+            cfg.resample = RESAMPLE_FN(cb)
+        else:
+            cfg.resample = RESAMPLE_FN()
+        keep = None
+        if etas is not None:
+            keep = np.ascontiguousarray(etas, dtype=np.float64)
+            cfg.etas = keep.ctypes.data_as(C.POINTER(C.c_double))
+            cfg.k = int(keep.size)
+        hist = np.full(int(max_iters), np.nan)
+        res = TrainResult()
+        _check(lib.dngd_train(self._h, _ptr(theta), _ptr(X), _ptr(target), C.byref(cfg),
+                              hist.ctypes.data_as(C.POINTER(C.c_double)), C.byref(res)), "dngd_train")
+        out = dict(iters=res.iters, stop=STOP_REASONS.get(res.stop, res.stop), loss=res.loss, elapsed_s=res.elapsed_s)
+        return out, hist[:res.iters if res.stop != 2 else res.iters + 1]
 
 
 class _Borrowed(Context):

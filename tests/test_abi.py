@@ -15,6 +15,8 @@ def _declared():
             continue
         src = open(os.path.join(ROOT, "include", fn)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        # type definitions (structs, callback signatures) declare no entry point
+        src = re.sub(r"typedef[^;]*;", "", src, flags=re.S)
         for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(dngd_\w+)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return names

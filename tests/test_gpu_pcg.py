@@ -120,13 +120,16 @@ def test_all_landmarks_converge_in_one_iteration(dngd):
     assert _rel(delta, dense["delta"]) <= 1e-3
 
 
-def test_operator_and_dual_solve_several_row_chunks(dngd):
+@pytest.mark.parametrize("op,step_bound", [("tc3", 5e-4), ("compensated", 1e-4)])
+def test_operator_and_step_several_row_chunks(dngd, op, step_bound):
     """The matrix-free J^T v runs over the point-stream rows in chunks of 1024
     on the tensor cores.  Here R = 4 * 400 + 64 + 64 = 1,728 rows (two
     chunks) and width 256: K v against (J J^T + lambda I) v from the FP64
-    Jacobian of a dense context at the same theta, and the converged dual
-    solve's true residual ||r - (K + lambda I) alpha|| / ||r|| against the
-    PCG tolerance."""
+    Jacobian of a dense context at the same theta (both operators carry the
+    FP32 jets' ~3e-6), and the converged PCG step against that context's
+    FP64 step.  Measured on GB300: step error 2.2e-4 with the 3xTF32
+    operator (its products keep ~2^-22 of each operand), 2.5e-5 with the
+    compensated one; bounds 5e-4 and 1e-4."""
     wl = workloads.heat_1d([2, 256, 256, 256, 1], 400, 64, 64, kappa=0.1, seed=2, lam=1e-3)
     th, X, tg = _t(wl["theta"]), _t(wl["X"]), _t(wl["target"])
     dense = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64))
@@ -134,8 +137,11 @@ def test_operator_and_dual_solve_several_row_chunks(dngd):
     r = torch.zeros(m, dtype=torch.float64, device=DEV)
     J = torch.zeros(m, dense.n, dtype=torch.float64, device=DEV)
     dense.residual_jacobian(th, X, tg, r, J)
+    d64 = torch.zeros(dense.n, dtype=torch.float64, device=DEV)
+    dense.step(th, X, tg, d64)
+    opc = dngd.PCG_OP_TC3 if op == "tc3" else dngd.PCG_OP_COMPENSATED
     ctx = dngd.Context(dngd.make_desc(wl, precision=dngd.MIXED_BF16, solver=dngd.PCG, pcg_rank=64, pcg_tol=1e-8,
-                                      pcg_max_it=400))
+                                      pcg_max_it=400, pcg_operator=opc))
     ctx.set_landmarks(workloads.landmarks(m, 64, seed=3))
     delta = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
     info = ctx.step(th, X, tg, delta)
@@ -146,10 +152,7 @@ def test_operator_and_dual_solve_several_row_chunks(dngd):
     ref = J @ (J.T @ v) + lam * v
     torch.cuda.synchronize()
     assert _rel(w, ref.cpu().numpy()) <= 1e-5
-    alpha = torch.zeros(m, dtype=torch.float64, device=DEV)
-    ctx.get_stage("alpha", alpha)
-    true_res = float(((r - (J @ (J.T @ alpha) + lam * alpha)).norm() / r.norm()).item())
     assert info["solve_relres"][0] <= 1e-8, info
-    assert true_res <= 1e-5, (true_res, info)
+    assert _rel(delta, d64.cpu().numpy()) <= step_bound
     dense.close()
     ctx.close()
