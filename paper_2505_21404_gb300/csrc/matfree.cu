@@ -29,7 +29,18 @@ namespace dngd {
 
 namespace {
 
-constexpr int kJtvChunk = 1024;   // point-stream rows per TMEM accumulation of J^T v
+// Tensor-core accumulation is FP32 in TMEM (not round-to-nearest), so long
+// reductions are cut into chunks that add in round-to-nearest FP32 (beta = 1):
+// point-stream rows per chunk of J^T v, and layer-input columns per chunk
+// of J u.
+#ifndef DNGD_MF_CHUNK
+#define DNGD_MF_CHUNK 1024
+#endif
+#ifndef DNGD_MF_KCHUNK
+#define DNGD_MF_KCHUNK (1 << 30)
+#endif
+constexpr int kJtvChunk = DNGD_MF_CHUNK;
+constexpr int kJuChunk = DNGD_MF_KCHUNK;
 
 // Layer-0 and bias parts of J^T v.  Thread = one output unit a of layer l.
 // Writes g[w_off[l] ...] and g[b_off[l] ...] for l = 0 (weights from the
@@ -348,10 +359,16 @@ dngd_status mf_jv(const MatFree& F, const float* u, double* y, cudaStream_t st) 
     const int wo = net.widths[l + 1], wi = net.widths[l];
     if (l > 0) {
       // Y = H_{l-1} U_l^T (K = the layer width)
-      dngd_status s = F.tc3 ? gemm_tc3(net.R, wo, wi, 1.0f, F.H.p[l - 1], wi, false, u + net.w_off[l], wi, false, 0.0f,
-                                       F.Y, wo, false, *F.tc3, F.status, st)
-                            : gemm_nt_comp(net.R, wo, wi, 1.0f, F.H.p[l - 1], wi, u + net.w_off[l], wi, 0.0f, F.Y,
-                                           wo, st);
+      dngd_status s = DNGD_OK;
+      if (F.tc3) {
+        for (int k0 = 0; k0 < wi && !s; k0 += kJuChunk) {
+          const int kc = wi - k0 < kJuChunk ? wi - k0 : kJuChunk;
+          s = gemm_tc3(net.R, wo, kc, 1.0f, F.H.p[l - 1] + k0, wi, false, u + net.w_off[l] + k0, wi, false,
+                       k0 ? 1.0f : 0.0f, F.Y, wo, false, *F.tc3, F.status, st);
+        }
+      } else {
+        s = gemm_nt_comp(net.R, wo, wi, 1.0f, F.H.p[l - 1], wi, u + net.w_off[l], wi, 0.0f, F.Y, wo, st);
+      }
       if (s) return s;
     }
     DNGD_NOTE_LAUNCH();
