@@ -5,9 +5,10 @@ Workload: 5-D Poisson -Laplace(u) = f on [0,1]^5, u = sum_i sin(pi x_i), tanh ML
 5-256-256-256-1 (n = 133,377), 3,000 interior + 1,000 boundary points
 (m = 4,000), Glorot init (seed 0), lambda = 1e-5 (the paper's rule
 lambda_k = min(loss, 1e-5) at this loss).  One timed step = one D-NGD
-iteration: dngd_step (jets + J, Gram K + lambda I on tcgen05 tensor cores,
-factor, refined solve for v, f_vv, refined solve for a, GA test) followed by
-the 31-point grid line search and the parameter update (dngd_line_search).
+iteration: dngd_step (FP64 jets + J, the exact Gram K + lambda I from 8-bit
+slices on the tcgen05 tensor cores, FP64 factor with sliced trailing updates,
+refined solve for v, f_vv, refined solve for a, GA test) followed by the
+31-point grid line search and the parameter update (dngd_line_search).
 
 Reported: steps/s of the mixed path (value, device-resident inputs), the same
 through host buffers (e2e), the FP64 GPU path's steps/s and step errors
@@ -41,6 +42,11 @@ L2_NOTE = {"oz": "working set larger than L2 (J: 2.13 GB FP32, slices 4.27 GB BF
            "oz64": "working set larger than L2 (J: 4.27 GB FP64, slices 4.27 GB BF16, Gram 128 MB FP64 per step)",
            "bf16": "working set larger than L2 (J: 2.13 GB FP32 + 1.07 GB BF16 per step)",
            "tf32": "working set larger than L2 (J: 2.13 GB FP32 per step)"}
+def _prec(dngd, name):
+    """The precision mode of a --precision name."""
+    return {"oz": dngd.MIXED_OZ, "oz64": dngd.MIXED_OZ64, "bf16": dngd.MIXED_BF16, "tf32": dngd.MIXED_TF32}[name]
+
+
 WORKLOAD = "poisson5d_dense: -Lap u = f on [0,1]^5, MLP 5-256-256-256-1 (n=133377), 3000+1000 pts (m=4000)"
 
 
@@ -243,7 +249,7 @@ def run_batch(args, rank, world, local_rank):
     dev = torch.device(f"cuda:{local_rank}")
     lam = args.lam
     wls = workloads.poisson2d_batch(64, seed=0, lam=lam)
-    bprec = dngd.MIXED_OZ if args.precision == "oz" else dngd.MIXED_BF16
+    bprec = _prec(dngd, args.precision)
     descs = [dngd.make_desc(wl, precision=bprec, refine_tol=args.refine_tol, refine_max_it=60) for wl in wls]
     ths = [torch.tensor(wl["theta"], device=dev) for wl in wls]
     Xs = [torch.tensor(wl["X"], device=dev) for wl in wls]
@@ -300,7 +306,7 @@ def run_batch(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_batch, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16/f32 (double-float accumulation in the refinement)", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
         "config": {"workload": "poisson2d_batch: 64 x (-Lap u = f on [0,1]^2, u = sin(k pi x) sin(k pi y), "
                                "MLP 2-w-w-1, w ~ U{32,64,128}, m ~ U[256,2048])", "lam": lam,
                    "step": "one batch step = one CUDA-graph launch with 64 parallel instance steps (no line search)"},
@@ -546,13 +552,6 @@ def run_serving(args, rank, world, local_rank):
     iterations each) offered to one dngd_server for a fixed window per
     arrival rate.  Reports completed iterations/s, device step latency
     p50/p99, job queueing delay and the admitted/queued/rejected counts."""
-    if args.precision == "oz":
-        # two device faults were reported in this configuration and their cause
-        # is not established; it is not run until it is
-        print(json.dumps({"workload": "serving", "refused": "exact-Gram (--precision oz) serving jobs are not run: "
-                          "a device fault was reported in this configuration and its cause is open; use "
-                          "--precision bf16"}))
-        return
     import torch
     from paper_2505_21404_gb300 import dngd, workloads
     torch.cuda.set_device(local_rank)
@@ -565,7 +564,7 @@ def run_serving(args, rank, world, local_rank):
     for rate in rates:
         n_jobs = int(min(args.max_jobs, max(4, rate * args.window * 1.2 + 2)))
         jobs = workloads.serving_jobs(n_jobs, rate_per_s=rate, seed=7, lam=args.lam)
-        sprec = dngd.MIXED_OZ if args.precision == "oz" else dngd.MIXED_BF16
+        sprec = _prec(dngd, args.precision)
         descs = [dngd.make_desc(wl, precision=sprec, refine_tol=args.refine_tol, refine_max_it=60)
                  for _, wl, _ in jobs]
         srv = dngd.Server(hbm_budget_bytes=0, max_slots=args.slots)
@@ -608,7 +607,7 @@ def run_serving(args, rank, world, local_rank):
         "metric": METRIC, "value": head["steps_per_s"], "unit": "job-steps/s", "n_gpus": 1,
         "steps": int(sum(r["steps_total"] for r in results)), "warmup": 0,
         "ms_per_step": 1000.0 / head["steps_per_s"] if head["steps_per_s"] else None, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32 (double-float accumulation in the refinement)",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": "serving: Poisson 2-D/5-D jobs, m ~ U[512,8192], MLP width ~ U{64..512}, depth 2-3, "
                                "50 iterations (step + 31-point line search) each", "lam": args.lam,
@@ -636,9 +635,10 @@ def main():
     ap.add_argument("--save-theta", default=None, help="write the parameters after the timed steps (.npy)")
     ap.add_argument("--gram-traffic", type=float, default=None,
                     help="DRAM bytes of one exact-Gram launch on the 5-D workload (from an ncu capture)")
-    ap.add_argument("--precision", default="oz", choices=["oz", "oz64", "bf16", "tf32"],
-                    help="oz (default): exact Gram from 8-bit slices on BF16 tensor cores, FP32 factor, FP64 Gram "
-                         "operator in the refinement; bf16 / tf32: low-precision Gram, FP32-J operator")
+    ap.add_argument("--precision", default="oz64", choices=["oz", "oz64", "bf16", "tf32"],
+                    help="oz64 (default): FP64 jets and J, exact Gram from four 8-bit slices on the BF16 tensor "
+                         "cores (15 products), FP64 factor, PCG on the exact Gram; oz: the same with FP32 jets and "
+                         "J (13 products); bf16 / tf32: low-precision Gram, FP32-J operator")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle leg (no step error)")
     ap.add_argument("--no-fp64", action="store_true")
@@ -738,8 +738,7 @@ def run_dense(args, wl, rank, world, local_rank):
                          "); line search not included",
                "blas_threads": _threads()}
 
-    prec = {"bf16": dngd.MIXED_BF16, "tf32": dngd.MIXED_TF32, "oz": dngd.MIXED_OZ,
-            "oz64": dngd.MIXED_OZ64}[args.precision]
+    prec = _prec(dngd, args.precision)
     m, n = int(wl["X"].shape[0]), dngd.dngd_num_params(dngd.make_desc(wl))
     th0 = torch.tensor(wl["theta"], device=dev)
     X = torch.tensor(wl["X"], device=dev)
