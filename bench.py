@@ -429,7 +429,7 @@ def run_heat(args, rank, world, local_rank):
             "note": "same theta, same landmarks; the compensated FP32 SIMT operator (Kahan sums, FP64 row "
                     "reductions) as the reference: the full-size FP64 Jacobian (8,192 x 12.6M) does not fit"},
         "ell_sweep": sweep,
-        "roofline": {"bound": "tensor", "kernel": "k_tc3 (3xTF32 factor-form K v: J^T v in 1,024-row chunks, J u)",
+        "roofline": {"bound": "tensor", "kernel": "k_tc3 (3xTF32 factor-form K v: J^T v and J u, TMEM chunks of 128 K-elements)",
                      "achieved": kv_flops / (kv_ms * 1e-3) / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
                      "frac": kv_flops / (kv_ms * 1e-3) / 1e12 / tf32_peak,
                      "executed_tflops": 3 * kv_flops / (kv_ms * 1e-3) / 1e12,

@@ -167,8 +167,9 @@ typedef struct {
                                         K v = J (J^T v) and of the landmark
                                         columns.  0: 3xTF32 on the
                                         tensor cores (operands split into two
-                                        TF32 terms, three products, FP32
-                                        accumulation in 1,024-row chunks);
+                                        TF32 terms, three products; TMEM
+                                        chunks of 128 K-elements added in
+                                        round-to-nearest FP32);
                                         1: FP32 SIMT with compensated
                                         (Kahan) accumulation and FP64 row
                                         reductions, slower and more

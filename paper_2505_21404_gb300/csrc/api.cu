@@ -771,13 +771,15 @@ dngd_status alloc_pcg(dngd_ctx* c, bool dry, size_t* bytes_out) {
   add(4 * (4 * (size_t)ell * ell + (size_t)m * ell + (size_t)ell * ell));
   add(8 * ((size_t)m * 12 + 3 * n + 16 * (size_t)(n > m ? n : m)));
   // split operands of the 3xTF32 GEMMs: the jets' layers (R x w x w), J u
-  // (R x w_out x w_in), the landmark columns (R x RI x w) and the chunks of
-  // J^T v (w_out x w_in x 1024)
+  // (R x w_out x w_in), the landmark columns (R x RI x w) and J^T v (w_out x
+  // w_in x R)
   size_t t3 = tc3_scratch_bytes(net.R, net.max_w, net.max_w);
   const size_t t3b = tc3_scratch_bytes(net.R, RI, wmax);
   const size_t t3c = tc3_scratch_bytes(3 * net.R, net.max_w, net.max_w);   // the f_vv sweep's stacked streams
+  const size_t t3d = tc3_scratch_bytes(net.max_w, net.max_w, net.R);
   t3 = t3 > t3b ? t3 : t3b;
   t3 = t3 > t3c ? t3 : t3c;
+  t3 = t3 > t3d ? t3 : t3d;
   add(t3);
   if (bytes_out) *bytes_out = tot;
   if (dry) return DNGD_OK;

@@ -29,12 +29,13 @@ namespace dngd {
 
 namespace {
 
-// Tensor-core accumulation is FP32 in TMEM (not round-to-nearest), so long
-// reductions are cut into chunks that add in round-to-nearest FP32 (beta = 1):
-// point-stream rows per chunk of J^T v, and layer-input columns per chunk
-// of J u.
+// The 3xTF32 GEMM drains its TMEM accumulator every 128 K-elements into
+// round-to-nearest FP32 registers, so the whole reduction runs in one launch.
+// These optional cuts (point-stream rows of J^T v, layer-input columns of
+// J u, added in FP32 with beta = 1) are compile-time parameters, off by
+// default.
 #ifndef DNGD_MF_CHUNK
-#define DNGD_MF_CHUNK 1024
+#define DNGD_MF_CHUNK (1 << 30)
 #endif
 #ifndef DNGD_MF_KCHUNK
 #define DNGD_MF_KCHUNK (1 << 30)
@@ -323,9 +324,8 @@ dngd_status mf_jtv(const MatFree& F, const double* v, float* g, cudaStream_t st)
   for (int l = 1; l < L; ++l) {
     const int wo = net.widths[l + 1], wi = net.widths[l];
     if (F.tc3) {
-      // G_l = D_l^T diag(v) H_{l-1} in chunks of kJtvChunk point-stream rows:
-      // each chunk accumulates in TMEM, the chunks add in round-to-nearest
-      // FP32 (beta = 1), so no accumulator runs over all R rows
+      // G_l = D_l^T diag(v) H_{l-1} over all R point-stream rows (or in cuts
+      // of kJtvChunk rows added with beta = 1)
       for (int r0 = 0; r0 < net.R; r0 += kJtvChunk) {
         const int cr = net.R - r0 < kJtvChunk ? net.R - r0 : kJtvChunk;
         dngd_status s = gemm_tc3(wo, wi, cr, 1.0f, F.D.p[l] + (long long)r0 * wo, wo, true,

@@ -5,8 +5,11 @@
 // (both rounded to nearest, so the tensor cores see exact TF32 values), and
 // A_op B_op^T ~= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T; the dropped
 // A_lo B_lo^T and the rounding of x_lo leave ~2^-21 relative error per
-// product (FP32 SIMT: 2^-24).  It serves the products that need no more: the
-// 31 trial forwards of the line search and the FP32 preconditioning factor.
+// product (FP32 SIMT: 2^-24).  The tensor cores' FP32 accumulation is not
+// round-to-nearest and its error grows with the reduction length, so the
+// TMEM accumulator only ever runs over 128 K-elements: chunks alternate
+// between two TMEM buffers and the epilogue adds each into round-to-nearest
+// FP32 registers while the next chunk is computed.
 //
 // The split copies (and, for a transposed operand, the transpose) go to a
 // caller-owned scratch as [rows x 2 Kp] FP32 (hi in columns [0, Kp), lo in
@@ -14,8 +17,8 @@
 // alignment from the caller's matrices.  Kernel: one 128 x 128 output tile
 // per CTA (lower-triangle tiles only when asked), a 3-stage TMA ring of
 // 64 KB stages (A_hi, A_lo, B_hi, B_lo for 32 K), warp 1 issuing 12
-// tcgen05.mma kind::tf32 per stage into one TMEM accumulator, warps 2..5
-// draining it once.  Waits are bounded (ST_TIMEOUT).
+// tcgen05.mma kind::tf32 per stage into the current TMEM buffer, warps 2..5
+// draining each chunk.  Waits are bounded (ST_TIMEOUT).
 #include <mutex>
 #include <vector>
 
@@ -36,6 +39,8 @@ constexpr int TILE3 = T3 * 128;             // 16 KB
 constexpr int STAGE3 = 4 * TILE3;           // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM3 = ST3 * STAGE3 + 1024;
 constexpr int THREADS3 = 192;
+constexpr int CH3 = 4;                      // stages per TMEM accumulation chunk (4 x 32 = 128 K)
+static_assert(4 * 4 * 32 * 33 * 4 <= ST3 * STAGE3, "the epilogue stages its accumulators in the operand ring");
 
 __device__ __forceinline__ float tf32_rn(float x) {
   uint32_t u = __float_as_uint(x);
@@ -101,26 +106,31 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[ST3];
   __shared__ __align__(8) uint64_t empty_bar[ST3];
-  __shared__ __align__(8) uint64_t acc_bar;
-  __shared__ __align__(8) uint64_t fin_bar;   // teardown: every issued MMA retired
+  __shared__ __align__(8) uint64_t accf_bar[2];   // MMA -> epilogue: chunk in buffer b done
+  __shared__ __align__(8) uint64_t acce_bar[2];   // epilogue -> MMA: buffer b drained
+  __shared__ __align__(8) uint64_t fin_bar;       // teardown: every issued MMA retired
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int nk = Kp / KB3;
+  const int nchunk = (nk + CH3 - 1) / CH3;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST3; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    mbar_init(smem_u32(&acc_bar), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf_bar[b]), 1);
+      mbar_init(smem_u32(&acce_bar[b]), 4);
+    }
     mbar_init(smem_u32(&fin_bar), 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(128));
+                 "r"(2 * T3));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -153,48 +163,91 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = tc3_idesc();
-      for (int it = 0; it < nk && !*abort_flag; ++it) {
-        const int st = it % ST3;
-        const uint32_t ph = (uint32_t)((it / ST3) & 1);
-        if (!mbar_wait(smem_u32(&full_bar[st]), ph, status, 22)) {
+      // CH3 stages per chunk, alternating between two TMEM buffers; a buffer
+      // is reused once the epilogue has drained its previous chunk
+      for (int c = 0; c < nchunk && !*abort_flag; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)(((c >> 1) - 1) & 1), status, 26)) {
           *abort_flag = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t sb = smem_base + st * STAGE3;
-        const uint64_t ahi = sw128_desc(sb), alo = sw128_desc(sb + TILE3);
-        const uint64_t bhi = sw128_desc(sb + 2 * TILE3), blo = sw128_desc(sb + 3 * TILE3);
+        const uint32_t dbuf = tmem + (uint32_t)(b * T3);
+        const int it1 = min(nk, (c + 1) * CH3);
+        bool stop = false;
+        for (int it = c * CH3; it < it1; ++it) {
+          const int st = it % ST3;
+          const uint32_t ph = (uint32_t)((it / ST3) & 1);
+          if (!mbar_wait(smem_u32(&full_bar[st]), ph, status, 22)) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t sb = smem_base + st * STAGE3;
+          const uint64_t ahi = sw128_desc(sb), alo = sw128_desc(sb + TILE3);
+          const uint64_t bhi = sw128_desc(sb + 2 * TILE3), blo = sw128_desc(sb + 3 * TILE3);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint64_t dk = (uint64_t)((32 * k) >> 4);
-          umma<1>(tmem, ahi + dk, bhi + dk, idesc, (it > 0 || k > 0) ? 1u : 0u);
-          umma<1>(tmem, ahi + dk, blo + dk, idesc, 1u);
-          umma<1>(tmem, alo + dk, bhi + dk, idesc, 1u);
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t dk = (uint64_t)((32 * k) >> 4);
+            umma<1>(dbuf, ahi + dk, bhi + dk, idesc, (it > c * CH3 || k > 0) ? 1u : 0u);
+            umma<1>(dbuf, ahi + dk, blo + dk, idesc, 1u);
+            umma<1>(dbuf, alo + dk, bhi + dk, idesc, 1u);
+          }
+          umma_commit(smem_u32(&empty_bar[st]));
         }
-        umma_commit(smem_u32(&empty_bar[st]));
+        if (stop) break;
+        umma_commit(smem_u32(&accf_bar[b]));
       }
-      umma_commit(smem_u32(&acc_bar));
     }
   } else {
+    // epilogue warps 2..5: warp w reads TMEM lanes 32 (w % 4).. (its 32 rows)
+    // and adds each chunk into round-to-nearest FP32 registers (the tensor
+    // cores' own accumulation is not round-to-nearest, so it only ever runs
+    // over CH3 x 32 products)
     const int q = warp & 3;
-    const bool ok = __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&acc_bar), 0u, status, 23)) ? 1 : 0) != 0;
-    if (!ok) {
-      *abort_flag = 1;
-    } else {
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    float acc[T3];
+#pragma unroll
+    for (int j = 0; j < T3; ++j) acc[j] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunk; ++c) {
+      const int b = c & 1;
+      ok = __all_sync(0xffffffffu,
+                      (!*abort_flag && mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)((c >> 1) & 1), status, 23)) ? 1
+                                                                                                                 : 0) != 0;
+      if (!ok) {
+        *abort_flag = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // all MMAs (hence all TMA stages) are done: stage 0 holds each warp's
-      // 32 x 33 transpose buffer, so C is written row by row, coalesced
-      float* tb = reinterpret_cast<float*>(smem_raw + (smem_base - smem_u32(smem_raw))) + (warp - 2) * 32 * 33;
-      const int row0 = bm * T3 + q * 32;
-      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-      for (int j4 = 0; j4 < 4; ++j4) {
+#pragma unroll
+      for (int j4 = 0; j4 < T3 / 32; ++j4) {
         uint32_t r[32];
-        TMEM_LD_32(base + (uint32_t)(j4 * 32), r);
+        TMEM_LD_32(lane_base + (uint32_t)(b * T3 + j4 * 32), r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int i = 0; i < 32; ++i) tb[lane * 33 + i] = __uint_as_float(r[i]);
-        __syncwarp();
+        for (int i = 0; i < 32; ++i) acc[j4 * 32 + i] += __uint_as_float(r[i]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[b])) : "memory");
+    }
+    if (ok && !*abort_flag) {
+      // all MMAs (hence all TMA stages) are done: stage 0 holds each warp's
+      // 32 x 33 transpose buffer, so C is written row by row, coalesced
+      float* tb4 = reinterpret_cast<float*>(smem_raw + (smem_base - smem_u32(smem_raw))) + (warp - 2) * 4 * 32 * 33;
+      const int row0 = bm * T3 + q * 32;
+      // the whole accumulator row goes to shared memory first, so no
+      // accumulator register stays live across the read-modify-write of C
+#pragma unroll
+      for (int j4 = 0; j4 < T3 / 32; ++j4)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) tb4[j4 * 32 * 33 + lane * 33 + i] = acc[j4 * 32 + i];
+      __syncwarp();
+#pragma unroll 1
+      for (int j4 = 0; j4 < T3 / 32; ++j4) {
+        const float* tb = tb4 + j4 * 32 * 33;
         const int col = bn * T3 + j4 * 32 + lane;
         if (col < N && nk > 0) {
           // all 32 reads of C are issued before the first write, so the
@@ -251,7 +304,7 @@ k_tc3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensor
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * T3));
   }
 }
 

@@ -122,14 +122,13 @@ def test_all_landmarks_converge_in_one_iteration(dngd):
 
 @pytest.mark.parametrize("op,step_bound", [("tc3", 5e-4), ("compensated", 1e-4)])
 def test_operator_and_step_several_row_chunks(dngd, op, step_bound):
-    """The matrix-free J^T v runs over the point-stream rows in chunks of 1024
-    on the tensor cores.  Here R = 4 * 400 + 64 + 64 = 1,728 rows (two
-    chunks) and width 256: K v against (J J^T + lambda I) v from the FP64
+    """The matrix-free J^T v reduces over the point-stream rows: here
+    R = 4 * 400 + 64 + 64 = 1,728 rows (14 TMEM chunks of 128 on the tensor
+    cores) and width 256.  K v against (J J^T + lambda I) v from the FP64
     Jacobian of a dense context at the same theta (both operators carry the
     FP32 jets' ~3e-6), and the converged PCG step against that context's
-    FP64 step.  Measured on GB300: step error 2.2e-4 with the 3xTF32
-    operator (its products keep ~2^-22 of each operand), 2.5e-5 with the
-    compensated one; bounds 5e-4 and 1e-4."""
+    FP64 step (bounds 5e-4 for the 3xTF32 operator, whose products keep
+    ~2^-22 of each operand, and 1e-4 for the compensated one)."""
     wl = workloads.heat_1d([2, 256, 256, 256, 1], 400, 64, 64, kappa=0.1, seed=2, lam=1e-3)
     th, X, tg = _t(wl["theta"]), _t(wl["X"]), _t(wl["target"])
     dense = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64))
