@@ -23,24 +23,26 @@
 //     (level g with n_g products is drained every 2^10 / n_g K columns), so
 //     the FP32 accumulator is exact; levels 3 and 4 (weights 2^-24 and
 //     2^-32 of level 0) are drained every 2048 columns and round in FP32
-//     (chunks below 2^27, so a unit is at most 8): even with each of a
-//     chunk's 512 (level 3) or 384 (level 4) MMA additions off by a full
-//     unit in the same direction this adds at most 2^-39 of the row scales
-//     times n (2^-39 = 512 x 8 x 2^8 x 2^-48 / 2048), below the slicing's
-//     own 2^-32; the epilogue adds each chunk into double-float registers
-//     (48-bit significand) times 2^(8(4-g)).
+//     (chunks below 2^27 units of level 3, so a unit is at most 8): even
+//     with each of a chunk's 896 MMA additions (levels 3 and 4 share one
+//     accumulator) off by a full unit in the same direction this adds at
+//     most 2^-38 of the row scales times n (896 x 8 x 2^8 x 2^-48 / 2048),
+//     below the slicing's own 2^-32; the epilogue adds each chunk into
+//     double-float registers (48-bit significand).
 //
-// Kernel roles (one 128 x 96 output tile touching the lower triangle and one
-// K range per CTA): warp 0 lane 0 streams, per 32-wide K block, all four A
-// slices (128 rows) and all four B slices (96 rows) with TMA (64-byte
-// swizzle) into a 4-stage ring of 56 KB stages, so one stage feeds all 13
-// slice products; warp 1 lane 0 issues tcgen05.mma (M = 128, N = 96) into
-// five per-level TMEM accumulators (480 columns) and commits a level at the
-// end of its chunk; the levels' chunk boundaries are staggered and a level
-// that starts a chunk is issued last in its stage, so its drain overlaps the
-// other levels' MMAs; warps 2..13 drain a level as soon as it is committed
-// (warp w: TMEM lanes 32 (w % 4).., 32 columns), release it to the MMA warp,
-// and add it times 2^(8(4-g)) into double-float registers.
+// Kernel roles (one 128 x 128 output tile touching the lower triangle and
+// one K range per CTA): warp 0 lane 0 streams, per 32-wide K block, all four
+// A slices and all four B slices with TMA (64-byte swizzle) into a 3-stage
+// ring of 64 KB stages, so one stage feeds every slice product; warp 1 lane
+// 0 issues tcgen05.mma (M = N = 128) into four TMEM accumulators (levels 0,
+// 1, 2 and the rounded levels together; the slices are stored pre-scaled by
+// 2^(-8 s), so a product carries its level's weight) and commits an
+// accumulator at the end of its chunk; the chunk boundaries are staggered
+// and an accumulator that starts a chunk is issued last in its stage, so its
+// drain overlaps the other accumulators' MMAs; warps 2..9 drain an
+// accumulator as soon as it is committed (two warps per TMEM lane quadrant,
+// 64 columns each), release it to the MMA warp, and add it into
+// double-float registers.
 // Split-K partial tiles (FP64) are summed in a fixed order by the reduction,
 // which applies the row scales and writes the full FP64 Gram (the
 // refinement operator) and its FP32 lower triangle plus the diagonal shift
@@ -64,8 +66,16 @@ namespace {
 using namespace tc;
 
 // Configurations <NS, NG>: NS 8-bit slices per value; the products
-// sigma_s sigma_t^T are summed by level g = s + t <= NG - 1, each level in
-// its own TMEM accumulator of TN columns (NG x TN <= 512).
+// sigma_s sigma_t^T are summed by level g = s + t <= NG - 1.  A level's
+// products go to one of NA TMEM accumulators of TN columns (NA x TN <= 512):
+// accumulator a takes the levels [lo(a), hi(a)].
+// * PRE (pre-scaled slices): slice s is stored as sigma_s 2^(-8 s), exact in
+//   BF16, so every product already carries its level's weight 2^(-8 g) and
+//   levels may share an accumulator.  The exact levels 0-2 keep one each
+//   (their chunks sum integers times 2^(-8 g), exact below 2^24 units); the
+//   rounded levels >= 3 share one, whose FP32 rounding is relative to level
+//   3's magnitude, ~2^-48 of level 0.  Without PRE (integer slices) every
+//   level has its own accumulator and the epilogue applies the weights.
 // * <4, 5>: levels g <= 4 (13 of the 16 products), for the FP32 Jacobian,
 //   whose own rounding is far larger than the dropped terms.
 // * <4, 6>: also level 5 (15 products), for the FP64 Jacobian.  The dropped
@@ -73,54 +83,63 @@ using namespace tc;
 //   squares), so for an accurate J the truncation is what limits the Gram,
 //   not the slicing: level 5 brings the step error at a trained theta from
 //   1.5e-4 to 6e-6 (CPU emulation), as close as a fifth slice would.
-// * <6, 7>: six slices, levels g <= 6 (26 of 36 products), for the trailing
-//   updates of the FP64 factorisation (K extent 64: every chunk exact).
+// * <6, 7>: six integer slices, levels g <= 6 (26 of 36 products), for the
+//   trailing updates of the FP64 factorisation (K extent 64: every chunk
+//   exact, one accumulator per level).
 template <int NS, int NG>
 struct OzCfg;
 template <>
 struct OzCfg<4, 5> {
-  static constexpr int TN = 96, OST = 4;
-  // Stages per chunk of level g.  Levels 0-2 are exact: n_g = g_hi - g_lo +
-  // 1 products of |sigma| <= 128 over period x 32 columns stay within 2^24
-  // (1 x 32 x 32, 2 x 16 x 32, 3 x 10 x 32, times 2^14).  Levels 3 and 4
-  // run 64 stages and round (their error bound is in the header).
-  __host__ __device__ static constexpr int period(int g) { return g == 0 ? 32 : g == 1 ? 16 : g == 2 ? 10 : 64; }
-  // Offsets that stagger the levels' chunk boundaries (the first chunk of
-  // level g is period - offset stages long): chunk ends fall on stages 31,
-  // 10/26, 7 + 10 i (modulo 32), 52 and 38 (modulo 64).
-  __host__ __device__ static constexpr int offset(int g) {
-    return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 11 : 25;
-  }
+  static constexpr int TN = 128, OST = 3, NA = 4;
+  static constexpr bool PRE = true;
+  __host__ __device__ static constexpr int lo(int a) { return a; }
+  __host__ __device__ static constexpr int hi(int a) { return a < 3 ? a : 4; }
+  // Stages per chunk of accumulator a.  Levels 0-2 are exact: n_g = g_hi -
+  // g_lo + 1 products of |sigma| <= 128 over period x 32 columns stay within
+  // 2^24 units (1 x 32 x 32, 2 x 16 x 32, 3 x 10 x 32, times 2^14).  The
+  // rounded levels run 64 stages (their error bound is in the header).
+  __host__ __device__ static constexpr int period(int a) { return a == 0 ? 32 : a == 1 ? 16 : a == 2 ? 10 : 64; }
+  // Offsets that stagger the accumulators' chunk boundaries (the first chunk
+  // of accumulator a is period - offset stages long): chunk ends fall on
+  // stages 31, 10/26, 7 + 10 i (modulo 32) and 52 (modulo 64).
+  __host__ __device__ static constexpr int offset(int a) { return a == 0 ? 0 : a == 1 ? 5 : a == 2 ? 2 : 11; }
 };
 template <>
 struct OzCfg<4, 6> {
-  static constexpr int TN = 80, OST = 4;
-  // As <4, 5>, plus level 5 (2 products, weight 2^-8 of level 4) rounded in
-  // 64-stage chunks like levels 3 and 4: its chunks stay below 2^26, and
-  // even with every one of a chunk's 256 MMA additions off by a full unit
-  // (at most 4) the added error is 256 x 4 x 2^-56 / 2048 = 2^-57 of the
-  // row scales per column.
-  __host__ __device__ static constexpr int period(int g) { return g == 0 ? 32 : g == 1 ? 16 : g == 2 ? 10 : 64; }
-  __host__ __device__ static constexpr int offset(int g) {
-    return g == 0 ? 0 : g == 1 ? 5 : g == 2 ? 2 : g == 3 ? 11 : g == 4 ? 25 : 44;
-  }
+  // As <4, 5>, with level 5 (2 products, weight 2^-8 of level 4) in the
+  // rounded accumulator.
+  static constexpr int TN = 128, OST = 3, NA = 4;
+  static constexpr bool PRE = true;
+  __host__ __device__ static constexpr int lo(int a) { return a; }
+  __host__ __device__ static constexpr int hi(int a) { return a < 3 ? a : 5; }
+  __host__ __device__ static constexpr int period(int a) { return a == 0 ? 32 : a == 1 ? 16 : a == 2 ? 10 : 64; }
+  __host__ __device__ static constexpr int offset(int a) { return a == 0 ? 0 : a == 1 ? 5 : a == 2 ? 2 : 11; }
 };
 template <>
 struct OzCfg<6, 7> {
-  static constexpr int TN = 64, OST = 2;
+  static constexpr int TN = 64, OST = 2, NA = 7;
+  static constexpr bool PRE = false;
+  __host__ __device__ static constexpr int lo(int a) { return a; }
+  __host__ __device__ static constexpr int hi(int a) { return a; }
   // K extent 64 = two stages: one chunk per level, 2 x 32 x 6 x 2^14 < 2^24,
   // so every level is exact.
-  __host__ __device__ static constexpr int period(int g) { return g >= 0 ? 2 : 2; }
-  __host__ __device__ static constexpr int offset(int g) { return g >= 0 ? 0 : 0; }
+  __host__ __device__ static constexpr int period(int a) { return a >= 0 ? 2 : 2; }
+  __host__ __device__ static constexpr int offset(int a) { return a >= 0 ? 0 : 0; }
 };
 
 constexpr int TM = 128;                     // output tile rows
 constexpr int KS = 32;                      // K per stage (64-byte rows, 64-byte swizzle)
 constexpr int A_TILE = TM * 64;             // 8 KB
-constexpr int OTHREADS = 448;               // TMA warp, MMA warp, 12 epilogue warps
-constexpr int EPI_WARPS = 12;
-constexpr uint32_t OTMEM = 512;             // NG level accumulators of TN columns
+constexpr uint32_t OTMEM = 512;             // NA accumulators of TN columns
 
+// Warps: 0 TMA, 1 MMA, then eight epilogue warps: two per TMEM lane
+// quadrant, each draining half of the tile's columns (cpw).
+template <int NS, int NG>
+__host__ __device__ constexpr int epi_warps() { return 8; }
+template <int NS, int NG>
+__host__ __device__ constexpr int cpw() { return OzCfg<NS, NG>::TN / 2; }
+template <int NS, int NG>
+__host__ __device__ constexpr int othreads() { return 64 + 32 * epi_warps<NS, NG>(); }
 template <int NS, int NG>
 __host__ __device__ constexpr int b_tile() { return OzCfg<NS, NG>::TN * 64; }
 template <int NS, int NG>
@@ -135,21 +154,28 @@ __host__ __device__ __forceinline__ int g_hi(int g) { return g < NS - 1 ? g : NS
 
 static_assert(32 * 32 * 1 <= 1024 && 16 * 32 * 2 <= 1024 && 10 * 32 * 3 <= 1024 && 2 * 32 * 6 <= 1024,
               "an exact chunk must stay within 2^24 = 2^10 x 2^14");
-static_assert(5 * OzCfg<4, 5>::TN <= (int)OTMEM && 6 * OzCfg<4, 6>::TN <= (int)OTMEM &&
-                  7 * OzCfg<6, 7>::TN <= (int)OTMEM,
-              "the level accumulators must fit the TMEM allocation");
+static_assert(OzCfg<4, 5>::NA * OzCfg<4, 5>::TN <= (int)OTMEM && OzCfg<4, 6>::NA * OzCfg<4, 6>::TN <= (int)OTMEM &&
+                  OzCfg<6, 7>::NA * OzCfg<6, 7>::TN <= (int)OTMEM,
+              "the accumulators must fit the TMEM allocation");
+static_assert(OzCfg<4, 5>::hi(OzCfg<4, 5>::NA - 1) == 4 && OzCfg<4, 6>::hi(OzCfg<4, 6>::NA - 1) == 5 &&
+                  OzCfg<6, 7>::hi(OzCfg<6, 7>::NA - 1) == 6,
+              "the accumulators cover every kept level");
 static_assert(osmem<4, 5>() <= 227 * 1024 && osmem<4, 6>() <= 227 * 1024 && osmem<6, 7>() <= 227 * 1024,
               "shared-memory ring too large");
-static_assert(EPI_WARPS * 32 * 33 * (int)sizeof(double) <= OzCfg<6, 7>::OST * ostage<6, 7>(),
+static_assert(epi_warps<6, 7>() * 32 * 33 * (int)sizeof(double) <= OzCfg<6, 7>::OST * ostage<6, 7>(),
               "the update epilogue stages its sub-tiles in the operand ring");
+static_assert(cpw<6, 7>() == 32 && cpw<4, 5>() % 32 == 0 && cpw<4, 6>() % 32 == 0 && cpw<4, 5>() <= 64 &&
+                  cpw<4, 6>() <= 64,
+              "an epilogue warp drains whole 32-column blocks (one for the update's staged sub-tile)");
 static_assert(b_tile<4, 5>() % 1024 == 0 && b_tile<4, 6>() % 1024 == 0 && b_tile<6, 7>() % 1024 == 0,
               "tiles keep 1024-byte alignment");
 
-// Chunk c of level g covers stages [start, end]: start = 0 for c = 0, else
-// c period - offset; end = (c + 1) period - offset - 1, clamped to nk - 1.
+// Chunk c of accumulator a covers stages [start, end]: start = 0 for c = 0,
+// else c period - offset; end = (c + 1) period - offset - 1, clamped to
+// nk - 1.
 template <int NS, int NG>
-__device__ __forceinline__ int chunk_end(int g, int c, int nk) {
-  return min(nk - 1, (c + 1) * OzCfg<NS, NG>::period(g) - OzCfg<NS, NG>::offset(g) - 1);
+__device__ __forceinline__ int chunk_end(int a, int c, int nk) {
+  return min(nk - 1, (c + 1) * OzCfg<NS, NG>::period(a) - OzCfg<NS, NG>::offset(a) - 1);
 }
 
 // BF16 x BF16 -> FP32, both K-major, M = 128, N = TN.
@@ -186,6 +212,10 @@ __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
   lo = l - (t - s);
   hi = t;
 }
+
+// Weight 2^(-8 s) of slice s in the pre-scaled layout (exact in BF16 for the
+// slice values |sigma| <= 128 and s <= 3).
+__device__ __forceinline__ float slice_weight(int s) { return __int_as_float((127 - 8 * s) << 23); }
 
 // The ND balanced base-256 digits of v = round(x 2^(8 ND - E)) for a double
 // x with |x| < 2^(E - 1), from x's bits with integer operations only (FP64
@@ -271,7 +301,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const TJ* __rest
           const float t = x[c] * 256.f;
           const float sg = rintf(t);
           x[c] = t - sg;
-          q[c] = __float2bfloat16_rn(sg);
+          q[c] = __float2bfloat16_rn(sg * slice_weight(s));
         }
         *reinterpret_cast<uint2*>(srow + (long long)s * ldb + 4 * k) = *reinterpret_cast<const uint2*>(q);
       }
@@ -283,7 +313,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const TJ* __rest
       for (int s = 0; s < 4; ++s) {
         __nv_bfloat16 q[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) q[c] = __float2bfloat16_rn(d[c][s]);
+        for (int c = 0; c < 4; ++c) q[c] = __float2bfloat16_rn(d[c][s] * slice_weight(s));
         *reinterpret_cast<uint2*>(srow + (long long)s * ldb + 4 * k) = *reinterpret_cast<const uint2*>(q);
       }
     }
@@ -294,17 +324,18 @@ __global__ void __launch_bounds__(256) k_oz_slice(int m, int n, const TJ* __rest
 // Gram and the update also its columns); its row i sits at slice row
 // row_off + i.  MODE: the epilogue (OZ_PARTIAL, OZ_UPDATE, OZ_GEMM).
 template <int NS, int NG, int MODE>
-__global__ void __launch_bounds__(OTHREADS, 1)
+__global__ void __launch_bounds__(othreads<NS, NG>(), 1)
 k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           const int2* __restrict__ tiles, int m, int row_off, int num_kblk, int ldb, double* __restrict__ out,
           long long ldo, long long split_stride, OzEpi epi, int* status) {
-  constexpr int TN = OzCfg<NS, NG>::TN, OST = OzCfg<NS, NG>::OST;
+  using Cfg = OzCfg<NS, NG>;
+  constexpr int TN = Cfg::TN, OST = Cfg::OST, NA = Cfg::NA, EPI = epi_warps<NS, NG>();
   constexpr int B_TILE = b_tile<NS, NG>(), OSTAGE = ostage<NS, NG>();
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[OST];
   __shared__ __align__(8) uint64_t empty_bar[OST];
-  __shared__ __align__(8) uint64_t accf_bar[NG];   // MMA -> epilogue: level g committed
-  __shared__ __align__(8) uint64_t acce_bar[NG];   // epilogue -> MMA: level g drained
+  __shared__ __align__(8) uint64_t accf_bar[NA];   // MMA -> epilogue: accumulator a committed
+  __shared__ __align__(8) uint64_t acce_bar[NA];   // epilogue -> MMA: accumulator a drained
   __shared__ __align__(8) uint64_t fin_bar;    // teardown: every issued MMA retired
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
@@ -324,9 +355,9 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    for (int g = 0; g < NG; ++g) {
-      mbar_init(smem_u32(&accf_bar[g]), 1);
-      mbar_init(smem_u32(&acce_bar[g]), EPI_WARPS);
+    for (int a = 0; a < NA; ++a) {
+      mbar_init(smem_u32(&accf_bar[a]), 1);
+      mbar_init(smem_u32(&acce_bar[a]), EPI);
     }
     mbar_init(smem_u32(&fin_bar), 1);
     abort_sh = 0;
@@ -368,13 +399,13 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = oz_idesc<TN>();
-      // per level: current chunk, its first and last stage
-      int cidx[NG], cstart[NG], cend[NG];
+      // per accumulator: current chunk, its first and last stage
+      int cidx[NA], cstart[NA], cend[NA];
 #pragma unroll
-      for (int g = 0; g < NG; ++g) {
-        cidx[g] = 0;
-        cstart[g] = 0;
-        cend[g] = chunk_end<NS, NG>(g, 0, nk);
+      for (int a = 0; a < NA; ++a) {
+        cidx[a] = 0;
+        cstart[a] = 0;
+        cend[a] = chunk_end<NS, NG>(a, 0, nk);
       }
       for (int it = 0; it < nk && !*abort_flag; ++it) {
         const int st = it % OST;
@@ -388,38 +419,41 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         // descriptors of the stage's first A and B tiles; the others differ
         // only in the start-address field (byte offset / 16, no carry out)
         const uint64_t da0 = sw64_desc(sbase), db0 = sw64_desc(sbase + NS * A_TILE);
-        // pass 0: levels inside a chunk; pass 1: levels starting one, which
-        // first wait until their previous chunk has been drained
+        // pass 0: accumulators inside a chunk; pass 1: those starting one,
+        // which first wait until their previous chunk has been drained
         bool stop = false;
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
-          for (int g = 0; g < NG; ++g) {
-            const bool first = cstart[g] == it;
+          for (int a = 0; a < NA; ++a) {
+            const bool first = cstart[a] == it;
             if (first != (pass == 1) || stop) continue;
             if (first) {
-              if (!mbar_wait(smem_u32(&acce_bar[g]), (uint32_t)((cidx[g] & 1) ^ 1), status, 15)) {
+              if (!mbar_wait(smem_u32(&acce_bar[a]), (uint32_t)((cidx[a] & 1) ^ 1), status, 15)) {
                 *abort_flag = 1;
                 stop = true;
                 continue;
               }
               asm volatile("tcgen05.fence::after_thread_sync;");
             }
-            const uint32_t dbuf = tmem + (uint32_t)(g * TN);
+            const uint32_t dbuf = tmem + (uint32_t)(a * TN);
 #pragma unroll
-            for (int sa = g_lo<NS>(g); sa <= g_hi<NS>(g); ++sa) {
+            for (int g = Cfg::lo(a); g <= Cfg::hi(a); ++g) {
 #pragma unroll
-              for (int k = 0; k < KS / 16; ++k) {
-                umma<0>(dbuf, da0 + (uint64_t)((sa * A_TILE + 32 * k) >> 4),
-                        db0 + (uint64_t)(((g - sa) * B_TILE + 32 * k) >> 4), idesc,
-                        (first && sa == g_lo<NS>(g) && k == 0) ? 0u : 1u);
+              for (int sa = g_lo<NS>(g); sa <= g_hi<NS>(g); ++sa) {
+#pragma unroll
+                for (int k = 0; k < KS / 16; ++k) {
+                  umma<0>(dbuf, da0 + (uint64_t)((sa * A_TILE + 32 * k) >> 4),
+                          db0 + (uint64_t)(((g - sa) * B_TILE + 32 * k) >> 4), idesc,
+                          (first && g == Cfg::lo(a) && sa == g_lo<NS>(g) && k == 0) ? 0u : 1u);
+                }
               }
             }
-            if (cend[g] == it) {
-              umma_commit(smem_u32(&accf_bar[g]));
-              ++cidx[g];
-              cstart[g] = it + 1;
-              cend[g] = chunk_end<NS, NG>(g, cidx[g], nk);
+            if (cend[a] == it) {
+              umma_commit(smem_u32(&accf_bar[a]));
+              ++cidx[a];
+              cstart[a] = it + 1;
+              cend[a] = chunk_end<NS, NG>(a, cidx[a], nk);
             }
           }
         }
@@ -428,40 +462,41 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       }
     }
   } else {
+    constexpr int CPW = cpw<NS, NG>();
     const int q = warp & 3;             // TMEM lane quadrant this warp may access
-    const int cg = (warp - 2) >> 2;     // column group: 32 of the TN columns (16 or none in the last)
-    const int ncol = TN - cg * 32 < 32 ? (TN - cg * 32 > 0 ? TN - cg * 32 : 0) : 32;
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * 32);
-    float hi[32], lo[32];
+    const int cg = (warp - 2) >> 2;     // column half: CPW of the TN columns
+    const int ncol = CPW;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * CPW);
+    float hi[CPW], lo[CPW];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < CPW; ++j) {
       hi[j] = 0.f;
       lo[j] = 0.f;
     }
     // the chunks in the order the MMA warp commits them: by last stage, a
     // chunk of one stage (issued in the second pass) after the others, then
-    // by level
-    int cidx[NG], cstart[NG], cend[NG];
+    // by accumulator
+    int cidx[NA], cstart[NA], cend[NA];
 #pragma unroll
-    for (int g = 0; g < NG; ++g) {
-      cidx[g] = 0;
-      cstart[g] = 0;
-      cend[g] = nk > 0 ? chunk_end<NS, NG>(g, 0, nk) : INT_MAX;
+    for (int a = 0; a < NA; ++a) {
+      cidx[a] = 0;
+      cstart[a] = 0;
+      cend[a] = nk > 0 ? chunk_end<NS, NG>(a, 0, nk) : INT_MAX;
     }
     while (!*abort_flag) {
-      int gsel = -1, kbest = INT_MAX;
+      int asel = -1, kbest = INT_MAX;
 #pragma unroll
-      for (int g = 0; g < NG; ++g) {
-        if (cend[g] == INT_MAX) continue;
-        const int key = cend[g] * 2 + (cstart[g] == cend[g] ? 1 : 0);
+      for (int a = 0; a < NA; ++a) {
+        if (cend[a] == INT_MAX) continue;
+        const int key = cend[a] * 2 + (cstart[a] == cend[a] ? 1 : 0);
         if (key < kbest) {
           kbest = key;
-          gsel = g;
+          asel = a;
         }
       }
-      if (gsel < 0) break;
+      if (asel < 0) break;
       const bool ok =
-          __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&accf_bar[gsel]), (uint32_t)(cidx[gsel] & 1),
+          __all_sync(0xffffffffu, (!*abort_flag && mbar_wait(smem_u32(&accf_bar[asel]), (uint32_t)(cidx[asel] & 1),
                                                              status, 13))
                                       ? 1
                                       : 0) != 0;
@@ -470,38 +505,34 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      uint32_t r[32];
-      if (ncol == 32) {
-        TMEM_LD_32(lane_base + (uint32_t)(gsel * TN), r);
-      } else if (ncol == 16) {
-        TMEM_LD_16(lane_base + (uint32_t)(gsel * TN), r);
+      // the chunk times 2^(8 (NG - 1)) with pre-scaled slices, else times its
+      // level's weight 2^(8 (NG - 1 - g)) (a power of two: exact), read in
+      // blocks of 8 columns to keep the registers low
+      const float sc = __int_as_float((127 + 8 * (NG - 1 - (Cfg::PRE ? 0 : asel))) << 23);
 #pragma unroll
-        for (int i = 16; i < 32; ++i) r[i] = 0u;
-      } else {
+      for (int h = 0; h < CPW / 8; ++h) {
+        uint32_t r[8];
+        TMEM_LD_8(lane_base + (uint32_t)(asel * TN + 8 * h), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int i = 0; i < 32; ++i) r[i] = 0u;
+        for (int i = 0; i < 8; ++i) df_add_exact(hi[8 * h + i], lo[8 * h + i], __uint_as_float(r[i]) * sc);
       }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0)
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[gsel])) : "memory");
-      // the level's chunk times 2^(8 (NG - 1 - g)) (a power of two: exact)
-      const float sc = __int_as_float((127 + 8 * (NG - 1 - gsel)) << 23);
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[asel])) : "memory");
+      // next chunk of this accumulator
 #pragma unroll
-      for (int i = 0; i < 32; ++i) df_add_exact(hi[i], lo[i], __uint_as_float(r[i]) * sc);
-      // next chunk of this level
-#pragma unroll
-      for (int g = 0; g < NG; ++g)
-        if (g == gsel) {
-          const int e = cend[g];
-          ++cidx[g];
-          cstart[g] = e + 1;
-          cend[g] = e + 1 < nk ? chunk_end<NS, NG>(g, cidx[g], nk) : INT_MAX;
+      for (int a = 0; a < NA; ++a)
+        if (a == asel) {
+          const int e = cend[a];
+          ++cidx[a];
+          cstart[a] = e + 1;
+          cend[a] = e + 1 < nk ? chunk_end<NS, NG>(a, cidx[a], nk) : INT_MAX;
         }
     }
     const int row = tile.x * TM + q * 32 + lane;
-    const int col0 = tile.y * TN + cg * 32;
+    const int col0 = tile.y * TN + cg * CPW;
     if (MODE == OZ_UPDATE) {
       // every MMA has completed, so the operand ring is idle: the warp's 32 x
       // 32 sub-tile (lane = row), scaled by 2^(E_row + E_col - eshift), goes
@@ -529,8 +560,8 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int er = epi.rexpA[row];
         double* crow = epi.C + (long long)row * epi.ldc + col0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < ncol && col0 + j < epi.ncols) {
+        for (int j = 0; j < CPW; ++j)
+          if (col0 + j < epi.ncols) {
             const double v = epi.alpha * ldexp((double)hi[j] + (double)lo[j], er + epi.rexpB[col0 + j] - epi.eshift);
             crow[j] = epi.beta == 0.0 ? v : v + epi.beta * crow[j];
           }
@@ -538,8 +569,8 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     } else if (row < m && !*abort_flag) {
       double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < ncol && col0 + j < m) orow[j] = (double)hi[j] + (double)lo[j];
+      for (int j = 0; j < CPW; ++j)
+        if (col0 + j < m) orow[j] = (double)hi[j] + (double)lo[j];
     }
   }
   __syncwarp();
@@ -798,10 +829,10 @@ dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_
   DNGD_NOTE_LAUNCH();
   const OzEpi none{nullptr, 0, nullptr, nullptr, 0, 0, 0, 0.0, 0.0};
   if (p->ng == 5)
-    k_gram_oz<4, 5, OZ_PARTIAL><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<4, 5>(), st>>>(
+    k_gram_oz<4, 5, OZ_PARTIAL><<<dim3(p->ntiles, p->nsplit), othreads<4, 5>(), osmem<4, 5>(), st>>>(
         p->mapA, p->mapB, p->d_tiles, p->m, 0, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, none, status);
   else
-    k_gram_oz<4, 6, OZ_PARTIAL><<<dim3(p->ntiles, p->nsplit), OTHREADS, osmem<4, 6>(), st>>>(
+    k_gram_oz<4, 6, OZ_PARTIAL><<<dim3(p->ntiles, p->nsplit), othreads<4, 6>(), osmem<4, 6>(), st>>>(
         p->mapA, p->mapB, p->d_tiles, p->m, 0, p->num_kblk, p->ldb, p->partials, p->ldp, p->sstride, none, status);
   DNGD_LAUNCH_CHECK();
   if (ev_after_mma) cudaEventRecord(ev_after_mma, st);
@@ -963,7 +994,7 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
     DNGD_LAUNCH_CHECK();
     const int ntiles = p->prefix[(r + TM - 1) / TM];
     DNGD_NOTE_LAUNCH();
-    k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(ntiles, 1), OTHREADS, osmem<FNS, FNG>(), st>>>(
+    k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(ntiles, 1), othreads<FNS, FNG>(), osmem<FNS, FNG>(), st>>>(
         p->mapA, p->mapB, p->d_tiles, r, row0, FNB / KS, FNB, nullptr, 0, 0, upd, status);
     DNGD_LAUNCH_CHECK();
   }
@@ -999,7 +1030,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_f64(int M, int K, int kp, co
     float d[4];
     oz_digits<4>(k < K && !bad ? at(k) : 0.0, E, d);
 #pragma unroll
-    for (int sl = 0; sl < 4; ++sl) sr[sl * kp + k] = __float2bfloat16_rn(d[sl]);
+    for (int sl = 0; sl < 4; ++sl) sr[sl * kp + k] = __float2bfloat16_rn(d[sl] * slice_weight(sl));
   }
 }
 
@@ -1066,7 +1097,7 @@ dngd_status oz_gemm(OzGemm* p, int M, int N, int K, double alpha, const double* 
   const int ntn = (N + TN - 1) / TN, ntm = (M + TM - 1) / TM;
   const OzEpi epi{C, ldc, p->ea, p->eb, 16 + 8 * 4, N, ntn, alpha, beta};
   DNGD_NOTE_LAUNCH();
-  k_gram_oz<4, 5, OZ_GEMM><<<dim3(ntm * ntn, 1), OTHREADS, osmem<4, 5>(), st>>>(
+  k_gram_oz<4, 5, OZ_GEMM><<<dim3(ntm * ntn, 1), othreads<4, 5>(), osmem<4, 5>(), st>>>(
       p->mapA, p->mapB, nullptr, M, 0, (K + KS - 1) / KS, p->kp, nullptr, 0, 0, epi, status);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
