@@ -651,6 +651,9 @@ def main():
                     help="poisson5d (default, the headline): dense 5-D step; poisson5d_w128: same points, hidden "
                          "width 128 (profiling case); poisson2d_batch: 64 independent 2-D instances stepped as one "
                          "graph; heat_pcg: matrix-free Nystrom-PCG step of the 1+1-D heat problem (n = 12.6M)")
+    ap.add_argument("--points", type=int, default=0,
+                    help="poisson5d: total collocation points instead of 4,000 (3:1 interior:boundary; a smaller "
+                         "case for profiler captures, not a bench line)")
     ap.add_argument("--ell", type=int, default=512, help="Nystrom landmarks for heat_pcg")
     ap.add_argument("--rates", default="0.1,0.3,1,5,200", help="serving: offered job arrival rates (jobs/s)")
     ap.add_argument("--window", type=float, default=20.0, help="serving: seconds per arrival rate")
@@ -664,7 +667,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     from paper_2505_21404_gb300 import workloads
-    if args.workload == "poisson5d":
+    if args.workload == "poisson5d" and args.points > 0:
+        ni = (3 * args.points) // 4
+        wl = workloads.poisson_sine(5, [5, 256, 256, 256, 1], ni, args.points - ni, k=1, seed=0, lam=args.lam)
+    elif args.workload == "poisson5d":
         wl = workloads.poisson5d_dense(seed=0, lam=args.lam)
     else:
         wl = workloads.poisson_sine(5, [5, 128, 128, 128, 1], 3000, 1000, k=1, seed=0, lam=args.lam)
@@ -955,7 +961,8 @@ def run_dense(args, wl, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "poisson5d" else args.workload,
+        "config": {"workload": (WORKLOAD if args.points <= 0 else f"poisson5d with {args.points} points")
+                               if args.workload == "poisson5d" else args.workload,
                    "lam": _lam_config(args),
                    "precision": f"mixed-{args.precision}",
                    "step": "dngd_step + 31-point line search + update",

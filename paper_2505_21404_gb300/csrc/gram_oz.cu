@@ -30,19 +30,20 @@
 //     below the slicing's own 2^-32; the epilogue adds each chunk into
 //     double-float registers (48-bit significand).
 //
-// Kernel roles (one 128 x 128 output tile touching the lower triangle and
-// one K range per CTA): warp 0 lane 0 streams, per 32-wide K block, all four
-// A slices and all four B slices with TMA (64-byte swizzle) into a 3-stage
-// ring of 64 KB stages, so one stage feeds every slice product; warp 1 lane
-// 0 issues tcgen05.mma (M = N = 128) into four TMEM accumulators (levels 0,
-// 1, 2 and the rounded levels together; the slices are stored pre-scaled by
-// 2^(-8 s), so a product carries its level's weight) and commits an
-// accumulator at the end of its chunk; the chunk boundaries are staggered
-// and an accumulator that starts a chunk is issued last in its stage, so its
-// drain overlaps the other accumulators' MMAs; warps 2..9 drain an
-// accumulator as soon as it is committed (two warps per TMEM lane quadrant,
-// 64 columns each), release it to the MMA warp, and add it into
-// double-float registers.
+// Kernel roles (one 128 x TN output tile touching the lower triangle and
+// one K range per CTA; TN = 128 for an FP32 Jacobian, 96 for an FP64 one):
+// warp 0 lane 0 streams, per 32-wide K block, all four A slices and all
+// four B slices with TMA (64-byte swizzle) into a ring of stages, so one
+// stage feeds every slice product; warp 1 lane 0 issues tcgen05.mma (M =
+// 128, N = TN) into four or five TMEM accumulators (levels 0, 1, 2 and the
+// rounded levels; the slices are stored pre-scaled by 2^(-8 s), so a
+// product carries its level's weight and levels can share an accumulator)
+// and commits an accumulator at the end of its chunk; the chunk boundaries
+// are staggered and an accumulator that starts a chunk is issued last in
+// its stage, so its drain overlaps the other accumulators' MMAs; warps
+// 2..9 drain an accumulator as soon as it is committed (two warps per TMEM
+// lane quadrant, TN / 2 columns each), release it to the MMA warp, and add
+// it into double-float registers.
 // Split-K partial tiles (FP64) are summed in a fixed order by the reduction,
 // which applies the row scales and writes the full FP64 Gram (the
 // refinement operator) and its FP32 lower triangle plus the diagonal shift
@@ -106,14 +107,21 @@ struct OzCfg<4, 5> {
 };
 template <>
 struct OzCfg<4, 6> {
-  // As <4, 5>, with level 5 (2 products, weight 2^-8 of level 4) in the
-  // rounded accumulator.
-  static constexpr int TN = 128, OST = 3, NA = 4;
+  // With an FP64 Jacobian the rounded levels must not share one accumulator:
+  // with levels 3-5 together (128 x 128 tiles) the step error at a trained
+  // theta rose from 1.3e-5 to 2.0e-4 (measured), the smaller levels' sums
+  // being cut at the ulps of level 3's.  Level 3 keeps its own accumulator
+  // and level 5 (2 products, weight 2^-8 of level 4) shares level 4's: five
+  // accumulators of 96 columns.
+  static constexpr int TN = 96, OST = 4, NA = 5;
   static constexpr bool PRE = true;
   __host__ __device__ static constexpr int lo(int a) { return a; }
-  __host__ __device__ static constexpr int hi(int a) { return a < 3 ? a : 5; }
+  __host__ __device__ static constexpr int hi(int a) { return a < 4 ? a : 5; }
   __host__ __device__ static constexpr int period(int a) { return a == 0 ? 32 : a == 1 ? 16 : a == 2 ? 10 : 64; }
-  __host__ __device__ static constexpr int offset(int a) { return a == 0 ? 0 : a == 1 ? 5 : a == 2 ? 2 : 11; }
+  // chunk ends on stages 31, 10/26, 7 + 10 i (modulo 32), 52 and 38 (modulo 64)
+  __host__ __device__ static constexpr int offset(int a) {
+    return a == 0 ? 0 : a == 1 ? 5 : a == 2 ? 2 : a == 3 ? 11 : 25;
+  }
 };
 template <>
 struct OzCfg<6, 7> {
@@ -164,9 +172,9 @@ static_assert(osmem<4, 5>() <= 227 * 1024 && osmem<4, 6>() <= 227 * 1024 && osme
               "shared-memory ring too large");
 static_assert(epi_warps<6, 7>() * 32 * 33 * (int)sizeof(double) <= OzCfg<6, 7>::OST * ostage<6, 7>(),
               "the update epilogue stages its sub-tiles in the operand ring");
-static_assert(cpw<6, 7>() == 32 && cpw<4, 5>() % 32 == 0 && cpw<4, 6>() % 32 == 0 && cpw<4, 5>() <= 64 &&
+static_assert(cpw<6, 7>() == 32 && cpw<4, 5>() % 8 == 0 && cpw<4, 6>() % 8 == 0 && cpw<4, 5>() <= 64 &&
                   cpw<4, 6>() <= 64,
-              "an epilogue warp drains whole 32-column blocks (one for the update's staged sub-tile)");
+              "an epilogue warp drains whole 8-column blocks (32 for the update's staged sub-tile)");
 static_assert(b_tile<4, 5>() % 1024 == 0 && b_tile<4, 6>() % 1024 == 0 && b_tile<6, 7>() % 1024 == 0,
               "tiles keep 1024-byte alignment");
 
@@ -1059,7 +1067,7 @@ dngd_status oz_gemm_plan(OzGemm** out, int max_m, int max_n, int max_k, void* wo
   p->SB = p->SA + (size_t)max_m * 4 * p->kp;
   p->ea = (int*)(p->SB + (size_t)max_n * 4 * p->kp);
   p->eb = p->ea + max_m;
-  constexpr int TN = OzCfg<4, 5>::TN;
+  constexpr int TN = OzCfg<4, 6>::TN;
   cuuint64_t gA[2] = {(cuuint64_t)(4 * p->kp), (cuuint64_t)max_m};
   cuuint64_t gB[2] = {(cuuint64_t)(4 * p->kp), (cuuint64_t)max_n};
   cuuint64_t stride[1] = {(cuuint64_t)(4 * p->kp * 2)};
@@ -1077,7 +1085,7 @@ dngd_status oz_gemm_plan(OzGemm** out, int max_m, int max_n, int max_k, void* wo
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gram_oz<4, 5, OZ_GEMM>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 5>());
+    cudaFuncSetAttribute(k_gram_oz<4, 6, OZ_GEMM>, cudaFuncAttributeMaxDynamicSharedMemorySize, osmem<4, 6>());
     attr = true;
   }
   *out = p;
@@ -1088,16 +1096,16 @@ dngd_status oz_gemm(OzGemm* p, int M, int N, int K, double alpha, const double* 
                     long long ldb, bool b_kn, double beta, double* C, long long ldc, int* status, cudaStream_t st) {
   if (M <= 0 || N <= 0) return DNGD_OK;
   if (M > p->max_m || N > p->max_n || K > p->kp || K <= 0) return DNGD_ERR_INVALID_ARG;
-  constexpr int TN = OzCfg<4, 5>::TN;
+  constexpr int TN = OzCfg<4, 6>::TN;
   DNGD_NOTE_LAUNCH();
   k_slice_rows_f64<<<(M + 7) / 8, 256, 0, st>>>(M, K, p->kp, A, lda, false, p->SA, p->ea);
   DNGD_NOTE_LAUNCH();
   k_slice_rows_f64<<<(N + 7) / 8, 256, 0, st>>>(N, K, p->kp, B, ldb, b_kn, p->SB, p->eb);
   DNGD_LAUNCH_CHECK();
   const int ntn = (N + TN - 1) / TN, ntm = (M + TM - 1) / TM;
-  const OzEpi epi{C, ldc, p->ea, p->eb, 16 + 8 * 4, N, ntn, alpha, beta};
+  const OzEpi epi{C, ldc, p->ea, p->eb, 16 + 8 * 5, N, ntn, alpha, beta};
   DNGD_NOTE_LAUNCH();
-  k_gram_oz<4, 5, OZ_GEMM><<<dim3(ntm * ntn, 1), othreads<4, 5>(), osmem<4, 5>(), st>>>(
+  k_gram_oz<4, 6, OZ_GEMM><<<dim3(ntm * ntn, 1), othreads<4, 6>(), osmem<4, 6>(), st>>>(
       p->mapA, p->mapB, nullptr, M, 0, (K + KS - 1) / KS, p->kp, nullptr, 0, 0, epi, status);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;

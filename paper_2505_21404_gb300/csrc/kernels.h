@@ -192,7 +192,7 @@ void oz_factor_free(OzFactor* plan);
 
 // C = alpha A B^T + beta C in FP64 (A [M x K] ld lda; B [N x K] ld ldb, or
 // with b_kn B given as [K x N]) from four 8-bit slices of every row of A and
-// of B^T on the BF16 tensor cores (13 slice products): each entry of A and B
+// of B^T on the BF16 tensor cores (15 slice products, levels <= 5): each entry of A and B
 // kept to 2^-33 of its row's largest, the products exact, so C is accurate
 // to ~2^-33 of the row scales times K.  M, N, K within the plan's capacity.
 size_t oz_gemm_bytes(int max_m, int max_n, int max_k);
