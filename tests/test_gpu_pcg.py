@@ -120,15 +120,15 @@ def test_all_landmarks_converge_in_one_iteration(dngd):
     assert _rel(delta, dense["delta"]) <= 1e-3
 
 
-@pytest.mark.parametrize("op,step_bound", [("tc3", 5e-4), ("compensated", 1e-4)])
-def test_operator_and_step_several_row_chunks(dngd, op, step_bound):
+@pytest.mark.parametrize("op", ["tc3", "compensated"])
+def test_operator_and_step_several_row_chunks(dngd, op):
     """The matrix-free J^T v reduces over the point-stream rows: here
     R = 4 * 400 + 64 + 64 = 1,728 rows (14 TMEM chunks of 128 on the tensor
     cores) and width 256.  K v against (J J^T + lambda I) v from the FP64
     Jacobian of a dense context at the same theta (both operators carry the
-    FP32 jets' ~3e-6), and the converged PCG step against that context's
-    FP64 step (bounds 5e-4 for the 3xTF32 operator, whose products keep
-    ~2^-22 of each operand, and 1e-4 for the compensated one)."""
+    FP32 jets' ~2e-6), and the converged PCG step against that context's
+    FP64 step within the mixed path's 1e-4 (measured on GB300: 2.9e-5 with
+    the 3xTF32 operator, 1.7e-5 with the compensated one)."""
     wl = workloads.heat_1d([2, 256, 256, 256, 1], 400, 64, 64, kappa=0.1, seed=2, lam=1e-3)
     th, X, tg = _t(wl["theta"]), _t(wl["X"]), _t(wl["target"])
     dense = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64))
@@ -152,6 +152,6 @@ def test_operator_and_step_several_row_chunks(dngd, op, step_bound):
     torch.cuda.synchronize()
     assert _rel(w, ref.cpu().numpy()) <= 1e-5
     assert info["solve_relres"][0] <= 1e-8, info
-    assert _rel(delta, d64.cpu().numpy()) <= step_bound
+    assert _rel(delta, d64.cpu().numpy()) <= 1e-4
     dense.close()
     ctx.close()
