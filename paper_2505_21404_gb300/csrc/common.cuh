@@ -103,6 +103,18 @@ __device__ __forceinline__ T warp_sum(T v) {
 __device__ __forceinline__ double tanh_t(double x) { return tanh(x); }
 __device__ __forceinline__ float tanh_t(float x) { return tanhf(x); }
 
+// A float widened to FP64 by rebuilding its bits with integer operations
+// (exponent rebiased by 1023 - 127, significand moved to the top), so the
+// widening does not occupy GB300's slow FP64 pipe; subnormal, infinite and
+// NaN inputs take the hardware conversion.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);   // +-0
+  if (e == 0u || e == 0xFFu) return (double)f;
+  return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)), (int)(b << 29));
+}
+
 // Double-float ("float2 as hi+lo") accumulation for FP32 data that needs an
 // accumulator with ~48 significant bits.  two_sum / two_prod are the
 // error-free transformations of Knuth and Dekker (the latter with fma).

@@ -243,12 +243,12 @@ __device__ __forceinline__ void oz_digits(double x, int E, float (&d)[ND]) {
   }
 #pragma unroll
   for (int s = ND - 1; s >= 1; --s) {
-    long long r = v & 255;     // v mod 256 (two's complement)
+    int r = (int)(v & 255);    // v mod 256 (two's complement)
     if (r >= 128) r -= 256;    // balanced digit in [-128, 127]
-    d[s] = (float)r;
+    d[s] = (float)r;           // 32-bit conversion: a 64-bit one runs on the slow FP64 pipe
     v = (v - r) >> 8;          // exact
   }
-  d[0] = (float)v;             // |v| <= 128
+  d[0] = (float)(int)v;        // |v| <= 128
 }
 
 // |x| as ordered integer bits (non-negative doubles compare like their bits)
@@ -553,14 +553,23 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int ec = (j < ncol && cj < m) ? epi.rexpA[row_off + cj] : 0;
         int e = er + ec - epi.eshift;
         e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-        tb[lane * 33 + j] = __longlong_as_double((long long)(e + 1023) << 52) * ((double)hi[j] + (double)lo[j]);
+        tb[lane * 33 + j] = __longlong_as_double((long long)(e + 1023) << 52) * (f2d_bits(hi[j]) + f2d_bits(lo[j]));
       }
       __syncwarp();
       if (!*abort_flag && lane < ncol) {
         const int col = col0 + lane;
+        // all 32 reads of C before the first write: the read-modify-write
+        // then costs one memory latency per sub-tile instead of 32
+        double cv[32];
+#pragma unroll
         for (int rr = 0; rr < 32; ++rr) {
           const int rw = tile.x * TM + q * 32 + rr;
-          if (rw < m && col <= rw) epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] -= tb[rr * 33 + lane];
+          cv[rr] = (rw < m && col <= rw) ? epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] : 0.0;
+        }
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) {
+          const int rw = tile.x * TM + q * 32 + rr;
+          if (rw < m && col <= rw) epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] = cv[rr] - tb[rr * 33 + lane];
         }
       }
     } else if (MODE == OZ_GEMM) {
@@ -570,7 +579,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 #pragma unroll
         for (int j = 0; j < CPW; ++j)
           if (col0 + j < epi.ncols) {
-            const double v = epi.alpha * ldexp((double)hi[j] + (double)lo[j], er + epi.rexpB[col0 + j] - epi.eshift);
+            const double v = epi.alpha * ldexp(f2d_bits(hi[j]) + f2d_bits(lo[j]), er + epi.rexpB[col0 + j] - epi.eshift);
             crow[j] = epi.beta == 0.0 ? v : v + epi.beta * crow[j];
           }
       }
@@ -578,7 +587,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0;
 #pragma unroll
       for (int j = 0; j < CPW; ++j)
-        if (col0 + j < m) orow[j] = (double)hi[j] + (double)lo[j];
+        if (col0 + j < m) orow[j] = f2d_bits(hi[j]) + f2d_bits(lo[j]);
     }
   }
   __syncwarp();

@@ -306,9 +306,14 @@ __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const doub
           hi = t;
           lo += te + e;
         }
-        const double v = (double)hi + (double)lo;
+        // renormalise (hi = fl32(hi + lo)), then one FP64 add of the two
+        // widened halves
+        const float sh = hi + lo;
+        lo = lo - (sh - hi);
+        hi = sh;
+        const double v = f2d_bits(hi) + f2d_bits(lo);
         Jrow[wo + (long long)a * win + b] = (TJ)v;
-        amax = fmaxf(amax, fabsf((float)v));
+        amax = fmaxf(amax, fabsf(hi));
       }
     }
   } else

@@ -341,14 +341,14 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 template dngd_status cholesky<double>(int, double*, long long, int*, double*, cudaStream_t);
 
 // FP64 diagonal block of one factorisation step, organised for GB300's slow
-// FP64 pipe and for few barriers: the block is factored in panels of 8
-// columns.  Warp 0 factors a panel alone (one reciprocal square root per
-// column by Newton-Raphson from a single-precision estimate, the panel's
-// own updates between warp syncs); then the whole CTA applies the panel's
-// rank-8 update to the trailing part (16 x 16 threads): two barriers per 8
-// columns.  The block's L and the reciprocals of its diagonal (rdiag[kb])
-// go to global memory; the panel below multiplies by them.
-constexpr int kDiagPanel = 8;
+// FP64 pipe: one reciprocal square root per column (Newton-Raphson from a
+// single-precision estimate; the panel below multiplies by it instead of
+// dividing), warp 0 scales the column, the rank-1 update is spread over a
+// 16 x 16 thread grid: two barriers per column.  (Factoring 8-column panels
+// in warp 0 alone, with two barriers per panel, measured slower: 85 us
+// against 75 us per block, one warp reaching a quarter of the SM's FP64
+// pipe.)  The block's L and the
+// reciprocals of its diagonal (rdiag[kb]) go to global memory.
 __global__ void __launch_bounds__(256) k_potrf_diag_rcp(int k0, int kb, double* A, long long lda,
                                                         double* __restrict__ rdiag, int* status) {
   __shared__ double S[kCholNB][kCholNB + 1];
@@ -362,49 +362,36 @@ __global__ void __launch_bounds__(256) k_potrf_diag_rcp(int k0, int kb, double* 
   }
   if (tid == 0) bad = -1;
   __syncthreads();
-  for (int jb = 0; jb < kb; jb += kDiagPanel) {
-    const int je = min(kb, jb + kDiagPanel);
+  for (int j = 0; j < kb; ++j) {
     if (tid < 32) {
-      for (int j = jb; j < je; ++j) {
-        // y = 1 / sqrt(piv): each Newton step y <- y (3 - piv y^2) / 2
-        // doubles the correct bits (24 -> 48 -> 53)
-        const double piv = S[j][j];
-        if (!(piv > 0.0 && piv < 1e300)) {
-          if (lane == 0) bad = j;
-          break;
-        }
+      // y = 1 / sqrt(piv) by Newton-Raphson on f(y) = 1/y^2 - piv from a
+      // single-precision start: each step y <- y (3 - piv y^2) / 2 doubles
+      // the correct bits (24 -> 48 -> 53)
+      const double piv = S[j][j];
+      const bool ok = piv > 0.0 && piv < 1e300;
+      double y = 0.0;
+      if (ok) {
         const float pf = (float)piv;
-        double y = (double)rsqrtf(pf > 1e-37f ? pf : 1e-37f);
+        y = (double)rsqrtf(pf > 1e-37f ? pf : 1e-37f);
         if (!(pf > 1e-37f)) y = 1.0 / sqrt(piv);   // outside the float range
         y = y * (1.5 - 0.5 * piv * y * y);
         y = y * (1.5 - 0.5 * piv * y * y);
         for (int i = j + 1 + lane; i < kb; i += 32) S[i][j] *= y;
-        __syncwarp();
-        if (lane == 0) {
+      }
+      if (lane == 0) {
+        if (ok) {
           S[j][j] = piv * y;   // sqrt(piv)
           rcp[j] = y;
+        } else {
+          bad = j;
         }
-        // the panel's later columns (every row from the column's diagonal down)
-        for (int c = j + 1; c < je; ++c) {
-          const double lcj = S[c][j];
-          for (int i = c + lane; i < kb; i += 32) S[i][c] -= S[i][j] * lcj;
-        }
-        __syncwarp();
       }
     }
     __syncthreads();
     if (bad >= 0) break;
-    // rank-8 update of the trailing block (rows and columns >= je)
-    for (int i = je + ty; i < kb; i += 16) {
-      double li[kDiagPanel];
-#pragma unroll
-      for (int p = 0; p < kDiagPanel; ++p) li[p] = jb + p < je ? S[i][jb + p] : 0.0;
-      for (int c = je + tx; c <= i; c += 16) {
-        double acc = S[i][c];
-#pragma unroll
-        for (int p = 0; p < kDiagPanel; ++p) acc -= li[p] * S[c][jb + p];
-        S[i][c] = acc;
-      }
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      const double lij = S[i][j];
+      for (int c = j + 1 + tx; c <= i; c += 16) S[i][c] -= lij * S[c][j];
     }
     __syncthreads();
   }
