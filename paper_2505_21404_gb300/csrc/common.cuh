@@ -103,16 +103,32 @@ __device__ __forceinline__ T warp_sum(T v) {
 __device__ __forceinline__ double tanh_t(double x) { return tanh(x); }
 __device__ __forceinline__ float tanh_t(float x) { return tanhf(x); }
 
-// A float widened to FP64 by rebuilding its bits with integer operations
-// (exponent rebiased by 1023 - 127, significand moved to the top), so the
-// widening does not occupy GB300's slow FP64 pipe; subnormal, infinite and
-// NaN inputs take the hardware conversion.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned e = (b >> 23) & 0xFFu;
-  if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);   // +-0
-  if (e == 0u || e == 0xFFu) return (double)f;
-  return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)), (int)(b << 29));
+// double(hi + lo) for a normalised double-float pair (|lo| <= ulp(hi) / 2),
+// assembled with integer operations (hi's significand shifted to the top of
+// the 53 bits, lo's added or subtracted below it, at most one bit of
+// renormalisation); a zero, subnormal or non-finite hi or lo, or a pair that
+// is not normalised, takes the FP64 add.
+__device__ __forceinline__ double df_to_double_bits(float hi, float lo) {
+  const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
+  const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
+  const bool lo_zero = (lb & 0x7FFFFFFFu) == 0u;
+  const int k = 29 - (eh - el);
+  if (eh == 0 || eh == 0xFF || (!lo_zero && (el == 0 || el == 0xFF || k > 5))) return (double)hi + (double)lo;
+  unsigned long long S = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
+  if (!lo_zero) {
+    unsigned long long Ml = (lb & 0x7FFFFFu) | 0x800000u;
+    if (k >= 0) Ml <<= k;
+    else if (k > -40) Ml = (Ml + (1ull << (-k - 1))) >> (-k);
+    else Ml = 0;
+    S = ((hb ^ lb) >> 31) ? S - Ml : S + Ml;
+  }
+  unsigned long long e = (unsigned long long)(eh + 896);   // 1023 - 127
+  if (S < (1ull << 52)) {
+    S <<= 1;
+    --e;
+  }
+  return __longlong_as_double(
+      (long long)(((unsigned long long)(hb >> 31) << 63) | (e << 52) | (S - (1ull << 52))));
 }
 
 // Double-float ("float2 as hi+lo") accumulation for FP32 data that needs an

@@ -553,7 +553,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int ec = (j < ncol && cj < m) ? epi.rexpA[row_off + cj] : 0;
         int e = er + ec - epi.eshift;
         e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-        tb[lane * 33 + j] = __longlong_as_double((long long)(e + 1023) << 52) * (f2d_bits(hi[j]) + f2d_bits(lo[j]));
+        tb[lane * 33 + j] = __longlong_as_double((long long)(e + 1023) << 52) * (df_to_double_bits(hi[j], lo[j]));
       }
       __syncwarp();
       if (!*abort_flag && lane < ncol) {
@@ -579,7 +579,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 #pragma unroll
         for (int j = 0; j < CPW; ++j)
           if (col0 + j < epi.ncols) {
-            const double v = epi.alpha * ldexp(f2d_bits(hi[j]) + f2d_bits(lo[j]), er + epi.rexpB[col0 + j] - epi.eshift);
+            const double v = epi.alpha * ldexp(df_to_double_bits(hi[j], lo[j]), er + epi.rexpB[col0 + j] - epi.eshift);
             crow[j] = epi.beta == 0.0 ? v : v + epi.beta * crow[j];
           }
       }
@@ -587,7 +587,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0;
 #pragma unroll
       for (int j = 0; j < CPW; ++j)
-        if (col0 + j < m) orow[j] = f2d_bits(hi[j]) + f2d_bits(lo[j]);
+        if (col0 + j < m) orow[j] = df_to_double_bits(hi[j], lo[j]);
     }
   }
   __syncwarp();
@@ -932,20 +932,34 @@ struct OzFactor {
   int m;
   double* C;
   long long ldc;
-  __nv_bfloat16* S;
-  int* rowexp;
-  int2* d_tiles;
+  __nv_bfloat16* S[2];       // panel slices of even / odd steps
+  int* rowexp[2];
+  int2* d_strip;             // tiles (I, 0): the trailing update's first column tile
+  int2* d_rest;              // tiles (I, J >= 1), row blocks in order
   double* rdiag;             // reciprocals of the current diagonal block's pivots
-  std::vector<int> prefix;   // tiles with row block < I, for I = 0 .. nI
-  CUtensorMap mapA, mapB;
+  std::vector<int> rest_prefix;   // rest tiles with row block < I, for I = 0 .. nI
+  CUtensorMap mapA[2], mapB[2];
+  cudaStream_t side = nullptr;    // the rest of each trailing update
+  cudaEvent_t ev_fork = nullptr, ev_slice = nullptr, ev_rest = nullptr;
 };
+
+namespace {
+size_t oz_factor_slice_bytes(int m) { return ((size_t)m * FLD * sizeof(__nv_bfloat16) + 255) & ~(size_t)255; }
+size_t oz_factor_exp_bytes(int m) { return ((size_t)m * sizeof(int) + 255) & ~(size_t)255; }
+}  // namespace
 
 size_t oz_factor_bytes(int m) {
   const int nI = (m + TM - 1) / TM, nJ = (m + OzCfg<FNS, FNG>::TN - 1) / OzCfg<FNS, FNG>::TN;
-  return (size_t)m * FLD * sizeof(__nv_bfloat16) + (size_t)m * sizeof(int) + (size_t)nI * nJ * sizeof(int2) +
+  return 2 * oz_factor_slice_bytes(m) + 2 * oz_factor_exp_bytes(m) + (size_t)nI * (nJ + 1) * sizeof(int2) +
          FNB * sizeof(double) + 1024;
 }
 
+// Tiles of the trailing update of a block of r rows: the first column tile
+// (the columns the next diagonal block and panel are cut from) is one
+// launch, the other tiles a second launch on a side stream, so the next
+// step's diagonal block, panel solve and slicing overlap the bulk of the
+// update; slices alternate between two buffers so the next step's slicing
+// does not overwrite what the side launch reads.
 dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void* work, cudaStream_t st) {
   EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
   if (!enc) return DNGD_ERR_CUDA;
@@ -954,37 +968,49 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
   p->m = m;
   p->C = C;
   p->ldc = ldc;
-  p->S = (__nv_bfloat16*)work;
-  p->rowexp = (int*)((char*)work + (size_t)m * FLD * sizeof(__nv_bfloat16));
-  p->d_tiles = (int2*)(((uintptr_t)(p->rowexp + m) + 255) & ~(uintptr_t)255);
-  // lower tiles, row blocks in order: the tiles of a trailing block of r
-  // rows are the first prefix[ceil(r / TM)] entries (the few that reach
-  // past r are masked in the epilogue)
-  std::vector<int2> tiles;
+  char* w = (char*)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  for (int b = 0; b < 2; ++b) {
+    p->S[b] = (__nv_bfloat16*)w;
+    w += oz_factor_slice_bytes(m);
+  }
+  for (int b = 0; b < 2; ++b) {
+    p->rowexp[b] = (int*)w;
+    w += oz_factor_exp_bytes(m);
+  }
   const int nI = (m + TM - 1) / TM, nJ = (m + TN - 1) / TN;
-  p->rdiag = (double*)(((uintptr_t)(p->d_tiles + (size_t)nI * nJ) + 255) & ~(uintptr_t)255);
-  p->prefix.assign(nI + 1, 0);
+  p->d_strip = (int2*)w;
+  p->d_rest = p->d_strip + nI;
+  p->rdiag = (double*)(((uintptr_t)(p->d_rest + (size_t)nI * nJ) + 255) & ~(uintptr_t)255);
+  std::vector<int2> tiles;
+  for (int I = 0; I < nI; ++I) tiles.push_back(make_int2(I, 0));
+  p->rest_prefix.assign(nI + 1, 0);
   for (int I = 0; I < nI; ++I) {
-    for (int Jc = 0; Jc < nJ && Jc * TN <= I * TM + TM - 1; ++Jc) tiles.push_back(make_int2(I, Jc));
-    p->prefix[I + 1] = (int)tiles.size();
+    for (int Jc = 1; Jc < nJ && Jc * TN <= I * TM + TM - 1; ++Jc) tiles.push_back(make_int2(I, Jc));
+    p->rest_prefix[I + 1] = (int)tiles.size() - nI;
   }
   cuuint64_t gdim[2] = {(cuuint64_t)FLD, (cuuint64_t)m};
   cuuint64_t gstride[1] = {(cuuint64_t)(FLD * 2)};
   cuuint32_t estride[2] = {1, 1};
   cuuint32_t boxA[2] = {(cuuint32_t)KS, (cuuint32_t)TM};
   cuuint32_t boxB[2] = {(cuuint32_t)KS, (cuuint32_t)TN};
-  if (enc(&p->mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S, gdim, gstride, boxA, estride,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-      enc(&p->mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S, gdim, gstride, boxB, estride,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-    delete p;
-    return DNGD_ERR_CUDA;
+  for (int b = 0; b < 2; ++b) {
+    if (enc(&p->mapA[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S[b], gdim, gstride, boxA, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&p->mapB[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p->S[b], gdim, gstride, boxB, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      delete p;
+      return DNGD_ERR_CUDA;
+    }
   }
-  if (cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st) !=
-      cudaSuccess) {
-    delete p;
+  if (cudaMemcpyAsync(p->d_strip, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_slice, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_rest, cudaEventDisableTiming) != cudaSuccess) {
+    oz_factor_free(p);
     return DNGD_ERR_CUDA;
   }
   static bool attr = false;
@@ -999,26 +1025,63 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
 
 dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
   const int m = p->m;
-  const OzEpi upd{p->C, p->ldc, p->rowexp, nullptr, 16 + 8 * (FNG - 1), 0, 0, 0.0, 0.0};
-  for (int k0 = 0; k0 < m; k0 += FNB) {
+  // the side stream joins the caller's stream here and is joined back at
+  // the end (also inside a stream capture)
+  DNGD_CUDA_CHECK(cudaEventRecord(p->ev_fork, st));
+  DNGD_CUDA_CHECK(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  bool rest_pending = false;
+  for (int k0 = 0, step = 0; k0 < m; k0 += FNB, ++step) {
+    // diagonal block and panel: after the previous step's first column
+    // tile, which the stream order gives
     dngd_status s = chol_step_f64(m, k0, p->C, p->ldc, p->rdiag, status, st);
-    if (s) return s;
+    if (s) {
+      cudaEventRecord(p->ev_rest, p->side);   // join the side stream before leaving
+      cudaStreamWaitEvent(st, p->ev_rest, 0);
+      return s;
+    }
     const int kb = (m - k0) < FNB ? (m - k0) : FNB;
     const int row0 = k0 + kb, r = m - row0;
     if (r <= 0) break;
+    const int b = step & 1;
     DNGD_NOTE_LAUNCH();
-    k_panel_slice<<<(r + 7) / 8, 256, 0, st>>>(m, row0, k0, kb, p->C, p->ldc, p->S, p->rowexp, status);
+    k_panel_slice<<<(r + 7) / 8, 256, 0, st>>>(m, row0, k0, kb, p->C, p->ldc, p->S[b], p->rowexp[b], status);
     DNGD_LAUNCH_CHECK();
-    const int ntiles = p->prefix[(r + TM - 1) / TM];
+    DNGD_CUDA_CHECK(cudaEventRecord(p->ev_slice, st));
+    const OzEpi upd{p->C, p->ldc, p->rowexp[b], nullptr, 16 + 8 * (FNG - 1), 0, 0, 0.0, 0.0};
+    const int nIr = (r + TM - 1) / TM;
+    // the first column tile also waits for the previous step's rest, which
+    // updated the same columns
+    if (rest_pending) DNGD_CUDA_CHECK(cudaStreamWaitEvent(st, p->ev_rest, 0));
     DNGD_NOTE_LAUNCH();
-    k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(ntiles, 1), othreads<FNS, FNG>(), osmem<FNS, FNG>(), st>>>(
-        p->mapA, p->mapB, p->d_tiles, r, row0, FNB / KS, FNB, nullptr, 0, 0, upd, status);
+    k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(nIr, 1), othreads<FNS, FNG>(), osmem<FNS, FNG>(), st>>>(
+        p->mapA[b], p->mapB[b], p->d_strip, r, row0, FNB / KS, FNB, nullptr, 0, 0, upd, status);
     DNGD_LAUNCH_CHECK();
+    const int nrest = p->rest_prefix[nIr];
+    DNGD_CUDA_CHECK(cudaStreamWaitEvent(p->side, p->ev_slice, 0));
+    if (nrest > 0) {
+      DNGD_NOTE_LAUNCH();
+      k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(nrest, 1), othreads<FNS, FNG>(), osmem<FNS, FNG>(), p->side>>>(
+          p->mapA[b], p->mapB[b], p->d_rest, r, row0, FNB / KS, FNB, nullptr, 0, 0, upd, status);
+      DNGD_LAUNCH_CHECK();
+    }
+    DNGD_CUDA_CHECK(cudaEventRecord(p->ev_rest, p->side));
+    rest_pending = true;
   }
+  // join: every update has landed before the caller's stream goes on
+  DNGD_CUDA_CHECK(cudaEventRecord(p->ev_rest, p->side));
+  DNGD_CUDA_CHECK(cudaStreamWaitEvent(st, p->ev_rest, 0));
   return DNGD_OK;
 }
 
-void oz_factor_free(OzFactor* p) { delete p; }
+void oz_factor_free(OzFactor* p) {
+  if (!p) return;
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_slice) cudaEventDestroy(p->ev_slice);
+  if (p->ev_rest) cudaEventDestroy(p->ev_rest);
+  if (p->side) cudaStreamDestroy(p->side);
+  delete p;
+}
+
 
 // ---------------------------------------------------------------------------
 // FP64 GEMM from exact slice products: C = alpha A B^T + beta C

@@ -306,12 +306,12 @@ __global__ void k_jac_write(NetInfo net, const T* __restrict__ theta, const doub
           hi = t;
           lo += te + e;
         }
-        // renormalise (hi = fl32(hi + lo)), then one FP64 add of the two
-        // widened halves
+        // renormalise (hi = fl32(hi + lo)), then assemble the FP64 value
+        // with integer operations
         const float sh = hi + lo;
         lo = lo - (sh - hi);
         hi = sh;
-        const double v = f2d_bits(hi) + f2d_bits(lo);
+        const double v = df_to_double_bits(hi, lo);
         Jrow[wo + (long long)a * win + b] = (TJ)v;
         amax = fmaxf(amax, fabsf(hi));
       }
