@@ -50,6 +50,12 @@ def _prec(dngd, name):
 WORKLOAD = "poisson5d_dense: -Lap u = f on [0,1]^5, MLP 5-256-256-256-1 (n=133377), 3000+1000 pts (m=4000)"
 
 
+# DRAM bytes (read + write) of one exact-Gram product launch on the 5-D
+# workload, from an ncu capture of k_gram_oz (profiles/k_gram_oz_poisson5d_oz64.md);
+# keyed by --precision, valid for the kernel as committed with that summary.
+GRAM_TRAFFIC = {"oz64": None}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -807,6 +813,7 @@ def run_dense(args, wl, rank, world, local_rank):
     lat = np.array([a.elapsed_time(b) for a, b in step_ev])
     value = job_value(world, ms_per_step)
     gram_ms = float(np.mean([i["phase_ms"][1] for i in infos]))
+    gram_kernel_ms = float(np.mean([i["gram_kernel_ms"] for i in infos]))
     phase = np.mean(np.array([i["phase_ms"] for i in infos]), axis=0).tolist()
     iters = np.mean(np.array([i["solve_iters"] for i in infos]), axis=0).tolist()
     theta_late = theta.cpu().numpy().copy()
@@ -908,8 +915,10 @@ def run_dense(args, wl, rank, world, local_rank):
     hbm, bf16_burst, bf16_sust, src = _peaks()
     alg_flops = float(m) * (m + 1) * n
     exec_flops = alg_flops * {dngd.MIXED_OZ: 13, dngd.MIXED_OZ64: 15}.get(prec, 1)
-    achieved = alg_flops / (gram_ms * 1e-3) / 1e12
-    executed = exec_flops / (gram_ms * 1e-3) / 1e12
+    # the product kernel alone (CUDA events around its launch)
+    kern_ms = gram_kernel_ms if gram_kernel_ms > 0 else gram_ms
+    achieved = alg_flops / (kern_ms * 1e-3) / 1e12
+    executed = exec_flops / (kern_ms * 1e-3) / 1e12
     peak = bf16_sust / 2.0 if prec == dngd.MIXED_TF32 else bf16_sust
     # the refinement's J^T p / J u GEMVs over the FP32 J (BF16 / TF32 paths)
     jt_ms = float(np.mean([i["jt_ms"] for i in infos]))
@@ -938,22 +947,28 @@ def run_dense(args, wl, rank, world, local_rank):
                      "algorithmic": "per PCG iteration 8 m^2 + 4 m^2 B (exact Gram operator, L^-1 and L^-T "
                                     "triangles); per solve 4 m n B (J^T x)",
                      "peak_source": f"{src} HBM copy bandwidth", "traffic": None}
+        traffic = args.gram_traffic
+        if traffic is None and args.workload == "poisson5d" and args.points <= 0:
+            traffic = GRAM_TRAFFIC.get(args.precision)
         roof_gram = {"bound": "tensor",
-                     "kernel": "k_oz_slice + k_gram_oz + k_oz_reduce (exact Gram: tcgen05 BF16 on 8-bit slices)",
+                     "kernel": "k_gram_oz (exact Gram: tcgen05 BF16 products of 8-bit slices)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "algorithmic": "m(m+1)n flop per Gram (the syrk of the 5-D workload, 2.135e12)",
-                     "flops_per_launch": alg_flops, "launch_ms": gram_ms,
+                     "flops_per_launch": alg_flops, "launch_ms": kern_ms,
+                     "phase_ms": gram_ms, "phase": "k_oz_slice + k_gram_oz (slicing and products)",
                      "executed_tflops": executed, "executed_frac": executed / peak,
                      "executed": ("15 m(m+1)n BF16 tensor flop (the 15 slice products of levels <= 5 of four "
                                   "slices)" if prec == dngd.MIXED_OZ64 else
                                   "13 m(m+1)n BF16 tensor flop (the 13 products of four slices)"),
                      "peak_source": f"{src} bf16 sustained",
-                     "traffic": args.gram_traffic if args.workload == "poisson5d" else None,
-                     "traffic_source": "profiles/k_gram_oz_poisson5d.md (ncu, one launch of the 5-D workload)"}
+                     "traffic": traffic,
+                     "traffic_source": ("profiles/k_gram_oz_poisson5d_oz64.md (ncu dram__bytes_read.sum + "
+                                        "dram__bytes_write.sum, one launch of the 5-D workload)")
+                     if traffic is not None else None}
     else:
         roof_gram = {"bound": "tensor", "kernel": "k_gram_tc (tcgen05 syrk, lower 128x256 tiles)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "flops_per_launch": alg_flops, "launch_ms": gram_ms,
+                     "flops_per_launch": alg_flops, "launch_ms": kern_ms, "phase_ms": gram_ms,
                      "peak_source": f"{src} bf16 sustained" + (" / 2 for tf32" if prec == dngd.MIXED_TF32 else ""),
                      "traffic": None}
     line = {

@@ -199,6 +199,9 @@ typedef struct {
                                the refinement (mixed, timing enabled): each
                                reads the FP32 J once */
   double lambda_used;       /* the damping this step solved with */
+  float gram_kernel_ms;     /* duration of the Gram's product kernel alone
+                               (tensor-core modes, timing enabled; without
+                               the slicing and the split-K reduction) */
 } dngd_step_info;
 
 typedef struct dngd_ctx dngd_ctx;

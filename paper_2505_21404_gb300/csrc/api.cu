@@ -98,7 +98,7 @@ struct dngd_ctx {
   int factor_attempts = 0;
   void* K0 = nullptr;      // mixed path: Gram + (lambda + mu0) I before factorisation
   double relres[2] = {0.0, 0.0};
-  cudaEvent_t ev[9] = {};
+  cudaEvent_t ev[10] = {};
   cudaEvent_t kev[4] = {};  // first J^T p / J u launches of the first solve
 
   // asynchronous (graph-capturable) stepping
@@ -444,9 +444,10 @@ void gram_set_shift(dngd_ctx* c, double shift) {
   if (c->oz) gram_oz_set_shift(c->oz, shift);
   else gram_tc_set_shift(c->gram, shift);
 }
-dngd_status gram_run(dngd_ctx* c, cudaEvent_t ev_after_mma) {
-  return c->oz ? gram_oz_run(c->oz, c->status, c->st, ev_after_mma)
-               : gram_tc_run(c->gram, c->status, c->st, ev_after_mma);
+dngd_status gram_run(dngd_ctx* c, bool timed) {
+  cudaEvent_t before = timed ? c->ev[9] : nullptr, after = timed ? c->ev[8] : nullptr;
+  return c->oz ? gram_oz_run(c->oz, c->status, c->st, before, after)
+               : gram_tc_run(c->gram, c->status, c->st, before, after);
 }
 
 template <typename T>
@@ -480,7 +481,7 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
     const double mu0 = mu;
     gram_set_shift(c, c->lambda + mu);
-    if ((s = gram_run(c, c->timing ? c->ev[8] : nullptr))) return s;
+    if ((s = gram_run(c, c->timing))) return s;
     c->factor_attempts = 0;
     if (!c->async && (s = diag_sum<float>(m, (const float*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
     for (int attempt = 0;; ++attempt) {
@@ -522,7 +523,7 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
       // no host round trip: one factorisation with the shift of the last
       // synchronous step; a failure is reported by the status word
       gram_set_shift(c, c->lambda + mu);
-      if ((s = gram_run(c, nullptr))) return s;
+      if ((s = gram_run(c, false))) return s;
       DNGD_CUDA_CHECK(cudaMemsetAsync(c->Linv, 0, sizeof(float) * (size_t)m * c->ldk, c->st));
       if ((s = cholesky_f32_inv(m, (float*)c->K, c->ldk, c->Linv, c->ldk, c->status, c->st, tc3p(c)))) return s;
       if ((s = trtri_offdiag_f32(m, (const float*)c->K, c->ldk, c->Linv, c->ldk, c->trtri_work, c->st, tc3p(c),
@@ -533,7 +534,7 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
       goto factored;
     }
     gram_set_shift(c, c->lambda + mu);
-    if ((s = gram_run(c, c->timing ? c->ev[8] : nullptr))) return s;
+    if ((s = gram_run(c, c->timing))) return s;
     // K0 = K + (lambda + mu0) I is kept, so a failed factorisation is retried
     // from the copy with a larger shift instead of recomputing the Gram
     DNGD_CUDA_CHECK(cudaMemcpyAsync(c->K0, c->K, sizeof(float) * (size_t)m * c->ldk, cudaMemcpyDeviceToDevice,
@@ -873,7 +874,7 @@ dngd_status alloc_pcg(dngd_ctx* c, bool dry, size_t* bytes_out) {
   DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->scal_h, sizeof(double) * S_COUNT));
   DNGD_CUDA_CHECK(cudaMallocHost(&c->status_h, sizeof(int) * 4));
-  for (int i = 0; i < 9; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
+  for (int i = 0; i < 10; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
   for (int i = 0; i < 4; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->kev[i]));
   // default landmarks: evenly spaced residual indices
   c->lm_host.resize(ell);
@@ -941,6 +942,7 @@ void info_from_host(dngd_ctx* c, dngd_step_info* info) {
     float tot = 0.f;
     cudaEventElapsedTime(&tot, c->ev[0], c->ev[7]);
     info->phase_ms[7] = tot;
+    if (c->prec != DNGD_FP64 && !c->pcg) cudaEventElapsedTime(&info->gram_kernel_ms, c->ev[9], c->ev[8]);
     if (!c->pcg && c->prec != DNGD_FP64 && c->iters[0] > 0) {
       float a = 0.f, b = 0.f;
       cudaEventElapsedTime(&a, c->kev[0], c->kev[1]);
@@ -1155,7 +1157,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
                      c->gram_partial_bytes, c->st);
     if (s) return s;
   }
-  for (int i = 0; i < 9; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
+  for (int i = 0; i < 10; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->ev[i]));
   for (int i = 0; i < 4; ++i) DNGD_CUDA_CHECK(cudaEventCreate(&c->kev[i]));
   return DNGD_OK;
 }
@@ -1178,7 +1180,7 @@ void free_ctx(dngd_ctx* c) {
   if (c->ozf) oz_factor_free(c->ozf);
   if (c->ozg) oz_gemm_free(c->ozg);
   if (c->ozi) oz_gemm_free(c->ozi);
-  for (int i = 0; i < 9; ++i)
+  for (int i = 0; i < 10; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (int i = 0; i < 4; ++i)
     if (c->kev[i]) cudaEventDestroy(c->kev[i]);

@@ -165,6 +165,62 @@ __device__ __forceinline__ dfloat df_fma(dfloat a, float x, float y) {
   return {hi, lo};
 }
 
+// Nearest double-float pair of an FP64 value (hi = RN(x), lo = RN(x - hi);
+// |x| within the float range).
+__device__ __forceinline__ dfloat df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+
+// a * b, ~2^-47 relative (the lo x lo term is dropped).
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float hi = p + e;
+  return {hi, e - (hi - p)};
+}
+
+// acc - a * b.
+__device__ __forceinline__ dfloat df_sub_mul(dfloat acc, dfloat a, dfloat b) {
+  const float p = a.hi * b.hi;
+  float pe = fmaf(a.hi, b.hi, -p);
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  float s, e;
+  two_sum(acc.hi, -p, s, e);
+  e += acc.lo - pe;
+  const float hi = s + e;
+  return {hi, e - (hi - s)};
+}
+
+// 1 / d for d > 0 (float range): one Newton-Raphson step y + y (1 - d y)
+// from the single-precision reciprocal, the residual 1 - d y formed in
+// double-float.
+__device__ __forceinline__ dfloat df_rcp(dfloat d) {
+  const float y = 1.0f / d.hi;
+  const float r = fmaf(-d.hi, y, 1.0f) - d.lo * y;   // 1 - d y (the first term exact)
+  const float c = y * r;
+  const float hi = y + c;
+  return {hi, c - (hi - y)};
+}
+
+// 1 / sqrt(d) for d > 0 (float range): a single-precision Newton step on
+// the rsqrt estimate, then one in double-float, y + y (1 - d y^2) / 2.
+__device__ __forceinline__ dfloat df_rsqrt(dfloat d) {
+  float y = rsqrtf(d.hi);
+  y = y * fmaf(-0.5f * d.hi, y * y, 1.5f);
+  const float p = y * y;
+  const float pe = fmaf(y, y, -p);             // y^2 = p + pe exactly
+  const float h = d.hi * p;
+  const float he = fmaf(d.hi, p, -h) + fmaf(d.hi, pe, d.lo * p);   // d y^2 = h + he
+  const float r = (1.0f - h) - he;             // 1 - h exact for h near 1
+  const float c = 0.5f * y * r;
+  const float hi = y + c;
+  return {hi, c - (hi - y)};
+}
+
 __device__ __forceinline__ dfloat df_shfl_xor(dfloat v, int o) {
   return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }

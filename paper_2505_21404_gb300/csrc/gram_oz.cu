@@ -152,8 +152,12 @@ template <int NS, int NG>
 __host__ __device__ constexpr int b_tile() { return OzCfg<NS, NG>::TN * 64; }
 template <int NS, int NG>
 __host__ __device__ constexpr int ostage() { return NS * (A_TILE + b_tile<NS, NG>()); }
+// The update configuration (six slices) also holds each epilogue warp's
+// 32 x 33 FP64 block of C.
 template <int NS, int NG>
-__host__ __device__ constexpr int osmem() { return OzCfg<NS, NG>::OST * ostage<NS, NG>() + 1024; }
+__host__ __device__ constexpr int cstage() { return NS == 6 ? 8 * 32 * 33 * (int)sizeof(double) : 0; }
+template <int NS, int NG>
+__host__ __device__ constexpr int osmem() { return OzCfg<NS, NG>::OST * ostage<NS, NG>() + cstage<NS, NG>() + 1024; }
 
 template <int NS>
 __host__ __device__ __forceinline__ int g_lo(int g) { return g > NS - 1 ? g - (NS - 1) : 0; }
@@ -170,8 +174,8 @@ static_assert(OzCfg<4, 5>::hi(OzCfg<4, 5>::NA - 1) == 4 && OzCfg<4, 6>::hi(OzCfg
               "the accumulators cover every kept level");
 static_assert(osmem<4, 5>() <= 227 * 1024 && osmem<4, 6>() <= 227 * 1024 && osmem<6, 7>() <= 227 * 1024,
               "shared-memory ring too large");
-static_assert(epi_warps<6, 7>() * 32 * 33 * (int)sizeof(double) <= OzCfg<6, 7>::OST * ostage<6, 7>(),
-              "the update epilogue stages its sub-tiles in the operand ring");
+static_assert(epi_warps<6, 7>() * 32 * 33 * (int)sizeof(double) == cstage<6, 7>(),
+              "the update epilogue keeps one block of C per epilogue warp");
 static_assert(cpw<6, 7>() == 32 && cpw<4, 5>() % 8 == 0 && cpw<4, 6>() % 8 == 0 && cpw<4, 5>() <= 64 &&
                   cpw<4, 6>() <= 64,
               "an epilogue warp drains whole 8-column blocks (32 for the update's staged sub-tile)");
@@ -219,6 +223,17 @@ __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
   const float t = s + l;
   lo = l - (t - s);
   hi = t;
+}
+
+// x 2^e: e added to the exponent field when x and the result are normal
+// (integer operations), else an FP64 multiply by 2^e with e clamped to the
+// normal range.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex != 0 && ex != 0x7FF && ex + e >= 1 && ex + e <= 2046) return __longlong_as_double(b + ((long long)e << 52));
+  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  return __longlong_as_double((long long)(e + 1023) << 52) * x;
 }
 
 // Weight 2^(-8 s) of slice s in the pre-scaled layout (exact in BF16 for the
@@ -481,6 +496,25 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       hi[j] = 0.f;
       lo[j] = 0.f;
     }
+    const int row = tile.x * TM + q * 32 + lane;
+    const int col0 = tile.y * TN + cg * CPW;
+    // OZ_UPDATE: the warp's 32 x 32 sub-tile of C (lane = column) is copied
+    // into its own shared-memory block while the operands load and the MMAs
+    // run
+    double* cs = reinterpret_cast<double*>(smem_raw + (smem_base - smem_u32(smem_raw)) + OST * OSTAGE) +
+                 (warp - 2) * 32 * 33;
+    if (MODE == OZ_UPDATE) {
+      const int col = col0 + lane;
+#pragma unroll 8
+      for (int rr = 0; rr < 32; ++rr) {
+        const int rw = tile.x * TM + q * 32 + rr;
+        if (lane < ncol && rw < m && col <= rw)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(cs + rr * 33 + lane)),
+                       "l"(epi.C + (long long)(row_off + rw) * epi.ldc + row_off + col)
+                       : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     // the chunks in the order the MMA warp commits them: by last stage, a
     // chunk of one stage (issued in the second pass) after the others, then
     // by accumulator
@@ -539,37 +573,26 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           cend[a] = e + 1 < nk ? chunk_end<NS, NG>(a, cidx[a], nk) : INT_MAX;
         }
     }
-    const int row = tile.x * TM + q * 32 + lane;
-    const int col0 = tile.y * TN + cg * CPW;
     if (MODE == OZ_UPDATE) {
-      // every MMA has completed, so the operand ring is idle: the warp's 32 x
-      // 32 sub-tile (lane = row), scaled by 2^(E_row + E_col - eshift), goes
-      // through shared memory and is subtracted row by row, coalesced
-      double* tb = reinterpret_cast<double*>(smem_raw + (smem_base - smem_u32(smem_raw))) + (warp - 2) * 32 * 33;
+      // the update, scaled by 2^(E_row + E_col - eshift), is subtracted in
+      // the shared copy by the thread of its row; the copy then goes back
+      // row by row (lane = column), coalesced
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncwarp();
       const int er = row < m ? epi.rexpA[row_off + row] : 0;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int cj = col0 + j;
-        const int ec = (j < ncol && cj < m) ? epi.rexpA[row_off + cj] : 0;
-        int e = er + ec - epi.eshift;
-        e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-        tb[lane * 33 + j] = __longlong_as_double((long long)(e + 1023) << 52) * (df_to_double_bits(hi[j], lo[j]));
+        if (j < ncol && row < m && cj <= row)
+          cs[lane * 33 + j] -= scale_pow2(df_to_double_bits(hi[j], lo[j]), er + epi.rexpA[row_off + cj] - epi.eshift);
       }
       __syncwarp();
       if (!*abort_flag && lane < ncol) {
         const int col = col0 + lane;
-        // all 32 reads of C before the first write: the read-modify-write
-        // then costs one memory latency per sub-tile instead of 32
-        double cv[32];
-#pragma unroll
+#pragma unroll 8
         for (int rr = 0; rr < 32; ++rr) {
           const int rw = tile.x * TM + q * 32 + rr;
-          cv[rr] = (rw < m && col <= rw) ? epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] : 0.0;
-        }
-#pragma unroll
-        for (int rr = 0; rr < 32; ++rr) {
-          const int rw = tile.x * TM + q * 32 + rr;
-          if (rw < m && col <= rw) epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] = cv[rr] - tb[rr * 33 + lane];
+          if (rw < m && col <= rw) epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] = cs[rr * 33 + lane];
         }
       }
     } else if (MODE == OZ_GEMM) {
@@ -834,7 +857,8 @@ dngd_status gram_oz_set_shift(OzPlan* p, double shift) {
   return DNGD_OK;
 }
 
-dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_after_mma) {
+dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_before_mma,
+                        cudaEvent_t ev_after_mma) {
   DNGD_NOTE_LAUNCH();
   if (p->j64)
     k_oz_slice<double><<<p->m, 256, 0, st>>>(p->m, p->n, (const double*)p->J, p->ldJ, p->S, p->ldS, p->ldb,
@@ -843,6 +867,7 @@ dngd_status gram_oz_run(OzPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_
     k_oz_slice<float><<<p->m, 256, 0, st>>>(p->m, p->n, (const float*)p->J, p->ldJ, p->S, p->ldS, p->ldb,
                                              p->rowmax, p->rowexp);
   DNGD_LAUNCH_CHECK();
+  if (ev_before_mma) cudaEventRecord(ev_before_mma, st);
   DNGD_NOTE_LAUNCH();
   const OzEpi none{nullptr, 0, nullptr, nullptr, 0, 0, 0, 0.0, 0.0};
   if (p->ng == 5)
@@ -934,9 +959,10 @@ struct OzFactor {
   long long ldc;
   __nv_bfloat16* S[2];       // panel slices of even / odd steps
   int* rowexp[2];
-  int2* d_strip;             // tiles (I, 0): the trailing update's first column tile
   int2* d_rest;              // tiles (I, J >= 1), row blocks in order
-  double* rdiag;             // reciprocals of the current diagonal block's pivots
+  float2* Ldf;               // the current diagonal block's L as pairs [64 x 64]
+  float2* rdf;               // its pivots' reciprocal square roots [64]
+  float2* Pdf;               // the solved panel as pairs [(m - k0 - 64) x 64]
   std::vector<int> rest_prefix;   // rest tiles with row block < I, for I = 0 .. nI
   CUtensorMap mapA[2], mapB[2];
   cudaStream_t side = nullptr;    // the rest of each trailing update
@@ -950,16 +976,16 @@ size_t oz_factor_exp_bytes(int m) { return ((size_t)m * sizeof(int) + 255) & ~(s
 
 size_t oz_factor_bytes(int m) {
   const int nI = (m + TM - 1) / TM, nJ = (m + OzCfg<FNS, FNG>::TN - 1) / OzCfg<FNS, FNG>::TN;
-  return 2 * oz_factor_slice_bytes(m) + 2 * oz_factor_exp_bytes(m) + (size_t)nI * (nJ + 1) * sizeof(int2) +
-         FNB * sizeof(double) + 1024;
+  return 2 * oz_factor_slice_bytes(m) + 2 * oz_factor_exp_bytes(m) + (size_t)nI * (nJ + 1) * sizeof(int2) + 256 +
+         (size_t)(FNB * FNB + FNB) * sizeof(float2) + (size_t)m * FNB * sizeof(float2) + 1024;
 }
 
-// Tiles of the trailing update of a block of r rows: the first column tile
-// (the columns the next diagonal block and panel are cut from) is one
-// launch, the other tiles a second launch on a side stream, so the next
-// step's diagonal block, panel solve and slicing overlap the bulk of the
-// update; slices alternate between two buffers so the next step's slicing
-// does not overwrite what the side launch reads.
+// The trailing update of a block of r rows: its first 64 columns (the
+// columns the next diagonal block and panel are cut from) in double-float
+// on the step's stream, the other column tiles from slices in one launch on
+// a side stream, so the next step's diagonal block, panel solve and slicing
+// overlap the bulk of the update; slices alternate between two buffers so
+// the next step's slicing does not overwrite what the side launch reads.
 dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void* work, cudaStream_t st) {
   EncodeTiledFn enc = (EncodeTiledFn)tensor_map_encoder();
   if (!enc) return DNGD_ERR_CUDA;
@@ -978,15 +1004,15 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
     w += oz_factor_exp_bytes(m);
   }
   const int nI = (m + TM - 1) / TM, nJ = (m + TN - 1) / TN;
-  p->d_strip = (int2*)w;
-  p->d_rest = p->d_strip + nI;
-  p->rdiag = (double*)(((uintptr_t)(p->d_rest + (size_t)nI * nJ) + 255) & ~(uintptr_t)255);
+  p->d_rest = (int2*)w;
+  p->Ldf = (float2*)(((uintptr_t)(p->d_rest + (size_t)nI * nJ) + 255) & ~(uintptr_t)255);
+  p->rdf = p->Ldf + FNB * FNB;
+  p->Pdf = p->rdf + FNB;
   std::vector<int2> tiles;
-  for (int I = 0; I < nI; ++I) tiles.push_back(make_int2(I, 0));
   p->rest_prefix.assign(nI + 1, 0);
   for (int I = 0; I < nI; ++I) {
     for (int Jc = 1; Jc < nJ && Jc * TN <= I * TM + TM - 1; ++Jc) tiles.push_back(make_int2(I, Jc));
-    p->rest_prefix[I + 1] = (int)tiles.size() - nI;
+    p->rest_prefix[I + 1] = (int)tiles.size();
   }
   cuuint64_t gdim[2] = {(cuuint64_t)FLD, (cuuint64_t)m};
   cuuint64_t gstride[1] = {(cuuint64_t)(FLD * 2)};
@@ -1004,7 +1030,7 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
       return DNGD_ERR_CUDA;
     }
   }
-  if (cudaMemcpyAsync(p->d_strip, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st) !=
+  if (cudaMemcpyAsync(p->d_rest, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -1031,9 +1057,9 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
   DNGD_CUDA_CHECK(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
   bool rest_pending = false;
   for (int k0 = 0, step = 0; k0 < m; k0 += FNB, ++step) {
-    // diagonal block and panel: after the previous step's first column
-    // tile, which the stream order gives
-    dngd_status s = chol_step_f64(m, k0, p->C, p->ldc, p->rdiag, status, st);
+    // diagonal block and panel (double-float): after the previous step's
+    // first 64 columns of its update, which the stream order gives
+    dngd_status s = chol_step_df(m, k0, p->C, p->ldc, p->Ldf, p->rdf, p->Pdf, status, st);
     if (s) {
       cudaEventRecord(p->ev_rest, p->side);   // join the side stream before leaving
       cudaStreamWaitEvent(st, p->ev_rest, 0);
@@ -1049,13 +1075,15 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
     DNGD_CUDA_CHECK(cudaEventRecord(p->ev_slice, st));
     const OzEpi upd{p->C, p->ldc, p->rowexp[b], nullptr, 16 + 8 * (FNG - 1), 0, 0, 0.0, 0.0};
     const int nIr = (r + TM - 1) / TM;
-    // the first column tile also waits for the previous step's rest, which
-    // updated the same columns
+    // the first 64 columns (double-float, from the panel's pairs) also wait
+    // for the previous step's rest, which updated the same columns
     if (rest_pending) DNGD_CUDA_CHECK(cudaStreamWaitEvent(st, p->ev_rest, 0));
-    DNGD_NOTE_LAUNCH();
-    k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(nIr, 1), othreads<FNS, FNG>(), osmem<FNS, FNG>(), st>>>(
-        p->mapA[b], p->mapB[b], p->d_strip, r, row0, FNB / KS, FNB, nullptr, 0, 0, upd, status);
-    DNGD_LAUNCH_CHECK();
+    s = strip_update_df(m, row0, p->Pdf, p->C, p->ldc, status, st);
+    if (s) {
+      cudaEventRecord(p->ev_rest, p->side);
+      cudaStreamWaitEvent(st, p->ev_rest, 0);
+      return s;
+    }
     const int nrest = p->rest_prefix[nIr];
     DNGD_CUDA_CHECK(cudaStreamWaitEvent(p->side, p->ev_slice, 0));
     if (nrest > 0) {

@@ -385,8 +385,10 @@ dngd_status gram_tc_set_shift(GramPlan* p, double shift) {
   return DNGD_OK;
 }
 
-dngd_status gram_tc_run(GramPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_after_mma) {
+dngd_status gram_tc_run(GramPlan* p, int* status, cudaStream_t st, cudaEvent_t ev_before_mma,
+                        cudaEvent_t ev_after_mma) {
   dim3 grid(p->ntiles, p->nsplit);
+  if (ev_before_mma) cudaEventRecord(ev_before_mma, st);
   DNGD_NOTE_LAUNCH();
   if (p->kind == 0)
     k_gram_tc<0><<<grid, GRAM_THREADS, SMEM_BYTES, st>>>(p->mapA, p->mapB, p->d_tiles, p->m, p->num_kblk, p->partials,

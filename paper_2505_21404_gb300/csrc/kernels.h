@@ -101,10 +101,17 @@ dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* D
 // bottom-up; the large nodes (k0, n1, n2) are returned bottom-up.
 dngd_status trtri_small_nodes_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
                                   cudaStream_t st, std::vector<int3>* large_out);
-// One 64-column step of the FP64 blocked Cholesky (diagonal block at k0 and
-// the panel solve below it; no trailing update; rdiag [64] device scratch).
-// A non-positive pivot sets ST_NOT_SPD and status[1] = column.
-dngd_status chol_step_f64(int m, int k0, double* A, long long lda, double* rdiag, int* status, cudaStream_t st);
+// One 64-column step of the blocked Cholesky of an FP64 matrix in
+// double-float arithmetic (diagonal block at k0 and the panel solve below
+// it; no trailing update).  Scratch: Ldf [64 x 64] and rdf [64] pairs of the
+// block's factor, P [(m - k0 - 64) x 64] pairs of the solved panel.  A
+// non-positive pivot sets ST_NOT_SPD and status[1] = column.
+dngd_status chol_step_df(int m, int k0, double* A, long long lda, float2* Ldf, float2* rdf, float2* P, int* status,
+                         cudaStream_t st);
+// The first 64 columns of that step's trailing update (rows and columns from
+// r0 = k0 + 64 on, lower triangle), from the panel pairs P.
+dngd_status strip_update_df(int m, int r0, const float2* P, double* C, long long ldc, const int* status,
+                            cudaStream_t st);
 dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const double* Dinv, const double* b, double* x,
                                 double* w, double* y, cudaStream_t st);
 
@@ -169,7 +176,8 @@ dngd_status gram_oz_plan(OzPlan** plan, const void* J, bool j64, int ng, long lo
                          cudaStream_t st);
 dngd_status gram_oz_read(const OzPlan* plan, double* out, cudaStream_t st);  // F as FP64 [m x ldf]
 dngd_status gram_oz_set_shift(OzPlan* plan, double shift);
-dngd_status gram_oz_run(OzPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
+dngd_status gram_oz_run(OzPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_before_mma,
+                        cudaEvent_t ev_after_mma);
 // Per-row largest |J| (float bits) that the writer of J fills for the slicing
 // (jets_backward_jacobian's rowmax); gram_oz_run reads it.
 unsigned* gram_oz_rowmax(OzPlan* plan);
@@ -333,7 +341,8 @@ struct GramPlan;
 // stream).
 dngd_status gram_tc_plan(GramPlan** plan, int kind, const void* Jlow, int m, int n, long long ld, float* K,
                          long long ldk, float* partials, size_t partial_bytes, cudaStream_t st);
-dngd_status gram_tc_run(GramPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_after_mma);
+dngd_status gram_tc_run(GramPlan* plan, int* status, cudaStream_t st, cudaEvent_t ev_before_mma,
+                        cudaEvent_t ev_after_mma);
 void gram_tc_free(GramPlan* plan);
 size_t gram_tc_partial_bytes(int m, int n);
 

@@ -57,7 +57,7 @@ class StepInfo(C.Structure):
                 ("ga_accepted", C.c_int), ("solve_iters", C.c_int * 2), ("solve_relres", C.c_double * 2),
                 ("not_spd_column", C.c_int), ("device_status", C.c_int), ("phase_ms", C.c_float * 8),
                 ("shift_used", C.c_double), ("factor_attempts", C.c_int), ("jt_ms", C.c_float),
-                ("j_ms", C.c_float), ("lambda_used", C.c_double)]
+                ("j_ms", C.c_float), ("lambda_used", C.c_double), ("gram_kernel_ms", C.c_float)]
 
     def as_dict(self):
         return dict(loss=self.loss, norm_v=self.norm_v, norm_a=self.norm_a, ga_ratio=self.ga_ratio,
@@ -65,7 +65,7 @@ class StepInfo(C.Structure):
                     solve_relres=list(self.solve_relres), not_spd_column=self.not_spd_column,
                     device_status=self.device_status, phase_ms=list(self.phase_ms),
                     shift_used=self.shift_used, factor_attempts=self.factor_attempts, jt_ms=self.jt_ms,
-                    j_ms=self.j_ms, lambda_used=self.lambda_used)
+                    j_ms=self.j_ms, lambda_used=self.lambda_used, gram_kernel_ms=self.gram_kernel_ms)
 
 
 class ServerCfg(C.Structure):

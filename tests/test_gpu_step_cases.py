@@ -128,6 +128,8 @@ def _oz_case(dngd, wl, sample=None, seed=0, prec="MIXED_OZ", step_tol=1e-4):
     m, n = ctx.m, ctx.n
     K = torch.zeros(m, m, dtype=torch.float64, device=DEV)
     ctx.get_stage("gram64", K)
+    L = torch.zeros(m, m, dtype=torch.float64, device=DEV)
+    ctx.get_stage("chol64", L)
     J32 = torch.zeros(m, n, dtype=torch.float64, device=DEV)
     ctx.residual_jacobian(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]),
                           torch.zeros(m, dtype=torch.float64, device=DEV), J32)
@@ -162,6 +164,18 @@ def _oz_case(dngd, wl, sample=None, seed=0, prec="MIXED_OZ", step_tol=1e-4):
         assert rel(Jr, ref["J"][rows]) <= j_tol
         del Jall
     assert max(info["solve_relres"]) <= 1e-10, info
+    # the factor (double-float diagonal blocks and panels, sliced trailing
+    # updates; read with the Gram, before the Jacobian call ends the step's
+    # state): L L^T against the matrix it factors, K + (lambda + mu) I,
+    # normwise on all rows or on the sampled ones (a backward error, so it
+    # does not depend on K's condition number)
+    Lh = L.cpu().numpy()
+    assert np.all(np.triu(Lh, 1) == 0) and np.all(np.diag(Lh) > 0)
+    sh = wl["lam"] + info["shift_used"]
+    rows_f = np.arange(m) if sample is None else np.sort(np.random.default_rng(seed + 1).choice(m, 64, False))
+    LLt = Lh[rows_f] @ Lh.T
+    Ks = Kh[rows_f] + sh * np.eye(m)[rows_f]
+    assert rel(LLt, Ks) <= 1e-11, rel(LLt, Ks)
     lb = layer_blocks(wl["widths"])
     cb = class_blocks(wl["classes"])
     check("delta", delta, ref["delta"], step_tol, lb)
