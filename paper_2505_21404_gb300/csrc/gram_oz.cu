@@ -579,12 +579,16 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       // row by row (lane = column), coalesced
       asm volatile("cp.async.wait_all;" ::: "memory");
       __syncwarp();
+      // row exponent per lane; the 32 column exponents loaded once (lane =
+      // column) and broadcast
       const int er = row < m ? epi.rexpA[row_off + row] : 0;
+      const int ecl = (lane < ncol && col0 + lane < m) ? epi.rexpA[row_off + col0 + lane] : 0;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int cj = col0 + j;
+        const int ec = __shfl_sync(0xffffffffu, ecl, j);
         if (j < ncol && row < m && cj <= row)
-          cs[lane * 33 + j] -= scale_pow2(df_to_double_bits(hi[j], lo[j]), er + epi.rexpA[row_off + cj] - epi.eshift);
+          cs[lane * 33 + j] -= scale_pow2(df_to_double_bits(hi[j], lo[j]), er + ec - epi.eshift);
       }
       __syncwarp();
       if (!*abort_flag && lane < ncol) {
@@ -596,15 +600,34 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
       }
     } else if (MODE == OZ_GEMM) {
-      if (row < m && !*abort_flag) {
-        const int er = epi.rexpA[row];
-        double* crow = epi.C + (long long)row * epi.ldc + col0;
+      // the tile, scaled by alpha 2^(EA_row + EB_col - eshift), goes through
+      // shared memory (the operand ring is idle: every MMA has completed)
+      // and is written row by row (lane = column), coalesced
+      constexpr int TS = CPW + 1;
+      static_assert(MODE != OZ_GEMM || EPI * 32 * TS * (int)sizeof(double) <= OST * OSTAGE,
+                    "the GEMM epilogue stages its sub-tiles in the operand ring");
+      double* tb = reinterpret_cast<double*>(smem_raw + (smem_base - smem_u32(smem_raw))) + (warp - 2) * 32 * TS;
+      const int er = row < m ? epi.rexpA[row] : 0;
+      const int eb0 = (lane < CPW && col0 + lane < epi.ncols) ? epi.rexpB[col0 + lane] : 0;
+      const int eb1 = (lane + 32 < CPW && col0 + lane + 32 < epi.ncols) ? epi.rexpB[col0 + lane + 32] : 0;
 #pragma unroll
-        for (int j = 0; j < CPW; ++j)
-          if (col0 + j < epi.ncols) {
-            const double v = epi.alpha * ldexp(df_to_double_bits(hi[j], lo[j]), er + epi.rexpB[col0 + j] - epi.eshift);
-            crow[j] = epi.beta == 0.0 ? v : v + epi.beta * crow[j];
-          }
+      for (int j = 0; j < CPW; ++j) {
+        const int eb = __shfl_sync(0xffffffffu, j < 32 ? eb0 : eb1, j & 31);
+        tb[lane * TS + j] = epi.alpha * scale_pow2(df_to_double_bits(hi[j], lo[j]), er + eb - epi.eshift);
+      }
+      __syncwarp();
+      if (!*abort_flag) {
+        for (int rr = 0; rr < 32; ++rr) {
+          const int rw = tile.x * TM + q * 32 + rr;
+          if (rw >= m) break;
+          double* crow = epi.C + (long long)rw * epi.ldc + col0;
+#pragma unroll
+          for (int j = lane; j < CPW; j += 32)
+            if (col0 + j < epi.ncols) {
+              const double v = tb[rr * TS + j];
+              crow[j] = epi.beta == 0.0 ? v : v + epi.beta * crow[j];
+            }
+        }
       }
     } else if (row < m && !*abort_flag) {
       double* orow = out + (long long)split * split_stride + (long long)row * ldo + col0;
@@ -922,32 +945,266 @@ constexpr int FNS = 6, FNG = 7;                       // six slices, levels <= 6
 constexpr int FNB = 64;                               // columns per step (the K extent of an update)
 constexpr int FLD = FNS * FNB;                        // slice row: 6 x 64 BF16
 
-// Rows i in [row0, m): the panel C[i, k0 .. k0 + kb) as six 8-bit slices of
-// 64 columns (zero beyond kb) and the row exponent E_i (|C| / 2^E_i < 0.5,
-// entries kept to 2^(E_i - 49)).  One warp per row.
-__global__ void __launch_bounds__(256) k_panel_slice(int m, int row0, int k0, int kb, const double* __restrict__ C,
-                                                     long long ldc, __nv_bfloat16* __restrict__ S,
-                                                     int* __restrict__ rowexp, const int* __restrict__ status) {
-  if (status[0] & ST_NOT_SPD) return;   // the factorisation already failed
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = row0 + blockIdx.x * 8 + warp;
-  if (row >= m) return;
-  const double* cr = C + (long long)row * ldc + k0;
-  const double x0 = lane < kb ? cr[lane] : 0.0;
-  const double x1 = lane + 32 < kb ? cr[lane + 32] : 0.0;
-  long long a = max(abs_bits(x0), abs_bits(x1));
-  for (int o = 16; o > 0; o >>= 1) a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
-  // a non-finite entry (a failed factorisation upstream) slices as zero
-  const int E = a >= 0x7FF0000000000000LL ? 1 : exp_of_abs_bits(a);
-  if (lane == 0) rowexp[row] = E;
-  float d0[FNS], d1[FNS];
-  oz_digits<FNS>(a >= 0x7FF0000000000000LL ? 0.0 : x0, E, d0);
-  oz_digits<FNS>(a >= 0x7FF0000000000000LL ? 0.0 : x1, E, d1);
-  __nv_bfloat16* sr = S + (long long)row * FLD;
+// The factorisation's 64-column steps compute in double-float arithmetic
+// (hi + lo FP32 pairs, ~2^-47 per operation) on the FP32 pipes: GB300's FP64
+// pipe retires 2 FMA per clock per SM, and these kernels are the latency
+// chain of the factorisation.  The factor preconditions a refinement against
+// the exact Gram and is rounded to FP32 afterwards, so the pairs keep far
+// more than it needs even at cond(K + lambda I) ~ 1e10.  The matrix itself
+// stays FP64: operands are read from it and results rounded once into it.
+
+// Entry e of the column-major numbering of a 64 x 64 lower triangle
+// (column c starts at c (129 - c) / 2 and holds rows c .. 63).
+__device__ __forceinline__ void tri64_entry(int e, int& i, int& c) {
+  int cc = (int)((129.0f - sqrtf((float)(16641 - 8 * e))) * 0.5f);
+  cc = max(0, min(63, cc));
+  while (cc < 63 && (cc + 1) * (129 - (cc + 1)) / 2 <= e) ++cc;
+  while (cc > 0 && cc * (129 - cc) / 2 > e) --cc;
+  c = cc;
+  i = cc + (e - cc * (129 - cc) / 2);
+}
+
+// Diagonal block A[k0 .. k0 + kb)^2 = L L^T (kb <= 64; rows beyond kb are
+// padded with the identity).  Right-looking with one barrier per column:
+// thread t keeps the entries e = t + 512 q of the lower triangle in
+// registers; at step j every thread updates its entries (i, c), c > j, by
+// a_ic -= a_ij a_cj / d_j from the unscaled column j, which sits in a
+// shared double buffer (the owners of column j + 1 publish it as soon as
+// their update makes it final).  A warp skips a slot whose 32 entries are
+// all finished (they run through the triangle column by column).  At the
+// end L_ic = a_ic / sqrt(d_c).  Outputs: L in A (FP64), L's strictly lower
+// part as pairs in Ldf[64][64], the pivots' reciprocal square roots in
+// rdf[64].  A pivot that is not positive sets ST_NOT_SPD with its column
+// (status[1]).
+constexpr int kDiagThreads = 512;
+__global__ void __launch_bounds__(kDiagThreads) k_potrf_diag_df(int k0, int kb, double* A, long long lda,
+                                                                float2* __restrict__ Ldf, float2* __restrict__ rdf,
+                                                                int* status) {
+  constexpr int NB = FNB, NE = NB * (NB + 1) / 2, Q = (NE + kDiagThreads - 1) / kDiagThreads;
+  static_assert(NB == 64, "the triangle numbering assumes 64 columns");
+  __shared__ float2 col[2][NB];
+  __shared__ float2 rs[NB];
+  const int tid = threadIdx.x;
+  int ri[Q], ci[Q];
+  double a0[Q];
 #pragma unroll
-  for (int s = 0; s < FNS; ++s) {
-    sr[s * FNB + lane] = __float2bfloat16_rn(d0[s]);
-    sr[s * FNB + lane + 32] = __float2bfloat16_rn(d1[s]);
+  for (int q = 0; q < Q; ++q) {
+    const int e = tid + kDiagThreads * q;
+    ri[q] = 0;    // a slot past the triangle: never updated, published or stored
+    ci[q] = -1;
+    if (e < NE) tri64_entry(e, ri[q], ci[q]);
+    a0[q] = (ci[q] >= 0 && ri[q] < kb) ? A[(long long)(k0 + ri[q]) * lda + k0 + ci[q]] : 0.0;
+  }
+  dfloat v[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    v[q] = ri[q] < kb ? df_from_double(a0[q]) : dfloat{ri[q] == ci[q] ? 1.f : 0.f, 0.f};
+    if (ci[q] == 0) col[0][ri[q]] = make_float2(v[q].hi, v[q].lo);
+  }
+  __syncthreads();
+  int bad = -1;
+  for (int j = 0; j < NB; ++j) {
+    const float2 dj = col[j & 1][j];
+    if (!(dj.x > 0.f && dj.x < 3.0e38f)) {   // the same decision in every thread
+      bad = j;
+      break;
+    }
+    const dfloat inv = df_rcp({dj.x, dj.y});
+    const float2* cj = col[j & 1];
+    float2* cn = col[(j + 1) & 1];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if (__any_sync(0xffffffffu, ci[q] > j)) {
+        const bool act = ci[q] > j;
+        const float2 aij = cj[ri[q]], acj = cj[act ? ci[q] : 0];
+        const dfloat nv = df_sub_mul(v[q], df_mul({aij.x, aij.y}, inv), {acj.x, acj.y});
+        if (act) v[q] = nv;
+        if (ci[q] == j + 1) cn[ri[q]] = make_float2(v[q].hi, v[q].lo);
+      }
+    }
+    __syncthreads();
+  }
+  if (bad >= 0) {
+    if (bad < kb && tid == 0) {
+      const int old = atomicOr(status, ST_NOT_SPD);
+      if (!(old & ST_NOT_SPD)) status[1] = k0 + bad;
+    }
+    return;
+  }
+  // r_c = 1 / sqrt(d_c) from the final diagonal entries
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    if (ri[q] == ci[q]) {
+      const dfloat r = df_rsqrt(v[q]);
+      rs[ri[q]] = make_float2(r.hi, r.lo);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = ri[q], c = ci[q];
+    if (c < 0 || i >= kb) continue;
+    const float2 r = rs[c];
+    const dfloat l = df_mul(v[q], {r.x, r.y});
+    A[(long long)(k0 + i) * lda + k0 + c] = df_to_double_bits(l.hi, l.lo);
+    Ldf[i * NB + c] = i > c ? make_float2(l.hi, l.lo) : make_float2(0.f, 0.f);
+  }
+  // entries above the diagonal of Ldf and rows beyond kb are zero
+  for (int e = tid; e < NB * NB; e += kDiagThreads) {
+    const int i = e >> 6, c = e & (NB - 1);
+    if (c > i || i >= kb) Ldf[e] = make_float2(0.f, 0.f);
+  }
+  if (tid < NB) rdf[tid] = tid < kb ? rs[tid] : make_float2(0.f, 0.f);
+}
+
+// Panel rows g in [k0 + kb, m): X L11^T = A_panel by forward substitution,
+// x_j = (a_j - sum_{i<j} x_i L_ji) r_j, then the row's exponent and six
+// 8-bit slices for the sliced trailing update.  A CTA takes 16 rows with 128
+// threads, eight per row: thread (row, q) keeps columns q + 8 t of its row
+// as pairs in registers; once x_j is final its owner scales it and a
+// width-8 shuffle hands it to the row's other threads.  Outputs: the solved
+// panel in A (FP64) and as pairs in P[(g - k0 - kb) * 64 + j] (for the
+// first 64 columns of the update), and slices S[g] (FLD BF16 per row, zero
+// beyond kb) with exponents rowexp[g] (|x| / 2^E < 0.5, entries kept to
+// 2^(E - 49)).
+constexpr int kPanelRows = 16;
+__global__ void __launch_bounds__(128) k_trsm_panel_df(int m, int k0, int kb, double* A, long long lda,
+                                                       const float2* __restrict__ Ldf,
+                                                       const float2* __restrict__ rdf, float2* __restrict__ P,
+                                                       __nv_bfloat16* __restrict__ Sl, int* __restrict__ rowexp,
+                                                       const int* status) {
+  if (status[0] & ST_NOT_SPD) return;
+  constexpr int NB = FNB;
+  __shared__ float2 Lsh[NB][NB + 1];
+  __shared__ float2 rc[NB];
+  const int tid = threadIdx.x;
+  {
+    float2 lv[NB * NB / 128];   // every load in flight before the first store
+#pragma unroll
+    for (int u = 0; u < NB * NB / 128; ++u) lv[u] = Ldf[tid + 128 * u];
+#pragma unroll
+    for (int u = 0; u < NB * NB / 128; ++u) Lsh[(tid + 128 * u) >> 6][(tid + 128 * u) & (NB - 1)] = lv[u];
+  }
+  if (tid < NB) rc[tid] = rdf[tid];
+  const int q = tid & 7;
+  const long long row = (long long)blockIdx.x * kPanelRows + (tid >> 3);
+  const long long g = (long long)k0 + kb + row;
+  const bool live = g < m;
+  dfloat x[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int j = q + 8 * t;
+    x[t] = (live && j < kb) ? df_from_double(A[g * lda + k0 + j]) : dfloat{0.f, 0.f};
+  }
+  __syncthreads();
+  const int base = (tid & 31) & ~7;
+  // column j = 8 t + o: the register slot t is unrolled, the owner o is a
+  // loop (a fully unrolled solve outgrows the instruction cache)
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+#pragma unroll 1
+    for (int o = 0; o < 8; ++o) {
+      const int j = 8 * t + o;
+      dfloat xj = {0.f, 0.f};
+      if (q == o) {
+        x[t] = df_mul(x[t], {rc[j].x, rc[j].y});
+        xj = x[t];
+      }
+      xj.hi = __shfl_sync(0xffffffffu, xj.hi, base + o);
+      xj.lo = __shfl_sync(0xffffffffu, xj.lo, base + o);
+      if (q > o) x[t] = df_sub_mul(x[t], xj, {Lsh[q + 8 * t][j].x, Lsh[q + 8 * t][j].y});
+#pragma unroll
+      for (int u = t + 1; u < 8; ++u) x[u] = df_sub_mul(x[u], xj, {Lsh[q + 8 * u][j].x, Lsh[q + 8 * u][j].y});
+    }
+  }
+  double xd[8];
+  long long amax = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    xd[t] = (live && q + 8 * t < kb) ? df_to_double_bits(x[t].hi, x[t].lo) : 0.0;
+    amax = max(amax, abs_bits(xd[t]));
+  }
+  for (int o = 4; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o, 8));
+  if (!live) return;
+  // a non-finite entry (a failed factorisation upstream) slices as zero
+  const bool bad = amax >= 0x7FF0000000000000LL;
+  const int E = bad ? 1 : exp_of_abs_bits(amax);
+  if (q == 0) rowexp[g] = E;
+  __nv_bfloat16* sr = Sl + g * FLD;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int j = q + 8 * t;
+    if (j < kb) A[g * lda + k0 + j] = xd[t];
+    P[row * NB + j] = j < kb ? make_float2(x[t].hi, x[t].lo) : make_float2(0.f, 0.f);
+    float d[FNS];
+    oz_digits<FNS>(bad ? 0.0 : xd[t], E, d);
+#pragma unroll
+    for (int s = 0; s < FNS; ++s) sr[s * FNB + j] = __float2bfloat16_rn(d[s]);
+  }
+}
+
+// The trailing update's first 64 columns (the next diagonal block and
+// panel): C[r0 + i, r0 + c] -= sum_t P_i,t P_c,t for rows i < r, columns
+// c < min(64, r), c <= i, r0 = k0 + kb, from the solved panel's pairs P
+// (row-major, 64 per row).  A CTA takes 16 rows x 64 columns with 256
+// threads, each one row x 4 columns (columns tx + 16 u), the sums in
+// double-float; the result is rounded once into the FP64 entry.
+constexpr int kStripRows = 16;
+__global__ void __launch_bounds__(256) k_strip_update_df(int m, int r0, const float2* __restrict__ P, double* C,
+                                                         long long ldc, const int* status) {
+  if (status[0] & ST_NOT_SPD) return;
+  constexpr int NB = FNB;
+  __shared__ float2 Pt[NB][NB + 1];            // the first 64 panel rows (the strip's columns)
+  __shared__ float2 Pr[kStripRows][NB + 1];    // this CTA's rows
+  const int tid = threadIdx.x, r = m - r0, nc = min(NB, r);
+  const int i0 = blockIdx.x * kStripRows;
+  {
+    // every load in flight before the first store
+    float2 pv[NB * NB / 256], rv[kStripRows * NB / 256];
+#pragma unroll
+    for (int u = 0; u < NB * NB / 256; ++u) {
+      const int e = tid + 256 * u;
+      pv[u] = (e >> 6) < nc ? P[e] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kStripRows * NB / 256; ++u) {
+      const int e = tid + 256 * u;
+      rv[u] = i0 + (e >> 6) < r ? P[(long long)i0 * NB + e] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < NB * NB / 256; ++u) Pt[(tid + 256 * u) >> 6][(tid + 256 * u) & (NB - 1)] = pv[u];
+#pragma unroll
+    for (int u = 0; u < kStripRows * NB / 256; ++u) Pr[(tid + 256 * u) >> 6][(tid + 256 * u) & (NB - 1)] = rv[u];
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;   // row ty; columns tx + 16 u
+  dfloat s[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) s[u] = {0.f, 0.f};
+#pragma unroll 4
+  for (int t = 0; t < NB; ++t) {
+    const float2 pa = Pr[ty][t];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 pb = Pt[tx + 16 * u][t];
+      // s += pa pb, the low part accumulated without renormalising
+      const float p = pa.x * pb.x;
+      const float e = fmaf(pa.x, pb.y, fmaf(pa.y, pb.x, fmaf(pa.x, pb.x, -p)));
+      float h, gq;
+      two_sum(s[u].hi, p, h, gq);
+      s[u].hi = h;
+      s[u].lo += gq + e;
+    }
+  }
+  const int i = i0 + ty;
+  if (i >= r) return;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = tx + 16 * u;
+    if (c >= nc || c > i) continue;
+    const float hi = s[u].hi + s[u].lo;
+    const float lo = s[u].lo - (hi - s[u].hi);
+    C[(long long)(r0 + i) * ldc + r0 + c] -= df_to_double_bits(hi, lo);
   }
 }
 
@@ -1057,20 +1314,19 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
   DNGD_CUDA_CHECK(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
   bool rest_pending = false;
   for (int k0 = 0, step = 0; k0 < m; k0 += FNB, ++step) {
-    // diagonal block and panel (double-float): after the previous step's
-    // first 64 columns of its update, which the stream order gives
-    dngd_status s = chol_step_df(m, k0, p->C, p->ldc, p->Ldf, p->rdf, p->Pdf, status, st);
-    if (s) {
-      cudaEventRecord(p->ev_rest, p->side);   // join the side stream before leaving
-      cudaStreamWaitEvent(st, p->ev_rest, 0);
-      return s;
-    }
+    // diagonal block, panel solve and slicing (double-float): after the
+    // previous step's first 64 columns of its update, which the stream order
+    // gives
     const int kb = (m - k0) < FNB ? (m - k0) : FNB;
     const int row0 = k0 + kb, r = m - row0;
-    if (r <= 0) break;
     const int b = step & 1;
     DNGD_NOTE_LAUNCH();
-    k_panel_slice<<<(r + 7) / 8, 256, 0, st>>>(m, row0, k0, kb, p->C, p->ldc, p->S[b], p->rowexp[b], status);
+    k_potrf_diag_df<<<1, kDiagThreads, 0, st>>>(k0, kb, p->C, p->ldc, p->Ldf, p->rdf, status);
+    DNGD_LAUNCH_CHECK();
+    if (r <= 0) break;
+    DNGD_NOTE_LAUNCH();
+    k_trsm_panel_df<<<cdiv(r, kPanelRows), 128, 0, st>>>(m, k0, kb, p->C, p->ldc, p->Ldf, p->rdf, p->Pdf, p->S[b],
+                                                        p->rowexp[b], status);
     DNGD_LAUNCH_CHECK();
     DNGD_CUDA_CHECK(cudaEventRecord(p->ev_slice, st));
     const OzEpi upd{p->C, p->ldc, p->rowexp[b], nullptr, 16 + 8 * (FNG - 1), 0, 0, 0.0, 0.0};
@@ -1078,12 +1334,9 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
     // the first 64 columns (double-float, from the panel's pairs) also wait
     // for the previous step's rest, which updated the same columns
     if (rest_pending) DNGD_CUDA_CHECK(cudaStreamWaitEvent(st, p->ev_rest, 0));
-    s = strip_update_df(m, row0, p->Pdf, p->C, p->ldc, status, st);
-    if (s) {
-      cudaEventRecord(p->ev_rest, p->side);
-      cudaStreamWaitEvent(st, p->ev_rest, 0);
-      return s;
-    }
+    DNGD_NOTE_LAUNCH();
+    k_strip_update_df<<<cdiv(r, kStripRows), 256, 0, st>>>(m, row0, p->Pdf, p->C, p->ldc, status);
+    DNGD_LAUNCH_CHECK();
     const int nrest = p->rest_prefix[nIr];
     DNGD_CUDA_CHECK(cudaStreamWaitEvent(p->side, p->ev_slice, 0));
     if (nrest > 0) {

@@ -101,17 +101,6 @@ dngd_status factor_to_f32(int m, const double* L, long long ldl, const double* D
 // bottom-up; the large nodes (k0, n1, n2) are returned bottom-up.
 dngd_status trtri_small_nodes_f32(int m, const float* L, long long ldl, float* Linv, long long ldi, float* work,
                                   cudaStream_t st, std::vector<int3>* large_out);
-// One 64-column step of the blocked Cholesky of an FP64 matrix in
-// double-float arithmetic (diagonal block at k0 and the panel solve below
-// it; no trailing update).  Scratch: Ldf [64 x 64] and rdf [64] pairs of the
-// block's factor, P [(m - k0 - 64) x 64] pairs of the solved panel.  A
-// non-positive pivot sets ST_NOT_SPD and status[1] = column.
-dngd_status chol_step_df(int m, int k0, double* A, long long lda, float2* Ldf, float2* rdf, float2* P, int* status,
-                         cudaStream_t st);
-// The first 64 columns of that step's trailing update (rows and columns from
-// r0 = k0 + 64 on, lower triangle), from the panel pairs P.
-dngd_status strip_update_df(int m, int r0, const float2* P, double* C, long long ldc, const int* status,
-                            cudaStream_t st);
 dngd_status chol_solve_f64_dinv(int m, const double* L, long long ldl, const double* Dinv, const double* b, double* x,
                                 double* w, double* y, cudaStream_t st);
 

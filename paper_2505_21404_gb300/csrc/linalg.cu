@@ -340,269 +340,6 @@ dngd_status cholesky(int m, TA* A, long long lda, int* status, double* work, cud
 
 template dngd_status cholesky<double>(int, double*, long long, int*, double*, cudaStream_t);
 
-// One 64-column step of the factorisation of the exact-Gram modes, in
-// double-float arithmetic (hi + lo FP32 pairs, ~2^-47 relative) on the FP32
-// pipes: GB300's FP64 pipe retires 2 FMA per clock per SM, so FP64 kernels
-// of this size are bound by it and by the latency of its long dependency
-// chains.  The factor is the preconditioner of a refinement against the
-// exact Gram, and it is rounded to FP32 afterwards; the pairs keep ~2^-47
-// of each entry, well beyond what that needs even at cond(K + lambda I) ~ 1e10.
-// Operands are read from and results written to the FP64 matrix.
-
-// Entry e of the column-major numbering of a 64 x 64 lower triangle
-// (column c starts at c (129 - c) / 2 and holds rows c .. 63).
-__device__ __forceinline__ void tri64_entry(int e, int& i, int& c) {
-  int cc = (int)((129.0f - sqrtf((float)(16641 - 8 * e))) * 0.5f);
-  cc = max(0, min(63, cc));
-  while (cc < 63 && (cc + 1) * (129 - (cc + 1)) / 2 <= e) ++cc;
-  while (cc > 0 && cc * (129 - cc) / 2 > e) --cc;
-  c = cc;
-  i = cc + (e - cc * (129 - cc) / 2);
-}
-
-// Diagonal block A[k0 .. k0 + kb)^2 = L L^T (kb <= 64; rows beyond kb are
-// padded with the identity).  Right-looking with one barrier per column:
-// thread t keeps the entries e = t + 256 q of the lower triangle in
-// registers; at step j every thread updates its entries (i, c), c > j, by
-// a_ic -= a_ij a_cj / d_j from the unscaled column j, which sits in a
-// shared double buffer (the owners of column j + 1 publish it as soon as
-// their update makes it final).  At the end L_ic = a_ic / sqrt(d_c).
-// Outputs: L in A (FP64), L's strictly lower part as pairs in Ldf[64][64],
-// the pivots' reciprocal square roots in rdf[64].  A pivot that is not
-// positive sets ST_NOT_SPD with its column (status[1]).
-__global__ void __launch_bounds__(256) k_potrf_diag_df(int k0, int kb, double* A, long long lda,
-                                                       float2* __restrict__ Ldf, float2* __restrict__ rdf,
-                                                       int* status) {
-  constexpr int NB = kCholNB, NE = NB * (NB + 1) / 2, Q = (NE + 255) / 256;
-  static_assert(NB == 64 && Q % 3 == 0, "the triangle numbering assumes 64 columns, nine slots a thread");
-  __shared__ float2 col[2][NB];
-  __shared__ float2 rs[NB];
-  const int tid = threadIdx.x;
-  int ri[Q], ci[Q];
-  dfloat v[Q];
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int e = tid + 256 * q;
-    ri[q] = 0;    // a slot past the triangle: never updated, published or stored
-    ci[q] = -1;
-    v[q] = {0.f, 0.f};
-    if (e < NE) {
-      int i, c;
-      tri64_entry(e, i, c);
-      ri[q] = i;
-      ci[q] = c;
-      if (i < kb) v[q] = df_from_double(A[(long long)(k0 + i) * lda + k0 + c]);
-      else if (i == c) v[q] = {1.f, 0.f};
-      if (c == 0) col[0][i] = make_float2(v[q].hi, v[q].lo);
-    }
-  }
-  __syncthreads();
-  int bad = -1;
-  for (int j = 0; j < NB; ++j) {
-    const float2 dj = col[j & 1][j];
-    if (!(dj.x > 0.f && dj.x < 3.0e38f)) {   // the same decision in every thread
-      bad = j;
-      break;
-    }
-    const dfloat inv = df_rcp({dj.x, dj.y});
-    const float2* cj = col[j & 1];
-    float2* cn = col[(j + 1) & 1];
-    // slots in groups of three: a group whose entries are all finished in
-    // the whole warp is skipped (a thread's slots run through the triangle
-    // column by column, so its finished slots are a prefix); inside a group
-    // the three updates are predicated, so their chains interleave
-#pragma unroll
-    for (int g = 0; g < Q; g += 3) {
-      if (__any_sync(0xffffffffu, ci[g] > j || ci[g + 1] > j || ci[g + 2] > j)) {
-#pragma unroll
-        for (int q = g; q < g + 3; ++q) {
-          const bool act = ci[q] > j;
-          const float2 aij = cj[ri[q]], acj = cj[act ? ci[q] : 0];
-          const dfloat nv = df_sub_mul(v[q], df_mul({aij.x, aij.y}, inv), {acj.x, acj.y});
-          if (act) v[q] = nv;
-          if (ci[q] == j + 1) cn[ri[q]] = make_float2(v[q].hi, v[q].lo);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (bad >= 0) {
-    if (bad < kb && tid == 0) {
-      const int old = atomicOr(status, ST_NOT_SPD);
-      if (!(old & ST_NOT_SPD)) status[1] = k0 + bad;
-    }
-    return;
-  }
-  // r_c = 1 / sqrt(d_c) from the final diagonal entries
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    if (ri[q] == ci[q]) {
-      const dfloat r = df_rsqrt(v[q]);
-      rs[ri[q]] = make_float2(r.hi, r.lo);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int i = ri[q], c = ci[q];
-    if (c < 0 || i >= kb) continue;
-    const float2 r = rs[c];
-    const dfloat l = df_mul(v[q], {r.x, r.y});
-    A[(long long)(k0 + i) * lda + k0 + c] = df_to_double_bits(l.hi, l.lo);
-    Ldf[i * NB + c] = i > c ? make_float2(l.hi, l.lo) : make_float2(0.f, 0.f);
-  }
-  // entries above the diagonal of Ldf and rows beyond kb are zero
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int i = e >> 6, c = e & (NB - 1);
-    if (c > i || i >= kb) Ldf[e] = make_float2(0.f, 0.f);
-  }
-  if (tid < NB) rdf[tid] = tid < kb ? rs[tid] : make_float2(0.f, 0.f);
-}
-
-// Panel rows g in [k0 + kb, m): X L11^T = A_panel by forward substitution,
-// x_j = (a_j - sum_{i<j} x_i L_ji) r_j.  A CTA takes 16 rows with 128
-// threads, eight per row: thread (row, q) keeps columns q + 8 t of its row
-// as pairs in registers; once x_j is final its owner scales it and a
-// width-8 shuffle hands it to the row's other threads.  The solved panel
-// goes to A (FP64) and, as pairs, to P[(g - k0 - kb) * 64 + j] for the
-// strip update.
-constexpr int kPanelRowsDf = 16;
-__global__ void __launch_bounds__(128) k_trsm_panel_df(int m, int k0, int kb, double* A, long long lda,
-                                                       const float2* __restrict__ Ldf,
-                                                       const float2* __restrict__ rdf, float2* __restrict__ P,
-                                                       const int* status) {
-  if (status[0] & ST_NOT_SPD) return;
-  constexpr int NB = kCholNB;
-  __shared__ float2 Lsh[NB][NB + 1];
-  __shared__ float2 rc[NB];
-  const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += 128) Lsh[e >> 6][e & (NB - 1)] = Ldf[e];
-  if (tid < NB) rc[tid] = rdf[tid];
-  const int q = tid & 7;
-  const long long row = (long long)blockIdx.x * kPanelRowsDf + (tid >> 3);
-  const long long g = (long long)k0 + kb + row;
-  const bool live = g < m;
-  dfloat x[8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const int j = q + 8 * t;
-    x[t] = (live && j < kb) ? df_from_double(A[g * lda + k0 + j]) : dfloat{0.f, 0.f};
-  }
-  __syncthreads();
-  const int base = (tid & 31) & ~7;
-  // column j = 8 t + o: the register slot t is unrolled, the owner o is a
-  // loop (a fully unrolled solve outgrows the instruction cache)
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-#pragma unroll 1
-    for (int o = 0; o < 8; ++o) {
-      const int j = 8 * t + o;
-      dfloat xj = {0.f, 0.f};
-      if (q == o) {
-        x[t] = df_mul(x[t], {rc[j].x, rc[j].y});
-        xj = x[t];
-      }
-      xj.hi = __shfl_sync(0xffffffffu, xj.hi, base + o);
-      xj.lo = __shfl_sync(0xffffffffu, xj.lo, base + o);
-      if (q > o) x[t] = df_sub_mul(x[t], xj, {Lsh[q + 8 * t][j].x, Lsh[q + 8 * t][j].y});
-#pragma unroll
-      for (int u = t + 1; u < 8; ++u) x[u] = df_sub_mul(x[u], xj, {Lsh[q + 8 * u][j].x, Lsh[q + 8 * u][j].y});
-    }
-  }
-  if (!live) return;
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const int j = q + 8 * t;
-    if (j < kb) A[g * lda + k0 + j] = df_to_double_bits(x[t].hi, x[t].lo);
-    P[row * NB + j] = j < kb ? make_float2(x[t].hi, x[t].lo) : make_float2(0.f, 0.f);
-  }
-}
-
-// The trailing update's first 64 columns (the next diagonal block and
-// panel): C[r0 + i, r0 + c] -= sum_t P_i,t P_c,t for rows i < r, columns
-// c < min(64, r), c <= i, r0 = k0 + kb, from the solved panel's pairs P
-// (row-major, 64 per row).  A CTA takes 16 rows x 64 columns with 256
-// threads, each one row x 4 columns (columns tx + 16 u), the sums in
-// double-float; the result is rounded once into the FP64 entry.
-constexpr int kStripRows = 16;
-__global__ void __launch_bounds__(256) k_strip_update_df(int m, int r0, const float2* __restrict__ P, double* C,
-                                                         long long ldc, const int* status) {
-  if (status[0] & ST_NOT_SPD) return;
-  constexpr int NB = kCholNB;
-  __shared__ float2 Pt[NB][NB + 1];            // the first 64 panel rows (the strip's columns)
-  __shared__ float2 Pr[kStripRows][NB + 1];    // this CTA's rows
-  const int tid = threadIdx.x, r = m - r0, nc = min(NB, r);
-  const int i0 = blockIdx.x * kStripRows;
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int c = e >> 6, t = e & (NB - 1);
-    Pt[c][t] = c < nc ? P[(long long)c * NB + t] : make_float2(0.f, 0.f);
-  }
-  for (int e = tid; e < kStripRows * NB; e += 256) {
-    const int i = e >> 6, t = e & (NB - 1);
-    Pr[i][t] = i0 + i < r ? P[(long long)(i0 + i) * NB + t] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  const int tx = tid & 15, ty = tid >> 4;   // row ty; columns tx + 16 u
-  dfloat s[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) s[u] = {0.f, 0.f};
-#pragma unroll 4
-  for (int t = 0; t < NB; ++t) {
-    const float2 pa = Pr[ty][t];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float2 pb = Pt[tx + 16 * u][t];
-      // s += pa pb, the low part accumulated without renormalising
-      const float p = pa.x * pb.x;
-      const float e = fmaf(pa.x, pb.y, fmaf(pa.y, pb.x, fmaf(pa.x, pb.x, -p)));
-      float h, g;
-      two_sum(s[u].hi, p, h, g);
-      s[u].hi = h;
-      s[u].lo += g + e;
-    }
-  }
-  const int i = i0 + ty;
-  if (i >= r) return;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int c = tx + 16 * u;
-    if (c >= nc || c > i) continue;
-    const float hi = s[u].hi + s[u].lo;
-    const float lo = s[u].lo - (hi - s[u].hi);
-    C[(long long)(r0 + i) * ldc + r0 + c] -= df_to_double_bits(hi, lo);
-  }
-}
-
-// One 64-column step without its trailing update: factor the diagonal block
-// at k0 and solve the panel below it (Ldf [64 x 64] and rdf [64] pair
-// scratch; P [(m - k0 - 64) x 64] pairs of the solved panel).
-dngd_status chol_step_df(int m, int k0, double* A, long long lda, float2* Ldf, float2* rdf, float2* P, int* status,
-                         cudaStream_t st) {
-  const int kb = (m - k0) < kCholNB ? (m - k0) : kCholNB;
-  DNGD_NOTE_LAUNCH();
-  k_potrf_diag_df<<<1, 256, 0, st>>>(k0, kb, A, lda, Ldf, rdf, status);
-  DNGD_LAUNCH_CHECK();
-  const int rest = m - k0 - kb;
-  if (rest > 0) {
-    DNGD_NOTE_LAUNCH();
-    k_trsm_panel_df<<<cdiv(rest, kPanelRowsDf), 128, 0, st>>>(m, k0, kb, A, lda, Ldf, rdf, P, status);
-    DNGD_LAUNCH_CHECK();
-  }
-  return DNGD_OK;
-}
-
-// The first 64 columns of the trailing update after chol_step_df (rows and
-// columns from r0 = k0 + 64 on).
-dngd_status strip_update_df(int m, int r0, const float2* P, double* C, long long ldc, const int* status,
-                            cudaStream_t st) {
-  const int r = m - r0;
-  if (r <= 0) return DNGD_OK;
-  DNGD_NOTE_LAUNCH();
-  k_strip_update_df<<<cdiv(r, kStripRows), 256, 0, st>>>(m, r0, P, C, ldc, status);
-  DNGD_LAUNCH_CHECK();
-  return DNGD_OK;
-}
-
 // ---------------------------------------------------------------------------
 // FP32 factorisation for the mixed path (a preconditioner, whose accuracy the
 // refinement restores).  One kernel factors a 64 x 64 diagonal block and
