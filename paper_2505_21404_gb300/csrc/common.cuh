@@ -106,14 +106,21 @@ __device__ __forceinline__ float tanh_t(float x) { return tanhf(x); }
 // double(hi + lo) for a normalised double-float pair (|lo| <= ulp(hi) / 2),
 // assembled with integer operations (hi's significand shifted to the top of
 // the 53 bits, lo's added or subtracted below it, at most one bit of
-// renormalisation); a zero, subnormal or non-finite hi or lo, or a pair that
-// is not normalised, takes the FP64 add.
+// renormalisation); a zero pair gives a signed zero; a subnormal or
+// non-finite hi or lo, or a pair that is not normalised, takes the FP64 add.
+// That fallback is a call, not inlined: inlined, the compiler may predicate
+// it into every use, and the float -> double conversions and the add then
+// occupy GB300's slow FP64 pipe for every value (measured: ~30k cycles for
+// 32 values a thread in the sliced update's epilogue).
+static __device__ __noinline__ double df_to_double_slow(float hi, float lo) { return (double)hi + (double)lo; }
+
 __device__ __forceinline__ double df_to_double_bits(float hi, float lo) {
   const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
   const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
   const bool lo_zero = (lb & 0x7FFFFFFFu) == 0u;
   const int k = 29 - (eh - el);
-  if (eh == 0 || eh == 0xFF || (!lo_zero && (el == 0 || el == 0xFF || k > 5))) return (double)hi + (double)lo;
+  if ((hb & 0x7FFFFFFFu) == 0u && lo_zero) return __longlong_as_double((long long)((unsigned long long)(hb >> 31) << 63));
+  if (eh == 0 || eh == 0xFF || (!lo_zero && (el == 0 || el == 0xFF || k > 5))) return df_to_double_slow(hi, lo);
   unsigned long long S = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
   if (!lo_zero) {
     unsigned long long Ml = (lb & 0x7FFFFFu) | 0x800000u;

@@ -228,12 +228,17 @@ __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
 // x 2^e: e added to the exponent field when x and the result are normal
 // (integer operations), else an FP64 multiply by 2^e with e clamped to the
 // normal range.
+// (the FP64 fallback is a call, so it is not predicated into every use)
+__device__ __noinline__ double scale_pow2_slow(double x, int e) {
+  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  return __longlong_as_double((long long)(e + 1023) << 52) * x;
+}
 __device__ __forceinline__ double scale_pow2(double x, int e) {
   const long long b = __double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FF);
   if (ex != 0 && ex != 0x7FF && ex + e >= 1 && ex + e <= 2046) return __longlong_as_double(b + ((long long)e << 52));
-  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-  return __longlong_as_double((long long)(e + 1023) << 52) * x;
+  if ((b & 0x7FFFFFFFFFFFFFFFLL) == 0) return x;   // a signed zero stays
+  return scale_pow2_slow(x, e);
 }
 
 // Weight 2^(-8 s) of slice s in the pre-scaled layout (exact in BF16 for the
@@ -365,13 +370,21 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  // OZ_UPDATE runs persistent: CTA b takes the tiles b, b + gridDim.x, ...
+  // of the epi.ncols listed, one after another; tile c is chunk c of every
+  // accumulator (its K extent is one chunk), so the MMA warp's chunk logic
+  // carries over unchanged and the next tile's operands load while the
+  // epilogue finishes the previous one
+  constexpr bool PERSIST = MODE == OZ_UPDATE;
+  const int my_tiles = PERSIST ? max(0, (epi.ncols - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x) : 1;
   const int2 tile = MODE == OZ_GEMM ? make_int2((int)blockIdx.x / epi.ntn, (int)blockIdx.x % epi.ntn)
                                     : tiles[blockIdx.x];
   const int split = blockIdx.y, nsplit = gridDim.y;
   const int kb_per = (num_kblk + nsplit - 1) / nsplit;
   const int kb0 = split * kb_per;
   const int kb1 = min(num_kblk, kb0 + kb_per);
-  const int nk = max(0, kb1 - kb0);
+  const int nk_tile = max(0, kb1 - kb0);
+  const int nk = nk_tile * my_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OST; ++s) {
@@ -410,11 +423,12 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const uint32_t fb = smem_u32(&full_bar[st]);
         mbar_expect_tx(fb, OSTAGE);
         const uint32_t sbase = smem_base + st * OSTAGE;
-        const int kc = (kb0 + it) * KS;
+        const int2 tl = PERSIST ? tiles[blockIdx.x + (it / nk_tile) * gridDim.x] : tile;
+        const int kc = (kb0 + (PERSIST ? it % nk_tile : it)) * KS;
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) {
-          tma_load_2d(sbase + sl * A_TILE, &mapA, fb, sl * ldb + kc, row_off + tile.x * TM);
-          tma_load_2d(sbase + NS * A_TILE + sl * B_TILE, &mapB, fb, sl * ldb + kc, row_off + tile.y * TN);
+          tma_load_2d(sbase + sl * A_TILE, &mapA, fb, sl * ldb + kc, row_off + tl.x * TM);
+          tma_load_2d(sbase + NS * A_TILE + sl * B_TILE, &mapB, fb, sl * ldb + kc, row_off + tl.y * TN);
         }
         ++issued;
       }
@@ -496,25 +510,55 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       hi[j] = 0.f;
       lo[j] = 0.f;
     }
-    const int row = tile.x * TM + q * 32 + lane;
-    const int col0 = tile.y * TN + cg * CPW;
+    int2 tcur = PERSIST ? (my_tiles > 0 ? tiles[blockIdx.x] : make_int2(0, 0)) : tile;
+    int row = tcur.x * TM + q * 32 + lane;
+    int col0 = tcur.y * TN + cg * CPW;
     // OZ_UPDATE: the warp's 32 x 32 sub-tile of C (lane = column) is copied
     // into its own shared-memory block while the operands load and the MMAs
     // run
     double* cs = reinterpret_cast<double*>(smem_raw + (smem_base - smem_u32(smem_raw)) + OST * OSTAGE) +
                  (warp - 2) * 32 * 33;
-    if (MODE == OZ_UPDATE) {
-      const int col = col0 + lane;
+    auto prefetch_c = [&](int2 t) {
+      const int col = t.y * TN + cg * CPW + lane;
 #pragma unroll 8
       for (int rr = 0; rr < 32; ++rr) {
-        const int rw = tile.x * TM + q * 32 + rr;
+        const int rw = t.x * TM + q * 32 + rr;
         if (lane < ncol && rw < m && col <= rw)
           asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(cs + rr * 33 + lane)),
                        "l"(epi.C + (long long)(row_off + rw) * epi.ldc + row_off + col)
                        : "memory");
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
-    }
+    };
+    // the update, scaled by 2^(E_row + E_col - eshift), is subtracted in the
+    // shared copy by the thread of its row; the copy then goes back row by
+    // row (lane = column), coalesced
+    auto update_c = [&]() {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncwarp();
+      // row exponent per lane; the 32 column exponents loaded once (lane =
+      // column) and broadcast
+      const int er = row < m ? epi.rexpA[row_off + row] : 0;
+      const int ecl = (lane < ncol && col0 + lane < m) ? epi.rexpA[row_off + col0 + lane] : 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int cj = col0 + j;
+        const int ec = __shfl_sync(0xffffffffu, ecl, j);
+        if (j < ncol && row < m && cj <= row)
+          cs[lane * 33 + j] -= scale_pow2(df_to_double_bits(hi[j], lo[j]), er + ec - epi.eshift);
+      }
+      __syncwarp();
+      if (!*abort_flag && lane < ncol) {
+        const int col = col0 + lane;
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) {
+          const int rw = tcur.x * TM + q * 32 + rr;
+          if (rw < m && col <= rw) epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] = cs[rr * 33 + lane];
+        }
+      }
+      __syncwarp();
+    };
+    if (MODE == OZ_UPDATE && my_tiles > 0) prefetch_c(tcur);
     // the chunks in the order the MMA warp commits them: by last stage, a
     // chunk of one stage (issued in the second pass) after the others, then
     // by accumulator
@@ -572,33 +616,28 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           cstart[a] = e + 1;
           cend[a] = e + 1 < nk ? chunk_end<NS, NG>(a, cidx[a], nk) : INT_MAX;
         }
-    }
-    if (MODE == OZ_UPDATE) {
-      // the update, scaled by 2^(E_row + E_col - eshift), is subtracted in
-      // the shared copy by the thread of its row; the copy then goes back
-      // row by row (lane = column), coalesced
-      asm volatile("cp.async.wait_all;" ::: "memory");
-      __syncwarp();
-      // row exponent per lane; the 32 column exponents loaded once (lane =
-      // column) and broadcast
-      const int er = row < m ? epi.rexpA[row_off + row] : 0;
-      const int ecl = (lane < ncol && col0 + lane < m) ? epi.rexpA[row_off + col0 + lane] : 0;
+      if (PERSIST && asel == NA - 1) {
+        // every accumulator of tile c = cidx - 1 is drained: finish the tile,
+        // start the next one's C copy
+        update_c();
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int cj = col0 + j;
-        const int ec = __shfl_sync(0xffffffffu, ecl, j);
-        if (j < ncol && row < m && cj <= row)
-          cs[lane * 33 + j] -= scale_pow2(df_to_double_bits(hi[j], lo[j]), er + ec - epi.eshift);
-      }
-      __syncwarp();
-      if (!*abort_flag && lane < ncol) {
-        const int col = col0 + lane;
-#pragma unroll 8
-        for (int rr = 0; rr < 32; ++rr) {
-          const int rw = tile.x * TM + q * 32 + rr;
-          if (rw < m && col <= rw) epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] = cs[rr * 33 + lane];
+        for (int j = 0; j < CPW; ++j) {
+          hi[j] = 0.f;
+          lo[j] = 0.f;
+        }
+        const int cn = cidx[NA - 1];
+        if (cn < my_tiles) {
+          tcur = tiles[blockIdx.x + cn * gridDim.x];
+          row = tcur.x * TM + q * 32 + lane;
+          col0 = tcur.y * TN + cg * CPW;
+          prefetch_c(tcur);
         }
       }
+    }
+    if (MODE == OZ_UPDATE) {
+      // every tile was finished in the loop; copies still in flight after an
+      // abort complete before the shared memory is released
+      asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (MODE == OZ_GEMM) {
       // the tile, scaled by alpha 2^(EA_row + EB_col - eshift), goes through
       // shared memory (the operand ring is idle: every MMA has completed)
@@ -1223,6 +1262,7 @@ struct OzFactor {
   std::vector<int> rest_prefix;   // rest tiles with row block < I, for I = 0 .. nI
   CUtensorMap mapA[2], mapB[2];
   cudaStream_t side = nullptr;    // the rest of each trailing update
+  int nsm = 148;                  // persistent CTAs of the sliced update
   cudaEvent_t ev_fork = nullptr, ev_slice = nullptr, ev_rest = nullptr;
 };
 
@@ -1302,6 +1342,8 @@ dngd_status oz_factor_plan(OzFactor** out, int m, double* C, long long ldc, void
                          osmem<FNS, FNG>());
     attr = true;
   }
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
   *out = p;
   return DNGD_OK;
 }
@@ -1329,7 +1371,7 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
                                                         p->rowexp[b], status);
     DNGD_LAUNCH_CHECK();
     DNGD_CUDA_CHECK(cudaEventRecord(p->ev_slice, st));
-    const OzEpi upd{p->C, p->ldc, p->rowexp[b], nullptr, 16 + 8 * (FNG - 1), 0, 0, 0.0, 0.0};
+    OzEpi upd{p->C, p->ldc, p->rowexp[b], nullptr, 16 + 8 * (FNG - 1), 0, 0, 0.0, 0.0};
     const int nIr = (r + TM - 1) / TM;
     // the first 64 columns (double-float, from the panel's pairs) also wait
     // for the previous step's rest, which updated the same columns
@@ -1340,8 +1382,10 @@ dngd_status oz_factor_run(OzFactor* p, int* status, cudaStream_t st) {
     const int nrest = p->rest_prefix[nIr];
     DNGD_CUDA_CHECK(cudaStreamWaitEvent(p->side, p->ev_slice, 0));
     if (nrest > 0) {
+      upd.ncols = nrest;   // the tile count of the persistent launch
       DNGD_NOTE_LAUNCH();
-      k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(nrest, 1), othreads<FNS, FNG>(), osmem<FNS, FNG>(), p->side>>>(
+      k_gram_oz<FNS, FNG, OZ_UPDATE><<<dim3(min(nrest, p->nsm), 1), othreads<FNS, FNG>(), osmem<FNS, FNG>(),
+                                       p->side>>>(
           p->mapA[b], p->mapB[b], p->d_rest, r, row0, FNB / KS, FNB, nullptr, 0, 0, upd, status);
       DNGD_LAUNCH_CHECK();
     }
