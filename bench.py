@@ -941,11 +941,13 @@ def run_dense(args, wl, rank, world, local_rank):
         solve_ms = float(np.mean([i["phase_ms"][3] + i["phase_ms"][5] for i in infos]))
         solve_bytes = iters_total * 12.0 * m * m + 2 * gemv_bytes * (2 if prec == dngd.MIXED_OZ64 else 1)
         solve_gbs = solve_bytes / (solve_ms * 1e-3) / 1e9 if solve_ms > 0 else 0.0
-        roof_gemv = {"bound": "hbm", "kernel": "k_pcg_persist (both solves) + k_gemv_t_f32 (map-back J^T x)",
+        mapback = "k_gemv_t (map-back J^T x over the FP64 J)" if prec == dngd.MIXED_OZ64 else \
+            "k_gemv_t_f32 (map-back J^T x over the FP32 J)"
+        roof_gemv = {"bound": "hbm", "kernel": f"k_pcg_persist (both solves) + {mapback}",
                      "achieved": solve_gbs, "peak": hbm, "unit": "GB/s", "frac": solve_gbs / hbm,
                      "bytes_per_step": solve_bytes, "solve_ms": solve_ms,
                      "algorithmic": "per PCG iteration 8 m^2 + 4 m^2 B (exact Gram operator, L^-1 and L^-T "
-                                    "triangles); per solve 4 m n B (J^T x)",
+                                    "triangles); per solve 8 m n B (FP64 J) or 4 m n B (FP32 J) for J^T x",
                      "peak_source": f"{src} HBM copy bandwidth", "traffic": None}
         traffic = args.gram_traffic
         if traffic is None and args.workload == "poisson5d" and args.points <= 0:

@@ -103,40 +103,46 @@ __device__ __forceinline__ T warp_sum(T v) {
 __device__ __forceinline__ double tanh_t(double x) { return tanh(x); }
 __device__ __forceinline__ float tanh_t(float x) { return tanhf(x); }
 
-// double(hi + lo) for a normalised double-float pair (|lo| <= ulp(hi) / 2),
-// assembled with integer operations (hi's significand shifted to the top of
-// the 53 bits, lo's added or subtracted below it, at most one bit of
-// renormalisation); a zero pair gives a signed zero; a subnormal or
-// non-finite hi or lo, or a pair that is not normalised, takes the FP64 add.
-// That fallback is a call, not inlined: inlined, the compiler may predicate
-// it into every use, and the float -> double conversions and the add then
-// occupy GB300's slow FP64 pipe for every value (measured: ~30k cycles for
-// 32 values a thread in the sliced update's epilogue).
-static __device__ __noinline__ double df_to_double_slow(float hi, float lo) { return (double)hi + (double)lo; }
+// (hi + lo) 2^e2 as an FP64 value, for a normalised double-float pair
+// (|lo| <= ulp(hi) / 2), assembled with 32-bit integer operations: hi's
+// sign, exponent (+ e2) and significand placed in the two words of the
+// double, and lo's significand, shifted to hi's FP64 units (rounded), added
+// to or subtracted from that bit pattern (one unit finer when it subtracts
+// from the bottom of hi's binade, where the pattern steps into the binade
+// below).  A zero pair gives a signed zero.  A subnormal or non-finite part,
+// a pair that is not normalised or a result outside the normal range takes
+// the FP64 path, which is a call: inlined, the compiler may predicate it
+// into every use, and conversions and adds on GB300's slow FP64 pipe then
+// cost every value.  (A first version with 64-bit variable shifts and
+// lane-divergent branches took ~1,000 cycles a value in the sliced update's
+// epilogue.)
+static __device__ __noinline__ double df_to_double_slow(float hi, float lo, int e2) {
+  return ldexp((double)hi + (double)lo, e2);
+}
 
-__device__ __forceinline__ double df_to_double_bits(float hi, float lo) {
+__device__ __forceinline__ double df_to_double_scaled(float hi, float lo, int e2) {
   const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
   const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
-  const bool lo_zero = (lb & 0x7FFFFFFFu) == 0u;
-  const int k = 29 - (eh - el);
-  if ((hb & 0x7FFFFFFFu) == 0u && lo_zero) return __longlong_as_double((long long)((unsigned long long)(hb >> 31) << 63));
-  if (eh == 0 || eh == 0xFF || (!lo_zero && (el == 0 || el == 0xFF || k > 5))) return df_to_double_slow(hi, lo);
-  unsigned long long S = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
-  if (!lo_zero) {
-    unsigned long long Ml = (lb & 0x7FFFFFu) | 0x800000u;
-    if (k >= 0) Ml <<= k;
-    else if (k > -40) Ml = (Ml + (1ull << (-k - 1))) >> (-k);
-    else Ml = 0;
-    S = ((hb ^ lb) >> 31) ? S - Ml : S + Ml;
-  }
-  unsigned long long e = (unsigned long long)(eh + 896);   // 1023 - 127
-  if (S < (1ull << 52)) {
-    S <<= 1;
-    --e;
-  }
-  return __longlong_as_double(
-      (long long)(((unsigned long long)(hb >> 31) << 63) | (e << 52) | (S - (1ull << 52))));
+  const unsigned lmag = lb & 0x7FFFFFFFu;
+  if ((hb & 0x7FFFFFFFu) == 0u && lmag == 0u) return __longlong_as_double((long long)((unsigned long long)(hb >> 31) << 63));
+  const int k = el - eh + 29;       // lo's significand in units of hi's FP64 ulp: Ml 2^k
+  const int eo = eh + 896 + e2;     // the result's biased exponent (1023 - 127 = 896)
+  if (eh == 0 || eh == 0xFF || eo < 2 || eo > 2046 || (lmag != 0u && (el == 0 || el == 0xFF || k > 5)))
+    return df_to_double_slow(hi, lo, e2);
+  const unsigned whi = (hb & 0x80000000u) | ((unsigned)eo << 20) | ((hb & 0x7FFFFFu) >> 3);
+  const unsigned wlo = (hb & 7u) << 29;
+  unsigned long long d = ((unsigned long long)whi << 32) | wlo;
+  const unsigned ml = (lb & 0x7FFFFFu) | 0x800000u;
+  const bool opp = ((hb ^ lb) >> 31) != 0u;
+  const int kk = k + ((opp && (hb & 0x7FFFFFu) == 0u) ? 1 : 0);
+  const int r = -kk;
+  unsigned c = kk >= 0 ? (ml << (kk > 0 ? kk : 0)) : (r < 25 ? (ml + (1u << (r - 1))) >> r : 0u);
+  c = lmag != 0u ? c : 0u;
+  d = opp ? d - c : d + c;
+  return __longlong_as_double((long long)d);
 }
+
+__device__ __forceinline__ double df_to_double_bits(float hi, float lo) { return df_to_double_scaled(hi, lo, 0); }
 
 // Double-float ("float2 as hi+lo") accumulation for FP32 data that needs an
 // accumulator with ~48 significant bits.  two_sum / two_prod are the

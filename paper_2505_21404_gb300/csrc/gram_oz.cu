@@ -225,22 +225,6 @@ __device__ __forceinline__ void df_add_exact(float& hi, float& lo, float c) {
   hi = t;
 }
 
-// x 2^e: e added to the exponent field when x and the result are normal
-// (integer operations), else an FP64 multiply by 2^e with e clamped to the
-// normal range.
-// (the FP64 fallback is a call, so it is not predicated into every use)
-__device__ __noinline__ double scale_pow2_slow(double x, int e) {
-  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-  return __longlong_as_double((long long)(e + 1023) << 52) * x;
-}
-__device__ __forceinline__ double scale_pow2(double x, int e) {
-  const long long b = __double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex != 0 && ex != 0x7FF && ex + e >= 1 && ex + e <= 2046) return __longlong_as_double(b + ((long long)e << 52));
-  if ((b & 0x7FFFFFFFFFFFFFFFLL) == 0) return x;   // a signed zero stays
-  return scale_pow2_slow(x, e);
-}
-
 // Weight 2^(-8 s) of slice s in the pre-scaled layout (exact in BF16 for the
 // slice values |sigma| <= 128 and s <= 3).
 __device__ __forceinline__ float slice_weight(int s) { return __int_as_float((127 - 8 * s) << 23); }
@@ -545,7 +529,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int cj = col0 + j;
         const int ec = __shfl_sync(0xffffffffu, ecl, j);
         if (j < ncol && row < m && cj <= row)
-          cs[lane * 33 + j] -= scale_pow2(df_to_double_bits(hi[j], lo[j]), er + ec - epi.eshift);
+          cs[lane * 33 + j] -= df_to_double_scaled(hi[j], lo[j], er + ec - epi.eshift);
       }
       __syncwarp();
       if (!*abort_flag && lane < ncol) {
@@ -652,7 +636,7 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 #pragma unroll
       for (int j = 0; j < CPW; ++j) {
         const int eb = __shfl_sync(0xffffffffu, j < 32 ? eb0 : eb1, j & 31);
-        tb[lane * TS + j] = epi.alpha * scale_pow2(df_to_double_bits(hi[j], lo[j]), er + eb - epi.eshift);
+        tb[lane * TS + j] = epi.alpha * df_to_double_scaled(hi[j], lo[j], er + eb - epi.eshift);
       }
       __syncwarp();
       if (!*abort_flag) {
