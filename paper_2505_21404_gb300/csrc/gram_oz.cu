@@ -524,12 +524,28 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       // column) and broadcast
       const int er = row < m ? epi.rexpA[row_off + row] : 0;
       const int ecl = (lane < ncol && col0 + lane < m) ? epi.rexpA[row_off + col0 + lane] : 0;
+      // all 32 values first (branch-free; the rare ones that need the FP64
+      // path are fixed up afterwards), then the read-modify-write
+      double vv[32];
+      unsigned slow = 0u;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int ec = __shfl_sync(0xffffffffu, ecl, j);
+        bool sl;
+        vv[j] = df_to_double_try(hi[j], lo[j], er + ec - epi.eshift, sl);
+        slow |= sl ? (1u << j) : 0u;
+      }
+      if (__any_sync(0xffffffffu, slow != 0u)) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int ec = __shfl_sync(0xffffffffu, ecl, j);
+          if ((slow >> j) & 1u) vv[j] = df_to_double_slow(hi[j], lo[j], er + ec - epi.eshift);
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int cj = col0 + j;
-        const int ec = __shfl_sync(0xffffffffu, ecl, j);
-        if (j < ncol && row < m && cj <= row)
-          cs[lane * 33 + j] -= df_to_double_scaled(hi[j], lo[j], er + ec - epi.eshift);
+        if (j < ncol && row < m && cj <= row) cs[lane * 33 + j] -= vv[j];
       }
       __syncwarp();
       if (!*abort_flag && lane < ncol) {
@@ -633,10 +649,20 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int er = row < m ? epi.rexpA[row] : 0;
       const int eb0 = (lane < CPW && col0 + lane < epi.ncols) ? epi.rexpB[col0 + lane] : 0;
       const int eb1 = (lane + 32 < CPW && col0 + lane + 32 < epi.ncols) ? epi.rexpB[col0 + lane + 32] : 0;
+      unsigned long long slow = 0ull;
 #pragma unroll
       for (int j = 0; j < CPW; ++j) {
         const int eb = __shfl_sync(0xffffffffu, j < 32 ? eb0 : eb1, j & 31);
-        tb[lane * TS + j] = epi.alpha * df_to_double_scaled(hi[j], lo[j], er + eb - epi.eshift);
+        bool sl;
+        tb[lane * TS + j] = epi.alpha * df_to_double_try(hi[j], lo[j], er + eb - epi.eshift, sl);
+        slow |= sl ? (1ull << j) : 0ull;
+      }
+      if (__any_sync(0xffffffffu, slow != 0ull)) {
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+          const int eb = __shfl_sync(0xffffffffu, j < 32 ? eb0 : eb1, j & 31);
+          if ((slow >> j) & 1ull) tb[lane * TS + j] = epi.alpha * df_to_double_slow(hi[j], lo[j], er + eb - epi.eshift);
+        }
       }
       __syncwarp();
       if (!*abort_flag) {
