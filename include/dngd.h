@@ -100,6 +100,21 @@ enum dngd_solver {
                       (FP32 jets and FP32 factor-form operator) */
 };
 
+/* Trailing updates of the exact-Gram modes' factorisation
+ * (dngd_problem_desc.factor_update) */
+enum dngd_factor_update {
+  DNGD_FACTOR_SLICED = 0,       /* the first 64 columns of each step's update
+                                   in double-float, the rest exact products
+                                   of six 8-bit slices on the tensor cores,
+                                   on a side stream (look-ahead) */
+  DNGD_FACTOR_DF = 1            /* the whole update in double-float
+                                   arithmetic, no look-ahead: what a batch of
+                                   exact-Gram instances uses, all instances'
+                                   steps in one launch per kernel; a single
+                                   context with this setting computes the
+                                   same factor as its batch */
+};
+
 /* GEMMs of the matrix-free operator (dngd_problem_desc.pcg_operator) */
 enum dngd_pcg_operator {
   DNGD_PCG_OP_TC3 = 0,          /* 3xTF32 on the tensor cores */
@@ -174,6 +189,14 @@ typedef struct {
                                         (Kahan) accumulation and FP64 row
                                         reductions, slower and more
                                         accurate (see dngd_kvp). */
+  int factor_update;                 /* enum dngd_factor_update (exact-Gram
+                                        modes, DNGD_DENSE): how the factor's
+                                        trailing updates are computed.  Both
+                                        keep ~2^-47 of each entry (the
+                                        factor preconditions a refinement on
+                                        the exact Gram).  Batches of
+                                        exact-Gram instances always use
+                                        DNGD_FACTOR_DF. */
 } dngd_problem_desc;
 
 typedef struct {
@@ -371,13 +394,15 @@ dngd_status dngd_precond_apply(dngd_ctx* ctx, const double* x, double* z_out);
 /* ---- asynchronous stepping and batches of independent instances --------
  * A dense context can step without any host synchronisation: the step reads
  * its inputs from the context's own staging buffers, runs the refinement for
- * a fixed budget of refine_max_it iterations (each kernel of an iteration is a
- * no-op once the device-side convergence flag is set, so results equal the
+ * a fixed budget of iterations (twice the last synchronous step's count plus
+ * two, at least 8 and at most refine_max_it; each kernel of an iteration is
+ * a no-op once the device-side convergence flag is set, so results equal the
  * synchronous step's) and factors the low-precision Gram once with the shift
  * of the previous synchronous step.  That step is captured once into a CUDA
- * graph and replayed (re-captured when lambda changes).  The first
- * asynchronous step of a context, and any step after a failed factorisation,
- * runs synchronously to choose the shift. */
+ * graph and replayed (re-captured when lambda, the shift or the budget
+ * changes).  The first asynchronous step of a context, and the step after a
+ * failed factorisation or after a captured solve that stopped at its budget
+ * above refine_tol, runs synchronously. */
 
 /* Enqueue one step on the context's stream (inputs are copied first; pointers
  * may be host or device; delta_out is written when the stream reaches it).
@@ -393,8 +418,17 @@ dngd_status dngd_step_wait(dngd_ctx* ctx, dngd_step_info* info);
 /* A batch of independent D-NGD instances of different shapes (e.g. many
  * small PINNs of uneven m and n).  Every instance has its own context and
  * stream; one batch step is ONE CUDA-graph launch that forks to all instance
- * streams (each runs its asynchronous step) and joins.  Instances never
- * share work, so each result equals the instance stepped alone. */
+ * streams (each runs its asynchronous step) and joins.  When every instance
+ * is an exact-Gram mode (DNGD_MIXED_OZ / OZ64), the instances' steps run in
+ * two halves around one batched factorisation: per 64-column step, one
+ * launch each for all instances' diagonal blocks, panel solves and trailing
+ * updates (double-float; such instances are created with factor_update =
+ * DNGD_FACTOR_DF, also for their synchronous steps).  The per-instance
+ * arithmetic never depends on the batch, so each result equals the instance
+ * stepped alone with the same descriptor (factor_update = DNGD_FACTOR_DF for
+ * exact-Gram modes).  An instance whose captured step failed its factor or
+ * stopped its refinement at the captured budget above tolerance is redone
+ * synchronously and the graph is re-captured. */
 typedef struct dngd_batch dngd_batch;
 
 /* descs [count] (dense solver); stream: master stream or NULL (own stream). */

@@ -57,6 +57,8 @@ struct dngd_ctx {
   float* trtri_work = nullptr;
   OzPlan* oz = nullptr;       // exact-Gram mode
   OzFactor* ozf = nullptr;    // its FP64 factorisation (exact sliced trailing updates)
+  OzBatchFactor* ozb = nullptr;   // the same with double-float trailing updates (factor_update = DF)
+  int phase = 0;              // batched steps: 1 stops before the factor, 2 starts after it
   OzGemm* ozi = nullptr;      // FP64 GEMMs of the factor's inverse (exact-Gram modes)
   void* ozi_work = nullptr;
   double *Li64 = nullptr, *LiT64 = nullptr;   // the factor's FP64 inverse and its transpose
@@ -116,6 +118,13 @@ struct dngd_ctx {
   float *ls_Z = nullptr, *ls_H = nullptr;  // their pre-activations / activations [G R max_w]
   int ls_G = 0;                            // trials per batched sweep
   double graph_mu = 0.0;
+  // refinement iterations of a captured (asynchronous) solve, which cannot
+  // stop on the host: twice the last synchronous step's count plus two (at
+  // least 8, at most refine_max_it); iterations after convergence are no-ops,
+  // and a captured solve that has not converged by then is redone
+  // synchronously (batch) or makes the next step synchronous
+  int async_it = 0;
+  int graph_it = 0;
   cudaStream_t gst = nullptr;        // private stream for capture / replay
   unsigned long long graph_kernels = 0;  // kernel launches captured in the graph
   cudaEvent_t gev[2] = {};           // fences between st and gst
@@ -385,7 +394,8 @@ dngd_status pcg_mixed(dngd_ctx* c, const double* b, double* x, int slot) {
   P.scal_h = c->scal_h;
   P.ev = (c->timing && slot == 0) ? c->kev : nullptr;
   const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
-  const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
+  int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
+  if (c->async && c->async_it > 0 && c->async_it < maxit) maxit = c->async_it;
   if (oz_mode(c->prec)) {
     // the exact FP64 Gram is the operator: one m x m GEMV per iteration; the
     // synchronous solve is one persistent cooperative kernel
@@ -455,12 +465,19 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
   dngd_status s;
   const int m = c->m;
   const int n = (int)c->n;
-  DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
-  evrec(c, 0);
+  // c->phase: 0 the whole step; in a batch of exact-Gram instances, 1 up to
+  // the factorisation and 2 from the factor's inverse on (the batch factors
+  // every instance in between)
+  if (c->phase != 2) {
+    DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+    evrec(c, 0);
+  }
   const T* thT = theta_in_T<T>(c, theta);
-  if ((s = residual_jacobian_T<T>(c, thT, X, target))) return s;
-  if ((s = apply_lambda_rule(c))) return s;
-  evrec(c, 1);
+  if (c->phase != 2) {
+    if ((s = residual_jacobian_T<T>(c, thT, X, target))) return s;
+    if ((s = apply_lambda_rule(c))) return s;
+    evrec(c, 1);
+  }
   // K + lambda I (lower)
   if (c->prec == DNGD_FP64) {
     if ((s = gemm_nt<double>(m, m, n, 1.0, (const double*)c->J, c->ldJ, (const double*)c->J, c->ldJ, 0.0,
@@ -478,32 +495,38 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     // exact Gram: FP64 factor of K + (lambda + mu) I with exact sliced
     // trailing updates (mu = 0 unless that fails at the Gram's own accuracy);
     // its FP32 rounding and inverse precondition PCG on the exact operator
-    double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
-    const double mu0 = mu;
-    gram_set_shift(c, c->lambda + mu);
-    if ((s = gram_run(c, c->timing))) return s;
-    c->factor_attempts = 0;
-    if (!c->async && (s = diag_sum<float>(m, (const float*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
-    for (int attempt = 0;; ++attempt) {
-      if (attempt > 0) {
-        gram_set_shift(c, c->lambda + mu);
-        if ((s = gram_oz_reduce(c->oz, c->st))) return s;
+    if (c->phase != 2) {
+      double mu = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
+      const double mu0 = mu;
+      gram_set_shift(c, c->lambda + mu);
+      if ((s = gram_run(c, c->timing))) return s;
+      c->factor_attempts = 0;
+      if (!c->async && (s = diag_sum<float>(m, (const float*)c->K, c->ldk, c->scal + S_TRACE, c->st))) return s;
+      for (int attempt = 0;; ++attempt) {
+        if (attempt > 0) {
+          gram_set_shift(c, c->lambda + mu);
+          if ((s = gram_oz_reduce(c->oz, c->st))) return s;
+        }
+        evrec(c, 2);
+        c->factor_attempts++;
+        if (c->phase == 1) {   // a batch factors all instances together
+          c->shift_used = mu;
+          return DNGD_OK;
+        }
+        if ((s = c->ozb ? oz_factor_batched_run(c->ozb, c->st) : oz_factor_run(c->ozf, c->status, c->st))) return s;
+        if (c->async) break;   // a failure is reported by the status word
+        const dngd_status fs = read_status(c);
+        if (fs != DNGD_ERR_NOT_SPD || attempt >= 15) break;
+        DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+        DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
+        const double tr = c->scal_h[S_TRACE] - m * (c->lambda + mu0);
+        const double base = 1e-10 * (tr > 0 ? tr : 1.0) / m;
+        mu = mu * 10.0 > base ? mu * 10.0 : base;
+        DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
       }
-      evrec(c, 2);
-      c->factor_attempts++;
-      if ((s = oz_factor_run(c->ozf, c->status, c->st))) return s;
-      if (c->async) break;   // a failure is reported by the status word
-      const dngd_status fs = read_status(c);
-      if (fs != DNGD_ERR_NOT_SPD || attempt >= 15) break;
-      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
-      DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
-      const double tr = c->scal_h[S_TRACE] - m * (c->lambda + mu0);
-      const double base = 1e-10 * (tr > 0 ? tr : 1.0) / m;
-      mu = mu * 10.0 > base ? mu * 10.0 : base;
-      DNGD_CUDA_CHECK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->st));
+      if (!c->async) c->mu_sticky = mu;
+      c->shift_used = mu;
     }
-    if (!c->async) c->mu_sticky = mu;
-    c->shift_used = mu;
     // the factor's inverse in FP64 from sliced products (its condition number
     // is the square root of K's, up to ~1e5 late in training, so an inverse
     // formed in FP32 arithmetic is off by far more than FP32 rounding), then
@@ -895,6 +918,16 @@ void info_from_host(dngd_ctx* c, dngd_step_info* info);
 
 // Fill info after an asynchronous step whose graph copied scal/status to the
 // pinned host buffers (the stream must have been synchronised).
+// A captured solve that stopped at async_it (below the full budget) above
+// the refinement tolerance.
+bool async_capped(const dngd_ctx* c) {
+  if (c->pcg || c->prec == DNGD_FP64 || c->async_it <= 0) return false;
+  const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
+  const double tol = c->desc.refine_tol > 0 ? c->desc.refine_tol : 1e-10;
+  if (c->async_it >= maxit) return false;
+  return c->relres[0] > tol || c->relres[1] > tol;
+}
+
 dngd_status finish_async(dngd_ctx* c, dngd_step_info* info) {
   const double* h = c->scal_h;
   for (int k = 0; k < 2; ++k) {
@@ -1145,6 +1178,11 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     if (s) return s;
     gram_oz_set_fp64_out(c->oz, c->Kd);
     if ((s = oz_factor_plan(&c->ozf, m, c->Kd, c->ldk, c->ozf_work, c->st))) return s;
+    if (c->desc.factor_update == DNGD_FACTOR_DF) {
+      OzFactor* f1[1] = {c->ozf};
+      int* s1[1] = {c->status};
+      if ((s = oz_factor_batched_plan(&c->ozb, 1, f1, s1, c->st))) return s;
+    }
     if ((s = oz_gemm_plan(&c->ozi, m, m, m, c->ozi_work))) return s;
     if (c->ozg_work) {
       if ((s = oz_gemm_plan(&c->ozg, 3 * net.R, net.max_w, net.max_w, c->ozg_work))) return s;
@@ -1177,6 +1215,7 @@ void free_ctx(dngd_ctx* c) {
   if (c->status_h) cudaFreeHost(c->status_h);
   if (c->gram) gram_tc_free(c->gram);
   if (c->oz) gram_oz_free(c->oz);
+  if (c->ozb) oz_factor_batched_free(c->ozb);
   if (c->ozf) oz_factor_free(c->ozf);
   if (c->ozg) oz_gemm_free(c->ozg);
   if (c->ozi) oz_gemm_free(c->ozi);
@@ -1249,6 +1288,8 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
     return DNGD_ERR_INVALID_ARG;
   if (desc->pcg_operator != DNGD_PCG_OP_TC3 && desc->pcg_operator != DNGD_PCG_OP_COMPENSATED)
     return DNGD_ERR_INVALID_ARG;
+  if (desc->factor_update != DNGD_FACTOR_SLICED && desc->factor_update != DNGD_FACTOR_DF)
+    return DNGD_ERR_INVALID_ARG;
   gemv_init();
   dngd_ctx* c = new dngd_ctx();
   c->desc = *desc;
@@ -1306,6 +1347,11 @@ dngd_status dngd_step(dngd_ctx* c, const double* theta, const double* X, const d
     return ds ? ds : s;
   }
   if ((s = out_copy(c, delta_out, c->delta, c->n))) return s;
+  if (!c->pcg && c->prec != DNGD_FP64) {
+    const int maxit = c->desc.refine_max_it > 0 ? c->desc.refine_max_it : 200;
+    const int used = c->iters[0] > c->iters[1] ? c->iters[0] : c->iters[1];
+    c->async_it = 2 * used + 2 < 8 ? 8 : (2 * used + 2 > maxit ? maxit : 2 * used + 2);
+  }
   if (info) return fill_info(c, info);
   return DNGD_OK;
 }
@@ -1666,6 +1712,7 @@ dngd_status enqueue_async(dngd_ctx* c) {
   c->timing = timing;
   c->async = false;
   if (s) return s;
+  if (c->phase == 1) return DNGD_OK;   // the step goes on after the batch's factorisation
   DNGD_CUDA_CHECK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->st));
   DNGD_CUDA_CHECK(cudaMemcpyAsync(c->status_h, c->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   return DNGD_OK;
@@ -1691,6 +1738,8 @@ struct dngd_batch {
   cudaGraphExec_t exec = nullptr;
   bool first = true;
   unsigned long long graph_kernels = 0;
+  OzBatchFactor* ozb = nullptr;     // every exact-Gram instance's factorisation together
+  cudaEvent_t fork2 = nullptr;      // after the batched factorisation
 };
 
 extern "C" {
@@ -1723,7 +1772,7 @@ dngd_status dngd_step_async(dngd_ctx* c, const double* theta, const double* X, c
   // the graph bakes in lambda and the preconditioner shift of the last
   // synchronous step; either changing means a new capture
   const double mu_now = c->mu_sticky > c->desc.shift_mu ? c->mu_sticky : c->desc.shift_mu;
-  if (!c->graph || c->graph_lambda != c->lambda || c->graph_mu != mu_now) {
+  if (!c->graph || c->graph_lambda != c->lambda || c->graph_mu != mu_now || c->graph_it != c->async_it) {
     if (c->graph) {
       cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
@@ -1748,6 +1797,7 @@ dngd_status dngd_step_async(dngd_ctx* c, const double* theta, const double* X, c
     cudaGraphDestroy(g);
     c->graph_lambda = c->lambda;
     c->graph_mu = mu_now;
+    c->graph_it = c->async_it;
   }
   DNGD_CUDA_CHECK(cudaEventRecord(c->gev[0], user));
   DNGD_CUDA_CHECK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
@@ -1764,7 +1814,9 @@ dngd_status dngd_step_wait(dngd_ctx* c, dngd_step_info* info) {
   if (!c) return DNGD_ERR_INVALID_ARG;
   DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
   dngd_status s = finish_async(c, info);
-  if (s == DNGD_ERR_NOT_SPD) c->async_ok = false;  // next step re-runs the shift search
+  // a failed factor or a capped solve that did not converge: the next step
+  // runs synchronously (shift search, full iteration budget)
+  if (s == DNGD_ERR_NOT_SPD || async_capped(c)) c->async_ok = false;
   return s;
 }
 
@@ -1782,8 +1834,13 @@ dngd_status dngd_batch_create(dngd_batch** out, const dngd_problem_desc* descs, 
       dngd_batch_destroy(b);
       return DNGD_ERR_CUDA;
     }
+    // exact-Gram instances factor with double-float trailing updates, the
+    // form the batch runs for all of them in one launch per kernel (also in
+    // each instance's synchronous steps, so they compute the same factor)
+    dngd_problem_desc d = descs[i];
+    if (d.precision == DNGD_MIXED_OZ || d.precision == DNGD_MIXED_OZ64) d.factor_update = DNGD_FACTOR_DF;
     dngd_ctx* c = nullptr;
-    dngd_status s = dngd_create(&c, &descs[i], st);
+    dngd_status s = dngd_create(&c, &d, st);
     if (s) {
       cudaStreamDestroy(st);
       dngd_batch_destroy(b);
@@ -1801,6 +1858,22 @@ dngd_status dngd_batch_create(dngd_batch** out, const dngd_problem_desc* descs, 
     b->own_master = true;
   }
   cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming);
+  bool all_oz = true;
+  for (dngd_ctx* c : b->ctx) all_oz = all_oz && c->ozf != nullptr;
+  if (all_oz) {
+    std::vector<OzFactor*> f;
+    std::vector<int*> st;
+    for (dngd_ctx* c : b->ctx) {
+      f.push_back(c->ozf);
+      st.push_back(c->status);
+    }
+    dngd_status s = oz_factor_batched_plan(&b->ozb, (int)f.size(), f.data(), st.data(), b->master);
+    if (s) {
+      dngd_batch_destroy(b);
+      return s;
+    }
+  }
   *out = b;
   return DNGD_OK;
 }
@@ -1816,6 +1889,8 @@ dngd_status dngd_batch_destroy(dngd_batch* b) {
     cudaEventDestroy(b->join[i]);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->fork2) cudaEventDestroy(b->fork2);
+  if (b->ozb) oz_factor_batched_free(b->ozb);
   if (b->own_master) cudaStreamDestroy(b->master);
   delete b;
   return DNGD_OK;
@@ -1849,13 +1924,25 @@ dngd_status dngd_batch_step(dngd_batch* b, const double* const* theta, const dou
     const unsigned long long k0 = dngd::g_launches.load();
     dngd_status s = DNGD_OK;
     if (cudaEventRecord(b->fork, b->master) != cudaSuccess) s = DNGD_ERR_CUDA;
-    for (int i = 0; i < nb && !s; ++i) {
-      dngd_ctx* c = b->ctx[i];
-      if (cudaStreamWaitEvent(c->st, b->fork, 0) != cudaSuccess) s = DNGD_ERR_CUDA;
-      if (!s) s = enqueue_async(c);
-      if (!s && cudaEventRecord(b->join[i], c->st) != cudaSuccess) s = DNGD_ERR_CUDA;
-      if (!s && cudaStreamWaitEvent(b->master, b->join[i], 0) != cudaSuccess) s = DNGD_ERR_CUDA;
+    // exact-Gram batches in two halves around one batched factorisation of
+    // every instance; otherwise one whole step per instance
+    const int halves = b->ozb ? 2 : 1;
+    for (int h = 0; h < halves && !s; ++h) {
+      cudaEvent_t ev = h == 0 ? b->fork : b->fork2;
+      for (int i = 0; i < nb && !s; ++i) {
+        dngd_ctx* c = b->ctx[i];
+        c->phase = b->ozb ? h + 1 : 0;
+        if (cudaStreamWaitEvent(c->st, ev, 0) != cudaSuccess) s = DNGD_ERR_CUDA;
+        if (!s) s = enqueue_async(c);
+        if (!s && cudaEventRecord(b->join[i], c->st) != cudaSuccess) s = DNGD_ERR_CUDA;
+        if (!s && cudaStreamWaitEvent(b->master, b->join[i], 0) != cudaSuccess) s = DNGD_ERR_CUDA;
+      }
+      if (!s && h == 0 && b->ozb) {
+        s = oz_factor_batched_run(b->ozb, b->master);
+        if (!s && cudaEventRecord(b->fork2, b->master) != cudaSuccess) s = DNGD_ERR_CUDA;
+      }
     }
+    for (dngd_ctx* c : b->ctx) c->phase = 0;
     const cudaError_t e = cudaStreamEndCapture(b->master, &g);
     b->graph_kernels = dngd::g_launches.load() - k0;
     dngd::g_launches.fetch_sub(b->graph_kernels);
@@ -1877,7 +1964,7 @@ dngd_status dngd_batch_step(dngd_batch* b, const double* const* theta, const dou
     dngd_ctx* c = b->ctx[i];
     c->have_step = true;
     dngd_status s = finish_async(c, infos ? &infos[i] : nullptr);
-    if (s == DNGD_ERR_NOT_SPD) {
+    if (s == DNGD_ERR_NOT_SPD || async_capped(c)) {
       // redo this instance synchronously (the shift search raises mu) and
       // rebuild the batch graph with the new shift
       s = dngd_step(c, theta[i], X[i], target[i], delta_out[i], infos ? &infos[i] : nullptr);

@@ -51,6 +51,7 @@
 // (ST_TIMEOUT, drain, free TMEM).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <climits>
 
 #include <vector>
@@ -1026,9 +1027,8 @@ __device__ __forceinline__ void tri64_entry(int e, int& i, int& c) {
 // rdf[64].  A pivot that is not positive sets ST_NOT_SPD with its column
 // (status[1]).
 constexpr int kDiagThreads = 512;
-__global__ void __launch_bounds__(kDiagThreads) k_potrf_diag_df(int k0, int kb, double* A, long long lda,
-                                                                float2* __restrict__ Ldf, float2* __restrict__ rdf,
-                                                                int* status) {
+__device__ __forceinline__ void potrf_diag_df_body(int k0, int kb, double* A, long long lda,
+                                                   float2* __restrict__ Ldf, float2* __restrict__ rdf, int* status) {
   constexpr int NB = FNB, NE = NB * (NB + 1) / 2, Q = (NE + kDiagThreads - 1) / kDiagThreads;
   static_assert(NB == 64, "the triangle numbering assumes 64 columns");
   __shared__ float2 col[2][NB];
@@ -1105,6 +1105,11 @@ __global__ void __launch_bounds__(kDiagThreads) k_potrf_diag_df(int k0, int kb, 
   }
   if (tid < NB) rdf[tid] = tid < kb ? rs[tid] : make_float2(0.f, 0.f);
 }
+__global__ void __launch_bounds__(kDiagThreads) k_potrf_diag_df(int k0, int kb, double* A, long long lda,
+                                                                float2* __restrict__ Ldf, float2* __restrict__ rdf,
+                                                                int* status) {
+  potrf_diag_df_body(k0, kb, A, lda, Ldf, rdf, status);
+}
 
 // Panel rows g in [k0 + kb, m): X L11^T = A_panel by forward substitution,
 // x_j = (a_j - sum_{i<j} x_i L_ji) r_j, then the row's exponent and six
@@ -1116,13 +1121,12 @@ __global__ void __launch_bounds__(kDiagThreads) k_potrf_diag_df(int k0, int kb, 
 // first 64 columns of the update), and slices S[g] (FLD BF16 per row, zero
 // beyond kb) with exponents rowexp[g] (|x| / 2^E < 0.5, entries kept to
 // 2^(E - 49)).
+// (Without slices, Sl = nullptr, the rows are only solved.)
 constexpr int kPanelRows = 16;
-__global__ void __launch_bounds__(128) k_trsm_panel_df(int m, int k0, int kb, double* A, long long lda,
-                                                       const float2* __restrict__ Ldf,
-                                                       const float2* __restrict__ rdf, float2* __restrict__ P,
-                                                       __nv_bfloat16* __restrict__ Sl, int* __restrict__ rowexp,
-                                                       const int* status) {
-  if (status[0] & ST_NOT_SPD) return;
+__device__ __forceinline__ void trsm_panel_df_body(int m, int k0, int kb, double* A, long long lda,
+                                                   const float2* __restrict__ Ldf, const float2* __restrict__ rdf,
+                                                   float2* __restrict__ P, __nv_bfloat16* __restrict__ Sl,
+                                                   int* __restrict__ rowexp, int blk) {
   constexpr int NB = FNB;
   __shared__ float2 Lsh[NB][NB + 1];
   __shared__ float2 rc[NB];
@@ -1136,7 +1140,7 @@ __global__ void __launch_bounds__(128) k_trsm_panel_df(int m, int k0, int kb, do
   }
   if (tid < NB) rc[tid] = rdf[tid];
   const int q = tid & 7;
-  const long long row = (long long)blockIdx.x * kPanelRows + (tid >> 3);
+  const long long row = (long long)blk * kPanelRows + (tid >> 3);
   const long long g = (long long)k0 + kb + row;
   const bool live = g < m;
   dfloat x[8];
@@ -1175,6 +1179,13 @@ __global__ void __launch_bounds__(128) k_trsm_panel_df(int m, int k0, int kb, do
   }
   for (int o = 4; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o, 8));
   if (!live) return;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int j = q + 8 * t;
+    if (j < kb) A[g * lda + k0 + j] = xd[t];
+    P[row * NB + j] = j < kb ? make_float2(x[t].hi, x[t].lo) : make_float2(0.f, 0.f);
+  }
+  if (Sl == nullptr) return;
   // a non-finite entry (a failed factorisation upstream) slices as zero
   const bool bad = amax >= 0x7FF0000000000000LL;
   const int E = bad ? 1 : exp_of_abs_bits(amax);
@@ -1183,13 +1194,19 @@ __global__ void __launch_bounds__(128) k_trsm_panel_df(int m, int k0, int kb, do
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const int j = q + 8 * t;
-    if (j < kb) A[g * lda + k0 + j] = xd[t];
-    P[row * NB + j] = j < kb ? make_float2(x[t].hi, x[t].lo) : make_float2(0.f, 0.f);
     float d[FNS];
     oz_digits<FNS>(bad ? 0.0 : xd[t], E, d);
 #pragma unroll
     for (int s = 0; s < FNS; ++s) sr[s * FNB + j] = __float2bfloat16_rn(d[s]);
   }
+}
+__global__ void __launch_bounds__(128) k_trsm_panel_df(int m, int k0, int kb, double* A, long long lda,
+                                                       const float2* __restrict__ Ldf,
+                                                       const float2* __restrict__ rdf, float2* __restrict__ P,
+                                                       __nv_bfloat16* __restrict__ Sl, int* __restrict__ rowexp,
+                                                       const int* status) {
+  if (status[0] & ST_NOT_SPD) return;
+  trsm_panel_df_body(m, k0, kb, A, lda, Ldf, rdf, P, Sl, rowexp, blockIdx.x);
 }
 
 // The trailing update's first 64 columns (the next diagonal block and
@@ -1198,22 +1215,23 @@ __global__ void __launch_bounds__(128) k_trsm_panel_df(int m, int k0, int kb, do
 // (row-major, 64 per row).  A CTA takes 16 rows x 64 columns with 256
 // threads, each one row x 4 columns (columns tx + 16 u), the sums in
 // double-float; the result is rounded once into the FP64 entry.
+// (strip_update_df_body: rows 16 blk .. 16 blk + 15 and the 64 columns from
+// c0 of the trailing block, c <= i.)
 constexpr int kStripRows = 16;
-__global__ void __launch_bounds__(256) k_strip_update_df(int m, int r0, const float2* __restrict__ P, double* C,
-                                                         long long ldc, const int* status) {
-  if (status[0] & ST_NOT_SPD) return;
+__device__ __forceinline__ void strip_update_df_body(int m, int r0, const float2* __restrict__ P, double* C,
+                                                     long long ldc, int blk, int c0) {
   constexpr int NB = FNB;
   __shared__ float2 Pt[NB][NB + 1];            // the first 64 panel rows (the strip's columns)
   __shared__ float2 Pr[kStripRows][NB + 1];    // this CTA's rows
-  const int tid = threadIdx.x, r = m - r0, nc = min(NB, r);
-  const int i0 = blockIdx.x * kStripRows;
+  const int tid = threadIdx.x, r = m - r0, nc = min(NB, r - c0);
+  const int i0 = blk * kStripRows;
   {
     // every load in flight before the first store
     float2 pv[NB * NB / 256], rv[kStripRows * NB / 256];
 #pragma unroll
     for (int u = 0; u < NB * NB / 256; ++u) {
       const int e = tid + 256 * u;
-      pv[u] = (e >> 6) < nc ? P[e] : make_float2(0.f, 0.f);
+      pv[u] = (e >> 6) < nc ? P[(long long)c0 * NB + e] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < kStripRows * NB / 256; ++u) {
@@ -1250,11 +1268,16 @@ __global__ void __launch_bounds__(256) k_strip_update_df(int m, int r0, const fl
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int c = tx + 16 * u;
-    if (c >= nc || c > i) continue;
+    if (c >= nc || c0 + c > i) continue;
     const float hi = s[u].hi + s[u].lo;
     const float lo = s[u].lo - (hi - s[u].hi);
-    C[(long long)(r0 + i) * ldc + r0 + c] -= df_to_double_bits(hi, lo);
+    C[(long long)(r0 + i) * ldc + r0 + c0 + c] -= df_to_double_bits(hi, lo);
   }
+}
+__global__ void __launch_bounds__(256) k_strip_update_df(int m, int r0, const float2* __restrict__ P, double* C,
+                                                         long long ldc, const int* status) {
+  if (status[0] & ST_NOT_SPD) return;
+  strip_update_df_body(m, r0, P, C, ldc, blockIdx.x, 0);
 }
 
 }  // namespace
@@ -1417,6 +1440,179 @@ void oz_factor_free(OzFactor* p) {
   delete p;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched factorisation of independent exact-Gram instances: one plan over
+// all of them, and per 64-column step three launches for every instance
+// together (diagonal blocks; panel solves; the whole trailing update in
+// double-float arithmetic, 16-row x 64-column units).  Many instances of
+// modest size then fill the device instead of each running its own chain of
+// small launches.  The per-instance arithmetic does not depend on the batch:
+// a plan of one instance computes the same factor bit for bit.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct BInst {
+  double* C;
+  long long ldc;
+  int m;
+  int* status;
+  float2 *Ldf, *rdf, *P;
+};
+
+// The participant of a launch that owns CTA b: parts are (instance, first
+// CTA) pairs in CTA order.
+__device__ __forceinline__ int2 find_part(const int2* __restrict__ parts, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (parts[mid].y <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return parts[lo];
+}
+
+__global__ void __launch_bounds__(kDiagThreads) k_potrf_diag_df_b(const BInst* __restrict__ inst,
+                                                                  const int* __restrict__ list, int k0) {
+  const BInst I = inst[list[blockIdx.x]];
+  if (I.status[0] & ST_NOT_SPD) return;
+  potrf_diag_df_body(k0, min(FNB, I.m - k0), I.C, I.ldc, I.Ldf, I.rdf, I.status);
+}
+
+__global__ void __launch_bounds__(128) k_trsm_panel_df_b(const BInst* __restrict__ inst,
+                                                         const int2* __restrict__ parts, int n, int k0) {
+  const int2 pt = find_part(parts, n, blockIdx.x);
+  const BInst I = inst[pt.x];
+  if (I.status[0] & ST_NOT_SPD) return;
+  trsm_panel_df_body(I.m, k0, FNB, I.C, I.ldc, I.Ldf, I.rdf, I.P, nullptr, nullptr, (int)blockIdx.x - pt.y);
+}
+
+// Unit u of an instance's trailing update: row block R (16 rows) has
+// floor(R / 4) + 1 units (64-column blocks J <= R / 4), so groups of four
+// row blocks hold 4 (q + 1) units and group q starts at unit 2 q (q + 1).
+__global__ void __launch_bounds__(256) k_trail_df_b(const BInst* __restrict__ inst, const int2* __restrict__ parts,
+                                                    int n, int k0) {
+  const int2 pt = find_part(parts, n, blockIdx.x);
+  const BInst I = inst[pt.x];
+  if (I.status[0] & ST_NOT_SPD) return;
+  const int u = (int)blockIdx.x - pt.y;
+  int q = (int)((sqrtf(1.0f + 2.0f * (float)u) - 1.0f) * 0.5f);
+  while (q > 0 && 2 * q * (q + 1) > u) --q;
+  while (2 * (q + 1) * (q + 2) <= u) ++q;
+  const int v = u - 2 * q * (q + 1);
+  const int R = 4 * q + v / (q + 1), J = v % (q + 1);
+  strip_update_df_body(I.m, k0 + FNB, I.P, I.C, I.ldc, R, FNB * J);
+}
+
+int trail_units(int r) {
+  const int nR = (r + kStripRows - 1) / kStripRows;
+  int u = 0;
+  for (int R = 0; R < nR; ++R) u += R / 4 + 1;
+  return u;
+}
+
+}  // namespace
+
+struct OzBatchFactor {
+  int n = 0, steps = 0;
+  BInst* d_inst = nullptr;
+  int* d_diag = nullptr;
+  int2* d_parts = nullptr;
+  std::vector<int> diag_off, diag_cnt, pan_off, pan_n, pan_cta, tr_off, tr_n, tr_cta;
+};
+
+void oz_factor_batched_free(OzBatchFactor* p) {
+  if (!p) return;
+  if (p->d_inst) cudaFree(p->d_inst);
+  if (p->d_diag) cudaFree(p->d_diag);
+  if (p->d_parts) cudaFree(p->d_parts);
+  delete p;
+}
+
+dngd_status oz_factor_batched_plan(OzBatchFactor** out, int n, OzFactor* const* f, int* const* status,
+                                   cudaStream_t st) {
+  *out = nullptr;
+  if (n < 1) return DNGD_ERR_INVALID_ARG;
+  OzBatchFactor* p = new OzBatchFactor();
+  p->n = n;
+  std::vector<BInst> hi(n);
+  int maxm = 0;
+  for (int b = 0; b < n; ++b) {
+    hi[b] = BInst{f[b]->C, f[b]->ldc, f[b]->m, status[b], f[b]->Ldf, f[b]->rdf, f[b]->Pdf};
+    maxm = std::max(maxm, f[b]->m);
+  }
+  p->steps = (maxm + FNB - 1) / FNB;
+  std::vector<int> diag;
+  std::vector<int2> parts;
+  for (int s = 0; s < p->steps; ++s) {
+    const int k0 = s * FNB;
+    p->diag_off.push_back((int)diag.size());
+    for (int b = 0; b < n; ++b)
+      if (hi[b].m > k0) diag.push_back(b);
+    p->diag_cnt.push_back((int)diag.size() - p->diag_off.back());
+    p->pan_off.push_back((int)parts.size());
+    int cta = 0;
+    for (int b = 0; b < n; ++b) {
+      const int r = hi[b].m - k0 - FNB;
+      if (r > 0) {
+        parts.push_back(make_int2(b, cta));
+        cta += (r + kPanelRows - 1) / kPanelRows;
+      }
+    }
+    p->pan_n.push_back((int)parts.size() - p->pan_off.back());
+    p->pan_cta.push_back(cta);
+    p->tr_off.push_back((int)parts.size());
+    cta = 0;
+    for (int b = 0; b < n; ++b) {
+      const int r = hi[b].m - k0 - FNB;
+      if (r > 0) {
+        parts.push_back(make_int2(b, cta));
+        cta += trail_units(r);
+      }
+    }
+    p->tr_n.push_back((int)parts.size() - p->tr_off.back());
+    p->tr_cta.push_back(cta);
+  }
+  if (cudaMalloc(&p->d_inst, sizeof(BInst) * n) != cudaSuccess ||
+      cudaMalloc(&p->d_diag, sizeof(int) * std::max<size_t>(1, diag.size())) != cudaSuccess ||
+      cudaMalloc(&p->d_parts, sizeof(int2) * std::max<size_t>(1, parts.size())) != cudaSuccess) {
+    oz_factor_batched_free(p);
+    return DNGD_ERR_OOM;
+  }
+  if (cudaMemcpyAsync(p->d_inst, hi.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (!diag.empty() &&
+       cudaMemcpyAsync(p->d_diag, diag.data(), sizeof(int) * diag.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      (!parts.empty() &&
+       cudaMemcpyAsync(p->d_parts, parts.data(), sizeof(int2) * parts.size(), cudaMemcpyHostToDevice, st) !=
+           cudaSuccess) ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    oz_factor_batched_free(p);
+    return DNGD_ERR_CUDA;
+  }
+  *out = p;
+  return DNGD_OK;
+}
+
+dngd_status oz_factor_batched_run(OzBatchFactor* p, cudaStream_t st) {
+  for (int s = 0; s < p->steps; ++s) {
+    const int k0 = s * FNB;
+    DNGD_NOTE_LAUNCH();
+    k_potrf_diag_df_b<<<p->diag_cnt[s], kDiagThreads, 0, st>>>(p->d_inst, p->d_diag + p->diag_off[s], k0);
+    DNGD_LAUNCH_CHECK();
+    if (p->pan_cta[s] > 0) {
+      DNGD_NOTE_LAUNCH();
+      k_trsm_panel_df_b<<<p->pan_cta[s], 128, 0, st>>>(p->d_inst, p->d_parts + p->pan_off[s], p->pan_n[s], k0);
+      DNGD_LAUNCH_CHECK();
+    }
+    if (p->tr_cta[s] > 0) {
+      DNGD_NOTE_LAUNCH();
+      k_trail_df_b<<<p->tr_cta[s], 256, 0, st>>>(p->d_inst, p->d_parts + p->tr_off[s], p->tr_n[s], k0);
+      DNGD_LAUNCH_CHECK();
+    }
+  }
+  return DNGD_OK;
+}
 
 // ---------------------------------------------------------------------------
 // FP64 GEMM from exact slice products: C = alpha A B^T + beta C

@@ -186,6 +186,15 @@ size_t oz_factor_bytes(int m);   // panel slices + row exponents + tile list
 dngd_status oz_factor_plan(OzFactor** plan, int m, double* C, long long ldc, void* work, cudaStream_t st);
 dngd_status oz_factor_run(OzFactor* plan, int* status, cudaStream_t st);
 void oz_factor_free(OzFactor* plan);
+// Batched factorisation of n independent instances (each with its own
+// OzFactor plan and status word): per 64-column step, one launch each for
+// every instance's diagonal block, panel solve and whole trailing update
+// (double-float).  A plan of one instance computes the same factor.
+struct OzBatchFactor;
+dngd_status oz_factor_batched_plan(OzBatchFactor** plan, int n, OzFactor* const* f, int* const* status,
+                                   cudaStream_t st);
+dngd_status oz_factor_batched_run(OzBatchFactor* plan, cudaStream_t st);
+void oz_factor_batched_free(OzBatchFactor* plan);
 
 // C = alpha A B^T + beta C in FP64 (A [M x K] ld lda; B [N x K] ld ldb, or
 // with b_kn B given as [K x N]) from four 8-bit slices of every row of A and

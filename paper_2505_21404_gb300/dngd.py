@@ -21,6 +21,7 @@ MAX_CLASSES = 4
 FP64, MIXED_BF16, MIXED_TF32, MIXED_OZ, MIXED_OZ64 = 0, 1, 2, 3, 4
 DENSE, PCG = 0, 1
 PCG_OP_TC3, PCG_OP_COMPENSATED = 0, 1
+FACTOR_SLICED, FACTOR_DF = 0, 1
 
 STATUS = {
     0: "DNGD_OK", -1: "DNGD_ERR_INVALID_ARG", -2: "DNGD_ERR_NOT_SPD", -3: "DNGD_ERR_NO_CONVERGE",
@@ -49,7 +50,7 @@ class ProblemDesc(C.Structure):
                 ("ga_ratio_max", C.c_double), ("refine_max_it", C.c_int), ("refine_tol", C.c_double),
                 ("shift_mu", C.c_double), ("pcg_rank", C.c_int), ("pcg_tol", C.c_double),
                 ("pcg_max_it", C.c_int), ("pcg_seed", C.c_uint64), ("keep_gram", C.c_int),
-                ("lambda_cap", C.c_double), ("pcg_operator", C.c_int)]
+                ("lambda_cap", C.c_double), ("pcg_operator", C.c_int), ("factor_update", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -192,11 +193,12 @@ def _ptr(a):
 
 def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_ratio_max=0.5, refine_max_it=200,
               refine_tol=1e-10, shift_mu=0.0, keep_gram=False, solver=DENSE, pcg_rank=512, pcg_tol=1e-6,
-              pcg_max_it=500, lambda_cap=0.0, pcg_operator=PCG_OP_TC3):
+              pcg_max_it=500, lambda_cap=0.0, pcg_operator=PCG_OP_TC3, factor_update=0):
     """Problem descriptor from a workload dict (see workloads.py).
     lambda_cap > 0 selects the damping rule lambda_k = min(L(theta_k), cap);
     pcg_operator: the matrix-free operator's GEMMs (PCG_OP_TC3 or
-    PCG_OP_COMPENSATED)."""
+    PCG_OP_COMPENSATED); factor_update: the exact-Gram factor's trailing
+    updates (FACTOR_SLICED or FACTOR_DF, what batches use)."""
     d = ProblemDesc()
     widths = list(spec["widths"])
     d.n_layers = len(widths) - 1
@@ -227,6 +229,7 @@ def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_rati
     d.keep_gram = int(bool(keep_gram))
     d.lambda_cap = float(lambda_cap)
     d.pcg_operator = int(pcg_operator)
+    d.factor_update = int(factor_update)
     return d
 
 

@@ -3,7 +3,9 @@
 Each instance of a batch must give the same result as the instance stepped
 alone: the batch only overlaps independent work on the device, it never
 changes what an instance computes (no batch-dependent split or reduction
-order)."""
+order).  Exact-Gram instances are factored together by the batch, with
+double-float trailing updates (FACTOR_DF); the same instance stepped alone
+with that factor setting must agree bit for bit."""
 import numpy as np
 import pytest
 
@@ -116,7 +118,8 @@ def test_crowded_batch_equals_alone(dngd):
     for _ in range(3):      # synchronous first step, then the captured graph twice
         batch.step(ths, Xs, tgs, db)
     torch.cuda.synchronize()
-    alone = [dngd.Context(d) for d in descs]
+    alone = [dngd.Context(dngd.make_desc(wl, precision=dngd.MIXED_OZ, refine_tol=1e-8, refine_max_it=60,
+                                         factor_update=dngd.FACTOR_DF)) for wl in wls]
     da = [torch.zeros_like(d) for d in db]
     for i, c in enumerate(alone):
         for _ in range(2):      # the first call is synchronous and fixes the shift, as in the batch
@@ -125,3 +128,36 @@ def test_crowded_batch_equals_alone(dngd):
     torch.cuda.synchronize()
     for i in range(len(wls)):
         assert torch.equal(da[i], db[i]), i
+
+
+@pytest.mark.parametrize("prec", ["MIXED_OZ", "MIXED_OZ64"])
+def test_exact_gram_batch_matches_oracle(dngd, prec):
+    """A batch of uneven exact-Gram instances (the batched factorisation of
+    every instance in one launch per kernel and 64-column step): each
+    instance's captured step against the FP64 oracle, and its factor L against
+    the matrix it factors, K + (lambda + mu) I (a backward error)."""
+    wls = _instances()
+    descs = [dngd.make_desc(wl, precision=getattr(dngd, prec), refine_tol=1e-10, refine_max_it=200) for wl in wls]
+    batch = dngd.Batch(descs)
+    ths = [_t(wl["theta"]) for wl in wls]
+    Xs = [_t(wl["X"]) for wl in wls]
+    tgs = [_t(wl["target"]) for wl in wls]
+    ds = [torch.zeros(len(wl["theta"]), dtype=torch.float64, device=DEV) for wl in wls]
+    for _ in range(3):      # synchronous first step, then the captured graph twice
+        infos = batch.step(ths, Xs, tgs, ds)
+    torch.cuda.synchronize()
+    for i, (wl, d) in enumerate(zip(wls, ds)):
+        ref = ostep.dense_step(wl["theta"], ores.problem_from_spec(wl), wl["X"], wl["target"], wl["lam"])
+        err = float(np.linalg.norm(d.cpu().numpy() - ref["delta"]) / np.linalg.norm(ref["delta"]))
+        assert err <= 1e-4, (i, err)
+        c = batch.context(i)
+        m = c.m
+        K = torch.zeros(m, m, dtype=torch.float64, device=DEV)
+        L = torch.zeros(m, m, dtype=torch.float64, device=DEV)
+        c.get_stage("gram64", K)
+        c.get_stage("chol64", L)
+        torch.cuda.synchronize()
+        Kh, Lh = K.cpu().numpy(), L.cpu().numpy()
+        assert np.all(np.triu(Lh, 1) == 0) and np.all(np.diag(Lh) > 0)
+        Ks = Kh + (wl["lam"] + infos[i]["shift_used"]) * np.eye(m)
+        assert np.linalg.norm(Lh @ Lh.T - Ks) <= 1e-11 * np.linalg.norm(Ks), i

@@ -117,11 +117,12 @@ def _oz_gram_bound(J, ns=4):
     return 2.0 ** -(8 * ns + 1) * (np.outer(l1, s) + np.outer(s, l1)) + n * t * np.outer(s, s)
 
 
-def _oz_case(dngd, wl, sample=None, seed=0, prec="MIXED_OZ", step_tol=1e-4):
+def _oz_case(dngd, wl, sample=None, seed=0, prec="MIXED_OZ", step_tol=1e-4, factor_update=0):
     ns = 4                       # slices per entry (both modes)
     prob = ores.problem_from_spec(wl)
     ref = ostep.dense_step(wl["theta"], prob, wl["X"], wl["target"], wl["lam"], use_ga=True)
-    ctx = dngd.Context(dngd.make_desc(wl, precision=getattr(dngd, prec), refine_tol=1e-10, refine_max_it=400))
+    ctx = dngd.Context(dngd.make_desc(wl, precision=getattr(dngd, prec), refine_tol=1e-10, refine_max_it=400,
+                                      factor_update=factor_update))
     delta = torch.zeros(ctx.n, dtype=torch.float64, device=DEV)
     info = ctx.step(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), delta)
     st = _stages(ctx, ["v", "a", "alpha", "beta"])
@@ -205,11 +206,15 @@ def test_dense_step_oz64(dngd, case):
     _oz_case(dngd, OZ64_CASES[case](), prec="MIXED_OZ64", step_tol=1e-5)
 
 
-@pytest.mark.parametrize("prec", ["MIXED_OZ", "MIXED_OZ64"])
-def test_dense_step_oz_m2000(dngd, prec):
-    """5-D Poisson, MLP 5-128-128-128-1 (n = 33,921), 1,500 + 500 points."""
+@pytest.mark.parametrize("prec,factor", [("MIXED_OZ", "FACTOR_SLICED"), ("MIXED_OZ64", "FACTOR_SLICED"),
+                                         ("MIXED_OZ64", "FACTOR_DF")])
+def test_dense_step_oz_m2000(dngd, prec, factor):
+    """5-D Poisson, MLP 5-128-128-128-1 (n = 33,921), 1,500 + 500 points;
+    both forms of the factor's trailing updates (sliced tensor-core products
+    with look-ahead, or double-float as in batches)."""
     wl = workloads.poisson_sine(5, [5, 128, 128, 128, 1], 1500, 500, k=1, seed=8, lam=1e-5)
-    _oz_case(dngd, wl, prec=prec, step_tol=1e-4 if prec == "MIXED_OZ" else 1e-5)
+    _oz_case(dngd, wl, prec=prec, step_tol=1e-4 if prec == "MIXED_OZ" else 1e-5,
+             factor_update=getattr(dngd, factor))
 
 
 @pytest.mark.parametrize("prec", ["MIXED_OZ", "MIXED_OZ64"])
