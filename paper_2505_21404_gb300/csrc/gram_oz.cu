@@ -986,7 +986,9 @@ int gram_oz_nsplit(const OzPlan* p) { return p->nsplit; }
 void gram_oz_set_fp64_out(OzPlan* p, double* Kd) { p->Kd = Kd; }
 
 // ---------------------------------------------------------------------------
-// FP64 blocked Cholesky with exact sliced trailing updates
+// Blocked Cholesky of an FP64 matrix: double-float diagonal blocks, panel
+// solves and the first 64 columns of each trailing update; the rest of each
+// update from exact slice products on the tensor cores (look-ahead)
 // ---------------------------------------------------------------------------
 
 namespace {

@@ -177,10 +177,12 @@ int gram_oz_nsplit(const OzPlan* plan);
 // when set (the FP64 factorisation's input), or not when Kd is null.
 void gram_oz_set_fp64_out(OzPlan* plan, double* Kd);
 
-// FP64 blocked Cholesky (64-column steps) of the lower triangle of C in
-// place, its trailing updates done exactly from six 8-bit slices per entry
-// of the panel on the BF16 tensor cores (products of levels <= 6, each entry
-// of the panel kept to 2^-49 of its row's largest).
+// Blocked Cholesky (64-column steps) of the lower triangle of the FP64
+// matrix C in place: diagonal blocks, panel solves and the first 64 columns
+// of each trailing update in double-float arithmetic (~2^-47); the rest of
+// each update exactly from six 8-bit slices per entry of the panel on the
+// BF16 tensor cores (products of levels <= 6, each entry kept to 2^-49 of
+// its row's largest), on a side stream beside the next step.
 struct OzFactor;
 size_t oz_factor_bytes(int m);   // panel slices + row exponents + tile list
 dngd_status oz_factor_plan(OzFactor** plan, int m, double* C, long long ldc, void* work, cudaStream_t st);
