@@ -53,7 +53,7 @@ WORKLOAD = "poisson5d_dense: -Lap u = f on [0,1]^5, MLP 5-256-256-256-1 (n=13337
 # DRAM bytes (read + write) of one exact-Gram product launch on the 5-D
 # workload, from an ncu capture of k_gram_oz (profiles/k_gram_oz_poisson5d_oz64.md);
 # keyed by --precision, valid for the kernel as committed with that summary.
-GRAM_TRAFFIC = {"oz64": 33.01e9}
+GRAM_TRAFFIC = {"oz64": 39.47e9}
 
 
 def _peaks():
