@@ -526,7 +526,7 @@ dngd_status dngd_server_drain(dngd_server* server, double timeout_s);
  * which loads this library keeps until the process exits, so m is limited to
  * 2000; larger m returns DNGD_ERR_INVALID_ARG with a message on stderr.
  * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current).
  * All calls share the array and it keeps the last call's contents: calls that
  * overlap on the GPU (other streams, other threads) race on it.  The call
  * synchronises the stream and returns DNGD_ERR_TIMEOUT if a bounded wait in
