@@ -50,3 +50,25 @@ def test_host_only_calls(lib):
     bad = lib.make_desc(wl)
     bad.widths[bad.n_layers] = 2          # output width must be 1
     assert lib.dngd_num_params(bad) == -1
+
+
+def _enum_values(name):
+    src = open(os.path.join(ROOT, "include", "dngd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"enum\s+" + name + r"\s*\{(.*?)\}", src, flags=re.S).group(1)
+    return {k: int(v) for k, v in re.findall(r"(DNGD_\w+)\s*=\s*(-?\d+)", body)}
+
+
+def test_descriptor_enums_match_the_header(lib):
+    """The binding's constants for the descriptor's enum fields are the
+    header's values, and the descriptor's last field is where ctypes puts it
+    (the structure sizes agree field by field in the GPU tests)."""
+    fu = _enum_values("dngd_factor_update")
+    assert fu == {"DNGD_FACTOR_SLICED": lib.FACTOR_SLICED, "DNGD_FACTOR_DF": lib.FACTOR_DF}
+    po = _enum_values("dngd_pcg_operator")
+    assert po == {"DNGD_PCG_OP_TC3": lib.PCG_OP_TC3, "DNGD_PCG_OP_COMPENSATED": lib.PCG_OP_COMPENSATED}
+    from paper_2505_21404_gb300 import workloads
+    d = lib.make_desc(workloads.poisson5d_dense(), precision=lib.MIXED_OZ64, factor_update=lib.FACTOR_DF)
+    assert d.factor_update == lib.FACTOR_DF
+    names = [f[0] for f in lib.ProblemDesc._fields_]
+    assert names[-2:] == ["pcg_operator", "factor_update"]
