@@ -141,12 +141,15 @@ constexpr int KS = 32;                      // K per stage (64-byte rows, 64-byt
 constexpr int A_TILE = TM * 64;             // 8 KB
 constexpr uint32_t OTMEM = 512;             // NA accumulators of TN columns
 
-// Warps: 0 TMA, 1 MMA, then eight epilogue warps: two per TMEM lane
-// quadrant, each draining half of the tile's columns (cpw).
+// Warps: 0 TMA, 1 MMA, then the epilogue warps, epi_warps / 4 per TMEM lane
+// quadrant, each draining cpw of the tile's columns: eight for the Gram and
+// the GEMM; sixteen for the factor's sliced update, whose epilogue (seven
+// drains and the FP64 read-modify-write of C) sets the persistent kernel's
+// period per tile.
 template <int NS, int NG>
-__host__ __device__ constexpr int epi_warps() { return 8; }
+__host__ __device__ constexpr int epi_warps() { return NS == 6 ? 16 : 8; }
 template <int NS, int NG>
-__host__ __device__ constexpr int cpw() { return OzCfg<NS, NG>::TN / 2; }
+__host__ __device__ constexpr int cpw() { return OzCfg<NS, NG>::TN * 4 / epi_warps<NS, NG>(); }
 template <int NS, int NG>
 __host__ __device__ constexpr int othreads() { return 64 + 32 * epi_warps<NS, NG>(); }
 template <int NS, int NG>
@@ -154,9 +157,11 @@ __host__ __device__ constexpr int b_tile() { return OzCfg<NS, NG>::TN * 64; }
 template <int NS, int NG>
 __host__ __device__ constexpr int ostage() { return NS * (A_TILE + b_tile<NS, NG>()); }
 // The update configuration (six slices) also holds each epilogue warp's
-// 32 x 33 FP64 block of C.
+// 32 x (cpw + 1) FP64 block of C.
 template <int NS, int NG>
-__host__ __device__ constexpr int cstage() { return NS == 6 ? 8 * 32 * 33 * (int)sizeof(double) : 0; }
+__host__ __device__ constexpr int cstage() {
+  return NS == 6 ? epi_warps<NS, NG>() * 32 * (cpw<NS, NG>() + 1) * (int)sizeof(double) : 0;
+}
 template <int NS, int NG>
 __host__ __device__ constexpr int osmem() { return OzCfg<NS, NG>::OST * ostage<NS, NG>() + cstage<NS, NG>() + 1024; }
 
@@ -175,11 +180,11 @@ static_assert(OzCfg<4, 5>::hi(OzCfg<4, 5>::NA - 1) == 4 && OzCfg<4, 6>::hi(OzCfg
               "the accumulators cover every kept level");
 static_assert(osmem<4, 5>() <= 227 * 1024 && osmem<4, 6>() <= 227 * 1024 && osmem<6, 7>() <= 227 * 1024,
               "shared-memory ring too large");
-static_assert(epi_warps<6, 7>() * 32 * 33 * (int)sizeof(double) == cstage<6, 7>(),
+static_assert(epi_warps<6, 7>() * 32 * (cpw<6, 7>() + 1) * (int)sizeof(double) == cstage<6, 7>(),
               "the update epilogue keeps one block of C per epilogue warp");
-static_assert(cpw<6, 7>() == 32 && cpw<4, 5>() % 8 == 0 && cpw<4, 6>() % 8 == 0 && cpw<4, 5>() <= 64 &&
-                  cpw<4, 6>() <= 64,
-              "an epilogue warp drains whole 8-column blocks (32 for the update's staged sub-tile)");
+static_assert(cpw<6, 7>() % 8 == 0 && cpw<6, 7>() <= 32 && cpw<4, 5>() % 8 == 0 && cpw<4, 6>() % 8 == 0 &&
+                  cpw<4, 5>() <= 64 && cpw<4, 6>() <= 64,
+              "an epilogue warp drains whole 8-column blocks (at most 32 for the update's staged sub-tile)");
 static_assert(b_tile<4, 5>() % 1024 == 0 && b_tile<4, 6>() % 1024 == 0 && b_tile<6, 7>() % 1024 == 0,
               "tiles keep 1024-byte alignment");
 
@@ -498,18 +503,18 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     int2 tcur = PERSIST ? (my_tiles > 0 ? tiles[blockIdx.x] : make_int2(0, 0)) : tile;
     int row = tcur.x * TM + q * 32 + lane;
     int col0 = tcur.y * TN + cg * CPW;
-    // OZ_UPDATE: the warp's 32 x 32 sub-tile of C (lane = column) is copied
+    // OZ_UPDATE: the warp's 32 x cpw sub-tile of C (lane = column) is copied
     // into its own shared-memory block while the operands load and the MMAs
     // run
     double* cs = reinterpret_cast<double*>(smem_raw + (smem_base - smem_u32(smem_raw)) + OST * OSTAGE) +
-                 (warp - 2) * 32 * 33;
+                 (warp - 2) * 32 * (CPW + 1);
     auto prefetch_c = [&](int2 t) {
       const int col = t.y * TN + cg * CPW + lane;
 #pragma unroll 8
       for (int rr = 0; rr < 32; ++rr) {
         const int rw = t.x * TM + q * 32 + rr;
         if (lane < ncol && rw < m && col <= rw)
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(cs + rr * 33 + lane)),
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(cs + rr * (CPW + 1) + lane)),
                        "l"(epi.C + (long long)(row_off + rw) * epi.ldc + row_off + col)
                        : "memory");
       }
@@ -527,10 +532,10 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       const int ecl = (lane < ncol && col0 + lane < m) ? epi.rexpA[row_off + col0 + lane] : 0;
       // all 32 values first (branch-free; the rare ones that need the FP64
       // path are fixed up afterwards), then the read-modify-write
-      double vv[32];
+      double vv[CPW];
       unsigned slow = 0u;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < CPW; ++j) {
         const int ec = __shfl_sync(0xffffffffu, ecl, j);
         bool sl;
         vv[j] = df_to_double_try(hi[j], lo[j], er + ec - epi.eshift, sl);
@@ -538,15 +543,15 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       }
       if (__any_sync(0xffffffffu, slow != 0u)) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < CPW; ++j) {
           const int ec = __shfl_sync(0xffffffffu, ecl, j);
           if ((slow >> j) & 1u) vv[j] = df_to_double_slow(hi[j], lo[j], er + ec - epi.eshift);
         }
       }
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < CPW; ++j) {
         const int cj = col0 + j;
-        if (j < ncol && row < m && cj <= row) cs[lane * 33 + j] -= vv[j];
+        if (j < ncol && row < m && cj <= row) cs[lane * (CPW + 1) + j] -= vv[j];
       }
       __syncwarp();
       if (!*abort_flag && lane < ncol) {
@@ -554,7 +559,8 @@ k_gram_oz(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 #pragma unroll 8
         for (int rr = 0; rr < 32; ++rr) {
           const int rw = tcur.x * TM + q * 32 + rr;
-          if (rw < m && col <= rw) epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] = cs[rr * 33 + lane];
+          if (rw < m && col <= rw)
+            epi.C[(long long)(row_off + rw) * epi.ldc + row_off + col] = cs[rr * (CPW + 1) + lane];
         }
       }
       __syncwarp();
