@@ -223,7 +223,7 @@ __device__ __forceinline__ dfloat df_sub_mul(dfloat acc, dfloat a, dfloat b) {
 // from the single-precision reciprocal, the residual 1 - d y formed in
 // double-float.
 __device__ __forceinline__ dfloat df_rcp(dfloat d) {
-  const float y = 1.0f / d.hi;
+  const float y = __frcp_rn(d.hi);   // the correctly rounded reciprocal, as 1.0f / d.hi
   const float r = fmaf(-d.hi, y, 1.0f) - d.lo * y;   // 1 - d y (the first term exact)
   const float c = y * r;
   const float hi = y + c;
