@@ -142,12 +142,13 @@ constexpr int A_TILE = TM * 64;             // 8 KB
 constexpr uint32_t OTMEM = 512;             // NA accumulators of TN columns
 
 // Warps: 0 TMA, 1 MMA, then the epilogue warps, epi_warps / 4 per TMEM lane
-// quadrant, each draining cpw of the tile's columns: eight for the Gram and
-// the GEMM; sixteen for the factor's sliced update, whose epilogue (seven
-// drains and the FP64 read-modify-write of C) sets the persistent kernel's
-// period per tile.
+// quadrant, each draining cpw of the tile's columns: sixteen for the FP64-J
+// Gram and GEMM and for the factor's sliced update (shorter drains, so an
+// accumulator that starts a new chunk waits less; in the update the
+// epilogue sets the persistent kernel's period per tile), eight for the
+// FP32-J Gram.
 template <int NS, int NG>
-__host__ __device__ constexpr int epi_warps() { return NS == 6 ? 16 : 8; }
+__host__ __device__ constexpr int epi_warps() { return (NS == 6 || NG == 6) ? 16 : 8; }
 template <int NS, int NG>
 __host__ __device__ constexpr int cpw() { return OzCfg<NS, NG>::TN * 4 / epi_warps<NS, NG>(); }
 template <int NS, int NG>
