@@ -72,3 +72,18 @@ def test_descriptor_enums_match_the_header(lib):
     assert d.factor_update == lib.FACTOR_DF
     names = [f[0] for f in lib.ProblemDesc._fields_]
     assert names[-2:] == ["pcg_operator", "factor_update"]
+
+
+def test_descriptor_validation_before_any_device_work(lib):
+    """dngd_create refuses out-of-range enum fields before it touches the
+    device (so this runs without a GPU)."""
+    import ctypes as C
+    from paper_2505_21404_gb300 import workloads
+    wl = workloads.poisson_sine(2, [2, 8, 8, 1], 30, 10, k=1, seed=0, lam=1e-5)
+    for field, bad in (("factor_update", 2), ("factor_update", -1), ("pcg_operator", 2), ("precision", 9),
+                       ("solver", 3)):
+        d = lib.make_desc(wl, precision=lib.MIXED_OZ64)
+        setattr(d, field, bad)
+        h = C.c_void_p()
+        assert lib.lib.dngd_create(C.byref(h), C.byref(d), None) == -1, (field, bad)
+        assert not h.value
