@@ -161,3 +161,34 @@ def test_exact_gram_batch_matches_oracle(dngd, prec):
         assert np.all(np.triu(Lh, 1) == 0) and np.all(np.diag(Lh) > 0)
         Ks = Kh + (wl["lam"] + infos[i]["shift_used"]) * np.eye(m)
         assert np.linalg.norm(Lh @ Lh.T - Ks) <= 1e-11 * np.linalg.norm(Ks), i
+
+
+def test_exact_gram_batch_block_edges(dngd):
+    """Instances at the 64-column step boundaries (m = 40, 64, 65, 129: a
+    diagonal block alone, one full block, a one-row panel, a trailing block of
+    one row) in one batched factorisation: each step against the oracle and
+    each factor against the matrix it factors."""
+    wls = [workloads.poisson_sine(2, [2, 16, 16, 1], m - round(0.2 * m), round(0.2 * m), k=2, seed=3000 + m,
+                                  lam=1e-5) for m in (40, 64, 65, 129)]
+    descs = [dngd.make_desc(wl, precision=dngd.MIXED_OZ64, refine_tol=1e-10, refine_max_it=200) for wl in wls]
+    batch = dngd.Batch(descs)
+    ths = [_t(wl["theta"]) for wl in wls]
+    Xs = [_t(wl["X"]) for wl in wls]
+    tgs = [_t(wl["target"]) for wl in wls]
+    ds = [torch.zeros(len(wl["theta"]), dtype=torch.float64, device=DEV) for wl in wls]
+    for _ in range(2):      # synchronous first step, then the captured graph
+        infos = batch.step(ths, Xs, tgs, ds)
+    torch.cuda.synchronize()
+    for i, (wl, d) in enumerate(zip(wls, ds)):
+        ref = ostep.dense_step(wl["theta"], ores.problem_from_spec(wl), wl["X"], wl["target"], wl["lam"])
+        err = float(np.linalg.norm(d.cpu().numpy() - ref["delta"]) / np.linalg.norm(ref["delta"]))
+        assert err <= 1e-6, (i, err)
+        c = batch.context(i)
+        K = torch.zeros(c.m, c.m, dtype=torch.float64, device=DEV)
+        L = torch.zeros(c.m, c.m, dtype=torch.float64, device=DEV)
+        c.get_stage("gram64", K)
+        c.get_stage("chol64", L)
+        torch.cuda.synchronize()
+        Kh, Lh = K.cpu().numpy(), L.cpu().numpy()
+        Ks = Kh + (wl["lam"] + infos[i]["shift_used"]) * np.eye(c.m)
+        assert np.linalg.norm(Lh @ Lh.T - Ks) <= 1e-11 * np.linalg.norm(Ks), i
