@@ -557,6 +557,69 @@ def run_c1(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
+def run_regime(args, rank, world, local_rank):
+    """Primal vs dual regime map (Sec. 3, primal vs dual perspectives; the
+    appendix's Navier-Stokes (m x n) sweep): the FP64 dense step solved in parameter space
+    ((J^T J + lambda I), n x n) and in residual space ((J J^T + lambda I),
+    m x m) on a grid of (m, n), each timed with CUDA events over --steps
+    steps after the warm-up.  Synthetic 2-D Poisson residuals on MLPs
+    2-w-w-1 (n = w^2 + 5w + 1) stand in for the paper's Navier-Stokes sweep."""
+    import torch
+    from paper_2505_21404_gb300 import dngd, workloads
+    torch.cuda.set_device(local_rank)
+    dev = torch.device(f"cuda:{local_rank}")
+    stream = torch.cuda.current_stream(dev)
+    ms_grid = [300, 1800, 3300, 6300]
+    ws = [15, 51, 71]                      # n = 301, 2,857, 5,397
+    steps = max(1, min(args.steps, 3))
+    cells = []
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    l0 = dngd.dngd_launch_count()
+    for m in ms_grid:
+        for w in ws:
+            ni = (4 * m) // 5
+            wl = workloads.poisson_sine(2, [2, w, w, 1], ni, m - ni, k=2, seed=m + w, lam=1e-5)
+            n = len(wl["theta"])
+            th, X, tg = (torch.tensor(np.ascontiguousarray(wl[k]), device=dev) for k in ("theta", "X", "target"))
+            cell = {"m": m, "n": n}
+            outs = {}
+            for name, space in (("primal", dngd.SPACE_PRIMAL), ("dual", dngd.SPACE_DUAL)):
+                ctx = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64, solve_space=space),
+                                   stream=stream.cuda_stream)
+                delta = torch.zeros(n, dtype=torch.float64, device=dev)
+                for _ in range(args.warmup):
+                    ctx.step(th, X, tg, delta, want_info=False)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                ev0.record(stream)
+                for _ in range(steps):
+                    ctx.step(th, X, tg, delta, want_info=False)
+                ev1.record(stream)
+                torch.cuda.synchronize(dev)
+                cell[name + "_ms"] = ev0.elapsed_time(ev1) / steps
+                outs[name] = delta.cpu().numpy()
+                ctx.close()
+            cell["winner"] = "primal" if cell["primal_ms"] < cell["dual_ms"] else "dual"
+            cell["auto"] = "primal" if n < m else "dual"
+            cell["step_diff"] = float(np.linalg.norm(outs["primal"] - outs["dual"]) / np.linalg.norm(outs["dual"]))
+            cells.append(cell)
+    launches = dngd.dngd_launch_count() - l0
+    clk = clocks.stop()
+    agree = sum(c["winner"] == c["auto"] for c in cells)
+    line = {
+        "metric": "automatic space choice = faster space (cells)", "value": agree / len(cells), "unit": "fraction",
+        "n_gpus": 1, "steps": steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "regime_map: 2-D Poisson, MLP 2-w-w-1 (w = 15, 51, 71), m = 300-6300 points, "
+                               "lambda = 1e-5, GA on, FP64 dense step in both spaces",
+                   "l2": "each cell's timed steps repeat the step; no flush (the spaces are compared, not the "
+                         "roofline)"},
+        "cells": cells, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def run_serving(args, rank, world, local_rank):
     """Serving loop: an arrival stream of PINN solve jobs (exponential
     inter-arrival times; 2-D / 5-D Poisson 50/50, k ~ U{1..8},
@@ -659,10 +722,11 @@ def main():
     ap.add_argument("--refine-tol", type=float, default=1e-5)
     ap.add_argument("--workload", default="poisson5d",
                     choices=["poisson5d", "poisson5d_w128", "poisson2d_fp64", "poisson2d_batch", "heat_pcg",
-                             "serving"],
+                             "serving", "regime_map"],
                     help="poisson5d (default, the headline): dense 5-D step; poisson5d_w128: same points, hidden "
                          "width 128 (profiling case); poisson2d_batch: 64 independent 2-D instances stepped as one "
-                         "graph; heat_pcg: matrix-free Nystrom-PCG step of the 1+1-D heat problem (n = 12.6M)")
+                         "graph; heat_pcg: matrix-free Nystrom-PCG step of the 1+1-D heat problem (n = 12.6M); regime_map: "
+                         "the FP64 step in parameter space vs residual space over a grid of (m, n)")
     ap.add_argument("--points", type=int, default=0,
                     help="poisson5d: total collocation points instead of 4,000 (3:1 interior:boundary; a smaller "
                          "case for profiler captures, not a bench line)")
@@ -695,6 +759,8 @@ def main():
         return run_heat(args, rank, world, local_rank)
     if args.workload == "serving":
         return run_serving(args, rank, world, local_rank)
+    if args.workload == "regime_map":
+        return run_regime(args, rank, world, local_rank)
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, wl)

@@ -115,6 +115,23 @@ enum dngd_factor_update {
                                    same factor as its batch */
 };
 
+/* Which form of the damped Gauss-Newton system the dense FP64 solver
+ * factors (dngd_problem_desc.solve_space).  Both give the same step: the
+ * dual (K + lambda I) y = r, v = -J^T y with K = J J^T [m x m] (Thm. 3.1,
+ * push-through), or the primal (J^T J + lambda I) v = -J^T r [n x n]
+ * (Prop. 3.1), and likewise the geodesic acceleration (Prop. 3.2: primal
+ * (J^T J + lambda I) a = -J^T f_vv; dual, in the push-through form this
+ * library uses, a = -J^T (K + lambda I)^{-1} f_vv).  The primal form costs
+ * O(m n^2 + n^3) time and n x n memory, the dual O(m^2 n + m^3) and m x m
+ * (Sec. 4.4), so the smaller of m and n decides which is cheaper. */
+enum dngd_solve_space {
+  DNGD_SPACE_DUAL = 0,          /* residual space (m x m) */
+  DNGD_SPACE_PRIMAL = 1,        /* parameter space (n x n); precision
+                                   DNGD_FP64 with solver DNGD_DENSE only */
+  DNGD_SPACE_AUTO = 2           /* primal when precision is DNGD_FP64, the
+                                   solver DNGD_DENSE and n < m; else dual */
+};
+
 /* GEMMs of the matrix-free operator (dngd_problem_desc.pcg_operator) */
 enum dngd_pcg_operator {
   DNGD_PCG_OP_TC3 = 0,          /* 3xTF32 on the tensor cores */
@@ -197,6 +214,11 @@ typedef struct {
                                         the exact Gram).  Batches of
                                         exact-Gram instances always use
                                         DNGD_FACTOR_DF. */
+  int solve_space;                   /* enum dngd_solve_space.  With the
+                                        primal space, the system dimension
+                                        of dngd_solve and of stages 6 and 7
+                                        is n instead of m, and stages 1 and
+                                        4 (the dual vectors) do not exist. */
 } dngd_problem_desc;
 
 typedef struct {
@@ -274,8 +296,14 @@ dngd_status dngd_step(dngd_ctx* ctx, const double* theta, const double* X, const
 
 /* Solve (K + lambda I) x = rhs with the factor / preconditioner of the last
  * dngd_step (Remark 3.1: the GA solve reuses the same operator).
- * rhs [m] -> x [m], float64.  Errors: STATE if no step was taken. */
+ * rhs [m] -> x [m], float64; a context in the primal space solves
+ * (J^T J + lambda I) x = rhs, rhs [n] -> x [n].  Errors: STATE if no step
+ * was taken. */
 dngd_status dngd_solve(dngd_ctx* ctx, const double* rhs, double* x_out);
+
+/* The space a context's dense solver works in (enum dngd_solve_space:
+ * DNGD_SPACE_AUTO resolved at dngd_create), or -1 for a NULL context. */
+int dngd_solve_space_of(const dngd_ctx* ctx);
 
 /* Loss L(theta + eta_j delta) = 1/2 ||r||^2 for k step sizes (the line search
  * of Alg. D-NGD Workflow).  etas [k] host array; loss_out [k] host array.
@@ -357,6 +385,8 @@ dngd_status dngd_fvv(dngd_ctx* ctx, const double* theta, const double* X, const 
  *         6 lower triangle of K + lambda I [m x m] row-major (dense, before
  *           factorisation; the upper triangle is left as zero),
  *         7 Cholesky factor L [m x m] row-major (dense solver),
+ *           (6 and 7 in the primal space: J^T J + lambda I and its factor,
+ *           [n x n]; 1 and 4 then give DNGD_ERR_STATE),
  *         8 landmark columns K_{:,I} [m x ell] row-major (PCG solver),
  *         9 exact Gram J J^T [m x m] row-major, full symmetric, no lambda
  *           (DNGD_MIXED_OZ, DNGD_MIXED_OZ64),

@@ -78,7 +78,13 @@ struct dngd_ctx {
   cudaGraphExec_t pcg_chunk[2] = {nullptr, nullptr};
   double pcg_chunk_key[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};   // lambda, chunk, kernels, x
   double* Dinv = nullptr;     // FP64 path: inverses of the factor's 64 x 64 diagonal blocks
-  double* tw = nullptr;       // FP64 path: [2 m] triangular-solve work
+  double* tw = nullptr;       // FP64 path: [2 ms] triangular-solve work
+  // FP64 path: the dense system's space (Prop. 3.1 primal, n x n, or
+  // Thm. 3.1 dual, m x m) and its dimension ms; gp [n]: -J^T of the
+  // right-hand side of a primal solve
+  bool primal = false;
+  int ms = 0;
+  double* gp = nullptr;
   float* gram_partials = nullptr;
   size_t gram_partial_bytes = 0;
   GramPlan* gram = nullptr;
@@ -266,6 +272,19 @@ const double* in_ptr(dngd_ctx* c, const double* p, double* stage, size_t count) 
   return stage;
 }
 
+// The dense system's space: 1 primal (n x n, Prop. 3.1), 0 dual (m x m,
+// Thm. 3.1), -1 an invalid request.  Automatic: the smaller system, primal
+// only where it is built (FP64, dense solver).
+int resolve_space(const dngd_problem_desc* d, const NetInfo& net) {
+  const bool can = d->precision == DNGD_FP64 && d->solver == DNGD_DENSE;
+  switch (d->solve_space) {
+    case DNGD_SPACE_DUAL: return 0;
+    case DNGD_SPACE_PRIMAL: return can ? 1 : -1;
+    case DNGD_SPACE_AUTO: return can && net.n < net.m ? 1 : 0;
+    default: return -1;
+  }
+}
+
 dngd_status read_status(dngd_ctx* c) {
   DNGD_CUDA_CHECK(cudaMemcpyAsync(c->status_h, c->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   DNGD_CUDA_CHECK(cudaStreamSynchronize(c->st));
@@ -422,7 +441,7 @@ dngd_status solve_last(dngd_ctx* c, const double* b, double* x, int slot) {
   if (c->prec == DNGD_FP64) {
     c->iters[slot] = 0;
     c->relres[slot] = 0.0;
-    return chol_solve_f64_dinv(c->m, (const double*)c->K, c->ldk, c->Dinv, b, x, c->tw, c->tw + c->m, c->st);
+    return chol_solve_f64_dinv(c->ms, (const double*)c->K, c->ldk, c->Dinv, b, x, c->tw, c->tw + c->ms, c->st);
   }
   return pcg_mixed(c, b, x, slot);
 }
@@ -478,19 +497,25 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
     if ((s = apply_lambda_rule(c))) return s;
     evrec(c, 1);
   }
-  // K + lambda I (lower)
+  // K + lambda I (lower), or J^T J + lambda I in the primal space
   if (c->prec == DNGD_FP64) {
-    if ((s = gemm_nt<double>(m, m, n, 1.0, (const double*)c->J, c->ldJ, (const double*)c->J, c->ldJ, 0.0,
-                             (double*)c->K, c->ldk, true, c->st)))
+    const int ms = c->ms;
+    if (c->primal) {
+      if ((s = gemm_tn<double>(ms, ms, m, 1.0, (const double*)c->J, c->ldJ, (const double*)c->J, c->ldJ, 0.0,
+                               (double*)c->K, c->ldk, nullptr, c->st, true)))
+        return s;
+    } else if ((s = gemm_nt<double>(m, m, n, 1.0, (const double*)c->J, c->ldJ, (const double*)c->J, c->ldJ, 0.0,
+                                    (double*)c->K, c->ldk, true, c->st))) {
       return s;
+    }
     evrec(c, 8);
-    if ((s = add_diag<double>(m, (double*)c->K, c->ldk, c->lambda, c->st))) return s;
+    if ((s = add_diag<double>(ms, (double*)c->K, c->ldk, c->lambda, c->st))) return s;
     if (c->Kcopy)
-      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(double) * (size_t)m * c->ldk,
+      DNGD_CUDA_CHECK(cudaMemcpyAsync(c->Kcopy, c->K, sizeof(double) * (size_t)ms * c->ldk,
                                       cudaMemcpyDeviceToDevice, c->st));
     evrec(c, 2);
-    if ((s = cholesky<double>(m, (double*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
-    if ((s = trtri_diag64(m, (const double*)c->K, c->ldk, c->Dinv, c->st))) return s;
+    if ((s = cholesky<double>(ms, (double*)c->K, c->ldk, c->status, nullptr, c->st))) return s;
+    if ((s = trtri_diag64(ms, (const double*)c->K, c->ldk, c->Dinv, c->st))) return s;
   } else if (c->ozf) {
     // exact Gram: FP64 factor of K + (lambda + mu) I with exact sliced
     // trailing updates (mu = 0 unless that fails at the Gram's own accuracy);
@@ -602,8 +627,14 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
 factored:
   evrec(c, 3);
   // alpha = (K + lambda I)^{-1} r ; v = -J^T alpha
-  if ((s = solve_last(c, c->r, c->alpha, 0))) return s;
-  if ((s = jt_x<T>(c, c->alpha, -1.0, c->v))) return s;
+  // (primal: v = (J^T J + lambda I)^{-1} (-J^T r))
+  if (c->primal) {
+    if ((s = jt_x<T>(c, c->r, -1.0, c->gp))) return s;
+    if ((s = solve_last(c, c->gp, c->v, 0))) return s;
+  } else {
+    if ((s = solve_last(c, c->r, c->alpha, 0))) return s;
+    if ((s = jt_x<T>(c, c->alpha, -1.0, c->v))) return s;
+  }
   evrec(c, 4);
   if (c->desc.use_ga) {
     const T* vT;
@@ -617,8 +648,13 @@ factored:
                          c->status)))
       return s;
     evrec(c, 5);
-    if ((s = solve_last(c, c->fvv, c->beta, 1))) return s;
-    if ((s = jt_x<T>(c, c->beta, -1.0, c->a))) return s;
+    if (c->primal) {
+      if ((s = jt_x<T>(c, c->fvv, -1.0, c->gp))) return s;
+      if ((s = solve_last(c, c->gp, c->a, 1))) return s;
+    } else {
+      if ((s = solve_last(c, c->fvv, c->beta, 1))) return s;
+      if ((s = jt_x<T>(c, c->beta, -1.0, c->a))) return s;
+    }
     evrec(c, 6);
   } else {
     evrec(c, 5);
@@ -1000,7 +1036,9 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   auto add = [&](size_t b) { tot += (b + 255) & ~(size_t)255; };
   c->ldJ = f64 ? n : round_up(n, 64);
   c->ldb = round_up(n, 64);
-  c->ldk = round_up(m, 4);
+  const int ms = c->primal ? (int)n : m;          // FP64 system dimension
+  c->ms = ms;
+  c->ldk = round_up(f64 ? ms : m, 4);
   const bool oz = oz_mode(c->prec);
   const int ng = c->prec == DNGD_MIXED_OZ64 ? 6 : 5;   // exact-Gram levels kept
   const bool bf = c->prec == DNGD_MIXED_BF16;
@@ -1027,9 +1065,11 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   add(3 * rowbuf);        // H3b
   add(es * (size_t)m * c->ldJ);
   if (bf) add(sizeof(__nv_bfloat16) * (size_t)m * c->ldb);
-  add(ek * (size_t)m * c->ldk);
-  if (c->desc.keep_gram) add(ek * (size_t)m * c->ldk);
-  if (f64) add(sizeof(double) * ((size_t)cdiv(m, 64) * 64 * 64 + 2 * (size_t)m));   // Dinv, tw
+  const int mk = f64 ? ms : m;    // rows of K
+  add(ek * (size_t)mk * c->ldk);
+  if (c->desc.keep_gram) add(ek * (size_t)mk * c->ldk);
+  if (f64) add(sizeof(double) * ((size_t)cdiv(ms, 64) * 64 * 64 + 2 * (size_t)ms));   // Dinv, tw
+  if (c->primal) add(sizeof(double) * n);                                              // gp
   if (!f64) {
     add(ek * (size_t)m * c->ldk);                 // K0
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
@@ -1106,10 +1146,11 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     DNGD_CUDA_CHECK(cudaMemsetAsync(c->J, 0, sizeof(float) * (size_t)m * c->ldJ, c->st));
   }
   if (f64) {
-    A_(c->K, double, (size_t)m * c->ldk);
-    if (c->desc.keep_gram) A_(c->Kcopy, double, (size_t)m * c->ldk);
-    A_(c->Dinv, double, (size_t)cdiv(m, 64) * 64 * 64);
-    A_(c->tw, double, 2 * (size_t)m);
+    A_(c->K, double, (size_t)ms * c->ldk);
+    if (c->desc.keep_gram) A_(c->Kcopy, double, (size_t)ms * c->ldk);
+    A_(c->Dinv, double, (size_t)cdiv(ms, 64) * 64 * 64);
+    A_(c->tw, double, 2 * (size_t)ms);
+    if (c->primal) A_(c->gp, double, n);
   } else {
     if (bf) {
       A_(c->Jb, __nv_bfloat16, (size_t)m * c->ldb);
@@ -1274,6 +1315,9 @@ dngd_status dngd_workspace_bytes(const dngd_problem_desc* desc, size_t* bytes) {
   dngd_status s = build_net(desc, &tmp.net);
   if (s) return s;
   tmp.prec = desc->precision;
+  const int sp = resolve_space(desc, tmp.net);
+  if (sp < 0) return DNGD_ERR_INVALID_ARG;
+  tmp.primal = sp == 1;
   if (desc->solver == DNGD_PCG) return alloc_pcg(&tmp, true, bytes);
   return alloc_workspace(&tmp, true, bytes);
 }
@@ -1290,6 +1334,9 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
     return DNGD_ERR_INVALID_ARG;
   if (desc->factor_update != DNGD_FACTOR_SLICED && desc->factor_update != DNGD_FACTOR_DF)
     return DNGD_ERR_INVALID_ARG;
+  if (desc->solve_space < DNGD_SPACE_DUAL || desc->solve_space > DNGD_SPACE_AUTO ||
+      (desc->solve_space == DNGD_SPACE_PRIMAL && (desc->precision != DNGD_FP64 || desc->solver != DNGD_DENSE)))
+    return DNGD_ERR_INVALID_ARG;
   gemv_init();
   dngd_ctx* c = new dngd_ctx();
   c->desc = *desc;
@@ -1305,6 +1352,7 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
   c->prec = desc->precision;
   c->lambda = desc->lambda;
   c->pcg = desc->solver == DNGD_PCG;
+  c->primal = resolve_space(desc, c->net) == 1;   // valid: checked above
   if ((s = c->pcg ? alloc_pcg(c, false, nullptr) : alloc_workspace(c, false, nullptr))) {
     free_ctx(c);
     return s;
@@ -1312,6 +1360,8 @@ dngd_status dngd_create(dngd_ctx** out, const dngd_problem_desc* desc, void* str
   *out = c;
   return DNGD_OK;
 }
+
+int dngd_solve_space_of(const dngd_ctx* c) { return c ? (c->primal ? DNGD_SPACE_PRIMAL : DNGD_SPACE_DUAL) : -1; }
 
 dngd_status dngd_destroy(dngd_ctx* c) {
   if (!c) return DNGD_ERR_INVALID_ARG;
@@ -1359,6 +1409,12 @@ dngd_status dngd_step(dngd_ctx* c, const double* theta, const double* X, const d
 dngd_status dngd_solve(dngd_ctx* c, const double* rhs, double* x_out) {
   if (!c || !rhs || !x_out) return DNGD_ERR_INVALID_ARG;
   if (!c->have_step) return DNGD_ERR_STATE;
+  if (c->primal) {
+    const double* b = in_ptr(c, rhs, c->nvec_s, c->n);
+    dngd_status s = solve_last(c, b, c->gp, 0);
+    if (s) return s;
+    return out_copy(c, x_out, c->gp, c->n);
+  }
   const double* b = in_ptr(c, rhs, c->mvec_s, c->m);
   dngd_status s = solve_last(c, b, c->xsol, 0);
   if (s) return s;
@@ -1584,6 +1640,7 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
   if (!c || !dst) return DNGD_ERR_INVALID_ARG;
   if (!c->have_step) return DNGD_ERR_STATE;
   const int m = c->m;
+  if (c->primal && (which == 1 || which == 4)) return DNGD_ERR_STATE;
   switch (which) {
     case 0: return out_copy(c, dst, c->r, m);
     case 1: return out_copy(c, dst, c->alpha, m);
@@ -1601,12 +1658,13 @@ dngd_status dngd_get_stage(dngd_ctx* c, int which, double* dst) {
       if (!src) return DNGD_ERR_STATE;
       const bool k64 = which == 11 || (which != 10 && c->prec == DNGD_FP64);
       if (which == 7 && !k64) return DNGD_ERR_STATE;
+      const int d = c->prec == DNGD_FP64 ? c->ms : m;   // n in the primal space
       double* buf = nullptr;
-      if (cudaMalloc(&buf, sizeof(double) * (size_t)m * m) != cudaSuccess) return DNGD_ERR_OOM;
-      dngd_status s = k64 ? lower_to_f64<double>(m, (const double*)src, c->ldk, buf, c->st)
-                                           : lower_to_f64<float>(m, (const float*)src, c->ldk, buf, c->st);
+      if (cudaMalloc(&buf, sizeof(double) * (size_t)d * d) != cudaSuccess) return DNGD_ERR_OOM;
+      dngd_status s = k64 ? lower_to_f64<double>(d, (const double*)src, c->ldk, buf, c->st)
+                                           : lower_to_f64<float>(d, (const float*)src, c->ldk, buf, c->st);
       if (!s) {
-        cudaMemcpyAsync(dst, buf, sizeof(double) * (size_t)m * m, cudaMemcpyDefault, c->st);
+        cudaMemcpyAsync(dst, buf, sizeof(double) * (size_t)d * d, cudaMemcpyDefault, c->st);
         cudaStreamSynchronize(c->st);
       }
       cudaFree(buf);

@@ -56,10 +56,10 @@ dngd_status gemm_nn(int M, int N, int K, T alpha, const T* A, long long lda, con
                     T beta, T* C, long long ldc, cudaStream_t st);
 
 // C[M x N] = alpha * A^T diag(kscale) B + beta * C, A [K x M], B [K x N]
-// row-major; kscale [K] may be null.
+// row-major; kscale [K] may be null.  lower: as gemm_nt.
 template <typename T>
 dngd_status gemm_tn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb, T beta,
-                    T* C, long long ldc, const T* kscale, cudaStream_t st);
+                    T* C, long long ldc, const T* kscale, cudaStream_t st, bool lower = false);
 
 // FP32 GEMMs with compensated (Kahan over BK-slabs) accumulation.
 dngd_status gemm_nt_comp(int M, int N, int K, float alpha, const float* A, long long lda, const float* B,

@@ -172,21 +172,22 @@ dngd_status gemm_nn(int M, int N, int K, T alpha, const T* A, long long lda, con
 
 // C[M x N] = alpha * A^T B + beta * C with A [K x M], B [K x N] row-major and
 // an optional scale of A's rows (the K index): C = A^T diag(kscale) B.
+// lower: skip output tiles strictly above the diagonal (syrk-style use).
 template <typename T>
 dngd_status gemm_tn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb, T beta,
-                    T* C, long long ldc, const T* kscale, cudaStream_t st) {
+                    T* C, long long ldc, const T* kscale, cudaStream_t st, bool lower) {
   if (M <= 0 || N <= 0) return DNGD_OK;
   using G = GemmCfg<T>;
   dim3 grid(cdiv(N, G::BN), cdiv(M, G::BM));
   DNGD_NOTE_LAUNCH();
   k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN, false, true>
-      <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0,
-                                                          kscale);
+      <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                          lower ? 1 : 0, kscale);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
 template dngd_status gemm_tn<float>(int, int, int, float, const float*, long long, const float*, long long, float,
-                                    float*, long long, const float*, cudaStream_t);
+                                    float*, long long, const float*, cudaStream_t, bool);
 
 // FP32 GEMMs with compensated accumulation (64 x 128 tiles, 4 x 8 per thread).
 dngd_status gemm_nt_comp(int M, int N, int K, float alpha, const float* A, long long lda, const float* B,
@@ -211,7 +212,7 @@ dngd_status gemm_tn_comp(int M, int N, int K, float alpha, const float* A, long 
   return DNGD_OK;
 }
 template dngd_status gemm_tn<double>(int, int, int, double, const double*, long long, const double*, long long,
-                                     double, double*, long long, const double*, cudaStream_t);
+                                     double, double*, long long, const double*, cudaStream_t, bool);
 
 template dngd_status gemm_nt<double>(int, int, int, double, const double*, long long, const double*, long long,
                                      double, double*, long long, bool, cudaStream_t);

@@ -22,6 +22,7 @@ FP64, MIXED_BF16, MIXED_TF32, MIXED_OZ, MIXED_OZ64 = 0, 1, 2, 3, 4
 DENSE, PCG = 0, 1
 PCG_OP_TC3, PCG_OP_COMPENSATED = 0, 1
 FACTOR_SLICED, FACTOR_DF = 0, 1
+SPACE_DUAL, SPACE_PRIMAL, SPACE_AUTO = 0, 1, 2
 
 STATUS = {
     0: "DNGD_OK", -1: "DNGD_ERR_INVALID_ARG", -2: "DNGD_ERR_NOT_SPD", -3: "DNGD_ERR_NO_CONVERGE",
@@ -50,7 +51,8 @@ class ProblemDesc(C.Structure):
                 ("ga_ratio_max", C.c_double), ("refine_max_it", C.c_int), ("refine_tol", C.c_double),
                 ("shift_mu", C.c_double), ("pcg_rank", C.c_int), ("pcg_tol", C.c_double),
                 ("pcg_max_it", C.c_int), ("pcg_seed", C.c_uint64), ("keep_gram", C.c_int),
-                ("lambda_cap", C.c_double), ("pcg_operator", C.c_int), ("factor_update", C.c_int)]
+                ("lambda_cap", C.c_double), ("pcg_operator", C.c_int), ("factor_update", C.c_int),
+                ("solve_space", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -128,6 +130,7 @@ def _load():
         "dngd_set_lambda": (C.c_int, [P, C.c_double]),
         "dngd_step": (C.c_int, [P, P, P, P, P, C.POINTER(StepInfo)]),
         "dngd_solve": (C.c_int, [P, P, P]),
+        "dngd_solve_space_of": (C.c_int, [P]),
         "dngd_loss": (C.c_int, [P, P, P, P, P, D, C.c_int, D]),
         "dngd_line_search": (C.c_int, [P, P, P, P, P, D, C.c_int, P, D]),
         "dngd_residual_jacobian": (C.c_int, [P, P, P, P, P, P]),
@@ -166,7 +169,8 @@ def _load():
 lib = _load()
 
 EXPORTED = ["dngd_status_string", "dngd_version", "dngd_launch_count", "dngd_num_params", "dngd_create", "dngd_workspace_bytes",
-            "dngd_destroy", "dngd_set_timing", "dngd_set_lambda", "dngd_step", "dngd_solve", "dngd_loss",
+            "dngd_destroy", "dngd_set_timing", "dngd_set_lambda", "dngd_step", "dngd_solve", "dngd_solve_space_of",
+            "dngd_loss",
             "dngd_line_search", "dngd_residual_jacobian", "dngd_fvv", "dngd_get_stage",
             "dngd_gram_bf16_noalloc", "dngd_set_landmarks", "dngd_kvp", "dngd_precond_apply",
             "dngd_step_async", "dngd_step_wait", "dngd_batch_create", "dngd_batch_destroy", "dngd_batch_size",
@@ -193,12 +197,14 @@ def _ptr(a):
 
 def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_ratio_max=0.5, refine_max_it=200,
               refine_tol=1e-10, shift_mu=0.0, keep_gram=False, solver=DENSE, pcg_rank=512, pcg_tol=1e-6,
-              pcg_max_it=500, lambda_cap=0.0, pcg_operator=PCG_OP_TC3, factor_update=0):
+              pcg_max_it=500, lambda_cap=0.0, pcg_operator=PCG_OP_TC3, factor_update=0,
+              solve_space=SPACE_DUAL):
     """Problem descriptor from a workload dict (see workloads.py).
     lambda_cap > 0 selects the damping rule lambda_k = min(L(theta_k), cap);
     pcg_operator: the matrix-free operator's GEMMs (PCG_OP_TC3 or
     PCG_OP_COMPENSATED); factor_update: the exact-Gram factor's trailing
-    updates (FACTOR_SLICED or FACTOR_DF, what batches use)."""
+    updates (FACTOR_SLICED or FACTOR_DF, what batches use); solve_space: the
+    dense FP64 system's space (SPACE_DUAL, SPACE_PRIMAL or SPACE_AUTO)."""
     d = ProblemDesc()
     widths = list(spec["widths"])
     d.n_layers = len(widths) - 1
@@ -230,6 +236,7 @@ def make_desc(spec, precision=FP64, lam=None, use_ga=True, eps_norm=0.0, ga_rati
     d.lambda_cap = float(lambda_cap)
     d.pcg_operator = int(pcg_operator)
     d.factor_update = int(factor_update)
+    d.solve_space = int(solve_space)
     return d
 
 
@@ -288,6 +295,11 @@ class Context:
                            C.byref(info) if info is not None else None)
         _check(st, "dngd_step")
         return info.as_dict() if info is not None else None
+
+    @property
+    def solve_space(self):
+        """SPACE_PRIMAL or SPACE_DUAL (SPACE_AUTO resolved at creation)."""
+        return int(lib.dngd_solve_space_of(self._h))
 
     def solve(self, rhs, x_out):
         _check(lib.dngd_solve(self._h, _ptr(rhs), _ptr(x_out)), "dngd_solve")

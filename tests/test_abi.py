@@ -67,11 +67,14 @@ def test_descriptor_enums_match_the_header(lib):
     assert fu == {"DNGD_FACTOR_SLICED": lib.FACTOR_SLICED, "DNGD_FACTOR_DF": lib.FACTOR_DF}
     po = _enum_values("dngd_pcg_operator")
     assert po == {"DNGD_PCG_OP_TC3": lib.PCG_OP_TC3, "DNGD_PCG_OP_COMPENSATED": lib.PCG_OP_COMPENSATED}
+    sp = _enum_values("dngd_solve_space")
+    assert sp == {"DNGD_SPACE_DUAL": lib.SPACE_DUAL, "DNGD_SPACE_PRIMAL": lib.SPACE_PRIMAL,
+                  "DNGD_SPACE_AUTO": lib.SPACE_AUTO}
     from paper_2505_21404_gb300 import workloads
     d = lib.make_desc(workloads.poisson5d_dense(), precision=lib.MIXED_OZ64, factor_update=lib.FACTOR_DF)
     assert d.factor_update == lib.FACTOR_DF
     names = [f[0] for f in lib.ProblemDesc._fields_]
-    assert names[-2:] == ["pcg_operator", "factor_update"]
+    assert names[-3:] == ["pcg_operator", "factor_update", "solve_space"]
 
 
 def test_descriptor_validation_before_any_device_work(lib):
@@ -87,3 +90,31 @@ def test_descriptor_validation_before_any_device_work(lib):
         h = C.c_void_p()
         assert lib.lib.dngd_create(C.byref(h), C.byref(d), None) == -1, (field, bad)
         assert not h.value
+    # the primal space is built for the dense FP64 solver only
+    for prec, solver, space in ((lib.FP64, lib.DENSE, 3), (lib.FP64, lib.DENSE, -1),
+                                (lib.MIXED_OZ64, lib.DENSE, lib.SPACE_PRIMAL),
+                                (lib.MIXED_BF16, lib.PCG, lib.SPACE_PRIMAL)):
+        d = lib.make_desc(wl, precision=prec, solver=solver, solve_space=space)
+        h = C.c_void_p()
+        assert lib.lib.dngd_create(C.byref(h), C.byref(d), None) == -1, (prec, solver, space)
+        assert not h.value
+
+
+def test_primal_space_workspace(lib):
+    """The primal space sizes the FP64 system by n (Prop. 3.1: n x n), the
+    dual by m; automatic selection takes the smaller system (host-only
+    sizing, no device work)."""
+    from paper_2505_21404_gb300 import workloads
+    tall = workloads.poisson_sine(2, [2, 8, 8, 1], 400, 100, k=1, seed=0, lam=1e-5)     # n = 105 < m = 500
+    wide = workloads.poisson_sine(2, [2, 32, 32, 1], 40, 10, k=1, seed=0, lam=1e-5)     # n = 1,185 > m = 50
+    for wl in (tall, wide):
+        m = sum(c["count"] for c in wl["classes"])
+        n = lib.dngd_num_params(lib.make_desc(wl))
+        by = {sp: lib.dngd_workspace_bytes(lib.make_desc(wl, solve_space=sp))
+              for sp in (lib.SPACE_DUAL, lib.SPACE_PRIMAL, lib.SPACE_AUTO)}
+        # the system buffers (K, Dinv, solve work) differ by the dimension
+        assert (by[lib.SPACE_PRIMAL] < by[lib.SPACE_DUAL]) == (n < m)
+        assert by[lib.SPACE_AUTO] == min(by[lib.SPACE_PRIMAL], by[lib.SPACE_DUAL])
+        # the automatic choice stays dual outside the dense FP64 solver
+        d = lib.make_desc(wl, precision=lib.MIXED_OZ64, solve_space=lib.SPACE_AUTO)
+        assert lib.dngd_workspace_bytes(d) == lib.dngd_workspace_bytes(lib.make_desc(wl, precision=lib.MIXED_OZ64))
