@@ -132,3 +132,47 @@ def test_primal_solve_and_stages(dngd):
         with pytest.raises(dngd.DngdError) as e:
             ctx.get_stage(name, torch.zeros(ctx.m, dtype=torch.float64, device=DEV))
         assert e.value.status == -8   # DNGD_ERR_STATE
+
+
+def test_primal_async_and_training(dngd):
+    """The primal space through the captured asynchronous step (replays equal
+    the synchronous step bit for bit) and through dngd_train (equal to the
+    hand-written loop bit for bit, the loss decreasing).  After six D-NGD
+    iterations the primal and dual parameters agree within 1e-6: once the
+    first step is taken, cond(J^T J + lambda I) is 4e8-8e8 on this problem, so
+    each step of either space carries ~cond * 2^-53 ~ 1e-7 of rounding, and
+    the oracle's own primal and dual trajectories (FP64, the same line-search
+    choices) differ by 4.7e-8 after six iterations."""
+    from oracle import linesearch as olin
+    wl = CASES["p2d_n337"]()
+    th, X, tg = _t(wl["theta"]), _t(wl["X"]), _t(wl["target"])
+    ctx, d_sync, _ = _step(dngd, wl, dngd.SPACE_PRIMAL)
+    d = torch.zeros_like(d_sync)
+    for _ in range(3):      # the first asynchronous step runs synchronously, then graph replays
+        ctx.step_async(th, X, tg, d)
+        ctx.step_wait()
+        torch.cuda.synchronize()
+        assert torch.equal(d, d_sync)
+    etas = olin.grid()
+    thetas, losses = {}, {}
+    for name, space in (("primal", dngd.SPACE_PRIMAL), ("dual", dngd.SPACE_DUAL)):
+        desc = dngd.make_desc(wl, precision=dngd.FP64, solve_space=space)
+        # the loop by hand
+        c = dngd.Context(desc)
+        t_h = _t(wl["theta"])
+        dd = torch.zeros_like(t_h)
+        hand = []
+        for _ in range(6):
+            hand.append(c.step(t_h, X, tg, dd)["loss"])
+            c.line_search_async(t_h, X, tg, dd, etas)
+        torch.cuda.synchronize()
+        # the native loop
+        t_n = _t(wl["theta"])
+        res, hist = dngd.Context(desc).train(t_n, X, tg, 6)
+        torch.cuda.synchronize()
+        assert res["iters"] == 6
+        assert np.array_equal(hist, np.array(hand))
+        assert torch.equal(t_n, t_h)
+        thetas[name], losses[name] = t_n.cpu().numpy(), hist
+    assert losses["primal"][-1] < losses["primal"][0]
+    assert rel(thetas["primal"], thetas["dual"]) <= 1e-6
