@@ -598,6 +598,11 @@ def run_regime(args, rank, world, local_rank):
                 ev1.record(stream)
                 torch.cuda.synchronize(dev)
                 cell[name + "_ms"] = ev0.elapsed_time(ev1) / steps
+                # one more step with the phase events: the Gram GEMM (J^T J or J J^T, lower
+                # triangle) alone
+                ctx.set_timing(True)
+                inf = ctx.step(th, X, tg, delta)
+                cell[name + "_gram_ms"] = inf["phase_ms"][1]
                 outs[name] = delta.cpu().numpy()
                 ctx.close()
             cell["winner"] = "primal" if cell["primal_ms"] < cell["dual_ms"] else "dual"
@@ -607,6 +612,12 @@ def run_regime(args, rank, world, local_rank):
     launches = dngd.dngd_launch_count() - l0
     clk = clocks.stop()
     agree = sum(c["winner"] == c["auto"] for c in cells)
+    # FP64 rate of the Gram GEMMs: n(n+1)m flop (primal) or m(m+1)n flop (dual), the lower triangle
+    fp64_peak = 1250.0
+    for c in cells:
+        c["primal_gram_gflops"] = c["n"] * (c["n"] + 1) * c["m"] / (c["primal_gram_ms"] * 1e6)
+        c["dual_gram_gflops"] = c["m"] * (c["m"] + 1) * c["n"] / (c["dual_gram_ms"] * 1e6)
+    top = max(cells, key=lambda c: c["n"] * c["n"] * c["m"])
     line = {
         "metric": "automatic space choice = faster space (cells)", "value": agree / len(cells), "unit": "fraction",
         "n_gpus": 1, "steps": steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
@@ -615,7 +626,14 @@ def run_regime(args, rank, world, local_rank):
                                "lambda = 1e-5, GA on, FP64 dense step in both spaces",
                    "l2": "each cell's timed steps repeat the step; no flush (the spaces are compared, not the "
                          "roofline)"},
-        "cells": cells, "gpu_launches": int(launches), "clocks": clk,
+        "cells": cells,
+        "roofline": {"bound": "alu", "kernel": f"k_gemm<double> (A^T B, lower): J^T J of the primal step at "
+                                               f"m = {top['m']}, n = {top['n']}",
+                     "achieved": top["primal_gram_gflops"], "peak": fp64_peak, "unit": "GFLOP/s",
+                     "frac": top["primal_gram_gflops"] / fp64_peak,
+                     "peak_source": "GB300 FP64 rate: 152 SMs x 2 FP64 FMA/clock x 2,070 MHz (1.26 TFLOP/s)",
+                     "traffic": None},
+        "gpu_launches": int(launches), "clocks": clk,
     }
     print(json.dumps(line))
 

@@ -176,3 +176,29 @@ def test_primal_async_and_training(dngd):
         thetas[name], losses[name] = t_n.cpu().numpy(), hist
     assert losses["primal"][-1] < losses["primal"][0]
     assert rel(thetas["primal"], thetas["dual"]) <= 1e-6
+
+
+@pytest.mark.parametrize("m,w", [(6300, 51), (3300, 51), (1800, 15)])
+def test_primal_dual_agree_at_regime_map_sizes(dngd, m, w):
+    """At the regime map's sizes (m = 6,300 and 3,300 with n = 2,857;
+    m = 1,800 with n = 301), where the oracle is too slow for a test, the two
+    spaces' steps agree within 1e-8 (push-through identity; cond(J^T J +
+    lambda I) at theta_0 is ~1e6 on these problems) and the primal step's
+    normal-equation residual ||(J^T J + lambda I) v + J^T r|| / ||J^T r|| is
+    at rounding level, with J and r read back from the context."""
+    ni = (4 * m) // 5
+    wl = workloads.poisson_sine(2, [2, w, w, 1], ni, m - ni, k=2, seed=m + w, lam=1e-5)
+    _, dp, _ = _step(dngd, wl, dngd.SPACE_PRIMAL)
+    cd, dd, _ = _step(dngd, wl, dngd.SPACE_DUAL)
+    n = cd.n
+    r = torch.zeros(m, dtype=torch.float64, device=DEV)
+    J = torch.zeros(m, n, dtype=torch.float64, device=DEV)
+    cd.residual_jacobian(_t(wl["theta"]), _t(wl["X"]), _t(wl["target"]), r, J)
+    cp, _, _ = _step(dngd, wl, dngd.SPACE_PRIMAL)
+    v = torch.zeros(n, dtype=torch.float64, device=DEV)
+    cp.get_stage("v", v)
+    torch.cuda.synchronize()
+    assert rel(dp, dd.cpu().numpy()) <= 1e-8
+    g = J.T @ r
+    res = J.T @ (J @ v) + wl["lam"] * v + g
+    assert float(torch.linalg.norm(res) / torch.linalg.norm(g)) <= 1e-7
