@@ -85,6 +85,7 @@ struct dngd_ctx {
   bool primal = false;
   int ms = 0;
   double* gp = nullptr;
+  double* gws = nullptr;      // FP64 path: the split Gram's partial products (null: one pass)
   float* gram_partials = nullptr;
   size_t gram_partial_bytes = 0;
   GramPlan* gram = nullptr;
@@ -500,14 +501,9 @@ dngd_status step_T(dngd_ctx* c, const double* theta, const double* X, const doub
   // K + lambda I (lower), or J^T J + lambda I in the primal space
   if (c->prec == DNGD_FP64) {
     const int ms = c->ms;
-    if (c->primal) {
-      if ((s = gemm_tn<double>(ms, ms, m, 1.0, (const double*)c->J, c->ldJ, (const double*)c->J, c->ldJ, 0.0,
-                               (double*)c->K, c->ldk, nullptr, c->st, true)))
-        return s;
-    } else if ((s = gemm_nt<double>(m, m, n, 1.0, (const double*)c->J, c->ldJ, (const double*)c->J, c->ldJ, 0.0,
-                                    (double*)c->K, c->ldk, true, c->st))) {
+    if ((s = gram_f64(c->primal, ms, c->primal ? m : n, (const double*)c->J, c->ldJ, (double*)c->K, c->ldk,
+                      c->gws, c->st)))
       return s;
-    }
     evrec(c, 8);
     if ((s = add_diag<double>(ms, (double*)c->K, c->ldk, c->lambda, c->st))) return s;
     if (c->Kcopy)
@@ -1070,6 +1066,8 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
   if (c->desc.keep_gram) add(ek * (size_t)mk * c->ldk);
   if (f64) add(sizeof(double) * ((size_t)cdiv(ms, 64) * 64 * 64 + 2 * (size_t)ms));   // Dinv, tw
   if (c->primal) add(sizeof(double) * n);                                              // gp
+  const int gsplit = f64 ? gram_f64_splits(ms, c->primal ? m : (int)n) : 1;
+  if (gsplit > 1) add(sizeof(double) * gsplit * (size_t)ms * c->ldk);                   // gws
   if (!f64) {
     add(ek * (size_t)m * c->ldk);                 // K0
     add(sizeof(float) * (size_t)m * c->ldk);      // Linv
@@ -1151,6 +1149,7 @@ dngd_status alloc_workspace(dngd_ctx* c, bool dry, size_t* bytes_out) {
     A_(c->Dinv, double, (size_t)cdiv(ms, 64) * 64 * 64);
     A_(c->tw, double, 2 * (size_t)ms);
     if (c->primal) A_(c->gp, double, n);
+    if (gsplit > 1) A_(c->gws, double, gsplit * (size_t)ms * c->ldk);
   } else {
     if (bf) {
       A_(c->Jb, __nv_bfloat16, (size_t)m * c->ldb);

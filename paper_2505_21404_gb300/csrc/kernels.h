@@ -61,6 +61,15 @@ template <typename T>
 dngd_status gemm_tn(int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb, T beta,
                     T* C, long long ldc, const T* kscale, cudaStream_t st, bool lower = false);
 
+// Lower triangle of the FP64 Gram C [M x M] = A^T A (at: A [K x M]) or
+// A A^T (A [M x K]), row-major.  With a workspace ws of gram_f64_splits(M, K)
+// x M x ldc doubles (when that is > 1) the K range is split over that many
+// slices of blocks, so that a small M still fills the GPU, and the slices'
+// partial products are added in a fixed order; ws = nullptr: one pass.
+int gram_f64_splits(int M, int K);
+dngd_status gram_f64(bool at, int M, int K, const double* A, long long lda, double* C, long long ldc, double* ws,
+                     cudaStream_t st);
+
 // FP32 GEMMs with compensated (Kahan over BK-slabs) accumulation.
 dngd_status gemm_nt_comp(int M, int N, int K, float alpha, const float* A, long long lda, const float* B,
                          long long ldb, float beta, float* C, long long ldc, cudaStream_t st);

@@ -21,11 +21,18 @@ namespace dngd {
 // plain accumulator, then added into (acc, cmp) with Kahan compensation, so
 // the error does not grow with K (used where the operator must stay
 // consistent over thousands of PCG applications).
+// kchunk > 0: split K; the block with blockIdx.z = z sums k in
+// [z kchunk, (z + 1) kchunk) and writes C + z cz (k_sum_splits adds the
+// partial products up in a fixed order).
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool BT, bool AT = false, bool COMP = false>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, const T* __restrict__ B,
-       long long ldb, T beta, T* __restrict__ C, long long ldc, int lower, const T* __restrict__ kscale = nullptr) {
+       long long ldb, T beta, T* __restrict__ C, long long ldc, int lower, const T* __restrict__ kscale = nullptr,
+       int kchunk = 0, long long cz = 0) {
   constexpr int NT = (BM / TM) * (BN / TN);
+  const int kb = kchunk > 0 ? (int)blockIdx.z * kchunk : 0;
+  const int ke = kchunk > 0 && kb + kchunk < K ? kb + kchunk : K;
+  C += (long long)blockIdx.z * cz;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
@@ -45,15 +52,15 @@ k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, con
 #pragma unroll
       for (int j = 0; j < (COMP ? TN : 1); ++j) cmp[i][j] = T(0);
   }
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  for (int k0 = kb; k0 < ke; k0 += BK) {
     if (AT) {
       // A is [K x M] row-major (C = A^T op(B)); optional per-k scale of A
 #pragma unroll
       for (int e = tid; e < BM * BK; e += NT) {
         const int kk = e / BM, r = e % BM;
         const int gr = bm + r, gk = k0 + kk;
-        T v = (gr < M && gk < K) ? A[(long long)gk * lda + gr] : T(0);
-        if (kscale && gk < K) v *= kscale[gk];
+        T v = (gr < M && gk < ke) ? A[(long long)gk * lda + gr] : T(0);
+        if (kscale && gk < ke) v *= kscale[gk];
         As[kk][r] = v;
       }
     } else {
@@ -61,7 +68,7 @@ k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, con
       for (int e = tid; e < BM * BK; e += NT) {
         const int r = e / BK, kk = e % BK;
         const int gr = bm + r, gk = k0 + kk;
-        As[kk][r] = (gr < M && gk < K) ? A[(long long)gr * lda + gk] : T(0);
+        As[kk][r] = (gr < M && gk < ke) ? A[(long long)gr * lda + gk] : T(0);
       }
     }
     if (BT) {
@@ -69,14 +76,14 @@ k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda, con
       for (int e = tid; e < BN * BK; e += NT) {
         const int c = e / BK, kk = e % BK;
         const int gc = bn + c, gk = k0 + kk;
-        Bs[kk][c] = (gc < N && gk < K) ? B[(long long)gc * ldb + gk] : T(0);
+        Bs[kk][c] = (gc < N && gk < ke) ? B[(long long)gc * ldb + gk] : T(0);
       }
     } else {
 #pragma unroll
       for (int e = tid; e < BN * BK; e += NT) {
         const int kk = e / BN, c = e % BN;
         const int gc = bn + c, gk = k0 + kk;
-        Bs[kk][c] = (gc < N && gk < K) ? B[(long long)gk * ldb + gc] : T(0);
+        Bs[kk][c] = (gc < N && gk < ke) ? B[(long long)gk * ldb + gc] : T(0);
       }
     }
     __syncthreads();
@@ -153,6 +160,56 @@ dngd_status gemm_nt(int M, int N, int K, T alpha, const T* A, long long lda, con
   k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN, true>
       <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
                                                           lower ? 1 : 0);
+  DNGD_LAUNCH_CHECK();
+  return DNGD_OK;
+}
+
+// C[r][c] = sum over s = 0..S-1 (in that order) of W[s][r][c], the lower
+// triangle (c <= r) of an M x M result.
+__global__ void k_sum_splits(int M, int S, const double* __restrict__ W, long long ldw, long long wz,
+                             double* __restrict__ C, long long ldc) {
+  const int r = blockIdx.y;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= r && c < M; c += gridDim.x * blockDim.x) {
+    double acc = W[(long long)r * ldw + c];
+    for (int z = 1; z < S; ++z) acc += W[(long long)z * wz + (long long)r * ldw + c];
+    C[(long long)r * ldc + c] = acc;
+  }
+}
+
+int gram_f64_splits(int M, int K) {
+  using G = GemmCfg<double>;
+  const int t = cdiv(M, G::BM);
+  const int tiles = t * (t + 1) / 2;                 // lower-triangle tiles
+  int S = cdiv(2 * 152, tiles);                      // about two blocks per SM
+  if (S > 16) S = 16;
+  if (S > K / 256) S = K / 256;                      // at least 256 k per split
+  return S < 1 ? 1 : S;
+}
+
+dngd_status gram_f64(bool at, int M, int K, const double* A, long long lda, double* C, long long ldc, double* ws,
+                     cudaStream_t st) {
+  if (M <= 0) return DNGD_OK;
+  using G = GemmCfg<double>;
+  const int S = ws ? gram_f64_splits(M, K) : 1;
+  if (S == 1)
+    return at ? gemm_tn<double>(M, M, K, 1.0, A, lda, A, lda, 0.0, C, ldc, nullptr, st, true)
+              : gemm_nt<double>(M, M, K, 1.0, A, lda, A, lda, 0.0, C, ldc, true, st);
+  const int kchunk = cdiv(cdiv(K, S), G::BK) * G::BK;
+  const int Sz = cdiv(K, kchunk);
+  const long long ldw = ldc, wz = (long long)M * ldw;
+  dim3 grid(cdiv(M, G::BN), cdiv(M, G::BM), Sz);
+  DNGD_NOTE_LAUNCH();
+  if (at)
+    k_gemm<double, G::BM, G::BN, G::BK, G::TM, G::TN, false, true>
+        <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, M, K, 1.0, A, lda, A, lda, 0.0, ws, ldw, 1,
+                                                            nullptr, kchunk, wz);
+  else
+    k_gemm<double, G::BM, G::BN, G::BK, G::TM, G::TN, true>
+        <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(M, M, K, 1.0, A, lda, A, lda, 0.0, ws, ldw, 1,
+                                                            nullptr, kchunk, wz);
+  DNGD_LAUNCH_CHECK();
+  DNGD_NOTE_LAUNCH();
+  k_sum_splits<<<dim3(cdiv(M, 256), M), 256, 0, st>>>(M, Sz, ws, ldw, wz, C, ldc);
   DNGD_LAUNCH_CHECK();
   return DNGD_OK;
 }
