@@ -571,44 +571,46 @@ def run_regime(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     ms_grid = [300, 1800, 3300, 6300]
     ws = [15, 51, 71]                      # n = 301, 2,857, 5,397
+    grid = [(m, w) for m in ms_grid for w in ws]
+    if args.cells:                         # a subset "m:w,m:w" (profiler captures)
+        grid = [tuple(int(x) for x in c.split(":")) for c in args.cells.split(",")]
     steps = max(1, min(args.steps, 3))
     cells = []
     clocks = ClockSampler(local_rank)
     clocks.start()
     l0 = dngd.dngd_launch_count()
-    for m in ms_grid:
-        for w in ws:
-            ni = (4 * m) // 5
-            wl = workloads.poisson_sine(2, [2, w, w, 1], ni, m - ni, k=2, seed=m + w, lam=1e-5)
-            n = len(wl["theta"])
-            th, X, tg = (torch.tensor(np.ascontiguousarray(wl[k]), device=dev) for k in ("theta", "X", "target"))
-            cell = {"m": m, "n": n}
-            outs = {}
-            for name, space in (("primal", dngd.SPACE_PRIMAL), ("dual", dngd.SPACE_DUAL)):
-                ctx = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64, solve_space=space),
-                                   stream=stream.cuda_stream)
-                delta = torch.zeros(n, dtype=torch.float64, device=dev)
-                for _ in range(args.warmup):
-                    ctx.step(th, X, tg, delta, want_info=False)
-                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize(dev)
-                ev0.record(stream)
-                for _ in range(steps):
-                    ctx.step(th, X, tg, delta, want_info=False)
-                ev1.record(stream)
-                torch.cuda.synchronize(dev)
-                cell[name + "_ms"] = ev0.elapsed_time(ev1) / steps
-                # one more step with the phase events: the Gram GEMM (J^T J or J J^T, lower
-                # triangle) alone
-                ctx.set_timing(True)
-                inf = ctx.step(th, X, tg, delta)
-                cell[name + "_gram_ms"] = inf["phase_ms"][1]
-                outs[name] = delta.cpu().numpy()
-                ctx.close()
-            cell["winner"] = "primal" if cell["primal_ms"] < cell["dual_ms"] else "dual"
-            cell["auto"] = "primal" if n < m else "dual"
-            cell["step_diff"] = float(np.linalg.norm(outs["primal"] - outs["dual"]) / np.linalg.norm(outs["dual"]))
-            cells.append(cell)
+    for m, w in grid:
+        ni = (4 * m) // 5
+        wl = workloads.poisson_sine(2, [2, w, w, 1], ni, m - ni, k=2, seed=m + w, lam=1e-5)
+        n = len(wl["theta"])
+        th, X, tg = (torch.tensor(np.ascontiguousarray(wl[k]), device=dev) for k in ("theta", "X", "target"))
+        cell = {"m": m, "n": n}
+        outs = {}
+        for name, space in (("primal", dngd.SPACE_PRIMAL), ("dual", dngd.SPACE_DUAL)):
+            ctx = dngd.Context(dngd.make_desc(wl, precision=dngd.FP64, solve_space=space),
+                               stream=stream.cuda_stream)
+            delta = torch.zeros(n, dtype=torch.float64, device=dev)
+            for _ in range(args.warmup):
+                ctx.step(th, X, tg, delta, want_info=False)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            ev0.record(stream)
+            for _ in range(steps):
+                ctx.step(th, X, tg, delta, want_info=False)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            cell[name + "_ms"] = ev0.elapsed_time(ev1) / steps
+            # one more step with the phase events: the Gram GEMM (J^T J or J J^T, lower
+            # triangle) alone
+            ctx.set_timing(True)
+            inf = ctx.step(th, X, tg, delta)
+            cell[name + "_gram_ms"] = inf["phase_ms"][1]
+            outs[name] = delta.cpu().numpy()
+            ctx.close()
+        cell["winner"] = "primal" if cell["primal_ms"] < cell["dual_ms"] else "dual"
+        cell["auto"] = "primal" if n < m else "dual"
+        cell["step_diff"] = float(np.linalg.norm(outs["primal"] - outs["dual"]) / np.linalg.norm(outs["dual"]))
+        cells.append(cell)
     launches = dngd.dngd_launch_count() - l0
     clk = clocks.stop()
     agree = sum(c["winner"] == c["auto"] for c in cells)
@@ -749,6 +751,7 @@ def main():
                     help="poisson5d: total collocation points instead of 4,000 (3:1 interior:boundary; a smaller "
                          "case for profiler captures, not a bench line)")
     ap.add_argument("--ell", type=int, default=512, help="Nystrom landmarks for heat_pcg")
+    ap.add_argument("--cells", default="", help="regime_map: only these cells, 'm:w,m:w' (MLP 2-w-w-1)")
     ap.add_argument("--rates", default="0.1,0.3,1,5,200", help="serving: offered job arrival rates (jobs/s)")
     ap.add_argument("--window", type=float, default=20.0, help="serving: seconds per arrival rate")
     ap.add_argument("--slots", type=int, default=16, help="serving: concurrent jobs")
