@@ -624,8 +624,8 @@ def run_regime(args, rank, world, local_rank):
         "metric": "automatic space choice = faster space (cells)", "value": agree / len(cells), "unit": "fraction",
         "n_gpus": 1, "steps": steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "regime_map: 2-D Poisson, MLP 2-w-w-1 (w = 15, 51, 71), m = 300-6300 points, "
-                               "lambda = 1e-5, GA on, FP64 dense step in both spaces",
+        "config": {"workload": "regime_map: 2-D Poisson, MLP 2-w-w-1, lambda = 1e-5, GA on, FP64 dense step in "
+                               "both spaces, cells (m, w) = " + ", ".join(f"({m}, {w})" for m, w in grid),
                    "l2": "each cell's timed steps repeat the step; no flush (the spaces are compared, not the "
                          "roofline)"},
         "cells": cells,

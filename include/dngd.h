@@ -229,7 +229,9 @@ typedef struct {
   int ga_accepted;
   int solve_iters[2];       /* CG/refinement iterations for r and for f_vv */
   double solve_relres[2];   /* final ||rhs - A x|| / ||rhs|| */
-  int not_spd_column;       /* failing pivot column, or -1 */
+  int not_spd_column;       /* failing pivot column, or -1 (a parameter
+                               index in the primal space, whose factored
+                               system is J^T J + lambda I) */
   int device_status;        /* raw device status word */
   float phase_ms[8];        /* jets+J, Gram, factor, solve r, f_vv, solve f_vv,
                                finish, total (filled when timing is enabled) */
