@@ -557,6 +557,21 @@ def run_c1(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
+def _regime_grid(cells=""):
+    """Cells (m, w) of the regime map: m in {300, 1800, 3300, 6300} points by
+    hidden width w in {15, 51, 71} (n = w^2 + 5w + 1 = 301, 2,857, 5,397), or
+    the subset 'm:w,m:w' given on the command line."""
+    if cells:
+        out = []
+        for c in cells.split(","):
+            m, w = (int(x) for x in c.split(":"))
+            if m < 5 or w < 1:
+                raise ValueError(f"regime_map cell {c!r}: need m >= 5 points and width w >= 1")
+            out.append((m, w))
+        return out
+    return [(m, w) for m in (300, 1800, 3300, 6300) for w in (15, 51, 71)]
+
+
 def run_regime(args, rank, world, local_rank):
     """Primal vs dual regime map (Sec. 3, primal vs dual perspectives; the
     appendix's Navier-Stokes (m x n) sweep): the FP64 dense step solved in parameter space
@@ -569,11 +584,7 @@ def run_regime(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device(f"cuda:{local_rank}")
     stream = torch.cuda.current_stream(dev)
-    ms_grid = [300, 1800, 3300, 6300]
-    ws = [15, 51, 71]                      # n = 301, 2,857, 5,397
-    grid = [(m, w) for m in ms_grid for w in ws]
-    if args.cells:                         # a subset "m:w,m:w" (profiler captures)
-        grid = [tuple(int(x) for x in c.split(":")) for c in args.cells.split(",")]
+    grid = _regime_grid(args.cells)
     steps = max(1, min(args.steps, 3))
     cells = []
     clocks = ClockSampler(local_rank)

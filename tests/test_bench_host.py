@@ -24,3 +24,21 @@ def test_sub_workload_caps_at_class_size():
     sub = bench._sub_workload(wl, 5)
     assert [c["count"] for c in sub["classes"]] == [3, 5]
     assert sub["X"].shape == (8, 2)
+
+
+def test_regime_grid_cells():
+    """The regime map's default grid spans both sides of n = m (n = w^2 + 5w + 1
+    for the 2-w-w-1 MLP of a 2-D input), and a command-line subset is parsed
+    as given."""
+    import pytest
+    grid = bench._regime_grid()
+    assert len(grid) == 12
+    ns = {w: w * w + 5 * w + 1 for _, w in grid}
+    assert ns == {15: 301, 51: 2857, 71: 5397}
+    for w, n in ns.items():
+        d = len(workloads.poisson_sine(2, [2, w, w, 1], 8, 2, k=2, seed=0, lam=1e-5)["theta"])
+        assert d == n
+    assert any(ns[w] < m for m, w in grid) and any(ns[w] > m for m, w in grid)
+    assert bench._regime_grid("6300:15,300:71") == [(6300, 15), (300, 71)]
+    with pytest.raises(ValueError):
+        bench._regime_grid("4:15")
