@@ -572,6 +572,33 @@ def _regime_grid(cells=""):
     return [(m, w) for m in (300, 1800, 3300, 6300) for w in (15, 51, 71)]
 
 
+def _regime_cpu_baseline(m=1800, w=15, seconds=10.0):
+    """The FP64 oracle on the host cores for one regime-map cell: its dense
+    step (jets, J, dual solve and GA) and, on the same J, r and f_vv, the
+    primal solves, each repeated for about `seconds`."""
+    from oracle import residual as ores, step as ostep
+    from paper_2505_21404_gb300 import workloads
+    ni = (4 * m) // 5
+    wl = workloads.poisson_sine(2, [2, w, w, 1], ni, m - ni, k=2, seed=m + w, lam=1e-5)
+    prob = ores.problem_from_spec(wl)
+    t0, k_d = time.perf_counter(), 0
+    while k_d < 1 or time.perf_counter() - t0 < seconds / 2:
+        ref = ostep.dense_step(wl["theta"], prob, wl["X"], wl["target"], wl["lam"], use_ga=True)
+        k_d += 1
+    t_dual = (time.perf_counter() - t0) / k_d
+    t0, k_p = time.perf_counter(), 0
+    while k_p < 1 or time.perf_counter() - t0 < seconds / 2:
+        ostep.primal_step(ref["J"], ref["r"], wl["lam"])
+        ostep.primal_step(ref["J"], ref["fvv"], wl["lam"])
+        k_p += 1
+    t_primal_solves = (time.perf_counter() - t0) / k_p
+    return {"value": 1.0 / t_dual, "unit": "steps/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"m = {m}, n = {len(wl['theta'])}: {k_d} FP64 oracle dense steps (dual, GA) "
+                      f"{1e3 * t_dual:.1f} ms each; the two primal solves on the same J "
+                      f"{1e3 * t_primal_solves:.1f} ms ({k_p} repeats)",
+            "blas_threads": _threads()}
+
+
 def run_regime(args, rank, world, local_rank):
     """Primal vs dual regime map (Sec. 3, primal vs dual perspectives; the
     appendix's Navier-Stokes (m x n) sweep): the FP64 dense step solved in parameter space
@@ -624,6 +651,7 @@ def run_regime(args, rank, world, local_rank):
         cells.append(cell)
     launches = dngd.dngd_launch_count() - l0
     clk = clocks.stop()
+    cpu = None if args.no_oracle else _regime_cpu_baseline()
     agree = sum(c["winner"] == c["auto"] for c in cells)
     # FP64 rate of the Gram GEMMs: n(n+1)m flop (primal) or m(m+1)n flop (dual), the lower triangle
     fp64_peak = 1250.0
@@ -646,6 +674,7 @@ def run_regime(args, rank, world, local_rank):
                      "frac": top["primal_gram_gflops"] / fp64_peak,
                      "peak_source": "GB300 FP64 rate: 152 SMs x 2 FP64 FMA/clock x 2,070 MHz (1.26 TFLOP/s)",
                      "traffic": None},
+        "cpu_baseline": cpu,
         "gpu_launches": int(launches), "clocks": clk,
     }
     print(json.dumps(line))

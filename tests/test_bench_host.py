@@ -42,3 +42,10 @@ def test_regime_grid_cells():
     assert bench._regime_grid("6300:15,300:71") == [(6300, 15), (300, 71)]
     with pytest.raises(ValueError):
         bench._regime_grid("4:15")
+
+
+def test_regime_cpu_baseline_is_the_oracle():
+    """The regime map's host baseline times the FP64 oracle (a tiny cell)."""
+    cpu = bench._regime_cpu_baseline(m=60, w=4, seconds=0.1)
+    assert cpu["kind"] == "oracle" and cpu["unit"] == "steps/s" and cpu["value"] > 0
+    assert "n = 37" in cpu["sample"]          # 2-4-4-1 MLP: 4^2 + 5*4 + 1 parameters
